@@ -1,0 +1,226 @@
+/*
+ * levy_hmat.h -- C ABI of the GB300 (sm_103a) H-matrix Crank-Nicolson solver for
+ * convection-diffusion equations driven by a Levy process.
+ *
+ * Method: Xu & Darve, "Efficient Numerical Method for Models Driven by Levy
+ * Process via Hierarchical Matrices" (arXiv 1812.08324).
+ *
+ *   u_t = a u_xx + b u_x + c u + L u,  L u = int (u(x+y) - u(x) - ...) nu(y) dy
+ *                                           (Sec. "Model Problem", Eq. ut)
+ *
+ * discretised on a uniform interior grid with u = 0 outside the domain into a
+ * dense generator G (Eq. Aij with G = -A, trapezoidal jump sum Eq. dl, and the
+ * singularity subtraction of Eqs. I1approx-I3approx for singular nu), stored
+ * as an H-matrix (App. "H Matrix", Sec. "Construction and Storage"), factored
+ * by H-LU (App. "LU Decomposition") and advanced by Crank-Nicolson
+ * (Eq. scheme):  (I - dt/2 G) u^{n+1} = (I + dt/2 G) u^n + dt/2 (f^n + f^{n+1}).
+ *
+ * Conventions for every entry point:
+ *   - Return value: HM_OK (0) or a negative HM_ERR_* code.  No exception or
+ *     abort crosses the ABI.  hm_error_string() names a code; hm_last_error()
+ *     gives the message of the last failure on the calling thread.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered; device errors found by kernels are reported by
+ *     the next call that synchronises (hm_stats, hm_sync) as HM_ERR_DEVICE_ASSERT.
+ *   - Vectors exchanged with the caller are device pointers to N doubles in
+ *     natural grid order (axis 0 fastest); the caller owns them.  The library
+ *     owns the H-matrix and the factors (freed by hm_free / hm_factors_free).
+ *   - The library allocates device memory only inside hm_build and hm_factor.
+ */
+#ifndef LEVY_HMAT_H
+#define LEVY_HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HM_OK 0
+#define HM_ERR_ARG (-1)            /* invalid argument (sizes, pointers, parameters) */
+#define HM_ERR_OOM (-2)            /* device allocation failed */
+#define HM_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define HM_ERR_RANK_CAP (-4)       /* a low-rank block needed more than its rank cap */
+#define HM_ERR_NOT_CONVERGED (-5)  /* refinement did not reach refine_tol in refine_max */
+#define HM_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define HM_ERR_DEVICE_ASSERT (-7)  /* a kernel found an invalid index or a non-finite value */
+#define HM_ERR_NO_DEVICE (-8)      /* no usable CUDA device (or not an sm_103 part) */
+
+/* ---- Levy measure families ---- */
+#define HM_NU_GAUSS 0   /* nu(y) = lam * exp(-eps^2 |y|^2)   (Merton jumps, Sec. H-matrix construction) */
+#define HM_NU_STABLE 1  /* nu(y) = c_{d,s} / |y|^{d+2s}      (fractional Laplacian, Introduction) */
+
+/* ---- storage precision of the factors (HM_FP64 keeps everything FP64) ---- */
+#define HM_FP64 0
+#define HM_MIXED_FP32 1
+
+/*
+ * Problem (Sec. "Model Problem"; Sec. "Singular and/or Slow Decaying Levy Measure").
+ * Interior grid: n[d] points per axis strictly inside [lo[d], hi[d]], spacing
+ * h = (hi - lo) / (n + 1), the same on both axes in 2D; u = 0 outside.
+ * The jump window is |y| <= LW (1D) or max-norm <= LW (2D); LW must be a
+ * whole number of grid steps.  r is the support radius of the subtraction
+ * window rho(y) = (1 - (|y|/r)^4)^3 (used only for HM_NU_STABLE).
+ * trunc: nu = 0 for |y| > trunc (INFINITY = no truncation).
+ */
+typedef struct hm_problem {
+  int dim;          /* 1 or 2 */
+  int n[2];         /* points per axis (n[1] ignored in 1D) */
+  double lo[2], hi[2];
+  double a;         /* diffusion coefficient a >= 0 (a = sigma^2 / 2) */
+  double b[2];      /* drift per axis */
+  double c;         /* reaction c <= 0 */
+  int kernel;       /* HM_NU_GAUSS or HM_NU_STABLE */
+  double s;         /* stable index s in (0, 1) (alpha = 2 s) */
+  double eps, lam;  /* Gaussian kernel parameters */
+  double trunc;     /* truncation radius of nu */
+  double LW;        /* window half-width L_W */
+  double r;         /* rho support radius */
+} hm_problem;
+
+/*
+ * Options (App. "Construction and Storage": N_min = leaf, eta of Eq. adm;
+ * Sec. "Application": eps_1 = aca_tol for construction, eps_2 = lu_tol for the
+ * additions inside H-LU).
+ */
+typedef struct hm_opts {
+  int leaf;          /* N_min: clusters with at most leaf points are not split */
+  double eta;        /* admissibility min(diam) <= eta * dist */
+  double aca_tol;    /* ACA stopping tolerance (relative Frobenius estimate) */
+  int max_rank;      /* rank cap of the ACA blocks */
+  double lu_tol;     /* relative truncation tolerance of low-rank sums in H-LU */
+  int lu_max_rank;   /* rank cap of the low-rank blocks of the factors */
+  int precision;     /* HM_FP64 or HM_MIXED_FP32 (storage of the factors) */
+  double refine_tol; /* stop refinement when ||s||_2 <= refine_tol ||rhs||_2 */
+  int refine_max;    /* max refinement sweeps per CN step (0 = plain H-LU solve) */
+} hm_opts;
+
+typedef struct hm_matrix hm_matrix;    /* opaque: H-matrix of G on the device */
+typedef struct hm_factors hm_factors;  /* opaque: H-LU factors of I + theta G */
+
+typedef struct hm_stats_t {
+  int64_t n;                  /* unknowns N */
+  int clusters, leaves, depth;
+  int dense_blocks, lowrank_blocks;
+  int64_t dense_entries;      /* entries stored in dense leaves */
+  int64_t lowrank_entries;    /* (m + n) * rank summed over low-rank blocks (actual ranks) */
+  int64_t h_bytes;            /* bytes of the H-matrix actually read by one H-matvec */
+  int64_t lu_bytes;           /* bytes of the factors read by one pair of triangular solves */
+  int max_rank_seen;          /* largest ACA rank */
+  int rank_capped_blocks;     /* ACA blocks that stopped at max_rank before aca_tol */
+  int lu_max_rank_seen;       /* largest rank in the factors */
+  int lu_rank_capped;         /* factor blocks truncated at lu_max_rank before lu_tol */
+  int last_refine_iters;      /* refinement sweeps used by the last cn_step */
+  double last_refine_resid;   /* ||s|| / ||rhs|| after the last cn_step */
+} hm_stats_t;
+
+/* ---- errors ---- */
+const char* hm_error_string(int status);
+const char* hm_last_error(void);
+
+/*
+ * Host-only planning (no GPU needed): the cluster tree (Morton order, binary
+ * in 1D / quadtree in 2D, App. "Construction and Storage") and the block tree
+ * with the admissibility of Eq. adm, evaluated exactly in integer cell units.
+ * Fills n, clusters, leaves, depth, dense_blocks, lowrank_blocks and
+ * dense_entries of *info; other fields are zero.
+ */
+int hm_plan_info(const hm_problem* prob, const hm_opts* opts, hm_stats_t* info);
+
+/*
+ * hm_plan_blocks: host-only export of the leaf blocks of the block tree, for
+ * checking the admissibility split.  For block b < *count: rows
+ * [row0[b], row0[b]+m[b]) and columns [col0[b], col0[b]+ncols[b]) in Morton
+ * order, type[b] = 1 (low rank) or 2 (dense).  perm (N ints, may be NULL)
+ * receives the natural index of each Morton position.  Arrays are caller
+ * owned; *count is in/out (capacity in, blocks out); HM_ERR_ARG if too small.
+ */
+int hm_plan_blocks(const hm_problem* prob, const hm_opts* opts, int* count, int* row0,
+                   int* m, int* col0, int* ncols, int* type, int* perm);
+
+/*
+ * hm_build: assemble G as an H-matrix on the current device.
+ * Steps (all on the device after the host-side tree): row-independent
+ * constants lambda_W, T, kappa (Eqs. dl, I2approx, I3approx) and the table of
+ * w nu(|y|) over grid offsets; dense leaves filled entry by entry (Eq. Aij);
+ * admissible blocks compressed by partially pivoted ACA to aca_tol or
+ * max_rank.  On success *out owns all device memory of the matrix.
+ */
+int hm_build(const hm_problem* prob, const hm_opts* opts, void* stream, hm_matrix** out);
+
+/*
+ * hm_matvec: y = alpha x + beta G x + gamma (w1 + w2)  (the H-matvec of App.
+ * "Matrix Vector Multiplication": dense leaves by GEMV, low-rank blocks as
+ * U (V' x)).  x, w1, w2 (w1/w2 may be NULL) and y are device vectors of N
+ * doubles in natural order; y must not alias x.
+ */
+int hm_matvec(const hm_matrix* H, double alpha, double beta, const double* x, double gamma,
+              const double* w1, const double* w2, double* y, void* stream);
+
+/*
+ * hm_to_dense: expand H into a dense N x N row-major device array (natural
+ * order), for checks at small N.  out must hold N*N doubles.
+ */
+int hm_to_dense(const hm_matrix* H, double* out, void* stream);
+
+/*
+ * hm_entries: G_{rows[q], cols[q]} for q < count from the device entry
+ * generator (natural indices; device arrays).  Evaluates the formula of
+ * Eq. Aij with the singular corrections, independent of the compression.
+ */
+int hm_entries(const hm_matrix* H, int64_t count, const int* rows, const int* cols, double* out,
+               void* stream);
+
+/*
+ * hm_factor: H-LU factorisation of M = I + theta G (App. "LU Decomposition":
+ * LU(A11); L11 U12 = A12; L21 U11 = A21; LU(A22 - L21 U12)), without pivoting
+ * (M = I - dt/2 G of Crank-Nicolson is row diagonally dominant).  Low-rank
+ * sums are truncated at opts.lu_tol / lu_max_rank.  Crank-Nicolson uses
+ * theta = -dt/2.  *out owns its device memory.
+ */
+int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out);
+
+/*
+ * hm_solve: x = (L U)^{-1} b by the H-triangular solves of App. "LU
+ * Decomposition" (forward then backward substitution over the block tree).
+ * Natural-order device vectors; x may alias b.
+ */
+int hm_solve(const hm_factors* F, const double* b, double* x, void* stream);
+
+/*
+ * cn_step: one Crank-Nicolson step (Eq. scheme) with theta = dt/2:
+ *   rhs = u_n + theta G u_n + theta (f_n + f_np1)      (H-matvec)
+ *   u_np1 = (I - theta G)^{-1} rhs                      (H-LU solve, then
+ *   refinement s = rhs - (I - theta G) z, z += (LU)^{-1} s with the H-matvec
+ *   residual, the H-LU acting as preconditioner as in Sec. "Solution to the
+ *   Model Problem", until ||s|| <= refine_tol ||rhs|| or refine_max sweeps).
+ * F must come from hm_factor(H, -dt/2); HM_ERR_ARG otherwise.  f_n / f_np1
+ * may be NULL (zero forcing).  u_np1 must not alias u_n.
+ */
+int cn_step(const hm_matrix* H, const hm_factors* F, double dt, const double* u_n,
+            const double* f_n, const double* f_np1, double* u_np1, void* stream);
+
+/*
+ * cn_solve: `steps` CN steps starting at level step0; u holds u^{step0} on
+ * entry and u^{step0+steps} on return.  f (may be NULL) holds the forcing at
+ * levels step0 .. step0+steps as (steps+1) consecutive N-vectors.  Resuming a
+ * run = rebuild (deterministic) + cn_solve from the saved level.
+ */
+int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int step0, double* u,
+             const double* f, void* stream);
+
+/* Synchronise the stream and report device-side errors of earlier calls. */
+int hm_sync(const hm_matrix* H, void* stream);
+
+/* Statistics (synchronises the stream).  F may be NULL. */
+int hm_stats(const hm_matrix* H, const hm_factors* F, hm_stats_t* out);
+
+void hm_free(hm_matrix* H);
+void hm_factors_free(hm_factors* F);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEVY_HMAT_H */

@@ -1,0 +1,375 @@
+// C ABI: planning, construction (hm_build), H-matvec and inspection calls.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "api_common.h"
+
+namespace hm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+int check_problem(const hm_problem* p, const hm_opts* o) {
+  if (!p || !o) { set_error("null problem or options"); return HM_ERR_ARG; }
+  if (p->kernel != HM_NU_GAUSS && p->kernel != HM_NU_STABLE) { set_error("unknown kernel"); return HM_ERR_ARG; }
+  if (p->kernel == HM_NU_STABLE && !(p->s > 0.0 && p->s < 1.0)) { set_error("s must lie in (0, 1)"); return HM_ERR_ARG; }
+  if (p->kernel == HM_NU_GAUSS && !(p->eps > 0.0)) { set_error("eps must be > 0"); return HM_ERR_ARG; }
+  if (!(p->a >= 0.0)) { set_error("a must be >= 0"); return HM_ERR_ARG; }
+  if (!(p->LW > 0.0)) { set_error("LW must be > 0"); return HM_ERR_ARG; }
+  if (p->kernel == HM_NU_STABLE && !(p->r > 0.0 && p->r <= p->LW)) { set_error("need 0 < r <= LW"); return HM_ERR_ARG; }
+  if (!(p->trunc > 0.0)) { set_error("trunc must be > 0"); return HM_ERR_ARG; }
+  if (o->max_rank < 1 || o->max_rank > ACA_MAXK) { set_error("max_rank must lie in [1, 128]"); return HM_ERR_ARG; }
+  if (!(o->aca_tol > 0.0)) { set_error("aca_tol must be > 0"); return HM_ERR_ARG; }
+  return HM_OK;
+}
+
+int device_ok() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { set_error(std::string("no CUDA device: ") + cudaGetErrorString(e)); return HM_ERR_NO_DEVICE; }
+  cudaDeviceProp pr;
+  e = cudaGetDeviceProperties(&pr, dev);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return HM_ERR_NO_DEVICE; }
+  if (pr.major != 10 || pr.minor != 3) {
+    set_error("kernels are built for sm_103a only; device is sm_" + std::to_string(pr.major) +
+              std::to_string(pr.minor));
+    return HM_ERR_NO_DEVICE;
+  }
+  return HM_OK;
+}
+
+NuParams nu_params(const hm_problem& p, const Plan& P, int* nw_out, std::string& err) {
+  NuParams q{};
+  q.dim = p.dim;
+  q.kernel = p.kernel;
+  q.h = P.h;
+  q.n0 = P.n[0];
+  q.n1 = P.dim == 2 ? P.n[1] : 1;
+  q.s = p.s;
+  q.eps = p.eps;
+  q.lam = p.lam;
+  q.trunc = p.trunc;
+  q.LW = p.LW;
+  q.r = p.r;
+  double ratio = p.LW / P.h;
+  int nw = (int)std::lround(ratio);
+  if (nw < 1 || std::fabs(ratio - nw) > 1e-9 * std::max(1.0, ratio)) err = "LW must be a whole number of grid steps";
+  q.nw = nw;
+  *nw_out = nw;
+  if (p.kernel == HM_NU_STABLE) {
+    double d = p.dim;
+    q.cds = std::pow(4.0, p.s) * std::tgamma(d / 2.0 + p.s) /
+            (std::pow(M_PI, d / 2.0) * std::fabs(std::tgamma(-p.s)));
+    q.expo = d + 2.0 * p.s;
+  }
+  return q;
+}
+
+}  // namespace
+
+}  // namespace hm
+
+namespace hm {
+int hm_matvec_morton(const hm_matrix* H, double alpha, double beta, const double* xm, double gamma,
+                     const double* w1m, const double* w2m, const double* w3m, double* ym,
+                     cudaStream_t st) {
+  return launch_matvec(H->mv, alpha, beta, xm, gamma, w1m, w2m, w3m, ym, st);
+}
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+const char* hm_error_string(int status) {
+  switch (status) {
+    case HM_OK: return "ok";
+    case HM_ERR_ARG: return "invalid argument";
+    case HM_ERR_OOM: return "device out of memory";
+    case HM_ERR_CUDA: return "CUDA error";
+    case HM_ERR_RANK_CAP: return "rank cap reached";
+    case HM_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case HM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case HM_ERR_DEVICE_ASSERT: return "device-side check failed";
+    case HM_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+int hm_plan_info(const hm_problem* prob, const hm_opts* opts, hm_stats_t* info) {
+  if (!info) { set_error("null info"); return HM_ERR_ARG; }
+  HM_TRY(check_problem(prob, opts));
+  Plan P;
+  std::string err;
+  HM_TRY(make_plan(*prob, *opts, P, err) == HM_OK ? HM_OK : (set_error(err), HM_ERR_ARG));
+  std::memset(info, 0, sizeof(*info));
+  info->n = P.N;
+  info->clusters = (int)P.cl.size();
+  info->leaves = (int)P.leaves.size();
+  info->depth = P.depth;
+  info->dense_blocks = (int)P.dense_block.size();
+  info->lowrank_blocks = (int)P.lr_block.size();
+  int64_t de = 0;
+  for (int b : P.dense_block) {
+    const Block& B = P.bl[b];
+    de += (int64_t)(P.cl[B.t].end - P.cl[B.t].begin) * (P.cl[B.s].end - P.cl[B.s].begin);
+  }
+  info->dense_entries = de;
+  return HM_OK;
+}
+
+int hm_plan_blocks(const hm_problem* prob, const hm_opts* opts, int* count, int* row0, int* m,
+                   int* col0, int* ncols, int* type, int* perm) {
+  if (!count || !row0 || !m || !col0 || !ncols || !type) { set_error("null output array"); return HM_ERR_ARG; }
+  HM_TRY(check_problem(prob, opts));
+  Plan P;
+  std::string err;
+  if (make_plan(*prob, *opts, P, err) != HM_OK) { set_error(err); return HM_ERR_ARG; }
+  int total = (int)(P.dense_block.size() + P.lr_block.size());
+  if (*count < total) { *count = total; set_error("output arrays too small"); return HM_ERR_ARG; }
+  int k = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<int>& L = pass == 0 ? P.lr_block : P.dense_block;
+    for (int b : L) {
+      const Block& B = P.bl[b];
+      row0[k] = P.cl[B.t].begin;
+      m[k] = P.cl[B.t].end - P.cl[B.t].begin;
+      col0[k] = P.cl[B.s].begin;
+      ncols[k] = P.cl[B.s].end - P.cl[B.s].begin;
+      type[k] = B.type;
+      ++k;
+    }
+  }
+  *count = total;
+  if (perm) std::copy(P.perm.begin(), P.perm.end(), perm);
+  return HM_OK;
+}
+
+static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t st, hm_matrix* H) {
+  HM_TRY(check_problem(prob, opts));
+  HM_TRY(device_ok());
+  H->prob = *prob;
+  H->opts = *opts;
+  HM_CK(cudaGetDevice(&H->device));
+  std::string err;
+  if (make_plan(*prob, *opts, H->plan, err) != HM_OK) { set_error(err); return HM_ERR_ARG; }
+  Plan& P = H->plan;
+  int nw = 0;
+  H->nuq = nu_params(*prob, P, &nw, err);
+  if (!err.empty()) { set_error(err); return HM_ERR_ARG; }
+  DevArena& A = H->arena;
+  const int N = P.N;
+
+  // grid tables
+  HM_TRY(A.upload(&H->d_perm, P.perm));
+  HM_TRY(A.upload(&H->d_iperm, P.iperm));
+  std::vector<int2> coord(N);
+  for (int q = 0; q < N; ++q) coord[q] = make_int2(P.coord[2 * q], P.coord[2 * q + 1]);
+  HM_TRY(A.upload(&H->d_coord, coord));
+  HM_TRY(A.alloc((void**)&H->d_tab, sizeof(double) * (size_t)H->nuq.n0 * H->nuq.n1));
+  HM_TRY(A.alloc((void**)&H->d_cscratch, sizeof(double) * 8));
+  HM_TRY(A.alloc((void**)&H->d_gc, sizeof(GenConst)));
+  HM_TRY(A.alloc((void**)&H->d_err, sizeof(int) * 4));
+  HM_CK(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
+  HM_CK(cudaMemsetAsync(H->d_cscratch, 0, sizeof(double) * 8, st));
+  HM_TRY(launch_constants(H->nuq, H->d_tab, H->d_cscratch, st));
+  HM_TRY(launch_finalize_constants(H->nuq, prob->a, prob->b, prob->c, H->d_cscratch, H->d_gc, st));
+  H->ectx.dim = P.dim;
+  H->ectx.n0 = H->nuq.n0;
+  H->ectx.n1 = H->nuq.n1;
+  H->ectx.coord = H->d_coord;
+  H->ectx.tab = H->d_tab;
+  H->ectx.gc = H->d_gc;
+
+  // dense leaves
+  int64_t off = 0;
+  for (int b : P.dense_block) {
+    const Block& B = P.bl[b];
+    DenseDesc D{};
+    D.r0 = P.cl[B.t].begin;
+    D.m = P.cl[B.t].end - D.r0;
+    D.c0 = P.cl[B.s].begin;
+    D.n = P.cl[B.s].end - D.c0;
+    D.ld = (D.n + 3) & ~3;
+    D.off = off;
+    off += (int64_t)D.m * D.ld;
+    H->h_dd.push_back(D);
+  }
+  H->d_pool = off;
+  HM_TRY(A.upload(&H->d_dd, H->h_dd));
+  HM_TRY(A.alloc((void**)&H->d_D, sizeof(double) * (size_t)std::max<int64_t>(off, 1)));
+  HM_CK(cudaMemsetAsync(H->d_D, 0, sizeof(double) * (size_t)std::max<int64_t>(off, 1), st));
+  HM_TRY(launch_near_fill(H->ectx, H->d_dd, (int)H->h_dd.size(), H->d_D, st));
+
+  // admissible blocks: ACA
+  int64_t uo = 0, vo = 0;
+  for (int b : P.lr_block) {
+    const Block& B = P.bl[b];
+    LRDesc L{};
+    L.r0 = P.cl[B.t].begin;
+    L.m = P.cl[B.t].end - L.r0;
+    L.c0 = P.cl[B.s].begin;
+    L.n = P.cl[B.s].end - L.c0;
+    L.kcap = std::min(opts->max_rank, std::min(L.m, L.n));
+    L.uoff = uo;
+    L.voff = vo;
+    uo += (int64_t)L.m * L.kcap;
+    vo += (int64_t)L.n * L.kcap;
+    H->max_m = std::max(H->max_m, L.m);
+    H->kmax = std::max(H->kmax, L.kcap);
+    H->h_ld.push_back(L);
+  }
+  H->u_pool = uo;
+  H->v_pool = vo;
+  const int nlr = (int)H->h_ld.size();
+  HM_TRY(A.upload(&H->d_ld, H->h_ld));
+  HM_TRY(A.alloc((void**)&H->d_rank, sizeof(int) * std::max(nlr, 1)));
+  HM_TRY(A.alloc((void**)&H->d_capped, sizeof(int) * std::max(nlr, 1)));
+  HM_TRY(A.alloc((void**)&H->d_U, sizeof(double) * (size_t)std::max<int64_t>(uo, 1)));
+  HM_TRY(A.alloc((void**)&H->d_V, sizeof(double) * (size_t)std::max<int64_t>(vo, 1)));
+  HM_TRY(launch_aca(H->ectx, H->d_ld, nlr, H->max_m, H->d_U, H->d_V, H->d_rank, H->d_capped,
+                    opts->aca_tol, st));
+
+  // H-matvec plan: row chunks over leaves, far-field V' x tasks
+  std::vector<std::vector<int>> lr_by_row(P.cl.size()), dense_by_row(P.cl.size());
+  for (int q = 0; q < nlr; ++q) lr_by_row[P.bl[P.lr_block[q]].t].push_back(q);
+  for (int d = 0; d < (int)P.dense_block.size(); ++d) dense_by_row[P.bl[P.dense_block[d]].t].push_back(d);
+  for (int leaf : P.leaves) {
+    RowChunk base{};
+    base.dense_begin = (int)H->h_dense_items.size();
+    for (int d : dense_by_row[leaf]) H->h_dense_items.push_back(d);
+    base.dense_end = (int)H->h_dense_items.size();
+    base.lr_begin = (int)H->h_lr_items.size();
+    for (int c = leaf; c >= 0; c = P.cl[c].parent)
+      for (int q : lr_by_row[c]) H->h_lr_items.push_back(q);
+    base.lr_end = (int)H->h_lr_items.size();
+    const Cluster& L = P.cl[leaf];
+    for (int r = L.begin; r < L.end; r += MV_CHUNK) {
+      RowChunk ch = base;
+      ch.r0 = r;
+      ch.nrow = std::min(MV_CHUNK, L.end - r);
+      H->h_chunks.push_back(ch);
+    }
+  }
+  std::vector<VTask> vt;
+  std::vector<int> vt_range(2 * (size_t)std::max(nlr, 1), 0);
+  for (int q = 0; q < nlr; ++q) {
+    vt_range[2 * q] = (int)vt.size();
+    for (int c = 0; c < H->h_ld[q].n; c += VT_CHUNK) {
+      VTask t{q, c, std::min(VT_CHUNK, H->h_ld[q].n - c), (int)vt.size()};
+      vt.push_back(t);
+    }
+    vt_range[2 * q + 1] = (int)vt.size();
+  }
+  MatvecPlan& M = H->mv;
+  M.nlr = nlr;
+  M.ndense = (int)H->h_dd.size();
+  M.nvt = (int)vt.size();
+  M.nchunk = (int)H->h_chunks.size();
+  M.ld = H->d_ld;
+  M.dd = H->d_dd;
+  M.rank = H->d_rank;
+  M.U = H->d_U;
+  M.V = H->d_V;
+  M.D = H->d_D;
+  M.kmax = H->kmax;
+  VTask* d_vt = nullptr;
+  int* d_vtr = nullptr;
+  RowChunk* d_ch = nullptr;
+  int* d_di = nullptr;
+  int* d_li = nullptr;
+  HM_TRY(A.upload(&d_vt, vt));
+  HM_TRY(A.upload(&d_vtr, vt_range));
+  HM_TRY(A.upload(&d_ch, H->h_chunks));
+  HM_TRY(A.upload(&d_di, H->h_dense_items));
+  HM_TRY(A.upload(&d_li, H->h_lr_items));
+  M.vt = d_vt;
+  M.vt_range = d_vtr;
+  M.chunks = d_ch;
+  M.dense_items = d_di;
+  M.lr_items = d_li;
+  HM_TRY(A.alloc((void**)&M.partial, sizeof(double) * (size_t)std::max(M.nvt, 1) * ACA_MAXK));
+  HM_TRY(A.alloc((void**)&M.tvec, sizeof(double) * (size_t)std::max(nlr, 1) * ACA_MAXK));
+  HM_TRY(A.alloc((void**)&H->d_work, sizeof(double) * (size_t)N * 8));
+
+  HM_CK(cudaStreamSynchronize(st));
+  H->h_rank.assign(nlr, 0);
+  std::vector<int> capped(nlr, 0);
+  if (nlr) {
+    HM_CK(cudaMemcpy(H->h_rank.data(), H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
+    HM_CK(cudaMemcpy(capped.data(), H->d_capped, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
+  }
+  H->capped_blocks = 0;
+  for (int c : capped) H->capped_blocks += c;
+  return HM_OK;
+}
+
+int hm_build(const hm_problem* prob, const hm_opts* opts, void* stream, hm_matrix** out) {
+  if (!out) { set_error("null out"); return HM_ERR_ARG; }
+  *out = nullptr;
+  hm_matrix* H = new hm_matrix();
+  int s = build_impl(prob, opts, (cudaStream_t)stream, H);
+  if (s != HM_OK) {
+    cudaDeviceSynchronize();
+    H->arena.release();
+    delete H;
+    return s;
+  }
+  *out = H;
+  return HM_OK;
+}
+
+void hm_free(hm_matrix* H) {
+  if (!H) return;
+  cudaDeviceSynchronize();
+  H->arena.release();
+  delete H;
+}
+
+int hm_matvec(const hm_matrix* H, double alpha, double beta, const double* x, double gamma,
+              const double* w1, const double* w2, double* y, void* stream) {
+  if (!H || !x || !y) { set_error("null argument"); return HM_ERR_ARG; }
+  if (x == y) { set_error("y must not alias x"); return HM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = H->plan.N;
+  if (H->plan.dim == 1) return hm_matvec_morton(H, alpha, beta, x, gamma, w1, w2, nullptr, y, st);
+  double* xm = H->d_work;
+  double* ym = H->d_work + N;
+  double* a = H->d_work + 2 * (size_t)N;
+  double* b = H->d_work + 3 * (size_t)N;
+  HM_TRY(launch_gather(H->d_perm, N, x, xm, st));
+  if (w1) HM_TRY(launch_gather(H->d_perm, N, w1, a, st));
+  if (w2) HM_TRY(launch_gather(H->d_perm, N, w2, b, st));
+  HM_TRY(hm_matvec_morton(H, alpha, beta, xm, gamma, w1 ? a : nullptr, w2 ? b : nullptr, nullptr, ym, st));
+  return launch_scatter(H->d_perm, N, ym, y, st);
+}
+
+int hm_to_dense(const hm_matrix* H, double* out, void* stream) {
+  if (!H || !out) { set_error("null argument"); return HM_ERR_ARG; }
+  return launch_to_dense(H->d_dd, (int)H->h_dd.size(), H->d_D, H->d_ld, (int)H->h_ld.size(),
+                         H->d_rank, H->d_U, H->d_V, H->d_perm, H->plan.N, out, (cudaStream_t)stream);
+}
+
+int hm_entries(const hm_matrix* H, int64_t count, const int* rows, const int* cols, double* out,
+               void* stream) {
+  if (!H || count < 0 || (count > 0 && (!rows || !cols || !out))) { set_error("bad argument"); return HM_ERR_ARG; }
+  return launch_entries(H->ectx, H->d_iperm, H->plan.N, count, rows, cols, out, H->d_err,
+                        (cudaStream_t)stream);
+}
+
+int hm_sync(const hm_matrix* H, void* stream) {
+  if (!H) { set_error("null argument"); return HM_ERR_ARG; }
+  HM_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int e = 0;
+  HM_CK(cudaMemcpy(&e, H->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) { set_error("device error flags " + std::to_string(e)); return HM_ERR_DEVICE_ASSERT; }
+  return HM_OK;
+}
+
+}  // extern "C"

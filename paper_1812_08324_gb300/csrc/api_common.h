@@ -1,0 +1,108 @@
+// Internal state behind the opaque handles of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "hm_internal.h"
+#include "hm_kernels.h"
+
+namespace hm {
+
+void set_error(const std::string& msg);
+
+// Record a failed CUDA call and turn it into a status code.
+#define HM_CK(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::hm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+      return e_ == cudaErrorMemoryAllocation ? HM_ERR_OOM : HM_ERR_CUDA;               \
+    }                                                                                  \
+  } while (0)
+
+#define HM_TRY(expr)               \
+  do {                             \
+    int s_ = (expr);               \
+    if (s_ != HM_OK) return s_;    \
+  } while (0)
+
+// Device allocations owned by one handle, freed together.
+struct DevArena {
+  std::vector<void*> ptrs;
+  int alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      *p = nullptr;
+      return HM_ERR_OOM;
+    }
+    ptrs.push_back(*p);
+    return HM_OK;
+  }
+  template <typename T>
+  int upload(T** p, const std::vector<T>& h) {
+    HM_TRY(alloc((void**)p, h.size() * sizeof(T)));
+    if (!h.empty()) HM_CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HM_OK;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+}  // namespace hm
+
+struct hm_matrix {
+  hm::Plan plan;
+  hm_problem prob;
+  hm_opts opts;
+  int device = 0;
+  hm::DevArena arena;
+  hm::NuParams nuq;
+  // device tables
+  int* d_perm = nullptr;
+  int* d_iperm = nullptr;
+  int2* d_coord = nullptr;
+  double* d_tab = nullptr;
+  double* d_cscratch = nullptr;
+  hm::GenConst* d_gc = nullptr;
+  hm::EntryCtx ectx;
+  // storage
+  std::vector<hm::LRDesc> h_ld;
+  std::vector<hm::DenseDesc> h_dd;
+  hm::LRDesc* d_ld = nullptr;
+  hm::DenseDesc* d_dd = nullptr;
+  int* d_rank = nullptr;
+  int* d_capped = nullptr;
+  double* d_U = nullptr;
+  double* d_V = nullptr;
+  double* d_D = nullptr;
+  int64_t u_pool = 0, v_pool = 0, d_pool = 0;
+  int max_m = 0, kmax = 0;
+  // matvec plan
+  hm::MatvecPlan mv;
+  std::vector<hm::RowChunk> h_chunks;
+  std::vector<int> h_dense_items, h_lr_items;
+  // work vectors (Morton order)
+  double* d_work = nullptr;  // 6 x N
+  int* d_err = nullptr;
+  // host copies of results
+  std::vector<int> h_rank;
+  int capped_blocks = 0;
+  int last_refine_iters = 0;
+  double last_refine_resid = 0.0;
+};
+
+namespace hm {
+// y = alpha x + beta G x + gamma (w1 + w2) + w3 on Morton-order device vectors.
+int hm_matvec_morton(const hm_matrix* H, double alpha, double beta, const double* xm, double gamma,
+                     const double* w1m, const double* w2m, const double* w3m, double* ym,
+                     cudaStream_t st);
+}  // namespace hm

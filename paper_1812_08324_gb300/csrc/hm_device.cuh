@@ -1,0 +1,93 @@
+// Device-side helpers shared by the kernels: entry evaluation and reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+// Device error word bits (set by kernels, read back by hm_sync / hm_stats).
+enum : int {
+  DEVERR_INDEX = 1,      // an index fell outside its buffer (access skipped)
+  DEVERR_NONFINITE = 2,  // a non-finite value appeared where it must not
+  DEVERR_RANKCAP = 4,    // a low-rank sum needed more than its capacity
+  DEVERR_ZEROPIVOT = 8,  // a zero pivot in an unpivoted dense LU
+};
+
+// G between Morton positions p (row) and q (column): the formula of Eq. Aij
+// (sign-flipped) with the singular corrections, evaluated from the offset
+// table w(j) nu(|j| h) and the row-independent constants.
+__device__ __forceinline__ double gen_entry(const EntryCtx& E, const GenConst& g, int p, int q) {
+  int2 cp = E.coord[p];
+  int2 cq = E.coord[q];
+  int d0 = cq.x - cp.x;
+  int d1 = cq.y - cp.y;
+  if (d0 == 0 && d1 == 0) return g.diag;
+  int a0 = d0 < 0 ? -d0 : d0;
+  int a1 = d1 < 0 ? -d1 : d1;
+  double v = E.tab[(size_t)a1 * E.n0 + a0];
+  if (a0 + a1 == 1) {
+    if (a0 == 1) v = v + (d0 > 0 ? g.stencil_p[0] : g.stencil_m[0]);
+    else v = v + (d1 > 0 ? g.stencil_p[1] : g.stencil_m[1]);
+  }
+  return v;
+}
+
+// Far entries (never the diagonal or an axis neighbour): table lookup only.
+__device__ __forceinline__ double far_entry(const EntryCtx& E, int p, int q) {
+  int2 cp = E.coord[p];
+  int2 cq = E.coord[q];
+  int a0 = abs(cq.x - cp.x);
+  int a1 = abs(cq.y - cp.y);
+  return E.tab[(size_t)a1 * E.n0 + a0];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  scratch: >= 32 elements.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T r = 0;
+  for (int i = 0; i < nw; ++i) r += scratch[i];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide argmax of |v| with ties to the smallest index.  Every thread gets
+// (best value (signed), best index); idx < 0 means "no candidate".
+__device__ __forceinline__ void argmax_merge(double& bv, int& bi, double v, int i) {
+  double av = fabs(v), ab = fabs(bv);
+  if (i >= 0 && (bi < 0 || av > ab || (av == ab && i < bi))) { bv = v; bi = i; }
+}
+
+__device__ __forceinline__ void block_argmax(double& v, int& idx, double* sv, int* si) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    argmax_merge(v, idx, ov, oi);
+  }
+  __syncthreads();
+  if (lane == 0) { sv[w] = v; si[w] = idx; }
+  __syncthreads();
+  double bv = 0;
+  int bi = -1;
+  for (int i = 0; i < nw; ++i) argmax_merge(bv, bi, sv[i], si[i]);
+  __syncthreads();
+  v = bv;
+  idx = bi;
+}
+
+}  // namespace hm

@@ -1,0 +1,167 @@
+// H-matvec (App. "Matrix Vector Multiplication"): dense leaves by GEMV and
+// low-rank blocks as U (V' x), flattened over the leaf blocks of the tree.
+//
+//   1. vt_kernel      partial products V[chunk]' x[chunk] of every low-rank
+//                     block, one CTA per 256-row chunk of its column cluster
+//   2. vt_reduce      t_q = sum of the partials of block q
+//   3. rows_kernel    one CTA per 32-row chunk: the dense leaves of its rows
+//                     (warp per 4 rows, 16-byte loads) plus U[rows] t_q of
+//                     every low-rank block covering the rows, then the
+//                     epilogue y = alpha x + beta (H x) + gamma (w1 + w2) + w3.
+// All vectors are in Morton order.  FP64 storage and FP64 accumulation.
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+
+namespace hm {
+
+namespace {
+
+__global__ void __launch_bounds__(256)
+vt_kernel(const VTask* vt, const LRDesc* ld, const int* rank, const double* Vpool,
+          const double* __restrict__ x, double* partial) {
+  __shared__ double xs[VT_CHUNK];
+  const VTask T = vt[blockIdx.x];
+  const LRDesc L = ld[T.lr];
+  const int k = rank[T.lr];
+  const double* xc = x + L.c0 + T.c_lo;
+  for (int j = threadIdx.x; j < T.len; j += blockDim.x) xs[j] = xc[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const double* V = Vpool + L.voff + T.c_lo;
+  for (int l = warp; l < k; l += nwarp) {
+    const double* Vl = V + (int64_t)l * L.n;
+    double acc = 0.0;
+    for (int j = lane; j < T.len; j += 32) acc += Vl[j] * xs[j];
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(int64_t)T.out * ACA_MAXK + l] = acc;
+  }
+}
+
+__global__ void vt_reduce_kernel(int nlr, const int* vt_range, const int* rank,
+                                 const double* partial, double* tvec) {
+  int q = blockIdx.x;
+  if (q >= nlr) return;
+  int b = vt_range[2 * q], e = vt_range[2 * q + 1];
+  int k = rank[q];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) {
+    double acc = 0.0;
+    for (int o = b; o < e; ++o) acc += partial[(int64_t)o * ACA_MAXK + l];
+    tvec[(int64_t)q * ACA_MAXK + l] = acc;
+  }
+}
+
+constexpr int ROWS_PER_WARP = MV_CHUNK / 8;  // 8 warps x 4 rows
+
+__global__ void __launch_bounds__(256)
+rows_kernel(const RowChunk* chunks, const int* dense_items, const int* lr_items,
+            const DenseDesc* dd, const double* Dpool, const LRDesc* ld, const int* rank,
+            const double* Upool, const double* tvec, double alpha, double beta,
+            const double* __restrict__ x, double gamma, const double* w1, const double* w2,
+            const double* w3, double* y) {
+  __shared__ double acc_d[MV_CHUNK];
+  __shared__ double acc_f[8][MV_CHUNK];
+  const RowChunk C = chunks[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < MV_CHUNK) acc_d[threadIdx.x] = 0.0;
+  acc_f[warp][lane] = 0.0;
+  __syncthreads();
+
+  // ---- dense leaves: warp handles ROWS_PER_WARP consecutive rows
+  double rsum[ROWS_PER_WARP];
+#pragma unroll
+  for (int r = 0; r < ROWS_PER_WARP; ++r) rsum[r] = 0.0;
+  const int rw0 = warp * ROWS_PER_WARP;
+  for (int it = C.dense_begin; it < C.dense_end; ++it) {
+    const DenseDesc D = dd[dense_items[it]];
+    const int i0 = C.r0 - D.r0 + rw0;
+    const double* xc = x + D.c0;
+    const double* base = Dpool + D.off + (int64_t)i0 * D.ld;
+    // 16-byte loads over column pairs; D.ld is a multiple of 4, D.off even
+    const int npair = D.n >> 1;
+    for (int p = lane; p < npair; p += 32) {
+      double x0 = xc[2 * p], x1 = xc[2 * p + 1];
+#pragma unroll
+      for (int r = 0; r < ROWS_PER_WARP; ++r) {
+        if (rw0 + r < C.nrow) {
+          double2 v = *reinterpret_cast<const double2*>(base + (int64_t)r * D.ld + 2 * p);
+          rsum[r] += v.x * x0 + v.y * x1;
+        }
+      }
+    }
+    if ((D.n & 1) && lane == 0) {
+      double xl = xc[D.n - 1];
+#pragma unroll
+      for (int r = 0; r < ROWS_PER_WARP; ++r)
+        if (rw0 + r < C.nrow) rsum[r] += base[(int64_t)r * D.ld + D.n - 1] * xl;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS_PER_WARP; ++r) {
+    double s = warp_sum(rsum[r]);
+    if (lane == 0) acc_d[rw0 + r] = s;
+  }
+
+  // ---- low-rank blocks: warp per block, lane per row
+  double facc = 0.0;
+  for (int it = C.lr_begin + warp; it < C.lr_end; it += 8) {
+    const int q = lr_items[it];
+    const LRDesc L = ld[q];
+    const int k = rank[q];
+    const int i = C.r0 - L.r0 + lane;
+    if (lane < C.nrow) {
+      const double* U = Upool + L.uoff + i;
+      const double* t = tvec + (int64_t)q * ACA_MAXK;
+      for (int l = 0; l < k; ++l) facc += U[(int64_t)l * L.m] * t[l];
+    }
+  }
+  acc_f[warp][lane] = facc;
+  __syncthreads();
+
+  if (threadIdx.x < C.nrow) {
+    const int r = threadIdx.x;
+    double hx = acc_d[r];
+    for (int w = 0; w < 8; ++w) hx += acc_f[w][r];
+    const int row = C.r0 + r;
+    double out = alpha * x[row] + beta * hx;
+    if (w1) out += gamma * w1[row];
+    if (w2) out += gamma * w2[row];
+    if (w3) out += w3[row];
+    y[row] = out;
+  }
+}
+
+__global__ void gather_kernel(const int* perm, int N, const double* src, double* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+
+__global__ void scatter_kernel(const int* perm, int N, const double* src, double* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    dst[perm[i]] = src[i];
+}
+
+}  // namespace
+
+int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* x, double gamma,
+                  const double* w1, const double* w2, const double* w3, double* y,
+                  cudaStream_t st) {
+  if (P.nvt > 0) {
+    vt_kernel<<<P.nvt, 256, 0, st>>>(P.vt, P.ld, P.rank, P.V, x, P.partial);
+    vt_reduce_kernel<<<P.nlr, 64, 0, st>>>(P.nlr, P.vt_range, P.rank, P.partial, P.tvec);
+  }
+  rows_kernel<<<P.nchunk, 256, 0, st>>>(P.chunks, P.dense_items, P.lr_items, P.dd, P.D, P.ld,
+                                        P.rank, P.U, P.tvec, alpha, beta, x, gamma, w1, w2, w3, y);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_gather(const int* perm, int N, const double* src, double* dst, cudaStream_t st) {
+  gather_kernel<<<std::min((N + 255) / 256, 152 * 8), 256, 0, st>>>(perm, N, src, dst);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_scatter(const int* perm, int N, const double* src, double* dst, cudaStream_t st) {
+  scatter_kernel<<<std::min((N + 255) / 256, 152 * 8), 256, 0, st>>>(perm, N, src, dst);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+}  // namespace hm

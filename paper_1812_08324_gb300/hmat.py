@@ -1,0 +1,287 @@
+"""Thin ctypes binding of the C ABI in ``include/levy_hmat.h``.
+
+Argument marshalling only: problem/option dictionaries become the C structs,
+torch CUDA tensors become device pointers, the current torch stream becomes
+the cudaStream_t.  Every numerical step runs in the CUDA library; if the
+library is missing this module raises instead of computing anything on the CPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "liblevyhm.so")
+
+HM_OK = 0
+HM_NU_GAUSS, HM_NU_STABLE = 0, 1
+HM_FP64, HM_MIXED_FP32 = 0, 1
+
+EXPORTED = [
+    "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
+    "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
+    "hm_sync", "hm_stats", "hm_free", "hm_factors_free",
+]
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 2), ("lo", C.c_double * 2), ("hi", C.c_double * 2),
+                ("a", C.c_double), ("b", C.c_double * 2), ("c", C.c_double), ("kernel", C.c_int),
+                ("s", C.c_double), ("eps", C.c_double), ("lam", C.c_double), ("trunc", C.c_double),
+                ("LW", C.c_double), ("r", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("leaf", C.c_int), ("eta", C.c_double), ("aca_tol", C.c_double),
+                ("max_rank", C.c_int), ("lu_tol", C.c_double), ("lu_max_rank", C.c_int),
+                ("precision", C.c_int), ("refine_tol", C.c_double), ("refine_max", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("clusters", C.c_int), ("leaves", C.c_int), ("depth", C.c_int),
+                ("dense_blocks", C.c_int), ("lowrank_blocks", C.c_int),
+                ("dense_entries", C.c_int64), ("lowrank_entries", C.c_int64),
+                ("h_bytes", C.c_int64), ("lu_bytes", C.c_int64), ("max_rank_seen", C.c_int),
+                ("rank_capped_blocks", C.c_int), ("lu_max_rank_seen", C.c_int),
+                ("lu_rank_capped", C.c_int), ("last_refine_iters", C.c_int),
+                ("last_refine_resid", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library (build it first with ``paper_1812_08324_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_1812_08324_gb300.build)")
+    lib = C.CDLL(LIB_PATH)
+    vp, d, i, i64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
+    P, O, S = C.POINTER(Problem), C.POINTER(Opts), C.POINTER(Stats)
+    sig = {
+        "hm_error_string": (C.c_char_p, [i]),
+        "hm_last_error": (C.c_char_p, []),
+        "hm_plan_info": (i, [P, O, S]),
+        "hm_plan_blocks": (i, [P, O, C.POINTER(i), vp, vp, vp, vp, vp, vp]),
+        "hm_build": (i, [P, O, vp, C.POINTER(vp)]),
+        "hm_matvec": (i, [vp, d, d, vp, d, vp, vp, vp, vp]),
+        "hm_to_dense": (i, [vp, vp, vp]),
+        "hm_entries": (i, [vp, i64, vp, vp, vp, vp]),
+        "hm_factor": (i, [vp, d, vp, C.POINTER(vp)]),
+        "hm_solve": (i, [vp, vp, vp, vp]),
+        "cn_step": (i, [vp, vp, d, vp, vp, vp, vp, vp]),
+        "cn_solve": (i, [vp, vp, d, i, i, vp, vp, vp]),
+        "hm_sync": (i, [vp, vp]),
+        "hm_stats": (i, [vp, vp, S]),
+        "hm_free": (None, [vp]),
+        "hm_factors_free": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != HM_OK:
+        lib = load()
+        raise HMError(status, f"{lib.hm_error_string(status).decode()}: {lib.hm_last_error().decode()}")
+
+
+def make_problem(p: dict) -> Problem:
+    s = Problem()
+    s.dim = int(p["dim"])
+    n = list(p["n"]) + [1]
+    s.n[0], s.n[1] = int(n[0]), int(n[1])
+    lo = list(p["lo"]) + [0.0]
+    hi = list(p["hi"]) + [0.0]
+    s.lo[0], s.lo[1] = float(lo[0]), float(lo[1])
+    s.hi[0], s.hi[1] = float(hi[0]), float(hi[1])
+    s.a = float(p.get("a", 0.0))
+    b = list(p.get("b", [0.0, 0.0])) + [0.0]
+    s.b[0], s.b[1] = float(b[0]), float(b[1])
+    s.c = float(p.get("c", 0.0))
+    s.kernel = HM_NU_GAUSS if p["kernel"] == "gauss" else HM_NU_STABLE
+    s.s = float(p.get("s", 0.0))
+    s.eps = float(p.get("eps", 0.0))
+    s.lam = float(p.get("lam", 0.0))
+    s.trunc = float(p.get("trunc", math.inf))
+    s.LW = float(p["LW"])
+    s.r = float(p.get("r", 0.2))
+    return s
+
+
+def make_opts(o: dict) -> Opts:
+    s = Opts()
+    s.leaf = int(o.get("leaf", 64))
+    s.eta = float(o.get("eta", 1.0))
+    s.aca_tol = float(o.get("aca_tol", 1e-10))
+    s.max_rank = int(o.get("max_rank", 64))
+    s.lu_tol = float(o.get("lu_tol", 1e-10))
+    s.lu_max_rank = int(o.get("lu_max_rank", 64))
+    prec = o.get("precision", "fp64")
+    s.precision = {"fp64": HM_FP64, "fp32": HM_MIXED_FP32, "mixed_fp32": HM_MIXED_FP32}.get(prec, prec) \
+        if isinstance(prec, str) else int(prec)
+    s.refine_tol = float(o.get("refine_tol", 1e-13))
+    s.refine_max = int(o.get("refine_max", 4))
+    return s
+
+
+def plan_info(problem: dict, opts: dict) -> dict:
+    """Cluster/block-tree statistics from the host planner (no GPU needed)."""
+    lib = load()
+    st = Stats()
+    _check(lib.hm_plan_info(C.byref(make_problem(problem)), C.byref(make_opts(opts)), C.byref(st)))
+    return st.as_dict()
+
+
+def plan_blocks(problem: dict, opts: dict):
+    """Leaf blocks of the block tree: (row0, m, col0, ncols, type, perm) numpy arrays."""
+    import numpy as np
+    lib = load()
+    info = plan_info(problem, opts)
+    cnt = info["dense_blocks"] + info["lowrank_blocks"]
+    arrs = [np.zeros(cnt, dtype=np.int32) for _ in range(5)]
+    perm = np.zeros(info["n"], dtype=np.int32)
+    c = C.c_int(cnt)
+    _check(lib.hm_plan_blocks(C.byref(make_problem(problem)), C.byref(make_opts(opts)), C.byref(c),
+                              *[a.ctypes.data for a in arrs], perm.ctypes.data))
+    return (*arrs, perm)
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return int(t.data_ptr())
+
+
+class HMatrix:
+    """Device-resident H-matrix of the discrete generator G (owned by the library)."""
+
+    def __init__(self, problem: dict, opts: dict, stream=None):
+        lib = load()
+        self.problem = dict(problem)
+        self.opts = dict(opts)
+        self._h = C.c_void_p()
+        self._p = make_problem(problem)
+        self._o = make_opts(opts)
+        _check(lib.hm_build(C.byref(self._p), C.byref(self._o), _stream(stream), C.byref(self._h)))
+        self.n = int(self.stats()["n"])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def matvec(self, x, alpha=0.0, beta=1.0, gamma=0.0, w1=None, w2=None, out=None, stream=None):
+        """out = alpha x + beta G x + gamma (w1 + w2)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().hm_matvec(self._h, alpha, beta, _ptr(x), gamma, _ptr(w1), _ptr(w2), _ptr(out),
+                                _stream(stream)))
+        return out
+
+    def to_dense(self, stream=None):
+        import torch
+        out = torch.zeros(self.n, self.n, dtype=torch.float64, device="cuda")
+        _check(load().hm_to_dense(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def entries(self, rows, cols, stream=None):
+        import torch
+        rows = rows.to(device="cuda", dtype=torch.int32).contiguous()
+        cols = cols.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(rows.numel(), dtype=torch.float64, device="cuda")
+        _check(load().hm_entries(self._h, rows.numel(), rows.data_ptr(), cols.data_ptr(), _ptr(out),
+                                 _stream(stream)))
+        return out
+
+    def sync(self, stream=None):
+        _check(load().hm_sync(self._h, _stream(stream)))
+
+    def stats(self, factors=None) -> dict:
+        st = Stats()
+        _check(load().hm_stats(self._h, factors._f if factors is not None else None, C.byref(st)))
+        return st.as_dict()
+
+    def factor(self, theta: float, stream=None) -> "Factors":
+        return Factors(self, theta, stream)
+
+    def free(self):
+        if self._h:
+            load().hm_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Factors:
+    """H-LU factors of I + theta G (owned by the library)."""
+
+    def __init__(self, H: HMatrix, theta: float, stream=None):
+        self.H = H
+        self.theta = theta
+        self._f = C.c_void_p()
+        _check(load().hm_factor(H.handle, theta, _stream(stream), C.byref(self._f)))
+
+    def solve(self, b, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(b)
+        _check(load().hm_solve(self._f, _ptr(b), _ptr(out), _stream(stream)))
+        return out
+
+    def free(self):
+        if self._f:
+            load().hm_factors_free(self._f)
+            self._f = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def cn_step(H: HMatrix, F: Factors, dt: float, u, f_n=None, f_np1=None, out=None, stream=None):
+    """One Crank-Nicolson step; returns u^{n+1}."""
+    import torch
+    if out is None:
+        out = torch.empty_like(u)
+    _check(load().cn_step(H.handle, F._f, dt, _ptr(u), _ptr(f_n), _ptr(f_np1), _ptr(out),
+                          _stream(stream)))
+    return out
+
+
+def cn_solve(H: HMatrix, F: Factors, dt: float, steps: int, u, f=None, step0: int = 0, stream=None):
+    """Advance u in place by `steps` CN steps; f is (steps+1) x N forcing or None."""
+    _check(load().cn_solve(H.handle, F._f, dt, int(steps), int(step0), _ptr(u), _ptr(f),
+                           _stream(stream)))
+    return u

@@ -1,0 +1,107 @@
+"""Host-side planner (no GPU): the C library loads on a CPU-only machine, exports
+every symbol the header declares, and its cluster/block trees satisfy the
+definitions of App. "Construction and Storage" checked by brute force."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1812_08324_gb300 import build, hmat, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    return hmat.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    header = open(os.path.join(ROOT, "include", "levy_hmat.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(\w+)\(", header, re.M))
+    declared = {d for d in declared if d.startswith(("hm_", "cn_"))}
+    assert declared == set(hmat.EXPORTED), declared ^ set(hmat.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _boxes(perm, dim, n0, row0, m):
+    if dim == 1:
+        idx = perm[row0:row0 + m][:, None]
+    else:
+        p = perm[row0:row0 + m]
+        idx = np.stack([p % n0, p // n0], axis=1)
+    return idx.min(0), idx.max(0) + 1
+
+
+def _adm(box_a, box_b, eta):
+    (la, ha), (lb, hb) = box_a, box_b
+    da = float(np.sum((ha - la) ** 2))
+    db = float(np.sum((hb - lb) ** 2))
+    gap = np.maximum(0, np.maximum(lb - ha, la - hb))
+    dist = float(np.sum(gap ** 2))
+    return math.sqrt(min(da, db)) <= eta * math.sqrt(dist)
+
+
+CASES = [
+    (W.frac_lap_1d(1023), dict(leaf=64, eta=1.0), (16, 46, 66)),
+    (W.levy_1d(4096), dict(leaf=256, eta=1.0), (16, 46, 66)),
+    (W.frac_lap_2d(32), dict(leaf=16, eta=1.0), None),
+    (W.frac_lap_2d(20), dict(leaf=16, eta=1.0), None),   # non power-of-two side
+    (dict(W.frac_lap_2d(24), n=[24, 24]), dict(leaf=10, eta=1.5), None),
+]
+
+
+@pytest.mark.parametrize("prob,opts,expect", CASES)
+def test_block_tree_partitions_and_admissibility(prob, opts, expect):
+    o = W.default_opts(**opts)
+    info = hmat.plan_info(prob, o)
+    row0, m, col0, nc, typ, perm = hmat.plan_blocks(prob, o)
+    N = info["n"]
+    assert sorted(perm.tolist()) == list(range(N))
+    # every (row, col) pair lies in exactly one leaf block
+    cover = np.zeros((N, N), dtype=np.int32)
+    for b in range(len(row0)):
+        cover[row0[b]:row0[b] + m[b], col0[b]:col0[b] + nc[b]] += 1
+    assert np.all(cover == 1)
+    dim, n0 = prob["dim"], prob["n"][0]
+    for b in range(len(row0)):
+        bt = _boxes(perm, dim, n0, row0[b], m[b])
+        bs = _boxes(perm, dim, n0, col0[b], nc[b])
+        if typ[b] == 1:
+            assert _adm(bt, bs, o["eta"]), b
+        else:
+            assert typ[b] == 2 and not _adm(bt, bs, o["eta"]) or row0[b] == col0[b]
+            assert m[b] <= o["leaf"] and nc[b] <= o["leaf"]
+    if expect is not None:
+        assert (info["leaves"], info["dense_blocks"], info["lowrank_blocks"]) == expect
+
+
+def test_paper_scale_block_counts():
+    """Counts of the spec configurations (1D: block-tridiagonal near
+    field; 2D: 5 x 5 neighbourhood minus its corners per leaf)."""
+    i1 = hmat.plan_info(W.levy_1d(65536), W.default_opts(leaf=256))
+    assert (i1["leaves"], i1["dense_blocks"], i1["lowrank_blocks"]) == (256, 766, 1482)
+    i2 = hmat.plan_info(W.frac_lap_2d(256), W.default_opts(leaf=256))
+    assert (i2["leaves"], i2["dense_blocks"], i2["lowrank_blocks"]) == (256, 4692, 13444)
+
+
+def test_morton_order_2d_is_z_curve():
+    row0, m, col0, nc, typ, perm = hmat.plan_blocks(W.frac_lap_2d(4), W.default_opts(leaf=1))
+    # Z-order of a 4 x 4 grid (axis 0 fastest in natural numbering)
+    z = [0, 1, 4, 5, 2, 3, 6, 7, 8, 9, 12, 13, 10, 11, 14, 15]
+    assert perm.tolist() == z
+
+
+def test_bad_arguments_are_rejected(lib):
+    p = W.frac_lap_1d(100)
+    p["LW"] = 2.0 + 1e-3   # not a whole number of steps is only checked at build; plan ok
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, dim=3), W.default_opts())
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p, W.default_opts(leaf=0))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, s=1.5), W.default_opts())
