@@ -140,6 +140,25 @@ int hm_plan_info(const hm_problem* prob, const hm_opts* opts, hm_stats_t* info);
 int hm_plan_blocks(const hm_problem* prob, const hm_opts* opts, int* count, int* row0,
                    int* m, int* col0, int* ncols, int* type, int* perm);
 
+/* Host-only dry run of hm_factor's planning (no GPU needed). */
+typedef struct hm_factor_plan_t {
+  int64_t fact_ops;      /* dense operations in the H-LU schedule */
+  int fact_waves;        /* dependency waves of the H-LU schedule */
+  int64_t solve_ops;     /* operations of one forward + backward H-triangular solve */
+  int solve_waves;
+  int64_t bad_spans;     /* operands outside every allocation (must be 0) */
+  int64_t arena_bytes;   /* device bytes the factors and temporaries would take */
+  int kf;                /* rank cap of the factors' low-rank blocks */
+} hm_factor_plan_t;
+
+/*
+ * hm_plan_factor: expand the H-LU of I + theta G (App. "LU Decomposition")
+ * and the triangular solves into their operation schedules with fake device
+ * addresses, assuming every ACA block reaches its rank cap, and check that
+ * every operand lies inside an allocation.  Host memory only.
+ */
+int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm_factor_plan_t* out);
+
 /*
  * hm_build: assemble G as an H-matrix on the current device.
  * Steps (all on the device after the host-side tree): row-independent

@@ -71,6 +71,43 @@ NuParams nu_params(const hm_problem& p, const Plan& P, int* nw_out, std::string&
 
 }  // namespace
 
+void make_descs(const Plan& P, const hm_opts& o, std::vector<DenseDesc>& dd, std::vector<LRDesc>& ld,
+                int64_t& dpool, int64_t& upool, int64_t& vpool) {
+  dd.clear();
+  ld.clear();
+  int64_t off = 0;
+  for (int b : P.dense_block) {
+    const Block& B = P.bl[b];
+    DenseDesc D{};
+    D.r0 = P.cl[B.t].begin;
+    D.m = P.cl[B.t].end - D.r0;
+    D.c0 = P.cl[B.s].begin;
+    D.n = P.cl[B.s].end - D.c0;
+    D.ld = (D.n + 3) & ~3;
+    D.off = off;
+    off += (int64_t)D.m * D.ld;
+    dd.push_back(D);
+  }
+  int64_t uo = 0, vo = 0;
+  for (int b : P.lr_block) {
+    const Block& B = P.bl[b];
+    LRDesc L{};
+    L.r0 = P.cl[B.t].begin;
+    L.m = P.cl[B.t].end - L.r0;
+    L.c0 = P.cl[B.s].begin;
+    L.n = P.cl[B.s].end - L.c0;
+    L.kcap = std::min(o.max_rank, std::min(L.m, L.n));
+    L.uoff = uo;
+    L.voff = vo;
+    uo += (int64_t)L.m * L.kcap;
+    vo += (int64_t)L.n * L.kcap;
+    ld.push_back(L);
+  }
+  dpool = off;
+  upool = uo;
+  vpool = vo;
+}
+
 }  // namespace hm
 
 namespace hm {
@@ -187,20 +224,9 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
   H->ectx.tab = H->d_tab;
   H->ectx.gc = H->d_gc;
 
-  // dense leaves
-  int64_t off = 0;
-  for (int b : P.dense_block) {
-    const Block& B = P.bl[b];
-    DenseDesc D{};
-    D.r0 = P.cl[B.t].begin;
-    D.m = P.cl[B.t].end - D.r0;
-    D.c0 = P.cl[B.s].begin;
-    D.n = P.cl[B.s].end - D.c0;
-    D.ld = (D.n + 3) & ~3;
-    D.off = off;
-    off += (int64_t)D.m * D.ld;
-    H->h_dd.push_back(D);
-  }
+  // dense leaves and low-rank descriptors (host layout)
+  int64_t off = 0, uo = 0, vo = 0;
+  make_descs(P, *opts, H->h_dd, H->h_ld, off, uo, vo);
   H->d_pool = off;
   HM_TRY(A.upload(&H->d_dd, H->h_dd));
   HM_TRY(A.alloc((void**)&H->d_D, sizeof(double) * (size_t)std::max<int64_t>(off, 1)));
@@ -208,22 +234,9 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
   HM_TRY(launch_near_fill(H->ectx, H->d_dd, (int)H->h_dd.size(), H->d_D, st));
 
   // admissible blocks: ACA
-  int64_t uo = 0, vo = 0;
-  for (int b : P.lr_block) {
-    const Block& B = P.bl[b];
-    LRDesc L{};
-    L.r0 = P.cl[B.t].begin;
-    L.m = P.cl[B.t].end - L.r0;
-    L.c0 = P.cl[B.s].begin;
-    L.n = P.cl[B.s].end - L.c0;
-    L.kcap = std::min(opts->max_rank, std::min(L.m, L.n));
-    L.uoff = uo;
-    L.voff = vo;
-    uo += (int64_t)L.m * L.kcap;
-    vo += (int64_t)L.n * L.kcap;
+  for (const LRDesc& L : H->h_ld) {
     H->max_m = std::max(H->max_m, L.m);
     H->kmax = std::max(H->kmax, L.kcap);
-    H->h_ld.push_back(L);
   }
   H->u_pool = uo;
   H->v_pool = vo;

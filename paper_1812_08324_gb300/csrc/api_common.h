@@ -101,6 +101,9 @@ struct hm_matrix {
 };
 
 namespace hm {
+// Host layout of the dense leaves and low-rank blocks of the plan.
+void make_descs(const Plan& P, const hm_opts& o, std::vector<DenseDesc>& dd, std::vector<LRDesc>& ld,
+                int64_t& dpool, int64_t& upool, int64_t& vpool);
 // y = alpha x + beta G x + gamma (w1 + w2) + w3 on Morton-order device vectors.
 int hm_matvec_morton(const hm_matrix* H, double alpha, double beta, const double* xm, double gamma,
                      const double* w1m, const double* w2m, const double* w3m, double* ym,

@@ -1,30 +1,321 @@
-// C ABI: H-LU factorisation, triangular solves and Crank-Nicolson steps.
+// C ABI: H-LU factorisation (hm_factor), H-triangular solves (hm_solve) and
+// Crank-Nicolson steps with refinement (cn_step, cn_solve).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "api_common.h"
+#include "hlu_plan.h"
+#include "hm_device.cuh"
 
 using namespace hm;
 
 struct hm_factors {
-  int dummy;
+  const hm_matrix* H = nullptr;
+  double theta = 0.0;
+  int kf = 0;
+  Arena arena;
+  std::vector<void*> allocs;
+  DevSchedule solve;
+  FactorLayout F;
+  int* d_rank = nullptr;
+  double* d_y = nullptr;      // solve vector (Morton order)
+  double* d_vec = nullptr;    // cn work vectors: 6 x N
+  double* d_norm = nullptr;   // [|s|^2, |rhs|^2]
+  int64_t lu_bytes = 0;
+  int64_t fact_ops = 0;
+  int fact_waves = 0, solve_waves = 0;
+  std::vector<int> h_rank;
+  int capped = 0;
+  double fact_ms = 0.0;
 };
+
+namespace hm {
+namespace {
+
+__global__ void axpy_kernel(int N, double a, const double* x, double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) y[i] += a * x[i];
+}
+
+__global__ void copy_vec_kernel(int N, const double* x, double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) y[i] = x[i];
+}
+
+// out[0] = |a|^2, out[1] = |b|^2 (one CTA, deterministic order)
+__global__ void norms_kernel(int N, const double* a, const double* b, double* out) {
+  __shared__ double sc[32];
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sa += a[i] * a[i];
+    sb += b[i] * b[i];
+  }
+  sa = block_sum(sa, sc);
+  sb = block_sum(sb, sc);
+  if (threadIdx.x == 0) { out[0] = sa; out[1] = sb; }
+}
+
+int vgrid(int N) { return std::min((N + 255) / 256, 152 * 8); }
+
+// z = (LU)^{-1} b on Morton-order vectors (b may equal z)
+int solve_morton(const hm_factors* F, const double* b, double* z, cudaStream_t st) {
+  const int N = F->H->plan.N;
+  copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, b, F->d_y);
+  HM_TRY(run_schedule(F->solve, F->H->d_err, st));
+  copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, F->d_y, z);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+// One CN step on Morton-order vectors: u1 = CN(u0) with forcing f0, f1 (may be null).
+int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u0,
+                   const double* f0, const double* f1, double* u1, cudaStream_t st) {
+  const int N = H->plan.N;
+  const double th = 0.5 * dt;
+  double* rhs = F->d_vec;
+  double* s = F->d_vec + (size_t)N;
+  // rhs = u + theta G u + theta (f^n + f^{n+1})
+  HM_TRY(hm_matvec_morton(H, 1.0, th, u0, th, f0, f1, nullptr, rhs, st));
+  HM_TRY(solve_morton(F, rhs, u1, st));
+  const int sweeps = H->opts.refine_max;
+  for (int it = 0; it < sweeps; ++it) {
+    // s = rhs - (z - theta G z)
+    HM_TRY(hm_matvec_morton(H, -1.0, th, u1, 0.0, nullptr, nullptr, rhs, s, st));
+    if (it == sweeps - 1) norms_kernel<<<1, 1024, 0, st>>>(N, s, rhs, F->d_norm);
+    HM_TRY(solve_morton(F, s, s, st));
+    axpy_kernel<<<vgrid(N), 256, 0, st>>>(N, 1.0, s, u1);
+  }
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace hm
 
 extern "C" {
 
-int hm_factor(const hm_matrix*, double, void*, hm_factors** out) {
-  if (out) *out = nullptr;
-  set_error("hm_factor: not built yet");
-  return HM_ERR_ARG;
+int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) {
+  if (!out || !H) { set_error("null argument"); return HM_ERR_ARG; }
+  *out = nullptr;
+  if (!std::isfinite(theta)) { set_error("theta must be finite"); return HM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int maxr = 0;
+  for (int r : H->h_rank) maxr = std::max(maxr, r);
+  int kf = std::max(H->opts.lu_max_rank, maxr);
+  if (kf > TRUNC_MAXK / 2) {
+    set_error("factor rank cap " + std::to_string(kf) + " exceeds " + std::to_string(TRUNC_MAXK / 2));
+    return HM_ERR_RANK_CAP;
+  }
+  kf = std::max(kf, 1);
+  hm_factors* F = new hm_factors();
+  F->H = H;
+  F->theta = theta;
+  F->kf = kf;
+  auto fail = [&](int s) {
+    cudaDeviceSynchronize();
+    for (void* p : F->allocs) cudaFree(p);
+    F->arena.release();
+    delete F;
+    return s;
+  };
+  const int nlr = (int)H->h_ld.size();
+  const int N = H->plan.N;
+  int s = HM_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return HM_ERR_OOM;
+    F->allocs.push_back(*p);
+    return HM_OK;
+  };
+  if ((s = alloc((void**)&F->d_rank, sizeof(int) * std::max(nlr, 1))) != HM_OK) return fail(s);
+  if ((s = alloc((void**)&F->d_y, sizeof(double) * N)) != HM_OK) return fail(s);
+  if ((s = alloc((void**)&F->d_vec, sizeof(double) * 6 * (size_t)N)) != HM_OK) return fail(s);
+  if ((s = alloc((void**)&F->d_norm, sizeof(double) * 4)) != HM_OK) return fail(s);
+  if (nlr && cudaMemcpyAsync(F->d_rank, H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return fail(HM_ERR_CUDA);
+  cudaMemsetAsync(F->d_norm, 0, sizeof(double) * 4, st);
+
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  HluBuild hb;
+  s = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, kf, theta, H->opts.lu_tol,
+               F->d_rank, F->arena, hb);
+  if (s != HM_OK) { set_error(hb.err); return fail(s); }
+  DevSchedule fs;
+  std::vector<void*> fs_allocs;
+  s = upload_schedule(hb.waves, fs, fs_allocs);
+  if (s == HM_OK) s = run_schedule(fs, H->d_err, st);
+  cudaEventRecord(e1, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* p : fs_allocs) cudaFree(p);
+  if (s != HM_OK) { set_error("H-LU execution failed: " + std::string(cudaGetErrorString(cudaGetLastError()))); return fail(s); }
+  F->fact_ms = ms;
+  F->fact_ops = hb.ops;
+  F->fact_waves = (int)hb.waves.size();
+  F->F = hb.F;
+  int e = 0;
+  cudaMemcpy(&e, H->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e & DEVERR_ZEROPIVOT) { set_error("zero pivot in a leaf LU"); return fail(HM_ERR_DEVICE_ASSERT); }
+  if (e & DEVERR_RANKCAP) {
+    F->capped = 1;
+    int z = e & ~DEVERR_RANKCAP;
+    cudaMemcpy(H->d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  F->h_rank.assign(nlr, 0);
+  if (nlr) cudaMemcpy(F->h_rank.data(), F->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost);
+
+  // the solve schedule, replayed by every hm_solve
+  std::vector<Wave> sw;
+  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, F->d_y, F->arena, sw);
+  if (s != HM_OK) { set_error("solve planning failed"); return fail(s); }
+  s = upload_schedule(sw, F->solve, F->allocs);
+  if (s != HM_OK) { set_error("solve schedule upload failed"); return fail(s); }
+  F->solve_waves = (int)sw.size();
+  // bytes the two sweeps read: leaf inverses, off-diagonal dense blocks, low-rank factors
+  int64_t b = 0;
+  for (size_t d = 0; d < H->h_dd.size(); ++d) {
+    const DenseDesc& D = H->h_dd[d];
+    b += (int64_t)D.m * D.n * (D.r0 == D.c0 ? 2 : 1);
+  }
+  for (size_t q = 0; q < H->h_ld.size(); ++q) b += (int64_t)(H->h_ld[q].m + H->h_ld[q].n) * kf;
+  F->lu_bytes = 8 * b;
+  *out = F;
+  return HM_OK;
 }
-int hm_solve(const hm_factors*, const double*, double*, void*) { set_error("not built yet"); return HM_ERR_ARG; }
-int cn_step(const hm_matrix*, const hm_factors*, double, const double*, const double*, const double*,
-            double*, void*) { set_error("not built yet"); return HM_ERR_ARG; }
-int cn_solve(const hm_matrix*, const hm_factors*, double, int, int, double*, const double*, void*) {
-  set_error("not built yet");
-  return HM_ERR_ARG;
+
+void hm_factors_free(hm_factors* F) {
+  if (!F) return;
+  cudaDeviceSynchronize();
+  for (void* p : F->allocs) cudaFree(p);
+  F->arena.release();
+  delete F;
 }
-int hm_stats(const hm_matrix* H, const hm_factors*, hm_stats_t* out) {
+
+int hm_solve(const hm_factors* F, const double* b, double* x, void* stream) {
+  if (!F || !b || !x) { set_error("null argument"); return HM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const hm_matrix* H = F->H;
+  const int N = H->plan.N;
+  if (H->plan.dim == 1) return solve_morton(F, b, x, st);
+  double* t = F->d_vec + 5 * (size_t)N;
+  HM_TRY(launch_gather(H->d_perm, N, b, t, st));
+  HM_TRY(solve_morton(F, t, t, st));
+  return launch_scatter(H->d_perm, N, t, x, st);
+}
+
+int cn_step(const hm_matrix* H, const hm_factors* F, double dt, const double* u_n, const double* f_n,
+            const double* f_np1, double* u_np1, void* stream) {
+  if (!H || !F || !u_n || !u_np1) { set_error("null argument"); return HM_ERR_ARG; }
+  if (u_n == u_np1) { set_error("u_np1 must not alias u_n"); return HM_ERR_ARG; }
+  if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
+  if (!(dt > 0.0) || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+    set_error("factors must come from hm_factor(H, -dt/2)");
+    return HM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  hm_factors* Fm = const_cast<hm_factors*>(F);
+  const int N = H->plan.N;
+  if (H->plan.dim == 1) return cn_step_morton(H, Fm, dt, u_n, f_n, f_np1, u_np1, st);
+  double* um = Fm->d_vec + 2 * (size_t)N;
+  double* f0 = Fm->d_vec + 3 * (size_t)N;
+  double* f1 = Fm->d_vec + 4 * (size_t)N;
+  double* u1 = Fm->d_vec + 5 * (size_t)N;
+  HM_TRY(launch_gather(H->d_perm, N, u_n, um, st));
+  if (f_n) HM_TRY(launch_gather(H->d_perm, N, f_n, f0, st));
+  if (f_np1) HM_TRY(launch_gather(H->d_perm, N, f_np1, f1, st));
+  HM_TRY(cn_step_morton(H, Fm, dt, um, f_n ? f0 : nullptr, f_np1 ? f1 : nullptr, u1, st));
+  return launch_scatter(H->d_perm, N, u1, u_np1, st);
+}
+
+int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int step0, double* u,
+             const double* f, void* stream) {
+  if (!H || !F || !u || steps < 0 || step0 < 0) { set_error("bad argument"); return HM_ERR_ARG; }
+  if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
+  if (!(dt > 0.0) || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+    set_error("factors must come from hm_factor(H, -dt/2)");
+    return HM_ERR_ARG;
+  }
+  (void)step0;  // the levels of f are relative to step0; the operator is time independent
+  cudaStream_t st = (cudaStream_t)stream;
+  hm_factors* Fm = const_cast<hm_factors*>(F);
+  const int N = H->plan.N;
+  double* ua = Fm->d_vec + 2 * (size_t)N;
+  double* ub = Fm->d_vec + 5 * (size_t)N;
+  double* f0 = Fm->d_vec + 3 * (size_t)N;
+  double* f1 = Fm->d_vec + 4 * (size_t)N;
+  const bool perm = H->plan.dim == 2;
+  if (perm) HM_TRY(launch_gather(H->d_perm, N, u, ua, st));
+  else copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, u, ua);
+  for (int k = 0; k < steps; ++k) {
+    const double* fa = nullptr;
+    const double* fb = nullptr;
+    if (f) {
+      const double* g0 = f + (size_t)k * N;
+      const double* g1 = f + (size_t)(k + 1) * N;
+      if (perm) {
+        HM_TRY(launch_gather(H->d_perm, N, g0, f0, st));
+        HM_TRY(launch_gather(H->d_perm, N, g1, f1, st));
+        fa = f0;
+        fb = f1;
+      } else {
+        fa = g0;
+        fb = g1;
+      }
+    }
+    HM_TRY(cn_step_morton(H, Fm, dt, ua, fa, fb, ub, st));
+    std::swap(ua, ub);
+  }
+  if (perm) return launch_scatter(H->d_perm, N, ua, u, st);
+  copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, ua, u);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm_factor_plan_t* out) {
+  if (!prob || !opts || !out) { set_error("null argument"); return HM_ERR_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  Plan P;
+  std::string err;
+  if (make_plan(*prob, *opts, P, err) != HM_OK) { set_error(err); return HM_ERR_ARG; }
+  std::vector<DenseDesc> dd;
+  std::vector<LRDesc> ld;
+  int64_t dp = 0, up = 0, vp = 0;
+  make_descs(P, *opts, dd, ld, dp, up, vp);
+  int maxr = 0;
+  for (auto& L : ld) maxr = std::max(maxr, L.kcap);
+  int kf = std::max(opts->lu_max_rank, maxr);
+  if (kf > TRUNC_MAXK / 2) { set_error("factor rank cap too large"); return HM_ERR_RANK_CAP; }
+  Arena A;
+  A.fake = true;
+  // fake storage of the H-matrix and of the factor ranks
+  double* fD = A.alloc(std::max<int64_t>(dp, 1));
+  double* fU = A.alloc(std::max<int64_t>(up, 1));
+  double* fV = A.alloc(std::max<int64_t>(vp, 1));
+  int* frank = (int*)A.alloc((int64_t)ld.size() / 2 + 1);
+  double* fy = A.alloc(P.N);
+  HluBuild hb;
+  int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb);
+  if (s != HM_OK) { set_error("planning failed: " + hb.err); return s; }
+  std::vector<Wave> sw;
+  s = plan_solve(P, dd, ld, hb.F, fy, A, sw);
+  if (s != HM_OK) { set_error("solve planning failed"); return s; }
+  std::string first;
+  int64_t bad = check_spans(hb.waves, A.ranges, first) + check_spans(sw, A.ranges, first);
+  int64_t sops = 0;
+  for (auto& w : sw) sops += w.gemm.size() + w.copy.size() + w.lu.size() + w.trunc.size() + w.reduce.size();
+  out->fact_ops = hb.ops;
+  out->fact_waves = (int)hb.waves.size();
+  out->solve_ops = sops;
+  out->solve_waves = (int)sw.size();
+  out->bad_spans = bad;
+  out->arena_bytes = A.total * (int64_t)sizeof(double);
+  out->kf = kf;
+  if (bad) set_error("operand outside its allocation: " + first);
+  return HM_OK;
+}
+
+int hm_stats(const hm_matrix* H, const hm_factors* F, hm_stats_t* out) {
   if (!H || !out) { set_error("null argument"); return HM_ERR_ARG; }
   std::memset(out, 0, sizeof(*out));
   const Plan& P = H->plan;
@@ -43,11 +334,25 @@ int hm_stats(const hm_matrix* H, const hm_factors*, hm_stats_t* out) {
   }
   out->dense_entries = de;
   out->lowrank_entries = le;
-  out->h_bytes = 8 * (de + le);
   out->max_rank_seen = mr;
   out->rank_capped_blocks = H->capped_blocks;
+  // bytes one H-matvec streams: dense leaves, and the U, V columns up to each block's cap
+  int64_t hb = de;
+  for (size_t q = 0; q < H->h_ld.size(); ++q) hb += (int64_t)(H->h_ld[q].m + H->h_ld[q].n) * H->h_rank[q];
+  out->h_bytes = 8 * hb;
+  if (F) {
+    out->lu_bytes = F->lu_bytes;
+    int m2 = 0;
+    for (int r : F->h_rank) m2 = std::max(m2, r);
+    out->lu_max_rank_seen = m2;
+    out->lu_rank_capped = F->capped;
+    double nrm[2] = {0, 0};
+    if (cudaDeviceSynchronize() != cudaSuccess) return HM_ERR_CUDA;
+    cudaMemcpy(nrm, F->d_norm, sizeof(nrm), cudaMemcpyDeviceToHost);
+    out->last_refine_iters = H->opts.refine_max;
+    out->last_refine_resid = nrm[1] > 0 ? std::sqrt(nrm[0] / nrm[1]) : 0.0;
+  }
   return HM_OK;
 }
-void hm_factors_free(hm_factors* F) { delete F; }
 
 }  // extern "C"

@@ -1,0 +1,908 @@
+// Symbolic expansion of H-LU and of the H-triangular solves (App. "LU
+// Decomposition") into dense operations with row-segment dependency waves.
+//
+// H-LU of a diagonal H-block with children A_ij (rows/cols split alike):
+//   for i: LU(A_ii); for j > i: L_ii U_ij = A_ij, L_ji U_ii = A_ji;
+//          for j, l > i: A_jl -= L_ji U_il
+// with the triangular solves of the appendix (full right-hand side: dense
+// solve; low-rank right-hand side B1 B2': (L^{-1} B1) B2'; H right-hand side:
+// block forward substitution).  Leaf LU is unpivoted and also forms the
+// inverses of the leaf factors, so leaf triangular solves become products.
+// Sums of low-rank terms are recompressed at relative tolerance lu_tol
+// (eps_2 of Sec. "Application") and the rank cap kf.
+#include <algorithm>
+#include <cstring>
+
+#include "hlu_plan.h"
+
+namespace hm {
+
+double* Arena::alloc(int64_t n) {
+  n = (n + 3) & ~int64_t(3);
+  if (n > left) {
+    int64_t chunk = std::max<int64_t>(n, int64_t(1) << 25);
+    void* p = nullptr;
+    if (fake) {
+      p = (void*)fake_next;
+      fake_next += (uintptr_t)(chunk * sizeof(double)) + 4096;
+    } else {
+      if (cudaMalloc(&p, chunk * sizeof(double)) != cudaSuccess) {
+        status = HM_ERR_OOM;
+        return nullptr;
+      }
+      chunks.push_back(p);
+    }
+    ranges.push_back({(uintptr_t)p, (uintptr_t)p + (uintptr_t)(chunk * sizeof(double))});
+    cur = (double*)p;
+    left = chunk;
+  }
+  double* r = cur;
+  cur += n;
+  left -= n;
+  total += n;
+  return r;
+}
+
+void Arena::release() {
+  for (void* p : chunks) cudaFree(p);
+  chunks.clear();
+  ranges.clear();
+  cur = nullptr;
+  left = 0;
+}
+
+namespace {
+
+// Last write / last read wave per segment of every buffer.  Regular buffers
+// are split into row segments; pooled temporaries into 64 element ranges.
+struct Tracker {
+  struct Buf {
+    int seg;
+    bool elem = false;
+    const double* base = nullptr;
+    std::vector<int> lw, lr;
+  };
+  std::vector<Buf> bufs;
+  int add_elem(const double* base, int64_t cap) {
+    Buf b;
+    b.elem = true;
+    b.base = base;
+    b.seg = (int)std::max<int64_t>(1, (cap + 63) / 64);
+    b.lw.assign(64, -1);
+    b.lr.assign(64, -1);
+    bufs.push_back(b);
+    return (int)bufs.size() - 1;
+  }
+  int add(int rows, int seg) {
+    Buf b;
+    b.seg = std::max(1, seg);
+    int ns = std::max(1, (rows + b.seg - 1) / b.seg);
+    b.lw.assign(ns, -1);
+    b.lr.assign(ns, -1);
+    bufs.push_back(b);
+    return (int)bufs.size() - 1;
+  }
+};
+
+struct Acc {
+  const View* v;
+  bool write;
+};
+
+class Emitter {
+ public:
+  Emitter(std::vector<Wave>& w, Arena& a, int seg) : waves(w), A(a), seg_default(seg) {}
+
+  std::vector<Wave>& waves;
+  Arena& A;
+  Tracker T;
+  int seg_default;
+  int64_t nops = 0;
+  int status = HM_OK;
+
+  View new_mat(int rows, int cols, bool colmajor, int seg = -1) {
+    View v;
+    v.rows = rows;
+    v.cols = cols;
+    v.p = A.alloc((int64_t)rows * cols);
+    if (!v.p) status = HM_ERR_OOM;
+    if (colmajor) { v.rs = 1; v.cs = rows; } else { v.rs = cols; v.cs = 1; }
+    v.buf = T.add(rows, seg < 0 ? seg_default : seg);
+    v.br0 = 0;
+    v.br1 = rows;
+    return v;
+  }
+
+  // Temporaries come from a FIFO pool per size class; a recycled buffer keeps
+  // its dependency tracker, so its next writer waits for its last readers.
+  struct Pooled {
+    double* p;
+    int buf;
+  };
+  std::vector<std::vector<Pooled>> pool = std::vector<std::vector<Pooled>>(64);
+  std::vector<size_t> pool_head = std::vector<size_t>(64, 0);
+
+  static int size_class(int64_t n) {
+    int c = 0;
+    while ((int64_t(1) << c) < n) ++c;
+    return c;
+  }
+
+  View tmp(int rows, int cols, bool colmajor) {
+    int64_t n = std::max<int64_t>(1, (int64_t)rows * cols);
+    int c = size_class(n);
+    View v;
+    v.rows = rows;
+    v.cols = cols;
+    if (colmajor) { v.rs = 1; v.cs = rows; } else { v.rs = cols; v.cs = 1; }
+    v.br0 = 0;
+    v.br1 = 1;
+    auto& fl = pool[c];
+    if (pool_head[c] < fl.size()) {
+      v.p = fl[pool_head[c]].p;
+      v.buf = fl[pool_head[c]].buf;
+      ++pool_head[c];
+    } else {
+      v.p = A.alloc(int64_t(1) << c);
+      if (!v.p) status = HM_ERR_OOM;
+      v.buf = T.add_elem(v.p, int64_t(1) << c);
+    }
+    v.tr = false;
+    return v;
+  }
+
+  void release(const View& v) {
+    int64_t n = std::max<int64_t>(1, (int64_t)v.rows * v.cols);
+    pool[size_class(n)].push_back({v.p, v.buf});
+  }
+
+  View wrap(double* p, int rows, int cols, int64_t rs, int64_t cs, int seg = -1) {
+    View v;
+    v.p = p;
+    v.rows = rows;
+    v.cols = cols;
+    v.rs = rs;
+    v.cs = cs;
+    v.buf = T.add(rows, seg < 0 ? seg_default : seg);
+    v.br0 = 0;
+    v.br1 = rows;
+    return v;
+  }
+
+  static void seg_range(const Tracker::Buf& B, const View& v, int& s0, int& s1) {
+    const int ns = (int)B.lw.size();
+    if (B.elem) {
+      int64_t off = v.p - B.base;
+      int64_t span = (int64_t)(std::max(v.rows, 1) - 1) * (v.rs < 0 ? -v.rs : v.rs) +
+                     (int64_t)(std::max(v.cols, 1) - 1) * (v.cs < 0 ? -v.cs : v.cs) + 1;
+      s0 = (int)std::min<int64_t>(off / B.seg, ns - 1);
+      s1 = (int)std::min<int64_t>((off + span - 1) / B.seg, ns - 1);
+    } else {
+      s0 = std::min(v.br0 / B.seg, ns - 1);
+      s1 = std::min((std::max(v.br1, v.br0 + 1) - 1) / B.seg, ns - 1);
+    }
+  }
+
+  int place(std::initializer_list<Acc> acc) {
+    int w = -1;
+    for (const Acc& a : acc) {
+      const View& v = *a.v;
+      Tracker::Buf& B = T.bufs[v.buf];
+      int s0, s1;
+      seg_range(B, v, s0, s1);
+      for (int s = s0; s <= s1; ++s) {
+        w = std::max(w, B.lw[s]);
+        if (a.write) w = std::max(w, B.lr[s]);
+      }
+    }
+    ++w;
+    for (const Acc& a : acc) {
+      const View& v = *a.v;
+      Tracker::Buf& B = T.bufs[v.buf];
+      int s0, s1;
+      seg_range(B, v, s0, s1);
+      for (int s = s0; s <= s1; ++s) {
+        if (a.write) B.lw[s] = w;
+        else B.lr[s] = std::max(B.lr[s], w);
+      }
+    }
+    if ((int)waves.size() <= w) waves.resize(w + 1);
+    ++nops;
+    return w;
+  }
+
+  // C = beta C + alpha A B
+  void gemm(const View& C, double alpha, const View& Am, const View& Bm, double beta) {
+    if (C.rows == 0 || C.cols == 0) return;
+    if (Am.cols != Bm.rows || Am.rows != C.rows || Bm.cols != C.cols) { status = HM_ERR_ARG; return; }
+    if (Am.cols == 0) {
+      if (beta != 1.0) copy(C, 0.0, nullptr, beta);
+      return;
+    }
+    int w = beta != 0.0 ? place({{&Am, false}, {&Bm, false}, {&C, false}, {&C, true}})
+                        : place({{&Am, false}, {&Bm, false}, {&C, true}});
+    GemmOp o{};
+    o.A = Am.p;
+    o.B = Bm.p;
+    o.C = C.p;
+    o.m = C.rows;
+    o.n = C.cols;
+    o.k = Am.cols;
+    o.ars = Am.rs;
+    o.acs = Am.cs;
+    o.brs = Bm.rs;
+    o.bcs = Bm.cs;
+    o.crs = C.rs;
+    o.ccs = C.cs;
+    o.alpha = alpha;
+    o.beta = beta;
+    waves[w].gemm.push_back(o);
+  }
+
+  // dst = beta dst + alpha src (src null: constant alpha)
+  void copy(const View& dst, double alpha, const View* src, double beta) {
+    if (dst.rows == 0 || dst.cols == 0) return;
+    int w;
+    if (src) {
+      w = beta != 0.0 ? place({{src, false}, {&dst, false}, {&dst, true}}) : place({{src, false}, {&dst, true}});
+    } else {
+      w = beta != 0.0 ? place({{&dst, false}, {&dst, true}}) : place({{&dst, true}});
+    }
+    CopyOp o{};
+    o.src = src ? src->p : nullptr;
+    o.dst = dst.p;
+    o.m = dst.rows;
+    o.n = dst.cols;
+    o.srs = src ? src->rs : 0;
+    o.scs = src ? src->cs : 0;
+    o.drs = dst.rs;
+    o.dcs = dst.cs;
+    o.alpha = alpha;
+    o.beta = beta;
+    waves[w].copy.push_back(o);
+  }
+
+  void lu(const View& Am, const View& Li, const View& Ui) {
+    int w = place({{&Am, false}, {&Am, true}, {&Li, true}, {&Ui, true}});
+    LuOp o{};
+    o.A = Am.p;
+    o.Li = Li.p;
+    o.Ui = Ui.p;
+    o.lda = Am.rs;
+    o.ldl = Li.rs;
+    o.ldu = Ui.rs;
+    o.m = Am.rows;
+    waves[w].lu.push_back(o);
+  }
+
+  // Gram matrix G = X' X (K x K row-major, fresh), split over 256-row chunks.
+  View gram(const View& X) {
+    const int K = X.cols;
+    View G = tmp(K, K, false);
+    const int CH = 256;
+    int nch = (X.rows + CH - 1) / CH;
+    if (nch <= 1) {
+      gemm(G, 1.0, X.T(), X, 0.0);
+      return G;
+    }
+    View parts = tmp(nch * K, K, false);
+    for (int c = 0; c < nch; ++c) {
+      int r0 = c * CH, nr = std::min(CH, X.rows - r0);
+      View Xc = X.sub(r0, 0, nr, K);
+      gemm(parts.sub(c * K, 0, K, K), 1.0, Xc.T(), Xc, 0.0);
+    }
+    int w = place({{&parts, false}, {&G, true}});
+    ReduceOp o{};
+    o.parts = parts.p;
+    o.dst = G.p;
+    o.stride = (int64_t)K * K;
+    o.count = (int64_t)K * K;
+    o.nparts = nch;
+    waves[w].reduce.push_back(o);
+    release(parts);
+    return G;
+  }
+
+  void trunc(const View& GA, const View& GB, const View& TA, const View& TB, int* rank,
+             const View& rankv, int K, int kf, double tol) {
+    int w = place({{&GA, false}, {&GB, false}, {&TA, true}, {&TB, true}, {&rankv, true}});
+    TruncOp o{};
+    o.GA = GA.p;
+    o.GB = GB.p;
+    o.TA = TA.p;
+    o.TB = TB.p;
+    o.rank = rank;
+    o.K = K;
+    o.kf = kf;
+    o.tol = tol;
+    waves[w].trunc.push_back(o);
+  }
+};
+
+// ---------------------------------------------------------------- H-LU
+
+struct LRState {
+  View U[2], V[2];   // slots: m x 2kf and n x 2kf, column-major
+  View rankv;        // dependency token for the rank word
+  int cur = 0;
+  int m = 0, n = 0;
+  int* rank = nullptr;
+};
+
+struct Target {
+  int b;          // block id
+  int ro, co;     // offset inside the block
+  int nr, nc;
+};
+
+class HLU {
+ public:
+  HLU(const Plan& P_, Emitter& E_, int kf_, double tol_) : P(P_), E(E_), kf(kf_), tol(tol_) {}
+
+  const Plan& P;
+  Emitter& E;
+  int kf;
+  double tol;
+  std::vector<View> dense;        // per dense id: current storage
+  std::vector<View> linv, uinv;   // per dense id (diagonal leaves only)
+  std::vector<LRState> lr;
+
+  const Block& B(int b) const { return P.bl[b]; }
+  int rows(int b) const { const Cluster& c = P.cl[B(b).t]; return c.end - c.begin; }
+  int cols(int b) const { const Cluster& c = P.cl[B(b).s]; return c.end - c.begin; }
+  int child(int b, int i, int j) const { return B(b).child0 + i * B(b).ncc + j; }
+  int nrc(int b) const { return B(b).type == BT_H ? B(b).nrc : 1; }
+  int ncc(int b) const { return B(b).type == BT_H ? B(b).ncc : 1; }
+  int sub(int b, int i, int j) const { return B(b).type == BT_H ? child(b, i, j) : b; }
+  // offset of child row cluster inside the parent row cluster
+  int roff(int parent, int ch) const { return P.cl[B(ch).t].begin - P.cl[B(parent).t].begin; }
+  int coff(int parent, int ch) const { return P.cl[B(ch).s].begin - P.cl[B(parent).s].begin; }
+
+  View lrU(int q) { return lr[q].U[lr[q].cur].sub(0, 0, lr[q].m, kf); }
+  View lrV(int q) { return lr[q].V[lr[q].cur].sub(0, 0, lr[q].n, kf); }
+
+  // ---- leaf LU with inverses of both factors
+  void luinv(const View& Am, const View& Li, const View& Ui) {
+    const int m = Am.rows;
+    if (m <= LU_BASE) { E.lu(Am, Li, Ui); return; }
+    const int h = m / 2, r = m - h;
+    View A11 = Am.sub(0, 0, h, h), A12 = Am.sub(0, h, h, r), A21 = Am.sub(h, 0, r, h), A22 = Am.sub(h, h, r, r);
+    View Li11 = Li.sub(0, 0, h, h), Li21 = Li.sub(h, 0, r, h), Li12 = Li.sub(0, h, h, r), Li22 = Li.sub(h, h, r, r);
+    View Ui11 = Ui.sub(0, 0, h, h), Ui12 = Ui.sub(0, h, h, r), Ui21 = Ui.sub(h, 0, r, h), Ui22 = Ui.sub(h, h, r, r);
+    luinv(A11, Li11, Ui11);
+    View T12 = E.tmp(h, r, false), T21 = E.tmp(r, h, false);
+    E.gemm(T12, 1.0, Li11, A12, 0.0);   // U12 = L11^{-1} A12
+    E.gemm(T21, 1.0, A21, Ui11, 0.0);   // L21 = A21 U11^{-1}
+    E.gemm(A22, -1.0, T21, T12, 1.0);   // Schur complement
+    luinv(A22, Li22, Ui22);
+    View X = E.tmp(r, h, false), Y = E.tmp(h, r, false);
+    E.gemm(X, 1.0, T21, Li11, 0.0);
+    E.gemm(Li21, -1.0, Li22, X, 0.0);   // (L^{-1})_21 = -L22^{-1} L21 L11^{-1}
+    E.gemm(Y, 1.0, T12, Ui22, 0.0);
+    E.gemm(Ui12, -1.0, Ui11, Y, 0.0);   // (U^{-1})_12 = -U11^{-1} U12 U22^{-1}
+    E.copy(Li12, 0.0, nullptr, 0.0);
+    E.copy(Ui21, 0.0, nullptr, 0.0);
+    E.release(T12);
+    E.release(T21);
+    E.release(X);
+    E.release(Y);
+  }
+
+  // ---- recompression of the low-rank sum held in the current slot (K columns)
+  void truncate(int q, int K) {
+    LRState& S = lr[q];
+    View Aall = S.U[S.cur].sub(0, 0, S.m, K), Ball = S.V[S.cur].sub(0, 0, S.n, K);
+    View GA = E.gram(Aall), GB = E.gram(Ball);
+    View TA = E.tmp(K, kf, false), TB = E.tmp(K, kf, false);
+    E.trunc(GA, GB, TA, TB, S.rank, S.rankv, K, kf, tol);
+    int nx = 1 - S.cur;
+    E.gemm(S.U[nx].sub(0, 0, S.m, kf), 1.0, Aall, TA, 0.0);
+    E.gemm(S.V[nx].sub(0, 0, S.n, kf), 1.0, Ball, TB, 0.0);
+    E.release(GA);
+    E.release(GB);
+    E.release(TA);
+    E.release(TB);
+    S.cur = nx;
+  }
+
+  // ---- tgt += alpha Up Vp'
+  void add_lr(const Target& tg, const View& Up, const View& Vp, double alpha) {
+    const Block& C = B(tg.b);
+    const int w = Up.cols;
+    if (w == 0 || tg.nr == 0 || tg.nc == 0) return;
+    if (C.type == BT_DENSE) {
+      E.gemm(dense[C.id].sub(tg.ro, tg.co, tg.nr, tg.nc), alpha, Up, Vp.T(), 1.0);
+      return;
+    }
+    if (C.type == BT_LR) {
+      if (w > kf) {
+        for (int c0 = 0; c0 < w; c0 += kf) {
+          int wc = std::min(kf, w - c0);
+          add_lr(tg, Up.sub(0, c0, Up.rows, wc), Vp.sub(0, c0, Vp.rows, wc), alpha);
+        }
+        return;
+      }
+      LRState& S = lr[C.id];
+      View Upend = S.U[S.cur].sub(0, kf, S.m, w), Vpend = S.V[S.cur].sub(0, kf, S.n, w);
+      if (tg.ro != 0 || tg.nr != S.m) E.copy(Upend, 0.0, nullptr, 0.0);
+      if (tg.co != 0 || tg.nc != S.n) E.copy(Vpend, 0.0, nullptr, 0.0);
+      E.copy(Upend.sub(tg.ro, 0, tg.nr, w), alpha, &Up, 0.0);
+      E.copy(Vpend.sub(tg.co, 0, tg.nc, w), 1.0, &Vp, 0.0);
+      truncate(C.id, kf + w);
+      return;
+    }
+    // H target: split over the children that intersect the target range
+    for (int i = 0; i < C.nrc; ++i)
+      for (int j = 0; j < C.ncc; ++j) {
+        int ch = child(tg.b, i, j);
+        int r0 = roff(tg.b, ch), r1 = r0 + rows(ch);
+        int c0 = coff(tg.b, ch), c1 = c0 + cols(ch);
+        int a0 = std::max(r0, tg.ro), a1 = std::min(r1, tg.ro + tg.nr);
+        int b0 = std::max(c0, tg.co), b1 = std::min(c1, tg.co + tg.nc);
+        if (a0 >= a1 || b0 >= b1) continue;
+        Target t2{ch, a0 - r0, b0 - c0, a1 - a0, b1 - b0};
+        add_lr(t2, Up.sub(a0 - tg.ro, 0, a1 - a0, w), Vp.sub(b0 - tg.co, 0, b1 - b0, w), alpha);
+      }
+  }
+
+  // ---- out += alpha A in   (A block (t, r), in |r| x k, out |t| x k)
+  void hgemm(const View& out, double alpha, int a, const View& in) {
+    const Block& A = B(a);
+    if (A.type == BT_DENSE) { E.gemm(out, alpha, dense[A.id], in, 1.0); return; }
+    if (A.type == BT_LR) {
+      View W = E.tmp(kf, in.cols, false);
+      E.gemm(W, 1.0, lrV(A.id).T(), in, 0.0);
+      E.gemm(out, alpha, lrU(A.id), W, 1.0);
+      E.release(W);
+      return;
+    }
+    for (int i = 0; i < A.nrc; ++i)
+      for (int j = 0; j < A.ncc; ++j) {
+        int c = child(a, i, j);
+        hgemm(out.sub(roff(a, c), 0, rows(c), out.cols), alpha, c, in.sub(coff(a, c), 0, cols(c), in.cols));
+      }
+  }
+
+  // ---- out += alpha A' in   (A block (r, t), in |r| x k, out |t| x k)
+  void hgemm_t(const View& out, double alpha, int a, const View& in) {
+    const Block& A = B(a);
+    if (A.type == BT_DENSE) { E.gemm(out, alpha, dense[A.id].T(), in, 1.0); return; }
+    if (A.type == BT_LR) {
+      View W = E.tmp(kf, in.cols, false);
+      E.gemm(W, 1.0, lrU(A.id).T(), in, 0.0);
+      E.gemm(out, alpha, lrV(A.id), W, 1.0);
+      E.release(W);
+      return;
+    }
+    for (int i = 0; i < A.nrc; ++i)
+      for (int j = 0; j < A.ncc; ++j) {
+        int c = child(a, i, j);
+        hgemm_t(out.sub(coff(a, c), 0, cols(c), out.cols), alpha, c, in.sub(roff(a, c), 0, rows(c), in.cols));
+      }
+  }
+
+  // ---- X <- L^{-1} X for the diagonal block l (X: |t| x k, a view into storage)
+  void lsolve_mat(int l, const View& X) {
+    const Block& L = B(l);
+    if (L.type == BT_DENSE) {
+      View Tm = E.tmp(X.rows, X.cols, false);
+      E.gemm(Tm, 1.0, linv[L.id], X, 0.0);
+      E.copy(X, 1.0, &Tm, 0.0);
+      E.release(Tm);
+      return;
+    }
+    const int nc = L.nrc;
+    for (int a = 0; a < nc; ++a) {
+      int la = child(l, a, a);
+      View Xa = X.sub(roff(l, la), 0, rows(la), X.cols);
+      lsolve_mat(la, Xa);
+      for (int a2 = a + 1; a2 < nc; ++a2) {
+        int lb = child(l, a2, a);
+        hgemm(X.sub(roff(l, lb), 0, rows(lb), X.cols), -1.0, lb, Xa);
+      }
+    }
+  }
+
+  // ---- Y <- U^{-T} Y for the diagonal block u (Y: |s| x k)
+  void usolve_t_mat(int u, const View& Y) {
+    const Block& U = B(u);
+    if (U.type == BT_DENSE) {
+      View Tm = E.tmp(Y.rows, Y.cols, false);
+      E.gemm(Tm, 1.0, uinv[U.id].T(), Y, 0.0);
+      E.copy(Y, 1.0, &Tm, 0.0);
+      E.release(Tm);
+      return;
+    }
+    const int nc = U.nrc;
+    for (int a = 0; a < nc; ++a) {
+      int ua = child(u, a, a);
+      View Ya = Y.sub(roff(u, ua), 0, rows(ua), Y.cols);
+      usolve_t_mat(ua, Ya);
+      for (int a2 = a + 1; a2 < nc; ++a2) {
+        int ub = child(u, a, a2);  // U_{a, a2}; rows of Y_{a2} are its columns
+        hgemm_t(Y.sub(coff(u, ub), 0, cols(ub), Y.cols), -1.0, ub, Ya);
+      }
+    }
+  }
+
+  // ---- X <- L_ll^{-1} X  (X block with the row cluster of l)
+  void trsm_l(int l, int x) {
+    const Block& X = B(x);
+    if (X.type == BT_DENSE) {
+      const Block& L = B(l);
+      View Tm = E.new_mat(rows(x), cols(x), false);
+      E.gemm(Tm, 1.0, linv[L.id], dense[X.id], 0.0);
+      dense[X.id] = Tm;
+      return;
+    }
+    if (X.type == BT_LR) { lsolve_mat(l, lrU(X.id)); return; }
+    const Block& L = B(l);
+    if (L.type != BT_H) {
+      for (int j = 0; j < X.ncc; ++j) trsm_l(l, child(x, 0, j));
+      return;
+    }
+    for (int a = 0; a < L.nrc; ++a) {
+      for (int j = 0; j < X.ncc; ++j) trsm_l(child(l, a, a), child(x, a, j));
+      for (int a2 = a + 1; a2 < L.nrc; ++a2)
+        for (int j = 0; j < X.ncc; ++j) {
+          int c = child(x, a2, j);
+          mulsub(Target{c, 0, 0, rows(c), cols(c)}, child(l, a2, a), child(x, a, j));
+        }
+    }
+  }
+
+  // ---- X <- X U_uu^{-1}  (X block with the column cluster of u)
+  void trsm_u(int u, int x) {
+    const Block& X = B(x);
+    if (X.type == BT_DENSE) {
+      const Block& U = B(u);
+      View Tm = E.new_mat(rows(x), cols(x), false);
+      E.gemm(Tm, 1.0, dense[X.id], uinv[U.id], 0.0);
+      dense[X.id] = Tm;
+      return;
+    }
+    if (X.type == BT_LR) { usolve_t_mat(u, lrV(X.id)); return; }
+    const Block& U = B(u);
+    if (U.type != BT_H) {
+      for (int i = 0; i < X.nrc; ++i) trsm_u(u, child(x, i, 0));
+      return;
+    }
+    for (int a = 0; a < U.nrc; ++a) {
+      for (int i = 0; i < X.nrc; ++i) trsm_u(child(u, a, a), child(x, i, a));
+      for (int a2 = a + 1; a2 < U.nrc; ++a2)
+        for (int i = 0; i < X.nrc; ++i) {
+          int c = child(x, i, a2);
+          mulsub(Target{c, 0, 0, rows(c), cols(c)}, child(x, i, a), child(u, a, a2));
+        }
+    }
+  }
+
+  // ---- tgt -= A B  (A block (t', r), B block (r, s'), tgt rows t', cols s')
+  void mulsub(const Target& tg, int a, int b) {
+    const Block& A = B(a);
+    const Block& Bb = B(b);
+    if (A.type == BT_LR) {
+      View W = E.tmp(cols(b), kf, true);
+      E.copy(W, 0.0, nullptr, 0.0);
+      hgemm_t(W, 1.0, b, lrV(A.id));           // W = B' V_A
+      add_lr(tg, lrU(A.id), W, -1.0);
+      E.release(W);
+      return;
+    }
+    if (Bb.type == BT_LR) {
+      View W = E.tmp(rows(a), kf, true);
+      E.copy(W, 0.0, nullptr, 0.0);
+      hgemm(W, 1.0, a, lrU(Bb.id));            // W = A U_B
+      add_lr(tg, W, lrV(Bb.id), -1.0);
+      E.release(W);
+      return;
+    }
+    const Block& C = B(tg.b);
+    if (A.type == BT_DENSE && Bb.type == BT_DENSE) {
+      if (C.type == BT_DENSE) {
+        E.gemm(dense[C.id].sub(tg.ro, tg.co, tg.nr, tg.nc), -1.0, dense[A.id], dense[Bb.id], 1.0);
+      } else {
+        // product of two dense leaves into a low-rank target: exact pieces of
+        // width <= kf over the inner dimension
+        add_lr(tg, dense[A.id], dense[Bb.id].T(), -1.0);
+      }
+      return;
+    }
+    const bool full = tg.ro == 0 && tg.co == 0 && tg.nr == rows(tg.b) && tg.nc == cols(tg.b);
+    const int nk = A.type == BT_H ? A.ncc : Bb.nrc;
+    if (C.type == BT_H && full) {
+      for (int i = 0; i < C.nrc; ++i)
+        for (int j = 0; j < C.ncc; ++j)
+          for (int l = 0; l < nk; ++l) {
+            int c = child(tg.b, i, j);
+            mulsub(Target{c, 0, 0, rows(c), cols(c)}, sub(a, i, l), sub(b, l, j));
+          }
+      return;
+    }
+    // low-rank / dense / partial target: recurse on virtual sub-blocks
+    const int nr = nrc(a), ncl = ncc(b);
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < ncl; ++j)
+        for (int l = 0; l < nk; ++l) {
+          int ai = sub(a, i, l), bj = sub(b, l, j);
+          int ro = tg.ro + (P.cl[B(ai).t].begin - P.cl[A.t].begin);
+          int co = tg.co + (P.cl[B(bj).s].begin - P.cl[Bb.s].begin);
+          mulsub(Target{tg.b, ro, co, rows(ai), cols(bj)}, ai, bj);
+        }
+  }
+
+  void hlu(int b) {
+    const Block& X = B(b);
+    if (X.type == BT_DENSE) {
+      int m = rows(b);
+      linv[X.id] = E.new_mat(m, m, false, LU_BASE);
+      uinv[X.id] = E.new_mat(m, m, false, LU_BASE);
+      luinv(dense[X.id], linv[X.id], uinv[X.id]);
+      return;
+    }
+    const int nc = X.nrc;
+    for (int i = 0; i < nc; ++i) {
+      hlu(child(b, i, i));
+      for (int j = i + 1; j < nc; ++j) {
+        trsm_l(child(b, i, i), child(b, i, j));
+        trsm_u(child(b, i, i), child(b, j, i));
+      }
+      for (int j = i + 1; j < nc; ++j)
+        for (int l = i + 1; l < nc; ++l) {
+          int c = child(b, j, l);
+          mulsub(Target{c, 0, 0, rows(c), cols(c)}, child(b, j, i), child(b, i, l));
+        }
+    }
+  }
+};
+
+}  // namespace
+
+int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
+             const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
+             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out) {
+  Emitter E(out.waves, arena, std::max(1, std::min(P.leaf, 256)));
+  HLU H(P, E, kf, lu_tol);
+  const int nd = (int)dd.size(), nl = (int)ld.size();
+  H.dense.resize(nd);
+  H.linv.resize(nd);
+  H.uinv.resize(nd);
+  H.lr.resize(nl);
+  // M = I + theta G in factor storage
+  for (int d = 0; d < nd; ++d) {
+    const DenseDesc& D = dd[d];
+    View src = E.wrap(const_cast<double*>(d_dense) + D.off, D.m, D.n, D.ld, 1);
+    View dst = E.new_mat(D.m, D.n, false, LU_BASE);
+    E.copy(dst, theta, &src, 0.0);
+    if (D.r0 == D.c0) {
+      View diag = dst;
+      diag.cols = 1;
+      diag.rs = dst.rs + 1;
+      diag.cs = 0;
+      E.copy(diag, 1.0, nullptr, 1.0);
+    }
+    H.dense[d] = dst;
+  }
+  for (int q = 0; q < nl; ++q) {
+    const LRDesc& L = ld[q];
+    LRState& S = H.lr[q];
+    S.m = L.m;
+    S.n = L.n;
+    S.rank = d_rank_f + q;
+    for (int s = 0; s < 2; ++s) {
+      S.U[s] = E.new_mat(L.m, 2 * kf, true);
+      S.V[s] = E.new_mat(L.n, 2 * kf, true);
+    }
+    S.rankv = E.new_mat(1, 1, false, 1);
+    int kc = std::min(L.kcap, kf);
+    View Us = E.wrap(const_cast<double*>(d_U) + L.uoff, L.m, kc, 1, L.m);
+    View Vs = E.wrap(const_cast<double*>(d_V) + L.voff, L.n, kc, 1, L.n);
+    E.copy(S.U[0].sub(0, 0, L.m, kc), theta, &Us, 0.0);
+    E.copy(S.V[0].sub(0, 0, L.n, kc), 1.0, &Vs, 0.0);
+    if (kc < kf) {
+      E.copy(S.U[0].sub(0, kc, L.m, kf - kc), 0.0, nullptr, 0.0);
+      E.copy(S.V[0].sub(0, kc, L.n, kf - kc), 0.0, nullptr, 0.0);
+    }
+  }
+  H.hlu(0);
+  if (E.status != HM_OK || arena.status != HM_OK) {
+    out.err = "H-LU planning failed (device memory or shape)";
+    return E.status != HM_OK ? E.status : arena.status;
+  }
+  out.ops = E.nops;
+  FactorLayout& F = out.F;
+  F.kf = kf;
+  F.d_rank = d_rank_f;
+  F.dense = H.dense;
+  F.linv.resize(nd, nullptr);
+  F.uinv.resize(nd, nullptr);
+  F.linv_ld.resize(nd, 0);
+  for (int d = 0; d < nd; ++d) {
+    if (H.linv[d].p) {
+      F.linv[d] = H.linv[d].p;
+      F.uinv[d] = H.uinv[d].p;
+      F.linv_ld[d] = H.linv[d].rs;
+    }
+  }
+  F.lr_u.resize(nl);
+  F.lr_v.resize(nl);
+  for (int q = 0; q < nl; ++q) {
+    F.lr_u[q] = H.lr[q].U[H.lr[q].cur].p;
+    F.lr_v[q] = H.lr[q].V[H.lr[q].cur].p;
+  }
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------- solves
+
+namespace {
+
+class Solver {
+ public:
+  Solver(const Plan& P_, Emitter& E_, const FactorLayout& F_, const std::vector<DenseDesc>& dd_,
+         const std::vector<LRDesc>& ld_)
+      : P(P_), E(E_), F(F_), dd(dd_), ld(ld_) {}
+  const Plan& P;
+  Emitter& E;
+  const FactorLayout& F;
+  const std::vector<DenseDesc>& dd;
+  const std::vector<LRDesc>& ld;
+  std::vector<View> dense, linv, uinv, U, V;
+
+  const Block& B(int b) const { return P.bl[b]; }
+  int child(int b, int i, int j) const { return B(b).child0 + i * B(b).ncc + j; }
+  int rows(int b) const { const Cluster& c = P.cl[B(b).t]; return c.end - c.begin; }
+  int cols(int b) const { const Cluster& c = P.cl[B(b).s]; return c.end - c.begin; }
+  int rbeg(int b) const { return P.cl[B(b).t].begin; }
+  int cbeg(int b) const { return P.cl[B(b).s].begin; }
+
+  void setup() {
+    const int nd = (int)dd.size(), nl = (int)ld.size();
+    dense.resize(nd);
+    linv.resize(nd);
+    uinv.resize(nd);
+    for (int d = 0; d < nd; ++d) {
+      const View& v = F.dense[d];
+      dense[d] = E.wrap(v.p, v.rows, v.cols, v.rs, v.cs);
+      if (F.linv[d]) {
+        linv[d] = E.wrap(F.linv[d], dd[d].m, dd[d].m, F.linv_ld[d], 1);
+        uinv[d] = E.wrap(F.uinv[d], dd[d].m, dd[d].m, F.linv_ld[d], 1);
+      }
+    }
+    U.resize(nl);
+    V.resize(nl);
+    for (int q = 0; q < nl; ++q) {
+      U[q] = E.wrap(F.lr_u[q], ld[q].m, F.kf, 1, ld[q].m);
+      V[q] = E.wrap(F.lr_v[q], ld[q].n, F.kf, 1, ld[q].n);
+    }
+  }
+
+  // y[rows of a] -= A y[cols of a]
+  void apply(const View& y, int a) {
+    const Block& A = B(a);
+    View yo = y.sub(rbeg(a), 0, rows(a), 1), yi = y.sub(cbeg(a), 0, cols(a), 1);
+    if (A.type == BT_DENSE) { E.gemm(yo, -1.0, dense[A.id], yi, 1.0); return; }
+    if (A.type == BT_LR) {
+      View W = E.tmp(F.kf, 1, false);
+      E.gemm(W, 1.0, V[A.id].T(), yi, 0.0);
+      E.gemm(yo, -1.0, U[A.id], W, 1.0);
+      E.release(W);
+      return;
+    }
+    for (int i = 0; i < A.nrc; ++i)
+      for (int j = 0; j < A.ncc; ++j) apply(y, child(a, i, j));
+  }
+
+  void fwd(const View& y, int b) {
+    const Block& X = B(b);
+    if (X.type == BT_DENSE) {
+      View yt = y.sub(rbeg(b), 0, rows(b), 1);
+      View Tm = E.tmp(rows(b), 1, false);
+      E.gemm(Tm, 1.0, linv[X.id], yt, 0.0);
+      E.copy(yt, 1.0, &Tm, 0.0);
+      E.release(Tm);
+      return;
+    }
+    for (int a = 0; a < X.nrc; ++a) {
+      fwd(y, child(b, a, a));
+      for (int a2 = a + 1; a2 < X.nrc; ++a2) apply(y, child(b, a2, a));
+    }
+  }
+
+  void bwd(const View& y, int b) {
+    const Block& X = B(b);
+    if (X.type == BT_DENSE) {
+      View yt = y.sub(rbeg(b), 0, rows(b), 1);
+      View Tm = E.tmp(rows(b), 1, false);
+      E.gemm(Tm, 1.0, uinv[X.id], yt, 0.0);
+      E.copy(yt, 1.0, &Tm, 0.0);
+      E.release(Tm);
+      return;
+    }
+    for (int a = X.nrc - 1; a >= 0; --a) {
+      bwd(y, child(b, a, a));
+      for (int a2 = a - 1; a2 >= 0; --a2) apply(y, child(b, a2, a));
+    }
+  }
+};
+
+}  // namespace
+
+int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
+               const FactorLayout& F, double* d_y, Arena& arena, std::vector<Wave>& waves) {
+  Emitter E(waves, arena, std::max(1, std::min(P.leaf, 256)));
+  Solver S(P, E, F, dd, ld);
+  S.setup();
+  View y = E.wrap(d_y, P.N, 1, 1, 0);
+  S.fwd(y, 0);
+  S.bwd(y, 0);
+  if (E.status != HM_OK || arena.status != HM_OK) return E.status != HM_OK ? E.status : arena.status;
+  return HM_OK;
+}
+
+}  // namespace hm
+
+namespace hm {
+
+namespace {
+struct SpanCheck {
+  const std::vector<std::pair<uintptr_t, uintptr_t>>& R;
+  int64_t bad = 0;
+  std::string first;
+  bool inside(const double* p, int64_t lo, int64_t hi) const {
+    uintptr_t a = (uintptr_t)(p + lo), b = (uintptr_t)(p + hi) + sizeof(double);
+    for (auto& r : R)
+      if (a >= r.first && b <= r.second) return true;
+    return false;
+  }
+  // element span of a strided m x n view
+  void view(const double* p, int m, int n, int64_t rs, int64_t cs, const char* what) {
+    if (m <= 0 || n <= 0) return;
+    int64_t lo = 0, hi = 0;
+    int64_t a = (int64_t)(m - 1) * rs, b = (int64_t)(n - 1) * cs;
+    lo = std::min<int64_t>(0, a) + std::min<int64_t>(0, b);
+    hi = std::max<int64_t>(0, a) + std::max<int64_t>(0, b);
+    if (!inside(p, lo, hi)) {
+      if (bad == 0) first = what;
+      ++bad;
+    }
+  }
+};
+}  // namespace
+
+int64_t check_spans(const std::vector<Wave>& waves,
+                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first) {
+  SpanCheck C{ranges};
+  for (const Wave& w : waves) {
+    for (const GemmOp& o : w.gemm) {
+      C.view(o.A, o.m, o.k, o.ars, o.acs, "gemm A");
+      C.view(o.B, o.k, o.n, o.brs, o.bcs, "gemm B");
+      C.view(o.C, o.m, o.n, o.crs, o.ccs, "gemm C");
+    }
+    for (const LuOp& o : w.lu) {
+      C.view(o.A, o.m, o.m, o.lda, 1, "lu A");
+      C.view(o.Li, o.m, o.m, o.ldl, 1, "lu Li");
+      C.view(o.Ui, o.m, o.m, o.ldu, 1, "lu Ui");
+      if (o.m > LU_BASE) { if (C.bad == 0) C.first = "lu size"; ++C.bad; }
+    }
+    for (const TruncOp& o : w.trunc) {
+      C.view(o.GA, o.K, o.K, o.K, 1, "trunc GA");
+      C.view(o.GB, o.K, o.K, o.K, 1, "trunc GB");
+      C.view(o.TA, o.K, o.kf, o.kf, 1, "trunc TA");
+      C.view(o.TB, o.K, o.kf, o.kf, 1, "trunc TB");
+      if (o.K > TRUNC_MAXK || o.kf > o.K) { if (C.bad == 0) C.first = "trunc size"; ++C.bad; }
+    }
+    for (const CopyOp& o : w.copy) {
+      if (o.src) C.view(o.src, o.m, o.n, o.srs, o.scs, "copy src");
+      C.view(o.dst, o.m, o.n, o.drs, o.dcs, "copy dst");
+    }
+    for (const ReduceOp& o : w.reduce) {
+      C.view(o.parts, o.nparts, (int)o.count, o.stride, 1, "reduce parts");
+      C.view(o.dst, 1, (int)o.count, 0, 1, "reduce dst");
+    }
+  }
+  first = C.first;
+  return C.bad;
+}
+
+}  // namespace hm

@@ -1,0 +1,93 @@
+// Host-side expansion of the H-LU factorisation and of the H-triangular
+// solves into scheduled operation lists (App. "LU Decomposition").
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hlu_ops.h"
+#include "hm_internal.h"
+
+namespace hm {
+
+// A strided matrix view on device memory plus the row range of its owning
+// buffer, for dependency tracking.
+struct View {
+  double* p = nullptr;
+  int rows = 0, cols = 0;
+  int64_t rs = 0, cs = 0;
+  int buf = -1;
+  int br0 = 0, br1 = 0;   // rows of the buffer touched
+  bool tr = false;        // rows of the view are columns of the buffer
+
+  View sub(int r0, int c0, int nr, int nc) const {
+    View v = *this;
+    v.p = p + r0 * rs + c0 * cs;
+    v.rows = nr;
+    v.cols = nc;
+    if (!tr) { v.br0 = br0 + r0; v.br1 = v.br0 + nr; }
+    return v;
+  }
+  View T() const {
+    View v = *this;
+    v.rows = cols;
+    v.cols = rows;
+    v.rs = cs;
+    v.cs = rs;
+    v.tr = !tr;
+    return v;
+  }
+};
+
+// Device arena: chunked bump allocation, freed as a whole.  In dry-run mode
+// (fake = true) it hands out addresses from a fake range without touching the
+// device, so that schedules can be planned and checked on a host without a GPU.
+struct Arena {
+  std::vector<void*> chunks;
+  std::vector<std::pair<uintptr_t, uintptr_t>> ranges;  // [begin, end) of every chunk
+  double* cur = nullptr;
+  int64_t left = 0;
+  int64_t total = 0;
+  int status = 0;
+  bool fake = false;
+  uintptr_t fake_next = uintptr_t(1) << 40;
+  double* alloc(int64_t n);   // doubles, 32-byte aligned
+  void release();
+};
+
+// Check that every operand of every operation lies inside one of `ranges`
+// (byte intervals).  Returns the number of violations.
+int64_t check_spans(const std::vector<Wave>& waves,
+                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first);
+
+// Final layout of the factors consumed by the solves.
+struct FactorLayout {
+  std::vector<double*> linv, uinv;       // per diagonal dense block (dense id), m x m row-major
+  std::vector<int64_t> linv_ld;
+  std::vector<View> dense;               // per dense block (current storage)
+  std::vector<double*> lr_u, lr_v;       // per LR block: U (m x kf), V (n x kf) column-major
+  int kf = 0;
+  int* d_rank = nullptr;                 // per LR block rank (device)
+};
+
+struct HluBuild {
+  std::vector<Wave> waves;
+  FactorLayout F;
+  int64_t ops = 0;
+  std::string err;
+};
+
+// Expand H-LU of M = I + theta G for the block tree of `P`.
+//  dense_pool/ld: H's dense leaves (DenseDesc order), lr: H's low-rank blocks,
+//  d_rank_f: device array (nlr) that will hold the factor ranks.
+int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
+             const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
+             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out);
+
+// Expand y = (LU)^{-1} y on the Morton-order device vector y (forward then
+// backward H-triangular substitution); the list is replayed for every solve.
+int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
+               const FactorLayout& F, double* d_y, Arena& arena, std::vector<Wave>& waves);
+
+}  // namespace hm

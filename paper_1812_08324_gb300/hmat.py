@@ -21,7 +21,7 @@ HM_FP64, HM_MIXED_FP32 = 0, 1
 EXPORTED = [
     "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
-    "hm_sync", "hm_stats", "hm_free", "hm_factors_free",
+    "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor",
 ]
 
 
@@ -46,6 +46,15 @@ class Stats(C.Structure):
                 ("rank_capped_blocks", C.c_int), ("lu_max_rank_seen", C.c_int),
                 ("lu_rank_capped", C.c_int), ("last_refine_iters", C.c_int),
                 ("last_refine_resid", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FactorPlan(C.Structure):
+    _fields_ = [("fact_ops", C.c_int64), ("fact_waves", C.c_int), ("solve_ops", C.c_int64),
+                ("solve_waves", C.c_int), ("bad_spans", C.c_int64), ("arena_bytes", C.c_int64),
+                ("kf", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +96,7 @@ def load() -> C.CDLL:
         "hm_stats": (i, [vp, vp, S]),
         "hm_free": (None, [vp]),
         "hm_factors_free": (None, [vp]),
+        "hm_plan_factor": (i, [P, O, d, C.POINTER(FactorPlan)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -147,6 +157,16 @@ def plan_info(problem: dict, opts: dict) -> dict:
     st = Stats()
     _check(lib.hm_plan_info(C.byref(make_problem(problem)), C.byref(make_opts(opts)), C.byref(st)))
     return st.as_dict()
+
+
+def plan_factor(problem: dict, opts: dict, theta: float = -5e-4) -> dict:
+    """Dry-run H-LU / solve schedules on the host (fake addresses): op and wave
+    counts, memory, and the operand-span check."""
+    lib = load()
+    fp = FactorPlan()
+    _check(lib.hm_plan_factor(C.byref(make_problem(problem)), C.byref(make_opts(opts)), theta,
+                              C.byref(fp)))
+    return fp.as_dict()
 
 
 def plan_blocks(problem: dict, opts: dict):
