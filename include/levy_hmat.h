@@ -230,6 +230,10 @@ int cn_step(const hm_matrix* H, const hm_factors* F, double dt, const double* u_
 int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int step0, double* u,
              const double* f, void* stream);
 
+/* Number of kernel launches this library has issued in the process so far
+ * (every launch helper counts itself; a persistent schedule counts once). */
+int64_t hm_launch_count(void);
+
 /* Synchronise the stream and report device-side errors of earlier calls. */
 int hm_sync(const hm_matrix* H, void* stream);
 

@@ -144,6 +144,7 @@ int launch_aca(const EntryCtx& E, const LRDesc* d_ld, int nlr, int max_m, double
   if (smem > 200 * 1024) return HM_ERR_ARG;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launches(1);
   aca_kernel<<<nlr, ACA_THREADS, smem, st>>>(E, d_ld, U, V, rank, capped, tol);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }

@@ -1,6 +1,7 @@
 // C ABI: planning, construction (hm_build), H-matvec and inspection calls.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 
 #include "api_common.h"
@@ -10,6 +11,9 @@ namespace hm {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches += n; }
 
 namespace {
 
@@ -138,6 +142,8 @@ const char* hm_error_string(int status) {
 }
 
 const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+int64_t hm_launch_count(void) { return g_launches.load(); }
 
 int hm_plan_info(const hm_problem* prob, const hm_opts* opts, hm_stats_t* info) {
   if (!info) { set_error("null info"); return HM_ERR_ARG; }

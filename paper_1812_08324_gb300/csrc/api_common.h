@@ -13,6 +13,7 @@
 namespace hm {
 
 void set_error(const std::string& msg);
+void count_launches(int n);
 
 // Record a failed CUDA call and turn it into a status code.
 #define HM_CK(call)                                                                    \

@@ -2,6 +2,8 @@
 // Crank-Nicolson steps with refinement (cn_step, cn_solve).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "api_common.h"
@@ -19,7 +21,8 @@ struct hm_factors {
   DevSchedule solve;
   FactorLayout F;
   int* d_rank = nullptr;
-  double* d_y = nullptr;      // solve vector (Morton order)
+  double* d_y = nullptr;      // solve input b (Morton order)
+  double* d_sv = nullptr;     // forward result y, backward result z, two accumulators: 4 x N
   double* d_vec = nullptr;    // cn work vectors: 6 x N
   double* d_norm = nullptr;   // [|s|^2, |rhs|^2]
   int64_t lu_bytes = 0;
@@ -56,12 +59,57 @@ __global__ void norms_kernel(int N, const double* a, const double* b, double* ou
 
 int vgrid(int N) { return std::min((N + 255) / 256, 152 * 8); }
 
+// Phase tracing (HM_PHASE_TRACE=1): run a schedule once with per-phase time
+// stamps and print where the time went, by the operation kinds of each phase.
+void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevSchedule& S, int* d_err,
+                    cudaStream_t st) {
+  unsigned long long* d_tr = nullptr;
+  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * (S.nphases + 1)) != cudaSuccess) return;
+  cudaStreamSynchronize(st);
+  run_schedule(S, d_err, st, d_tr);
+  cudaStreamSynchronize(st);
+  std::vector<unsigned long long> tr(S.nphases + 1);
+  cudaMemcpy(tr.data(), d_tr, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost);
+  cudaFree(d_tr);
+  const char* names[7] = {"gemm", "lu", "trunc", "copy", "reduce", "rows", "vpart"};
+  double by[7] = {0, 0, 0, 0, 0, 0, 0};
+  int cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+  std::vector<std::pair<double, int>> slow;
+  for (int p = 0; p < S.nphases; ++p) {
+    double dt = (double)(tr[p + 1] - tr[p]) * 1e-3;  // us
+    const Wave& W = waves[p];
+    size_t n[7] = {W.gemm.size(), W.lu.size(), W.trunc.size(), W.copy.size(), W.reduce.size(), W.rows.size(),
+                   W.vpart.size()};
+    int dom = 0;
+    // attribute a phase to its most expensive-looking kind: trunc > lu > gemm > rows > others
+    const int pri[7] = {2, 1, 0, 5, 6, 4, 3};
+    for (int k : pri)
+      if (n[k]) { dom = k; break; }
+    by[dom] += dt;
+    cnt[dom]++;
+    slow.push_back({dt, p});
+  }
+  std::sort(slow.rbegin(), slow.rend());
+  double tot = (double)(tr[S.nphases] - tr[0]) * 1e-3;
+  fprintf(stderr, "[trace] %s: %d phases, %.1f us total, %.2f us/phase\n", what, S.nphases, tot,
+          tot / std::max(1, S.nphases));
+  for (int k = 0; k < 7; ++k)
+    if (cnt[k]) fprintf(stderr, "[trace]   phases led by %-6s: %6d  %10.1f us  (%.2f us each)\n", names[k], cnt[k], by[k], by[k] / cnt[k]);
+  for (int i = 0; i < std::min<int>(8, (int)slow.size()); ++i) {
+    const Wave& W = waves[slow[i].second];
+    fprintf(stderr, "[trace]   slow phase %d: %.1f us gemm=%zu lu=%zu trunc=%zu copy=%zu reduce=%zu rows=%zu vpart=%zu\n",
+            slow[i].second, slow[i].first, W.gemm.size(), W.lu.size(), W.trunc.size(), W.copy.size(),
+            W.reduce.size(), W.rows.size(), W.vpart.size());
+  }
+}
+
 // z = (LU)^{-1} b on Morton-order vectors (b may equal z)
 int solve_morton(const hm_factors* F, const double* b, double* z, cudaStream_t st) {
   const int N = F->H->plan.N;
+  count_launches(2);
   copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, b, F->d_y);
   HM_TRY(run_schedule(F->solve, F->H->d_err, st));
-  copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, F->d_y, z);
+  copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, F->d_sv + (size_t)N, z);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
@@ -79,8 +127,12 @@ int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u
   for (int it = 0; it < sweeps; ++it) {
     // s = rhs - (z - theta G z)
     HM_TRY(hm_matvec_morton(H, -1.0, th, u1, 0.0, nullptr, nullptr, rhs, s, st));
-    if (it == sweeps - 1) norms_kernel<<<1, 1024, 0, st>>>(N, s, rhs, F->d_norm);
+    if (it == sweeps - 1) {
+      count_launches(1);
+      norms_kernel<<<1, 1024, 0, st>>>(N, s, rhs, F->d_norm);
+    }
     HM_TRY(solve_morton(F, s, s, st));
+    count_launches(1);
     axpy_kernel<<<vgrid(N), 256, 0, st>>>(N, 1.0, s, u1);
   }
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
@@ -125,6 +177,7 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   };
   if ((s = alloc((void**)&F->d_rank, sizeof(int) * std::max(nlr, 1))) != HM_OK) return fail(s);
   if ((s = alloc((void**)&F->d_y, sizeof(double) * N)) != HM_OK) return fail(s);
+  if ((s = alloc((void**)&F->d_sv, sizeof(double) * 4 * (size_t)N)) != HM_OK) return fail(s);
   if ((s = alloc((void**)&F->d_vec, sizeof(double) * 6 * (size_t)N)) != HM_OK) return fail(s);
   if ((s = alloc((void**)&F->d_norm, sizeof(double) * 4)) != HM_OK) return fail(s);
   if (nlr && cudaMemcpyAsync(F->d_rank, H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -142,7 +195,12 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   DevSchedule fs;
   std::vector<void*> fs_allocs;
   s = upload_schedule(hb.waves, fs, fs_allocs);
-  if (s == HM_OK) s = run_schedule(fs, H->d_err, st);
+  const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
+  if (s == HM_OK && tracing) {
+    trace_schedule("factor", hb.waves, fs, H->d_err, st);  // note: runs the factorisation
+  } else if (s == HM_OK) {
+    s = run_schedule(fs, H->d_err, st);
+  }
   cudaEventRecord(e1, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
   float ms = 0.f;
@@ -168,10 +226,16 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
 
   // the solve schedule, replayed by every hm_solve
   std::vector<Wave> sw;
-  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, F->d_y, F->arena, sw);
+  std::vector<RowSrc> srcs;
+  SolveVectors sv{F->d_y, F->d_sv, F->d_sv + (size_t)N, F->d_sv + 2 * (size_t)N, F->d_sv + 3 * (size_t)N};
+  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, sv, F->arena, sw, srcs);
   if (s != HM_OK) { set_error("solve planning failed"); return fail(s); }
-  s = upload_schedule(sw, F->solve, F->allocs);
+  s = upload_schedule(sw, F->solve, F->allocs, &srcs);
   if (s != HM_OK) { set_error("solve schedule upload failed"); return fail(s); }
+  if (tracing) {
+    trace_schedule("solve", sw, F->solve, H->d_err, st);
+    trace_schedule("solve", sw, F->solve, H->d_err, st);
+  }
   F->solve_waves = (int)sw.size();
   // bytes the two sweeps read: leaf inverses, off-diagonal dense blocks, low-rank factors
   int64_t b = 0;
@@ -247,7 +311,10 @@ int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int 
   double* f1 = Fm->d_vec + 4 * (size_t)N;
   const bool perm = H->plan.dim == 2;
   if (perm) HM_TRY(launch_gather(H->d_perm, N, u, ua, st));
-  else copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, u, ua);
+  else {
+    count_launches(1);
+    copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, u, ua);
+  }
   for (int k = 0; k < steps; ++k) {
     const double* fa = nullptr;
     const double* fb = nullptr;
@@ -268,6 +335,7 @@ int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int 
     std::swap(ua, ub);
   }
   if (perm) return launch_scatter(H->d_perm, N, ua, u, st);
+  count_launches(1);
   copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, ua, u);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
@@ -293,17 +361,21 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   double* fU = A.alloc(std::max<int64_t>(up, 1));
   double* fV = A.alloc(std::max<int64_t>(vp, 1));
   int* frank = (int*)A.alloc((int64_t)ld.size() / 2 + 1);
-  double* fy = A.alloc(P.N);
+  double* fy = A.alloc(5 * (int64_t)P.N);
   HluBuild hb;
   int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb);
   if (s != HM_OK) { set_error("planning failed: " + hb.err); return s; }
   std::vector<Wave> sw;
-  s = plan_solve(P, dd, ld, hb.F, fy, A, sw);
+  std::vector<RowSrc> srcs;
+  SolveVectors sv{fy, fy + P.N, fy + 2 * (int64_t)P.N, fy + 3 * (int64_t)P.N, fy + 4 * (int64_t)P.N};
+  s = plan_solve(P, dd, ld, hb.F, sv, A, sw, srcs);
   if (s != HM_OK) { set_error("solve planning failed"); return s; }
   std::string first;
-  int64_t bad = check_spans(hb.waves, A.ranges, first) + check_spans(sw, A.ranges, first);
+  int64_t bad = check_spans(hb.waves, A.ranges, first) + check_spans(sw, A.ranges, first, &srcs);
   int64_t sops = 0;
-  for (auto& w : sw) sops += w.gemm.size() + w.copy.size() + w.lu.size() + w.trunc.size() + w.reduce.size();
+  for (auto& w : sw)
+    sops += w.gemm.size() + w.copy.size() + w.lu.size() + w.trunc.size() + w.reduce.size() + w.rows.size() +
+            w.vpart.size();
   out->fact_ops = hb.ops;
   out->fact_waves = (int)hb.waves.size();
   out->solve_ops = sops;

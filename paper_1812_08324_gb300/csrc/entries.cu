@@ -153,6 +153,7 @@ __global__ void to_dense_lr_kernel(const LRDesc* ld, const int* rank, const doub
 int launch_constants(const NuParams& q, double* d_tab, double* d_scratch, cudaStream_t st) {
   int64_t total = (int64_t)q.n0 * q.n1;
   int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  count_launches(q.dim == 2 ? 3 : 2);
   nu_table_kernel<<<grid, 256, 0, st>>>(q, q.n0, q.n1, d_tab);
   window_sums_kernel<<<1, 1024, 0, st>>>(q, d_scratch);
   if (q.dim == 2) tail2d_kernel<<<1, 1024, 0, st>>>(q, d_scratch + 2);
@@ -163,6 +164,7 @@ int launch_near_fill(const EntryCtx& E, const DenseDesc* d_dd, int ndense, doubl
                      cudaStream_t st) {
   if (ndense == 0) return HM_OK;
   dim3 grid(ndense, 8);
+  count_launches(1);
   near_fill_kernel<<<grid, 256, 0, st>>>(E, d_dd, pool);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
@@ -239,6 +241,7 @@ __global__ void finalize_constants_kernel(NuParams q, double a, double b0, doubl
 
 int launch_finalize_constants(const NuParams& q, double a, const double* b, double c,
                               const double* d_scratch, GenConst* d_gc, cudaStream_t st) {
+  count_launches(1);
   finalize_constants_kernel<<<1, 32, 0, st>>>(q, a, b[0], q.dim == 2 ? b[1] : 0.0, c, d_scratch, d_gc);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }

@@ -5,6 +5,7 @@
 #include "hm_device.cuh"
 #include "hlu_ops.h"
 #include "hm_internal.h"
+#include "hm_kernels.h"
 
 namespace hm {
 
@@ -13,19 +14,10 @@ namespace {
 constexpr int GT = 32;   // GEMM output tile
 constexpr int GK = 16;   // GEMM k chunk
 
-__global__ void __launch_bounds__(256)
-gemm_batch_kernel(const GemmOp* ops, const int* prefix, int nops) {
-  __shared__ double As[GT][GK + 1];
-  __shared__ double Bs[GK][GT + 1];
-  const int tile = blockIdx.x;
-  // locate the op owning this tile: prefix[o] <= tile < prefix[o + 1]
-  int lo = 0, hi = nops - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
-  }
-  const GemmOp op = ops[lo];
-  const int local = tile - prefix[lo];
+// One 32 x 32 output tile of C = beta C + alpha A B (256 threads).
+__device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem) {
+  double (*As)[GK + 1] = reinterpret_cast<double (*)[GK + 1]>(smem);
+  double (*Bs)[GT + 1] = reinterpret_cast<double (*)[GT + 1]>(smem + GT * (GK + 1));
   const int tn = (op.n + GT - 1) / GT;
   const int i0 = (local / tn) * GT, j0 = (local % tn) * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
@@ -64,14 +56,14 @@ gemm_batch_kernel(const GemmOp* ops, const int* prefix, int nops) {
         *c = op.beta == 0.0 ? v : op.beta * (*c) + v;
       }
     }
+  __syncthreads();
 }
 
 // Base LU (m <= LU_BASE) in shared memory, then the inverses of L (unit
 // lower) and U by substitution against the identity.
-__global__ void lu_base_kernel(const LuOp* ops, int* err) {
-  __shared__ double A[LU_BASE][LU_BASE + 1];
-  __shared__ double X[LU_BASE][LU_BASE + 1];
-  const LuOp op = ops[blockIdx.x];
+__device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
+  double (*A)[LU_BASE + 1] = reinterpret_cast<double (*)[LU_BASE + 1]>(smem);
+  double (*X)[LU_BASE + 1] = reinterpret_cast<double (*)[LU_BASE + 1]>(smem + LU_BASE * (LU_BASE + 1));
   const int m = op.m, t = threadIdx.x;
   for (int e = t; e < m * m; e += blockDim.x) A[e / m][e % m] = op.A[(e / m) * op.lda + e % m];
   __syncthreads();
@@ -115,6 +107,7 @@ __global__ void lu_base_kernel(const LuOp* ops, int* err) {
   }
   __syncthreads();
   for (int e = t; e < m * m; e += blockDim.x) op.Ui[(e / m) * op.ldu + e % m] = X[e / m][e % m];
+  __syncthreads();
 }
 
 // ---- truncation core (one CTA): pivoted Cholesky of both Gram matrices,
@@ -125,6 +118,33 @@ struct TruncSmem {
   double* GB;   // K x K
   double* C;    // K x K
 };
+
+// Warp 0: largest v[j * stride] over p <= j < K (ties -> smallest j) and the
+// sum of those entries; results in red_v[0] (max), red_v[1] (sum), red_i[0].
+__device__ __forceinline__ void warp0_max_sum(const double* v, int stride, int p, int K, double* red_v,
+                                              int* red_i) {
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  double best = -1.0, sum = 0.0;
+  int q = -1;
+  for (int j = p + lane; j < K; j += 32) {
+    double x = v[j * stride];
+    sum += x;
+    if (q < 0 || x > best) { best = x; q = j; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oq = __shfl_xor_sync(0xffffffffu, q, o);
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (oq >= 0 && (q < 0 || ob > best || (ob == best && oq < q))) { best = ob; q = oq; }
+  }
+  if (lane == 0) {
+    red_v[0] = best;
+    red_v[1] = sum;
+    red_i[0] = q < 0 ? p : q;
+  }
+}
 
 // In-place pivoted Cholesky of the symmetric K x K matrix G (row-major);
 // perm[c] = original index of pivot c; returns the rank (pivots above thresh).
@@ -139,14 +159,7 @@ __device__ int pivoted_cholesky(double* G, int K, int* perm, double rel_thresh, 
   int rank = 0;
   for (int p = 0; p < K; ++p) {
     __syncthreads();
-    if (t == 0) {
-      int q = p;
-      double best = G[p * K + p];
-      for (int j = p + 1; j < K; ++j)
-        if (G[j * K + j] > best) { best = G[j * K + j]; q = j; }
-      red_v[0] = best;
-      red_i[0] = q;
-    }
+    warp0_max_sum(G, K + 1, p, K, red_v, red_i);
     __syncthreads();
     const double best = red_v[0];
     const int q = red_i[0];
@@ -186,14 +199,17 @@ __device__ int pivoted_cholesky(double* G, int K, int* perm, double rel_thresh, 
   return rank;
 }
 
-__global__ void trunc_core_kernel(const TruncOp* ops, int* err) {
-  extern __shared__ double sm[];
-  __shared__ int permA[TRUNC_MAXK], permB[TRUNC_MAXK], permC[TRUNC_MAXK];
-  __shared__ int posA[TRUNC_MAXK], posB[TRUNC_MAXK];
-  __shared__ double cn[TRUNC_MAXK], tau[TRUNC_MAXK];
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  const TruncOp op = ops[blockIdx.x];
+__device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
+  // scratch after the three K x K matrices
+  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
+  double* tau = cn + TRUNC_MAXK;
+  double* red_v = tau + TRUNC_MAXK;
+  int* permA = reinterpret_cast<int*>(red_v + 32);
+  int* permB = permA + TRUNC_MAXK;
+  int* permC = permB + TRUNC_MAXK;
+  int* posA = permC + TRUNC_MAXK;
+  int* posB = posA + TRUNC_MAXK;
+  int* red_i = posB + TRUNC_MAXK;
   const int K = op.K, kf = op.kf, t = threadIdx.x;
   double* GA = sm;
   double* GB = sm + K * K;
@@ -238,19 +254,9 @@ __global__ void trunc_core_kernel(const TruncOp* ops, int* err) {
   bool capped = false;
   for (int p = 0; p < min(rA, rB); ++p) {
     __syncthreads();
-    if (t == 0) {
-      double rem = 0.0;
-      int q = p;
-      double best = -1.0;
-      for (int j = p; j < rB; ++j) {
-        rem += cn[j];
-        if (cn[j] > best) { best = cn[j]; q = j; }
-      }
-      red_v[0] = rem;
-      red_i[0] = q;
-    }
+    warp0_max_sum(cn, 1, p, rB, red_v, red_i);
     __syncthreads();
-    const double rem = red_v[0];
+    const double rem = red_v[1];
     if (!(rem > op.tol * op.tol * total) || total <= 0.0) break;
     if (p == rmax) { capped = true; break; }
     const int q = red_i[0];
@@ -267,9 +273,15 @@ __global__ void trunc_core_kernel(const TruncOp* ops, int* err) {
     }
     __syncthreads();
     // Householder vector for column p, rows p..rA-1 (stored below the diagonal)
-    if (t == 0) {
+    if ((t >> 5) == 0) {
       double s = 0.0;
-      for (int i = p; i < rA; ++i) s += C[i * K + p] * C[i * K + p];
+      for (int i = p + (t & 31); i < rA; i += 32) s += C[i * K + p] * C[i * K + p];
+      s = warp_sum(s);
+      if (t == 0) red_v[3] = s;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double s = red_v[3];
       double nrm = sqrt(s);
       double x0 = C[p * K + p];
       double alpha = x0 >= 0.0 ? -nrm : nrm;
@@ -379,13 +391,12 @@ __global__ void trunc_core_kernel(const TruncOp* ops, int* err) {
     *op.rank = r;
     if (capped) atomicOr(err, DEVERR_RANKCAP);
   }
+  __syncthreads();
 }
 
-__global__ void copy_batch_kernel(const CopyOp* ops) {
-  const CopyOp op = ops[blockIdx.y];
+__device__ void dev_copy(const CopyOp& op, int chunk, int nchunks) {
   const int64_t tot = (int64_t)op.m * op.n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = chunk * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)nchunks * blockDim.x) {
     int i = (int)(e / op.n), j = (int)(e % op.n);
     double v = op.src ? op.alpha * op.src[i * op.srs + j * op.scs] : op.alpha;
     double* d = op.dst + i * op.drs + j * op.dcs;
@@ -393,55 +404,179 @@ __global__ void copy_batch_kernel(const CopyOp* ops) {
   }
 }
 
-__global__ void reduce_batch_kernel(const ReduceOp* ops) {
-  const ReduceOp op = ops[blockIdx.y];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < op.count;
-       i += (int64_t)gridDim.x * blockDim.x) {
+__device__ void dev_reduce(const ReduceOp& op, int chunk, int nchunks) {
+  const int64_t count = (int64_t)op.m * op.n;
+  for (int64_t e = chunk * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)nchunks * blockDim.x) {
     double s = 0.0;
-    for (int p = 0; p < op.nparts; ++p) s += op.parts[p * op.stride + i];
-    op.dst[i] = s;
+    for (int p = 0; p < op.nparts; ++p) s += op.parts[p * op.stride + e];
+    const int i = (int)(e / op.n), j = (int)(e % op.n);
+    double* d = op.dst + i * op.drs + j * op.dcs;
+    *d = op.beta == 0.0 ? op.alpha * s : op.beta * (*d) + op.alpha * s;
   }
+}
+
+
+// Row task: 8 warps.  Dense sources: warp per row (rows w, w+8, ...), lanes
+// over columns.  Low-rank sources: warp per source (round robin), lane per
+// row, after summing the source's partial products.  Per-row totals are
+// combined in a fixed order, so results are bitwise reproducible.
+__device__ void dev_rows(const RowsOp& op, const RowSrc* srcs, double* smem) {
+  double* acc_d = smem;               // 32
+  double* acc_l = smem + 32;          // 8 x 32
+  double* wsum = smem + 32 + 256;     // 8 x 64 (per-warp low-rank coefficient vector)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nr = op.nr;
+  for (int r = warp; r < 32; r += 8) {
+    double acc = 0.0;
+    if (r < nr) {
+      for (int s = op.src_begin; s < op.src_end; ++s) {
+        const RowSrc S = srcs[s];
+        if (S.nparts) continue;
+        const double* Mr = S.M + r * S.rs;
+        double a = 0.0;
+        for (int c = lane; c < S.ncols; c += 32) a += Mr[c * S.cs] * S.x[c];
+        acc += S.sign * a;
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) acc_d[r] = acc;
+  }
+  double la = 0.0;
+  int k = 0;
+  for (int s = op.src_begin; s < op.src_end; ++s) {
+    const RowSrc S = srcs[s];
+    if (!S.nparts) continue;
+    if ((k++ & 7) != warp) continue;
+    double* w = wsum + warp * 64;
+    for (int l = lane; l < S.ncols; l += 32) {
+      // eight independent chains keep eight loads in flight
+      double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int p = 0;
+      for (; p + 8 <= S.nparts; p += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] += S.x[(p + u) * S.ncols + l];
+      for (; p < S.nparts; ++p) v[0] += S.x[p * S.ncols + l];
+      w[l] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    }
+    __syncwarp();
+    if (lane < nr) {
+      const double* Mr = S.M + lane * S.rs;
+      double a = 0.0;
+      for (int l = 0; l < S.ncols; ++l) a += Mr[l * S.cs] * w[l];
+      la += S.sign * a;
+    }
+    __syncwarp();
+  }
+  acc_l[warp * 32 + lane] = la;
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    const int r = threadIdx.x;
+    double v = op.base ? op.base[op.r0 + r] : 0.0;
+    v += acc_d[r];
+    for (int w = 0; w < 8; ++w) v += acc_l[w * 32 + r];
+    op.out[op.r0 + r] = v;
+  }
+  __syncthreads();
+}
+
+__device__ void dev_vpart(const VPartOp& op) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = warp; l < op.kf; l += 8) {
+    const double* Vl = op.V + l * op.ldv;
+    double a = 0.0;
+    for (int r = lane; r < op.len; r += 32) a += Vl[r] * op.y[r];
+    a = warp_sum(a);
+    if (lane == 0) op.part[l] = a;
+  }
+}
+
+constexpr int EXEC_THREADS = 256;
+constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
+                             sizeof(int) * 6 * TRUNC_MAXK;
+constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s per phase boundary
+
+struct ExecArgs {
+  const GemmOp* gemm;
+  const LuOp* lu;
+  const TruncOp* trunc;
+  const CopyOp* copy;
+  const ReduceOp* reduce;
+  const RowsOp* rows;
+  const VPartOp* vpart;
+  const RowSrc* srcs;
+  const Task* tasks;
+  const int* phase_begin;
+  int nphases;
+  unsigned* bar;
+  int* err;
+  unsigned long long* trace;  // optional: start time of every phase (ns)
+};
+
+__global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
+  extern __shared__ double smem[];
+  for (int ph = 0; ph < a.nphases; ++ph) {
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[ph] = global_ns();
+    const int b = a.phase_begin[ph], e = a.phase_begin[ph + 1];
+    for (int t = b + (int)blockIdx.x; t < e; t += (int)gridDim.x) {
+      const Task T = a.tasks[t];
+      switch (T.kind) {
+        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
+        case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
+        case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
+        case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
+        case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
+        case TK_ROWS: dev_rows(a.rows[T.op], a.srcs, smem); break;
+        case TK_VPART: dev_vpart(a.vpart[T.op]); break;
+        default: break;
+      }
+      __syncthreads();
+    }
+    if (ph + 1 < a.nphases && !grid_barrier(a.bar, gridDim.x, a.err, BARRIER_LIMIT_NS)) return;
+  }
+  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[a.nphases] = global_ns();
 }
 
 }  // namespace
 
 int gemm_tiles(int m, int n) { return ((m + GT - 1) / GT) * ((n + GT - 1) / GT); }
 
-int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs) {
+int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs,
+                    const std::vector<RowSrc>* srcs) {
+  std::vector<RowsOp> ro;
+  std::vector<VPartOp> vp;
   std::vector<GemmOp> g;
   std::vector<LuOp> l;
   std::vector<TruncOp> tr;
   std::vector<CopyOp> c;
   std::vector<ReduceOp> r;
-  std::vector<int> prefix;
-  S.nwaves = (int)waves.size();
-  S.begin.assign(5 * S.nwaves, 0);
-  S.end.assign(5 * S.nwaves, 0);
-  S.h_gemm_tiles_total.assign(S.nwaves, 0);
-  for (int w = 0; w < S.nwaves; ++w) {
-    const Wave& W = waves[w];
-    S.begin[5 * w + 0] = (int)g.size();
-    int tiles = 0;
+  std::vector<Task> tasks;
+  std::vector<int> pb;
+  auto chunks = [](int64_t elems) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, elems / 4096)); };
+  for (const Wave& W : waves) {
+    pb.push_back((int)tasks.size());
     for (const GemmOp& o : W.gemm) {
-      prefix.push_back(tiles);
-      tiles += gemm_tiles(o.m, o.n);
+      int nt = gemm_tiles(o.m, o.n);
+      for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt});
       g.push_back(o);
     }
-    S.end[5 * w + 0] = (int)g.size();
-    S.h_gemm_tiles_total[w] = tiles;
-    S.begin[5 * w + 1] = (int)l.size();
-    l.insert(l.end(), W.lu.begin(), W.lu.end());
-    S.end[5 * w + 1] = (int)l.size();
-    S.begin[5 * w + 2] = (int)tr.size();
-    tr.insert(tr.end(), W.trunc.begin(), W.trunc.end());
-    S.end[5 * w + 2] = (int)tr.size();
-    S.begin[5 * w + 3] = (int)c.size();
-    c.insert(c.end(), W.copy.begin(), W.copy.end());
-    S.end[5 * w + 3] = (int)c.size();
-    S.begin[5 * w + 4] = (int)r.size();
-    r.insert(r.end(), W.reduce.begin(), W.reduce.end());
-    S.end[5 * w + 4] = (int)r.size();
+    for (const LuOp& o : W.lu) { tasks.push_back({TK_LU, (int)l.size(), 0, 1}); l.push_back(o); }
+    for (const TruncOp& o : W.trunc) { tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1}); tr.push_back(o); }
+    for (const CopyOp& o : W.copy) {
+      int nc = chunks((int64_t)o.m * o.n);
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc});
+      c.push_back(o);
+    }
+    for (const ReduceOp& o : W.reduce) {
+      int nc = chunks((int64_t)o.m * o.n);
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc});
+      r.push_back(o);
+    }
+    for (const RowsOp& o : W.rows) { tasks.push_back({TK_ROWS, (int)ro.size(), 0, 1}); ro.push_back(o); }
+    for (const VPartOp& o : W.vpart) { tasks.push_back({TK_VPART, (int)vp.size(), 0, 1}); vp.push_back(o); }
   }
+  pb.push_back((int)tasks.size());
+  S.nphases = (int)waves.size();
+  S.ntasks = (int64_t)tasks.size();
   auto up = [&](auto& vec, auto** dst) -> int {
     size_t bytes = std::max<size_t>(vec.size() * sizeof(vec[0]), 16);
     void* p = nullptr;
@@ -458,33 +593,38 @@ int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<
   if ((s = up(tr, &S.trunc)) != HM_OK) return s;
   if ((s = up(c, &S.copy)) != HM_OK) return s;
   if ((s = up(r, &S.reduce)) != HM_OK) return s;
-  if ((s = up(prefix, &S.gemm_tile_prefix)) != HM_OK) return s;
+  if ((s = up(ro, &S.rows)) != HM_OK) return s;
+  if ((s = up(vp, &S.vpart)) != HM_OK) return s;
+  std::vector<RowSrc> nos;
+  if ((s = up(srcs ? *srcs : nos, &S.srcs)) != HM_OK) return s;
+  if ((s = up(tasks, &S.tasks)) != HM_OK) return s;
+  if ((s = up(pb, &S.phase_begin)) != HM_OK) return s;
+  std::vector<unsigned> bar(2, 0u);
+  if ((s = up(bar, &S.barrier)) != HM_OK) return s;
   return HM_OK;
 }
 
-int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st) {
-  static bool attr_set = false;
-  const size_t trunc_smem = 3 * sizeof(double) * TRUNC_MAXK * TRUNC_MAXK;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(trunc_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)trunc_smem) != cudaSuccess)
+int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned long long* trace) {
+  if (S.nphases == 0) return HM_OK;
+  static int grid = 0;
+  if (grid == 0) {
+    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EXEC_SMEM) != cudaSuccess)
       return HM_ERR_CUDA;
-    attr_set = true;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, exec_kernel, EXEC_THREADS, EXEC_SMEM) != cudaSuccess || per < 1)
+      return HM_ERR_CUDA;
+    grid = sms * per;
   }
-  for (int w = 0; w < S.nwaves; ++w) {
-    int b, e;
-    b = S.begin[5 * w + 0]; e = S.end[5 * w + 0];
-    if (e > b) gemm_batch_kernel<<<S.h_gemm_tiles_total[w], 256, 0, st>>>(S.gemm + b, S.gemm_tile_prefix + b, e - b);
-    b = S.begin[5 * w + 1]; e = S.end[5 * w + 1];
-    if (e > b) lu_base_kernel<<<e - b, 256, 0, st>>>(S.lu + b, d_err);
-    b = S.begin[5 * w + 2]; e = S.end[5 * w + 2];
-    if (e > b) trunc_core_kernel<<<e - b, 256, trunc_smem, st>>>(S.trunc + b, d_err);
-    b = S.begin[5 * w + 3]; e = S.end[5 * w + 3];
-    if (e > b) copy_batch_kernel<<<dim3(32, e - b), 256, 0, st>>>(S.copy + b);
-    b = S.begin[5 * w + 4]; e = S.end[5 * w + 4];
-    if (e > b) reduce_batch_kernel<<<dim3(16, e - b), 256, 0, st>>>(S.reduce + b);
-  }
-  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+  if (cudaMemsetAsync(S.barrier, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return HM_ERR_CUDA;
+  ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.phase_begin,
+             S.nphases, S.barrier, d_err, trace};
+  void* args[] = {&a};
+  count_launches(1);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)exec_kernel, dim3(grid), dim3(EXEC_THREADS), args,
+                                              EXEC_SMEM, st);
+  return e == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
 }  // namespace hm

@@ -58,13 +58,46 @@ struct CopyOp {
   double alpha, beta;
 };
 
-// dst[i] = sum_{p < nparts} parts[p * stride + i], i < count.
+// dst(i, j) = beta dst(i, j) + alpha sum_{p < nparts} parts[p * stride + i * n + j]
+// for i < m, j < n (dst strided; beta == 0 does not read dst).
 struct ReduceOp {
   const double* parts;
   double* dst;
-  int64_t stride, count;
+  int64_t stride, drs, dcs;
+  int m, n;
   int nparts;
   int pad;
+  double alpha, beta;
+};
+
+// One source of a row task: dense row-major block (x = a vector segment of
+// ncols entries) or low-rank factor rows (column-major, x = the sum of nparts
+// partial products of kf entries each, laid out back to back).
+struct RowSrc {
+  const double* M;   // element (r, c) of the task's rows: M[r * rs + c * cs], r relative to the task
+  int64_t rs, cs;
+  const double* x;
+  int ncols;
+  int nparts;        // 0: dense source; > 0: low-rank source
+  double sign;
+};
+
+// out[r] = base[r] + sum over sources, rows r0 .. r0 + nr - 1 (nr <= 32);
+// base == nullptr means 0.
+struct RowsOp {
+  double* out;
+  const double* base;
+  int r0, nr;
+  int src_begin, src_end;
+};
+
+// part[l] = sum_{r < len} V[r + l * ldv] y[r], l < kf.
+struct VPartOp {
+  const double* V;
+  const double* y;
+  double* part;
+  int64_t ldv;
+  int len, kf;
 };
 
 constexpr int LU_BASE = 32;    // leaf LU base-case size (one CTA)
@@ -76,25 +109,43 @@ struct Wave {
   std::vector<TruncOp> trunc;
   std::vector<CopyOp> copy;
   std::vector<ReduceOp> reduce;
+  std::vector<RowsOp> rows;
+  std::vector<VPartOp> vpart;
 };
 
-// Device-resident copy of a schedule, executed wave by wave.
+// A unit of work for one CTA of the persistent executor: kind, index of the
+// operation in its per-kind array, and the part (tile / chunk) of it.
+enum TaskKind { TK_GEMM = 0, TK_LU = 1, TK_TRUNC = 2, TK_COPY = 3, TK_REDUCE = 4, TK_ROWS = 5, TK_VPART = 6 };
+struct Task {
+  int kind, op, sub, nsub;
+};
+
+// Device-resident schedule: tasks grouped into phases; phase p holds tasks
+// [phase_begin[p], phase_begin[p+1]).  All tasks of a phase are independent.
 struct DevSchedule {
-  int nwaves = 0;
-  // per wave: [begin, end) into the flat per-kind arrays, 5 kinds
-  std::vector<int> begin, end;  // size 5 * nwaves each
-  std::vector<int> tile_begin;  // per wave: first tile of its GEMMs in the flat tile prefix
+  int nphases = 0;
+  int64_t ntasks = 0;
   GemmOp* gemm = nullptr;
   LuOp* lu = nullptr;
   TruncOp* trunc = nullptr;
   CopyOp* copy = nullptr;
   ReduceOp* reduce = nullptr;
-  int* gemm_tile_prefix = nullptr;  // per GEMM op: first tile (global prefix)
-  std::vector<int> h_gemm_tiles_total;  // per wave: tiles
+  RowsOp* rows = nullptr;
+  VPartOp* vpart = nullptr;
+  RowSrc* srcs = nullptr;
+  Task* tasks = nullptr;
+  int* phase_begin = nullptr;
+  unsigned* barrier = nullptr;  // 2 words: arrival count, generation
 };
 
-int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs);
-int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st);
+int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs,
+                    const std::vector<RowSrc>* srcs = nullptr);
+
+// Run all phases in one persistent cooperative launch (one CTA per SM); a
+// phase boundary is a grid barrier whose waits are bounded in time (on expiry
+// the kernel sets DEVERR_TIMEOUT in *d_err and returns).
+int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st,
+                 unsigned long long* trace = nullptr);
 
 int gemm_tiles(int m, int n);
 

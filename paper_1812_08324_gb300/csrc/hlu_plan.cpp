@@ -211,7 +211,26 @@ class Emitter {
     return w;
   }
 
-  // C = beta C + alpha A B
+  // C = beta C + alpha sum_p parts[p]  (parts: nparts blocks of C.rows x C.cols, row-major)
+  void reduce(const View& C, double alpha, const View& parts, int nparts, double beta) {
+    int w = beta != 0.0 ? place({{&parts, false}, {&C, false}, {&C, true}}) : place({{&parts, false}, {&C, true}});
+    ReduceOp o{};
+    o.parts = parts.p;
+    o.dst = C.p;
+    o.stride = (int64_t)C.rows * C.cols;
+    o.drs = C.rs;
+    o.dcs = C.cs;
+    o.m = C.rows;
+    o.n = C.cols;
+    o.nparts = nparts;
+    o.alpha = alpha;
+    o.beta = beta;
+    waves[w].reduce.push_back(o);
+  }
+
+  // C = beta C + alpha A B; a long inner dimension with few output tiles is
+  // split into 256-wide slices reduced afterwards (FP64 throughput per SM is
+  // low, so the work must reach many SMs).
   void gemm(const View& C, double alpha, const View& Am, const View& Bm, double beta) {
     if (C.rows == 0 || C.cols == 0) return;
     if (Am.cols != Bm.rows || Am.rows != C.rows || Bm.cols != C.cols) { status = HM_ERR_ARG; return; }
@@ -219,6 +238,25 @@ class Emitter {
       if (beta != 1.0) copy(C, 0.0, nullptr, beta);
       return;
     }
+    const int K = Am.cols;
+    const int tiles = gemm_tiles(C.rows, C.cols);
+    if (K > 512 && tiles < 64) {
+      const int KS = 256;
+      const int ns = (K + KS - 1) / KS;
+      View parts = tmp(ns * C.rows, C.cols, false);
+      for (int c = 0; c < ns; ++c) {
+        int k0 = c * KS, kn = std::min(KS, K - k0);
+        gemm_direct(parts.sub(c * C.rows, 0, C.rows, C.cols), 1.0, Am.sub(0, k0, Am.rows, kn),
+                    Bm.sub(k0, 0, kn, Bm.cols), 0.0);
+      }
+      reduce(C, alpha, parts, ns, beta);
+      release(parts);
+      return;
+    }
+    gemm_direct(C, alpha, Am, Bm, beta);
+  }
+
+  void gemm_direct(const View& C, double alpha, const View& Am, const View& Bm, double beta) {
     int w = beta != 0.0 ? place({{&Am, false}, {&Bm, false}, {&C, false}, {&C, true}})
                         : place({{&Am, false}, {&Bm, false}, {&C, true}});
     GemmOp o{};
@@ -282,23 +320,16 @@ class Emitter {
     const int CH = 256;
     int nch = (X.rows + CH - 1) / CH;
     if (nch <= 1) {
-      gemm(G, 1.0, X.T(), X, 0.0);
+      gemm_direct(G, 1.0, X.T(), X, 0.0);
       return G;
     }
     View parts = tmp(nch * K, K, false);
     for (int c = 0; c < nch; ++c) {
       int r0 = c * CH, nr = std::min(CH, X.rows - r0);
       View Xc = X.sub(r0, 0, nr, K);
-      gemm(parts.sub(c * K, 0, K, K), 1.0, Xc.T(), Xc, 0.0);
+      gemm_direct(parts.sub(c * K, 0, K, K), 1.0, Xc.T(), Xc, 0.0);
     }
-    int w = place({{&parts, false}, {&G, true}});
-    ReduceOp o{};
-    o.parts = parts.p;
-    o.dst = G.p;
-    o.stride = (int64_t)K * K;
-    o.count = (int64_t)K * K;
-    o.nparts = nch;
-    waves[w].reduce.push_back(o);
+    reduce(G, 1.0, parts, nch, 0.0);
     release(parts);
     return G;
   }
@@ -705,6 +736,39 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     }
   }
   H.hlu(0);
+  // leaf-inverse scaling of the off-diagonal factor blocks for the solves
+  FactorLayout& FL = out.F;
+  std::vector<int> diag_of_cluster(P.cl.size(), -1);
+  for (int d = 0; d < nd; ++d)
+    if (dd[d].r0 == dd[d].c0) diag_of_cluster[P.bl[P.dense_block[d]].t] = d;
+  FL.leaf_diag.resize(P.leaves.size());
+  for (size_t i = 0; i < P.leaves.size(); ++i) FL.leaf_diag[i] = diag_of_cluster[P.leaves[i]];
+  FL.pdense.assign(nd, nullptr);
+  for (int d = 0; d < nd; ++d) {
+    if (dd[d].r0 == dd[d].c0) continue;
+    const int dt = diag_of_cluster[P.bl[P.dense_block[d]].t];
+    const View& inv = dd[d].r0 > dd[d].c0 ? H.linv[dt] : H.uinv[dt];
+    View o = E.new_mat(dd[d].m, dd[d].n, false);
+    E.gemm(o, 1.0, inv, H.dense[d], 0.0);
+    FL.pdense[d] = o.p;
+  }
+  FL.plr.assign(nl, nullptr);
+  for (int q = 0; q < nl; ++q) {
+    const LRDesc& L = ld[q];
+    const bool lower = L.r0 > L.c0;
+    View U = H.lrU(q);
+    View o = E.new_mat(L.m, kf, true);
+    const Cluster& T = P.cl[P.bl[P.lr_block[q]].t];
+    for (int leaf : P.leaves) {
+      const Cluster& c = P.cl[leaf];
+      if (c.begin < T.begin || c.end > T.end) continue;
+      const int dt = diag_of_cluster[leaf];
+      const View& inv = lower ? H.linv[dt] : H.uinv[dt];
+      int r = c.begin - T.begin, sz = c.end - c.begin;
+      E.gemm(o.sub(r, 0, sz, kf), 1.0, inv, U.sub(r, 0, sz, kf), 0.0);
+    }
+    FL.plr[q] = o.p;
+  }
   if (E.status != HM_OK || arena.status != HM_OK) {
     out.err = "H-LU planning failed (device memory or shape)";
     return E.status != HM_OK ? E.status : arena.status;
@@ -712,6 +776,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   out.ops = E.nops;
   FactorLayout& F = out.F;
   F.kf = kf;
+  (void)F;
   F.d_rank = d_rank_f;
   F.dense = H.dense;
   F.linv.resize(nd, nullptr);
@@ -734,94 +799,167 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
 }
 
 // ---------------------------------------------------------------- solves
+//
+// Forward substitution L y = b leaf by leaf (Morton order).  With the leaf
+// inverses folded into the factors (P_pj = L_pp^{-1} L_pj, and likewise for
+// the rows of low-rank U factors),
+//     y_p = L_pp^{-1} b_p - sum_{j < p} P_pj y_j - sum_{q in L, rows(q) > p} (L_pp^{-1} U_q)[p] (V_q' y_s(q)),
+// a sum of independent row dot products.  Each source becomes ready when its
+// input is final; sources ready two phases early are summed by a
+// non-critical task one phase ahead, the rest by the critical task that
+// writes y_p.  V_q' y is accumulated as one partial product per leaf of the
+// column cluster.  Backward substitution U z = y runs the same way in reverse.
 
 namespace {
 
-class Solver {
+struct Src {
+  RowSrc s;
+  int ready;
+};
+
+class SolvePlanner {
  public:
-  Solver(const Plan& P_, Emitter& E_, const FactorLayout& F_, const std::vector<DenseDesc>& dd_,
-         const std::vector<LRDesc>& ld_)
-      : P(P_), E(E_), F(F_), dd(dd_), ld(ld_) {}
+  SolvePlanner(const Plan& P_, const std::vector<DenseDesc>& dd_, const std::vector<LRDesc>& ld_,
+               const FactorLayout& F_, Arena& A_, std::vector<Wave>& W_, std::vector<RowSrc>& S_)
+      : P(P_), dd(dd_), ld(ld_), F(F_), A(A_), waves(W_), srcs(S_) {}
   const Plan& P;
-  Emitter& E;
-  const FactorLayout& F;
   const std::vector<DenseDesc>& dd;
   const std::vector<LRDesc>& ld;
-  std::vector<View> dense, linv, uinv, U, V;
+  const FactorLayout& F;
+  Arena& A;
+  std::vector<Wave>& waves;
+  std::vector<RowSrc>& srcs;
+  int status = HM_OK;
 
-  const Block& B(int b) const { return P.bl[b]; }
-  int child(int b, int i, int j) const { return B(b).child0 + i * B(b).ncc + j; }
-  int rows(int b) const { const Cluster& c = P.cl[B(b).t]; return c.end - c.begin; }
-  int cols(int b) const { const Cluster& c = P.cl[B(b).s]; return c.end - c.begin; }
-  int rbeg(int b) const { return P.cl[B(b).t].begin; }
-  int cbeg(int b) const { return P.cl[B(b).s].begin; }
+  Wave& at(int ph) {
+    if ((int)waves.size() <= ph) waves.resize(ph + 1);
+    return waves[ph];
+  }
 
-  void setup() {
-    const int nd = (int)dd.size(), nl = (int)ld.size();
-    dense.resize(nd);
-    linv.resize(nd);
-    uinv.resize(nd);
-    for (int d = 0; d < nd; ++d) {
-      const View& v = F.dense[d];
-      dense[d] = E.wrap(v.p, v.rows, v.cols, v.rs, v.cs);
-      if (F.linv[d]) {
-        linv[d] = E.wrap(F.linv[d], dd[d].m, dd[d].m, F.linv_ld[d], 1);
-        uinv[d] = E.wrap(F.uinv[d], dd[d].m, dd[d].m, F.linv_ld[d], 1);
+  void emit_rows(int ph, double* out, const double* base, int r0, int nr, int chunk,
+                 const std::vector<RowSrc>& list) {
+    for (int c = 0; c < nr; c += chunk) {
+      RowsOp o{};
+      o.out = out;
+      o.base = base;
+      o.r0 = r0 + c;
+      o.nr = std::min(chunk, nr - c);
+      o.src_begin = (int)srcs.size();
+      for (RowSrc s : list) {
+        s.M = s.M + (int64_t)c * s.rs;
+        srcs.push_back(s);
       }
-    }
-    U.resize(nl);
-    V.resize(nl);
-    for (int q = 0; q < nl; ++q) {
-      U[q] = E.wrap(F.lr_u[q], ld[q].m, F.kf, 1, ld[q].m);
-      V[q] = E.wrap(F.lr_v[q], ld[q].n, F.kf, 1, ld[q].n);
+      o.src_end = (int)srcs.size();
+      at(ph).rows.push_back(o);
     }
   }
 
-  // y[rows of a] -= A y[cols of a]
-  void apply(const View& y, int a) {
-    const Block& A = B(a);
-    View yo = y.sub(rbeg(a), 0, rows(a), 1), yi = y.sub(cbeg(a), 0, cols(a), 1);
-    if (A.type == BT_DENSE) { E.gemm(yo, -1.0, dense[A.id], yi, 1.0); return; }
-    if (A.type == BT_LR) {
-      View W = E.tmp(F.kf, 1, false);
-      E.gemm(W, 1.0, V[A.id].T(), yi, 0.0);
-      E.gemm(yo, -1.0, U[A.id], W, 1.0);
-      E.release(W);
-      return;
+  // one sweep; lower = forward with L, otherwise backward with U
+  void sweep(bool lower, const double* in, const std::vector<int>& in_ready, double* out, double* acc,
+             std::vector<int>& out_ready) {
+    const int nl = (int)P.leaves.size();
+    const int kf = F.kf;
+    std::vector<int> leaf_of(P.N, 0);
+    for (int i = 0; i < nl; ++i)
+      for (int r = P.cl[P.leaves[i]].begin; r < P.cl[P.leaves[i]].end; ++r) leaf_of[r] = i;
+    // per LR block of this triangle: partial products, one per leaf of its column cluster
+    std::vector<double*> part(ld.size(), nullptr), wfin(ld.size(), nullptr);
+    std::vector<int> nparts(ld.size(), 0), w_ready(ld.size(), -1), seen(ld.size(), 0);
+    std::vector<std::vector<int>> lr_by_rowleaf(nl), lr_by_colleaf(nl), dense_by_rowleaf(nl);
+    for (size_t q = 0; q < ld.size(); ++q) {
+      const bool isl = ld[q].r0 > ld[q].c0;
+      if (isl != lower) continue;
+      nparts[q] = 0;
+      for (int r = ld[q].c0; r < ld[q].c0 + ld[q].n; r = P.cl[P.leaves[leaf_of[r]]].end) {
+        lr_by_colleaf[leaf_of[r]].push_back((int)q);
+        ++nparts[q];
+      }
+      for (int r = ld[q].r0; r < ld[q].r0 + ld[q].m; r = P.cl[P.leaves[leaf_of[r]]].end)
+        lr_by_rowleaf[leaf_of[r]].push_back((int)q);
+      part[q] = A.alloc((int64_t)nparts[q] * kf);
+      wfin[q] = nparts[q] > 1 ? A.alloc(kf) : part[q];
+      if (!part[q] || !wfin[q]) status = HM_ERR_OOM;
     }
-    for (int i = 0; i < A.nrc; ++i)
-      for (int j = 0; j < A.ncc; ++j) apply(y, child(a, i, j));
-  }
-
-  void fwd(const View& y, int b) {
-    const Block& X = B(b);
-    if (X.type == BT_DENSE) {
-      View yt = y.sub(rbeg(b), 0, rows(b), 1);
-      View Tm = E.tmp(rows(b), 1, false);
-      E.gemm(Tm, 1.0, linv[X.id], yt, 0.0);
-      E.copy(yt, 1.0, &Tm, 0.0);
-      E.release(Tm);
-      return;
+    for (size_t d = 0; d < dd.size(); ++d) {
+      if (dd[d].r0 == dd[d].c0) continue;
+      if ((dd[d].r0 > dd[d].c0) != lower) continue;
+      dense_by_rowleaf[leaf_of[dd[d].r0]].push_back((int)d);
     }
-    for (int a = 0; a < X.nrc; ++a) {
-      fwd(y, child(b, a, a));
-      for (int a2 = a + 1; a2 < X.nrc; ++a2) apply(y, child(b, a2, a));
-    }
-  }
-
-  void bwd(const View& y, int b) {
-    const Block& X = B(b);
-    if (X.type == BT_DENSE) {
-      View yt = y.sub(rbeg(b), 0, rows(b), 1);
-      View Tm = E.tmp(rows(b), 1, false);
-      E.gemm(Tm, 1.0, uinv[X.id], yt, 0.0);
-      E.copy(yt, 1.0, &Tm, 0.0);
-      E.release(Tm);
-      return;
-    }
-    for (int a = X.nrc - 1; a >= 0; --a) {
-      bwd(y, child(b, a, a));
-      for (int a2 = a - 1; a2 >= 0; --a2) apply(y, child(b, a2, a));
+    out_ready.assign(nl, -1);
+    for (int it = 0; it < nl; ++it) {
+      const int p = lower ? it : nl - 1 - it;
+      const Cluster& C = P.cl[P.leaves[p]];
+      const int rb = C.begin, nr = C.end - C.begin;
+      const int dg = F.leaf_diag[p];
+      std::vector<Src> list;
+      {
+        RowSrc s{};
+        s.M = lower ? F.linv[dg] : F.uinv[dg];
+        s.rs = F.linv_ld[dg];
+        s.cs = 1;
+        s.x = in + rb;
+        s.ncols = nr;
+        s.nparts = 0;
+        s.sign = 1.0;
+        list.push_back({s, in_ready[p]});
+      }
+      for (int d : dense_by_rowleaf[p]) {
+        RowSrc s{};
+        s.M = F.pdense[d];
+        s.rs = dd[d].n;
+        s.cs = 1;
+        s.x = out + dd[d].c0;
+        s.ncols = dd[d].n;
+        s.sign = -1.0;
+        list.push_back({s, out_ready[leaf_of[dd[d].c0]]});
+      }
+      for (int q : lr_by_rowleaf[p]) {
+        RowSrc s{};
+        s.M = F.plr[q] + (rb - ld[q].r0);
+        s.rs = 1;
+        s.cs = ld[q].m;
+        s.x = wfin[q];
+        s.ncols = kf;
+        s.nparts = 1;
+        s.sign = -1.0;
+        list.push_back({s, w_ready[q]});
+      }
+      int ph = 0;
+      for (const Src& s : list) ph = std::max(ph, s.ready + 1);
+      std::vector<RowSrc> all;
+      for (const Src& s : list) all.push_back(s.s);
+      emit_rows(ph, out, nullptr, rb, nr, 8, all);
+      out_ready[p] = ph;
+      // partial products V_q' y for the blocks whose column cluster holds this
+      // leaf; after the last one, one task sums them into w_q
+      for (int q : lr_by_colleaf[p]) {
+        int seg = 0;
+        for (int r = ld[q].c0; r < rb; r = P.cl[P.leaves[leaf_of[r]]].end) ++seg;
+        VPartOp v{};
+        v.V = F.lr_v[q] + (rb - ld[q].c0);
+        v.ldv = ld[q].n;
+        v.y = out + rb;
+        v.len = nr;
+        v.kf = kf;
+        v.part = part[q] + (int64_t)seg * kf;
+        at(ph + 1).vpart.push_back(v);
+        w_ready[q] = std::max(w_ready[q], ph + 1);
+        if (++seen[q] == nparts[q] && nparts[q] > 1) {
+          ReduceOp o{};
+          o.parts = part[q];
+          o.dst = wfin[q];
+          o.stride = kf;
+          o.drs = 0;
+          o.dcs = 1;
+          o.m = 1;
+          o.n = kf;
+          o.nparts = nparts[q];
+          o.alpha = 1.0;
+          o.beta = 0.0;
+          at(w_ready[q] + 1).reduce.push_back(o);
+          w_ready[q] += 1;
+        }
+      }
     }
   }
 };
@@ -829,14 +967,14 @@ class Solver {
 }  // namespace
 
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
-               const FactorLayout& F, double* d_y, Arena& arena, std::vector<Wave>& waves) {
-  Emitter E(waves, arena, std::max(1, std::min(P.leaf, 256)));
-  Solver S(P, E, F, dd, ld);
-  S.setup();
-  View y = E.wrap(d_y, P.N, 1, 1, 0);
-  S.fwd(y, 0);
-  S.bwd(y, 0);
-  if (E.status != HM_OK || arena.status != HM_OK) return E.status != HM_OK ? E.status : arena.status;
+               const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
+               std::vector<RowSrc>& srcs) {
+  SolvePlanner S(P, dd, ld, F, arena, waves, srcs);
+  const int nl = (int)P.leaves.size();
+  std::vector<int> b_ready(nl, -1), y_ready, z_ready;
+  S.sweep(true, v.b, b_ready, v.y, v.acc1, y_ready);
+  S.sweep(false, v.y, y_ready, v.z, v.acc2, z_ready);
+  if (S.status != HM_OK || arena.status != HM_OK) return S.status != HM_OK ? S.status : arena.status;
   return HM_OK;
 }
 
@@ -847,6 +985,7 @@ namespace hm {
 namespace {
 struct SpanCheck {
   const std::vector<std::pair<uintptr_t, uintptr_t>>& R;
+  const std::vector<RowSrc>* srcs = nullptr;
   int64_t bad = 0;
   std::string first;
   bool inside(const double* p, int64_t lo, int64_t hi) const {
@@ -871,8 +1010,9 @@ struct SpanCheck {
 }  // namespace
 
 int64_t check_spans(const std::vector<Wave>& waves,
-                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first) {
-  SpanCheck C{ranges};
+                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first,
+                    const std::vector<RowSrc>* srcs) {
+  SpanCheck C{ranges, srcs};
   for (const Wave& w : waves) {
     for (const GemmOp& o : w.gemm) {
       C.view(o.A, o.m, o.k, o.ars, o.acs, "gemm A");
@@ -897,8 +1037,24 @@ int64_t check_spans(const std::vector<Wave>& waves,
       C.view(o.dst, o.m, o.n, o.drs, o.dcs, "copy dst");
     }
     for (const ReduceOp& o : w.reduce) {
-      C.view(o.parts, o.nparts, (int)o.count, o.stride, 1, "reduce parts");
-      C.view(o.dst, 1, (int)o.count, 0, 1, "reduce dst");
+      C.view(o.parts, o.nparts, o.m * o.n, o.stride, 1, "reduce parts");
+      C.view(o.dst, o.m, o.n, o.drs, o.dcs, "reduce dst");
+    }
+    for (const VPartOp& o : w.vpart) {
+      C.view(o.V, o.len, o.kf, 1, o.ldv, "vpart V");
+      C.view(o.y, o.len, 1, 1, 0, "vpart y");
+      C.view(o.part, o.kf, 1, 1, 0, "vpart part");
+    }
+    for (const RowsOp& o : w.rows) {
+      C.view(o.out + o.r0, o.nr, 1, 1, 0, "rows out");
+      if (o.base) C.view(o.base + o.r0, o.nr, 1, 1, 0, "rows base");
+      if (C.srcs) {
+        for (int k = o.src_begin; k < o.src_end; ++k) {
+          const RowSrc& r = (*C.srcs)[k];
+          C.view(r.M, o.nr, r.ncols, r.rs, r.cs, "rows src M");
+          C.view(r.x, std::max(r.nparts, 1) * r.ncols, 1, 1, 0, "rows src x");
+        }
+      }
     }
   }
   first = C.first;

@@ -59,7 +59,8 @@ struct Arena {
 // Check that every operand of every operation lies inside one of `ranges`
 // (byte intervals).  Returns the number of violations.
 int64_t check_spans(const std::vector<Wave>& waves,
-                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first);
+                    const std::vector<std::pair<uintptr_t, uintptr_t>>& ranges, std::string& first,
+                    const std::vector<RowSrc>* srcs = nullptr);
 
 // Final layout of the factors consumed by the solves.
 struct FactorLayout {
@@ -69,6 +70,12 @@ struct FactorLayout {
   std::vector<double*> lr_u, lr_v;       // per LR block: U (m x kf), V (n x kf) column-major
   int kf = 0;
   int* d_rank = nullptr;                 // per LR block rank (device)
+  // factors scaled by the leaf inverses for the solves: dense block (p, j)
+  // becomes L_pp^{-1} L_pj (j < p) or U_pp^{-1} U_pj (j > p); a low-rank block
+  // keeps V and scales the rows of U leaf by leaf the same way.
+  std::vector<int> leaf_diag;            // per leaf (Morton order) -> dense id of its diagonal block
+  std::vector<double*> pdense;           // per dense id (off-diagonal), m x n row-major
+  std::vector<double*> plr;              // per LR id, m x kf column-major
 };
 
 struct HluBuild {
@@ -85,9 +92,18 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out);
 
-// Expand y = (LU)^{-1} y on the Morton-order device vector y (forward then
-// backward H-triangular substitution); the list is replayed for every solve.
+// Expand z = U^{-1} L^{-1} b (forward then backward H-triangular
+// substitution, leaf by leaf over the scaled factors) into phases of row and
+// partial-product tasks on Morton-order device vectors; replayed per solve.
+struct SolveVectors {
+  const double* b;
+  double* y;     // forward result
+  double* z;     // backward result
+  double* acc1;  // forward partial rows
+  double* acc2;  // backward partial rows
+};
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
-               const FactorLayout& F, double* d_y, Arena& arena, std::vector<Wave>& waves);
+               const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
+               std::vector<RowSrc>& srcs);
 
 }  // namespace hm

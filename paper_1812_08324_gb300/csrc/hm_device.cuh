@@ -13,7 +13,49 @@ enum : int {
   DEVERR_NONFINITE = 2,  // a non-finite value appeared where it must not
   DEVERR_RANKCAP = 4,    // a low-rank sum needed more than its capacity
   DEVERR_ZEROPIVOT = 8,  // a zero pivot in an unpivoted dense LU
+  DEVERR_TIMEOUT = 16,   // a bounded wait in a persistent kernel gave up
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch: bar[0] counts arrivals, bar[1]
+// is the generation.  Waits at most limit_ns; returns false (and sets
+// DEVERR_TIMEOUT) if the other CTAs did not arrive in time.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                                             unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      // pure polling (a sleeping warp wakes up far later than requested);
+      // the clock is checked every 256 polls to bound the wait
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      while (*vgen == g) {
+        if ((++polls & 255u) == 0 && global_ns() - t0 > limit_ns) {
+          atomicOr(err, DEVERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
 
 // G between Morton positions p (row) and q (column): the formula of Eq. Aij
 // (sign-flipped) with the singular corrections, evaluated from the offset

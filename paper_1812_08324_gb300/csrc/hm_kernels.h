@@ -7,6 +7,8 @@
 
 namespace hm {
 
+void count_launches(int n);  // process-wide launch statistics
+
 // Parameters of nu and of the discretisation, passed by value to kernels.
 struct NuParams {
   int dim, kernel, nw, n0, n1;

@@ -145,6 +145,7 @@ __global__ void scatter_kernel(const int* perm, int N, const double* src, double
 int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* x, double gamma,
                   const double* w1, const double* w2, const double* w3, double* y,
                   cudaStream_t st) {
+  count_launches(P.nvt > 0 ? 3 : 1);
   if (P.nvt > 0) {
     vt_kernel<<<P.nvt, 256, 0, st>>>(P.vt, P.ld, P.rank, P.V, x, P.partial);
     vt_reduce_kernel<<<P.nlr, 64, 0, st>>>(P.nlr, P.vt_range, P.rank, P.partial, P.tvec);
@@ -155,11 +156,13 @@ int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* 
 }
 
 int launch_gather(const int* perm, int N, const double* src, double* dst, cudaStream_t st) {
+  count_launches(1);
   gather_kernel<<<std::min((N + 255) / 256, 152 * 8), 256, 0, st>>>(perm, N, src, dst);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
 int launch_scatter(const int* perm, int N, const double* src, double* dst, cudaStream_t st) {
+  count_launches(1);
   scatter_kernel<<<std::min((N + 255) / 256, 152 * 8), 256, 0, st>>>(perm, N, src, dst);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }

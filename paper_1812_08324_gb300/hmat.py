@@ -21,7 +21,7 @@ HM_FP64, HM_MIXED_FP32 = 0, 1
 EXPORTED = [
     "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
-    "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor",
+    "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor", "hm_launch_count",
 ]
 
 
@@ -97,6 +97,7 @@ def load() -> C.CDLL:
         "hm_free": (None, [vp]),
         "hm_factors_free": (None, [vp]),
         "hm_plan_factor": (i, [P, O, d, C.POINTER(FactorPlan)]),
+        "hm_launch_count": (i64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -181,6 +182,11 @@ def plan_blocks(problem: dict, opts: dict):
     _check(lib.hm_plan_blocks(C.byref(make_problem(problem)), C.byref(make_opts(opts)), C.byref(c),
                               *[a.ctypes.data for a in arrs], perm.ctypes.data))
     return (*arrs, perm)
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(load().hm_launch_count())
 
 
 def _stream(stream=None) -> int:
