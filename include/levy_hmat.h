@@ -179,6 +179,28 @@ int hm_matvec(const hm_matrix* H, double alpha, double beta, const double* x, do
               const double* w1, const double* w2, double* y, void* stream);
 
 /*
+ * hm_matvec_noalloc: the same product as hm_matvec, for callers that must not
+ * allocate device memory when they call it -- e.g. a server that admits work
+ * against a fixed device-memory budget, or code running where cudaMalloc
+ * would synchronise the device or is forbidden by the host application.  It
+ * allocates nothing: its scratch (the V'x partial products, the per-block
+ * coefficient vectors and, in 2D, Morton-order copies of the vectors) is one
+ * fixed library-wide array of 2^21 doubles (16 MiB) in device global memory,
+ * which every GPU that loads the library holds until the process exits.
+ * H must need at most that much scratch (about N/256 * 3 * depth partials of
+ * 128 doubles in 1D); larger problems get HM_ERR_ARG and a message with the
+ * size needed.  The first call on a device looks up the array's device address
+ * with cudaGetSymbolAddress (that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; every entry a call reads is written earlier in the same
+ * call, so nothing needs clearing.  Calls that overlap on the GPU (other
+ * streams, other threads) race on the array: serialise them.  The paper has
+ * no counterpart; this is a library facility.  Arguments as hm_matvec.
+ */
+int hm_matvec_noalloc(const hm_matrix* H, double alpha, double beta, const double* x, double gamma,
+                      const double* w1, const double* w2, double* y, void* stream);
+
+/*
  * hm_to_dense: expand H into a dense N x N row-major device array (natural
  * order), for checks at small N.  out must hold N*N doubles.
  */

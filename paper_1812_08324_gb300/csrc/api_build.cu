@@ -369,6 +369,37 @@ int hm_matvec(const hm_matrix* H, double alpha, double beta, const double* x, do
   return launch_scatter(H->d_perm, N, ym, y, st);
 }
 
+int hm_matvec_noalloc(const hm_matrix* H, double alpha, double beta, const double* x, double gamma,
+                      const double* w1, const double* w2, double* y, void* stream) {
+  if (!H || !x || !y) { set_error("null argument"); return HM_ERR_ARG; }
+  if (x == y) { set_error("y must not alias x"); return HM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = H->plan.N;
+  const size_t part = (size_t)H->mv.nvt * ACA_MAXK, tv = (size_t)H->mv.nlr * ACA_MAXK;
+  const size_t vecs = H->plan.dim == 2 ? 4 * (size_t)N : 0;
+  const size_t need = part + tv + vecs;
+  if (need > noalloc_capacity()) {
+    set_error("hm_matvec_noalloc: this H-matrix needs " + std::to_string(need) +
+              " doubles of scratch; the fixed scratch holds " + std::to_string(noalloc_capacity()));
+    return HM_ERR_ARG;
+  }
+  double* s = nullptr;
+  if (noalloc_scratch(&s) != HM_OK) { set_error("cudaGetSymbolAddress of the fixed scratch failed"); return HM_ERR_CUDA; }
+  MatvecPlan Q = H->mv;
+  Q.partial = s;
+  Q.tvec = s + part;
+  if (H->plan.dim == 1) return launch_matvec(Q, alpha, beta, x, gamma, w1, w2, nullptr, y, st);
+  double* xm = s + part + tv;
+  double* ym = xm + N;
+  double* a = ym + N;
+  double* c = a + N;
+  HM_TRY(launch_gather(H->d_perm, N, x, xm, st));
+  if (w1) HM_TRY(launch_gather(H->d_perm, N, w1, a, st));
+  if (w2) HM_TRY(launch_gather(H->d_perm, N, w2, c, st));
+  HM_TRY(launch_matvec(Q, alpha, beta, xm, gamma, w1 ? a : nullptr, w2 ? c : nullptr, nullptr, ym, st));
+  return launch_scatter(H->d_perm, N, ym, y, st);
+}
+
 int hm_to_dense(const hm_matrix* H, double* out, void* stream) {
   if (!H || !out) { set_error("null argument"); return HM_ERR_ARG; }
   return launch_to_dense(H->d_dd, (int)H->h_dd.size(), H->d_D, H->d_ld, (int)H->h_ld.size(),

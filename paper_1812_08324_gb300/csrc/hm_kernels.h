@@ -58,6 +58,11 @@ struct MatvecPlan {
 int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* x, double gamma,
                   const double* w1, const double* w2, const double* w3, double* y, cudaStream_t st);
 
+// Fixed scratch of hm_matvec_noalloc: capacity in doubles and device address
+// (looked up on first use per device).
+size_t noalloc_capacity();
+int noalloc_scratch(double** out);
+
 int launch_gather(const int* perm, int N, const double* src, double* dst, cudaStream_t st);
 int launch_scatter(const int* perm, int N, const double* src, double* dst, cudaStream_t st);
 

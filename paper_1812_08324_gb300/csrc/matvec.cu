@@ -142,6 +142,33 @@ __global__ void scatter_kernel(const int* perm, int N, const double* src, double
 
 }  // namespace
 
+// ---- scratch for hm_matvec_noalloc ------------------------------------------
+// A fixed array of 2^21 doubles (16 MiB) in device global memory, loaded with
+// the library on every GPU that uses it and held until the process exits.  It
+// takes the V'x partial products and the per-block coefficient vectors of one
+// H-matvec (and, in 2D, the Morton-order copies of the vectors).
+constexpr size_t NOALLOC_DOUBLES = size_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+size_t noalloc_capacity() { return NOALLOC_DOUBLES; }
+
+// Device address of the array for the current device.  In host code the
+// symbol name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(double** out) {
+  static double* addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HM_ERR_CUDA;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return HM_ERR_CUDA;
+    addr[dev] = static_cast<double*>(p);
+  }
+  *out = addr[dev];
+  return HM_OK;
+}
+
 int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* x, double gamma,
                   const double* w1, const double* w2, const double* w3, double* y,
                   cudaStream_t st) {

@@ -22,6 +22,7 @@ EXPORTED = [
     "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
     "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor", "hm_launch_count",
+    "hm_matvec_noalloc",
 ]
 
 
@@ -98,6 +99,7 @@ def load() -> C.CDLL:
         "hm_factors_free": (None, [vp]),
         "hm_plan_factor": (i, [P, O, d, C.POINTER(FactorPlan)]),
         "hm_launch_count": (i64, []),
+        "hm_matvec_noalloc": (i, [vp, d, d, vp, d, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
