@@ -59,48 +59,50 @@ __global__ void norms_kernel(int N, const double* a, const double* b, double* ou
 
 int vgrid(int N) { return std::min((N + 255) / 256, 152 * 8); }
 
-// Phase tracing (HM_PHASE_TRACE=1): run a schedule once with per-phase time
-// stamps and print where the time went, by the operation kinds of each phase.
+// Tracing (HM_PHASE_TRACE=1): run a schedule once recording every op's
+// finish time and print the span, the time per op kind along the waves, and
+// the ops that finished last.
 void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevSchedule& S, int* d_err,
                     cudaStream_t st) {
   unsigned long long* d_tr = nullptr;
-  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * (S.nphases + 1)) != cudaSuccess) return;
+  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * std::max(S.nops, 1)) != cudaSuccess) return;
+  cudaMemsetAsync(d_tr, 0, sizeof(unsigned long long) * std::max(S.nops, 1), st);
   cudaStreamSynchronize(st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
   run_schedule(S, d_err, st, d_tr);
+  cudaEventRecord(e1, st);
   cudaStreamSynchronize(st);
-  std::vector<unsigned long long> tr(S.nphases + 1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  std::vector<unsigned long long> tr(std::max(S.nops, 1));
   cudaMemcpy(tr.data(), d_tr, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost);
   cudaFree(d_tr);
+  unsigned long long t0 = ~0ull, t1 = 0;
+  for (auto t : tr)
+    if (t) { t0 = std::min(t0, t); t1 = std::max(t1, t); }
+  // wave finish time = latest finish of its ops; attribute each wave's advance
   const char* names[7] = {"gemm", "lu", "trunc", "copy", "reduce", "rows", "vpart"};
   double by[7] = {0, 0, 0, 0, 0, 0, 0};
-  int cnt[7] = {0, 0, 0, 0, 0, 0, 0};
-  std::vector<std::pair<double, int>> slow;
-  for (int p = 0; p < S.nphases; ++p) {
-    double dt = (double)(tr[p + 1] - tr[p]) * 1e-3;  // us
-    const Wave& W = waves[p];
-    size_t n[7] = {W.gemm.size(), W.lu.size(), W.trunc.size(), W.copy.size(), W.reduce.size(), W.rows.size(),
-                   W.vpart.size()};
+  unsigned long long prev = t0;
+  for (const Wave& W : waves) {
+    unsigned long long wt = 0;
     int dom = 0;
-    // attribute a phase to its most expensive-looking kind: trunc > lu > gemm > rows > others
-    const int pri[7] = {2, 1, 0, 5, 6, 4, 3};
-    for (int k : pri)
-      if (n[k]) { dom = k; break; }
-    by[dom] += dt;
-    cnt[dom]++;
-    slow.push_back({dt, p});
+    unsigned long long best = 0;
+    const std::vector<int>* ids[7] = {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id, &W.rows_id, &W.vpart_id};
+    for (int k = 0; k < 7; ++k)
+      for (int id : *ids[k]) {
+        wt = std::max(wt, tr[id]);
+        if (tr[id] > best) { best = tr[id]; dom = k; }
+      }
+    if (wt > prev) { by[dom] += (double)(wt - prev) * 1e-3; prev = wt; }
   }
-  std::sort(slow.rbegin(), slow.rend());
-  double tot = (double)(tr[S.nphases] - tr[0]) * 1e-3;
-  fprintf(stderr, "[trace] %s: %d phases, %.1f us total, %.2f us/phase\n", what, S.nphases, tot,
-          tot / std::max(1, S.nphases));
+  fprintf(stderr, "[trace] %s: %d waves, %d ops, kernel %.3f ms, op span %.3f ms\n", what, S.nwaves, S.nops, ms,
+          (double)(t1 - t0) * 1e-6);
   for (int k = 0; k < 7; ++k)
-    if (cnt[k]) fprintf(stderr, "[trace]   phases led by %-6s: %6d  %10.1f us  (%.2f us each)\n", names[k], cnt[k], by[k], by[k] / cnt[k]);
-  for (int i = 0; i < std::min<int>(8, (int)slow.size()); ++i) {
-    const Wave& W = waves[slow[i].second];
-    fprintf(stderr, "[trace]   slow phase %d: %.1f us gemm=%zu lu=%zu trunc=%zu copy=%zu reduce=%zu rows=%zu vpart=%zu\n",
-            slow[i].second, slow[i].first, W.gemm.size(), W.lu.size(), W.trunc.size(), W.copy.size(),
-            W.reduce.size(), W.rows.size(), W.vpart.size());
-  }
+    if (by[k] > 0) fprintf(stderr, "[trace]   advance led by %-6s %10.1f us\n", names[k], by[k]);
 }
 
 // z = (LU)^{-1} b on Morton-order vectors (b may equal z)
@@ -194,7 +196,7 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   if (s != HM_OK) { set_error(hb.err); return fail(s); }
   DevSchedule fs;
   std::vector<void*> fs_allocs;
-  s = upload_schedule(hb.waves, fs, fs_allocs);
+  s = upload_schedule(hb.waves, hb.graph, fs, fs_allocs);
   const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
   if (s == HM_OK && tracing) {
     trace_schedule("factor", hb.waves, fs, H->d_err, st);  // note: runs the factorisation
@@ -227,10 +229,11 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   // the solve schedule, replayed by every hm_solve
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
+  OpGraph sg;
   SolveVectors sv{F->d_y, F->d_sv, F->d_sv + (size_t)N, F->d_sv + 2 * (size_t)N, F->d_sv + 3 * (size_t)N};
-  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, sv, F->arena, sw, srcs);
+  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, sv, F->arena, sw, srcs, sg);
   if (s != HM_OK) { set_error("solve planning failed"); return fail(s); }
-  s = upload_schedule(sw, F->solve, F->allocs, &srcs);
+  s = upload_schedule(sw, sg, F->solve, F->allocs, &srcs);
   if (s != HM_OK) { set_error("solve schedule upload failed"); return fail(s); }
   if (tracing) {
     trace_schedule("solve", sw, F->solve, H->d_err, st);
@@ -367,8 +370,9 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   if (s != HM_OK) { set_error("planning failed: " + hb.err); return s; }
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
+  OpGraph sg;
   SolveVectors sv{fy, fy + P.N, fy + 2 * (int64_t)P.N, fy + 3 * (int64_t)P.N, fy + 4 * (int64_t)P.N};
-  s = plan_solve(P, dd, ld, hb.F, sv, A, sw, srcs);
+  s = plan_solve(P, dd, ld, hb.F, sv, A, sw, srcs, sg);
   if (s != HM_OK) { set_error("solve planning failed"); return s; }
   std::string first;
   int64_t bad = check_spans(hb.waves, A.ranges, first) + check_spans(sw, A.ranges, first, &srcs);

@@ -420,34 +420,101 @@ __device__ void dev_reduce(const ReduceOp& op, int chunk, int nchunks) {
 // over columns.  Low-rank sources: warp per source (round robin), lane per
 // row, after summing the source's partial products.  Per-row totals are
 // combined in a fixed order, so results are bitwise reproducible.
-__device__ void dev_rows(const RowsOp& op, const RowSrc* srcs, double* smem) {
-  double* acc_d = smem;               // 32
-  double* acc_l = smem + 32;          // 8 x 32
-  double* wsum = smem + 32 + 256;     // 8 x 64 (per-warp low-rank coefficient vector)
+// Shared-memory layout of a row task: accumulators, per-warp coefficient
+// vectors, staged descriptors, then prefetched rows of dense sources.
+constexpr int ROWS_PREFETCH_DOUBLES = 8192;  // 64 KB of prefetched matrix rows
+struct RowsSmem {
+  double* acc_d;    // 32
+  double* acc_l;    // 8 x 32
+  double* wsum;     // 8 x 64
+  RowSrc* srcs;     // up to 256 descriptors
+  double* pre;      // prefetched rows
+  int* pre_off;     // per source: offset into pre (-1: not prefetched), up to 256
+};
+
+__device__ __forceinline__ RowsSmem rows_smem(double* smem) {
+  RowsSmem L;
+  L.acc_d = smem;
+  L.acc_l = smem + 32;
+  L.wsum = smem + 32 + 256;
+  L.srcs = reinterpret_cast<RowSrc*>(smem + 32 + 256 + 512);
+  L.pre = smem + 32 + 256 + 512 + 256 * (sizeof(RowSrc) / sizeof(double));
+  L.pre_off = reinterpret_cast<int*>(L.pre + ROWS_PREFETCH_DOUBLES);
+  return L;
+}
+
+// Stage the descriptors and copy the rows of dense sources (static data) into
+// shared memory; runs before the task waits on its producers.
+__device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double* smem) {
+  RowsSmem L = rows_smem(smem);
+  const int nsrc = min(op.src_end - op.src_begin, 256);
+  {
+    const int words = nsrc * (int)(sizeof(RowSrc) / sizeof(long long));
+    const long long* g = reinterpret_cast<const long long*>(srcs_g + op.src_begin);
+    long long* d = reinterpret_cast<long long*>(L.srcs);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) d[w] = g[w];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int used = 0;
+    for (int s = 0; s < nsrc; ++s) {
+      const RowSrc& S = L.srcs[s];
+      const int need = op.nr * S.ncols;
+      if (!S.nparts && used + need <= ROWS_PREFETCH_DOUBLES) {
+        L.pre_off[s] = used;
+        used += need;
+      } else {
+        L.pre_off[s] = -1;
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < nsrc; ++s) {
+    const int off = L.pre_off[s];
+    if (off < 0) continue;
+    const RowSrc& S = L.srcs[s];
+    const int nc = S.ncols, tot = op.nr * nc;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int r = e / nc, c = e % nc;
+      L.pre[off + e] = S.M[r * S.rs + c * S.cs];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void dev_rows(const RowsOp& op, double* smem) {
+  RowsSmem L = rows_smem(smem);
+  const int nsrc = min(op.src_end - op.src_begin, 256);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nr = op.nr;
   for (int r = warp; r < 32; r += 8) {
     double acc = 0.0;
     if (r < nr) {
-      for (int s = op.src_begin; s < op.src_end; ++s) {
-        const RowSrc S = srcs[s];
+      for (int s = 0; s < nsrc; ++s) {
+        const RowSrc& S = L.srcs[s];
         if (S.nparts) continue;
-        const double* Mr = S.M + r * S.rs;
         double a = 0.0;
-        for (int c = lane; c < S.ncols; c += 32) a += Mr[c * S.cs] * S.x[c];
+        const int off = L.pre_off[s];
+        if (off >= 0) {
+          const double* Mr = L.pre + off + r * S.ncols;
+          for (int c = lane; c < S.ncols; c += 32) a += Mr[c] * S.x[c];
+        } else {
+          const double* Mr = S.M + r * S.rs;
+          for (int c = lane; c < S.ncols; c += 32) a += Mr[c * S.cs] * S.x[c];
+        }
         acc += S.sign * a;
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) acc_d[r] = acc;
+    if (lane == 0) L.acc_d[r] = acc;
   }
   double la = 0.0;
   int k = 0;
-  for (int s = op.src_begin; s < op.src_end; ++s) {
-    const RowSrc S = srcs[s];
+  for (int s = 0; s < nsrc; ++s) {
+    const RowSrc& S = L.srcs[s];
     if (!S.nparts) continue;
     if ((k++ & 7) != warp) continue;
-    double* w = wsum + warp * 64;
+    double* w = L.wsum + warp * 64;
     for (int l = lane; l < S.ncols; l += 32) {
       // eight independent chains keep eight loads in flight
       double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -462,18 +529,19 @@ __device__ void dev_rows(const RowsOp& op, const RowSrc* srcs, double* smem) {
     if (lane < nr) {
       const double* Mr = S.M + lane * S.rs;
       double a = 0.0;
+#pragma unroll 4
       for (int l = 0; l < S.ncols; ++l) a += Mr[l * S.cs] * w[l];
       la += S.sign * a;
     }
     __syncwarp();
   }
-  acc_l[warp * 32 + lane] = la;
+  L.acc_l[warp * 32 + lane] = la;
   __syncthreads();
   if (threadIdx.x < nr) {
     const int r = threadIdx.x;
     double v = op.base ? op.base[op.r0 + r] : 0.0;
-    v += acc_d[r];
-    for (int w = 0; w < 8; ++w) v += acc_l[w * 32 + r];
+    v += L.acc_d[r];
+    for (int w = 0; w < 8; ++w) v += L.acc_l[w * 32 + r];
     op.out[op.r0 + r] = v;
   }
   __syncthreads();
@@ -493,7 +561,7 @@ __device__ void dev_vpart(const VPartOp& op) {
 constexpr int EXEC_THREADS = 256;
 constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
                              sizeof(int) * 6 * TRUNC_MAXK;
-constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s per phase boundary
+constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;  // 4 s for one dependency wait
 
 struct ExecArgs {
   const GemmOp* gemm;
@@ -505,43 +573,86 @@ struct ExecArgs {
   const VPartOp* vpart;
   const RowSrc* srcs;
   const Task* tasks;
-  const int* phase_begin;
-  int nphases;
-  unsigned* bar;
+  const int* wave_begin;
+  const OpInfo* ops;
+  const int* deps;
+  int* counters;
+  int* grab;        // next task to hand out
+  int ntasks;
   int* err;
-  unsigned long long* trace;  // optional: start time of every phase (ns)
+  unsigned long long* trace;  // optional: finish time of every op (ns), first task to finish last
 };
 
+// Wait until every producer of op `id` has finished all its tasks.  Warp 0
+// polls the counters (lanes split the producer list); bounded in time.
+__device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
+  __shared__ int ok;
+  if (threadIdx.x < 32) {
+    const OpInfo op = a.ops[id];
+    bool good = true;
+    const unsigned long long t0 = global_ns();
+    for (int k = op.dep_begin + (int)threadIdx.x; k < op.dep_end && good; k += 32) {
+      const int d = a.deps[k];
+      const int need = a.ops[d].ntasks;
+      volatile const int* c = a.counters + d;
+      unsigned polls = 0;
+      while (*c < need) {
+        if ((++polls & 255u) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) {
+          atomicOr(a.err, DEVERR_TIMEOUT);
+          good = false;
+          break;
+        }
+      }
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (threadIdx.x == 0) {
+      ok = good ? 1 : 0;
+      __threadfence();  // acquire: the producers' writes are visible after this
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Tasks are taken in topological order from a global counter, so a CTA
+// waiting on a producer never holds up a task that is ready elsewhere.
 __global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
   extern __shared__ double smem[];
-  for (int ph = 0; ph < a.nphases; ++ph) {
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[ph] = global_ns();
-    const int b = a.phase_begin[ph], e = a.phase_begin[ph + 1];
-    for (int t = b + (int)blockIdx.x; t < e; t += (int)gridDim.x) {
-      const Task T = a.tasks[t];
-      switch (T.kind) {
-        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
-        case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
-        case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
-        case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
-        case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
-        case TK_ROWS: dev_rows(a.rows[T.op], a.srcs, smem); break;
-        case TK_VPART: dev_vpart(a.vpart[T.op]); break;
-        default: break;
-      }
-      __syncthreads();
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(a.grab, 1);
+    __syncthreads();
+    const int t = next;
+    __syncthreads();
+    if (t >= a.ntasks) return;
+    const Task T = a.tasks[t];
+    if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem);
+    if (!wait_deps(a, T.id)) return;
+    switch (T.kind) {
+      case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
+      case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
+      case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
+      case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
+      case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
+      case TK_ROWS: dev_rows(a.rows[T.op], smem); break;
+      case TK_VPART: dev_vpart(a.vpart[T.op]); break;
+      default: break;
     }
-    if (ph + 1 < a.nphases && !grid_barrier(a.bar, gridDim.x, a.err, BARRIER_LIMIT_NS)) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // release: this task's writes before its completion count
+      atomicAdd(a.counters + T.id, 1);
+      if (a.trace) a.trace[T.id] = global_ns();
+    }
   }
-  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[a.nphases] = global_ns();
 }
 
 }  // namespace
 
 int gemm_tiles(int m, int n) { return ((m + GT - 1) / GT) * ((n + GT - 1) / GT); }
 
-int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs,
-                    const std::vector<RowSrc>* srcs) {
+int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSchedule& S,
+                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs) {
   std::vector<RowsOp> ro;
   std::vector<VPartOp> vp;
   std::vector<GemmOp> g;
@@ -550,32 +661,63 @@ int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<
   std::vector<CopyOp> c;
   std::vector<ReduceOp> r;
   std::vector<Task> tasks;
-  std::vector<int> pb;
+  std::vector<int> wb;
+  const int nops = (int)graph.deps.size();
+  std::vector<OpInfo> info(std::max(nops, 1), OpInfo{0, 0, 0, 0});
+  std::vector<int> deps;
+  for (int id = 0; id < nops; ++id) {
+    info[id].dep_begin = (int)deps.size();
+    for (int d : graph.deps[id]) deps.push_back(d);
+    info[id].dep_end = (int)deps.size();
+  }
   auto chunks = [](int64_t elems) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, elems / 4096)); };
   for (const Wave& W : waves) {
-    pb.push_back((int)tasks.size());
-    for (const GemmOp& o : W.gemm) {
-      int nt = gemm_tiles(o.m, o.n);
-      for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt});
+    wb.push_back((int)tasks.size());
+    for (size_t k = 0; k < W.gemm.size(); ++k) {
+      const GemmOp& o = W.gemm[k];
+      int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k];
+      for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
+      info[id].ntasks = nt;
       g.push_back(o);
     }
-    for (const LuOp& o : W.lu) { tasks.push_back({TK_LU, (int)l.size(), 0, 1}); l.push_back(o); }
-    for (const TruncOp& o : W.trunc) { tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1}); tr.push_back(o); }
-    for (const CopyOp& o : W.copy) {
-      int nc = chunks((int64_t)o.m * o.n);
-      for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc});
+    for (size_t k = 0; k < W.lu.size(); ++k) {
+      tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k]});
+      info[W.lu_id[k]].ntasks = 1;
+      l.push_back(W.lu[k]);
+    }
+    for (size_t k = 0; k < W.trunc.size(); ++k) {
+      tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k]});
+      info[W.trunc_id[k]].ntasks = 1;
+      tr.push_back(W.trunc[k]);
+    }
+    for (size_t k = 0; k < W.copy.size(); ++k) {
+      const CopyOp& o = W.copy[k];
+      int nc = chunks((int64_t)o.m * o.n), id = W.copy_id[k];
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc, id});
+      info[id].ntasks = nc;
       c.push_back(o);
     }
-    for (const ReduceOp& o : W.reduce) {
-      int nc = chunks((int64_t)o.m * o.n);
-      for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc});
+    for (size_t k = 0; k < W.reduce.size(); ++k) {
+      const ReduceOp& o = W.reduce[k];
+      int nc = chunks((int64_t)o.m * o.n), id = W.reduce_id[k];
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
+      info[id].ntasks = nc;
       r.push_back(o);
     }
-    for (const RowsOp& o : W.rows) { tasks.push_back({TK_ROWS, (int)ro.size(), 0, 1}); ro.push_back(o); }
-    for (const VPartOp& o : W.vpart) { tasks.push_back({TK_VPART, (int)vp.size(), 0, 1}); vp.push_back(o); }
+    for (size_t k = 0; k < W.rows.size(); ++k) {
+      tasks.push_back({TK_ROWS, (int)ro.size(), 0, 1, W.rows_id[k]});
+      info[W.rows_id[k]].ntasks = 1;
+      ro.push_back(W.rows[k]);
+    }
+    for (size_t k = 0; k < W.vpart.size(); ++k) {
+      tasks.push_back({TK_VPART, (int)vp.size(), 0, 1, W.vpart_id[k]});
+      info[W.vpart_id[k]].ntasks = 1;
+      vp.push_back(W.vpart[k]);
+    }
   }
-  pb.push_back((int)tasks.size());
-  S.nphases = (int)waves.size();
+  wb.push_back((int)tasks.size());
+  S.nwaves = (int)waves.size();
+  S.nops = nops;
   S.ntasks = (int64_t)tasks.size();
   auto up = [&](auto& vec, auto** dst) -> int {
     size_t bytes = std::max<size_t>(vec.size() * sizeof(vec[0]), 16);
@@ -598,14 +740,16 @@ int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<
   std::vector<RowSrc> nos;
   if ((s = up(srcs ? *srcs : nos, &S.srcs)) != HM_OK) return s;
   if ((s = up(tasks, &S.tasks)) != HM_OK) return s;
-  if ((s = up(pb, &S.phase_begin)) != HM_OK) return s;
-  std::vector<unsigned> bar(2, 0u);
-  if ((s = up(bar, &S.barrier)) != HM_OK) return s;
+  if ((s = up(wb, &S.wave_begin)) != HM_OK) return s;
+  if ((s = up(info, &S.ops)) != HM_OK) return s;
+  if ((s = up(deps, &S.deps)) != HM_OK) return s;
+  std::vector<int> cnt(nops + 1, 0);
+  if ((s = up(cnt, &S.counters)) != HM_OK) return s;
   return HM_OK;
 }
 
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned long long* trace) {
-  if (S.nphases == 0) return HM_OK;
+  if (S.ntasks == 0) return HM_OK;
   static int grid = 0;
   if (grid == 0) {
     if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EXEC_SMEM) != cudaSuccess)
@@ -617,9 +761,10 @@ int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned lon
       return HM_ERR_CUDA;
     grid = sms * per;
   }
-  if (cudaMemsetAsync(S.barrier, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return HM_ERR_CUDA;
-  ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.phase_begin,
-             S.nphases, S.barrier, d_err, trace};
+  // counters[nops] is the task dispenser
+  if (cudaMemsetAsync(S.counters, 0, sizeof(int) * (S.nops + 1), st) != cudaSuccess) return HM_ERR_CUDA;
+  ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.wave_begin,
+             S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, d_err, trace};
   void* args[] = {&a};
   count_launches(1);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)exec_kernel, dim3(grid), dim3(EXEC_THREADS), args,

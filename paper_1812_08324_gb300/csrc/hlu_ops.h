@@ -103,6 +103,7 @@ struct VPartOp {
 constexpr int LU_BASE = 32;    // leaf LU base-case size (one CTA)
 constexpr int TRUNC_MAXK = 96;   // 3 K x K FP64 matrices fit in 227 KB of shared memory
 
+// Operations of one wave (a topological level), with their global op ids.
 struct Wave {
   std::vector<GemmOp> gemm;
   std::vector<LuOp> lu;
@@ -111,19 +112,46 @@ struct Wave {
   std::vector<ReduceOp> reduce;
   std::vector<RowsOp> rows;
   std::vector<VPartOp> vpart;
+  std::vector<int> gemm_id, lu_id, trunc_id, copy_id, reduce_id, rows_id, vpart_id;
+  void add(const GemmOp& o, int id) { gemm.push_back(o); gemm_id.push_back(id); }
+  void add(const LuOp& o, int id) { lu.push_back(o); lu_id.push_back(id); }
+  void add(const TruncOp& o, int id) { trunc.push_back(o); trunc_id.push_back(id); }
+  void add(const CopyOp& o, int id) { copy.push_back(o); copy_id.push_back(id); }
+  void add(const ReduceOp& o, int id) { reduce.push_back(o); reduce_id.push_back(id); }
+  void add(const RowsOp& o, int id) { rows.push_back(o); rows_id.push_back(id); }
+  void add(const VPartOp& o, int id) { vpart.push_back(o); vpart_id.push_back(id); }
+  size_t size() const {
+    return gemm.size() + lu.size() + trunc.size() + copy.size() + reduce.size() + rows.size() + vpart.size();
+  }
+};
+
+// Producer ops of every op (by op id): an op may start once all its
+// producers have finished (read-after-write, write-after-read, write-after-write).
+struct OpGraph {
+  std::vector<std::vector<int>> deps;
+  int add_op(std::vector<int> d) {
+    deps.push_back(std::move(d));
+    return (int)deps.size() - 1;
+  }
 };
 
 // A unit of work for one CTA of the persistent executor: kind, index of the
-// operation in its per-kind array, and the part (tile / chunk) of it.
+// operation in its per-kind array, the part (tile / chunk) of it, and the op id.
 enum TaskKind { TK_GEMM = 0, TK_LU = 1, TK_TRUNC = 2, TK_COPY = 3, TK_REDUCE = 4, TK_ROWS = 5, TK_VPART = 6 };
 struct Task {
-  int kind, op, sub, nsub;
+  int kind, op, sub, nsub, id;
 };
 
-// Device-resident schedule: tasks grouped into phases; phase p holds tasks
-// [phase_begin[p], phase_begin[p+1]).  All tasks of a phase are independent.
+struct OpInfo {
+  int ntasks, dep_begin, dep_end, pad;
+};
+
+// Device-resident schedule.  Tasks are listed wave by wave; CTA c takes the
+// tasks of each wave whose position is c modulo the grid, in wave order, and
+// starts a task once the completion counters of its op's producers are full.
 struct DevSchedule {
-  int nphases = 0;
+  int nwaves = 0;
+  int nops = 0;
   int64_t ntasks = 0;
   GemmOp* gemm = nullptr;
   LuOp* lu = nullptr;
@@ -134,16 +162,18 @@ struct DevSchedule {
   VPartOp* vpart = nullptr;
   RowSrc* srcs = nullptr;
   Task* tasks = nullptr;
-  int* phase_begin = nullptr;
-  unsigned* barrier = nullptr;  // 2 words: arrival count, generation
+  int* wave_begin = nullptr;
+  OpInfo* ops = nullptr;
+  int* deps = nullptr;
+  int* counters = nullptr;   // per op: finished tasks
 };
 
-int upload_schedule(const std::vector<Wave>& waves, DevSchedule& S, std::vector<void*>& allocs,
-                    const std::vector<RowSrc>* srcs = nullptr);
+int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedule& S,
+                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs = nullptr);
 
-// Run all phases in one persistent cooperative launch (one CTA per SM); a
-// phase boundary is a grid barrier whose waits are bounded in time (on expiry
-// the kernel sets DEVERR_TIMEOUT in *d_err and returns).
+// Run a schedule in one persistent cooperative launch (one CTA per SM).  Every
+// wait is bounded in time: on expiry the kernel sets DEVERR_TIMEOUT in *d_err
+// and returns instead of hanging.
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st,
                  unsigned long long* trace = nullptr);
 

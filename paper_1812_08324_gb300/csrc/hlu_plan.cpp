@@ -11,7 +11,10 @@
 // Sums of low-rank terms are recompressed at relative tolerance lu_tol
 // (eps_2 of Sec. "Application") and the rank cap kf.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 
 #include "hlu_plan.h"
 
@@ -60,7 +63,9 @@ struct Tracker {
     int seg;
     bool elem = false;
     const double* base = nullptr;
-    std::vector<int> lw, lr;
+    std::vector<int> lw, lr;              // waves of the last write / latest read
+    std::vector<int> wop;                 // op id of the last write (-1: none)
+    std::vector<std::vector<int>> rops;   // op ids of the reads since the last write
   };
   std::vector<Buf> bufs;
   int add_elem(const double* base, int64_t cap) {
@@ -70,6 +75,8 @@ struct Tracker {
     b.seg = (int)std::max<int64_t>(1, (cap + 63) / 64);
     b.lw.assign(64, -1);
     b.lr.assign(64, -1);
+    b.wop.assign(64, -1);
+    b.rops.resize(64);
     bufs.push_back(b);
     return (int)bufs.size() - 1;
   }
@@ -79,6 +86,8 @@ struct Tracker {
     int ns = std::max(1, (rows + b.seg - 1) / b.seg);
     b.lw.assign(ns, -1);
     b.lr.assign(ns, -1);
+    b.wop.assign(ns, -1);
+    b.rops.resize(ns);
     bufs.push_back(b);
     return (int)bufs.size() - 1;
   }
@@ -91,9 +100,11 @@ struct Acc {
 
 class Emitter {
  public:
-  Emitter(std::vector<Wave>& w, Arena& a, int seg) : waves(w), A(a), seg_default(seg) {}
+  Emitter(std::vector<Wave>& w, OpGraph& g, Arena& a, int seg) : waves(w), graph(g), A(a), seg_default(seg) {}
 
   std::vector<Wave>& waves;
+  OpGraph& graph;
+  int cur_id = -1;  // op id assigned by the last place()
   Arena& A;
   Tracker T;
   int seg_default;
@@ -183,8 +194,10 @@ class Emitter {
     }
   }
 
+  // Wave and producers of a new op from its accesses; records the op.
   int place(std::initializer_list<Acc> acc) {
     int w = -1;
+    std::vector<int> deps;
     for (const Acc& a : acc) {
       const View& v = *a.v;
       Tracker::Buf& B = T.bufs[v.buf];
@@ -192,22 +205,36 @@ class Emitter {
       seg_range(B, v, s0, s1);
       for (int s = s0; s <= s1; ++s) {
         w = std::max(w, B.lw[s]);
-        if (a.write) w = std::max(w, B.lr[s]);
+        if (B.wop[s] >= 0) deps.push_back(B.wop[s]);
+        if (a.write) {
+          w = std::max(w, B.lr[s]);
+          deps.insert(deps.end(), B.rops[s].begin(), B.rops[s].end());
+        }
       }
     }
     ++w;
+    std::sort(deps.begin(), deps.end());
+    deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+    const int id = graph.add_op(std::move(deps));
     for (const Acc& a : acc) {
       const View& v = *a.v;
       Tracker::Buf& B = T.bufs[v.buf];
       int s0, s1;
       seg_range(B, v, s0, s1);
       for (int s = s0; s <= s1; ++s) {
-        if (a.write) B.lw[s] = w;
-        else B.lr[s] = std::max(B.lr[s], w);
+        if (a.write) {
+          B.lw[s] = w;
+          B.wop[s] = id;
+          B.rops[s].clear();
+        } else {
+          B.lr[s] = std::max(B.lr[s], w);
+          B.rops[s].push_back(id);
+        }
       }
     }
     if ((int)waves.size() <= w) waves.resize(w + 1);
     ++nops;
+    cur_id = id;
     return w;
   }
 
@@ -225,7 +252,7 @@ class Emitter {
     o.nparts = nparts;
     o.alpha = alpha;
     o.beta = beta;
-    waves[w].reduce.push_back(o);
+    waves[w].add(o, cur_id);
   }
 
   // C = beta C + alpha A B; a long inner dimension with few output tiles is
@@ -240,8 +267,13 @@ class Emitter {
     }
     const int K = Am.cols;
     const int tiles = gemm_tiles(C.rows, C.cols);
-    if (K > 512 && tiles < 64) {
-      const int KS = 256;
+    // a 32x32 tile costs 32*32*k FP64 FMAs on one SM (about 0.25 us per unit of
+    // k): long inner dimensions with few tiles are split so that the work
+    // reaches more SMs
+    int KS = 0;
+    if (K > 512 && tiles < 64) KS = 256;
+    else if (K >= 128 && tiles < 76) KS = 64;
+    if (KS) {
       const int ns = (K + KS - 1) / KS;
       View parts = tmp(ns * C.rows, C.cols, false);
       for (int c = 0; c < ns; ++c) {
@@ -274,7 +306,7 @@ class Emitter {
     o.ccs = C.cs;
     o.alpha = alpha;
     o.beta = beta;
-    waves[w].gemm.push_back(o);
+    waves[w].add(o, cur_id);
   }
 
   // dst = beta dst + alpha src (src null: constant alpha)
@@ -297,7 +329,7 @@ class Emitter {
     o.dcs = dst.cs;
     o.alpha = alpha;
     o.beta = beta;
-    waves[w].copy.push_back(o);
+    waves[w].add(o, cur_id);
   }
 
   void lu(const View& Am, const View& Li, const View& Ui) {
@@ -310,7 +342,7 @@ class Emitter {
     o.ldl = Li.rs;
     o.ldu = Ui.rs;
     o.m = Am.rows;
-    waves[w].lu.push_back(o);
+    waves[w].add(o, cur_id);
   }
 
   // Gram matrix G = X' X (K x K row-major, fresh), split over 256-row chunks.
@@ -346,7 +378,7 @@ class Emitter {
     o.K = K;
     o.kf = kf;
     o.tol = tol;
-    waves[w].trunc.push_back(o);
+    waves[w].add(o, cur_id);
   }
 };
 
@@ -692,7 +724,7 @@ class HLU {
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out) {
-  Emitter E(out.waves, arena, std::max(1, std::min(P.leaf, 256)));
+  Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
   HLU H(P, E, kf, lu_tol);
   const int nd = (int)dd.size(), nl = (int)ld.size();
   H.dense.resize(nd);
@@ -815,13 +847,68 @@ namespace {
 struct Src {
   RowSrc s;
   int ready;
+  std::vector<int64_t> res;  // resources the source reads
 };
+
+// Producer tracking on named resources (vector segments, partial products).
+struct ResTracker {
+  struct Res {
+    int wop = -1;
+    std::vector<int> rops;
+  };
+  std::map<int64_t, Res> res;
+  OpGraph& graph;
+  std::vector<int> op_wave;
+  int bad = 0;
+  explicit ResTracker(OpGraph& g) : graph(g) {}
+  int add(int wave, const std::vector<int64_t>& reads, const std::vector<int64_t>& writes) {
+    std::vector<int> deps;
+    for (int64_t r : reads) {
+      auto it = res.find(r);
+      if (it != res.end() && it->second.wop >= 0) deps.push_back(it->second.wop);
+    }
+    for (int64_t r : writes) {
+      Res& R = res[r];
+      if (R.wop >= 0) deps.push_back(R.wop);
+      deps.insert(deps.end(), R.rops.begin(), R.rops.end());
+    }
+    std::sort(deps.begin(), deps.end());
+    deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+    for (int d : deps)
+      if (op_wave[d] >= wave) {
+        ++bad;  // producers must sit in earlier waves
+        if (getenv("HM_DEBUG_PLAN")) fprintf(stderr, "dep %d (wave %d) of new op in wave %d\n", d, op_wave[d], wave);
+      }
+    const int id = graph.add_op(deps);
+    op_wave.push_back(wave);
+    for (int64_t r : reads) res[r].rops.push_back(id);
+    for (int64_t r : writes) {
+      Res& R = res[r];
+      R.wop = id;
+      R.rops.clear();
+    }
+    return id;
+  }
+};
+
+// y / z / accumulator rows of a leaf are written chunk by chunk (one op per
+// chunk of rows); a reader of the leaf depends on every chunk.
+int64_t key_y(int sweep, int p, int c = 0) { return (int64_t(1 + sweep) << 40) | (int64_t(p) << 12) | c; }
+int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 40) | (int64_t(p) << 12) | c; }
+constexpr int CR_ROWS = 8, NC_ROWS = 32;
+std::vector<int64_t> chunk_keys(int64_t base, int nr, int chunk) {
+  std::vector<int64_t> k;
+  for (int c = 0; c * chunk < nr; ++c) k.push_back(base | c);
+  return k;
+}
+int64_t key_part(int sweep, int q, int seg) { return (int64_t(3 + sweep) << 40) | (int64_t(q) << 16) | seg; }
+int64_t key_w(int sweep, int q) { return (int64_t(5 + sweep) << 40) | q; }
 
 class SolvePlanner {
  public:
   SolvePlanner(const Plan& P_, const std::vector<DenseDesc>& dd_, const std::vector<LRDesc>& ld_,
-               const FactorLayout& F_, Arena& A_, std::vector<Wave>& W_, std::vector<RowSrc>& S_)
-      : P(P_), dd(dd_), ld(ld_), F(F_), A(A_), waves(W_), srcs(S_) {}
+               const FactorLayout& F_, Arena& A_, std::vector<Wave>& W_, std::vector<RowSrc>& S_, OpGraph& G_)
+      : P(P_), dd(dd_), ld(ld_), F(F_), A(A_), waves(W_), srcs(S_), RT(G_) {}
   const Plan& P;
   const std::vector<DenseDesc>& dd;
   const std::vector<LRDesc>& ld;
@@ -829,6 +916,7 @@ class SolvePlanner {
   Arena& A;
   std::vector<Wave>& waves;
   std::vector<RowSrc>& srcs;
+  ResTracker RT;
   int status = HM_OK;
 
   Wave& at(int ph) {
@@ -836,8 +924,12 @@ class SolvePlanner {
     return waves[ph];
   }
 
-  void emit_rows(int ph, double* out, const double* base, int r0, int nr, int chunk,
-                 const std::vector<RowSrc>& list) {
+  // one op per chunk of rows; chunk c writes resource wbase | c
+  void emit_rows(int ph, double* out, const double* base, int r0, int nr, int chunk, const std::vector<Src>& list,
+                 const std::vector<int64_t>& extra_reads, int64_t wbase) {
+    std::vector<int64_t> reads = extra_reads;
+    for (const Src& s : list) reads.insert(reads.end(), s.res.begin(), s.res.end());
+    if (list.size() > 256) status = HM_ERR_ARG;  // a row task stages at most 256 sources
     for (int c = 0; c < nr; c += chunk) {
       RowsOp o{};
       o.out = out;
@@ -845,31 +937,31 @@ class SolvePlanner {
       o.r0 = r0 + c;
       o.nr = std::min(chunk, nr - c);
       o.src_begin = (int)srcs.size();
-      for (RowSrc s : list) {
-        s.M = s.M + (int64_t)c * s.rs;
-        srcs.push_back(s);
+      for (const Src& s : list) {
+        RowSrc r = s.s;
+        r.M = r.M + (int64_t)c * r.rs;
+        srcs.push_back(r);
       }
       o.src_end = (int)srcs.size();
-      at(ph).rows.push_back(o);
+      int id = RT.add(ph, reads, {wbase | (int64_t)(c / chunk)});
+      at(ph).add(o, id);
     }
   }
 
   // one sweep; lower = forward with L, otherwise backward with U
-  void sweep(bool lower, const double* in, const std::vector<int>& in_ready, double* out, double* acc,
+  void sweep(int sw, bool lower, const double* in, const std::vector<int>& in_ready, double* out, double* acc,
              std::vector<int>& out_ready) {
     const int nl = (int)P.leaves.size();
     const int kf = F.kf;
     std::vector<int> leaf_of(P.N, 0);
     for (int i = 0; i < nl; ++i)
       for (int r = P.cl[P.leaves[i]].begin; r < P.cl[P.leaves[i]].end; ++r) leaf_of[r] = i;
-    // per LR block of this triangle: partial products, one per leaf of its column cluster
     std::vector<double*> part(ld.size(), nullptr), wfin(ld.size(), nullptr);
     std::vector<int> nparts(ld.size(), 0), w_ready(ld.size(), -1), seen(ld.size(), 0);
     std::vector<std::vector<int>> lr_by_rowleaf(nl), lr_by_colleaf(nl), dense_by_rowleaf(nl);
     for (size_t q = 0; q < ld.size(); ++q) {
       const bool isl = ld[q].r0 > ld[q].c0;
       if (isl != lower) continue;
-      nparts[q] = 0;
       for (int r = ld[q].c0; r < ld[q].c0 + ld[q].n; r = P.cl[P.leaves[leaf_of[r]]].end) {
         lr_by_colleaf[leaf_of[r]].push_back((int)q);
         ++nparts[q];
@@ -893,42 +985,60 @@ class SolvePlanner {
       const int dg = F.leaf_diag[p];
       std::vector<Src> list;
       {
-        RowSrc s{};
-        s.M = lower ? F.linv[dg] : F.uinv[dg];
-        s.rs = F.linv_ld[dg];
-        s.cs = 1;
-        s.x = in + rb;
-        s.ncols = nr;
-        s.nparts = 0;
-        s.sign = 1.0;
-        list.push_back({s, in_ready[p]});
+        Src s{};
+        s.s.M = lower ? F.linv[dg] : F.uinv[dg];
+        s.s.rs = F.linv_ld[dg];
+        s.s.cs = 1;
+        s.s.x = in + rb;
+        s.s.ncols = nr;
+        s.s.nparts = 0;
+        s.s.sign = 1.0;
+        s.ready = in_ready[p];
+        if (sw == 1) s.res = chunk_keys(key_y(0, p), nr, CR_ROWS);
+        list.push_back(s);
       }
       for (int d : dense_by_rowleaf[p]) {
-        RowSrc s{};
-        s.M = F.pdense[d];
-        s.rs = dd[d].n;
-        s.cs = 1;
-        s.x = out + dd[d].c0;
-        s.ncols = dd[d].n;
-        s.sign = -1.0;
-        list.push_back({s, out_ready[leaf_of[dd[d].c0]]});
+        Src s{};
+        s.s.M = F.pdense[d];
+        s.s.rs = dd[d].n;
+        s.s.cs = 1;
+        s.s.x = out + dd[d].c0;
+        s.s.ncols = dd[d].n;
+        s.s.sign = -1.0;
+        s.ready = out_ready[leaf_of[dd[d].c0]];
+        s.res = chunk_keys(key_y(sw, leaf_of[dd[d].c0]), dd[d].n, CR_ROWS);
+        list.push_back(s);
       }
       for (int q : lr_by_rowleaf[p]) {
-        RowSrc s{};
-        s.M = F.plr[q] + (rb - ld[q].r0);
-        s.rs = 1;
-        s.cs = ld[q].m;
-        s.x = wfin[q];
-        s.ncols = kf;
-        s.nparts = 1;
-        s.sign = -1.0;
-        list.push_back({s, w_ready[q]});
+        Src s{};
+        s.s.M = F.plr[q] + (rb - ld[q].r0);
+        s.s.rs = 1;
+        s.s.cs = ld[q].m;
+        s.s.x = wfin[q];
+        s.s.ncols = kf;
+        s.s.nparts = 1;
+        s.s.sign = -1.0;
+        s.ready = w_ready[q];
+        s.res.push_back(key_w(sw, q));
+        list.push_back(s);
       }
-      int ph = 0;
-      for (const Src& s : list) ph = std::max(ph, s.ready + 1);
-      std::vector<RowSrc> all;
-      for (const Src& s : list) all.push_back(s.s);
-      emit_rows(ph, out, nullptr, rb, nr, 8, all);
+      // sources ready early are summed by a non-critical task placed as soon
+      // as they are ready; the critical task adds the late ones
+      int latest = -1;
+      for (const Src& s : list) latest = std::max(latest, s.ready);
+      std::vector<Src> nc, cr;
+      for (const Src& s : list) (s.ready < latest - 1 ? nc : cr).push_back(s);
+      int ph;
+      if (!nc.empty()) {
+        int phn = 0;
+        for (const Src& s : nc) phn = std::max(phn, s.ready + 1);
+        emit_rows(phn, acc, nullptr, rb, nr, NC_ROWS, nc, {}, key_acc(sw, p));
+        ph = std::max(phn, latest) + 1;
+        emit_rows(ph, out, acc, rb, nr, CR_ROWS, cr, chunk_keys(key_acc(sw, p), nr, NC_ROWS), key_y(sw, p));
+      } else {
+        ph = latest + 1;
+        emit_rows(ph, out, nullptr, rb, nr, CR_ROWS, cr, {}, key_y(sw, p));
+      }
       out_ready[p] = ph;
       // partial products V_q' y for the blocks whose column cluster holds this
       // leaf; after the last one, one task sums them into w_q
@@ -942,7 +1052,9 @@ class SolvePlanner {
         v.len = nr;
         v.kf = kf;
         v.part = part[q] + (int64_t)seg * kf;
-        at(ph + 1).vpart.push_back(v);
+        const int64_t pk = nparts[q] > 1 ? key_part(sw, q, seg) : key_w(sw, q);
+        int id = RT.add(ph + 1, chunk_keys(key_y(sw, p), nr, CR_ROWS), {pk});
+        at(ph + 1).add(v, id);
         w_ready[q] = std::max(w_ready[q], ph + 1);
         if (++seen[q] == nparts[q] && nparts[q] > 1) {
           ReduceOp o{};
@@ -956,7 +1068,10 @@ class SolvePlanner {
           o.nparts = nparts[q];
           o.alpha = 1.0;
           o.beta = 0.0;
-          at(w_ready[q] + 1).reduce.push_back(o);
+          std::vector<int64_t> rd;
+          for (int sg = 0; sg < nparts[q]; ++sg) rd.push_back(key_part(sw, q, sg));
+          int rid = RT.add(w_ready[q] + 1, rd, {key_w(sw, q)});
+          at(w_ready[q] + 1).add(o, rid);
           w_ready[q] += 1;
         }
       }
@@ -968,12 +1083,13 @@ class SolvePlanner {
 
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
                const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
-               std::vector<RowSrc>& srcs) {
-  SolvePlanner S(P, dd, ld, F, arena, waves, srcs);
+               std::vector<RowSrc>& srcs, OpGraph& graph) {
+  SolvePlanner S(P, dd, ld, F, arena, waves, srcs, graph);
   const int nl = (int)P.leaves.size();
   std::vector<int> b_ready(nl, -1), y_ready, z_ready;
-  S.sweep(true, v.b, b_ready, v.y, v.acc1, y_ready);
-  S.sweep(false, v.y, y_ready, v.z, v.acc2, z_ready);
+  S.sweep(0, true, v.b, b_ready, v.y, v.acc1, y_ready);
+  S.sweep(1, false, v.y, y_ready, v.z, v.acc2, z_ready);
+  if (S.RT.bad) return HM_ERR_ARG;
   if (S.status != HM_OK || arena.status != HM_OK) return S.status != HM_OK ? S.status : arena.status;
   return HM_OK;
 }

@@ -80,6 +80,7 @@ struct FactorLayout {
 
 struct HluBuild {
   std::vector<Wave> waves;
+  OpGraph graph;
   FactorLayout F;
   int64_t ops = 0;
   std::string err;
@@ -104,6 +105,6 @@ struct SolveVectors {
 };
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
                const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
-               std::vector<RowSrc>& srcs);
+               std::vector<RowSrc>& srcs, OpGraph& graph);
 
 }  // namespace hm
