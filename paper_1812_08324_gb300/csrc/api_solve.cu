@@ -65,8 +65,9 @@ int vgrid(int N) { return std::min((N + 255) / 256, 152 * 8); }
 void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevSchedule& S, int* d_err,
                     cudaStream_t st) {
   unsigned long long* d_tr = nullptr;
-  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * std::max(S.nops, 1)) != cudaSuccess) return;
-  cudaMemsetAsync(d_tr, 0, sizeof(unsigned long long) * std::max(S.nops, 1), st);
+  const size_t ntr = 3 * (size_t)std::max(S.nops, 1);
+  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * ntr) != cudaSuccess) return;
+  cudaMemsetAsync(d_tr, 0, sizeof(unsigned long long) * ntr, st);
   cudaStreamSynchronize(st);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -77,9 +78,29 @@ void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevS
   cudaStreamSynchronize(st);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  std::vector<unsigned long long> tr(std::max(S.nops, 1));
-  cudaMemcpy(tr.data(), d_tr, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> trall(ntr);
+  cudaMemcpy(trall.data(), d_tr, sizeof(unsigned long long) * ntr, cudaMemcpyDeviceToHost);
   cudaFree(d_tr);
+  std::vector<unsigned long long> tr(trall.begin(), trall.begin() + std::max(S.nops, 1));
+  if (const char* fn = std::getenv("HM_TRACE_FILE")) {
+    // one line per op: id wave kind rows finish ready grabbed (ns)
+    std::string path = std::string(fn) + "." + what + ".txt";
+    FILE* f = fopen(path.c_str(), "a");
+    if (f) {
+      const int nops = std::max(S.nops, 1);
+      for (size_t w = 0; w < waves.size(); ++w) {
+        const Wave& W = waves[w];
+        const std::vector<int>* ids[7] = {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id, &W.rows_id, &W.vpart_id};
+        for (int k = 0; k < 7; ++k)
+          for (size_t j = 0; j < ids[k]->size(); ++j) {
+            int id = (*ids[k])[j];
+            int nr = k == 5 ? W.rows[j].nr : 0;
+            fprintf(f, "%d %zu %d %d %llu %llu %llu\n", id, w, k, nr, trall[id], trall[nops + id], trall[2 * nops + id]);
+          }
+      }
+      fclose(f);
+    }
+  }
   unsigned long long t0 = ~0ull, t1 = 0;
   for (auto t : tr)
     if (t) { t0 = std::min(t0, t); t1 = std::max(t1, t); }

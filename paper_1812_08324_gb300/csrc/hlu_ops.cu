@@ -459,8 +459,8 @@ __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double
     int used = 0;
     for (int s = 0; s < nsrc; ++s) {
       const RowSrc& S = L.srcs[s];
-      const int need = op.nr * S.ncols;
-      if (!S.nparts && used + need <= ROWS_PREFETCH_DOUBLES) {
+      const int need = op.nr * S.ncols;  // dense rows, or low-rank U rows (nr x kf)
+      if (used + need <= ROWS_PREFETCH_DOUBLES) {
         L.pre_off[s] = used;
         used += need;
       } else {
@@ -495,12 +495,18 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
         if (S.nparts) continue;
         double a = 0.0;
         const int off = L.pre_off[s];
-        if (off >= 0) {
-          const double* Mr = L.pre + off + r * S.ncols;
-          for (int c = lane; c < S.ncols; c += 32) a += Mr[c] * S.x[c];
-        } else {
-          const double* Mr = S.M + r * S.rs;
-          for (int c = lane; c < S.ncols; c += 32) a += Mr[c * S.cs] * S.x[c];
+        // eight loads per lane issued before any use (latency, not bandwidth, bounds these)
+        for (int c0 = lane; c0 < S.ncols; c0 += 256) {
+          double xv[8], mv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = c0 + 32 * u;
+            const bool in = c < S.ncols;
+            xv[u] = in ? S.x[c] : 0.0;
+            mv[u] = in ? (off >= 0 ? L.pre[off + r * S.ncols + c] : S.M[r * S.rs + c * S.cs]) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a += mv[u] * xv[u];
         }
         acc += S.sign * a;
       }
@@ -527,10 +533,16 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
     }
     __syncwarp();
     if (lane < nr) {
-      const double* Mr = S.M + lane * S.rs;
+      const int off = L.pre_off[s];
       double a = 0.0;
-#pragma unroll 4
-      for (int l = 0; l < S.ncols; ++l) a += Mr[l * S.cs] * w[l];
+      if (off >= 0) {
+        const double* Mr = L.pre + off + lane * S.ncols;
+        for (int l = 0; l < S.ncols; ++l) a += Mr[l] * w[l];
+      } else {
+        const double* Mr = S.M + lane * S.rs;
+#pragma unroll 8
+        for (int l = 0; l < S.ncols; ++l) a += Mr[l * S.cs] * w[l];
+      }
       la += S.sign * a;
     }
     __syncwarp();
@@ -552,7 +564,17 @@ __device__ void dev_vpart(const VPartOp& op) {
   for (int l = warp; l < op.kf; l += 8) {
     const double* Vl = op.V + l * op.ldv;
     double a = 0.0;
-    for (int r = lane; r < op.len; r += 32) a += Vl[r] * op.y[r];
+    for (int r0 = lane; r0 < op.len; r0 += 256) {
+      double vv[8], yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = r0 + 32 * u;
+        vv[u] = r < op.len ? Vl[r] : 0.0;
+        yv[u] = r < op.len ? op.y[r] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a += vv[u] * yv[u];
+    }
     a = warp_sum(a);
     if (lane == 0) op.part[l] = a;
   }
@@ -579,8 +601,9 @@ struct ExecArgs {
   int* counters;
   int* grab;        // next task to hand out
   int ntasks;
+  int nops;
   int* err;
-  unsigned long long* trace;  // optional: finish time of every op (ns), first task to finish last
+  unsigned long long* trace;  // optional, 3 x nops: finish, producers-ready, grabbed times (ns)
 };
 
 // Wait until every producer of op `id` has finished all its tasks.  Warp 0
@@ -626,8 +649,10 @@ __global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
     __syncthreads();
     if (t >= a.ntasks) return;
     const Task T = a.tasks[t];
+    if (a.trace && threadIdx.x == 0) a.trace[2 * a.nops + T.id] = global_ns();
     if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem);
     if (!wait_deps(a, T.id)) return;
+    if (a.trace && threadIdx.x == 0) a.trace[a.nops + T.id] = global_ns();
     switch (T.kind) {
       case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
       case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
@@ -764,7 +789,7 @@ int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned lon
   // counters[nops] is the task dispenser
   if (cudaMemsetAsync(S.counters, 0, sizeof(int) * (S.nops + 1), st) != cudaSuccess) return HM_ERR_CUDA;
   ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.wave_begin,
-             S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, d_err, trace};
+             S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, S.nops, d_err, trace};
   void* args[] = {&a};
   count_launches(1);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)exec_kernel, dim3(grid), dim3(EXEC_THREADS), args,
