@@ -406,6 +406,21 @@ __device__ void dev_copy(const CopyOp& op, int chunk, int nchunks) {
 
 __device__ void dev_reduce(const ReduceOp& op, int chunk, int nchunks) {
   const int64_t count = (int64_t)op.m * op.n;
+  if (count <= 64 && op.nparts > 8) {
+    // few outputs, many parts: a warp per output, lanes over the parts
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t e = chunk * 8 + warp; e < count; e += (int64_t)nchunks * 8) {
+      double s = 0.0;
+      for (int p = lane; p < op.nparts; p += 32) s += op.parts[p * op.stride + e];
+      s = warp_sum(s);
+      if (lane == 0) {
+        const int i = (int)(e / op.n), j = (int)(e % op.n);
+        double* d = op.dst + i * op.drs + j * op.dcs;
+        *d = op.beta == 0.0 ? op.alpha * s : op.beta * (*d) + op.alpha * s;
+      }
+    }
+    return;
+  }
   for (int64_t e = chunk * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)nchunks * blockDim.x) {
     double s = 0.0;
     for (int p = 0; p < op.nparts; ++p) s += op.parts[p * op.stride + e];
@@ -421,15 +436,21 @@ __device__ void dev_reduce(const ReduceOp& op, int chunk, int nchunks) {
 // row, after summing the source's partial products.  Per-row totals are
 // combined in a fixed order, so results are bitwise reproducible.
 // Shared-memory layout of a row task: accumulators, per-warp coefficient
-// vectors, staged descriptors, then prefetched rows of dense sources.
+// vectors, staged descriptors, prefetched static rows, gathered dynamic inputs.
 constexpr int ROWS_PREFETCH_DOUBLES = 8192;  // 64 KB of prefetched matrix rows
+constexpr int ROWS_DYN_DOUBLES = 10240;      // 80 KB of gathered inputs (x, partials, base)
+constexpr int ROWS_MAX_SRC = 256;
 struct RowsSmem {
   double* acc_d;    // 32
   double* acc_l;    // 8 x 32
   double* wsum;     // 8 x 64
-  RowSrc* srcs;     // up to 256 descriptors
+  RowSrc* srcs;     // up to ROWS_MAX_SRC descriptors
   double* pre;      // prefetched rows
-  int* pre_off;     // per source: offset into pre (-1: not prefetched), up to 256
+  double* dyn;      // gathered dynamic inputs
+  int* pre_off;     // per source: offset into pre (-1: not prefetched)
+  int* dyn_off;     // per source: offset into dyn (-1: read from global); [nsrc] = base
+  int* dstart;      // per source: start of its gathered range (non-decreasing)
+  int* dyn_total;   // [0] = total gathered doubles
 };
 
 __device__ __forceinline__ RowsSmem rows_smem(double* smem) {
@@ -438,16 +459,20 @@ __device__ __forceinline__ RowsSmem rows_smem(double* smem) {
   L.acc_l = smem + 32;
   L.wsum = smem + 32 + 256;
   L.srcs = reinterpret_cast<RowSrc*>(smem + 32 + 256 + 512);
-  L.pre = smem + 32 + 256 + 512 + 256 * (sizeof(RowSrc) / sizeof(double));
-  L.pre_off = reinterpret_cast<int*>(L.pre + ROWS_PREFETCH_DOUBLES);
+  L.pre = smem + 32 + 256 + 512 + ROWS_MAX_SRC * (sizeof(RowSrc) / sizeof(double));
+  L.dyn = L.pre + ROWS_PREFETCH_DOUBLES;
+  L.pre_off = reinterpret_cast<int*>(L.dyn + ROWS_DYN_DOUBLES);
+  L.dyn_off = L.pre_off + ROWS_MAX_SRC;
+  L.dstart = L.dyn_off + ROWS_MAX_SRC + 1;
+  L.dyn_total = L.dstart + ROWS_MAX_SRC + 1;
   return L;
 }
 
-// Stage the descriptors and copy the rows of dense sources (static data) into
-// shared memory; runs before the task waits on its producers.
+// Before the wait: stage descriptors, copy static rows into shared memory and
+// lay out the space for the dynamic inputs.
 __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double* smem) {
   RowsSmem L = rows_smem(smem);
-  const int nsrc = min(op.src_end - op.src_begin, 256);
+  const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   {
     const int words = nsrc * (int)(sizeof(RowSrc) / sizeof(long long));
     const long long* g = reinterpret_cast<const long long*>(srcs_g + op.src_begin);
@@ -456,35 +481,85 @@ __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int used = 0;
+    int used = 0, dused = 0;
     for (int s = 0; s < nsrc; ++s) {
       const RowSrc& S = L.srcs[s];
-      const int need = op.nr * S.ncols;  // dense rows, or low-rank U rows (nr x kf)
+      // dense rows, or low-rank U rows (nr x kf, padded to kf + 1 against bank conflicts)
+      const int need = op.nr * (S.nparts ? S.ncols + 1 : S.ncols);
       if (used + need <= ROWS_PREFETCH_DOUBLES) {
         L.pre_off[s] = used;
         used += need;
       } else {
         L.pre_off[s] = -1;
       }
+      const int dneed = S.nparts ? S.nparts * S.ncols : S.ncols;
+      L.dstart[s] = dused;
+      if (dused + dneed <= ROWS_DYN_DOUBLES - 32) {
+        L.dyn_off[s] = dused;
+        dused += dneed;
+      } else {
+        L.dyn_off[s] = -1;
+      }
     }
+    L.dyn_off[nsrc] = dused;  // base rows
+    L.dyn_total[0] = dused + (op.base ? op.nr : 0);
   }
   __syncthreads();
   for (int s = 0; s < nsrc; ++s) {
     const int off = L.pre_off[s];
     if (off < 0) continue;
     const RowSrc& S = L.srcs[s];
-    const int nc = S.ncols, tot = op.nr * nc;
+    const int nc = S.ncols, tot = op.nr * nc, ld = S.nparts ? nc + 1 : nc;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int r = e / nc, c = e % nc;
-      L.pre[off + e] = S.M[r * S.rs + c * S.cs];
+      L.pre[off + r * ld + c] = S.M[r * S.rs + c * S.cs];
     }
+  }
+  __syncthreads();
+}
+
+// After the wait: gather every dynamic input (x vectors, partial products,
+// base rows) with eight independent loads in flight per thread.
+__device__ void dev_rows_gather(const RowsOp& op, double* smem) {
+  RowsSmem L = rows_smem(smem);
+  const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
+  const int total = L.dyn_total[0];
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+    double v[8];
+    int dst[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      dst[u] = -1;
+      v[u] = 0.0;
+      if (e < total) {
+        if (e >= L.dyn_off[nsrc]) {
+          v[u] = op.base[op.r0 + (e - L.dyn_off[nsrc])];
+          dst[u] = e;
+        } else {
+          // source owning element e: the last s with dstart[s] <= e (sources
+          // that gather nothing share their start with the next one)
+          int lo = 0, hi = nsrc - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.dstart[mid] <= e) lo = mid; else hi = mid - 1;
+          }
+          v[u] = L.srcs[lo].x[e - L.dstart[lo]];
+          dst[u] = e;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (dst[u] >= 0) L.dyn[dst[u]] = v[u];
   }
   __syncthreads();
 }
 
 __device__ void dev_rows(const RowsOp& op, double* smem) {
   RowsSmem L = rows_smem(smem);
-  const int nsrc = min(op.src_end - op.src_begin, 256);
+  dev_rows_gather(op, smem);
+  const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nr = op.nr;
   for (int r = warp; r < 32; r += 8) {
@@ -494,15 +569,14 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
         const RowSrc& S = L.srcs[s];
         if (S.nparts) continue;
         double a = 0.0;
-        const int off = L.pre_off[s];
-        // eight loads per lane issued before any use (latency, not bandwidth, bounds these)
+        const int off = L.pre_off[s], xo = L.dyn_off[s];
         for (int c0 = lane; c0 < S.ncols; c0 += 256) {
           double xv[8], mv[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int c = c0 + 32 * u;
             const bool in = c < S.ncols;
-            xv[u] = in ? S.x[c] : 0.0;
+            xv[u] = in ? (xo >= 0 ? L.dyn[xo + c] : S.x[c]) : 0.0;
             mv[u] = in ? (off >= 0 ? L.pre[off + r * S.ncols + c] : S.M[r * S.rs + c * S.cs]) : 0.0;
           }
 #pragma unroll
@@ -521,14 +595,15 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
     if (!S.nparts) continue;
     if ((k++ & 7) != warp) continue;
     double* w = L.wsum + warp * 64;
+    const int xo = L.dyn_off[s];
     for (int l = lane; l < S.ncols; l += 32) {
-      // eight independent chains keep eight loads in flight
       double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int p = 0;
       for (; p + 8 <= S.nparts; p += 8)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] += S.x[(p + u) * S.ncols + l];
-      for (; p < S.nparts; ++p) v[0] += S.x[p * S.ncols + l];
+        for (int u = 0; u < 8; ++u)
+          v[u] += xo >= 0 ? L.dyn[xo + (p + u) * S.ncols + l] : S.x[(p + u) * S.ncols + l];
+      for (; p < S.nparts; ++p) v[0] += xo >= 0 ? L.dyn[xo + p * S.ncols + l] : S.x[p * S.ncols + l];
       w[l] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     }
     __syncwarp();
@@ -536,7 +611,7 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
       const int off = L.pre_off[s];
       double a = 0.0;
       if (off >= 0) {
-        const double* Mr = L.pre + off + lane * S.ncols;
+        const double* Mr = L.pre + off + lane * (S.ncols + 1);
         for (int l = 0; l < S.ncols; ++l) a += Mr[l] * w[l];
       } else {
         const double* Mr = S.M + lane * S.rs;
@@ -551,7 +626,7 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
   __syncthreads();
   if (threadIdx.x < nr) {
     const int r = threadIdx.x;
-    double v = op.base ? op.base[op.r0 + r] : 0.0;
+    double v = op.base ? L.dyn[L.dyn_off[nsrc] + r] : 0.0;
     v += L.acc_d[r];
     for (int w = 0; w < 8; ++w) v += L.acc_l[w * 32 + r];
     op.out[op.r0 + r] = v;
@@ -559,22 +634,39 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
   __syncthreads();
 }
 
-__device__ void dev_vpart(const VPartOp& op) {
+// V' y over one piece: V (static) is copied to shared memory before the
+// wait (when it fits), y is gathered after it.
+constexpr int VPART_SMEM = 16384;
+__device__ void dev_vpart_prefetch(const VPartOp& op, double* smem) {
+  if (op.len * op.kf > VPART_SMEM) return;
+  for (int e = threadIdx.x; e < op.len * op.kf; e += blockDim.x) {
+    const int l = e / op.len, r = e % op.len;
+    smem[e] = op.V[l * op.ldv + r];
+  }
+  __syncthreads();
+}
+
+__device__ void dev_vpart(const VPartOp& op, double* smem) {
+  const bool pre = op.len * op.kf <= VPART_SMEM;
+  double* ys = smem + VPART_SMEM;
+  for (int r0 = threadIdx.x; r0 < op.len; r0 += 8 * blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = r0 + u * blockDim.x;
+      v[u] = r < op.len ? op.y[r] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = r0 + u * blockDim.x;
+      if (r < op.len) ys[r] = v[u];
+    }
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = warp; l < op.kf; l += 8) {
-    const double* Vl = op.V + l * op.ldv;
     double a = 0.0;
-    for (int r0 = lane; r0 < op.len; r0 += 256) {
-      double vv[8], yv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int r = r0 + 32 * u;
-        vv[u] = r < op.len ? Vl[r] : 0.0;
-        yv[u] = r < op.len ? op.y[r] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a += vv[u] * yv[u];
-    }
+    for (int r = lane; r < op.len; r += 32) a += (pre ? smem[l * op.len + r] : op.V[l * op.ldv + r]) * ys[r];
     a = warp_sum(a);
     if (lane == 0) op.part[l] = a;
   }
@@ -606,6 +698,19 @@ struct ExecArgs {
   unsigned long long* trace;  // optional, 3 x nops: finish, producers-ready, grabbed times (ns)
 };
 
+// Acquire load / release add at GPU scope: the pattern of a CTA-wide barrier
+// followed by one thread's release publishes all of the CTA's prior writes; an
+// acquire load that observes it makes them visible to the reader's CTA after
+// its next barrier.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Wait until every producer of op `id` has finished all its tasks.  Warp 0
 // polls the counters (lanes split the producer list); bounded in time.
 __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
@@ -617,9 +722,9 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
     for (int k = op.dep_begin + (int)threadIdx.x; k < op.dep_end && good; k += 32) {
       const int d = a.deps[k];
       const int need = a.ops[d].ntasks;
-      volatile const int* c = a.counters + d;
+      const int* c = a.counters + d;
       unsigned polls = 0;
-      while (*c < need) {
+      while (ld_acquire(c) < need) {
         if ((++polls & 255u) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) {
           atomicOr(a.err, DEVERR_TIMEOUT);
           good = false;
@@ -628,10 +733,7 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
       }
     }
     good = __all_sync(0xffffffffu, good);
-    if (threadIdx.x == 0) {
-      ok = good ? 1 : 0;
-      __threadfence();  // acquire: the producers' writes are visible after this
-    }
+    if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
   return ok != 0;
@@ -651,6 +753,7 @@ __global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
     const Task T = a.tasks[t];
     if (a.trace && threadIdx.x == 0) a.trace[2 * a.nops + T.id] = global_ns();
     if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem);
+    if (T.kind == TK_VPART) dev_vpart_prefetch(a.vpart[T.op], smem);
     if (!wait_deps(a, T.id)) return;
     if (a.trace && threadIdx.x == 0) a.trace[a.nops + T.id] = global_ns();
     switch (T.kind) {
@@ -660,13 +763,12 @@ __global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
       case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
       case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
       case TK_ROWS: dev_rows(a.rows[T.op], smem); break;
-      case TK_VPART: dev_vpart(a.vpart[T.op]); break;
+      case TK_VPART: dev_vpart(a.vpart[T.op], smem); break;
       default: break;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();  // release: this task's writes before its completion count
-      atomicAdd(a.counters + T.id, 1);
+      red_release_add(a.counters + T.id, 1);  // publishes the CTA's writes (after the barrier)
       if (a.trace) a.trace[T.id] = global_ns();
     }
   }

@@ -768,38 +768,80 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     }
   }
   H.hlu(0);
-  // leaf-inverse scaling of the off-diagonal factor blocks for the solves
+  // Solve blocks and their exact diagonal inverses, then the scaled couplings.
   FactorLayout& FL = out.F;
-  std::vector<int> diag_of_cluster(P.cl.size(), -1);
-  for (int d = 0; d < nd; ++d)
-    if (dd[d].r0 == dd[d].c0) diag_of_cluster[P.bl[P.dense_block[d]].t] = d;
-  FL.leaf_diag.resize(P.leaves.size());
-  for (size_t i = 0; i < P.leaves.size(); ++i) FL.leaf_diag[i] = diag_of_cluster[P.leaves[i]];
-  FL.pdense.assign(nd, nullptr);
+  {
+    std::vector<int> stack = {0};
+    while (!stack.empty()) {
+      int c = stack.back();
+      stack.pop_back();
+      const Cluster& C = P.cl[c];
+      if (C.end - C.begin <= SOLVE_BLOCK || C.nchild == 0) {
+        FL.sb_cluster.push_back(c);
+      } else {
+        for (int k = C.nchild - 1; k >= 0; --k) stack.push_back(C.child[k]);
+      }
+    }
+    std::sort(FL.sb_cluster.begin(), FL.sb_cluster.end(),
+              [&](int x, int y) { return P.cl[x].begin < P.cl[y].begin; });
+  }
+  std::vector<int> diag_block(P.cl.size(), -1);
+  for (int bi = 0; bi < (int)P.bl.size(); ++bi)
+    if (P.bl[bi].t == P.bl[bi].s) diag_block[P.bl[bi].t] = bi;
+  const int nsb = (int)FL.sb_cluster.size();
+  std::vector<View> sbL(nsb), sbU(nsb);
+  for (int k = 0; k < nsb; ++k) {
+    const Cluster& C = P.cl[FL.sb_cluster[k]];
+    const int S = C.end - C.begin;
+    const int db = diag_block[FL.sb_cluster[k]];
+    View Li = E.new_mat(S, S, false), UiT = E.new_mat(S, S, false), Ui = E.new_mat(S, S, false);
+    for (View* X : {&Li, &UiT}) {
+      E.copy(*X, 0.0, nullptr, 0.0);
+      View dg = *X;
+      dg.cols = 1;
+      dg.rs = X->rs + 1;
+      dg.cs = 0;
+      E.copy(dg, 1.0, nullptr, 1.0);
+    }
+    H.lsolve_mat(db, Li);      // L_BB^{-1}
+    H.usolve_t_mat(db, UiT);   // U_BB^{-T}
+    View UiTt = UiT.T();
+    E.copy(Ui, 1.0, &UiTt, 0.0);
+    sbL[k] = Li;
+    sbU[k] = Ui;
+    FL.sb_linv.push_back(Li.p);
+    FL.sb_uinv.push_back(Ui.p);
+  }
+  std::vector<int> sb_of_row(P.N, 0);
+  for (int k = 0; k < nsb; ++k)
+    for (int r = P.cl[FL.sb_cluster[k]].begin; r < P.cl[FL.sb_cluster[k]].end; ++r) sb_of_row[r] = k;
+  auto couple = [&](int tcl, int scl, bool lowrank, int id, bool lower, const View& rowsrc) {
+    // rowsrc: the block's rows (dense m x n, or U m x kf); scale each part in a solve block
+    const Cluster& T = P.cl[tcl];
+    const Cluster& Sc = P.cl[scl];
+    for (int r = T.begin; r < T.end;) {
+      const int k = sb_of_row[r];
+      const Cluster& C = P.cl[FL.sb_cluster[k]];
+      const int e = std::min(T.end, C.end);
+      const bool internal = Sc.begin >= C.begin && Sc.end <= C.end && T.begin >= C.begin && T.end <= C.end;
+      if (!internal) {
+        const int S = C.end - C.begin, len = e - r;
+        const View& inv = lower ? sbL[k] : sbU[k];
+        View o = E.new_mat(S, rowsrc.cols, false);
+        E.gemm(o, 1.0, inv.sub(0, r - C.begin, S, len), rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
+        FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols});
+      }
+      r = e;
+    }
+  };
   for (int d = 0; d < nd; ++d) {
     if (dd[d].r0 == dd[d].c0) continue;
-    const int dt = diag_of_cluster[P.bl[P.dense_block[d]].t];
-    const View& inv = dd[d].r0 > dd[d].c0 ? H.linv[dt] : H.uinv[dt];
-    View o = E.new_mat(dd[d].m, dd[d].n, false);
-    E.gemm(o, 1.0, inv, H.dense[d], 0.0);
-    FL.pdense[d] = o.p;
+    const Block& Bk = P.bl[P.dense_block[d]];
+    couple(Bk.t, Bk.s, false, d, dd[d].r0 > dd[d].c0, H.dense[d]);
   }
-  FL.plr.assign(nl, nullptr);
   for (int q = 0; q < nl; ++q) {
-    const LRDesc& L = ld[q];
-    const bool lower = L.r0 > L.c0;
-    View U = H.lrU(q);
-    View o = E.new_mat(L.m, kf, true);
-    const Cluster& T = P.cl[P.bl[P.lr_block[q]].t];
-    for (int leaf : P.leaves) {
-      const Cluster& c = P.cl[leaf];
-      if (c.begin < T.begin || c.end > T.end) continue;
-      const int dt = diag_of_cluster[leaf];
-      const View& inv = lower ? H.linv[dt] : H.uinv[dt];
-      int r = c.begin - T.begin, sz = c.end - c.begin;
-      E.gemm(o.sub(r, 0, sz, kf), 1.0, inv, U.sub(r, 0, sz, kf), 0.0);
-    }
-    FL.plr[q] = o.p;
+    const Block& Bk = P.bl[P.lr_block[q]];
+    couple(Bk.t, Bk.s, true, q, ld[q].r0 > ld[q].c0, H.lrU(q));
   }
   if (E.status != HM_OK || arena.status != HM_OK) {
     out.err = "H-LU planning failed (device memory or shape)";
@@ -894,7 +936,7 @@ struct ResTracker {
 // y / z / accumulator rows of a leaf are written chunk by chunk (one op per
 // chunk of rows); a reader of the leaf depends on every chunk.
 int64_t key_y(int sweep, int p, int c = 0) { return (int64_t(1 + sweep) << 40) | (int64_t(p) << 12) | c; }
-int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 40) | (int64_t(p) << 12) | c; }
+int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 44) | (int64_t(p) << 12) | c; }
 constexpr int CR_ROWS = 8, NC_ROWS = 32;
 std::vector<int64_t> chunk_keys(int64_t base, int nr, int chunk) {
   std::vector<int64_t> k;
@@ -929,7 +971,7 @@ class SolvePlanner {
                  const std::vector<int64_t>& extra_reads, int64_t wbase) {
     std::vector<int64_t> reads = extra_reads;
     for (const Src& s : list) reads.insert(reads.end(), s.res.begin(), s.res.end());
-    if (list.size() > 256) status = HM_ERR_ARG;  // a row task stages at most 256 sources
+    if (list.size() > 256) status = HM_ERR_ARG;  // a row task stages at most 256 sources (ROWS_MAX_SRC)
     for (int c = 0; c < nr; c += chunk) {
       RowsOp o{};
       o.out = out;
@@ -948,78 +990,88 @@ class SolvePlanner {
     }
   }
 
-  // one sweep; lower = forward with L, otherwise backward with U
+  // One sweep over the solve blocks; lower = forward with L, otherwise
+  // backward with U.  Block k: out_k = Binv_k in_k - sum of scaled couplings.
   void sweep(int sw, bool lower, const double* in, const std::vector<int>& in_ready, double* out, double* acc,
              std::vector<int>& out_ready) {
-    const int nl = (int)P.leaves.size();
+    const int nb = (int)F.sb_cluster.size();
     const int kf = F.kf;
-    std::vector<int> leaf_of(P.N, 0);
-    for (int i = 0; i < nl; ++i)
-      for (int r = P.cl[P.leaves[i]].begin; r < P.cl[P.leaves[i]].end; ++r) leaf_of[r] = i;
+    std::vector<int> sb_of(P.N, 0);
+    for (int k = 0; k < nb; ++k)
+      for (int r = P.cl[F.sb_cluster[k]].begin; r < P.cl[F.sb_cluster[k]].end; ++r) sb_of[r] = k;
+    auto sbeg = [&](int k) { return P.cl[F.sb_cluster[k]].begin; };
+    auto send = [&](int k) { return P.cl[F.sb_cluster[k]].end; };
+    // low-rank blocks of this triangle: one partial V_q' y per piece of at most
+    // 256 columns inside one solve block; consumers sum the partials
+    constexpr int VP_ROWS = 256;
     std::vector<double*> part(ld.size(), nullptr), wfin(ld.size(), nullptr);
     std::vector<int> nparts(ld.size(), 0), w_ready(ld.size(), -1), seen(ld.size(), 0);
-    std::vector<std::vector<int>> lr_by_rowleaf(nl), lr_by_colleaf(nl), dense_by_rowleaf(nl);
+    std::vector<std::vector<std::pair<int, int>>> pieces(ld.size());  // (first col, length) per part
+    std::vector<std::vector<int>> lr_by_colsb(nb);
+    std::vector<bool> used(ld.size(), false);
+    for (const FactorLayout::Scaled& s : F.scaled)
+      if (s.lowrank && s.lower == lower) used[s.id] = true;
     for (size_t q = 0; q < ld.size(); ++q) {
-      const bool isl = ld[q].r0 > ld[q].c0;
-      if (isl != lower) continue;
-      for (int r = ld[q].c0; r < ld[q].c0 + ld[q].n; r = P.cl[P.leaves[leaf_of[r]]].end) {
-        lr_by_colleaf[leaf_of[r]].push_back((int)q);
-        ++nparts[q];
+      if (!used[q]) continue;
+      const int c0 = ld[q].c0, c1 = ld[q].c0 + ld[q].n;
+      for (int r = c0; r < c1;) {
+        const int k = sb_of[r], e = std::min(send(k), c1);
+        if (lr_by_colsb[k].empty() || lr_by_colsb[k].back() != (int)q) lr_by_colsb[k].push_back((int)q);
+        for (int a = r; a < e; a += VP_ROWS) pieces[q].push_back({a, std::min(VP_ROWS, e - a)});
+        r = e;
       }
-      for (int r = ld[q].r0; r < ld[q].r0 + ld[q].m; r = P.cl[P.leaves[leaf_of[r]]].end)
-        lr_by_rowleaf[leaf_of[r]].push_back((int)q);
+      nparts[q] = (int)pieces[q].size();
       part[q] = A.alloc((int64_t)nparts[q] * kf);
-      wfin[q] = nparts[q] > 1 ? A.alloc(kf) : part[q];
-      if (!part[q] || !wfin[q]) status = HM_ERR_OOM;
+      wfin[q] = nparts[q] > 4 ? A.alloc(kf) : nullptr;
+      if (!part[q] || (nparts[q] > 4 && !wfin[q])) status = HM_ERR_OOM;
     }
-    for (size_t d = 0; d < dd.size(); ++d) {
-      if (dd[d].r0 == dd[d].c0) continue;
-      if ((dd[d].r0 > dd[d].c0) != lower) continue;
-      dense_by_rowleaf[leaf_of[dd[d].r0]].push_back((int)d);
-    }
-    out_ready.assign(nl, -1);
-    for (int it = 0; it < nl; ++it) {
-      const int p = lower ? it : nl - 1 - it;
-      const Cluster& C = P.cl[P.leaves[p]];
-      const int rb = C.begin, nr = C.end - C.begin;
-      const int dg = F.leaf_diag[p];
+    std::vector<std::vector<const FactorLayout::Scaled*>> by_row(nb);
+    for (const FactorLayout::Scaled& s : F.scaled)
+      if (s.lower == lower) by_row[s.sb].push_back(&s);
+    out_ready.assign(nb, -1);
+    for (int it = 0; it < nb; ++it) {
+      const int k = lower ? it : nb - 1 - it;
+      const int rb = sbeg(k), nr = send(k) - rb;
       std::vector<Src> list;
       {
         Src s{};
-        s.s.M = lower ? F.linv[dg] : F.uinv[dg];
-        s.s.rs = F.linv_ld[dg];
+        s.s.M = lower ? F.sb_linv[k] : F.sb_uinv[k];
+        s.s.rs = nr;
         s.s.cs = 1;
         s.s.x = in + rb;
         s.s.ncols = nr;
         s.s.nparts = 0;
         s.s.sign = 1.0;
-        s.ready = in_ready[p];
-        if (sw == 1) s.res = chunk_keys(key_y(0, p), nr, CR_ROWS);
+        s.ready = in_ready[k];
+        if (sw == 1) s.res = chunk_keys(key_y(0, k), nr, CR_ROWS);
         list.push_back(s);
       }
-      for (int d : dense_by_rowleaf[p]) {
+      for (const FactorLayout::Scaled* e : by_row[k]) {
         Src s{};
-        s.s.M = F.pdense[d];
-        s.s.rs = dd[d].n;
+        s.s.M = e->M;
+        s.s.rs = e->ncols;
         s.s.cs = 1;
-        s.s.x = out + dd[d].c0;
-        s.s.ncols = dd[d].n;
+        s.s.ncols = e->ncols;
         s.s.sign = -1.0;
-        s.ready = out_ready[leaf_of[dd[d].c0]];
-        s.res = chunk_keys(key_y(sw, leaf_of[dd[d].c0]), dd[d].n, CR_ROWS);
-        list.push_back(s);
-      }
-      for (int q : lr_by_rowleaf[p]) {
-        Src s{};
-        s.s.M = F.plr[q] + (rb - ld[q].r0);
-        s.s.rs = 1;
-        s.s.cs = ld[q].m;
-        s.s.x = wfin[q];
-        s.s.ncols = kf;
-        s.s.nparts = 1;
-        s.s.sign = -1.0;
-        s.ready = w_ready[q];
-        s.res.push_back(key_w(sw, q));
+        if (e->lowrank) {
+          const int q = e->id;
+          if (wfin[q]) {  // summed once by a reduction task
+            s.s.x = wfin[q];
+            s.s.nparts = 1;
+            s.res.push_back(key_w(sw, q));
+          } else {        // few partials: summed by the consumer
+            s.s.x = part[q];
+            s.s.nparts = nparts[q];
+            for (int sg = 0; sg < nparts[q]; ++sg) s.res.push_back(key_part(sw, q, sg));
+          }
+          s.ready = w_ready[q];
+        } else {
+          const int c0 = dd[e->id].c0, j = sb_of[c0];
+          s.s.x = out + c0;
+          s.s.nparts = 0;
+          s.ready = out_ready[j];
+          s.res = chunk_keys(key_y(sw, j), send(j) - sbeg(j), CR_ROWS);
+        }
         list.push_back(s);
       }
       // sources ready early are summed by a non-critical task placed as soon
@@ -1030,49 +1082,77 @@ class SolvePlanner {
       for (const Src& s : list) (s.ready < latest - 1 ? nc : cr).push_back(s);
       int ph;
       if (!nc.empty()) {
+        // non-critical sources in groups of at most 96, chained through
+        // per-group accumulators (acc_g = acc_{g-1} + group g)
+        std::stable_sort(nc.begin(), nc.end(), [](const Src& x, const Src& y) { return x.ready < y.ready; });
+        // the first group is the block-inverse product alone when it is ready
+        // first, so every block's share of it runs in bulk at the start
+        std::vector<std::vector<Src>> groups;
+        size_t i0 = 0;
+        if (nc.size() > 1 && nc[0].ready < nc[1].ready) groups.push_back({nc[0]}), i0 = 1;
+        for (size_t g0 = i0; g0 < nc.size(); g0 += 96)
+          groups.emplace_back(nc.begin() + g0, nc.begin() + std::min(nc.size(), g0 + 96));
+        const double* prev = nullptr;
+        int64_t prev_key = -1;
         int phn = 0;
-        for (const Src& s : nc) phn = std::max(phn, s.ready + 1);
-        emit_rows(phn, acc, nullptr, rb, nr, NC_ROWS, nc, {}, key_acc(sw, p));
-        ph = std::max(phn, latest) + 1;
-        emit_rows(ph, out, acc, rb, nr, CR_ROWS, cr, chunk_keys(key_acc(sw, p), nr, NC_ROWS), key_y(sw, p));
+        // the chain reaches this block about two phases after the previous
+        // one: the early groups go just ahead of that, overlapping the chain
+        const int prev_ph = it > 0 ? out_ready[lower ? k - 1 : k + 1] : 0;
+        phn = std::max(0, prev_ph - 2);
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+          const size_t g0 = gi * 96;
+          const std::vector<Src>& grp = groups[gi];
+          for (const Src& s : grp) phn = std::max(phn, s.ready + 1);
+          double* accg = g0 == 0 ? acc : A.alloc(P.N) ;
+          if (!accg) { status = HM_ERR_OOM; return; }
+          const int64_t gk = key_acc(sw, k) + (int64_t(g0 / 96) << 32);
+          std::vector<int64_t> rd;
+          if (prev) rd = chunk_keys(prev_key, nr, NC_ROWS);
+          emit_rows(phn, accg, prev, rb, nr, NC_ROWS, grp, rd, gk);
+          prev = accg;
+          prev_key = gk;
+          ++phn;
+        }
+        ph = std::max(phn, latest + 1);
+        emit_rows(ph, out, prev, rb, nr, CR_ROWS, cr, chunk_keys(prev_key, nr, NC_ROWS), key_y(sw, k));
       } else {
         ph = latest + 1;
-        emit_rows(ph, out, nullptr, rb, nr, CR_ROWS, cr, {}, key_y(sw, p));
+        emit_rows(ph, out, nullptr, rb, nr, CR_ROWS, cr, {}, key_y(sw, k));
       }
-      out_ready[p] = ph;
-      // partial products V_q' y for the blocks whose column cluster holds this
-      // leaf; after the last one, one task sums them into w_q
-      for (int q : lr_by_colleaf[p]) {
-        int seg = 0;
-        for (int r = ld[q].c0; r < rb; r = P.cl[P.leaves[leaf_of[r]]].end) ++seg;
-        VPartOp v{};
-        v.V = F.lr_v[q] + (rb - ld[q].c0);
-        v.ldv = ld[q].n;
-        v.y = out + rb;
-        v.len = nr;
-        v.kf = kf;
-        v.part = part[q] + (int64_t)seg * kf;
-        const int64_t pk = nparts[q] > 1 ? key_part(sw, q, seg) : key_w(sw, q);
-        int id = RT.add(ph + 1, chunk_keys(key_y(sw, p), nr, CR_ROWS), {pk});
-        at(ph + 1).add(v, id);
-        w_ready[q] = std::max(w_ready[q], ph + 1);
-        if (++seen[q] == nparts[q] && nparts[q] > 1) {
-          ReduceOp o{};
-          o.parts = part[q];
-          o.dst = wfin[q];
-          o.stride = kf;
-          o.drs = 0;
-          o.dcs = 1;
-          o.m = 1;
-          o.n = kf;
-          o.nparts = nparts[q];
-          o.alpha = 1.0;
-          o.beta = 0.0;
-          std::vector<int64_t> rd;
-          for (int sg = 0; sg < nparts[q]; ++sg) rd.push_back(key_part(sw, q, sg));
-          int rid = RT.add(w_ready[q] + 1, rd, {key_w(sw, q)});
-          at(w_ready[q] + 1).add(o, rid);
-          w_ready[q] += 1;
+      out_ready[k] = ph;
+      // partial products V_q' y over the pieces of this solve block's columns
+      for (int q : lr_by_colsb[k]) {
+        for (int sg = 0; sg < nparts[q]; ++sg) {
+          const int lo = pieces[q][sg].first, len = pieces[q][sg].second;
+          if (lo < rb || lo >= send(k)) continue;
+          VPartOp v{};
+          v.V = F.lr_v[q] + (lo - ld[q].c0);
+          v.ldv = ld[q].n;
+          v.y = out + lo;
+          v.len = len;
+          v.kf = kf;
+          v.part = part[q] + (int64_t)sg * kf;
+          int id = RT.add(ph + 1, chunk_keys(key_y(sw, k), nr, CR_ROWS), {key_part(sw, q, sg)});
+          at(ph + 1).add(v, id);
+          w_ready[q] = std::max(w_ready[q], ph + 1);
+          if (++seen[q] == nparts[q] && wfin[q]) {
+            ReduceOp o{};
+            o.parts = part[q];
+            o.dst = wfin[q];
+            o.stride = kf;
+            o.drs = 0;
+            o.dcs = 1;
+            o.m = 1;
+            o.n = kf;
+            o.nparts = nparts[q];
+            o.alpha = 1.0;
+            o.beta = 0.0;
+            std::vector<int64_t> rd;
+            for (int g = 0; g < nparts[q]; ++g) rd.push_back(key_part(sw, q, g));
+            int rid = RT.add(w_ready[q] + 1, rd, {key_w(sw, q)});
+            at(w_ready[q] + 1).add(o, rid);
+            w_ready[q] += 1;
+          }
         }
       }
     }
@@ -1085,8 +1165,8 @@ int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vecto
                const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
                std::vector<RowSrc>& srcs, OpGraph& graph) {
   SolvePlanner S(P, dd, ld, F, arena, waves, srcs, graph);
-  const int nl = (int)P.leaves.size();
-  std::vector<int> b_ready(nl, -1), y_ready, z_ready;
+  const int nb = (int)F.sb_cluster.size();
+  std::vector<int> b_ready(nb, -1), y_ready, z_ready;
   S.sweep(0, true, v.b, b_ready, v.y, v.acc1, y_ready);
   S.sweep(1, false, v.y, y_ready, v.z, v.acc2, z_ready);
   if (S.RT.bad) return HM_ERR_ARG;

@@ -70,13 +70,26 @@ struct FactorLayout {
   std::vector<double*> lr_u, lr_v;       // per LR block: U (m x kf), V (n x kf) column-major
   int kf = 0;
   int* d_rank = nullptr;                 // per LR block rank (device)
-  // factors scaled by the leaf inverses for the solves: dense block (p, j)
-  // becomes L_pp^{-1} L_pj (j < p) or U_pp^{-1} U_pj (j > p); a low-rank block
-  // keeps V and scales the rows of U leaf by leaf the same way.
-  std::vector<int> leaf_diag;            // per leaf (Morton order) -> dense id of its diagonal block
-  std::vector<double*> pdense;           // per dense id (off-diagonal), m x n row-major
-  std::vector<double*> plr;              // per LR id, m x kf column-major
+  // Solve blocks: a cut of the cluster tree (clusters of at most
+  // SOLVE_BLOCK rows).  Each keeps the exact inverses of its diagonal factor
+  // blocks L_BB and U_BB (dense, row-major), and every factor block that
+  // couples two solve blocks is stored scaled by the inverse of its row
+  // block: P = L_BB^{-1} L_BA (dense blocks, S x n) or L_BB^{-1} U_q (rows of a
+  // low-rank block's U inside B, S x kf), likewise with U_BB^{-1}.
+  struct Scaled {
+    bool lower;    // L part (row block after the columns) or U part
+    bool lowrank;  // low-rank block q (x = V_q' y) or dense block (x = y[cols])
+    int id;        // dense id or LR id
+    int sb;        // solve block of the rows
+    double* M;     // S x ncols row-major
+    int ncols;
+  };
+  std::vector<int> sb_cluster;           // cluster of each solve block (Morton order)
+  std::vector<double*> sb_linv, sb_uinv; // S x S row-major
+  std::vector<Scaled> scaled;
 };
+
+constexpr int SOLVE_BLOCK = 1024;
 
 struct HluBuild {
   std::vector<Wave> waves;
