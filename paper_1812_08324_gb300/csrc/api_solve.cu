@@ -62,12 +62,12 @@ int vgrid(int N) { return std::min((N + 255) / 256, 152 * 8); }
 // Tracing (HM_PHASE_TRACE=1): run a schedule once recording every op's
 // finish time and print the span, the time per op kind along the waves, and
 // the ops that finished last.
-void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevSchedule& S, int* d_err,
-                    cudaStream_t st) {
+void trace_schedule(const char* what, const std::vector<Wave>& waves, const OpGraph& graph,
+                    const DevSchedule& S, int* d_err, cudaStream_t st) {
+  const size_t nt = std::max<size_t>(S.host_tasks.size(), 1);
   unsigned long long* d_tr = nullptr;
-  const size_t ntr = 3 * (size_t)std::max(S.nops, 1);
-  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * ntr) != cudaSuccess) return;
-  cudaMemsetAsync(d_tr, 0, sizeof(unsigned long long) * ntr, st);
+  if (cudaMalloc(&d_tr, sizeof(unsigned long long) * TRACE_STRIDE * nt) != cudaSuccess) return;
+  cudaMemsetAsync(d_tr, 0, sizeof(unsigned long long) * TRACE_STRIDE * nt, st);
   cudaStreamSynchronize(st);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -78,52 +78,55 @@ void trace_schedule(const char* what, const std::vector<Wave>& waves, const DevS
   cudaStreamSynchronize(st);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  std::vector<unsigned long long> trall(ntr);
-  cudaMemcpy(trall.data(), d_tr, sizeof(unsigned long long) * ntr, cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> tr(TRACE_STRIDE * nt);
+  cudaMemcpy(tr.data(), d_tr, sizeof(unsigned long long) * TRACE_STRIDE * nt, cudaMemcpyDeviceToHost);
   cudaFree(d_tr);
-  std::vector<unsigned long long> tr(trall.begin(), trall.begin() + std::max(S.nops, 1));
+  // op -> wave
+  std::vector<int> wave_of(std::max(S.nops, 1), 0);
+  for (size_t w = 0; w < waves.size(); ++w) {
+    const Wave& W = waves[w];
+    const std::vector<int>* ids[7] = {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id, &W.rows_id, &W.vpart_id};
+    for (int k = 0; k < 7; ++k)
+      for (int id : *ids[k]) wave_of[id] = (int)w;
+  }
   if (const char* fn = std::getenv("HM_TRACE_FILE")) {
-    // one line per op: id wave kind rows finish ready grabbed (ns)
+    // one line per task: task op wave kind parts cta grabbed ready finished gathered summed (ns) sm : the op's producers
     std::string path = std::string(fn) + "." + what + ".txt";
     FILE* f = fopen(path.c_str(), "a");
     if (f) {
-      const int nops = std::max(S.nops, 1);
-      for (size_t w = 0; w < waves.size(); ++w) {
-        const Wave& W = waves[w];
-        const std::vector<int>* ids[7] = {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id, &W.rows_id, &W.vpart_id};
-        for (int k = 0; k < 7; ++k)
-          for (size_t j = 0; j < ids[k]->size(); ++j) {
-            int id = (*ids[k])[j];
-            int nr = k == 5 ? W.rows[j].nr : 0;
-            fprintf(f, "%d %zu %d %d %llu %llu %llu\n", id, w, k, nr, trall[id], trall[nops + id], trall[2 * nops + id]);
-          }
+      fprintf(f, "# run\n");
+      for (size_t t = 0; t < S.host_tasks.size(); ++t) {
+        const Task& T = S.host_tasks[t];
+        const unsigned long long* q = &tr[TRACE_STRIDE * t];
+        fprintf(f, "%zu %d %d %d %d %llu %llu %llu %llu %llu %llu %llu :", t, T.id, wave_of[T.id], T.kind, T.nsub, q[3],
+                q[0], q[1], q[2], q[4], q[5], q[6]);
+        if (T.id < (int)graph.deps.size())
+          for (int d : graph.deps[T.id]) fprintf(f, " %d", d);
+        fprintf(f, "\n");
       }
       fclose(f);
     }
   }
   unsigned long long t0 = ~0ull, t1 = 0;
-  for (auto t : tr)
-    if (t) { t0 = std::min(t0, t); t1 = std::max(t1, t); }
-  // wave finish time = latest finish of its ops; attribute each wave's advance
+  for (size_t t = 0; t < S.host_tasks.size(); ++t)
+    if (tr[TRACE_STRIDE * t + 2]) { t0 = std::min(t0, tr[TRACE_STRIDE * t]); t1 = std::max(t1, tr[TRACE_STRIDE * t + 2]); }
+  // busy time per kind (producers-ready to finished), summed over tasks
   const char* names[7] = {"gemm", "lu", "trunc", "copy", "reduce", "rows", "vpart"};
-  double by[7] = {0, 0, 0, 0, 0, 0, 0};
-  unsigned long long prev = t0;
-  for (const Wave& W : waves) {
-    unsigned long long wt = 0;
-    int dom = 0;
-    unsigned long long best = 0;
-    const std::vector<int>* ids[7] = {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id, &W.rows_id, &W.vpart_id};
-    for (int k = 0; k < 7; ++k)
-      for (int id : *ids[k]) {
-        wt = std::max(wt, tr[id]);
-        if (tr[id] > best) { best = tr[id]; dom = k; }
-      }
-    if (wt > prev) { by[dom] += (double)(wt - prev) * 1e-3; prev = wt; }
+  double busy[7] = {0, 0, 0, 0, 0, 0, 0};
+  int cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (size_t t = 0; t < S.host_tasks.size(); ++t) {
+    const int k = S.host_tasks[t].kind;
+    if (k >= 0 && k < 7 && tr[TRACE_STRIDE * t + 2] > tr[TRACE_STRIDE * t + 1]) {
+      busy[k] += (double)(tr[TRACE_STRIDE * t + 2] - tr[TRACE_STRIDE * t + 1]) * 1e-3;
+      ++cnt[k];
+    }
   }
-  fprintf(stderr, "[trace] %s: %d waves, %d ops, kernel %.3f ms, op span %.3f ms\n", what, S.nwaves, S.nops, ms,
-          (double)(t1 - t0) * 1e-6);
+  fprintf(stderr, "[trace] %s: %d waves, %d ops, %zu tasks, kernel %.3f ms, task span %.3f ms\n", what, S.nwaves,
+          S.nops, S.host_tasks.size(), ms, (double)(t1 - t0) * 1e-6);
   for (int k = 0; k < 7; ++k)
-    if (by[k] > 0) fprintf(stderr, "[trace]   advance led by %-6s %10.1f us\n", names[k], by[k]);
+    if (cnt[k] > 0)
+      fprintf(stderr, "[trace]   %-6s %8d tasks, busy %10.1f us (%.2f us per task)\n", names[k], cnt[k], busy[k],
+              busy[k] / cnt[k]);
 }
 
 // z = (LU)^{-1} b on Morton-order vectors (b may equal z)
@@ -220,7 +223,7 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   s = upload_schedule(hb.waves, hb.graph, fs, fs_allocs);
   const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
   if (s == HM_OK && tracing) {
-    trace_schedule("factor", hb.waves, fs, H->d_err, st);  // note: runs the factorisation
+    trace_schedule("factor", hb.waves, hb.graph, fs, H->d_err, st);  // note: runs the factorisation
   } else if (s == HM_OK) {
     s = run_schedule(fs, H->d_err, st);
   }
@@ -252,13 +255,13 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   std::vector<RowSrc> srcs;
   OpGraph sg;
   SolveVectors sv{F->d_y, F->d_sv, F->d_sv + (size_t)N, F->d_sv + 2 * (size_t)N, F->d_sv + 3 * (size_t)N};
-  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, sv, F->arena, sw, srcs, sg);
+  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, &F->h_rank, sv, F->arena, sw, srcs, sg);
   if (s != HM_OK) { set_error("solve planning failed"); return fail(s); }
   s = upload_schedule(sw, sg, F->solve, F->allocs, &srcs);
   if (s != HM_OK) { set_error("solve schedule upload failed"); return fail(s); }
   if (tracing) {
-    trace_schedule("solve", sw, F->solve, H->d_err, st);
-    trace_schedule("solve", sw, F->solve, H->d_err, st);
+    trace_schedule("solve", sw, sg, F->solve, H->d_err, st);
+    trace_schedule("solve", sw, sg, F->solve, H->d_err, st);
   }
   F->solve_waves = (int)sw.size();
   // bytes the two sweeps read: leaf inverses, off-diagonal dense blocks, low-rank factors
@@ -393,7 +396,7 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   std::vector<RowSrc> srcs;
   OpGraph sg;
   SolveVectors sv{fy, fy + P.N, fy + 2 * (int64_t)P.N, fy + 3 * (int64_t)P.N, fy + 4 * (int64_t)P.N};
-  s = plan_solve(P, dd, ld, hb.F, sv, A, sw, srcs, sg);
+  s = plan_solve(P, dd, ld, hb.F, nullptr, sv, A, sw, srcs, sg);
   if (s != HM_OK) { set_error("solve planning failed"); return s; }
   std::string first;
   int64_t bad = check_spans(hb.waves, A.ranges, first) + check_spans(sw, A.ranges, first, &srcs);

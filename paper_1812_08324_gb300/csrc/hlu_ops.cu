@@ -435,22 +435,23 @@ __device__ void dev_reduce(const ReduceOp& op, int chunk, int nchunks) {
 // over columns.  Low-rank sources: warp per source (round robin), lane per
 // row, after summing the source's partial products.  Per-row totals are
 // combined in a fixed order, so results are bitwise reproducible.
+// 8-byte asynchronous global -> shared copy (operands written by an earlier
+// kernel only: the copy goes through L1) and the wait for all of a thread's copies.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory layout of a row task: accumulators, per-warp coefficient
-// vectors, staged descriptors, prefetched static rows, gathered dynamic inputs.
-constexpr int ROWS_PREFETCH_DOUBLES = 8192;  // 64 KB of prefetched matrix rows
-constexpr int ROWS_DYN_DOUBLES = 10240;      // 80 KB of gathered inputs (x, partials, base)
-constexpr int ROWS_MAX_SRC = 256;
+// vectors, staged descriptors, copied static rows, gathered dynamic inputs.
 struct RowsSmem {
   double* acc_d;    // 32
   double* acc_l;    // 8 x 32
   double* wsum;     // 8 x 64
   RowSrc* srcs;     // up to ROWS_MAX_SRC descriptors
-  double* pre;      // prefetched rows
+  double* pre;      // copied rows of M
   double* dyn;      // gathered dynamic inputs
-  int* pre_off;     // per source: offset into pre (-1: not prefetched)
-  int* dyn_off;     // per source: offset into dyn (-1: read from global); [nsrc] = base
-  int* dstart;      // per source: start of its gathered range (non-decreasing)
-  int* dyn_total;   // [0] = total gathered doubles
 };
 
 __device__ __forceinline__ RowsSmem rows_smem(double* smem) {
@@ -461,15 +462,13 @@ __device__ __forceinline__ RowsSmem rows_smem(double* smem) {
   L.srcs = reinterpret_cast<RowSrc*>(smem + 32 + 256 + 512);
   L.pre = smem + 32 + 256 + 512 + ROWS_MAX_SRC * (sizeof(RowSrc) / sizeof(double));
   L.dyn = L.pre + ROWS_PREFETCH_DOUBLES;
-  L.pre_off = reinterpret_cast<int*>(L.dyn + ROWS_DYN_DOUBLES);
-  L.dyn_off = L.pre_off + ROWS_MAX_SRC;
-  L.dstart = L.dyn_off + ROWS_MAX_SRC + 1;
-  L.dyn_total = L.dstart + ROWS_MAX_SRC + 1;
   return L;
 }
 
-// Before the wait: stage descriptors, copy static rows into shared memory and
-// lay out the space for the dynamic inputs.
+__device__ __forceinline__ int dyn_start(const RowSrc& S) { return S.dyn_off >= 0 ? S.dyn_off : -(S.dyn_off + 1); }
+
+// Before the wait: stage the descriptors and start the asynchronous copies of
+// the static rows; they complete while the CTA waits for its producers.
 __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double* smem) {
   RowsSmem L = rows_smem(smem);
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
@@ -480,42 +479,15 @@ __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double
     for (int w = threadIdx.x; w < words; w += blockDim.x) d[w] = g[w];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int used = 0, dused = 0;
-    for (int s = 0; s < nsrc; ++s) {
-      const RowSrc& S = L.srcs[s];
-      // dense rows, or low-rank U rows (nr x kf, padded to kf + 1 against bank conflicts)
-      const int need = op.nr * (S.nparts ? S.ncols + 1 : S.ncols);
-      if (used + need <= ROWS_PREFETCH_DOUBLES) {
-        L.pre_off[s] = used;
-        used += need;
-      } else {
-        L.pre_off[s] = -1;
-      }
-      const int dneed = S.nparts ? S.nparts * S.ncols : S.ncols;
-      L.dstart[s] = dused;
-      if (dused + dneed <= ROWS_DYN_DOUBLES - 32) {
-        L.dyn_off[s] = dused;
-        dused += dneed;
-      } else {
-        L.dyn_off[s] = -1;
-      }
-    }
-    L.dyn_off[nsrc] = dused;  // base rows
-    L.dyn_total[0] = dused + (op.base ? op.nr : 0);
-  }
-  __syncthreads();
   for (int s = 0; s < nsrc; ++s) {
-    const int off = L.pre_off[s];
-    if (off < 0) continue;
     const RowSrc& S = L.srcs[s];
+    if (S.pre_off < 0) continue;
     const int nc = S.ncols, tot = op.nr * nc, ld = S.nparts ? nc + 1 : nc;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int r = e / nc, c = e % nc;
-      L.pre[off + r * ld + c] = S.M[r * S.rs + c * S.cs];
+      cp_async8(L.pre + S.pre_off + r * ld + c, S.M + r * S.rs + c * S.cs);
     }
   }
-  __syncthreads();
 }
 
 // After the wait: gather every dynamic input (x vectors, partial products,
@@ -523,53 +495,54 @@ __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double
 __device__ void dev_rows_gather(const RowsOp& op, double* smem) {
   RowsSmem L = rows_smem(smem);
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
-  const int total = L.dyn_total[0];
+  const int total = op.dyn_total;
   for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
     double v[8];
-    int dst[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * blockDim.x;
-      dst[u] = -1;
       v[u] = 0.0;
       if (e < total) {
-        if (e >= L.dyn_off[nsrc]) {
-          v[u] = op.base[op.r0 + (e - L.dyn_off[nsrc])];
-          dst[u] = e;
+        if (e >= op.dyn_base) {
+          v[u] = op.base[op.r0 + (e - op.dyn_base)];
         } else {
-          // source owning element e: the last s with dstart[s] <= e (sources
-          // that gather nothing share their start with the next one)
+          // owning source: the last s whose range starts at or before e
+          // (sources read from global memory own empty ranges)
           int lo = 0, hi = nsrc - 1;
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (L.dstart[mid] <= e) lo = mid; else hi = mid - 1;
+            if (dyn_start(L.srcs[mid]) <= e) lo = mid; else hi = mid - 1;
           }
-          v[u] = L.srcs[lo].x[e - L.dstart[lo]];
-          dst[u] = e;
+          v[u] = L.srcs[lo].x[e - L.srcs[lo].dyn_off];
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (dst[u] >= 0) L.dyn[dst[u]] = v[u];
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < total) L.dyn[e] = v[u];
+    }
   }
   __syncthreads();
 }
 
-__device__ void dev_rows(const RowsOp& op, double* smem) {
+// ts (tracing only, else nullptr): times after the gather and after the sums
+__device__ void dev_rows(const RowsOp& op, double* smem, unsigned long long* ts) {
   RowsSmem L = rows_smem(smem);
+  cp_async_wait_all();
   dev_rows_gather(op, smem);
+  if (ts && threadIdx.x == 0) ts[0] = global_ns();
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nr = op.nr;
-  for (int r = warp; r < 32; r += 8) {
+  for (int r = warp; r < nr; r += 8) {
     double acc = 0.0;
-    if (r < nr) {
+    {
       for (int s = 0; s < nsrc; ++s) {
         const RowSrc& S = L.srcs[s];
         if (S.nparts) continue;
         double a = 0.0;
-        const int off = L.pre_off[s], xo = L.dyn_off[s];
+        const int off = S.pre_off, xo = S.dyn_off;
         for (int c0 = lane; c0 < S.ncols; c0 += 256) {
           double xv[8], mv[8];
 #pragma unroll
@@ -595,7 +568,7 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
     if (!S.nparts) continue;
     if ((k++ & 7) != warp) continue;
     double* w = L.wsum + warp * 64;
-    const int xo = L.dyn_off[s];
+    const int xo = S.dyn_off;
     for (int l = lane; l < S.ncols; l += 32) {
       double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int p = 0;
@@ -608,7 +581,7 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
     }
     __syncwarp();
     if (lane < nr) {
-      const int off = L.pre_off[s];
+      const int off = S.pre_off;
       double a = 0.0;
       if (off >= 0) {
         const double* Mr = L.pre + off + lane * (S.ncols + 1);
@@ -624,9 +597,10 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
   }
   L.acc_l[warp * 32 + lane] = la;
   __syncthreads();
+  if (ts && threadIdx.x == 0) ts[1] = global_ns();
   if (threadIdx.x < nr) {
     const int r = threadIdx.x;
-    double v = op.base ? L.dyn[L.dyn_off[nsrc] + r] : 0.0;
+    double v = op.base ? L.dyn[op.dyn_base + r] : 0.0;
     v += L.acc_d[r];
     for (int w = 0; w < 8; ++w) v += L.acc_l[w * 32 + r];
     op.out[op.r0 + r] = v;
@@ -636,18 +610,19 @@ __device__ void dev_rows(const RowsOp& op, double* smem) {
 
 // V' y over one piece: V (static) is copied to shared memory before the
 // wait (when it fits), y is gathered after it.
-constexpr int VPART_SMEM = 16384;
+constexpr int VPART_SMEM =
+    SOLVE_CTAS_PER_SM == 1 ? 16384 : SOLVE_CTAS_PER_SM == 2 ? 8192 : SOLVE_CTAS_PER_SM == 3 ? 6144 : 4096;
 __device__ void dev_vpart_prefetch(const VPartOp& op, double* smem) {
   if (op.len * op.kf > VPART_SMEM) return;
   for (int e = threadIdx.x; e < op.len * op.kf; e += blockDim.x) {
     const int l = e / op.len, r = e % op.len;
-    smem[e] = op.V[l * op.ldv + r];
+    cp_async8(smem + e, op.V + l * op.ldv + r);
   }
-  __syncthreads();
 }
 
 __device__ void dev_vpart(const VPartOp& op, double* smem) {
   const bool pre = op.len * op.kf <= VPART_SMEM;
+  cp_async_wait_all();
   double* ys = smem + VPART_SMEM;
   for (int r0 = threadIdx.x; r0 < op.len; r0 += 8 * blockDim.x) {
     double v[8];
@@ -675,7 +650,16 @@ __device__ void dev_vpart(const VPartOp& op, double* smem) {
 constexpr int EXEC_THREADS = 256;
 constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
                              sizeof(int) * 6 * TRUNC_MAXK;
+// solve schedules (row, partial-product, reduction, copy tasks): SOLVE_CTAS_PER_SM CTAs per SM
+constexpr size_t ROWS_SMEM = sizeof(double) * (32 + 256 + 512 + ROWS_PREFETCH_DOUBLES + ROWS_DYN_DOUBLES) +
+                             sizeof(RowSrc) * ROWS_MAX_SRC;
+constexpr size_t VPART_SMEM_BYTES = sizeof(double) * (VPART_SMEM + 256);
+constexpr size_t SOLVE_SMEM = ROWS_SMEM > VPART_SMEM_BYTES ? ROWS_SMEM : VPART_SMEM_BYTES;
+static_assert(SOLVE_CTAS_PER_SM * (SOLVE_SMEM + 1024) <= 228 * 1024, "solve executor shared memory");
 constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;  // 4 s for one dependency wait
+#ifndef HM_POLL_NS
+#define HM_POLL_NS 0  // pause between two polls of a producer counter (build-time tuning parameter)
+#endif
 
 struct ExecArgs {
   const GemmOp* gemm;
@@ -695,24 +679,26 @@ struct ExecArgs {
   int ntasks;
   int nops;
   int* err;
-  unsigned long long* trace;  // optional, 3 x nops: finish, producers-ready, grabbed times (ns)
+  unsigned long long* trace;  // optional, TRACE_STRIDE per task: grabbed, producers-ready, finished (ns), CTA, sub-steps
 };
 
-// Acquire load / release add at GPU scope: the pattern of a CTA-wide barrier
-// followed by one thread's release publishes all of the CTA's prior writes; an
-// acquire load that observes it makes them visible to the reader's CTA after
-// its next barrier.
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
+// Release add at GPU scope: a CTA-wide barrier followed by one thread's
+// release publishes all of the CTA's prior writes; a reader that observes the
+// count and then executes an acquire fence sees them, and so does the rest of
+// its CTA after the next barrier.
 __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Wait until every producer of op `id` has finished all its tasks.  Warp 0
-// polls the counters (lanes split the producer list); bounded in time.
+// polls the counters with relaxed loads (lanes split the producer list); each
+// polling lane's acquire fence after observing the counts pairs with the
+// producers' release adds.  Bounded in time.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
   __shared__ int ok;
   if (threadIdx.x < 32) {
@@ -724,7 +710,10 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
       const int need = a.ops[d].ntasks;
       const int* c = a.counters + d;
       unsigned polls = 0;
-      while (ld_acquire(c) < need) {
+      while (ld_relaxed(c) < need) {
+#if HM_POLL_NS > 0
+        __nanosleep(HM_POLL_NS);
+#endif
         if ((++polls & 255u) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) {
           atomicOr(a.err, DEVERR_TIMEOUT);
           good = false;
@@ -732,6 +721,7 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
         }
       }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     good = __all_sync(0xffffffffu, good);
     if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
@@ -741,7 +731,8 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
 
 // Tasks are taken in topological order from a global counter, so a CTA
 // waiting on a producer never holds up a task that is ready elsewhere.
-__global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
+template <bool SOLVE>
+__global__ void __launch_bounds__(EXEC_THREADS, SOLVE ? SOLVE_CTAS_PER_SM : 1) exec_kernel(ExecArgs a) {
   extern __shared__ double smem[];
   __shared__ int next;
   for (;;) {
@@ -751,30 +742,68 @@ __global__ void __launch_bounds__(EXEC_THREADS, 1) exec_kernel(ExecArgs a) {
     __syncthreads();
     if (t >= a.ntasks) return;
     const Task T = a.tasks[t];
-    if (a.trace && threadIdx.x == 0) a.trace[2 * a.nops + T.id] = global_ns();
+    if (a.trace && threadIdx.x == 0) {
+      a.trace[TRACE_STRIDE * (size_t)t] = global_ns();
+      a.trace[TRACE_STRIDE * (size_t)t + 3] = blockIdx.x;
+      unsigned sm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+      a.trace[TRACE_STRIDE * (size_t)t + 6] = sm;
+    }
     if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem);
     if (T.kind == TK_VPART) dev_vpart_prefetch(a.vpart[T.op], smem);
-    if (!wait_deps(a, T.id)) return;
-    if (a.trace && threadIdx.x == 0) a.trace[a.nops + T.id] = global_ns();
+    if (!wait_deps(a, T.id)) {
+      cp_async_wait_all();  // no copy may outlive the CTA
+      return;
+    }
+    if (a.trace && threadIdx.x == 0) a.trace[TRACE_STRIDE * (size_t)t + 1] = global_ns();
+    if constexpr (!SOLVE) {
+      switch (T.kind) {
+        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
+        case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
+        case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
+        default: break;
+      }
+    }
     switch (T.kind) {
-      case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
-      case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
-      case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
       case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
       case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
-      case TK_ROWS: dev_rows(a.rows[T.op], smem); break;
+      case TK_ROWS: dev_rows(a.rows[T.op], smem, a.trace ? a.trace + TRACE_STRIDE * (size_t)t + 4 : nullptr); break;
       case TK_VPART: dev_vpart(a.vpart[T.op], smem); break;
       default: break;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       red_release_add(a.counters + T.id, 1);  // publishes the CTA's writes (after the barrier)
-      if (a.trace) a.trace[T.id] = global_ns();
+      if (a.trace) a.trace[TRACE_STRIDE * (size_t)t + 2] = global_ns();
     }
   }
 }
 
 }  // namespace
+
+void plan_rows_staging(RowsOp& op, RowSrc* src) {
+  const int nsrc = op.src_end - op.src_begin;
+  int used = 0, dused = 0;
+  for (int s = 0; s < nsrc; ++s) {
+    RowSrc& S = src[s];
+    const int need = op.nr * (S.nparts ? S.ncols + 1 : S.ncols);
+    if (s < ROWS_MAX_SRC && used + need <= ROWS_PREFETCH_DOUBLES) {
+      S.pre_off = used;
+      used += need;
+    } else {
+      S.pre_off = -1;
+    }
+    const int dneed = S.nparts ? S.nparts * S.ncols : S.ncols;
+    if (s < ROWS_MAX_SRC && dused + dneed <= ROWS_DYN_DOUBLES - 32) {
+      S.dyn_off = dused;
+      dused += dneed;
+    } else {
+      S.dyn_off = -(dused + 1);
+    }
+  }
+  op.dyn_base = dused;
+  op.dyn_total = dused + (op.base ? op.nr : 0);
+}
 
 int gemm_tiles(int m, int n) { return ((m + GT - 1) / GT) * ((n + GT - 1) / GT); }
 
@@ -832,8 +861,8 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
       r.push_back(o);
     }
     for (size_t k = 0; k < W.rows.size(); ++k) {
-      tasks.push_back({TK_ROWS, (int)ro.size(), 0, 1, W.rows_id[k]});
-      info[W.rows_id[k]].ntasks = 1;
+      tasks.push_back({TK_ROWS, (int)ro.size(), 0, W.rows[k].nr, W.rows_id[k]});  // nsub: rows of the chunk
+      info[W.rows_id[k]].ntasks += 1;  // the chunks of one row op share its id
       ro.push_back(W.rows[k]);
     }
     for (size_t k = 0; k < W.vpart.size(); ++k) {
@@ -867,6 +896,8 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
   std::vector<RowSrc> nos;
   if ((s = up(srcs ? *srcs : nos, &S.srcs)) != HM_OK) return s;
   if ((s = up(tasks, &S.tasks)) != HM_OK) return s;
+  S.host_tasks = tasks;
+  S.solve_only = g.empty() && l.empty() && tr.empty();
   if ((s = up(wb, &S.wave_begin)) != HM_OK) return s;
   if ((s = up(info, &S.ops)) != HM_OK) return s;
   if ((s = up(deps, &S.deps)) != HM_OK) return s;
@@ -877,16 +908,19 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
 
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned long long* trace) {
   if (S.ntasks == 0) return HM_OK;
-  static int grid = 0;
-  if (grid == 0) {
-    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EXEC_SMEM) != cudaSuccess)
+  static int grid[2] = {0, 0};
+  const int m = S.solve_only ? 1 : 0;
+  void* fn = m ? (void*)exec_kernel<true> : (void*)exec_kernel<false>;
+  const size_t smem = m ? SOLVE_SMEM : EXEC_SMEM;
+  if (grid[m] == 0) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HM_ERR_CUDA;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, exec_kernel, EXEC_THREADS, EXEC_SMEM) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXEC_THREADS, smem) != cudaSuccess || per < 1)
       return HM_ERR_CUDA;
-    grid = sms * per;
+    grid[m] = sms * per;
   }
   // counters[nops] is the task dispenser
   if (cudaMemsetAsync(S.counters, 0, sizeof(int) * (S.nops + 1), st) != cudaSuccess) return HM_ERR_CUDA;
@@ -894,8 +928,7 @@ int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned lon
              S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, S.nops, d_err, trace};
   void* args[] = {&a};
   count_launches(1);
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)exec_kernel, dim3(grid), dim3(EXEC_THREADS), args,
-                                              EXEC_SMEM, st);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid[m]), dim3(EXEC_THREADS), args, smem, st);
   return e == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

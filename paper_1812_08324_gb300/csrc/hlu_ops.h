@@ -80,6 +80,9 @@ struct RowSrc {
   int ncols;
   int nparts;        // 0: dense source; > 0: low-rank source
   double sign;
+  // shared-memory staging of the task, set by plan_rows_staging:
+  int pre_off;       // offset of the copied rows of M (-1: read from global memory)
+  int dyn_off;       // offset of the gathered x; -(start + 1) when x is read from global memory
 };
 
 // out[r] = base[r] + sum over sources, rows r0 .. r0 + nr - 1 (nr <= 32);
@@ -89,7 +92,26 @@ struct RowsOp {
   const double* base;
   int r0, nr;
   int src_begin, src_end;
+  int dyn_base, dyn_total;  // gathered base rows start at dyn_base; dyn_total doubles in all
 };
+
+// Executor CTAs per SM for solve schedules (build-time tuning parameter), and
+// the shared-memory staging of a row task (doubles) sized to fit that many.
+#ifndef HM_SOLVE_CTAS
+#define HM_SOLVE_CTAS 2
+#endif
+constexpr int SOLVE_CTAS_PER_SM = HM_SOLVE_CTAS;
+static_assert(SOLVE_CTAS_PER_SM >= 1 && SOLVE_CTAS_PER_SM <= 4, "1 to 4 solve CTAs per SM");
+constexpr int ROWS_PREFETCH_DOUBLES =  // copied matrix rows
+    SOLVE_CTAS_PER_SM == 1 ? 8192 : SOLVE_CTAS_PER_SM == 2 ? 6144 : SOLVE_CTAS_PER_SM == 3 ? 4096 : 3072;
+constexpr int ROWS_DYN_DOUBLES =       // gathered inputs: x vectors, partials, base rows
+    SOLVE_CTAS_PER_SM == 1 ? 10240 : SOLVE_CTAS_PER_SM == 2 ? 5120 : SOLVE_CTAS_PER_SM == 3 ? 3584 : 2560;
+constexpr int ROWS_MAX_SRC = 64;
+
+// Lays out the staging of one row task: the rows of M of each source go to
+// shared memory while they fit (low-rank rows padded to ncols + 1 against bank
+// conflicts), and so do the source vectors and the base rows.
+void plan_rows_staging(RowsOp& op, RowSrc* src);
 
 // part[l] = sum_{r < len} V[r + l * ldv] y[r], l < kf.
 struct VPartOp {
@@ -166,6 +188,8 @@ struct DevSchedule {
   OpInfo* ops = nullptr;
   int* deps = nullptr;
   int* counters = nullptr;   // per op: finished tasks
+  std::vector<Task> host_tasks;  // the task list in hand-out order (for tracing)
+  bool solve_only = false;       // only row, partial-product, reduction and copy tasks
 };
 
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedule& S,
@@ -174,6 +198,7 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedul
 // Run a schedule in one persistent cooperative launch (one CTA per SM).  Every
 // wait is bounded in time: on expiry the kernel sets DEVERR_TIMEOUT in *d_err
 // and returns instead of hanging.
+constexpr int TRACE_STRIDE = 8;  // trace words per task
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st,
                  unsigned long long* trace = nullptr);
 

@@ -829,7 +829,10 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
         const View& inv = lower ? sbL[k] : sbU[k];
         View o = E.new_mat(S, rowsrc.cols, false);
         E.gemm(o, 1.0, inv.sub(0, r - C.begin, S, len), rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
-        FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols});
+        // a lower (upper) triangular inverse leaves the rows above (below) the
+        // source rows zero
+        const int lo = lower ? r - C.begin : 0, hi = lower ? S : e - C.begin;
+        FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols, lo, hi});
       }
       r = e;
     }
@@ -890,6 +893,8 @@ struct Src {
   RowSrc s;
   int ready;
   std::vector<int64_t> res;  // resources the source reads
+  int row_lo = 0, row_hi = 1 << 30;  // rows (relative to the task rows' start) where M can be nonzero
+  int tri = 0;                       // 1: M lower triangular, 2: upper triangular (square, cs == 1)
 };
 
 // Producer tracking on named resources (vector segments, partial products).
@@ -949,12 +954,14 @@ int64_t key_w(int sweep, int q) { return (int64_t(5 + sweep) << 40) | q; }
 class SolvePlanner {
  public:
   SolvePlanner(const Plan& P_, const std::vector<DenseDesc>& dd_, const std::vector<LRDesc>& ld_,
-               const FactorLayout& F_, Arena& A_, std::vector<Wave>& W_, std::vector<RowSrc>& S_, OpGraph& G_)
-      : P(P_), dd(dd_), ld(ld_), F(F_), A(A_), waves(W_), srcs(S_), RT(G_) {}
+               const FactorLayout& F_, const std::vector<int>* rank_, Arena& A_, std::vector<Wave>& W_,
+               std::vector<RowSrc>& S_, OpGraph& G_)
+      : P(P_), dd(dd_), ld(ld_), F(F_), rank(rank_), A(A_), waves(W_), srcs(S_), RT(G_) {}
   const Plan& P;
   const std::vector<DenseDesc>& dd;
   const std::vector<LRDesc>& ld;
   const FactorLayout& F;
+  const std::vector<int>* rank;
   Arena& A;
   std::vector<Wave>& waves;
   std::vector<RowSrc>& srcs;
@@ -966,12 +973,16 @@ class SolvePlanner {
     return waves[ph];
   }
 
-  // one op per chunk of rows; chunk c writes resource wbase | c
+  // rows r0 .. r0 + nr - 1 in chunks of `chunk` rows; chunk c writes resource wbase | c
   void emit_rows(int ph, double* out, const double* base, int r0, int nr, int chunk, const std::vector<Src>& list,
                  const std::vector<int64_t>& extra_reads, int64_t wbase) {
     std::vector<int64_t> reads = extra_reads;
     for (const Src& s : list) reads.insert(reads.end(), s.res.begin(), s.res.end());
-    if (list.size() > 256) status = HM_ERR_ARG;  // a row task stages at most 256 sources (ROWS_MAX_SRC)
+    if (list.size() > ROWS_MAX_SRC) status = HM_ERR_ARG;  // a row task stages at most this many sources
+    // one op for all chunks: its consumers wait on a single counter
+    std::vector<int64_t> writes;
+    for (int c = 0; c < nr; c += chunk) writes.push_back(wbase | (int64_t)(c / chunk));
+    const int id = RT.add(ph, reads, writes);
     for (int c = 0; c < nr; c += chunk) {
       RowsOp o{};
       o.out = out;
@@ -980,12 +991,20 @@ class SolvePlanner {
       o.nr = std::min(chunk, nr - c);
       o.src_begin = (int)srcs.size();
       for (const Src& s : list) {
+        if (s.row_hi <= c || s.row_lo >= c + o.nr) continue;  // zero rows in this chunk
         RowSrc r = s.s;
         r.M = r.M + (int64_t)c * r.rs;
+        if (s.tri == 1) {
+          r.ncols = std::min(r.ncols, c + o.nr);  // columns <= the chunk's last row
+        } else if (s.tri == 2) {
+          r.M += c;                               // columns >= the chunk's first row
+          r.x += c;
+          r.ncols -= c;
+        }
         srcs.push_back(r);
       }
       o.src_end = (int)srcs.size();
-      int id = RT.add(ph, reads, {wbase | (int64_t)(c / chunk)});
+      plan_rows_staging(o, srcs.data() + o.src_begin);
       at(ph).add(o, id);
     }
   }
@@ -1009,8 +1028,9 @@ class SolvePlanner {
     std::vector<std::vector<std::pair<int, int>>> pieces(ld.size());  // (first col, length) per part
     std::vector<std::vector<int>> lr_by_colsb(nb);
     std::vector<bool> used(ld.size(), false);
+    auto kq = [&](int q) { return rank ? std::max(0, std::min((*rank)[q], kf)) : kf; };
     for (const FactorLayout::Scaled& s : F.scaled)
-      if (s.lowrank && s.lower == lower) used[s.id] = true;
+      if (s.lowrank && s.lower == lower && kq(s.id) > 0) used[s.id] = true;
     for (size_t q = 0; q < ld.size(); ++q) {
       if (!used[q]) continue;
       const int c0 = ld[q].c0, c1 = ld[q].c0 + ld[q].n;
@@ -1021,8 +1041,8 @@ class SolvePlanner {
         r = e;
       }
       nparts[q] = (int)pieces[q].size();
-      part[q] = A.alloc((int64_t)nparts[q] * kf);
-      wfin[q] = nparts[q] > 4 ? A.alloc(kf) : nullptr;
+      part[q] = A.alloc((int64_t)nparts[q] * kq(q));
+      wfin[q] = nparts[q] > 4 ? A.alloc(kq(q)) : nullptr;
       if (!part[q] || (nparts[q] > 4 && !wfin[q])) status = HM_ERR_OOM;
     }
     std::vector<std::vector<const FactorLayout::Scaled*>> by_row(nb);
@@ -1043,16 +1063,20 @@ class SolvePlanner {
         s.s.nparts = 0;
         s.s.sign = 1.0;
         s.ready = in_ready[k];
+        s.tri = lower ? 1 : 2;
         if (sw == 1) s.res = chunk_keys(key_y(0, k), nr, CR_ROWS);
         list.push_back(s);
       }
       for (const FactorLayout::Scaled* e : by_row[k]) {
+        if (e->lowrank && !used[e->id]) continue;  // rank 0
         Src s{};
         s.s.M = e->M;
         s.s.rs = e->ncols;
         s.s.cs = 1;
-        s.s.ncols = e->ncols;
+        s.s.ncols = e->lowrank ? kq(e->id) : e->ncols;
         s.s.sign = -1.0;
+        s.row_lo = e->row_lo;
+        s.row_hi = e->row_hi;
         if (e->lowrank) {
           const int q = e->id;
           if (wfin[q]) {  // summed once by a reduction task
@@ -1080,9 +1104,17 @@ class SolvePlanner {
       for (const Src& s : list) latest = std::max(latest, s.ready);
       std::vector<Src> nc, cr;
       for (const Src& s : list) (s.ready < latest - 1 ? nc : cr).push_back(s);
+      if ((int)cr.size() > ROWS_MAX_SRC) {
+        // the critical task stages a bounded number of sources: the earliest
+        // ready of the rest join the non-critical groups
+        std::stable_sort(cr.begin(), cr.end(), [](const Src& x, const Src& y) { return x.ready < y.ready; });
+        const size_t extra = cr.size() - ROWS_MAX_SRC;
+        nc.insert(nc.end(), cr.begin(), cr.begin() + extra);
+        cr.erase(cr.begin(), cr.begin() + extra);
+      }
       int ph;
       if (!nc.empty()) {
-        // non-critical sources in groups of at most 96, chained through
+        // non-critical sources in groups of at most ROWS_MAX_SRC, chained through
         // per-group accumulators (acc_g = acc_{g-1} + group g)
         std::stable_sort(nc.begin(), nc.end(), [](const Src& x, const Src& y) { return x.ready < y.ready; });
         // the first group is the block-inverse product alone when it is ready
@@ -1090,8 +1122,8 @@ class SolvePlanner {
         std::vector<std::vector<Src>> groups;
         size_t i0 = 0;
         if (nc.size() > 1 && nc[0].ready < nc[1].ready) groups.push_back({nc[0]}), i0 = 1;
-        for (size_t g0 = i0; g0 < nc.size(); g0 += 96)
-          groups.emplace_back(nc.begin() + g0, nc.begin() + std::min(nc.size(), g0 + 96));
+        for (size_t g0 = i0; g0 < nc.size(); g0 += ROWS_MAX_SRC)
+          groups.emplace_back(nc.begin() + g0, nc.begin() + std::min(nc.size(), g0 + ROWS_MAX_SRC));
         const double* prev = nullptr;
         int64_t prev_key = -1;
         int phn = 0;
@@ -1100,12 +1132,12 @@ class SolvePlanner {
         const int prev_ph = it > 0 ? out_ready[lower ? k - 1 : k + 1] : 0;
         phn = std::max(0, prev_ph - 2);
         for (size_t gi = 0; gi < groups.size(); ++gi) {
-          const size_t g0 = gi * 96;
+          const size_t g0 = gi;
           const std::vector<Src>& grp = groups[gi];
           for (const Src& s : grp) phn = std::max(phn, s.ready + 1);
           double* accg = g0 == 0 ? acc : A.alloc(P.N) ;
           if (!accg) { status = HM_ERR_OOM; return; }
-          const int64_t gk = key_acc(sw, k) + (int64_t(g0 / 96) << 32);
+          const int64_t gk = key_acc(sw, k) + (int64_t(g0) << 32);
           std::vector<int64_t> rd;
           if (prev) rd = chunk_keys(prev_key, nr, NC_ROWS);
           emit_rows(phn, accg, prev, rb, nr, NC_ROWS, grp, rd, gk);
@@ -1130,8 +1162,8 @@ class SolvePlanner {
           v.ldv = ld[q].n;
           v.y = out + lo;
           v.len = len;
-          v.kf = kf;
-          v.part = part[q] + (int64_t)sg * kf;
+          v.kf = kq(q);
+          v.part = part[q] + (int64_t)sg * kq(q);
           int id = RT.add(ph + 1, chunk_keys(key_y(sw, k), nr, CR_ROWS), {key_part(sw, q, sg)});
           at(ph + 1).add(v, id);
           w_ready[q] = std::max(w_ready[q], ph + 1);
@@ -1139,11 +1171,11 @@ class SolvePlanner {
             ReduceOp o{};
             o.parts = part[q];
             o.dst = wfin[q];
-            o.stride = kf;
+            o.stride = kq(q);
             o.drs = 0;
             o.dcs = 1;
             o.m = 1;
-            o.n = kf;
+            o.n = kq(q);
             o.nparts = nparts[q];
             o.alpha = 1.0;
             o.beta = 0.0;
@@ -1162,9 +1194,9 @@ class SolvePlanner {
 }  // namespace
 
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
-               const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
-               std::vector<RowSrc>& srcs, OpGraph& graph) {
-  SolvePlanner S(P, dd, ld, F, arena, waves, srcs, graph);
+               const FactorLayout& F, const std::vector<int>* rank, const SolveVectors& v, Arena& arena,
+               std::vector<Wave>& waves, std::vector<RowSrc>& srcs, OpGraph& graph) {
+  SolvePlanner S(P, dd, ld, F, rank, arena, waves, srcs, graph);
   const int nb = (int)F.sb_cluster.size();
   std::vector<int> b_ready(nb, -1), y_ready, z_ready;
   S.sweep(0, true, v.b, b_ready, v.y, v.acc1, y_ready);

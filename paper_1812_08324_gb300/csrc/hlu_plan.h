@@ -83,6 +83,7 @@ struct FactorLayout {
     int sb;        // solve block of the rows
     double* M;     // S x ncols row-major
     int ncols;
+    int row_lo, row_hi;  // rows of M that can be nonzero (the inverse is triangular)
   };
   std::vector<int> sb_cluster;           // cluster of each solve block (Morton order)
   std::vector<double*> sb_linv, sb_uinv; // S x S row-major
@@ -116,8 +117,9 @@ struct SolveVectors {
   double* acc1;  // forward partial rows
   double* acc2;  // backward partial rows
 };
+// rank: the factor ranks of the low-rank blocks (nullptr: the storage width kf).
 int plan_solve(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
-               const FactorLayout& F, const SolveVectors& v, Arena& arena, std::vector<Wave>& waves,
-               std::vector<RowSrc>& srcs, OpGraph& graph);
+               const FactorLayout& F, const std::vector<int>* rank, const SolveVectors& v, Arena& arena,
+               std::vector<Wave>& waves, std::vector<RowSrc>& srcs, OpGraph& graph);
 
 }  // namespace hm
