@@ -149,6 +149,8 @@ typedef struct hm_factor_plan_t {
   int64_t bad_spans;     /* operands outside every allocation (must be 0) */
   int64_t arena_bytes;   /* device bytes the factors and temporaries would take */
   int kf;                /* rank cap of the factors' low-rank blocks */
+  double gemm_fma[3];    /* FP64 FMAs of the factor's GEMMs at the rank cap: H-LU proper,
+                            solve-block inverses, scaled couplings */
 } hm_factor_plan_t;
 
 /*

@@ -106,6 +106,22 @@ void trace_schedule(const char* what, const std::vector<Wave>& waves, const OpGr
       }
       fclose(f);
     }
+    // one line per op: id kind dims (gemm m n k; lu m; trunc K kf; copy m n; reduce m n parts; rows nr; vpart len kf)
+    FILE* g = fopen((std::string(fn) + "." + what + ".ops.txt").c_str(), "w");
+    if (g) {
+      for (const Wave& W : waves) {
+        for (size_t j = 0; j < W.gemm.size(); ++j)
+          fprintf(g, "%d 0 %d %d %d\n", W.gemm_id[j], W.gemm[j].m, W.gemm[j].n, W.gemm[j].k);
+        for (size_t j = 0; j < W.lu.size(); ++j) fprintf(g, "%d 1 %d 0 0\n", W.lu_id[j], W.lu[j].m);
+        for (size_t j = 0; j < W.trunc.size(); ++j) fprintf(g, "%d 2 %d %d 0\n", W.trunc_id[j], W.trunc[j].K, W.trunc[j].kf);
+        for (size_t j = 0; j < W.copy.size(); ++j) fprintf(g, "%d 3 %d %d 0\n", W.copy_id[j], W.copy[j].m, W.copy[j].n);
+        for (size_t j = 0; j < W.reduce.size(); ++j)
+          fprintf(g, "%d 4 %d %d %d\n", W.reduce_id[j], W.reduce[j].m, W.reduce[j].n, W.reduce[j].nparts);
+        for (size_t j = 0; j < W.rows.size(); ++j) fprintf(g, "%d 5 %d 0 0\n", W.rows_id[j], W.rows[j].nr);
+        for (size_t j = 0; j < W.vpart.size(); ++j) fprintf(g, "%d 6 %d %d 0\n", W.vpart_id[j], W.vpart[j].len, W.vpart[j].kf);
+      }
+      fclose(g);
+    }
   }
   unsigned long long t0 = ~0ull, t1 = 0;
   for (size_t t = 0; t < S.host_tasks.size(); ++t)
@@ -411,6 +427,7 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   out->bad_spans = bad;
   out->arena_bytes = A.total * (int64_t)sizeof(double);
   out->kf = kf;
+  for (int i = 0; i < 3; ++i) out->gemm_fma[i] = hb.gemm_fma[i];
   if (bad) set_error("operand outside its allocation: " + first);
   return HM_OK;
 }

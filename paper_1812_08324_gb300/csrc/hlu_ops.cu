@@ -11,25 +11,29 @@ namespace hm {
 
 namespace {
 
-constexpr int GT = 32;   // GEMM output tile
+constexpr int GT = 32;   // GEMM output tile (square shape)
 constexpr int GK = 16;   // GEMM k chunk
 
-// One 32 x 32 output tile of C = beta C + alpha A B (256 threads).
-__device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem) {
+// One TM x TN output tile of C = beta C + alpha A B (256 threads, 1024
+// outputs, 2 x 2 per thread).  Narrow outputs (n or m <= 16) take the 64 x 16
+// or 16 x 64 shape so that no thread computes padding.
+template <int TM, int TN>
+__device__ void gemm_tile(const GemmOp& op, int local, double* smem) {
+  constexpr int TX = TN / 2;  // threads along n
   double (*As)[GK + 1] = reinterpret_cast<double (*)[GK + 1]>(smem);
-  double (*Bs)[GT + 1] = reinterpret_cast<double (*)[GT + 1]>(smem + GT * (GK + 1));
-  const int tn = (op.n + GT - 1) / GT;
-  const int i0 = (local / tn) * GT, j0 = (local % tn) * GT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
+  double (*Bs)[TN + 1] = reinterpret_cast<double (*)[TN + 1]>(smem + TM * (GK + 1));
+  const int tn = (op.n + TN - 1) / TN;
+  const int i0 = (local / tn) * TM, j0 = (local % tn) * TN;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int k0 = 0; k0 < op.k; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+    for (int e = threadIdx.x; e < TM * GK; e += 256) {
       int r = e / GK, c = e % GK;
       int gi = i0 + r, gk = k0 + c;
       As[r][c] = (gi < op.m && gk < op.k) ? op.A[gi * op.ars + gk * op.acs] : 0.0;
     }
-    for (int e = threadIdx.x; e < GK * GT; e += 256) {
-      int r = e / GT, c = e % GT;
+    for (int e = threadIdx.x; e < GK * TN; e += 256) {
+      int r = e / TN, c = e % TN;
       int gk = k0 + r, gj = j0 + c;
       Bs[r][c] = (gk < op.k && gj < op.n) ? op.B[gk * op.brs + gj * op.bcs] : 0.0;
     }
@@ -59,54 +63,145 @@ __device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem) {
   __syncthreads();
 }
 
+__device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem) {
+  if (op.shape == 1) gemm_tile<64, 16>(op, local, smem);
+  else if (op.shape == 2) gemm_tile<16, 64>(op, local, smem);
+  else gemm_tile<32, 32>(op, local, smem);
+}
+
 // Base LU (m <= LU_BASE) in shared memory, then the inverses of L (unit
-// lower) and U by substitution against the identity.
-__device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
-  double (*A)[LU_BASE + 1] = reinterpret_cast<double (*)[LU_BASE + 1]>(smem);
-  double (*X)[LU_BASE + 1] = reinterpret_cast<double (*)[LU_BASE + 1]>(smem + LU_BASE * (LU_BASE + 1));
-  const int m = op.m, t = threadIdx.x;
-  for (int e = t; e < m * m; e += blockDim.x) A[e / m][e % m] = op.A[(e / m) * op.lda + e % m];
+// lower) and U.  FP64 on this GPU issues one warp instruction per 64 cycles
+// on each SM sub-partition and a division takes about ten of them, so the
+// work is laid out to keep dependent FP64 chains short: one reciprocal per
+// pivot (warp 0, overlapped with the other warps' updates), and blocked
+// inverses (8 x 8 diagonal blocks by substitution, then two doubling steps of
+// small products).  The block is padded to 32 with the identity.
+constexpr int LB = LU_BASE;
+struct LuSmem {
+  double (*A)[LB + 1];
+  double (*XL)[LB + 1];
+  double (*XU)[LB + 1];
+  double* TL;   // 2 x 16 x 16 products of the doubling steps
+  double* TU;
+  double* rd;   // 1 / U[i][i]
+  double* rp;   // reciprocal of the current pivot
+};
+
+__device__ __forceinline__ LuSmem lu_smem(double* smem) {
+  LuSmem S;
+  S.A = reinterpret_cast<double (*)[LB + 1]>(smem);
+  S.XL = reinterpret_cast<double (*)[LB + 1]>(smem + LB * (LB + 1));
+  S.XU = reinterpret_cast<double (*)[LB + 1]>(smem + 2 * LB * (LB + 1));
+  S.TL = smem + 3 * LB * (LB + 1);
+  S.TU = S.TL + 512;
+  S.rd = S.TU + 512;
+  S.rp = S.rd + LB;
+  return S;
+}
+
+// One doubling step of the blocked inverses: blocks of size s combine into
+// blocks of size 2s (XL21 = -XL22 L21 XL11, XU12 = -XU11 U12 XU22).
+__device__ void lu_inv_double(const LuSmem& S, int s) {
+  const int np = LB / (2 * s), per = np * s * s, t = threadIdx.x;
+  for (int e = t; e < 2 * per; e += blockDim.x) {
+    const int f = e / per, r = e % per, pr = r / (s * s), i = (r % (s * s)) / s, j = r % s, b = pr * 2 * s;
+    double acc = 0.0;
+    if (f == 0) {
+      for (int k = 0; k < s; ++k) acc += S.A[b + s + i][b + k] * S.XL[b + k][b + j];
+      S.TL[r] = acc;
+    } else {
+      for (int k = 0; k < s; ++k) acc += S.A[b + i][b + s + k] * S.XU[b + s + k][b + s + j];
+      S.TU[r] = acc;
+    }
+  }
   __syncthreads();
-  for (int p = 0; p < m; ++p) {
-    double piv = A[p][p];
+  for (int e = t; e < 2 * per; e += blockDim.x) {
+    const int f = e / per, r = e % per, pr = r / (s * s), i = (r % (s * s)) / s, j = r % s, b = pr * 2 * s;
+    const double* T = (f == 0 ? S.TL : S.TU) + pr * s * s;
+    double acc = 0.0;
+    if (f == 0) {
+      for (int k = 0; k < s; ++k) acc += S.XL[b + s + i][b + s + k] * T[k * s + j];
+      S.XL[b + s + i][b + j] = -acc;
+    } else {
+      for (int k = 0; k < s; ++k) acc += S.XU[b + i][b + k] * T[k * s + j];
+      S.XU[b + i][b + s + j] = -acc;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
+  const LuSmem S = lu_smem(smem);
+  const int m = op.m, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int e = t; e < LB * LB; e += blockDim.x) {
+    const int i = e / LB, j = e % LB;
+    S.A[i][j] = (i < m && j < m) ? op.A[i * op.lda + j] : (i == j ? 1.0 : 0.0);
+    S.XL[i][j] = 0.0;
+    S.XU[i][j] = 0.0;
+  }
+  __syncthreads();
+  auto recip = [&](double piv) {
     if (piv == 0.0 || !isfinite(piv)) {
-      if (t == 0) atomicOr(err, DEVERR_ZEROPIVOT);
+      atomicOr(err, DEVERR_ZEROPIVOT);
       piv = 1e-300;
     }
+    return 1.0 / piv;
+  };
+  if (t == 0) S.rp[0] = recip(S.A[0][0]);
+  __syncthreads();
+  // right-looking elimination; warp 0 updates the next pivot first and takes
+  // its reciprocal while warps 1..7 update the rest
+  for (int p = 0; p < m; ++p) {
+    const double rp = S.rp[0];
+    for (int i = p + 1 + t; i < m; i += blockDim.x) S.A[i][p] *= rp;
     __syncthreads();
-    for (int i = p + 1 + t; i < m; i += blockDim.x) A[i][p] /= piv;
-    __syncthreads();
-    for (int e = t; e < (m - p - 1) * (m - p - 1); e += blockDim.x) {
-      int i = p + 1 + e / (m - p - 1), j = p + 1 + e % (m - p - 1);
-      A[i][j] -= A[i][p] * A[p][j];
+    const int w = m - p - 1;
+    if (warp == 0) {
+      if (lane == 0 && w > 0) {
+        const double v = S.A[p + 1][p + 1] - S.A[p + 1][p] * S.A[p][p + 1];
+        S.A[p + 1][p + 1] = v;
+        S.rp[0] = recip(v);
+      }
+    } else {
+      for (int e = t - 32; e < w * w; e += blockDim.x - 32) {
+        if (e == 0) continue;  // the next pivot: warp 0
+        const int i = p + 1 + e / w, j = p + 1 + e % w;
+        S.A[i][j] -= S.A[i][p] * S.A[p][j];
+      }
     }
     __syncthreads();
   }
-  // L^{-1}: column j by forward substitution (thread per column)
-  if (t < m) {
-    const int j = t;
-    for (int i = 0; i < m; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) v -= A[i][k] * X[k][j];
-      X[i][j] = i < j ? 0.0 : v;
+  // diagonal 8 x 8 blocks of both inverses by substitution: warp 0 L, warp 1 U
+  if (warp == 1) {  // padded rows have 1 on the diagonal; a zero pivot was flagged above
+    const double d = S.A[lane][lane];
+    S.rd[lane] = 1.0 / (d == 0.0 ? 1e-300 : d);
+  }
+  __syncwarp();
+  if (warp == 0) {
+    const int b = (lane >> 3) * 8, j = lane & 7;
+    S.XL[b + j][b + j] = 1.0;
+    for (int i = j + 1; i < 8; ++i) {
+      double v = 0.0;
+      for (int k = j; k < i; ++k) v -= S.A[b + i][b + k] * S.XL[b + k][b + j];
+      S.XL[b + i][b + j] = v;
+    }
+  } else if (warp == 1) {
+    const int b = (lane >> 3) * 8, j = lane & 7;
+    S.XU[b + j][b + j] = S.rd[b + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double v = 0.0;
+      for (int k = i + 1; k <= j; ++k) v += S.A[b + i][b + k] * S.XU[b + k][b + j];
+      S.XU[b + i][b + j] = -v * S.rd[b + i];
     }
   }
   __syncthreads();
-  for (int e = t; e < m * m; e += blockDim.x) op.Li[(e / m) * op.ldl + e % m] = X[e / m][e % m];
-  __syncthreads();
-  // U^{-1}: column j by back substitution
-  if (t < m) {
-    const int j = t;
-    for (int i = m - 1; i >= 0; --i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      if (i > j) { X[i][j] = 0.0; continue; }
-      for (int k = i + 1; k <= j; ++k) v -= A[i][k] * X[k][j];
-      double d = A[i][i];
-      X[i][j] = v / (d == 0.0 ? 1e-300 : d);
-    }
+  lu_inv_double(S, 8);
+  lu_inv_double(S, 16);
+  for (int e = t; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    op.Li[i * op.ldl + j] = S.XL[i][j];
+    op.Ui[i * op.ldu + j] = S.XU[i][j];
   }
-  __syncthreads();
-  for (int e = t; e < m * m; e += blockDim.x) op.Ui[(e / m) * op.ldu + e % m] = X[e / m][e % m];
   __syncthreads();
 }
 
@@ -805,7 +900,12 @@ void plan_rows_staging(RowsOp& op, RowSrc* src) {
   op.dyn_total = dused + (op.base ? op.nr : 0);
 }
 
-int gemm_tiles(int m, int n) { return ((m + GT - 1) / GT) * ((n + GT - 1) / GT); }
+int gemm_shape(int m, int n) { return n <= 16 && m > 16 ? 1 : (m <= 16 && n > 16 ? 2 : 0); }
+int gemm_tiles(int m, int n) {
+  const int sh = gemm_shape(m, n);
+  const int tm = sh == 1 ? 64 : sh == 2 ? 16 : 32, tn = sh == 1 ? 16 : sh == 2 ? 64 : 32;
+  return ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
+}
 
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSchedule& S,
                     std::vector<void*>& allocs, const std::vector<RowSrc>* srcs) {
@@ -826,7 +926,9 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
     for (int d : graph.deps[id]) deps.push_back(d);
     info[id].dep_end = (int)deps.size();
   }
-  auto chunks = [](int64_t elems) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, elems / 4096)); };
+  // copies and reductions are split so that one task does about 2048 FP64
+  // operations (a few microseconds on one SM)
+  auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
   for (const Wave& W : waves) {
     wb.push_back((int)tasks.size());
     for (size_t k = 0; k < W.gemm.size(); ++k) {
@@ -855,7 +957,7 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
     }
     for (size_t k = 0; k < W.reduce.size(); ++k) {
       const ReduceOp& o = W.reduce[k];
-      int nc = chunks((int64_t)o.m * o.n), id = W.reduce_id[k];
+      int nc = chunks((int64_t)o.m * o.n * std::max(o.nparts, 1)), id = W.reduce_id[k];
       for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
       info[id].ntasks = nc;
       r.push_back(o);

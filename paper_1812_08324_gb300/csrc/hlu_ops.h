@@ -19,7 +19,7 @@ struct GemmOp {
   const double* B;
   double* C;
   int m, n, k;
-  int pad;
+  int shape;         // output tile: 0 = 32 x 32, 1 = 64 x 16, 2 = 16 x 64 (gemm_shape)
   int64_t ars, acs, brs, bcs, crs, ccs;
   double alpha, beta;
 };
@@ -202,6 +202,7 @@ constexpr int TRACE_STRIDE = 8;  // trace words per task
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st,
                  unsigned long long* trace = nullptr);
 
-int gemm_tiles(int m, int n);
+int gemm_shape(int m, int n);  // tile shape of an m x n output
+int gemm_tiles(int m, int n);  // tasks of an m x n output
 
 }  // namespace hm

@@ -98,6 +98,14 @@ struct Acc {
   bool write;
 };
 
+#ifndef HM_KSLICE
+#define HM_KSLICE 64  // smallest split-K slice (build-time tuning parameter)
+#endif
+#ifndef HM_GRAM_CHUNK
+#define HM_GRAM_CHUNK 64  // rows per partial Gram product (build-time tuning parameter)
+#endif
+constexpr int GRAM_CHUNK = HM_GRAM_CHUNK;
+
 class Emitter {
  public:
   Emitter(std::vector<Wave>& w, OpGraph& g, Arena& a, int seg) : waves(w), graph(g), A(a), seg_default(seg) {}
@@ -110,6 +118,8 @@ class Emitter {
   int seg_default;
   int64_t nops = 0;
   int status = HM_OK;
+  int phase = 0;                        // FMA accounting bucket of the ops emitted now
+  double gemm_fma[3] = {0.0, 0.0, 0.0};
 
   View new_mat(int rows, int cols, bool colmajor, int seg = -1) {
     View v;
@@ -267,12 +277,15 @@ class Emitter {
     }
     const int K = Am.cols;
     const int tiles = gemm_tiles(C.rows, C.cols);
-    // a 32x32 tile costs 32*32*k FP64 FMAs on one SM (about 0.25 us per unit of
-    // k): long inner dimensions with few tiles are split so that the work
-    // reaches more SMs
+    // a tile costs 1024 k FP64 FMAs on one SM (about 0.27 us per unit of k at
+    // two FP64 FMAs per cycle): long inner dimensions with few tiles are split
+    // so that the work reaches more SMs, in slices of at least HM_KSLICE
     int KS = 0;
-    if (K > 512 && tiles < 64) KS = 256;
-    else if (K >= 128 && tiles < 76) KS = 64;
+    if (tiles < 76 && K >= 2 * HM_KSLICE) {
+      const int want = std::max(2, 152 / tiles);            // slices that fill the SMs
+      const int ns = std::min(want, K / HM_KSLICE);
+      if (ns >= 2) KS = ((K + ns - 1) / ns + 15) / 16 * 16;
+    }
     if (KS) {
       const int ns = (K + KS - 1) / KS;
       View parts = tmp(ns * C.rows, C.cols, false);
@@ -289,6 +302,7 @@ class Emitter {
   }
 
   void gemm_direct(const View& C, double alpha, const View& Am, const View& Bm, double beta) {
+    gemm_fma[phase] += (double)C.rows * C.cols * Am.cols;
     int w = beta != 0.0 ? place({{&Am, false}, {&Bm, false}, {&C, false}, {&C, true}})
                         : place({{&Am, false}, {&Bm, false}, {&C, true}});
     GemmOp o{};
@@ -298,6 +312,7 @@ class Emitter {
     o.m = C.rows;
     o.n = C.cols;
     o.k = Am.cols;
+    o.shape = gemm_shape(o.m, o.n);
     o.ars = Am.rs;
     o.acs = Am.cs;
     o.brs = Bm.rs;
@@ -345,11 +360,12 @@ class Emitter {
     waves[w].add(o, cur_id);
   }
 
-  // Gram matrix G = X' X (K x K row-major, fresh), split over 256-row chunks.
+  // Gram matrix G = X' X (K x K row-major, fresh), split over GRAM_CHUNK-row
+  // chunks so that the K x K x rows FMAs of one Gram matrix spread over SMs.
   View gram(const View& X) {
     const int K = X.cols;
     View G = tmp(K, K, false);
-    const int CH = 256;
+    const int CH = GRAM_CHUNK;
     int nch = (X.rows + CH - 1) / CH;
     if (nch <= 1) {
       gemm_direct(G, 1.0, X.T(), X, 0.0);
@@ -384,10 +400,17 @@ class Emitter {
 
 // ---------------------------------------------------------------- H-LU
 
+// Low-rank updates are accumulated: a block's current slot holds its factor in
+// the first kf columns and pending update terms after them; the sum is
+// recompressed once, when the pending columns are full or the block is read.
+#ifndef HM_LR_ACC
+#define HM_LR_ACC 3  // pending capacity in multiples of kf (build-time tuning parameter)
+#endif
 struct LRState {
-  View U[2], V[2];   // slots: m x 2kf and n x 2kf, column-major
+  View U[2], V[2];   // slots: m x (1 + nacc) kf and n x (1 + nacc) kf, column-major
   View rankv;        // dependency token for the rank word
   int cur = 0;
+  int pend = 0;      // pending columns after the first kf of the current slot
   int m = 0, n = 0;
   int* rank = nullptr;
 };
@@ -421,8 +444,19 @@ class HLU {
   int roff(int parent, int ch) const { return P.cl[B(ch).t].begin - P.cl[B(parent).t].begin; }
   int coff(int parent, int ch) const { return P.cl[B(ch).s].begin - P.cl[B(parent).s].begin; }
 
-  View lrU(int q) { return lr[q].U[lr[q].cur].sub(0, 0, lr[q].m, kf); }
-  View lrV(int q) { return lr[q].V[lr[q].cur].sub(0, 0, lr[q].n, kf); }
+  // pending update columns a block may hold (the truncation core takes at most TRUNC_MAXK)
+  int nacc() const { return std::max(1, std::min(HM_LR_ACC, TRUNC_MAXK / kf - 1)); }
+  int pend_cap() const { return nacc() * kf; }
+  // readers see the recompressed factor
+  View lrU(int q) { flush(q); return lr[q].U[lr[q].cur].sub(0, 0, lr[q].m, kf); }
+  View lrV(int q) { flush(q); return lr[q].V[lr[q].cur].sub(0, 0, lr[q].n, kf); }
+  void flush(int q) {
+    if (lr[q].pend > 0) {
+      const int K = kf + lr[q].pend;
+      lr[q].pend = 0;
+      truncate(q, K);
+    }
+  }
 
   // ---- leaf LU with inverses of both factors
   void luinv(const View& Am, const View& Li, const View& Ui) {
@@ -486,12 +520,13 @@ class HLU {
         return;
       }
       LRState& S = lr[C.id];
-      View Upend = S.U[S.cur].sub(0, kf, S.m, w), Vpend = S.V[S.cur].sub(0, kf, S.n, w);
+      if (S.pend + w > pend_cap()) flush(C.id);
+      View Upend = S.U[S.cur].sub(0, kf + S.pend, S.m, w), Vpend = S.V[S.cur].sub(0, kf + S.pend, S.n, w);
       if (tg.ro != 0 || tg.nr != S.m) E.copy(Upend, 0.0, nullptr, 0.0);
       if (tg.co != 0 || tg.nc != S.n) E.copy(Vpend, 0.0, nullptr, 0.0);
       E.copy(Upend.sub(tg.ro, 0, tg.nr, w), alpha, &Up, 0.0);
       E.copy(Vpend.sub(tg.co, 0, tg.nc, w), 1.0, &Vp, 0.0);
-      truncate(C.id, kf + w);
+      S.pend += w;
       return;
     }
     // H target: split over the children that intersect the target range
@@ -753,8 +788,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     S.n = L.n;
     S.rank = d_rank_f + q;
     for (int s = 0; s < 2; ++s) {
-      S.U[s] = E.new_mat(L.m, 2 * kf, true);
-      S.V[s] = E.new_mat(L.n, 2 * kf, true);
+      S.U[s] = E.new_mat(L.m, (1 + H.nacc()) * kf, true);
+      S.V[s] = E.new_mat(L.n, (1 + H.nacc()) * kf, true);
     }
     S.rankv = E.new_mat(1, 1, false, 1);
     int kc = std::min(L.kcap, kf);
@@ -768,6 +803,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     }
   }
   H.hlu(0);
+  for (int q = 0; q < nl; ++q) H.flush(q);  // recompress what is still pending
+  E.phase = 1;
   // Solve blocks and their exact diagonal inverses, then the scaled couplings.
   FactorLayout& FL = out.F;
   {
@@ -815,6 +852,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   std::vector<int> sb_of_row(P.N, 0);
   for (int k = 0; k < nsb; ++k)
     for (int r = P.cl[FL.sb_cluster[k]].begin; r < P.cl[FL.sb_cluster[k]].end; ++r) sb_of_row[r] = k;
+  E.phase = 2;
   auto couple = [&](int tcl, int scl, bool lowrank, int id, bool lower, const View& rowsrc) {
     // rowsrc: the block's rows (dense m x n, or U m x kf); scale each part in a solve block
     const Cluster& T = P.cl[tcl];
@@ -851,6 +889,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     return E.status != HM_OK ? E.status : arena.status;
   }
   out.ops = E.nops;
+  for (int i = 0; i < 3; ++i) out.gemm_fma[i] = E.gemm_fma[i];
   FactorLayout& F = out.F;
   F.kf = kf;
   (void)F;

@@ -97,6 +97,7 @@ struct HluBuild {
   OpGraph graph;
   FactorLayout F;
   int64_t ops = 0;
+  double gemm_fma[3] = {0.0, 0.0, 0.0};  // GEMM FMAs: H-LU, solve-block inverses, scaled couplings
   std::string err;
 };
 

@@ -55,10 +55,12 @@ class Stats(C.Structure):
 class FactorPlan(C.Structure):
     _fields_ = [("fact_ops", C.c_int64), ("fact_waves", C.c_int), ("solve_ops", C.c_int64),
                 ("solve_waves", C.c_int), ("bad_spans", C.c_int64), ("arena_bytes", C.c_int64),
-                ("kf", C.c_int)]
+                ("kf", C.c_int), ("gemm_fma", C.c_double * 3)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["gemm_fma"] = list(self.gemm_fma)
+        return d
 
 
 class HMError(RuntimeError):
