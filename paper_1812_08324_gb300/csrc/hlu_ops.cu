@@ -205,6 +205,16 @@ __device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
   __syncthreads();
 }
 
+// Biased exponent of a Gram diagonal entry (0 for zero or subnormal) and an
+// exact power of two 2^n (|n| clamped to the normal range).
+__device__ __forceinline__ int gram_exponent(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+__device__ __forceinline__ double pow2i(int n) {
+  n = max(-1000, min(1000, n));
+  return __longlong_as_double((long long)(1023 + n) << 52);
+}
+
 // ---- truncation core (one CTA): pivoted Cholesky of both Gram matrices,
 // core C = R_A P_A' P_B R_B', column-pivoted Householder QR of C, then the
 // coefficient matrices TA, TB (see TruncOp).
@@ -309,9 +319,25 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
   double* GA = sm;
   double* GB = sm + K * K;
   double* C = sm + 2 * K * K;
+  int* kexp = red_i + 8;  // K ints (the int scratch holds 7 x TRUNC_MAXK)
   for (int e = t; e < K * K; e += blockDim.x) {
     GA[e] = op.GA[e];
     GB[e] = op.GB[e];
+  }
+  __syncthreads();
+  // Balance every column pair (a_i, b_i) by an exact power of two,
+  // a_i 2^k_i and b_i 2^-k_i with |a_i| ~ |b_i|, so that the Gram diagonals
+  // measure the norms |a_i||b_i| of the terms of the sum: otherwise a small
+  // column of A whose partner in B is large falls below the Cholesky cut.
+  for (int i = t; i < K; i += blockDim.x) {
+    const int ea = gram_exponent(GA[i * K + i]), eb = gram_exponent(GB[i * K + i]);
+    kexp[i] = (ea > 0 && eb > 0) ? (eb - ea) >> 2 : 0;
+  }
+  __syncthreads();
+  for (int e = t; e < K * K; e += blockDim.x) {
+    const int s = kexp[e / K] + kexp[e % K];
+    GA[e] *= pow2i(s);
+    GB[e] *= pow2i(-s);
   }
   __syncthreads();
   // Gram entries below (tol/10)^2 of the largest carry nothing the truncation keeps
@@ -450,7 +476,7 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
   __syncthreads();
   for (int e = t; e < K * kf; e += blockDim.x) {
     int i = e / kf, c = e % kf;
-    op.TA[permA[i] * kf + c] = GA[i * kf + c];
+    op.TA[permA[i] * kf + c] = GA[i * kf + c] * pow2i(kexp[permA[i]]);
   }
   // T_B (pivoted rows) = R11_B^{-1} Z, Z[j][c] = R_C[c][posC(j)] for j < rB
   __syncthreads();
@@ -480,7 +506,7 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
   __syncthreads();
   for (int e = t; e < K * kf; e += blockDim.x) {
     int i = e / kf, c = e % kf;
-    op.TB[permB[i] * kf + c] = (i < rB && c < r) ? GA[i * kf + c] : 0.0;
+    op.TB[permB[i] * kf + c] = (i < rB && c < r) ? GA[i * kf + c] * pow2i(-kexp[permB[i]]) : 0.0;
   }
   if (t == 0) {
     *op.rank = r;
@@ -744,7 +770,7 @@ __device__ void dev_vpart(const VPartOp& op, double* smem) {
 
 constexpr int EXEC_THREADS = 256;
 constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
-                             sizeof(int) * 6 * TRUNC_MAXK;
+                             sizeof(int) * 7 * TRUNC_MAXK;
 // solve schedules (row, partial-product, reduction, copy tasks): SOLVE_CTAS_PER_SM CTAs per SM
 constexpr size_t ROWS_SMEM = sizeof(double) * (32 + 256 + 512 + ROWS_PREFETCH_DOUBLES + ROWS_DYN_DOUBLES) +
                              sizeof(RowSrc) * ROWS_MAX_SRC;

@@ -42,7 +42,8 @@ def test_hlu_solve_matches_dense(name, prob, opts, dt):
         x = host(F.solve(dev(b)))
         ref = np.linalg.solve(M, b)
         err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
-        assert err < 1e-6, err
+        # the compression tolerances are 1e-10: the factors solve to ~1e-11
+        assert err < 1e-8, err
     st = H.stats(F)
     assert st["lu_bytes"] > 0
 
@@ -90,3 +91,32 @@ def test_factor_rejects_mismatched_dt():
     u = dev(np.zeros(prob["n"][0]))
     with pytest.raises(hmat.HMError):
         hmat.cn_step(H, F, 2 * dt, u)
+
+
+@pytest.mark.slow
+def test_hlu_solve_accuracy_full_size_levy1d():
+    """1D Levy generator at N = 65536 (leaf 256, ACA rank <= 32, factor rank
+    <= 16, dt = 1e-3): one H-LU solve of a random right-hand side agrees with
+    its iteratively refined solution (FP64 H-matvec residuals) to 1e-9, and the
+    refined solution leaves a relative residual below 1e-12 in the H system.
+    A property that holds at any size; the dense oracle does not reach N = 65536."""
+    prob, opts, dt, steps, kind = W.WORKLOADS["levy_1d_n65536"]
+    H = hmat.HMatrix(prob, dict(opts, lu_max_rank=16, lu_tol=1e-10))
+    F = H.factor(-0.5 * dt)
+    N = prob["n"][0]
+    rng = np.random.default_rng(5)
+    b = dev(rng.standard_normal(N))
+
+    def apply_m(x):  # (I - dt/2 G) x = 2x - (I + dt/2 G) x
+        return 2 * x - H.matvec(x, alpha=1.0, beta=0.5 * dt)
+
+    x0 = F.solve(b)
+    x = x0.clone()
+    for _ in range(4):
+        x = x + F.solve(b - apply_m(x))
+    err = (torch.linalg.norm(x0 - x) / torch.linalg.norm(x)).item()
+    res = (torch.linalg.norm(b - apply_m(x)) / torch.linalg.norm(b)).item()
+    assert err < 1e-9, err
+    assert res < 1e-12, res
+    F.free()
+    H.free()
