@@ -982,6 +982,10 @@ struct ResTracker {
 int64_t key_y(int sweep, int p, int c = 0) { return (int64_t(1 + sweep) << 40) | (int64_t(p) << 12) | c; }
 int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 44) | (int64_t(p) << 12) | c; }
 constexpr int CR_ROWS = 8, NC_ROWS = 32;
+#ifndef HM_NC_LEAD
+#define HM_NC_LEAD 8  // phases by which non-critical row groups precede their block (tuning parameter)
+#endif
+constexpr int NC_LEAD = HM_NC_LEAD;
 std::vector<int64_t> chunk_keys(int64_t base, int nr, int chunk) {
   std::vector<int64_t> k;
   for (int c = 0; c * chunk < nr; ++c) k.push_back(base | c);
@@ -1167,9 +1171,9 @@ class SolvePlanner {
         int64_t prev_key = -1;
         int phn = 0;
         // the chain reaches this block about two phases after the previous
-        // one: the early groups go just ahead of that, overlapping the chain
+        // one: the early groups go NC_LEAD phases ahead of that, overlapping the chain
         const int prev_ph = it > 0 ? out_ready[lower ? k - 1 : k + 1] : 0;
-        phn = std::max(0, prev_ph - 2);
+        phn = std::max(0, prev_ph - NC_LEAD);
         for (size_t gi = 0; gi < groups.size(); ++gi) {
           const size_t g0 = gi;
           const std::vector<Src>& grp = groups[gi];

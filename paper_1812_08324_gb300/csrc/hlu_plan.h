@@ -90,7 +90,10 @@ struct FactorLayout {
   std::vector<Scaled> scaled;
 };
 
-constexpr int SOLVE_BLOCK = 1024;
+#ifndef HM_SOLVE_BLOCK
+#define HM_SOLVE_BLOCK 1024  // largest solve block (build-time tuning parameter)
+#endif
+constexpr int SOLVE_BLOCK = HM_SOLVE_BLOCK;
 
 struct HluBuild {
   std::vector<Wave> waves;
