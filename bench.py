@@ -104,6 +104,19 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms_local: float, units_local: float, world: int, device: str = "cpu"):
+    """Whole-job timing over replicas: the slowest rank's time per step and the
+    units all ranks processed per second (every rank runs the same replica)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_local / (ms * 1e-3)
+
+
 def workload(refine=0):
     from paper_1812_08324_gb300 import workloads as W
     prob, opts, dt, steps, kind = W.WORKLOADS[WORKLOAD]
@@ -224,12 +237,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     clocks = sampler.stop()
     H.sync()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * cn_steps / (ms * 1e-3)
+    ms, value = aggregate(ms, N * cn_steps, world, "cuda")
 
     # ---- accuracy of the timed configuration: the same CN run with three FP64
     # refinement sweeps per step (solves converged to the FP64 H system) as reference

@@ -92,7 +92,7 @@ typedef struct hm_opts {
   int max_rank;      /* rank cap of the ACA blocks */
   double lu_tol;     /* relative truncation tolerance of low-rank sums in H-LU */
   int lu_max_rank;   /* rank cap of the low-rank blocks of the factors */
-  int precision;     /* HM_FP64 or HM_MIXED_FP32 (storage of the factors) */
+  int precision;     /* HM_FP64 (HM_MIXED_FP32 is reserved: hm_build returns HM_ERR_ARG) */
   double refine_tol; /* stop refinement when ||s||_2 <= refine_tol ||rhs||_2 */
   int refine_max;    /* max refinement sweeps per CN step (0 = plain H-LU solve) */
 } hm_opts;

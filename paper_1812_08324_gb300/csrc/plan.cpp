@@ -146,6 +146,7 @@ int make_plan(const hm_problem& p, const hm_opts& o, Plan& P, std::string& err) 
   if (p.n[0] < 1 || (p.dim == 2 && p.n[1] < 1)) { err = "n must be positive"; return HM_ERR_ARG; }
   if (o.leaf < 1) { err = "leaf must be >= 1"; return HM_ERR_ARG; }
   if (!(o.eta > 0)) { err = "eta must be > 0"; return HM_ERR_ARG; }
+  if (o.precision != HM_FP64) { err = "only HM_FP64 storage is built"; return HM_ERR_ARG; }
   P = Plan();
   P.dim = p.dim;
   P.n[0] = p.n[0];

@@ -105,3 +105,11 @@ def test_bad_arguments_are_rejected(lib):
         hmat.plan_info(p, W.default_opts(leaf=0))
     with pytest.raises(hmat.HMError):
         hmat.plan_info(dict(p, s=1.5), W.default_opts())
+
+
+def test_unbuilt_precision_is_refused():
+    """Only FP64 storage is built: any other precision is an argument error,
+    never a silent FP64 run."""
+    prob = W.frac_lap_1d(255, 0.5)
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(prob, W.default_opts(leaf=32, precision="mixed_fp32"))
