@@ -226,6 +226,19 @@ int hm_entries(const hm_matrix* H, int64_t count, const int* rows, const int* co
 int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out);
 
 /*
+ * hm_factor_batch: hm_factor of `count` independent matrices in one
+ * persistent launch.  The H-LU operation graphs of all problems are planned
+ * on host threads and executed side by side by one dataflow schedule, so small
+ * problems share the GPU; out[i] equals hm_factor(H[i], theta[i]) bit for bit
+ * (the same operations in the same order of arithmetic).  out has count
+ * entries, each owning its device memory; on error all are NULL.  Device-side
+ * failures are reported through H[0]'s error word.  The paper has no batched
+ * form (it factors one problem at a time).
+ */
+int hm_factor_batch(const hm_matrix* const* H, const double* theta, int count, void* stream,
+                    hm_factors** out);
+
+/*
  * hm_solve: x = (L U)^{-1} b by the H-triangular solves of App. "LU
  * Decomposition" (forward then backward substitution over the block tree).
  * Natural-order device vectors; x may alias b.
@@ -253,6 +266,25 @@ int cn_step(const hm_matrix* H, const hm_factors* F, double dt, const double* u_
  */
 int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int step0, double* u,
              const double* f, void* stream);
+
+/*
+ * cn_solve_batch: `steps` Crank-Nicolson steps without forcing (Eq. scheme)
+ * of `count` independent problems sharing dt.  Per step: one batched
+ * H-matvec (three launches for all problems), one merged solve schedule (one
+ * persistent launch) and batched copies (plus the same per refinement sweep),
+ * recorded once as a CUDA graph and replayed `steps` times.  u[i] (device,
+ * natural order, N_i doubles) holds problem i's state and is updated in
+ * place; the u[i] must not overlap.  Each F[i] must come from
+ * hm_factor(H[i], -dt/2) or hm_factor_batch, and all H[i] must share
+ * opts.refine_max; HM_ERR_ARG otherwise.  Results equal count separate
+ * cn_solve calls bit for bit.
+ */
+int cn_solve_batch(const hm_matrix* const* H, const hm_factors* const* F, int count, double dt, int steps,
+                   double* const* u, void* stream);
+
+/* 1 if the last cn_solve_batch replayed its step as a CUDA graph, 0 if it
+ * launched every step directly (stream capture refused). */
+int hm_batch_graphed(void);
 
 /* Number of kernel launches this library has issued in the process so far
  * (every launch helper counts itself; a persistent schedule counts once). */

@@ -5,12 +5,16 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <thread>
 
 #include "api_common.h"
 #include "hlu_plan.h"
 #include "hm_device.cuh"
 
 using namespace hm;
+
+namespace { bool g_batch_graphed = false; }
 
 struct hm_factors {
   const hm_matrix* H = nullptr;
@@ -31,6 +35,10 @@ struct hm_factors {
   std::vector<int> h_rank;
   int capped = 0;
   double fact_ms = 0.0;
+  // host copy of the solve schedule, for merging into batched solves
+  std::vector<Wave> sw;
+  std::vector<RowSrc> srcs;
+  OpGraph sg;
 };
 
 namespace hm {
@@ -180,16 +188,110 @@ int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
-}  // namespace
-}  // namespace hm
+// ---- batched vector operations: y = x (mode 0) or y += a x (mode 1) for many
+// vectors in one launch, 2048 elements per CTA
 
-extern "C" {
+struct VecJob {
+  const double* x;
+  double* y;
+  double a;
+  int n;
+  int mode;
+};
 
-int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) {
-  if (!out || !H) { set_error("null argument"); return HM_ERR_ARG; }
-  *out = nullptr;
+__device__ __forceinline__ int batch_job_of(const int* off, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int VEC_CHUNK = 2048;
+
+__global__ void vec_batch_kernel(const VecJob* jobs, const int* off, int count) {
+  const int j = batch_job_of(off, count, blockIdx.x);
+  const VecJob J = jobs[j];
+  const int i0 = (blockIdx.x - off[j]) * VEC_CHUNK, i1 = min(J.n, i0 + VEC_CHUNK);
+  if (J.mode == 0) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] = J.x[i];
+  } else {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] += J.a * J.x[i];
+  }
+}
+
+// Device copy of a job table plus block offsets; freed by the owner.
+template <class Job>
+struct DevJobs {
+  Job* jobs = nullptr;
+  int* off = nullptr;
+  int total = 0;
+  int count = 0;
+};
+
+template <class Job, class Blocks>
+int upload_jobs(const std::vector<Job>& h, Blocks blocks, DevJobs<Job>& d, std::vector<void*>& allocs) {
+  std::vector<int> off(h.size() + 1, 0);
+  for (size_t i = 0; i < h.size(); ++i) off[i + 1] = off[i] + blocks(h[i]);
+  d.count = (int)h.size();
+  d.total = off.back();
+  if (cudaMalloc((void**)&d.jobs, sizeof(Job) * std::max<size_t>(h.size(), 1)) != cudaSuccess) return HM_ERR_OOM;
+  allocs.push_back(d.jobs);
+  if (cudaMalloc((void**)&d.off, sizeof(int) * off.size()) != cudaSuccess) return HM_ERR_OOM;
+  allocs.push_back(d.off);
+  if (!h.empty() && cudaMemcpy(d.jobs, h.data(), sizeof(Job) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return HM_ERR_CUDA;
+  if (cudaMemcpy(d.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return HM_ERR_CUDA;
+  return HM_OK;
+}
+
+int launch_vec_batch(const DevJobs<VecJob>& d, cudaStream_t st) {
+  if (d.total == 0) return HM_OK;
+  count_launches(1);
+  vec_batch_kernel<<<d.total, 256, 0, st>>>(d.jobs, d.off, d.count);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+// Batched H-matvec table: per job its plan, per launch kind its block offsets.
+int upload_mv_batch(const std::vector<MvJob>& h, MvBatch& B, std::vector<void*>& allocs) {
+  DevJobs<MvJob> d0, d1, d2;
+  HM_TRY(upload_jobs(h, [](const MvJob& J) { return J.P.nvt > 0 ? J.P.nvt : 0; }, d0, allocs));
+  HM_TRY(upload_jobs(h, [](const MvJob& J) { return J.P.nvt > 0 ? J.P.nlr : 0; }, d1, allocs));
+  HM_TRY(upload_jobs(h, [](const MvJob& J) { return J.P.nchunk; }, d2, allocs));
+  B.jobs = d0.jobs;
+  B.off[0] = d0.off;
+  B.off[1] = d1.off;
+  B.off[2] = d2.off;
+  B.total[0] = d0.total;
+  B.total[1] = d1.total;
+  B.total[2] = d2.total;
+  B.count = (int)h.size();
+  return HM_OK;
+}
+
+// ---- factorisation in phases (shared by hm_factor and hm_factor_batch)
+
+struct FactorJob {
+  const hm_matrix* H = nullptr;
+  hm_factors* F = nullptr;
+  HluBuild hb;
+  int status = HM_OK;
+  std::string err;
+};
+
+void factor_discard(FactorJob& J) {
+  if (!J.F) return;
+  for (void* p : J.F->allocs) cudaFree(p);
+  J.F->arena.release();
+  delete J.F;
+  J.F = nullptr;
+}
+
+// Rank cap, per-factor vectors and the copy of the ACA ranks (main thread).
+int factor_alloc(FactorJob& J, const hm_matrix* H, double theta, cudaStream_t st) {
   if (!std::isfinite(theta)) { set_error("theta must be finite"); return HM_ERR_ARG; }
-  cudaStream_t st = (cudaStream_t)stream;
   int maxr = 0;
   for (int r : H->h_rank) maxr = std::max(maxr, r);
   int kf = std::max(H->opts.lu_max_rank, maxr);
@@ -197,51 +299,165 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
     set_error("factor rank cap " + std::to_string(kf) + " exceeds " + std::to_string(TRUNC_MAXK / 2));
     return HM_ERR_RANK_CAP;
   }
-  kf = std::max(kf, 1);
-  hm_factors* F = new hm_factors();
+  J.H = H;
+  J.F = new hm_factors();
+  hm_factors* F = J.F;
   F->H = H;
   F->theta = theta;
-  F->kf = kf;
-  auto fail = [&](int s) {
-    cudaDeviceSynchronize();
-    for (void* p : F->allocs) cudaFree(p);
-    F->arena.release();
-    delete F;
-    return s;
-  };
+  F->kf = std::max(kf, 1);
   const int nlr = (int)H->h_ld.size();
   const int N = H->plan.N;
-  int s = HM_OK;
   auto alloc = [&](void** p, size_t bytes) {
     if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return HM_ERR_OOM;
     F->allocs.push_back(*p);
     return HM_OK;
   };
-  if ((s = alloc((void**)&F->d_rank, sizeof(int) * std::max(nlr, 1))) != HM_OK) return fail(s);
-  if ((s = alloc((void**)&F->d_y, sizeof(double) * N)) != HM_OK) return fail(s);
-  if ((s = alloc((void**)&F->d_sv, sizeof(double) * 4 * (size_t)N)) != HM_OK) return fail(s);
-  if ((s = alloc((void**)&F->d_vec, sizeof(double) * 6 * (size_t)N)) != HM_OK) return fail(s);
-  if ((s = alloc((void**)&F->d_norm, sizeof(double) * 4)) != HM_OK) return fail(s);
+  int s;
+  if ((s = alloc((void**)&F->d_rank, sizeof(int) * std::max(nlr, 1))) != HM_OK) return s;
+  if ((s = alloc((void**)&F->d_y, sizeof(double) * N)) != HM_OK) return s;
+  if ((s = alloc((void**)&F->d_sv, sizeof(double) * 4 * (size_t)N)) != HM_OK) return s;
+  if ((s = alloc((void**)&F->d_vec, sizeof(double) * 6 * (size_t)N)) != HM_OK) return s;
+  if ((s = alloc((void**)&F->d_norm, sizeof(double) * 4)) != HM_OK) return s;
   if (nlr && cudaMemcpyAsync(F->d_rank, H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return fail(HM_ERR_CUDA);
-  cudaMemsetAsync(F->d_norm, 0, sizeof(double) * 4, st);
+    return HM_ERR_CUDA;
+  if (cudaMemsetAsync(F->d_norm, 0, sizeof(double) * 4, st) != cudaSuccess) return HM_ERR_CUDA;
+  return HM_OK;
+}
 
+// H-LU planning (host; safe to run for different jobs on different threads).
+void factor_plan(FactorJob& J) {
+  const hm_matrix* H = J.H;
+  hm_factors* F = J.F;
+  J.status = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, F->kf, F->theta, H->opts.lu_tol,
+                      F->d_rank, F->arena, J.hb);
+  if (J.status != HM_OK) { J.err = J.hb.err; return; }
+  F->fact_ops = J.hb.ops;
+  F->fact_waves = (int)J.hb.waves.size();
+  F->F = J.hb.F;
+}
+
+// Solve planning once the factor ranks are on the host (thread-safe per job).
+void factor_plan_solve(FactorJob& J) {
+  const hm_matrix* H = J.H;
+  hm_factors* F = J.F;
+  const int N = H->plan.N;
+  SolveVectors sv{F->d_y, F->d_sv, F->d_sv + (size_t)N, F->d_sv + 2 * (size_t)N, F->d_sv + 3 * (size_t)N};
+  J.status = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, &F->h_rank, sv, F->arena, F->sw, F->srcs, F->sg);
+  if (J.status != HM_OK) { J.err = "solve planning failed"; return; }
+  F->solve_waves = (int)F->sw.size();
+  // bytes the two sweeps read: leaf inverses, off-diagonal dense blocks, low-rank factors
+  int64_t b = 0;
+  for (size_t d = 0; d < H->h_dd.size(); ++d) {
+    const DenseDesc& D = H->h_dd[d];
+    b += (int64_t)D.m * D.n * (D.r0 == D.c0 ? 2 : 1);
+  }
+  for (size_t q = 0; q < H->h_ld.size(); ++q) b += (int64_t)(H->h_ld[q].m + H->h_ld[q].n) * F->kf;
+  F->lu_bytes = 8 * b;
+}
+
+// Run fn(0..n-1) on up to hardware_concurrency host threads.
+template <class Fn>
+void parallel_for(int n, Fn fn) {
+  const int nt = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (int i = next++; i < n; i = next++) fn(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
+// Appends schedule (w, g[, s]) to (W, G[, S]): op ids shift by G's size, wave
+// k joins wave k, row tasks' source ranges shift by S's size.
+void merge_schedule(std::vector<Wave>& W, OpGraph& G, std::vector<RowSrc>* S, const std::vector<Wave>& w,
+                    const OpGraph& g, const std::vector<RowSrc>* s) {
+  const int off = (int)G.deps.size();
+  for (const std::vector<int>& d : g.deps) {
+    std::vector<int> v(d);
+    for (int& x : v) x += off;
+    G.deps.push_back(std::move(v));
+  }
+  const int soff = S ? (int)S->size() : 0;
+  if (W.size() < w.size()) W.resize(w.size());
+  for (size_t i = 0; i < w.size(); ++i) {
+    Wave& D = W[i];
+    const Wave& X = w[i];
+    for (size_t k = 0; k < X.gemm.size(); ++k) D.add(X.gemm[k], X.gemm_id[k] + off);
+    for (size_t k = 0; k < X.lu.size(); ++k) D.add(X.lu[k], X.lu_id[k] + off);
+    for (size_t k = 0; k < X.trunc.size(); ++k) D.add(X.trunc[k], X.trunc_id[k] + off);
+    for (size_t k = 0; k < X.copy.size(); ++k) D.add(X.copy[k], X.copy_id[k] + off);
+    for (size_t k = 0; k < X.reduce.size(); ++k) D.add(X.reduce[k], X.reduce_id[k] + off);
+    for (size_t k = 0; k < X.rows.size(); ++k) {
+      RowsOp o = X.rows[k];
+      o.src_begin += soff;
+      o.src_end += soff;
+      D.add(o, X.rows_id[k] + off);
+    }
+    for (size_t k = 0; k < X.vpart.size(); ++k) D.add(X.vpart[k], X.vpart_id[k] + off);
+  }
+  if (S && s) S->insert(S->end(), s->begin(), s->end());
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" {
+
+int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) {
+  return hm_factor_batch(&H, &theta, 1, stream, out);
+}
+
+int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count, void* stream,
+                    hm_factors** out) {
+  if (!out || !Hs || !thetas || count < 1) { set_error("bad argument"); return HM_ERR_ARG; }
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<FactorJob> jobs(count);
+  auto fail_all = [&](int s) {
+    cudaDeviceSynchronize();
+    for (FactorJob& J : jobs) factor_discard(J);
+    return s;
+  };
+  int s = HM_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!Hs[i]) { set_error("null matrix"); return fail_all(HM_ERR_ARG); }
+    if ((s = factor_alloc(jobs[i], Hs[i], thetas[i], st)) != HM_OK) return fail_all(s);
+  }
+  // host planning of every H-LU (independent problems: one host thread each)
+  parallel_for(count, [&](int i) { factor_plan(jobs[i]); });
+  for (FactorJob& J : jobs)
+    if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
+  // one schedule for all: the problems' operation graphs side by side
+  std::vector<Wave> waves;
+  OpGraph graph;
+  if (count == 1) {
+    waves.swap(jobs[0].hb.waves);
+    graph.deps.swap(jobs[0].hb.graph.deps);
+  } else {
+    for (FactorJob& J : jobs) {
+      merge_schedule(waves, graph, nullptr, J.hb.waves, J.hb.graph, nullptr);
+      std::vector<Wave>().swap(J.hb.waves);
+      std::vector<std::vector<int>>().swap(J.hb.graph.deps);
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  HluBuild hb;
-  s = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, kf, theta, H->opts.lu_tol,
-               F->d_rank, F->arena, hb);
-  if (s != HM_OK) { set_error(hb.err); return fail(s); }
   DevSchedule fs;
   std::vector<void*> fs_allocs;
-  s = upload_schedule(hb.waves, hb.graph, fs, fs_allocs);
+  s = upload_schedule(waves, graph, fs, fs_allocs);
+  int* d_err = Hs[0]->d_err;  // the batch shares the first matrix's error word
   const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
   if (s == HM_OK && tracing) {
-    trace_schedule("factor", hb.waves, hb.graph, fs, H->d_err, st);  // note: runs the factorisation
+    trace_schedule("factor", waves, graph, fs, d_err, st);  // note: runs the factorisation
   } else if (s == HM_OK) {
-    s = run_schedule(fs, H->d_err, st);
+    s = run_schedule(fs, d_err, st);
   }
   cudaEventRecord(e1, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
@@ -250,47 +466,181 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (void* p : fs_allocs) cudaFree(p);
-  if (s != HM_OK) { set_error("H-LU execution failed: " + std::string(cudaGetErrorString(cudaGetLastError()))); return fail(s); }
-  F->fact_ms = ms;
-  F->fact_ops = hb.ops;
-  F->fact_waves = (int)hb.waves.size();
-  F->F = hb.F;
+  if (s != HM_OK) {
+    set_error("H-LU execution failed: " + std::string(cudaGetErrorString(cudaGetLastError())));
+    return fail_all(s);
+  }
   int e = 0;
-  cudaMemcpy(&e, H->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e & DEVERR_ZEROPIVOT) { set_error("zero pivot in a leaf LU"); return fail(HM_ERR_DEVICE_ASSERT); }
+  cudaMemcpy(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e & DEVERR_ZEROPIVOT) { set_error("zero pivot in a leaf LU"); return fail_all(HM_ERR_DEVICE_ASSERT); }
+  if (e & DEVERR_TIMEOUT) { set_error("bounded wait gave up in the H-LU schedule"); return fail_all(HM_ERR_TIMEOUT); }
   if (e & DEVERR_RANKCAP) {
-    F->capped = 1;
     int z = e & ~DEVERR_RANKCAP;
-    cudaMemcpy(H->d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
   }
-  F->h_rank.assign(nlr, 0);
-  if (nlr) cudaMemcpy(F->h_rank.data(), F->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost);
-
-  // the solve schedule, replayed by every hm_solve
-  std::vector<Wave> sw;
-  std::vector<RowSrc> srcs;
-  OpGraph sg;
-  SolveVectors sv{F->d_y, F->d_sv, F->d_sv + (size_t)N, F->d_sv + 2 * (size_t)N, F->d_sv + 3 * (size_t)N};
-  s = plan_solve(H->plan, H->h_dd, H->h_ld, F->F, &F->h_rank, sv, F->arena, sw, srcs, sg);
-  if (s != HM_OK) { set_error("solve planning failed"); return fail(s); }
-  s = upload_schedule(sw, sg, F->solve, F->allocs, &srcs);
-  if (s != HM_OK) { set_error("solve schedule upload failed"); return fail(s); }
-  if (tracing) {
-    trace_schedule("solve", sw, sg, F->solve, H->d_err, st);
-    trace_schedule("solve", sw, sg, F->solve, H->d_err, st);
+  for (FactorJob& J : jobs) {
+    J.F->fact_ms = ms;
+    J.F->capped = (e & DEVERR_RANKCAP) ? 1 : 0;  // in a batch: some problem reached its cap
+    const int nlr = (int)J.H->h_ld.size();
+    J.F->h_rank.assign(nlr, 0);
+    if (nlr) cudaMemcpy(J.F->h_rank.data(), J.F->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost);
   }
-  F->solve_waves = (int)sw.size();
-  // bytes the two sweeps read: leaf inverses, off-diagonal dense blocks, low-rank factors
-  int64_t b = 0;
-  for (size_t d = 0; d < H->h_dd.size(); ++d) {
-    const DenseDesc& D = H->h_dd[d];
-    b += (int64_t)D.m * D.n * (D.r0 == D.c0 ? 2 : 1);
+  // the solve schedules (they read the factor ranks), planned in parallel
+  parallel_for(count, [&](int i) { factor_plan_solve(jobs[i]); });
+  for (FactorJob& J : jobs)
+    if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
+  for (FactorJob& J : jobs) {
+    hm_factors* F = J.F;
+    s = upload_schedule(F->sw, F->sg, F->solve, F->allocs, &F->srcs);
+    if (s != HM_OK) { set_error("solve schedule upload failed"); return fail_all(s); }
+    if (tracing && count == 1) {
+      trace_schedule("solve", F->sw, F->sg, F->solve, J.H->d_err, st);
+      trace_schedule("solve", F->sw, F->sg, F->solve, J.H->d_err, st);
+    }
   }
-  for (size_t q = 0; q < H->h_ld.size(); ++q) b += (int64_t)(H->h_ld[q].m + H->h_ld[q].n) * kf;
-  F->lu_bytes = 8 * b;
-  *out = F;
+  for (int i = 0; i < count; ++i) {
+    out[i] = jobs[i].F;
+    jobs[i].F = nullptr;
+  }
   return HM_OK;
 }
+
+int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int count, double dt, int steps,
+                   double* const* u, void* stream) {
+  if (!Hs || !Fs || !u || count < 1 || steps < 0 || !(dt > 0.0)) { set_error("bad argument"); return HM_ERR_ARG; }
+  const int R = Hs[0] ? Hs[0]->opts.refine_max : 0;
+  for (int i = 0; i < count; ++i) {
+    if (!Hs[i] || !Fs[i] || !u[i]) { set_error("null entry"); return HM_ERR_ARG; }
+    if (Fs[i]->H != Hs[i]) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
+    if (std::fabs(Fs[i]->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+      set_error("factors must come from hm_factor(H, -dt/2)");
+      return HM_ERR_ARG;
+    }
+    if (Hs[i]->opts.refine_max != R) { set_error("all matrices must share refine_max"); return HM_ERR_ARG; }
+    for (int j = 0; j < i; ++j)
+      if (Hs[j] == Hs[i] || Fs[j] == Fs[i]) { set_error("matrices and factors must be distinct"); return HM_ERR_ARG; }
+  }
+  if (steps == 0) return HM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double th = 0.5 * dt;
+  std::vector<void*> allocs;
+  auto cleanup = [&](int s) {
+    for (void* p : allocs) cudaFree(p);
+    return s;
+  };
+  // one solve schedule for all problems
+  std::vector<Wave> W;
+  OpGraph G;
+  std::vector<RowSrc> S;
+  for (int i = 0; i < count; ++i) merge_schedule(W, G, &S, Fs[i]->sw, Fs[i]->sg, &Fs[i]->srcs);
+  DevSchedule MS;
+  int s = upload_schedule(W, G, MS, allocs, &S);
+  if (s != HM_OK) { set_error("batched solve schedule upload failed"); return cleanup(s); }
+  std::vector<Wave>().swap(W);
+  std::vector<RowSrc>().swap(S);
+  // per problem: state x (Morton order), rhs, residual, refined iterate, solve output z
+  std::vector<MvJob> jA(count), jB(count);
+  std::vector<VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out, gath;
+  for (int i = 0; i < count; ++i) {
+    const hm_matrix* H = Hs[i];
+    hm_factors* F = const_cast<hm_factors*>(Fs[i]);
+    const int N = H->plan.N;
+    double* rhs = F->d_vec;
+    double* res = F->d_vec + (size_t)N;
+    double* u1 = F->d_vec + 2 * (size_t)N;
+    double* x = H->plan.dim == 1 ? u[i] : F->d_vec + 3 * (size_t)N;
+    double* z = F->d_sv + (size_t)N;
+    jA[i] = MvJob{H->mv, 1.0, th, th, x, nullptr, nullptr, nullptr, rhs};   // rhs = x + th G x
+    jB[i] = MvJob{H->mv, -1.0, th, 0.0, u1, nullptr, nullptr, rhs, res};    // res = rhs - (u1 - th G u1)
+    rhs_in.push_back({rhs, F->d_y, 0.0, N, 0});
+    s_in.push_back({res, F->d_y, 0.0, N, 0});
+    z_out.push_back({z, x, 0.0, N, 0});
+    z_u1.push_back({z, u1, 0.0, N, 0});
+    u1_add.push_back({z, u1, 1.0, N, 1});
+    u1_out.push_back({u1, x, 0.0, N, 0});
+  }
+  auto vblocks = [](const VecJob& J) { return (J.n + VEC_CHUNK - 1) / VEC_CHUNK; };
+  MvBatch A{}, B{};
+  DevJobs<VecJob> d_rhs, d_s, d_z, d_zu1, d_add, d_u1;
+  if ((s = upload_mv_batch(jA, A, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_mv_batch(jB, B, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(rhs_in, vblocks, d_rhs, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(s_in, vblocks, d_s, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(z_out, vblocks, d_z, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(z_u1, vblocks, d_zu1, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(u1_add, vblocks, d_add, allocs)) != HM_OK) return cleanup(s);
+  if ((s = upload_jobs(u1_out, vblocks, d_u1, allocs)) != HM_OK) return cleanup(s);
+  int* d_err = Hs[0]->d_err;
+  auto one_step = [&](cudaStream_t cs) -> int {
+    HM_TRY(launch_matvec_batch(A, cs));
+    HM_TRY(launch_vec_batch(d_rhs, cs));
+    HM_TRY(run_schedule(MS, d_err, cs));
+    if (R == 0) return launch_vec_batch(d_z, cs);
+    HM_TRY(launch_vec_batch(d_zu1, cs));
+    for (int it = 0; it < R; ++it) {
+      HM_TRY(launch_matvec_batch(B, cs));
+      HM_TRY(launch_vec_batch(d_s, cs));
+      HM_TRY(run_schedule(MS, d_err, cs));
+      HM_TRY(launch_vec_batch(d_add, cs));
+    }
+    return launch_vec_batch(d_u1, cs);
+  };
+  if ((s = prepare_executor(MS)) != HM_OK) return cleanup(s);
+  // a private stream ordered after the caller's stream (the caller's may be the legacy default stream)
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cleanup(HM_ERR_CUDA);
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, st);
+  cudaStreamWaitEvent(cs, ev, 0);
+  for (int i = 0; i < count; ++i)
+    if (Hs[i]->plan.dim != 1 && s == HM_OK)
+      s = launch_gather(Hs[i]->d_perm, Hs[i]->plan.N, u[i], const_cast<hm_factors*>(Fs[i])->d_vec + 3 * (size_t)Hs[i]->plan.N, cs);
+  // record one step as a CUDA graph and replay it
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t per_step = 0;
+  if (s == HM_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const int64_t l0 = hm_launch_count();
+    const int sc = one_step(cs);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    per_step = hm_launch_count() - l0;
+    count_launches(-(int)per_step);  // counted when the graph runs
+    if (sc != HM_OK || ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (gexec) cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+    }
+  } else {
+    cudaGetLastError();
+  }
+  g_batch_graphed = gexec != nullptr;
+  for (int k = 0; k < steps && s == HM_OK; ++k) {
+    if (gexec) {
+      s = cudaGraphLaunch(gexec, cs) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+      count_launches((int)per_step);
+    } else {
+      s = one_step(cs);
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (Hs[i]->plan.dim != 1 && s == HM_OK)
+      s = launch_scatter(Hs[i]->d_perm, Hs[i]->plan.N, const_cast<hm_factors*>(Fs[i])->d_vec + 3 * (size_t)Hs[i]->plan.N, u[i], cs);
+  if (cudaStreamSynchronize(cs) != cudaSuccess && s == HM_OK) s = HM_ERR_CUDA;
+  cudaEventRecord(ev, cs);
+  cudaStreamWaitEvent(st, ev, 0);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(cs);
+  if (s != HM_OK) set_error("batched CN steps failed: " + std::string(cudaGetErrorString(cudaGetLastError())));
+  int e = 0;
+  cudaMemcpy(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (s == HM_OK && (e & DEVERR_TIMEOUT)) { set_error("bounded wait gave up in a solve"); s = HM_ERR_TIMEOUT; }
+  return cleanup(s);
+}
+
+int hm_batch_graphed(void) { return g_batch_graphed ? 1 : 0; }
 
 void hm_factors_free(hm_factors* F) {
   if (!F) return;

@@ -1034,22 +1034,34 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
   return HM_OK;
 }
 
+namespace {
+int g_exec_grid[2] = {0, 0};
+}
+
+int prepare_executor(const DevSchedule& S) {
+  const int m = S.solve_only ? 1 : 0;
+  if (g_exec_grid[m] != 0) return HM_OK;
+  void* fn = m ? (void*)exec_kernel<true> : (void*)exec_kernel<false>;
+  const size_t smem = m ? SOLVE_SMEM : EXEC_SMEM;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HM_ERR_CUDA;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXEC_THREADS, smem) != cudaSuccess || per < 1)
+    return HM_ERR_CUDA;
+  g_exec_grid[m] = sms * per;
+  return HM_OK;
+}
+
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned long long* trace) {
   if (S.ntasks == 0) return HM_OK;
-  static int grid[2] = {0, 0};
   const int m = S.solve_only ? 1 : 0;
   void* fn = m ? (void*)exec_kernel<true> : (void*)exec_kernel<false>;
   const size_t smem = m ? SOLVE_SMEM : EXEC_SMEM;
-  if (grid[m] == 0) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return HM_ERR_CUDA;
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXEC_THREADS, smem) != cudaSuccess || per < 1)
-      return HM_ERR_CUDA;
-    grid[m] = sms * per;
-  }
+  int s = prepare_executor(S);
+  if (s != HM_OK) return s;
+  int* grid = g_exec_grid;
   // counters[nops] is the task dispenser
   if (cudaMemsetAsync(S.counters, 0, sizeof(int) * (S.nops + 1), st) != cudaSuccess) return HM_ERR_CUDA;
   ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.wave_begin,

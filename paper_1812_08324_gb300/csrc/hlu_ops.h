@@ -198,6 +198,10 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedul
 // Run a schedule in one persistent cooperative launch (one CTA per SM).  Every
 // wait is bounded in time: on expiry the kernel sets DEVERR_TIMEOUT in *d_err
 // and returns instead of hanging.
+// Kernel attributes and grid size of the executor for S (done once per kind;
+// also done by run_schedule, but must precede any stream capture).
+int prepare_executor(const DevSchedule& S);
+
 constexpr int TRACE_STRIDE = 8;  // trace words per task
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st,
                  unsigned long long* trace = nullptr);

@@ -58,6 +58,27 @@ struct MatvecPlan {
 int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* x, double gamma,
                   const double* w1, const double* w2, const double* w3, double* y, cudaStream_t st);
 
+// One H-matvec of a batch: y = alpha x + beta (H x) + gamma (w1 + w2) (+ w3).
+struct MvJob {
+  MatvecPlan P;
+  double alpha, beta, gamma;
+  const double* x;
+  const double* w1;
+  const double* w2;
+  const double* w3;
+  double* y;
+};
+// Device job table of a batch and, per launch kind (V'x tasks, reductions,
+// row chunks), the first block of every job (count + 1 entries) and the total.
+// Jobs without V'x tasks contribute no blocks to the first two launches.
+struct MvBatch {
+  const MvJob* jobs;
+  const int* off[3];
+  int total[3];
+  int count;
+};
+int launch_matvec_batch(const MvBatch& B, cudaStream_t st);
+
 // Fixed scratch of hm_matvec_noalloc: capacity in doubles and device address
 // (looked up on first use per device).
 size_t noalloc_capacity();

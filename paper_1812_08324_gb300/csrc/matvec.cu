@@ -16,51 +16,45 @@ namespace hm {
 
 namespace {
 
-__global__ void __launch_bounds__(256)
-vt_kernel(const VTask* vt, const LRDesc* ld, const int* rank, const double* Vpool,
-          const double* __restrict__ x, double* partial) {
+// ---- bodies shared by the single and the batched launches
+
+__device__ __forceinline__ void vt_body(const MatvecPlan& P, int task, const double* __restrict__ x) {
   __shared__ double xs[VT_CHUNK];
-  const VTask T = vt[blockIdx.x];
-  const LRDesc L = ld[T.lr];
-  const int k = rank[T.lr];
+  const VTask T = P.vt[task];
+  const LRDesc L = P.ld[T.lr];
+  const int k = P.rank[T.lr];
   const double* xc = x + L.c0 + T.c_lo;
   for (int j = threadIdx.x; j < T.len; j += blockDim.x) xs[j] = xc[j];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const double* V = Vpool + L.voff + T.c_lo;
+  const double* V = P.V + L.voff + T.c_lo;
   for (int l = warp; l < k; l += nwarp) {
     const double* Vl = V + (int64_t)l * L.n;
     double acc = 0.0;
     for (int j = lane; j < T.len; j += 32) acc += Vl[j] * xs[j];
     acc = warp_sum(acc);
-    if (lane == 0) partial[(int64_t)T.out * ACA_MAXK + l] = acc;
+    if (lane == 0) P.partial[(int64_t)T.out * ACA_MAXK + l] = acc;
   }
 }
 
-__global__ void vt_reduce_kernel(int nlr, const int* vt_range, const int* rank,
-                                 const double* partial, double* tvec) {
-  int q = blockIdx.x;
-  if (q >= nlr) return;
-  int b = vt_range[2 * q], e = vt_range[2 * q + 1];
-  int k = rank[q];
+__device__ __forceinline__ void vt_reduce_body(const MatvecPlan& P, int q) {
+  const int b = P.vt_range[2 * q], e = P.vt_range[2 * q + 1];
+  const int k = P.rank[q];
   for (int l = threadIdx.x; l < k; l += blockDim.x) {
     double acc = 0.0;
-    for (int o = b; o < e; ++o) acc += partial[(int64_t)o * ACA_MAXK + l];
-    tvec[(int64_t)q * ACA_MAXK + l] = acc;
+    for (int o = b; o < e; ++o) acc += P.partial[(int64_t)o * ACA_MAXK + l];
+    P.tvec[(int64_t)q * ACA_MAXK + l] = acc;
   }
 }
 
 constexpr int ROWS_PER_WARP = MV_CHUNK / 8;  // 8 warps x 4 rows
 
-__global__ void __launch_bounds__(256)
-rows_kernel(const RowChunk* chunks, const int* dense_items, const int* lr_items,
-            const DenseDesc* dd, const double* Dpool, const LRDesc* ld, const int* rank,
-            const double* Upool, const double* tvec, double alpha, double beta,
-            const double* __restrict__ x, double gamma, const double* w1, const double* w2,
-            const double* w3, double* y) {
+__device__ __forceinline__ void rows_body(const MatvecPlan& P, int chunk, double alpha, double beta,
+                                          const double* __restrict__ x, double gamma, const double* w1,
+                                          const double* w2, const double* w3, double* y) {
   __shared__ double acc_d[MV_CHUNK];
   __shared__ double acc_f[8][MV_CHUNK];
-  const RowChunk C = chunks[blockIdx.x];
+  const RowChunk C = P.chunks[chunk];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < MV_CHUNK) acc_d[threadIdx.x] = 0.0;
   acc_f[warp][lane] = 0.0;
@@ -72,10 +66,10 @@ rows_kernel(const RowChunk* chunks, const int* dense_items, const int* lr_items,
   for (int r = 0; r < ROWS_PER_WARP; ++r) rsum[r] = 0.0;
   const int rw0 = warp * ROWS_PER_WARP;
   for (int it = C.dense_begin; it < C.dense_end; ++it) {
-    const DenseDesc D = dd[dense_items[it]];
+    const DenseDesc D = P.dd[P.dense_items[it]];
     const int i0 = C.r0 - D.r0 + rw0;
     const double* xc = x + D.c0;
-    const double* base = Dpool + D.off + (int64_t)i0 * D.ld;
+    const double* base = P.D + D.off + (int64_t)i0 * D.ld;
     // 16-byte loads over column pairs; D.ld is a multiple of 4, D.off even
     const int npair = D.n >> 1;
     for (int p = lane; p < npair; p += 32) {
@@ -104,13 +98,13 @@ rows_kernel(const RowChunk* chunks, const int* dense_items, const int* lr_items,
   // ---- low-rank blocks: warp per block, lane per row
   double facc = 0.0;
   for (int it = C.lr_begin + warp; it < C.lr_end; it += 8) {
-    const int q = lr_items[it];
-    const LRDesc L = ld[q];
-    const int k = rank[q];
+    const int q = P.lr_items[it];
+    const LRDesc L = P.ld[q];
+    const int k = P.rank[q];
     const int i = C.r0 - L.r0 + lane;
     if (lane < C.nrow) {
-      const double* U = Upool + L.uoff + i;
-      const double* t = tvec + (int64_t)q * ACA_MAXK;
+      const double* U = P.U + L.uoff + i;
+      const double* t = P.tvec + (int64_t)q * ACA_MAXK;
       for (int l = 0; l < k; ++l) facc += U[(int64_t)l * L.m] * t[l];
     }
   }
@@ -128,6 +122,48 @@ rows_kernel(const RowChunk* chunks, const int* dense_items, const int* lr_items,
     if (w3) out += w3[row];
     y[row] = out;
   }
+}
+
+__global__ void __launch_bounds__(256) vt_kernel(MatvecPlan P, const double* __restrict__ x) {
+  vt_body(P, blockIdx.x, x);
+}
+
+__global__ void vt_reduce_kernel(MatvecPlan P) {
+  if ((int)blockIdx.x < P.nlr) vt_reduce_body(P, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+rows_kernel(MatvecPlan P, double alpha, double beta, const double* __restrict__ x, double gamma, const double* w1,
+            const double* w2, const double* w3, double* y) {
+  rows_body(P, blockIdx.x, alpha, beta, x, gamma, w1, w2, w3, y);
+}
+
+// ---- batched: many independent H-matvecs in three launches.  off[j] is the
+// first block of job j in the launch (kind: 0 = V'x tasks, 1 = reductions,
+// 2 = row chunks), off[count] the total.
+__device__ __forceinline__ int batch_job(const int* off, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) vt_batch_kernel(const MvJob* jobs, const int* off, int count) {
+  const int j = batch_job(off, count, blockIdx.x);
+  vt_body(jobs[j].P, blockIdx.x - off[j], jobs[j].x);
+}
+
+__global__ void vt_reduce_batch_kernel(const MvJob* jobs, const int* off, int count) {
+  const int j = batch_job(off, count, blockIdx.x);
+  vt_reduce_body(jobs[j].P, blockIdx.x - off[j]);
+}
+
+__global__ void __launch_bounds__(256) rows_batch_kernel(const MvJob* jobs, const int* off, int count) {
+  const int j = batch_job(off, count, blockIdx.x);
+  const MvJob& J = jobs[j];
+  rows_body(J.P, blockIdx.x - off[j], J.alpha, J.beta, J.x, J.gamma, J.w1, J.w2, J.w3, J.y);
 }
 
 __global__ void gather_kernel(const int* perm, int N, const double* src, double* dst) {
@@ -174,11 +210,21 @@ int launch_matvec(const MatvecPlan& P, double alpha, double beta, const double* 
                   cudaStream_t st) {
   count_launches(P.nvt > 0 ? 3 : 1);
   if (P.nvt > 0) {
-    vt_kernel<<<P.nvt, 256, 0, st>>>(P.vt, P.ld, P.rank, P.V, x, P.partial);
-    vt_reduce_kernel<<<P.nlr, 64, 0, st>>>(P.nlr, P.vt_range, P.rank, P.partial, P.tvec);
+    vt_kernel<<<P.nvt, 256, 0, st>>>(P, x);
+    vt_reduce_kernel<<<P.nlr, 64, 0, st>>>(P);
   }
-  rows_kernel<<<P.nchunk, 256, 0, st>>>(P.chunks, P.dense_items, P.lr_items, P.dd, P.D, P.ld,
-                                        P.rank, P.U, P.tvec, alpha, beta, x, gamma, w1, w2, w3, y);
+  rows_kernel<<<P.nchunk, 256, 0, st>>>(P, alpha, beta, x, gamma, w1, w2, w3, y);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_matvec_batch(const MvBatch& B, cudaStream_t st) {
+  if (B.count == 0) return HM_OK;
+  count_launches(B.total[0] > 0 ? 3 : 1);
+  if (B.total[0] > 0) {
+    vt_batch_kernel<<<B.total[0], 256, 0, st>>>(B.jobs, B.off[0], B.count);
+    vt_reduce_batch_kernel<<<B.total[1], 64, 0, st>>>(B.jobs, B.off[1], B.count);
+  }
+  rows_batch_kernel<<<B.total[2], 256, 0, st>>>(B.jobs, B.off[2], B.count);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

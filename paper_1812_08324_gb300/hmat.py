@@ -22,7 +22,7 @@ EXPORTED = [
     "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
     "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor", "hm_launch_count",
-    "hm_matvec_noalloc",
+    "hm_matvec_noalloc", "hm_factor_batch", "cn_solve_batch", "hm_batch_graphed",
 ]
 
 
@@ -102,6 +102,9 @@ def load() -> C.CDLL:
         "hm_plan_factor": (i, [P, O, d, C.POINTER(FactorPlan)]),
         "hm_launch_count": (i64, []),
         "hm_matvec_noalloc": (i, [vp, d, d, vp, d, vp, vp, vp, vp]),
+        "hm_factor_batch": (i, [C.POINTER(vp), C.POINTER(d), i, vp, C.POINTER(vp)]),
+        "cn_solve_batch": (i, [C.POINTER(vp), C.POINTER(vp), i, d, i, C.POINTER(vp), vp]),
+        "hm_batch_graphed": (i, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -275,10 +278,13 @@ class HMatrix:
 class Factors:
     """H-LU factors of I + theta G (owned by the library)."""
 
-    def __init__(self, H: HMatrix, theta: float, stream=None):
+    def __init__(self, H: HMatrix, theta: float, stream=None, _handle=None):
         self.H = H
         self.theta = theta
         self._f = C.c_void_p()
+        if _handle is not None:
+            self._f = C.c_void_p(_handle)
+            return
         _check(load().hm_factor(H.handle, theta, _stream(stream), C.byref(self._f)))
 
     def solve(self, b, out=None, stream=None):
@@ -315,3 +321,29 @@ def cn_solve(H: HMatrix, F: Factors, dt: float, steps: int, u, f=None, step0: in
     _check(load().cn_solve(H.handle, F._f, dt, int(steps), int(step0), _ptr(u), _ptr(f),
                            _stream(stream)))
     return u
+
+
+def factor_batch(Hs, thetas, stream=None):
+    """H-LU factors of I + theta_i G_i for many matrices in one persistent launch;
+    returns one Factors per matrix (each equal to H.factor(theta) bit for bit)."""
+    n = len(Hs)
+    hs = (C.c_void_p * n)(*[H.handle.value for H in Hs])
+    th = (C.c_double * n)(*[float(t) for t in thetas])
+    out = (C.c_void_p * n)()
+    _check(load().hm_factor_batch(hs, th, n, _stream(stream), out))
+    return [Factors(H, t, _handle=out[i]) for i, (H, t) in enumerate(zip(Hs, thetas))]
+
+
+def cn_solve_batch(Hs, Fs, dt: float, steps: int, us, stream=None):
+    """Advance every us[i] in place by `steps` CN steps (no forcing), all
+    problems per step in one batched H-matvec and one merged solve launch."""
+    n = len(Hs)
+    hs = (C.c_void_p * n)(*[H.handle.value for H in Hs])
+    fs = (C.c_void_p * n)(*[F._f.value for F in Fs])
+    ps = (C.c_void_p * n)(*[_ptr(u) for u in us])
+    _check(load().cn_solve_batch(hs, fs, n, float(dt), int(steps), ps, _stream(stream)))
+    return us
+
+
+def batch_graphed() -> bool:
+    return bool(load().hm_batch_graphed())

@@ -125,6 +125,61 @@ WORKLOADS = {
 }
 
 
+# ----------------------------------------------------------------------------
+# Workload 4: many independent 1D Levy solves (batched), parameters drawn by
+# splitmix64 (seed 0) in the order N, alpha, b, sigma per solve
+# ----------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea, Flood 2014): state += 0x9E3779B97F4A7C15, then
+    two xor-shift-multiply rounds; uniform doubles from the top 53 bits."""
+
+    def __init__(self, seed: int = 0):
+        self.state = seed & _M64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _M64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        return z ^ (z >> 31)
+
+    def uniform(self, a: float = 0.0, b: float = 1.0) -> float:
+        return a + (b - a) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+
+def batch_leaf(n: int) -> int:
+    """Leaf size of a batched solve by problem size (the rule the leaf autotuner
+    starts from; see autotune.py)."""
+    return 256 if n >= 8192 else (128 if n >= 2048 else 64)
+
+
+def levy_batch(count: int = 512, seed: int = 0, log2_lo: float = 10.0, log2_hi: float = 15.0):
+    """The batched workload: per solve N = round(2^U(10,15)), alpha ~ U(0.5,1.9),
+    b ~ U(-1,1), sigma ~ U(0,0.5); truncation 2, u0 = exp(-50 x^2),
+    dt = 1/500, 500 steps; ACA rank <= 32, factor rank <= 16.  Returns a list
+    of (problem, options); dt and steps are LEVY_BATCH_DT / LEVY_BATCH_STEPS."""
+    g = SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(2.0 ** g.uniform(log2_lo, log2_hi)))
+        alpha = g.uniform(0.5, 1.9)
+        b = g.uniform(-1.0, 1.0)
+        sigma = g.uniform(0.0, 0.5)
+        prob = levy_1d(n, sigma=sigma, b=b, alpha=alpha)
+        opts = default_opts(leaf=batch_leaf(n), aca_tol=1e-10, max_rank=32, lu_tol=1e-10, lu_max_rank=16,
+                            refine_max=0)
+        out.append((prob, opts))
+    return out
+
+
+LEVY_BATCH_DT = 1.0 / 500
+LEVY_BATCH_STEPS = 500
+
+
 def initial_data(prob: dict, kind: str) -> np.ndarray:
     if kind == "unit_ball":
         return manufactured_unit_ball(prob)[0]

@@ -1,0 +1,89 @@
+"""Batched factorisation and CN steps: every problem's result equals the
+one-problem path bit for bit, and a small member matches the dense oracle."""
+import numpy as np
+import pytest
+
+from oracle import levy_dense as O
+from paper_1812_08324_gb300 import hmat, workloads as W
+
+from gpu_util import dev, host, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _small_batch(count=6):
+    # the batched workload's parameter stream at sizes the oracle can check
+    return W.levy_batch(count, seed=0, log2_lo=8.0, log2_hi=11.0)
+
+
+def test_factor_batch_equals_single():
+    batch = _small_batch()
+    dt = W.LEVY_BATCH_DT
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    Fb = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+    rng = np.random.default_rng(3)
+    for H, Fi in zip(Hs, Fb):
+        F1 = H.factor(-0.5 * dt)
+        b = dev(rng.standard_normal(H.n))
+        x1 = host(F1.solve(b))
+        xb = host(Fi.solve(b))
+        assert np.array_equal(x1, xb)
+        assert H.stats(Fi)["lu_max_rank_seen"] == H.stats(F1)["lu_max_rank_seen"]
+
+
+def test_cn_solve_batch_equals_single_and_oracle():
+    batch = _small_batch()
+    dt, steps = W.LEVY_BATCH_DT, 20
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+    u0s = [W.gaussian_u0(p, 50.0) for p, _ in batch]
+    ub = [dev(u) for u in u0s]
+    hmat.cn_solve_batch(Hs, Fs, dt, steps, ub)
+    torch.cuda.synchronize()
+    for H, F, u0, u in zip(Hs, Fs, u0s, ub):
+        us = dev(u0)
+        hmat.cn_solve(H, F, dt, steps, us)
+        assert np.array_equal(host(us), host(u)), "batched CN differs from the single path"
+    # the smallest member against the dense oracle
+    i = int(np.argmin([p["n"][0] for p, _ in batch]))
+    G = O.generator_dense(batch[i][0])
+    ref = O.cn_solve(G, u0s[i], dt, steps)
+    err = np.linalg.norm(host(ub[i]) - ref) / np.linalg.norm(ref)
+    assert err < 1e-8, err
+
+
+def test_cn_solve_batch_mixed_1d_2d_with_refinement():
+    """A 2D member exercises the Morton gather/scatter; one refinement sweep
+    exercises the residual path; results still equal the single path."""
+    dt, steps = 1e-3, 5
+    probs = [(W.frac_lap_2d(24, 0.75), W.default_opts(leaf=36, aca_tol=1e-9, max_rank=32, lu_max_rank=32,
+                                                        refine_max=1)),
+             (W.levy_1d(700, sigma=0.3, b=-0.4, alpha=1.2), W.default_opts(leaf=64, max_rank=32, lu_max_rank=16,
+                                                                             refine_max=1))]
+    Hs = [hmat.HMatrix(p, o) for p, o in probs]
+    Fs = [H.factor(-0.5 * dt) for H in Hs]
+    u0s = [W.bump_u0(probs[0][0]), W.gaussian_u0(probs[1][0], 50.0)]
+    ub = [dev(u) for u in u0s]
+    hmat.cn_solve_batch(Hs, Fs, dt, steps, ub)
+    torch.cuda.synchronize()
+    for H, F, u0, u in zip(Hs, Fs, u0s, ub):
+        us = dev(u0)
+        hmat.cn_solve(H, F, dt, steps, us)
+        assert np.array_equal(host(us), host(u))
+
+
+def test_cn_solve_batch_rejects_bad_input():
+    batch = _small_batch(2)
+    dt = W.LEVY_BATCH_DT
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    Fs = hmat.factor_batch(Hs, [-0.5 * dt] * 2)
+    us = [dev(W.gaussian_u0(p, 50.0)) for p, _ in batch]
+    with pytest.raises(hmat.HMError):      # factors of another dt
+        hmat.cn_solve_batch(Hs, Fs, 2 * dt, 3, us)
+    with pytest.raises(hmat.HMError):      # the same problem twice
+        hmat.cn_solve_batch([Hs[0], Hs[0]], [Fs[0], Fs[0]], dt, 3, us)

@@ -113,3 +113,17 @@ def test_unbuilt_precision_is_refused():
     prob = W.frac_lap_1d(255, 0.5)
     with pytest.raises(hmat.HMError):
         hmat.plan_info(prob, W.default_opts(leaf=32, precision="mixed_fp32"))
+
+
+def test_splitmix64_published_outputs_and_batch_stream():
+    """splitmix64 with seed 0 gives the reference implementation's first
+    outputs; the batched workload's parameters stay in their ranges."""
+    g = W.SplitMix64(0)
+    assert [g.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    batch = W.levy_batch(512)
+    ns = np.array([p["n"][0] for p, _ in batch])
+    assert ns.min() >= 1024 and ns.max() <= 32768
+    assert 4.0e6 < ns.sum() < 5.2e6
+    for p, o in batch[:32]:
+        assert 0.25 <= p["s"] <= 0.95 and -1 <= p["b"][0] <= 1 and 0 <= p["a"] <= 0.125
+    assert W.levy_batch(4) == W.levy_batch(4)
