@@ -533,8 +533,12 @@ int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int 
   OpGraph G;
   std::vector<RowSrc> S;
   for (int i = 0; i < count; ++i) merge_schedule(W, G, &S, Fs[i]->sw, Fs[i]->sg, &Fs[i]->srcs);
+  // many independent chains: the throughput mode (more CTAs per SM, smaller
+  // staging; staging changes where operands are read from, not the arithmetic)
+  for (Wave& w : W)
+    for (RowsOp& o : w.rows) plan_rows_staging(o, S.data() + o.src_begin, SOLVE_MODE_THROUGHPUT);
   DevSchedule MS;
-  int s = upload_schedule(W, G, MS, allocs, &S);
+  int s = upload_schedule(W, G, MS, allocs, &S, SOLVE_MODE_THROUGHPUT);
   if (s != HM_OK) { set_error("batched solve schedule upload failed"); return cleanup(s); }
   std::vector<Wave>().swap(W);
   std::vector<RowSrc>().swap(S);

@@ -575,14 +575,14 @@ struct RowsSmem {
   double* dyn;      // gathered dynamic inputs
 };
 
-__device__ __forceinline__ RowsSmem rows_smem(double* smem) {
+__device__ __forceinline__ RowsSmem rows_smem(double* smem, int pre_cap) {
   RowsSmem L;
   L.acc_d = smem;
   L.acc_l = smem + 32;
   L.wsum = smem + 32 + 256;
   L.srcs = reinterpret_cast<RowSrc*>(smem + 32 + 256 + 512);
   L.pre = smem + 32 + 256 + 512 + ROWS_MAX_SRC * (sizeof(RowSrc) / sizeof(double));
-  L.dyn = L.pre + ROWS_PREFETCH_DOUBLES;
+  L.dyn = L.pre + pre_cap;
   return L;
 }
 
@@ -590,8 +590,8 @@ __device__ __forceinline__ int dyn_start(const RowSrc& S) { return S.dyn_off >= 
 
 // Before the wait: stage the descriptors and start the asynchronous copies of
 // the static rows; they complete while the CTA waits for its producers.
-__device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double* smem) {
-  RowsSmem L = rows_smem(smem);
+__device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double* smem, int pre_cap) {
+  RowsSmem L = rows_smem(smem, pre_cap);
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   {
     const int words = nsrc * (int)(sizeof(RowSrc) / sizeof(long long));
@@ -613,8 +613,8 @@ __device__ void dev_rows_prefetch(const RowsOp& op, const RowSrc* srcs_g, double
 
 // After the wait: gather every dynamic input (x vectors, partial products,
 // base rows) with eight independent loads in flight per thread.
-__device__ void dev_rows_gather(const RowsOp& op, double* smem) {
-  RowsSmem L = rows_smem(smem);
+__device__ void dev_rows_gather(const RowsOp& op, double* smem, int pre_cap) {
+  RowsSmem L = rows_smem(smem, pre_cap);
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   const int total = op.dyn_total;
   for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
@@ -648,10 +648,10 @@ __device__ void dev_rows_gather(const RowsOp& op, double* smem) {
 }
 
 // ts (tracing only, else nullptr): times after the gather and after the sums
-__device__ void dev_rows(const RowsOp& op, double* smem, unsigned long long* ts) {
-  RowsSmem L = rows_smem(smem);
+__device__ void dev_rows(const RowsOp& op, double* smem, int pre_cap, unsigned long long* ts) {
+  RowsSmem L = rows_smem(smem, pre_cap);
   cp_async_wait_all();
-  dev_rows_gather(op, smem);
+  dev_rows_gather(op, smem, pre_cap);
   if (ts && threadIdx.x == 0) ts[0] = global_ns();
   const int nsrc = min(op.src_end - op.src_begin, ROWS_MAX_SRC);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -731,20 +731,18 @@ __device__ void dev_rows(const RowsOp& op, double* smem, unsigned long long* ts)
 
 // V' y over one piece: V (static) is copied to shared memory before the
 // wait (when it fits), y is gathered after it.
-constexpr int VPART_SMEM =
-    SOLVE_CTAS_PER_SM == 1 ? 16384 : SOLVE_CTAS_PER_SM == 2 ? 8192 : SOLVE_CTAS_PER_SM == 3 ? 6144 : 4096;
-__device__ void dev_vpart_prefetch(const VPartOp& op, double* smem) {
-  if (op.len * op.kf > VPART_SMEM) return;
+__device__ void dev_vpart_prefetch(const VPartOp& op, double* smem, int vcap) {
+  if (op.len * op.kf > vcap) return;
   for (int e = threadIdx.x; e < op.len * op.kf; e += blockDim.x) {
     const int l = e / op.len, r = e % op.len;
     cp_async8(smem + e, op.V + l * op.ldv + r);
   }
 }
 
-__device__ void dev_vpart(const VPartOp& op, double* smem) {
-  const bool pre = op.len * op.kf <= VPART_SMEM;
+__device__ void dev_vpart(const VPartOp& op, double* smem, int vcap) {
+  const bool pre = op.len * op.kf <= vcap;
   cp_async_wait_all();
-  double* ys = smem + VPART_SMEM;
+  double* ys = smem + vcap;
   for (int r0 = threadIdx.x; r0 < op.len; r0 += 8 * blockDim.x) {
     double v[8];
 #pragma unroll
@@ -771,12 +769,16 @@ __device__ void dev_vpart(const VPartOp& op, double* smem) {
 constexpr int EXEC_THREADS = 256;
 constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
                              sizeof(int) * 7 * TRUNC_MAXK;
-// solve schedules (row, partial-product, reduction, copy tasks): SOLVE_CTAS_PER_SM CTAs per SM
-constexpr size_t ROWS_SMEM = sizeof(double) * (32 + 256 + 512 + ROWS_PREFETCH_DOUBLES + ROWS_DYN_DOUBLES) +
-                             sizeof(RowSrc) * ROWS_MAX_SRC;
-constexpr size_t VPART_SMEM_BYTES = sizeof(double) * (VPART_SMEM + 256);
-constexpr size_t SOLVE_SMEM = ROWS_SMEM > VPART_SMEM_BYTES ? ROWS_SMEM : VPART_SMEM_BYTES;
-static_assert(SOLVE_CTAS_PER_SM * (SOLVE_SMEM + 1024) <= 228 * 1024, "solve executor shared memory");
+// shared memory of a solve mode: the larger of a row task's and a partial-product task's needs
+constexpr size_t rows_smem_bytes(int m) {
+  return sizeof(double) * (32 + 256 + 512 + mode_prefetch(m) + mode_dyn(m)) + sizeof(RowSrc) * ROWS_MAX_SRC;
+}
+constexpr size_t vpart_smem_bytes(int m) { return sizeof(double) * (mode_vpart(m) + 256); }
+constexpr size_t mode_smem(int m) {
+  return m == 0 ? EXEC_SMEM : (rows_smem_bytes(m) > vpart_smem_bytes(m) ? rows_smem_bytes(m) : vpart_smem_bytes(m));
+}
+static_assert(mode_ctas(1) * (mode_smem(1) + 1024) <= 228 * 1024, "latency solve mode shared memory");
+static_assert(mode_ctas(2) * (mode_smem(2) + 1024) <= 228 * 1024, "throughput solve mode shared memory");
 constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;  // 4 s for one dependency wait
 #ifndef HM_POLL_NS
 #define HM_POLL_NS 0  // pause between two polls of a producer counter (build-time tuning parameter)
@@ -852,8 +854,9 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
 
 // Tasks are taken in topological order from a global counter, so a CTA
 // waiting on a producer never holds up a task that is ready elsewhere.
-template <bool SOLVE>
-__global__ void __launch_bounds__(EXEC_THREADS, SOLVE ? SOLVE_CTAS_PER_SM : 1) exec_kernel(ExecArgs a) {
+template <int MODE>
+__global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(ExecArgs a) {
+  constexpr bool SOLVE = MODE != 0;
   extern __shared__ double smem[];
   __shared__ int next;
   for (;;) {
@@ -870,8 +873,10 @@ __global__ void __launch_bounds__(EXEC_THREADS, SOLVE ? SOLVE_CTAS_PER_SM : 1) e
       asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
       a.trace[TRACE_STRIDE * (size_t)t + 6] = sm;
     }
-    if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem);
-    if (T.kind == TK_VPART) dev_vpart_prefetch(a.vpart[T.op], smem);
+    if constexpr (SOLVE) {
+      if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem, mode_prefetch(MODE));
+      if (T.kind == TK_VPART) dev_vpart_prefetch(a.vpart[T.op], smem, mode_vpart(MODE));
+    }
     if (!wait_deps(a, T.id)) {
       cp_async_wait_all();  // no copy may outlive the CTA
       return;
@@ -888,8 +893,13 @@ __global__ void __launch_bounds__(EXEC_THREADS, SOLVE ? SOLVE_CTAS_PER_SM : 1) e
     switch (T.kind) {
       case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
       case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
-      case TK_ROWS: dev_rows(a.rows[T.op], smem, a.trace ? a.trace + TRACE_STRIDE * (size_t)t + 4 : nullptr); break;
-      case TK_VPART: dev_vpart(a.vpart[T.op], smem); break;
+      case TK_ROWS:
+        if constexpr (SOLVE)
+          dev_rows(a.rows[T.op], smem, mode_prefetch(MODE), a.trace ? a.trace + TRACE_STRIDE * (size_t)t + 4 : nullptr);
+        break;
+      case TK_VPART:
+        if constexpr (SOLVE) dev_vpart(a.vpart[T.op], smem, mode_vpart(MODE));
+        break;
       default: break;
     }
     __syncthreads();
@@ -902,20 +912,21 @@ __global__ void __launch_bounds__(EXEC_THREADS, SOLVE ? SOLVE_CTAS_PER_SM : 1) e
 
 }  // namespace
 
-void plan_rows_staging(RowsOp& op, RowSrc* src) {
+void plan_rows_staging(RowsOp& op, RowSrc* src, int mode) {
+  const int pre_cap = mode_prefetch(mode), dyn_cap = mode_dyn(mode);
   const int nsrc = op.src_end - op.src_begin;
   int used = 0, dused = 0;
   for (int s = 0; s < nsrc; ++s) {
     RowSrc& S = src[s];
     const int need = op.nr * (S.nparts ? S.ncols + 1 : S.ncols);
-    if (s < ROWS_MAX_SRC && used + need <= ROWS_PREFETCH_DOUBLES) {
+    if (s < ROWS_MAX_SRC && used + need <= pre_cap) {
       S.pre_off = used;
       used += need;
     } else {
       S.pre_off = -1;
     }
     const int dneed = S.nparts ? S.nparts * S.ncols : S.ncols;
-    if (s < ROWS_MAX_SRC && dused + dneed <= ROWS_DYN_DOUBLES - 32) {
+    if (s < ROWS_MAX_SRC && dused + dneed <= dyn_cap - 32) {
       S.dyn_off = dused;
       dused += dneed;
     } else {
@@ -934,7 +945,7 @@ int gemm_tiles(int m, int n) {
 }
 
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSchedule& S,
-                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs) {
+                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs, int mode) {
   std::vector<RowsOp> ro;
   std::vector<VPartOp> vp;
   std::vector<GemmOp> g;
@@ -1025,7 +1036,7 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
   if ((s = up(srcs ? *srcs : nos, &S.srcs)) != HM_OK) return s;
   if ((s = up(tasks, &S.tasks)) != HM_OK) return s;
   S.host_tasks = tasks;
-  S.solve_only = g.empty() && l.empty() && tr.empty();
+  S.mode = (g.empty() && l.empty() && tr.empty()) ? (mode == SOLVE_MODE_THROUGHPUT ? 2 : 1) : 0;
   if ((s = up(wb, &S.wave_begin)) != HM_OK) return s;
   if ((s = up(info, &S.ops)) != HM_OK) return s;
   if ((s = up(deps, &S.deps)) != HM_OK) return s;
@@ -1035,14 +1046,17 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
 }
 
 namespace {
-int g_exec_grid[2] = {0, 0};
+int g_exec_grid[EXEC_MODES] = {0, 0, 0};
+void* exec_fn(int m) {
+  return m == 0 ? (void*)exec_kernel<0> : (m == 1 ? (void*)exec_kernel<1> : (void*)exec_kernel<2>);
+}
 }
 
 int prepare_executor(const DevSchedule& S) {
-  const int m = S.solve_only ? 1 : 0;
+  const int m = S.mode;
   if (g_exec_grid[m] != 0) return HM_OK;
-  void* fn = m ? (void*)exec_kernel<true> : (void*)exec_kernel<false>;
-  const size_t smem = m ? SOLVE_SMEM : EXEC_SMEM;
+  void* fn = exec_fn(m);
+  const size_t smem = mode_smem(m);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HM_ERR_CUDA;
   int dev = 0, sms = 0, per = 0;
@@ -1050,15 +1064,15 @@ int prepare_executor(const DevSchedule& S) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXEC_THREADS, smem) != cudaSuccess || per < 1)
     return HM_ERR_CUDA;
-  g_exec_grid[m] = sms * per;
+  g_exec_grid[m] = sms * std::min(per, mode_ctas(m));
   return HM_OK;
 }
 
 int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned long long* trace) {
   if (S.ntasks == 0) return HM_OK;
-  const int m = S.solve_only ? 1 : 0;
-  void* fn = m ? (void*)exec_kernel<true> : (void*)exec_kernel<false>;
-  const size_t smem = m ? SOLVE_SMEM : EXEC_SMEM;
+  const int m = S.mode;
+  void* fn = exec_fn(m);
+  const size_t smem = mode_smem(m);
   int s = prepare_executor(S);
   if (s != HM_OK) return s;
   int* grid = g_exec_grid;

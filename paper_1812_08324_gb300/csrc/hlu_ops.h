@@ -95,23 +95,23 @@ struct RowsOp {
   int dyn_base, dyn_total;  // gathered base rows start at dyn_base; dyn_total doubles in all
 };
 
-// Executor CTAs per SM for solve schedules (build-time tuning parameter), and
-// the shared-memory staging of a row task (doubles) sized to fit that many.
-#ifndef HM_SOLVE_CTAS
-#define HM_SOLVE_CTAS 2
-#endif
-constexpr int SOLVE_CTAS_PER_SM = HM_SOLVE_CTAS;
-static_assert(SOLVE_CTAS_PER_SM >= 1 && SOLVE_CTAS_PER_SM <= 4, "1 to 4 solve CTAs per SM");
-constexpr int ROWS_PREFETCH_DOUBLES =  // copied matrix rows
-    SOLVE_CTAS_PER_SM == 1 ? 8192 : SOLVE_CTAS_PER_SM == 2 ? 6144 : SOLVE_CTAS_PER_SM == 3 ? 4096 : 3072;
-constexpr int ROWS_DYN_DOUBLES =       // gathered inputs: x vectors, partials, base rows
-    SOLVE_CTAS_PER_SM == 1 ? 10240 : SOLVE_CTAS_PER_SM == 2 ? 5120 : SOLVE_CTAS_PER_SM == 3 ? 3584 : 2560;
+// Executor modes: 0 runs H-LU schedules (one CTA per SM, 225 KB shared
+// memory); the solve modes trade shared-memory staging for CTAs per SM:
+// mode 1 (latency: one solve) two CTAs per SM, mode 2 (throughput: batched
+// solves) four.  Staging of a row task (doubles): copied matrix rows, gathered
+// inputs; and the copied V rows of a partial-product task.
+constexpr int EXEC_MODES = 3;
+constexpr int SOLVE_MODE_LATENCY = 1, SOLVE_MODE_THROUGHPUT = 2;
+__host__ __device__ constexpr int mode_ctas(int m) { return m == 0 ? 1 : (m == 1 ? 2 : 4); }
+__host__ __device__ constexpr int mode_prefetch(int m) { return m == 1 ? 6144 : 3072; }
+__host__ __device__ constexpr int mode_dyn(int m) { return m == 1 ? 5120 : 2560; }
+__host__ __device__ constexpr int mode_vpart(int m) { return m == 1 ? 8192 : 4096; }
 constexpr int ROWS_MAX_SRC = 64;
 
 // Lays out the staging of one row task: the rows of M of each source go to
 // shared memory while they fit (low-rank rows padded to ncols + 1 against bank
 // conflicts), and so do the source vectors and the base rows.
-void plan_rows_staging(RowsOp& op, RowSrc* src);
+void plan_rows_staging(RowsOp& op, RowSrc* src, int mode);
 
 // part[l] = sum_{r < len} V[r + l * ldv] y[r], l < kf.
 struct VPartOp {
@@ -189,11 +189,13 @@ struct DevSchedule {
   int* deps = nullptr;
   int* counters = nullptr;   // per op: finished tasks
   std::vector<Task> host_tasks;  // the task list in hand-out order (for tracing)
-  bool solve_only = false;       // only row, partial-product, reduction and copy tasks
+  int mode = 0;                  // executor mode (0: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
 };
 
+// mode: executor mode of a solve schedule (ignored when the schedule holds H-LU operations).
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedule& S,
-                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs = nullptr);
+                    std::vector<void*>& allocs, const std::vector<RowSrc>* srcs = nullptr,
+                    int mode = SOLVE_MODE_LATENCY);
 
 // Run a schedule in one persistent cooperative launch (one CTA per SM).  Every
 // wait is bounded in time: on expiry the kernel sets DEVERR_TIMEOUT in *d_err

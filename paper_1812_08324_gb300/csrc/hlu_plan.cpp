@@ -1047,7 +1047,7 @@ class SolvePlanner {
         srcs.push_back(r);
       }
       o.src_end = (int)srcs.size();
-      plan_rows_staging(o, srcs.data() + o.src_begin);
+      plan_rows_staging(o, srcs.data() + o.src_begin, SOLVE_MODE_LATENCY);
       at(ph).add(o, id);
     }
   }

@@ -87,3 +87,21 @@ def test_cn_solve_batch_rejects_bad_input():
         hmat.cn_solve_batch(Hs, Fs, 2 * dt, 3, us)
     with pytest.raises(hmat.HMError):      # the same problem twice
         hmat.cn_solve_batch([Hs[0], Hs[0]], [Fs[0], Fs[0]], dt, 3, us)
+
+
+def test_autotune_picks_a_candidate_and_batch_stays_exact():
+    from paper_1812_08324_gb300 import autotune
+    batch = _small_batch(3)
+    dt = W.LEVY_BATCH_DT
+    leafs = autotune.tune_batch(batch, dt, 50, candidates=(32, 64), probe_steps=2)
+    assert all(l in (32, 64) for l in leafs)
+    tuned = [(p, dict(o, leaf=l)) for (p, o), l in zip(batch, leafs)]
+    Hs = [hmat.HMatrix(p, o) for p, o in tuned]
+    Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+    us = [dev(W.gaussian_u0(p, 50.0)) for p, _ in tuned]
+    hmat.cn_solve_batch(Hs, Fs, dt, 10, us)
+    assert hmat.batch_graphed()
+    for (p, o), u in zip(tuned, us):
+        G = O.generator_dense(p)
+        ref = O.cn_solve(G, W.gaussian_u0(p, 50.0), dt, 10)
+        assert np.linalg.norm(host(u) - ref) / np.linalg.norm(ref) < 1e-8
