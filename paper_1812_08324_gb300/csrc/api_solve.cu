@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <chrono>
 #include <thread>
 
 #include "api_common.h"
@@ -372,36 +373,6 @@ void parallel_for(int n, Fn fn) {
   for (auto& th : pool) th.join();
 }
 
-// Appends schedule (w, g[, s]) to (W, G[, S]): op ids shift by G's size, wave
-// k joins wave k, row tasks' source ranges shift by S's size.
-void merge_schedule(std::vector<Wave>& W, OpGraph& G, std::vector<RowSrc>* S, const std::vector<Wave>& w,
-                    const OpGraph& g, const std::vector<RowSrc>* s) {
-  const int off = (int)G.deps.size();
-  for (const std::vector<int>& d : g.deps) {
-    std::vector<int> v(d);
-    for (int& x : v) x += off;
-    G.deps.push_back(std::move(v));
-  }
-  const int soff = S ? (int)S->size() : 0;
-  if (W.size() < w.size()) W.resize(w.size());
-  for (size_t i = 0; i < w.size(); ++i) {
-    Wave& D = W[i];
-    const Wave& X = w[i];
-    for (size_t k = 0; k < X.gemm.size(); ++k) D.add(X.gemm[k], X.gemm_id[k] + off);
-    for (size_t k = 0; k < X.lu.size(); ++k) D.add(X.lu[k], X.lu_id[k] + off);
-    for (size_t k = 0; k < X.trunc.size(); ++k) D.add(X.trunc[k], X.trunc_id[k] + off);
-    for (size_t k = 0; k < X.copy.size(); ++k) D.add(X.copy[k], X.copy_id[k] + off);
-    for (size_t k = 0; k < X.reduce.size(); ++k) D.add(X.reduce[k], X.reduce_id[k] + off);
-    for (size_t k = 0; k < X.rows.size(); ++k) {
-      RowsOp o = X.rows[k];
-      o.src_begin += soff;
-      o.src_end += soff;
-      D.add(o, X.rows_id[k] + off);
-    }
-    for (size_t k = 0; k < X.vpart.size(); ++k) D.add(X.vpart[k], X.vpart_id[k] + off);
-  }
-  if (S && s) S->insert(S->end(), s->begin(), s->end());
-}
 
 }  // namespace
 }  // namespace hm
@@ -417,6 +388,16 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
   if (!out || !Hs || !thetas || count < 1) { set_error("bad argument"); return HM_ERR_ARG; }
   for (int i = 0; i < count; ++i) out[i] = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
+  // HM_TIME_PHASES=1: host wall time of every phase on stderr
+  const bool timing = std::getenv("HM_TIME_PHASES") != nullptr;
+  auto tp = std::chrono::steady_clock::now();
+  auto phase = [&](const char* what) {
+    if (!timing) return;
+    cudaStreamSynchronize(st);
+    auto t = std::chrono::steady_clock::now();
+    fprintf(stderr, "[factor x%d] %-14s %8.1f ms\n", count, what, std::chrono::duration<double, std::milli>(t - tp).count());
+    tp = t;
+  };
   std::vector<FactorJob> jobs(count);
   auto fail_all = [&](int s) {
     cudaDeviceSynchronize();
@@ -429,33 +410,26 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
     if ((s = factor_alloc(jobs[i], Hs[i], thetas[i], st)) != HM_OK) return fail_all(s);
   }
   // host planning of every H-LU (independent problems: one host thread each)
+  phase("allocate");
   parallel_for(count, [&](int i) { factor_plan(jobs[i]); });
   for (FactorJob& J : jobs)
     if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
+  phase("plan H-LU");
   // one schedule for all: the problems' operation graphs side by side
-  std::vector<Wave> waves;
-  OpGraph graph;
-  if (count == 1) {
-    waves.swap(jobs[0].hb.waves);
-    graph.deps.swap(jobs[0].hb.graph.deps);
-  } else {
-    for (FactorJob& J : jobs) {
-      merge_schedule(waves, graph, nullptr, J.hb.waves, J.hb.graph, nullptr);
-      std::vector<Wave>().swap(J.hb.waves);
-      std::vector<std::vector<int>>().swap(J.hb.graph.deps);
-    }
-  }
+  std::vector<SchedPart> parts;
+  for (FactorJob& J : jobs) parts.push_back(SchedPart{&J.hb.waves, &J.hb.graph, nullptr});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
   DevSchedule fs;
   std::vector<void*> fs_allocs;
-  s = upload_schedule(waves, graph, fs, fs_allocs);
+  s = upload_schedules(parts, fs, fs_allocs, 0, false);
+  phase("upload");
   int* d_err = Hs[0]->d_err;  // the batch shares the first matrix's error word
   const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
-  if (s == HM_OK && tracing) {
-    trace_schedule("factor", waves, graph, fs, d_err, st);  // note: runs the factorisation
+  if (s == HM_OK && tracing && count == 1) {
+    trace_schedule("factor", jobs[0].hb.waves, jobs[0].hb.graph, fs, d_err, st);  // note: runs the factorisation
   } else if (s == HM_OK) {
     s = run_schedule(fs, d_err, st);
   }
@@ -466,6 +440,11 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (void* p : fs_allocs) cudaFree(p);
+  for (FactorJob& J : jobs) {
+    std::vector<Wave>().swap(J.hb.waves);
+    std::vector<std::vector<int>>().swap(J.hb.graph.deps);
+  }
+  phase("run H-LU");
   if (s != HM_OK) {
     set_error("H-LU execution failed: " + std::string(cudaGetErrorString(cudaGetLastError())));
     return fail_all(s);
@@ -486,9 +465,11 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
     if (nlr) cudaMemcpy(J.F->h_rank.data(), J.F->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost);
   }
   // the solve schedules (they read the factor ranks), planned in parallel
+  phase("ranks");
   parallel_for(count, [&](int i) { factor_plan_solve(jobs[i]); });
   for (FactorJob& J : jobs)
     if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
+  phase("plan solves");
   for (FactorJob& J : jobs) {
     hm_factors* F = J.F;
     s = upload_schedule(F->sw, F->sg, F->solve, F->allocs, &F->srcs);
@@ -498,6 +479,7 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
       trace_schedule("solve", F->sw, F->sg, F->solve, J.H->d_err, st);
     }
   }
+  phase("upload solves");
   for (int i = 0; i < count; ++i) {
     out[i] = jobs[i].F;
     jobs[i].F = nullptr;
@@ -528,20 +510,14 @@ int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int 
     for (void* p : allocs) cudaFree(p);
     return s;
   };
-  // one solve schedule for all problems
-  std::vector<Wave> W;
-  OpGraph G;
-  std::vector<RowSrc> S;
-  for (int i = 0; i < count; ++i) merge_schedule(W, G, &S, Fs[i]->sw, Fs[i]->sg, &Fs[i]->srcs);
-  // many independent chains: the throughput mode (more CTAs per SM, smaller
-  // staging; staging changes where operands are read from, not the arithmetic)
-  for (Wave& w : W)
-    for (RowsOp& o : w.rows) plan_rows_staging(o, S.data() + o.src_begin, SOLVE_MODE_THROUGHPUT);
+  // one solve schedule for all problems, in the throughput mode (more CTAs per
+  // SM, smaller staging; staging changes where operands are read from, not
+  // the arithmetic)
+  std::vector<SchedPart> parts;
+  for (int i = 0; i < count; ++i) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
   DevSchedule MS;
-  int s = upload_schedule(W, G, MS, allocs, &S, SOLVE_MODE_THROUGHPUT);
+  int s = upload_schedules(parts, MS, allocs, SOLVE_MODE_THROUGHPUT, true);
   if (s != HM_OK) { set_error("batched solve schedule upload failed"); return cleanup(s); }
-  std::vector<Wave>().swap(W);
-  std::vector<RowSrc>().swap(S);
   // per problem: state x (Morton order), rhs, residual, refined iterate, solve output z
   std::vector<MvJob> jA(count), jB(count);
   std::vector<VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out, gath;

@@ -1,6 +1,7 @@
 // Batched executors of the H-LU schedule (FP64): strided GEMM tiles, leaf LU
 // with triangular inverses, low-rank truncation cores, copies and reductions.
 #include <algorithm>
+#include <cstdlib>
 
 #include "hm_device.cuh"
 #include "hlu_ops.h"
@@ -946,6 +947,11 @@ int gemm_tiles(int m, int n) {
 
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSchedule& S,
                     std::vector<void*>& allocs, const std::vector<RowSrc>* srcs, int mode) {
+  return upload_schedules({SchedPart{&waves, &graph, srcs}}, S, allocs, mode, false);
+}
+
+int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::vector<void*>& allocs, int mode,
+                     bool restage) {
   std::vector<RowsOp> ro;
   std::vector<VPartOp> vp;
   std::vector<GemmOp> g;
@@ -955,63 +961,96 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
   std::vector<ReduceOp> r;
   std::vector<Task> tasks;
   std::vector<int> wb;
-  const int nops = (int)graph.deps.size();
+  std::vector<RowSrc> msrc;
+  // op id and row-source offsets of every part
+  std::vector<int> off(parts.size() + 1, 0), soff(parts.size() + 1, 0);
+  size_t nw = 0;
+  for (size_t p = 0; p < parts.size(); ++p) {
+    off[p + 1] = off[p] + (int)parts[p].graph->deps.size();
+    soff[p + 1] = soff[p] + (parts[p].srcs ? (int)parts[p].srcs->size() : 0);
+    nw = std::max(nw, parts[p].waves->size());
+  }
+  const int nops = off.back();
   std::vector<OpInfo> info(std::max(nops, 1), OpInfo{0, 0, 0, 0});
   std::vector<int> deps;
-  for (int id = 0; id < nops; ++id) {
-    info[id].dep_begin = (int)deps.size();
-    for (int d : graph.deps[id]) deps.push_back(d);
-    info[id].dep_end = (int)deps.size();
+  size_t ndeps = 0;
+  for (const SchedPart& P : parts)
+    for (const auto& d : P.graph->deps) ndeps += d.size();
+  deps.reserve(ndeps);
+  for (size_t p = 0; p < parts.size(); ++p) {
+    const auto& gd = parts[p].graph->deps;
+    for (size_t i = 0; i < gd.size(); ++i) {
+      const int id = off[p] + (int)i;
+      info[id].dep_begin = (int)deps.size();
+      for (int d : gd[i]) deps.push_back(d + off[p]);
+      info[id].dep_end = (int)deps.size();
+    }
+  }
+  if (soff.back() > 0) {
+    msrc.reserve(soff.back());
+    for (const SchedPart& P : parts)
+      if (P.srcs) msrc.insert(msrc.end(), P.srcs->begin(), P.srcs->end());
   }
   // copies and reductions are split so that one task does about 2048 FP64
   // operations (a few microseconds on one SM)
   auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
-  for (const Wave& W : waves) {
+  for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
-    for (size_t k = 0; k < W.gemm.size(); ++k) {
-      const GemmOp& o = W.gemm[k];
-      int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k];
-      for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
-      info[id].ntasks = nt;
-      g.push_back(o);
-    }
-    for (size_t k = 0; k < W.lu.size(); ++k) {
-      tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k]});
-      info[W.lu_id[k]].ntasks = 1;
-      l.push_back(W.lu[k]);
-    }
-    for (size_t k = 0; k < W.trunc.size(); ++k) {
-      tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k]});
-      info[W.trunc_id[k]].ntasks = 1;
-      tr.push_back(W.trunc[k]);
-    }
-    for (size_t k = 0; k < W.copy.size(); ++k) {
-      const CopyOp& o = W.copy[k];
-      int nc = chunks((int64_t)o.m * o.n), id = W.copy_id[k];
-      for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc, id});
-      info[id].ntasks = nc;
-      c.push_back(o);
-    }
-    for (size_t k = 0; k < W.reduce.size(); ++k) {
-      const ReduceOp& o = W.reduce[k];
-      int nc = chunks((int64_t)o.m * o.n * std::max(o.nparts, 1)), id = W.reduce_id[k];
-      for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
-      info[id].ntasks = nc;
-      r.push_back(o);
-    }
-    for (size_t k = 0; k < W.rows.size(); ++k) {
-      tasks.push_back({TK_ROWS, (int)ro.size(), 0, W.rows[k].nr, W.rows_id[k]});  // nsub: rows of the chunk
-      info[W.rows_id[k]].ntasks += 1;  // the chunks of one row op share its id
-      ro.push_back(W.rows[k]);
-    }
-    for (size_t k = 0; k < W.vpart.size(); ++k) {
-      tasks.push_back({TK_VPART, (int)vp.size(), 0, 1, W.vpart_id[k]});
-      info[W.vpart_id[k]].ntasks = 1;
-      vp.push_back(W.vpart[k]);
+    for (size_t p = 0; p < parts.size(); ++p) {
+      if (w >= parts[p].waves->size()) continue;
+      const Wave& W = (*parts[p].waves)[w];
+      const int o0 = off[p];
+      for (size_t k = 0; k < W.gemm.size(); ++k) {
+        GemmOp o = W.gemm[k];
+        o.shape = gemm_shape(o.m, o.n);
+        int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k] + o0;
+        for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
+        info[id].ntasks = nt;
+        g.push_back(o);
+      }
+      for (size_t k = 0; k < W.lu.size(); ++k) {
+        tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k] + o0});
+        info[W.lu_id[k] + o0].ntasks = 1;
+        l.push_back(W.lu[k]);
+      }
+      for (size_t k = 0; k < W.trunc.size(); ++k) {
+        tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k] + o0});
+        info[W.trunc_id[k] + o0].ntasks = 1;
+        tr.push_back(W.trunc[k]);
+      }
+      for (size_t k = 0; k < W.copy.size(); ++k) {
+        const CopyOp& o = W.copy[k];
+        int nc = chunks((int64_t)o.m * o.n), id = W.copy_id[k] + o0;
+        for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc, id});
+        info[id].ntasks = nc;
+        c.push_back(o);
+      }
+      for (size_t k = 0; k < W.reduce.size(); ++k) {
+        const ReduceOp& o = W.reduce[k];
+        int nc = chunks((int64_t)o.m * o.n * std::max(o.nparts, 1)), id = W.reduce_id[k] + o0;
+        for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
+        info[id].ntasks = nc;
+        r.push_back(o);
+      }
+      for (size_t k = 0; k < W.rows.size(); ++k) {
+        RowsOp o = W.rows[k];
+        o.src_begin += soff[p];
+        o.src_end += soff[p];
+        if (restage) plan_rows_staging(o, msrc.data() + o.src_begin, mode);
+        const int id = W.rows_id[k] + o0;
+        tasks.push_back({TK_ROWS, (int)ro.size(), 0, o.nr, id});  // nsub: rows of the chunk
+        info[id].ntasks += 1;  // the chunks of one row op share its id
+        ro.push_back(o);
+      }
+      for (size_t k = 0; k < W.vpart.size(); ++k) {
+        tasks.push_back({TK_VPART, (int)vp.size(), 0, 1, W.vpart_id[k] + o0});
+        info[W.vpart_id[k] + o0].ntasks = 1;
+        vp.push_back(W.vpart[k]);
+      }
     }
   }
   wb.push_back((int)tasks.size());
-  S.nwaves = (int)waves.size();
+  S.nwaves = (int)nw;
   S.nops = nops;
   S.ntasks = (int64_t)tasks.size();
   auto up = [&](auto& vec, auto** dst) -> int {
@@ -1024,24 +1063,23 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
     *dst = (std::remove_reference_t<decltype(**dst)>*)p;
     return HM_OK;
   };
-  int s;
-  if ((s = up(g, &S.gemm)) != HM_OK) return s;
-  if ((s = up(l, &S.lu)) != HM_OK) return s;
-  if ((s = up(tr, &S.trunc)) != HM_OK) return s;
-  if ((s = up(c, &S.copy)) != HM_OK) return s;
-  if ((s = up(r, &S.reduce)) != HM_OK) return s;
-  if ((s = up(ro, &S.rows)) != HM_OK) return s;
-  if ((s = up(vp, &S.vpart)) != HM_OK) return s;
-  std::vector<RowSrc> nos;
-  if ((s = up(srcs ? *srcs : nos, &S.srcs)) != HM_OK) return s;
-  if ((s = up(tasks, &S.tasks)) != HM_OK) return s;
-  S.host_tasks = tasks;
+  int st;
+  if ((st = up(g, &S.gemm)) != HM_OK) return st;
+  if ((st = up(l, &S.lu)) != HM_OK) return st;
+  if ((st = up(tr, &S.trunc)) != HM_OK) return st;
+  if ((st = up(c, &S.copy)) != HM_OK) return st;
+  if ((st = up(r, &S.reduce)) != HM_OK) return st;
+  if ((st = up(ro, &S.rows)) != HM_OK) return st;
+  if ((st = up(vp, &S.vpart)) != HM_OK) return st;
+  if ((st = up(msrc, &S.srcs)) != HM_OK) return st;
+  if ((st = up(tasks, &S.tasks)) != HM_OK) return st;
   S.mode = (g.empty() && l.empty() && tr.empty()) ? (mode == SOLVE_MODE_THROUGHPUT ? 2 : 1) : 0;
-  if ((s = up(wb, &S.wave_begin)) != HM_OK) return s;
-  if ((s = up(info, &S.ops)) != HM_OK) return s;
-  if ((s = up(deps, &S.deps)) != HM_OK) return s;
+  if (std::getenv("HM_PHASE_TRACE")) S.host_tasks.swap(tasks);  // kept for tracing only
+  if ((st = up(wb, &S.wave_begin)) != HM_OK) return st;
+  if ((st = up(info, &S.ops)) != HM_OK) return st;
+  if ((st = up(deps, &S.deps)) != HM_OK) return st;
   std::vector<int> cnt(nops + 1, 0);
-  if ((s = up(cnt, &S.counters)) != HM_OK) return s;
+  if ((st = up(cnt, &S.counters)) != HM_OK) return st;
   return HM_OK;
 }
 

@@ -192,6 +192,19 @@ struct DevSchedule {
   int mode = 0;                  // executor mode (0: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
 };
 
+// One schedule among several uploaded side by side (independent problems):
+// its waves, producer graph and row-task sources.
+struct SchedPart {
+  const std::vector<Wave>* waves;
+  const OpGraph* graph;
+  const std::vector<RowSrc>* srcs;
+};
+// Uploads the parts as one schedule: op ids shift by the ops of the parts
+// before, wave k of every part joins wave k, row tasks' sources shift
+// likewise; restage: re-plan row-task staging for `mode`.
+int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::vector<void*>& allocs, int mode,
+                     bool restage);
+
 // mode: executor mode of a solve schedule (ignored when the schedule holds H-LU operations).
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedule& S,
                     std::vector<void*>& allocs, const std::vector<RowSrc>* srcs = nullptr,

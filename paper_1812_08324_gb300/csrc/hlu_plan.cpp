@@ -623,6 +623,60 @@ class HLU {
     }
   }
 
+  // ---- X <- L_l^{-1} [D | I] for the diagonal block l: X (rows(l) x (c0 +
+  // rows(l))) holds arbitrary columns D in [0, c0) and, implicitly, the identity
+  // of l's rows in [c0, c0 + rows(l)); the columns after that are zero and
+  // stay zero (the inverse is lower triangular), so they are not touched.
+  void linv_ident(int l, const View& X, int c0) {
+    const Block& L = B(l);
+    const int m = rows(l);
+    if (L.type == BT_DENSE) {
+      if (c0 > 0) {
+        View Tm = E.tmp(m, c0, false);
+        E.gemm(Tm, 1.0, linv[L.id], X.sub(0, 0, m, c0), 0.0);
+        E.copy(X.sub(0, 0, m, c0), 1.0, &Tm, 0.0);
+        E.release(Tm);
+      }
+      E.copy(X.sub(0, c0, m, m), 1.0, &linv[L.id], 0.0);  // L^{-1} I
+      return;
+    }
+    for (int a = 0; a < L.nrc; ++a) {
+      const int la = child(l, a, a), ra = roff(l, la), w = c0 + ra + rows(la);
+      View Xa = X.sub(ra, 0, rows(la), w);
+      linv_ident(la, Xa, c0 + ra);
+      for (int a2 = a + 1; a2 < L.nrc; ++a2) {
+        const int lb = child(l, a2, a);
+        hgemm(X.sub(roff(l, lb), 0, rows(lb), w), -1.0, lb, Xa);
+      }
+    }
+  }
+
+  // ---- Y <- U_u^{-T} [D | I], the same for the transposed upper factor
+  void uinvt_ident(int u, const View& Y, int c0) {
+    const Block& U = B(u);
+    const int m = rows(u);
+    if (U.type == BT_DENSE) {
+      View UiT = uinv[U.id].T();
+      if (c0 > 0) {
+        View Tm = E.tmp(m, c0, false);
+        E.gemm(Tm, 1.0, UiT, Y.sub(0, 0, m, c0), 0.0);
+        E.copy(Y.sub(0, 0, m, c0), 1.0, &Tm, 0.0);
+        E.release(Tm);
+      }
+      E.copy(Y.sub(0, c0, m, m), 1.0, &UiT, 0.0);  // U^{-T} I
+      return;
+    }
+    for (int a = 0; a < U.nrc; ++a) {
+      const int ua = child(u, a, a), ra = roff(u, ua), w = c0 + ra + rows(ua);
+      View Ya = Y.sub(ra, 0, rows(ua), w);
+      uinvt_ident(ua, Ya, c0 + ra);
+      for (int a2 = a + 1; a2 < U.nrc; ++a2) {
+        const int ub = child(u, a, a2);  // U_{a, a2}; rows of Y_{a2} are its columns
+        hgemm_t(Y.sub(coff(u, ub), 0, cols(ub), w), -1.0, ub, Ya);
+      }
+    }
+  }
+
   // ---- X <- L_ll^{-1} X  (X block with the row cluster of l)
   void trsm_l(int l, int x) {
     const Block& X = B(x);
@@ -832,16 +886,9 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     const int S = C.end - C.begin;
     const int db = diag_block[FL.sb_cluster[k]];
     View Li = E.new_mat(S, S, false), UiT = E.new_mat(S, S, false), Ui = E.new_mat(S, S, false);
-    for (View* X : {&Li, &UiT}) {
-      E.copy(*X, 0.0, nullptr, 0.0);
-      View dg = *X;
-      dg.cols = 1;
-      dg.rs = X->rs + 1;
-      dg.cs = 0;
-      E.copy(dg, 1.0, nullptr, 1.0);
-    }
-    H.lsolve_mat(db, Li);      // L_BB^{-1}
-    H.usolve_t_mat(db, UiT);   // U_BB^{-T}
+    for (View* X : {&Li, &UiT}) E.copy(*X, 0.0, nullptr, 0.0);
+    H.linv_ident(db, Li, 0);    // L_BB^{-1}
+    H.uinvt_ident(db, UiT, 0);  // U_BB^{-T}
     View UiTt = UiT.T();
     E.copy(Ui, 1.0, &UiTt, 0.0);
     sbL[k] = Li;
@@ -866,10 +913,13 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
         const int S = C.end - C.begin, len = e - r;
         const View& inv = lower ? sbL[k] : sbU[k];
         View o = E.new_mat(S, rowsrc.cols, false);
-        E.gemm(o, 1.0, inv.sub(0, r - C.begin, S, len), rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
         // a lower (upper) triangular inverse leaves the rows above (below) the
-        // source rows zero
+        // source rows zero: only rows [lo, hi) are products, the rest is zero
         const int lo = lower ? r - C.begin : 0, hi = lower ? S : e - C.begin;
+        E.gemm(o.sub(lo, 0, hi - lo, rowsrc.cols), 1.0, inv.sub(lo, r - C.begin, hi - lo, len),
+               rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
+        if (lo > 0) E.copy(o.sub(0, 0, lo, rowsrc.cols), 0.0, nullptr, 0.0);
+        if (hi < S) E.copy(o.sub(hi, 0, S - hi, rowsrc.cols), 0.0, nullptr, 0.0);
         FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols, lo, hi});
       }
       r = e;
