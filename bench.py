@@ -8,6 +8,12 @@ alpha = 1.5 truncated to |y| <= 2, leaf 256, ACA rank <= 32, 1000 CN steps,
 dt = 1e-3).  The metric is unknown-steps/s = N * CN steps / time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload levy_1d_n65536|levy_batch] [--batch-count C]
+
+--workload levy_batch measures the batched workload instead: 512 independent
+1D Levy solves (splitmix64 seed 0: N = round(2^U(10,15)), alpha, drift,
+sigma), leaf sizes from the autotuner, 500 CN steps each at dt = 1/500; one
+step = build all H-matrices + one batched H-LU launch + the batched CN run.
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own
 replica (the solve does not shard); value = total unknown-steps / max time.
@@ -41,6 +47,9 @@ def parse():
     ap.add_argument("--cn-steps", type=int, default=None, help="override the workload's CN steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refine", type=int, default=0, help="refinement sweeps per CN step")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "levy_batch"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--group-unknowns", type=int, default=1200000)
     return ap.parse_args()
 
 
@@ -176,10 +185,157 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The batched workload (see the module docstring)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1812_08324_gb300 import autotune, build, hmat, workloads as W
+    build.build()
+    hmat.load()
+    batch = W.levy_batch(args.batch_count)
+    dt = W.LEVY_BATCH_DT
+    cn_steps = args.cn_steps or W.LEVY_BATCH_STEPS
+    batch = [(p, dict(o, refine_max=args.refine)) for p, o in batch]
+    leafs = autotune.tune_batch(batch, dt, cn_steps, probe_steps=3)
+    batch = [(p, dict(o, leaf=l)) for (p, o), l in zip(batch, leafs)]
+    ns = [p["n"][0] for p, _ in batch]
+    units = float(sum(ns)) * cn_steps
+    u0_host = [torch.tensor(W.gaussian_u0(p, 50.0), dtype=torch.float64).pin_memory() for p, _ in batch]
+    u0_dev = [u.to("cuda") for u in u0_host]
+    us = [torch.empty_like(u) for u in u0_dev]
+    stream = torch.cuda.current_stream()
+
+    # consecutive groups of at most group_unknowns unknowns share the GPU at a
+    # time (the factors of all 512 problems would not fit in HBM at once)
+    groups, cur, tot = [], [], 0
+    for i, n in enumerate(ns):
+        if cur and tot + n > args.group_unknowns:
+            groups.append(cur)
+            cur, tot = [], 0
+        cur.append(i)
+        tot += n
+    groups.append(cur)
+
+    def step(srcs, keep_last=False):
+        kept = None
+        for gi, g in enumerate(groups):
+            Hs = [hmat.HMatrix(*batch[i]) for i in g]
+            Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+            for i in g:
+                us[i].copy_(srcs[i])
+            hmat.cn_solve_batch(Hs, Fs, dt, cn_steps, [us[i] for i in g])
+            if keep_last and gi == len(groups) - 1:
+                kept = (Hs, Fs, g)
+            else:
+                release(Hs, Fs)
+        return kept
+
+    def release(Hs, Fs):
+        for F in Fs:
+            F.free()
+        for H in Hs:
+            H.free()
+
+    for _ in range(args.warmup):
+        step(u0_dev)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    l0 = hmat.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        kept = step(u0_dev, keep_last=k == args.steps - 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = (hmat.launch_count() - l0) // max(1, args.steps)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop()
+    ms, value = aggregate(ms, units, world, "cuda")
+    graphed = hmat.batch_graphed()
+
+    # accuracy: a few members against their converged solves (the batch equals the single path bit for bit)
+    errs = []
+    for i in np.linspace(0, len(batch) - 1, 3).astype(int):
+        p, o = batch[i]
+        H3 = hmat.HMatrix(p, dict(o, refine_max=3))
+        F3 = H3.factor(-0.5 * dt)
+        ur = u0_dev[i].clone()
+        hmat.cn_solve(H3, F3, dt, cn_steps, ur)
+        errs.append(float(torch.linalg.norm(us[i] - ur) / torch.linalg.norm(ur)))
+        F3.free()
+        H3.free()
+    # CN part alone on the last group and its bytes per step (roofline of the batched step)
+    Hs, Fs, g = kept
+    sts = [H.stats(F) for H, F in zip(Hs, Fs)]
+    byts = float(sum(st["h_bytes"] + st["lu_bytes"] for st in sts))
+    gus = [u0_dev[i].clone() for i in g]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    hmat.cn_solve_batch(Hs, Fs, dt, 20, gus)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cn_ms = c0.elapsed_time(c1) / 20
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = byts / (cn_ms * 1e-3) / 1e9
+    roofline = {"kernel": "batched CN step (batched H-matvec + merged solve schedule, one CUDA graph)",
+                "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                "peak_source": "hbm_gbs " + ("of measured" if peaks else "of fallback"),
+                "algorithmic_bytes": byts, "ms": cn_ms}
+
+    # end to end from pinned host memory
+    release(Hs, Fs)
+    outs = [torch.empty_like(u).pin_memory() for u in u0_host]
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    devs = [u.to("cuda", non_blocking=True) for u in u0_host]
+    step(devs)
+    for o, u in zip(outs, us):
+        o.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * sum(ns),
+           "d2h_bytes_per_step": 8 * sum(ns)}
+    line = {"metric": METRIC.replace("(H-matrix build + H-LU + CN run)", "(batched: build + H-LU + CN run)"),
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"levy_batch x{len(batch)} (splitmix64 seed 0)", "sum_N": int(sum(ns)),
+                       "cn_steps": cn_steps, "dt": dt, "leafs": {str(l): leafs.count(l) for l in sorted(set(leafs))},
+                       "groups": len(groups), "group_unknowns_max": args.group_unknowns,
+                       "refine_sweeps": args.refine, "parallelism": f"replicas x{world}", "cuda_graph": graphed,
+                       "l2": "working set (H + factors of all problems) exceeds L2; no flush needed"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "accuracy": {"rel_l2_vs_converged_fp64_solves_sampled": errs,
+                         "reference": "three members, same H-matrix CN run with 3 FP64 refinement sweeps per step"}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "levy_batch":
+        return run_batch(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()
