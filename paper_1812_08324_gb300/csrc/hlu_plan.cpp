@@ -406,6 +406,9 @@ class Emitter {
 #ifndef HM_LR_ACC
 #define HM_LR_ACC 3  // pending capacity in multiples of kf (build-time tuning parameter)
 #endif
+#ifndef HM_TRUNC_KCAP
+#define HM_TRUNC_KCAP 96  // widest accumulated sum, kf + pending (build-time tuning parameter)
+#endif
 struct LRState {
   View U[2], V[2];   // slots: m x (1 + nacc) kf and n x (1 + nacc) kf, column-major
   View rankv;        // dependency token for the rank word
@@ -444,8 +447,10 @@ class HLU {
   int roff(int parent, int ch) const { return P.cl[B(ch).t].begin - P.cl[B(parent).t].begin; }
   int coff(int parent, int ch) const { return P.cl[B(ch).s].begin - P.cl[B(parent).s].begin; }
 
-  // pending update columns a block may hold (the truncation core takes at most TRUNC_MAXK)
-  int nacc() const { return std::max(1, std::min(HM_LR_ACC, TRUNC_MAXK / kf - 1)); }
+  // pending update columns a block may hold: the recompression of kf + pending
+  // columns costs about K^3 FP64 operations on one SM, so the accumulated width
+  // K stays within HM_TRUNC_KCAP (and the truncation core's TRUNC_MAXK)
+  int nacc() const { return std::max(1, std::min(HM_LR_ACC, std::min(TRUNC_MAXK, HM_TRUNC_KCAP) / kf - 1)); }
   int pend_cap() const { return nacc() * kf; }
   // readers see the recompressed factor
   View lrU(int q) { flush(q); return lr[q].U[lr[q].cur].sub(0, 0, lr[q].m, kf); }
