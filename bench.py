@@ -10,6 +10,8 @@ dt = 1e-3).  The metric is unknown-steps/s = N * CN steps / time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload levy_1d_n65536|levy_batch] [--batch-count C]
 
+--workload serve serves a seeded Poisson request stream (continuous batching,
+150 GB admission budget) and adds p50/p99 latency to the line.
 --workload levy_batch measures the batched workload instead: 512 independent
 1D Levy solves (splitmix64 seed 0: N = round(2^U(10,15)), alpha, drift,
 sigma), leaf sizes from the autotuner, 500 CN steps each at dt = 1/500; one
@@ -47,7 +49,9 @@ def parse():
     ap.add_argument("--cn-steps", type=int, default=None, help="override the workload's CN steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refine", type=int, default=0, help="refinement sweeps per CN step")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "levy_batch"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "levy_batch", "serve"])
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-sides", default="32,48,64", help="2D grid sides of the served stream")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--group-unknowns", type=int, default=1200000)
     return ap.parse_args()
@@ -330,12 +334,86 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """The served request stream: Poisson arrivals (rate 200/s, splitmix64
+    seed 0), half 1D (N = round(2^U(10,16))) and half 2D fractional Laplacian
+    requests, s ~ U(0.2,0.9), 100..1000 CN steps, 150 GB admission budget.
+    One bench step serves the whole stream; value = unknown-steps/s over the
+    stream's span; latency percentiles per request (arrival to result on the
+    host)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1812_08324_gb300 import build, hmat, serve, workloads as W
+    build.build()
+    hmat.load()
+    sides = tuple(int(x) for x in args.serve_sides.split(","))
+    reqs = W.serve_stream(args.serve_count, seed=0, rate=200.0, sides_2d=sides)
+    warm = W.serve_stream(6, seed=1, rate=200.0, log2_1d=(10.0, 12.0), sides_2d=(32,), steps=(20, 40))
+    for _ in range(args.warmup):
+        serve.Server(hbm_budget=150e9).run(warm)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = hmat.launch_count()
+    summaries = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        srv = serve.Server(hbm_budget=150e9, tick_steps=20)
+        res = srv.run(reqs)
+        summaries.append(serve.summary(res))
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.steps
+    clocks = sampler.stop()
+    launches = (hmat.launch_count() - l0) // max(1, args.steps)
+    last = summaries[-1]
+    work = float(sum(r.n * r.steps for r in res))
+    value = work / wall
+    # a sample of results against the same requests solved alone with refinement
+    errs = []
+    for r, q in list(zip(res, reqs))[:: max(1, len(reqs) // 3)][:3]:
+        H = hmat.HMatrix(q["problem"], dict(q["opts"], refine_max=3))
+        F = H.factor(-0.5 * q["dt"])
+        u = torch.tensor(q["u0"], dtype=torch.float64, device="cuda")
+        hmat.cn_solve(H, F, q["dt"], q["steps"], u)
+        ref = u.cpu().numpy()
+        errs.append(float(np.linalg.norm(r.u - ref) / np.linalg.norm(ref)))
+        F.free()
+        H.free()
+    ns1 = [r.n for r, q in zip(res, reqs) if q["problem"]["dim"] == 1]
+    ns2 = [r.n for r, q in zip(res, reqs) if q["problem"]["dim"] == 2]
+    line = {"metric": METRIC.replace("(H-matrix build + H-LU + CN run)", "(served stream: admission + build + H-LU + CN run)"),
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serve_stream x{len(reqs)} (Poisson 200/s, splitmix64 seed 0)",
+                       "requests_1d": len(ns1), "requests_2d": len(ns2), "sides_2d": list(sides),
+                       "sum_N_steps": work, "hbm_budget_bytes": 150e9, "tick_steps": 20,
+                       "peak_device_bytes": srv.peak_used, "batches_built": srv.batches_built,
+                       "l2": "working set exceeds L2; no flush needed"},
+            "latency": {"p50_s": last["p50_latency_s"], "p99_s": last["p99_latency_s"], "span_s": last["span_s"]},
+            "clocks": clocks,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 8 * sum(r.n for r in res),
+                    "d2h_bytes_per_step": 8 * sum(r.n for r in res),
+                    "note": "the server run is end to end: host u0 in, host result out per request"},
+            "gpu_launches": int(launches), "roofline": None,
+            "accuracy": {"rel_l2_vs_alone_refined_sampled": errs}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "levy_batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()

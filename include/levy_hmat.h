@@ -114,6 +114,7 @@ typedef struct hm_stats_t {
   int lu_rank_capped;         /* factor blocks truncated at lu_max_rank before lu_tol */
   int last_refine_iters;      /* refinement sweeps used by the last cn_step */
   double last_refine_resid;   /* ||s|| / ||rhs|| after the last cn_step */
+  int64_t device_bytes;       /* device memory held by H (and by F when given) */
 } hm_stats_t;
 
 /* ---- errors ---- */
@@ -282,8 +283,25 @@ int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int 
 int cn_solve_batch(const hm_matrix* const* H, const hm_factors* const* F, int count, double dt, int steps,
                    double* const* u, void* stream);
 
-/* 1 if the last cn_solve_batch replayed its step as a CUDA graph, 0 if it
- * launched every step directly (stream capture refused). */
+/*
+ * Persistent batches (continuous batching of independent problems).
+ * hm_batch_create: stepping state for `count` problems with their own dt[i]
+ * (each F[i] from hm_factor(H[i], -dt[i]/2); distinct matrices and factors;
+ * a common opts.refine_max).  It uploads the merged solve schedule and the
+ * batched H-matvec tables once and records one step of all problems as a CUDA
+ * graph.  The batch borrows H[i] and F[i]: free it before them.
+ * hm_batch_step: `steps` CN steps (no forcing) of every problem; u[i] (device,
+ * natural order) is read on entry and written on return; results equal
+ * separate cn_solve calls bit for bit.  Stream-ordered after `stream`.
+ */
+typedef struct hm_batch hm_batch;
+int hm_batch_create(const hm_matrix* const* H, const hm_factors* const* F, const double* dt, int count,
+                    hm_batch** out);
+int hm_batch_step(hm_batch* B, double* const* u, int steps, void* stream);
+void hm_batch_free(hm_batch* B);
+
+/* 1 if the last batch created replays its step as a CUDA graph, 0 if every
+ * step is launched directly (stream capture refused). */
 int hm_batch_graphed(void);
 
 /* Number of kernel launches this library has issued in the process so far

@@ -34,6 +34,7 @@ void count_launches(int n);
 // Device allocations owned by one handle, freed together.
 struct DevArena {
   std::vector<void*> ptrs;
+  int64_t bytes_held = 0;
   int alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -44,6 +45,7 @@ struct DevArena {
       return HM_ERR_OOM;
     }
     ptrs.push_back(*p);
+    bytes_held += (int64_t)bytes;
     return HM_OK;
   }
   template <typename T>

@@ -377,6 +377,49 @@ void parallel_for(int n, Fn fn) {
 }  // namespace
 }  // namespace hm
 
+// A set of problems stepped together (hm_batch_create): the merged solve
+// schedule, the batched H-matvec and vector job tables, the batch-owned
+// Morton-order states and the recorded CUDA graph of one step.
+struct hm_batch {
+  std::vector<const hm_matrix*> H;
+  std::vector<const hm_factors*> F;
+  std::vector<double*> state;
+  int refine = 0;
+  DevSchedule sched;
+  hm::MvBatch A{}, B{};
+  hm::DevJobs<hm::VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out;
+  std::vector<void*> allocs;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t per_step = 0;
+};
+
+namespace hm {
+namespace {
+
+// One CN step of every problem of the batch (stream-ordered launches only,
+// so that it can be recorded as a graph).
+int batch_one_step(hm_batch* B, cudaStream_t cs) {
+  int* d_err = B->H[0]->d_err;
+  HM_TRY(launch_matvec_batch(B->A, cs));
+  HM_TRY(launch_vec_batch(B->rhs_in, cs));
+  HM_TRY(run_schedule(B->sched, d_err, cs));
+  if (B->refine == 0) return launch_vec_batch(B->z_out, cs);
+  HM_TRY(launch_vec_batch(B->z_u1, cs));
+  for (int it = 0; it < B->refine; ++it) {
+    HM_TRY(launch_matvec_batch(B->B, cs));
+    HM_TRY(launch_vec_batch(B->s_in, cs));
+    HM_TRY(run_schedule(B->sched, d_err, cs));
+    HM_TRY(launch_vec_batch(B->u1_add, cs));
+  }
+  return launch_vec_batch(B->u1_out, cs);
+}
+
+}  // namespace
+}  // namespace hm
+
 extern "C" {
 
 int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) {
@@ -487,14 +530,16 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
   return HM_OK;
 }
 
-int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int count, double dt, int steps,
-                   double* const* u, void* stream) {
-  if (!Hs || !Fs || !u || count < 1 || steps < 0 || !(dt > 0.0)) { set_error("bad argument"); return HM_ERR_ARG; }
+int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, const double* dts, int count,
+                    hm_batch** out) {
+  if (!out) { set_error("null argument"); return HM_ERR_ARG; }
+  *out = nullptr;
+  if (!Hs || !Fs || !dts || count < 1) { set_error("bad argument"); return HM_ERR_ARG; }
   const int R = Hs[0] ? Hs[0]->opts.refine_max : 0;
   for (int i = 0; i < count; ++i) {
-    if (!Hs[i] || !Fs[i] || !u[i]) { set_error("null entry"); return HM_ERR_ARG; }
+    if (!Hs[i] || !Fs[i]) { set_error("null entry"); return HM_ERR_ARG; }
     if (Fs[i]->H != Hs[i]) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
-    if (std::fabs(Fs[i]->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+    if (!(dts[i] > 0.0) || std::fabs(Fs[i]->theta + 0.5 * dts[i]) > 1e-12 * std::fabs(0.5 * dts[i])) {
       set_error("factors must come from hm_factor(H, -dt/2)");
       return HM_ERR_ARG;
     }
@@ -502,12 +547,12 @@ int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int 
     for (int j = 0; j < i; ++j)
       if (Hs[j] == Hs[i] || Fs[j] == Fs[i]) { set_error("matrices and factors must be distinct"); return HM_ERR_ARG; }
   }
-  if (steps == 0) return HM_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  const double th = 0.5 * dt;
-  std::vector<void*> allocs;
-  auto cleanup = [&](int s) {
-    for (void* p : allocs) cudaFree(p);
+  hm_batch* B = new hm_batch();
+  B->H.assign(Hs, Hs + count);
+  B->F.assign(Fs, Fs + count);
+  B->refine = R;
+  auto fail = [&](int s) {
+    hm_batch_free(B);
     return s;
   };
   // one solve schedule for all problems, in the throughput mode (more CTAs per
@@ -515,21 +560,23 @@ int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int 
   // the arithmetic)
   std::vector<SchedPart> parts;
   for (int i = 0; i < count; ++i) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
-  DevSchedule MS;
-  int s = upload_schedules(parts, MS, allocs, SOLVE_MODE_THROUGHPUT, true);
-  if (s != HM_OK) { set_error("batched solve schedule upload failed"); return cleanup(s); }
-  // per problem: state x (Morton order), rhs, residual, refined iterate, solve output z
+  int s = upload_schedules(parts, B->sched, B->allocs, SOLVE_MODE_THROUGHPUT, true);
+  if (s != HM_OK) { set_error("batched solve schedule upload failed"); return fail(s); }
+  // per problem: Morton-order state x (owned by the batch), rhs, residual,
+  // refined iterate, solve output z
   std::vector<MvJob> jA(count), jB(count);
-  std::vector<VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out, gath;
+  std::vector<VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out;
   for (int i = 0; i < count; ++i) {
     const hm_matrix* H = Hs[i];
     hm_factors* F = const_cast<hm_factors*>(Fs[i]);
     const int N = H->plan.N;
+    const double th = 0.5 * dts[i];
     double* rhs = F->d_vec;
     double* res = F->d_vec + (size_t)N;
     double* u1 = F->d_vec + 2 * (size_t)N;
-    double* x = H->plan.dim == 1 ? u[i] : F->d_vec + 3 * (size_t)N;
+    double* x = F->d_vec + 3 * (size_t)N;
     double* z = F->d_sv + (size_t)N;
+    B->state.push_back(x);
     jA[i] = MvJob{H->mv, 1.0, th, th, x, nullptr, nullptr, nullptr, rhs};   // rhs = x + th G x
     jB[i] = MvJob{H->mv, -1.0, th, 0.0, u1, nullptr, nullptr, rhs, res};    // res = rhs - (u1 - th G u1)
     rhs_in.push_back({rhs, F->d_y, 0.0, N, 0});
@@ -540,84 +587,111 @@ int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int 
     u1_out.push_back({u1, x, 0.0, N, 0});
   }
   auto vblocks = [](const VecJob& J) { return (J.n + VEC_CHUNK - 1) / VEC_CHUNK; };
-  MvBatch A{}, B{};
-  DevJobs<VecJob> d_rhs, d_s, d_z, d_zu1, d_add, d_u1;
-  if ((s = upload_mv_batch(jA, A, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_mv_batch(jB, B, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(rhs_in, vblocks, d_rhs, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(s_in, vblocks, d_s, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(z_out, vblocks, d_z, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(z_u1, vblocks, d_zu1, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(u1_add, vblocks, d_add, allocs)) != HM_OK) return cleanup(s);
-  if ((s = upload_jobs(u1_out, vblocks, d_u1, allocs)) != HM_OK) return cleanup(s);
-  int* d_err = Hs[0]->d_err;
-  auto one_step = [&](cudaStream_t cs) -> int {
-    HM_TRY(launch_matvec_batch(A, cs));
-    HM_TRY(launch_vec_batch(d_rhs, cs));
-    HM_TRY(run_schedule(MS, d_err, cs));
-    if (R == 0) return launch_vec_batch(d_z, cs);
-    HM_TRY(launch_vec_batch(d_zu1, cs));
-    for (int it = 0; it < R; ++it) {
-      HM_TRY(launch_matvec_batch(B, cs));
-      HM_TRY(launch_vec_batch(d_s, cs));
-      HM_TRY(run_schedule(MS, d_err, cs));
-      HM_TRY(launch_vec_batch(d_add, cs));
-    }
-    return launch_vec_batch(d_u1, cs);
-  };
-  if ((s = prepare_executor(MS)) != HM_OK) return cleanup(s);
-  // a private stream ordered after the caller's stream (the caller's may be the legacy default stream)
-  cudaStream_t cs = nullptr;
-  cudaEvent_t ev = nullptr;
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cleanup(HM_ERR_CUDA);
-  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  cudaEventRecord(ev, st);
-  cudaStreamWaitEvent(cs, ev, 0);
-  for (int i = 0; i < count; ++i)
-    if (Hs[i]->plan.dim != 1 && s == HM_OK)
-      s = launch_gather(Hs[i]->d_perm, Hs[i]->plan.N, u[i], const_cast<hm_factors*>(Fs[i])->d_vec + 3 * (size_t)Hs[i]->plan.N, cs);
-  // record one step as a CUDA graph and replay it
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int64_t per_step = 0;
-  if (s == HM_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+  if ((s = upload_mv_batch(jA, B->A, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_mv_batch(jB, B->B, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(rhs_in, vblocks, B->rhs_in, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(s_in, vblocks, B->s_in, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(z_out, vblocks, B->z_out, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(z_u1, vblocks, B->z_u1, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(u1_add, vblocks, B->u1_add, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(u1_out, vblocks, B->u1_out, B->allocs)) != HM_OK) return fail(s);
+  if ((s = prepare_executor(B->sched)) != HM_OK) return fail(s);
+  if (cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking) != cudaSuccess) return fail(HM_ERR_CUDA);
+  cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  // record one step as a CUDA graph (replayed by hm_batch_step); without
+  // capture support every step is launched directly
+  if (cudaStreamBeginCapture(B->cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     const int64_t l0 = hm_launch_count();
-    const int sc = one_step(cs);
-    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
-    per_step = hm_launch_count() - l0;
-    count_launches(-(int)per_step);  // counted when the graph runs
-    if (sc != HM_OK || ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+    const int sc = batch_one_step(B, B->cs);
+    const cudaError_t ec = cudaStreamEndCapture(B->cs, &B->graph);
+    B->per_step = hm_launch_count() - l0;
+    count_launches(-(int)B->per_step);  // counted when the graph runs
+    if (sc != HM_OK || ec != cudaSuccess || cudaGraphInstantiate(&B->gexec, B->graph, 0) != cudaSuccess) {
       cudaGetLastError();
-      if (gexec) cudaGraphExecDestroy(gexec);
-      gexec = nullptr;
+      if (B->gexec) cudaGraphExecDestroy(B->gexec);
+      B->gexec = nullptr;
     }
   } else {
     cudaGetLastError();
   }
-  g_batch_graphed = gexec != nullptr;
-  for (int k = 0; k < steps && s == HM_OK; ++k) {
-    if (gexec) {
-      s = cudaGraphLaunch(gexec, cs) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
-      count_launches((int)per_step);
+  g_batch_graphed = B->gexec != nullptr;
+  *out = B;
+  return HM_OK;
+}
+
+int hm_batch_step(hm_batch* B, double* const* u, int steps, void* stream) {
+  if (!B || !u || steps < 0) { set_error("bad argument"); return HM_ERR_ARG; }
+  const int count = (int)B->H.size();
+  for (int i = 0; i < count; ++i)
+    if (!u[i]) { set_error("null state vector"); return HM_ERR_ARG; }
+  if (steps == 0) return HM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // ordered after the caller's stream (which may be the legacy default stream)
+  cudaEventRecord(B->ev, st);
+  cudaStreamWaitEvent(B->cs, B->ev, 0);
+  int s = HM_OK;
+  for (int i = 0; i < count && s == HM_OK; ++i) {
+    const hm_matrix* H = B->H[i];
+    const int N = H->plan.N;
+    if (H->plan.dim == 1) {
+      count_launches(1);
+      copy_vec_kernel<<<vgrid(N), 256, 0, B->cs>>>(N, u[i], B->state[i]);
+      s = cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
     } else {
-      s = one_step(cs);
+      s = launch_gather(H->d_perm, N, u[i], B->state[i], B->cs);
     }
   }
-  for (int i = 0; i < count; ++i)
-    if (Hs[i]->plan.dim != 1 && s == HM_OK)
-      s = launch_scatter(Hs[i]->d_perm, Hs[i]->plan.N, const_cast<hm_factors*>(Fs[i])->d_vec + 3 * (size_t)Hs[i]->plan.N, u[i], cs);
-  if (cudaStreamSynchronize(cs) != cudaSuccess && s == HM_OK) s = HM_ERR_CUDA;
-  cudaEventRecord(ev, cs);
-  cudaStreamWaitEvent(st, ev, 0);
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  cudaEventDestroy(ev);
-  cudaStreamDestroy(cs);
+  for (int k = 0; k < steps && s == HM_OK; ++k) {
+    if (B->gexec) {
+      s = cudaGraphLaunch(B->gexec, B->cs) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+      count_launches((int)B->per_step);
+    } else {
+      s = batch_one_step(B, B->cs);
+    }
+  }
+  for (int i = 0; i < count && s == HM_OK; ++i) {
+    const hm_matrix* H = B->H[i];
+    const int N = H->plan.N;
+    if (H->plan.dim == 1) {
+      count_launches(1);
+      copy_vec_kernel<<<vgrid(N), 256, 0, B->cs>>>(N, B->state[i], u[i]);
+      s = cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+    } else {
+      s = launch_scatter(H->d_perm, N, B->state[i], u[i], B->cs);
+    }
+  }
+  cudaEventRecord(B->ev, B->cs);
+  cudaStreamWaitEvent(st, B->ev, 0);
   if (s != HM_OK) set_error("batched CN steps failed: " + std::string(cudaGetErrorString(cudaGetLastError())));
+  return s;
+}
+
+void hm_batch_free(hm_batch* B) {
+  if (!B) return;
+  if (B->cs) cudaStreamSynchronize(B->cs);
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->ev) cudaEventDestroy(B->ev);
+  if (B->cs) cudaStreamDestroy(B->cs);
+  for (void* p : B->allocs) cudaFree(p);
+  delete B;
+}
+
+int cn_solve_batch(const hm_matrix* const* Hs, const hm_factors* const* Fs, int count, double dt, int steps,
+                   double* const* u, void* stream) {
+  if (!Hs || !Fs || !u || count < 1 || steps < 0 || !(dt > 0.0)) { set_error("bad argument"); return HM_ERR_ARG; }
+  for (int i = 0; i < count; ++i)
+    if (!u[i]) { set_error("null state vector"); return HM_ERR_ARG; }
+  std::vector<double> dts(count, dt);
+  hm_batch* B = nullptr;
+  HM_TRY(hm_batch_create(Hs, Fs, dts.data(), count, &B));
+  const int s = hm_batch_step(B, u, steps, stream);
+  if (s == HM_OK) cudaStreamSynchronize(B->cs);
   int e = 0;
-  cudaMemcpy(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (s == HM_OK && (e & DEVERR_TIMEOUT)) { set_error("bounded wait gave up in a solve"); s = HM_ERR_TIMEOUT; }
-  return cleanup(s);
+  cudaMemcpy(&e, Hs[0]->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  hm_batch_free(B);
+  if (s == HM_OK && (e & DEVERR_TIMEOUT)) { set_error("bounded wait gave up in a solve"); return HM_ERR_TIMEOUT; }
+  return s;
 }
 
 int hm_batch_graphed(void) { return g_batch_graphed ? 1 : 0; }
@@ -787,7 +861,9 @@ int hm_stats(const hm_matrix* H, const hm_factors* F, hm_stats_t* out) {
   int64_t hb = de;
   for (size_t q = 0; q < H->h_ld.size(); ++q) hb += (int64_t)(H->h_ld[q].m + H->h_ld[q].n) * H->h_rank[q];
   out->h_bytes = 8 * hb;
+  out->device_bytes = H->arena.bytes_held;
   if (F) {
+    for (auto& r : F->arena.ranges) out->device_bytes += (int64_t)(r.second - r.first);
     out->lu_bytes = F->lu_bytes;
     int m2 = 0;
     for (int r : F->h_rank) m2 = std::max(m2, r);

@@ -23,6 +23,7 @@ EXPORTED = [
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
     "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor", "hm_launch_count",
     "hm_matvec_noalloc", "hm_factor_batch", "cn_solve_batch", "hm_batch_graphed",
+    "hm_batch_create", "hm_batch_step", "hm_batch_free",
 ]
 
 
@@ -46,7 +47,7 @@ class Stats(C.Structure):
                 ("h_bytes", C.c_int64), ("lu_bytes", C.c_int64), ("max_rank_seen", C.c_int),
                 ("rank_capped_blocks", C.c_int), ("lu_max_rank_seen", C.c_int),
                 ("lu_rank_capped", C.c_int), ("last_refine_iters", C.c_int),
-                ("last_refine_resid", C.c_double)]
+                ("last_refine_resid", C.c_double), ("device_bytes", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -105,6 +106,9 @@ def load() -> C.CDLL:
         "hm_factor_batch": (i, [C.POINTER(vp), C.POINTER(d), i, vp, C.POINTER(vp)]),
         "cn_solve_batch": (i, [C.POINTER(vp), C.POINTER(vp), i, d, i, C.POINTER(vp), vp]),
         "hm_batch_graphed": (i, []),
+        "hm_batch_create": (i, [C.POINTER(vp), C.POINTER(vp), C.POINTER(d), i, C.POINTER(vp)]),
+        "hm_batch_step": (i, [vp, C.POINTER(vp), i, vp]),
+        "hm_batch_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -347,3 +351,35 @@ def cn_solve_batch(Hs, Fs, dt: float, steps: int, us, stream=None):
 
 def batch_graphed() -> bool:
     return bool(load().hm_batch_graphed())
+
+
+class Batch:
+    """Problems stepped together: merged solve schedule and batched H-matvec,
+    one CUDA graph per step (hm_batch_create).  Keeps references to its
+    matrices and factors; free() before freeing them."""
+
+    def __init__(self, Hs, Fs, dts):
+        n = len(Hs)
+        self.Hs, self.Fs = list(Hs), list(Fs)
+        hs = (C.c_void_p * n)(*[H.handle.value for H in Hs])
+        fs = (C.c_void_p * n)(*[F._f.value for F in Fs])
+        ds = (C.c_double * n)(*[float(x) for x in dts])
+        self._b = C.c_void_p()
+        _check(load().hm_batch_create(hs, fs, ds, n, C.byref(self._b)))
+
+    def step(self, us, steps: int, stream=None):
+        n = len(self.Hs)
+        ps = (C.c_void_p * n)(*[_ptr(u) for u in us])
+        _check(load().hm_batch_step(self._b, ps, int(steps), _stream(stream)))
+        return us
+
+    def free(self):
+        if self._b:
+            load().hm_batch_free(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

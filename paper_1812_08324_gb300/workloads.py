@@ -180,6 +180,42 @@ LEVY_BATCH_DT = 1.0 / 500
 LEVY_BATCH_STEPS = 500
 
 
+# ----------------------------------------------------------------------------
+# Workload 5: a served request stream (Poisson arrivals, splitmix64 seed 0)
+# ----------------------------------------------------------------------------
+
+def serve_stream(count: int = 2000, seed: int = 0, rate: float = 200.0, log2_1d=(10.0, 16.0),
+                 sides_2d=(64, 128, 256, 512), steps=(100, 1000)):
+    """Requests in arrival order, drawn per request in this order: the
+    exponential inter-arrival gap (rate per second), 1D or 2D (half each),
+    N = round(2^U(log2_1d)) or a side from sides_2d, s ~ U(0.2, 0.9), steps
+    ~ U{steps}; dt = 1/steps.  Fractional Laplacian with a Gaussian bump.
+    Returns dicts with arrival (s), problem, opts, dt, steps, u0."""
+    g = SplitMix64(seed)
+    t = 0.0
+    out = []
+    for rid in range(count):
+        t += -math.log(max(g.uniform(), 1e-300)) / rate
+        two_d = g.uniform() >= 0.5
+        if two_d:
+            side = int(sides_2d[min(int(g.uniform() * len(sides_2d)), len(sides_2d) - 1)])
+        else:
+            n = int(round(2.0 ** g.uniform(*log2_1d)))
+        s = g.uniform(0.2, 0.9)
+        st = steps[0] + min(int(g.uniform() * (steps[1] - steps[0] + 1)), steps[1] - steps[0])
+        if two_d:
+            prob = frac_lap_2d(side, s)
+            opts = default_opts(leaf=256, aca_tol=1e-8, max_rank=64, lu_tol=1e-10, lu_max_rank=16, refine_max=0)
+            u0 = bump_u0(prob)
+        else:
+            prob = frac_lap_1d(n, s)
+            opts = default_opts(leaf=batch_leaf(n), aca_tol=1e-10, max_rank=32, lu_tol=1e-10, lu_max_rank=16,
+                                refine_max=0)
+            u0 = gaussian_u0(prob, 50.0)
+        out.append(dict(rid=rid, arrival=t, problem=prob, opts=opts, dt=1.0 / st, steps=st, u0=u0))
+    return out
+
+
 def initial_data(prob: dict, kind: str) -> np.ndarray:
     if kind == "unit_ball":
         return manufactured_unit_ball(prob)[0]

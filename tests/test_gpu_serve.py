@@ -1,0 +1,57 @@
+"""Continuous batching: requests that arrive while others run are admitted,
+share the device, and every result equals the request solved alone."""
+import numpy as np
+import pytest
+
+from paper_1812_08324_gb300 import hmat, serve, workloads as W
+
+from gpu_util import dev, host, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _stream():
+    # the serving stream's generator at sizes that run in seconds
+    return W.serve_stream(8, seed=0, rate=50.0, log2_1d=(9.0, 11.0), sides_2d=(16, 24), steps=(20, 60))
+
+
+def test_served_results_equal_alone_and_overlap():
+    reqs = _stream()
+    srv = serve.Server(hbm_budget=50e9, tick_steps=7, realtime=True)
+    res = srv.run(reqs)
+    assert len(res) == len(reqs)
+    overlapped = False
+    for r, q in zip(res, reqs):
+        H = hmat.HMatrix(q["problem"], q["opts"])
+        F = H.factor(-0.5 * q["dt"])
+        u = dev(q["u0"])
+        hmat.cn_solve(H, F, q["dt"], q["steps"], u)
+        assert np.array_equal(host(u), r.u), f"request {q['rid']} differs alone and in the mix"
+        assert r.finished >= r.admitted >= 0 and r.latency > 0
+        F.free()
+        H.free()
+    # some request was admitted while another one was still running
+    for a in res:
+        for b in res:
+            if a is not b and b.admitted < a.finished and b.admitted > a.admitted:
+                overlapped = True
+    assert overlapped
+    assert srv.batches_built >= 2 and srv.used == pytest.approx(0.0, abs=1.0)
+    s = serve.summary(res)
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_budget_admits_one_at_a_time():
+    """A budget below two requests' footprint serialises them (and still
+    admits a request that alone exceeds the budget, so nothing starves)."""
+    reqs = _stream()[:3]
+    srv = serve.Server(hbm_budget=1.0, tick_steps=10, realtime=False)
+    res = srv.run(reqs)
+    spans = sorted((r.admitted, r.finished) for r in res)
+    for (a0, f0), (a1, f1) in zip(spans, spans[1:]):
+        assert a1 >= f0 - 1e-6
