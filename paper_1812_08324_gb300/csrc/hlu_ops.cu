@@ -252,61 +252,109 @@ __device__ __forceinline__ void warp0_max_sum(const double* v, int stride, int p
   }
 }
 
-// In-place pivoted Cholesky of the symmetric K x K matrix G (row-major);
-// perm[c] = original index of pivot c; returns the rank (pivots above thresh).
-__device__ int pivoted_cholesky(double* G, int K, int* perm, double rel_thresh, double* red_v,
-                                int* red_i) {
-  const int t = threadIdx.x;
-  for (int c = t; c < K; c += blockDim.x) perm[c] = c;
-  __syncthreads();
-  double dmax0 = 0.0;
-  for (int c = 0; c < K; ++c) dmax0 = fmax(dmax0, G[c * K + c]);
+// Barrier over `n` threads: the whole CTA (id 0) or one half (ids 1, 2).
+__device__ __forceinline__ void group_sync(int id, int n) {
+  if (id == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// In-place pivoted Cholesky P' G P = R' R of the symmetric K x K matrix G
+// (row-major), run by the `nthr` threads of a group (index ht, barrier bar).
+// Only the upper triangle is read and written (entry (i, j), i <= j, at
+// G[i K + j]); rows are swapped physically.  On return R is the upper
+// triangle of G's first `rank` rows, perm[c] the original index of pivot c.
+// Pivots stop at rel_thresh times the largest initial diagonal.  FP64 issue
+// is the limit here: one rsqrt per pivot, multiplications for the row
+// scaling, and the symmetric half of the trailing update.
+__device__ int pivoted_cholesky(double* G, int K, int* perm, double rel_thresh, double* red_v, int* red_i,
+                                int ht, int nthr, int bar) {
+  for (int c = ht; c < K; c += nthr) perm[c] = c;
+  if (ht < 32) {
+    double m = 0.0;
+    for (int c = ht; c < K; c += 32) m = fmax(m, G[c * K + c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (ht == 0) red_v[0] = m;
+  }
+  group_sync(bar, nthr);
+  const double dmax0 = red_v[0];
   const double thresh = rel_thresh * dmax0;
   int rank = 0;
   for (int p = 0; p < K; ++p) {
-    __syncthreads();
-    warp0_max_sum(G, K + 1, p, K, red_v, red_i);
-    __syncthreads();
-    const double best = red_v[0];
-    const int q = red_i[0];
-    if (!(best > thresh) || dmax0 <= 0.0) break;
-    // symmetric swap of p and q
-    if (q != p) {
-      for (int j = t; j < K; j += blockDim.x) {
-        double a = G[p * K + j];
-        G[p * K + j] = G[q * K + j];
-        G[q * K + j] = a;
+    // pivot: the largest remaining diagonal (ties: smallest index); warp 0 of the group
+    if (ht < 32) {
+      double best = -1.0;
+      int q = -1;
+      for (int c = p + ht; c < K; c += 32) {
+        const double x = G[c * K + c];
+        if (q < 0 || x > best) { best = x; q = c; }
       }
-      __syncthreads();
-      for (int i = t; i < K; i += blockDim.x) {
-        double a = G[i * K + p];
-        G[i * K + p] = G[i * K + q];
-        G[i * K + q] = a;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+        if (oq >= 0 && (q < 0 || ob > best || (ob == best && oq < q))) { best = ob; q = oq; }
       }
-      if (t == 0) {
-        int a = perm[p];
-        perm[p] = perm[q];
-        perm[q] = a;
+      if (ht == 0) {
+        red_v[1] = best;
+        red_i[0] = q;
       }
-      __syncthreads();
     }
-    const double d = sqrt(best);
-    __syncthreads();
-    for (int j = p + t; j < K; j += blockDim.x) G[p * K + j] = (j == p) ? d : G[p * K + j] / d;
-    __syncthreads();
+    group_sync(bar, nthr);
+    const double best = red_v[1];
+    const int q = red_i[0];
+    if (q < 0 || !(best > thresh) || dmax0 <= 0.0) break;
+    if (q != p) {
+      // symmetric swap of indices p and q in the upper-triangle storage
+      for (int x = ht; x < K; x += nthr) {
+        if (x == p || x == q) continue;
+        double* a = &G[min(p, x) * K + max(p, x)];
+        double* b = &G[min(q, x) * K + max(q, x)];
+        const double t = *a;
+        *a = *b;
+        *b = t;
+      }
+      if (ht == 0) {
+        const double t = G[p * K + p];
+        G[p * K + p] = G[q * K + q];
+        G[q * K + q] = t;
+        const int u = perm[p];
+        perm[p] = perm[q];
+        perm[q] = u;
+      }
+      group_sync(bar, nthr);
+    }
+    const double rs = rsqrt(best);  // every thread: one reciprocal square root per pivot
+    for (int j = p + ht; j < K; j += nthr) G[p * K + j] = (j == p) ? best * rs : G[p * K + j] * rs;
+    group_sync(bar, nthr);
+    // trailing update of the upper triangle: (i, j), p < i <= j
     const int w = K - p - 1;
-    for (int e = t; e < w * w; e += blockDim.x) {
-      int i = p + 1 + e / w, j = p + 1 + e % w;
-      G[i * K + j] -= G[p * K + i] * G[p * K + j];
+    const int tri = w * (w + 1) / 2;
+    for (int e = ht; e < tri; e += nthr) {
+      // e -> (i, j), i <= j: rows k and w-1-k paired (w + 1 entries per pair)
+      const int k = e / (w + 1), o = e % (w + 1);
+      int i, j;
+      if (o < w - k) {
+        i = k;
+        j = k + o;
+      } else {
+        i = w - 1 - k;
+        j = i + (o - (w - k));
+      }
+      const int gi = p + 1 + i, gj = p + 1 + j;
+      G[gi * K + gj] -= G[p * K + gi] * G[p * K + gj];
     }
     ++rank;
+    group_sync(bar, nthr);
   }
-  __syncthreads();
+  group_sync(bar, nthr);
   return rank;
 }
 
-__device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
-  // scratch after the three K x K matrices
+// Tail of the truncation when Q and Z do not fit beside the K x K matrices:
+// Q is formed in the output TA (global memory), then staged through GA.
+__device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K, int kf, int rA, int rB, int r,
+                                  bool capped) {
   double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
   double* tau = cn + TRUNC_MAXK;
   double* red_v = tau + TRUNC_MAXK;
@@ -316,129 +364,13 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
   int* posA = permC + TRUNC_MAXK;
   int* posB = posA + TRUNC_MAXK;
   int* red_i = posB + TRUNC_MAXK;
-  const int K = op.K, kf = op.kf, t = threadIdx.x;
+  int* kexp = red_i + 8;
+  const int t = threadIdx.x;
   double* GA = sm;
   double* GB = sm + K * K;
   double* C = sm + 2 * K * K;
-  int* kexp = red_i + 8;  // K ints (the int scratch holds 7 x TRUNC_MAXK)
-  for (int e = t; e < K * K; e += blockDim.x) {
-    GA[e] = op.GA[e];
-    GB[e] = op.GB[e];
-  }
-  __syncthreads();
-  // Balance every column pair (a_i, b_i) by an exact power of two,
-  // a_i 2^k_i and b_i 2^-k_i with |a_i| ~ |b_i|, so that the Gram diagonals
-  // measure the norms |a_i||b_i| of the terms of the sum: otherwise a small
-  // column of A whose partner in B is large falls below the Cholesky cut.
-  for (int i = t; i < K; i += blockDim.x) {
-    const int ea = gram_exponent(GA[i * K + i]), eb = gram_exponent(GB[i * K + i]);
-    kexp[i] = (ea > 0 && eb > 0) ? (eb - ea) >> 2 : 0;
-  }
-  __syncthreads();
-  for (int e = t; e < K * K; e += blockDim.x) {
-    const int s = kexp[e / K] + kexp[e % K];
-    GA[e] *= pow2i(s);
-    GB[e] *= pow2i(-s);
-  }
-  __syncthreads();
-  // Gram entries below (tol/10)^2 of the largest carry nothing the truncation keeps
-  const double rel = fmax(0.01 * op.tol * op.tol, 1e-15);
-  const int rA = pivoted_cholesky(GA, K, permA, rel, red_v, red_i);
-  const int rB = pivoted_cholesky(GB, K, permB, rel, red_v, red_i);
-  for (int c = t; c < K; c += blockDim.x) {
-    posA[permA[c]] = c;
-    posB[permB[c]] = c;
-  }
-  __syncthreads();
-  // C[i][j] = sum_o R_A[i][posA(o)] R_B[j][posB(o)]  (R upper: entry nonzero for col >= row)
-  for (int e = t; e < rA * rB; e += blockDim.x) {
-    int i = e / rB, j = e % rB;
-    double acc = 0.0;
-    for (int o = 0; o < K; ++o) {
-      int ca = posA[o], cb = posB[o];
-      if (ca >= i && cb >= j) acc += GA[i * K + ca] * GB[j * K + cb];
-    }
-    C[i * K + j] = acc;
-  }
-  __syncthreads();
-  // Householder QR of C (rA x rB) with column pivoting; stop on the trailing norm
-  for (int j = t; j < rB; j += blockDim.x) {
-    permC[j] = j;
-    double s = 0.0;
-    for (int i = 0; i < rA; ++i) s += C[i * K + j] * C[i * K + j];
-    cn[j] = s;
-  }
-  __syncthreads();
-  double total = 0.0;
-  for (int j = 0; j < rB; ++j) total += cn[j];
-  int r = 0;
-  const int rmax = min(min(rA, rB), kf);
-  bool capped = false;
-  for (int p = 0; p < min(rA, rB); ++p) {
-    __syncthreads();
-    warp0_max_sum(cn, 1, p, rB, red_v, red_i);
-    __syncthreads();
-    const double rem = red_v[1];
-    if (!(rem > op.tol * op.tol * total) || total <= 0.0) break;
-    if (p == rmax) { capped = true; break; }
-    const int q = red_i[0];
-    if (q != p) {
-      for (int i = t; i < rA; i += blockDim.x) {
-        double a = C[i * K + p];
-        C[i * K + p] = C[i * K + q];
-        C[i * K + q] = a;
-      }
-      if (t == 0) {
-        int a = permC[p]; permC[p] = permC[q]; permC[q] = a;
-        double b = cn[p]; cn[p] = cn[q]; cn[q] = b;
-      }
-    }
-    __syncthreads();
-    // Householder vector for column p, rows p..rA-1 (stored below the diagonal)
-    if ((t >> 5) == 0) {
-      double s = 0.0;
-      for (int i = p + (t & 31); i < rA; i += 32) s += C[i * K + p] * C[i * K + p];
-      s = warp_sum(s);
-      if (t == 0) red_v[3] = s;
-    }
-    __syncthreads();
-    if (t == 0) {
-      double s = red_v[3];
-      double nrm = sqrt(s);
-      double x0 = C[p * K + p];
-      double alpha = x0 >= 0.0 ? -nrm : nrm;
-      double v0 = x0 - alpha;
-      double vnorm2 = s - x0 * x0 + v0 * v0;
-      tau[p] = (vnorm2 > 0.0) ? 2.0 / vnorm2 : 0.0;
-      red_v[1] = v0;
-      red_v[2] = alpha;
-    }
-    __syncthreads();
-    const double v0 = red_v[1], alpha = red_v[2], tp = tau[p];
-    // apply H = I - tau v v' to columns p+1.. (v = [v0, C[p+1..rA-1][p]])
-    for (int j = p + 1 + t; j < rB; j += blockDim.x) {
-      double dot = v0 * C[p * K + j];
-      for (int i = p + 1; i < rA; ++i) dot += C[i * K + p] * C[i * K + j];
-      dot *= tp;
-      C[p * K + j] -= dot * v0;
-      for (int i = p + 1; i < rA; ++i) C[i * K + j] -= dot * C[i * K + p];
-      cn[j] -= C[p * K + j] * C[p * K + j];
-    }
-    __syncthreads();
-    if (t == 0) {
-      C[p * K + p] = alpha;  // R diagonal; v0 kept in red-free storage below
-      cn[p] = v0;            // reuse: v0 of reflector p
-    }
-    __syncthreads();
-    // trailing column norms, recomputed (no downdating drift)
-    for (int j = p + 1 + t; j < rB; j += blockDim.x) {
-      double s = 0.0;
-      for (int i = p + 1; i < rA; ++i) s += C[i * K + j] * C[i * K + j];
-      cn[j] = s;
-    }
-    ++r;
-  }
-  __syncthreads();
+  (void)posA;
+  (void)posB;
   // Q_C[:, :r]: apply reflectors to E = [I_r; 0], stored into GB's free rows? use TA scratch in global
   // Q (rA x r) is formed in the first rA x r entries of a scratch area: reuse GA rows >= rA? Not safe;
   // write Q into op.TA temporarily (K x kf, row-major) then overwrite with the final T_A.
@@ -514,6 +446,235 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
     if (capped) atomicOr(err, DEVERR_RANKCAP);
   }
   __syncthreads();
+}
+
+// Tail of the truncation with Q and Z in shared memory: Q = the first r
+// columns of C's orthogonal factor, TA = R_A^{-1} Q (half 0) and Z = R_C P_C',
+// TB = R_B^{-1} Z (half 1) side by side; reciprocal diagonals precomputed.
+__device__ void trunc_tail_smem(const TruncOp& op, int* err, double* sm, int K, int kf, int rA, int rB, int r,
+                                bool capped) {
+  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
+  double* tau = cn + TRUNC_MAXK;
+  double* red_v = tau + TRUNC_MAXK;
+  int* permA = reinterpret_cast<int*>(red_v + 32);
+  int* permB = permA + TRUNC_MAXK;
+  int* permC = permB + TRUNC_MAXK;
+  int* posA = permC + TRUNC_MAXK;
+  int* posB = posA + TRUNC_MAXK;
+  int* red_i = posB + TRUNC_MAXK;
+  int* kexp = red_i + 8;
+  const int t = threadIdx.x;
+  double* GA = sm;
+  double* GB = sm + K * K;
+  double* C = sm + 2 * K * K;
+  double* Q = sm + 3 * K * K;   // rA x r, stride kf
+  double* Z = Q + K * kf;       // rB x r, stride kf
+  (void)posA;
+  (void)posB;
+  for (int e = t; e < K * kf; e += blockDim.x) Q[e] = 0.0;
+  __syncthreads();
+  for (int c = t; c < r; c += blockDim.x) Q[c * kf + c] = 1.0;
+  // Z[j][c] = R_C[c][pos(j)] (zero below R_C's diagonal), pos(j): permC[pos] = j
+  for (int e = t; e < rB * r; e += blockDim.x) {
+    const int j = e / r, c = e % r;
+    int pc = 0;
+    for (int u = 0; u < rB; ++u)
+      if (permC[u] == j) { pc = u; break; }
+    Z[j * kf + c] = (pc >= c) ? C[c * K + pc] : 0.0;
+  }
+  __syncthreads();
+  for (int p = r - 1; p >= 0; --p) {
+    const double v0 = cn[p], tp = tau[p];
+    for (int c = t; c < r; c += blockDim.x) {
+      double dot = v0 * Q[p * kf + c];
+      for (int i = p + 1; i < rA; ++i) dot += C[i * K + p] * Q[i * kf + c];
+      dot *= tp;
+      Q[p * kf + c] -= dot * v0;
+      for (int i = p + 1; i < rA; ++i) Q[i * kf + c] -= dot * C[i * K + p];
+    }
+    __syncthreads();
+  }
+  // reciprocal diagonals of R_A and R_B (cn and tau are free now)
+  for (int i = t; i < rA; i += blockDim.x) cn[i] = 1.0 / GA[i * K + i];
+  for (int i = t; i < rB; i += blockDim.x) tau[i] = 1.0 / GB[i * K + i];
+  __syncthreads();
+  // back substitutions: half 0 solves R_A X = Q, half 1 solves R_B Y = Z
+  {
+    const int h = t >> 7, ht = t & 127;
+    const double* R = h ? GB : GA;
+    double* X = h ? Z : Q;
+    const double* rd = h ? tau : cn;
+    const int n = h ? rB : rA;
+    for (int c = ht; c < r; c += 128) {
+      for (int i = n - 1; i >= 0; --i) {
+        double v = X[i * kf + c];
+        for (int k = i + 1; k < n; ++k) v -= R[i * K + k] * X[k * kf + c];
+        X[i * kf + c] = v * rd[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < K * kf; e += blockDim.x) {
+    const int i = e / kf, c = e % kf;
+    op.TA[permA[i] * kf + c] = (i < rA && c < r) ? Q[i * kf + c] * pow2i(kexp[permA[i]]) : 0.0;
+    op.TB[permB[i] * kf + c] = (i < rB && c < r) ? Z[i * kf + c] * pow2i(-kexp[permB[i]]) : 0.0;
+  }
+  if (t == 0) {
+    *op.rank = r;
+    if (capped) atomicOr(err, DEVERR_RANKCAP);
+  }
+  __syncthreads();
+}
+
+__device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
+  // scratch after the three K x K matrices
+  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
+  double* tau = cn + TRUNC_MAXK;
+  double* red_v = tau + TRUNC_MAXK;
+  int* permA = reinterpret_cast<int*>(red_v + 32);
+  int* permB = permA + TRUNC_MAXK;
+  int* permC = permB + TRUNC_MAXK;
+  int* posA = permC + TRUNC_MAXK;
+  int* posB = posA + TRUNC_MAXK;
+  int* red_i = posB + TRUNC_MAXK;
+  const int K = op.K, kf = op.kf, t = threadIdx.x;
+  double* GA = sm;
+  double* GB = sm + K * K;
+  double* C = sm + 2 * K * K;
+  int* kexp = red_i + 8;  // K ints (the int scratch holds 7 x TRUNC_MAXK)
+  for (int e = t; e < K * K; e += blockDim.x) {
+    GA[e] = op.GA[e];
+    GB[e] = op.GB[e];
+  }
+  __syncthreads();
+  // Balance every column pair (a_i, b_i) by an exact power of two,
+  // a_i 2^k_i and b_i 2^-k_i with |a_i| ~ |b_i|, so that the Gram diagonals
+  // measure the norms |a_i||b_i| of the terms of the sum: otherwise a small
+  // column of A whose partner in B is large falls below the Cholesky cut.
+  for (int i = t; i < K; i += blockDim.x) {
+    const int ea = gram_exponent(GA[i * K + i]), eb = gram_exponent(GB[i * K + i]);
+    kexp[i] = (ea > 0 && eb > 0) ? (eb - ea) >> 2 : 0;
+  }
+  __syncthreads();
+  for (int e = t; e < K * K; e += blockDim.x) {
+    const int s = kexp[e / K] + kexp[e % K];
+    GA[e] *= pow2i(s);
+    GB[e] *= pow2i(-s);
+  }
+  __syncthreads();
+  // Gram entries below (tol/10)^2 of the largest carry nothing the truncation
+  // keeps.  The two factorizations run side by side on the CTA's halves.
+  const double rel = fmax(0.01 * op.tol * op.tol, 1e-15);
+  {
+    const int h = t >> 7;
+    const int r = pivoted_cholesky(h ? GB : GA, K, h ? permB : permA, rel, red_v + 8 * h, red_i + 4 * h,
+                                   t & 127, 128, 1 + h);
+    if ((t & 127) == 0) red_i[2 + 4 * h] = r;
+  }
+  __syncthreads();
+  const int rA = red_i[2], rB = red_i[6];
+  for (int c = t; c < K; c += blockDim.x) {
+    posA[permA[c]] = c;
+    posB[permB[c]] = c;
+  }
+  __syncthreads();
+  // C[i][j] = sum_o R_A[i][posA(o)] R_B[j][posB(o)] over the upper triangles:
+  // walk A's pivot positions c >= i and keep the terms with posB(o) >= j
+  for (int e = t; e < rA * rB; e += blockDim.x) {
+    const int i = e / rB, j = e % rB;
+    double acc = 0.0;
+    for (int c = i; c < K; ++c) {
+      const int cb = posB[permA[c]];
+      if (cb >= j) acc += GA[i * K + c] * GB[j * K + cb];
+    }
+    C[i * K + j] = acc;
+  }
+  __syncthreads();
+  // Householder QR of C (rA x rB) with column pivoting; stop on the trailing norm
+  for (int j = t; j < rB; j += blockDim.x) {
+    permC[j] = j;
+    double sq = 0.0;
+    for (int i = 0; i < rA; ++i) sq += C[i * K + j] * C[i * K + j];
+    cn[j] = sq;
+  }
+  __syncthreads();
+  if (t < 32) {
+    double sm_ = 0.0;
+    for (int j = t; j < rB; j += 32) sm_ += cn[j];
+    sm_ = warp_sum(sm_);
+    if (t == 0) red_v[4] = sm_;
+  }
+  __syncthreads();
+  const double total = red_v[4];
+  int r = 0;
+  const int rmax = min(min(rA, rB), kf);
+  bool capped = false;
+  for (int p = 0; p < min(rA, rB); ++p) {
+    warp0_max_sum(cn, 1, p, rB, red_v, red_i);
+    __syncthreads();
+    const double rem = red_v[1];
+    if (!(rem > op.tol * op.tol * total) || total <= 0.0) break;
+    if (p == rmax) { capped = true; break; }
+    const int q = red_i[0];
+    // swap columns p and q; the thread that owns row p in the swap (thread p,
+    // rA <= TRUNC_MAXK < blockDim.x) first forms the reflector of column q:
+    // s = sum_{i >= p} C[i][q]^2 is its trailing norm, the maximum red_v[0]
+    if (t == p) {
+      const double sq = red_v[0];
+      const double nrm = sqrt(sq);
+      const double x0 = C[p * K + q];
+      const double alpha = x0 >= 0.0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vnorm2 = sq - x0 * x0 + v0 * v0;
+      tau[p] = (vnorm2 > 0.0) ? 2.0 / vnorm2 : 0.0;
+      red_v[2] = v0;
+      red_v[3] = alpha;
+    }
+    if (q != p) {
+      for (int i = t; i < rA; i += blockDim.x) {
+        const double a = C[i * K + p];
+        C[i * K + p] = C[i * K + q];
+        C[i * K + q] = a;
+      }
+      if (t == 32) {
+        const int a = permC[p];
+        permC[p] = permC[q];
+        permC[q] = a;
+        const double b = cn[p];
+        cn[p] = cn[q];
+        cn[q] = b;
+      }
+    }
+    __syncthreads();
+    const double v0 = red_v[2], alpha = red_v[3], tp = tau[p];
+    // apply H = I - tau v v' to columns p+1.. (v = [v0, C[p+1..rA-1][p]]) and
+    // recompute their trailing norms in the same pass
+    for (int j = p + 1 + t; j < rB; j += blockDim.x) {
+      double dot = v0 * C[p * K + j];
+      for (int i = p + 1; i < rA; ++i) dot += C[i * K + p] * C[i * K + j];
+      dot *= tp;
+      C[p * K + j] -= dot * v0;
+      double sq = 0.0;
+      for (int i = p + 1; i < rA; ++i) {
+        const double x = C[i * K + j] - dot * C[i * K + p];
+        C[i * K + j] = x;
+        sq += x * x;
+      }
+      cn[j] = sq;
+    }
+    if (t == 0) {
+      C[p * K + p] = alpha;  // R diagonal; v0 of reflector p kept in cn[p]
+      cn[p] = v0;
+    }
+    ++r;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (3 * K * K + 2 * K * kf <= 3 * TRUNC_MAXK * TRUNC_MAXK) {
+    trunc_tail_smem(op, err, sm, K, kf, rA, rB, r, capped);
+    return;
+  }
+  trunc_tail_global(op, err, sm, K, kf, rA, rB, r, capped);
 }
 
 __device__ void dev_copy(const CopyOp& op, int chunk, int nchunks) {
@@ -768,6 +929,7 @@ __device__ void dev_vpart(const VPartOp& op, double* smem, int vcap) {
 }
 
 constexpr int EXEC_THREADS = 256;
+static_assert(TRUNC_MAXK < EXEC_THREADS, "the truncation core maps rows of C to threads");
 constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
                              sizeof(int) * 7 * TRUNC_MAXK;
 // shared memory of a solve mode: the larger of a row task's and a partial-product task's needs
