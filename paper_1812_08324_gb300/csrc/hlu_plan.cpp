@@ -172,6 +172,36 @@ class Emitter {
     return v;
   }
 
+  // Pooled scratch for `ns` parts of rows x cols (row-major): part i starts at
+  // element i * stride, a multiple of the dependency tracker's segment of the
+  // pooled buffer (1/64 of its capacity), so that operations on different
+  // parts are independent.  Returns the whole buffer (one row) and the stride.
+  // (The tracker has 64 segments per pooled buffer: more than 64 parts are
+  // laid out contiguously, with some false dependencies between neighbours.)
+  View tmp_parts(int ns, int rows, int cols, int64_t& stride) {
+    const int64_t n = std::max<int64_t>(1, (int64_t)rows * cols);
+    stride = n;
+    if (ns > 64) return tmp(1, (int)(ns * n), false);
+    int c = size_class(ns * n);
+    for (int it = 0; it < 64; ++it) {
+      const int64_t cap = int64_t(1) << c, seg = std::max<int64_t>(1, (cap + 63) / 64);
+      stride = (n + seg - 1) / seg * seg;
+      const int c2 = size_class(ns * stride);
+      if (c2 <= c) break;
+      c = c2;
+    }
+    return tmp(1, (int)(ns * stride), false);
+  }
+  static View part_of(const View& whole, int64_t stride, int i, int rows, int cols) {
+    View v = whole;
+    v.p = whole.p + i * stride;
+    v.rows = rows;
+    v.cols = cols;
+    v.rs = cols;
+    v.cs = 1;
+    return v;
+  }
+
   void release(const View& v) {
     int64_t n = std::max<int64_t>(1, (int64_t)v.rows * v.cols);
     pool[size_class(n)].push_back({v.p, v.buf});
@@ -249,12 +279,13 @@ class Emitter {
   }
 
   // C = beta C + alpha sum_p parts[p]  (parts: nparts blocks of C.rows x C.cols, row-major)
-  void reduce(const View& C, double alpha, const View& parts, int nparts, double beta) {
+  // stride: elements from one part to the next (0: C.rows * C.cols)
+  void reduce(const View& C, double alpha, const View& parts, int nparts, double beta, int64_t stride = 0) {
     int w = beta != 0.0 ? place({{&parts, false}, {&C, false}, {&C, true}}) : place({{&parts, false}, {&C, true}});
     ReduceOp o{};
     o.parts = parts.p;
     o.dst = C.p;
-    o.stride = (int64_t)C.rows * C.cols;
+    o.stride = stride > 0 ? stride : (int64_t)C.rows * C.cols;
     o.drs = C.rs;
     o.dcs = C.cs;
     o.m = C.rows;
@@ -288,13 +319,14 @@ class Emitter {
     }
     if (KS) {
       const int ns = (K + KS - 1) / KS;
-      View parts = tmp(ns * C.rows, C.cols, false);
+      int64_t stride = 0;
+      View parts = tmp_parts(ns, C.rows, C.cols, stride);
       for (int c = 0; c < ns; ++c) {
         int k0 = c * KS, kn = std::min(KS, K - k0);
-        gemm_direct(parts.sub(c * C.rows, 0, C.rows, C.cols), 1.0, Am.sub(0, k0, Am.rows, kn),
+        gemm_direct(part_of(parts, stride, c, C.rows, C.cols), 1.0, Am.sub(0, k0, Am.rows, kn),
                     Bm.sub(k0, 0, kn, Bm.cols), 0.0);
       }
-      reduce(C, alpha, parts, ns, beta);
+      reduce(C, alpha, parts, ns, beta, stride);
       release(parts);
       return;
     }
@@ -371,13 +403,14 @@ class Emitter {
       gemm_direct(G, 1.0, X.T(), X, 0.0);
       return G;
     }
-    View parts = tmp(nch * K, K, false);
+    int64_t stride = 0;
+    View parts = tmp_parts(nch, K, K, stride);
     for (int c = 0; c < nch; ++c) {
       int r0 = c * CH, nr = std::min(CH, X.rows - r0);
       View Xc = X.sub(r0, 0, nr, K);
-      gemm_direct(parts.sub(c * K, 0, K, K), 1.0, Xc.T(), Xc, 0.0);
+      gemm_direct(part_of(parts, stride, c, K, K), 1.0, Xc.T(), Xc, 0.0);
     }
-    reduce(G, 1.0, parts, nch, 0.0);
+    reduce(G, 1.0, parts, nch, 0.0, stride);
     release(parts);
     return G;
   }
