@@ -36,6 +36,7 @@ struct hm_factors {
   std::vector<int> h_rank;
   int capped = 0;
   double fact_ms = 0.0;
+  hm_batch* batch1 = nullptr;  // cn_solve's persistent one-problem batch (created on first use)
   // host copy of the solve schedule, for merging into batched solves
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
@@ -558,10 +559,15 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   // one solve schedule for all problems, in the throughput mode (more CTAs per
   // SM, smaller staging; staging changes where operands are read from, not
   // the arithmetic)
-  std::vector<SchedPart> parts;
-  for (int i = 0; i < count; ++i) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
-  int s = upload_schedules(parts, B->sched, B->allocs, SOLVE_MODE_THROUGHPUT, true);
-  if (s != HM_OK) { set_error("batched solve schedule upload failed"); return fail(s); }
+  int s = HM_OK;
+  if (count == 1) {
+    B->sched = Fs[0]->solve;  // one problem: its own schedule, latency mode (borrowed, not freed here)
+  } else {
+    std::vector<SchedPart> parts;
+    for (int i = 0; i < count; ++i) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
+    s = upload_schedules(parts, B->sched, B->allocs, SOLVE_MODE_THROUGHPUT, true);
+    if (s != HM_OK) { set_error("batched solve schedule upload failed"); return fail(s); }
+  }
   // per problem: Morton-order state x (owned by the batch), rhs, residual,
   // refined iterate, solve output z
   std::vector<MvJob> jA(count), jB(count);
@@ -698,6 +704,7 @@ int hm_batch_graphed(void) { return g_batch_graphed ? 1 : 0; }
 
 void hm_factors_free(hm_factors* F) {
   if (!F) return;
+  if (F->batch1) hm_batch_free(F->batch1);
   cudaDeviceSynchronize();
   for (void* p : F->allocs) cudaFree(p);
   F->arena.release();
@@ -750,6 +757,13 @@ int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int 
   }
   (void)step0;  // the levels of f are relative to step0; the operator is time independent
   cudaStream_t st = (cudaStream_t)stream;
+  if (!f && H->opts.refine_max == 0 && steps > 1) {
+    // no forcing, no refinement: the persistent-batch path with one problem,
+    // one step recorded as a CUDA graph and replayed (same arithmetic)
+    hm_factors* Fb = const_cast<hm_factors*>(F);
+    if (!Fb->batch1) HM_TRY(hm_batch_create(&H, &F, &dt, 1, &Fb->batch1));
+    return hm_batch_step(Fb->batch1, &u, steps, stream);
+  }
   hm_factors* Fm = const_cast<hm_factors*>(F);
   const int N = H->plan.N;
   double* ua = Fm->d_vec + 2 * (size_t)N;
