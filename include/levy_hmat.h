@@ -78,7 +78,17 @@ typedef struct hm_problem {
   double trunc;     /* truncation radius of nu */
   double LW;        /* window half-width L_W */
   double r;         /* rho support radius */
+  /* Variable-order application (Sec. "Application: Variable-Order Fractional
+   * Poisson Equation"); zero for the problems above. */
+  int domain;       /* HM_DOMAIN_BOX, or HM_DOMAIN_L (2D): the box minus its closed upper-right
+                       quadrant (points with both coordinates >= the box centre are not unknowns) */
+  double s_slope;   /* order of the row at x: s(x) = s - s_slope d(x), d = distance from x to the
+                       domain boundary; 0 = constant order.  Non-zero needs HM_NU_STABLE, 2D,
+                       a = b = c = 0 and untruncated nu. */
 } hm_problem;
+
+#define HM_DOMAIN_BOX 0
+#define HM_DOMAIN_L 1
 
 /*
  * Options (App. "Construction and Storage": N_min = leaf, eta of Eq. adm;
@@ -225,6 +235,31 @@ int hm_entries(const hm_matrix* H, int64_t count, const int* rows, const int* co
  * theta = -dt/2.  *out owns its device memory.
  */
 int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out);
+
+/*
+ * hm_factor_shifted: H-LU of M = alpha I + theta G, the same algorithm as
+ * hm_factor (which is alpha = 1).  alpha = 0, theta = 1 factors the generator
+ * itself for the variable-order fractional Poisson problem G u = f (Sec.
+ * "Application: Variable-Order Fractional Poisson Equation"); -G is an
+ * M-matrix there (positive diagonal, non-positive off-diagonal, row sums >= 0),
+ * so LU without pivoting applies.  Factors with alpha != 1 are refused by the
+ * Crank-Nicolson entry points (HM_ERR_ARG); HM_ERR_ARG for non-finite alpha.
+ */
+int hm_factor_shifted(const hm_matrix* H, double alpha, double theta, void* stream, hm_factors** out);
+
+/*
+ * hm_shifted_solve: x with M x = b, M = alpha I + theta G of F's factors
+ * (F from hm_factor or hm_factor_shifted of H), by Richardson iteration
+ * preconditioned with the H-LU:  x_0 = (L U)^{-1} b,
+ * x_{k+1} = x_k + (L U)^{-1} (b - M x_k), M applied by the H-matvec.  Stops
+ * when |b - M x_k| <= tol |b| (2-norms) or after maxit corrections; *iters
+ * gets the corrections taken and *resid the last relative residual (either
+ * may be NULL).  Natural-order device vectors of N doubles; x must not alias
+ * b.  Synchronises the stream once per iteration to test convergence.
+ * HM_ERR_NOT_CONVERGED (x holds the last iterate) when tol was not reached.
+ */
+int hm_shifted_solve(const hm_matrix* H, const hm_factors* F, const double* b, double* x, double tol,
+                     int maxit, void* stream, int* iters, double* resid);
 
 /*
  * hm_factor_batch: hm_factor of `count` independent matrices in one

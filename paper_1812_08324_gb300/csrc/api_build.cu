@@ -26,6 +26,15 @@ int check_problem(const hm_problem* p, const hm_opts* o) {
   if (!(p->LW > 0.0)) { set_error("LW must be > 0"); return HM_ERR_ARG; }
   if (p->kernel == HM_NU_STABLE && !(p->r > 0.0 && p->r <= p->LW)) { set_error("need 0 < r <= LW"); return HM_ERR_ARG; }
   if (!(p->trunc > 0.0)) { set_error("trunc must be > 0"); return HM_ERR_ARG; }
+  if (p->domain != HM_DOMAIN_BOX && p->domain != HM_DOMAIN_L) { set_error("unknown domain"); return HM_ERR_ARG; }
+  if (p->domain == HM_DOMAIN_L && p->dim != 2) { set_error("the L-shaped domain is 2D"); return HM_ERR_ARG; }
+  if (p->s_slope != 0.0) {
+    if (!std::isfinite(p->s_slope) || p->kernel != HM_NU_STABLE || p->dim != 2 || p->a != 0.0 || p->b[0] != 0.0 ||
+        p->b[1] != 0.0 || p->c != 0.0 || std::isfinite(p->trunc)) {
+      set_error("a variable order needs the 2D stable kernel, a = b = c = 0 and no truncation");
+      return HM_ERR_ARG;
+    }
+  }
   if (o->max_rank < 1 || o->max_rank > ACA_MAXK) { set_error("max_rank must lie in [1, 128]"); return HM_ERR_ARG; }
   if (!(o->aca_tol > 0.0)) { set_error("aca_tol must be > 0"); return HM_ERR_ARG; }
   return HM_OK;
@@ -194,6 +203,90 @@ int hm_plan_blocks(const hm_problem* prob, const hm_opts* opts, int* count, int*
   return HM_OK;
 }
 
+// Variable order (Sec. "Application: Variable-Order Fractional Poisson
+// Equation"): s_p = s - s_slope d(x_p) per Morton row.  The row constants
+// lambda_W(s), T(s), kappa(s) are smooth in s: they are computed by the
+// constant-order kernels at 24 Chebyshev points of [min s_p, max s_p] and
+// interpolated per row (Chebyshev series, Clenshaw's recurrence).
+static int variable_order_rows(hm_matrix* H, cudaStream_t st) {
+  const Plan& P = H->plan;
+  const hm_problem& p = H->prob;
+  const int N = P.N;
+  const double h = P.h;
+  const double cx = 0.5 * (p.lo[0] + p.hi[0]), cy = 0.5 * (p.lo[1] + p.hi[1]);
+  std::vector<double> sp(N);
+  double s_lo = 1e300, s_hi = -1e300;
+  for (int q = 0; q < N; ++q) {
+    const double x = p.lo[0] + (P.coord[2 * q] + 1) * h, y = p.lo[1] + (P.coord[2 * q + 1] + 1) * h;
+    double d = std::min(std::min(x - p.lo[0], p.hi[0] - x), std::min(y - p.lo[1], p.hi[1] - y));
+    if (p.domain == HM_DOMAIN_L) d = std::min(d, std::hypot(std::max(0.0, cx - x), std::max(0.0, cy - y)));
+    sp[q] = p.s - p.s_slope * d;
+    s_lo = std::min(s_lo, sp[q]);
+    s_hi = std::max(s_hi, sp[q]);
+  }
+  if (!(s_lo > 0.0 && s_hi < 1.0)) { set_error("the variable order leaves (0, 1)"); return HM_ERR_ARG; }
+  const int M = s_hi - s_lo > 1e-12 ? 24 : 1;
+  const double mid = 0.5 * (s_lo + s_hi), half = 0.5 * (s_hi - s_lo);
+  auto cds = [](double s) { return std::pow(4.0, s) * std::tgamma(1.0 + s) / (M_PI * std::fabs(std::tgamma(-s))); };
+  std::vector<double> fl(M), ft(M), fk(M), tm(M);
+  for (int m = 0; m < M; ++m) {
+    tm[m] = M > 1 ? std::cos(M_PI * (m + 0.5) / M) : 0.0;
+    NuParams q = H->nuq;
+    q.s = mid + half * tm[m];
+    q.cds = cds(q.s);
+    q.expo = 2.0 + 2.0 * q.s;
+    HM_CK(cudaMemsetAsync(H->d_cscratch, 0, sizeof(double) * 8, st));
+    HM_TRY(launch_constants(q, H->d_tab, H->d_cscratch, st));
+    HM_TRY(launch_finalize_constants(q, 0.0, p.b, 0.0, H->d_cscratch, H->d_gc, st));
+    GenConst g;
+    HM_CK(cudaMemcpyAsync(&g, H->d_gc, sizeof(GenConst), cudaMemcpyDeviceToHost, st));
+    HM_CK(cudaStreamSynchronize(st));
+    fl[m] = g.lam_w;
+    ft[m] = g.tail;
+    fk[m] = g.kappa;
+  }
+  // Chebyshev coefficients c_k = (2/M) sum_m f_m T_k(t_m), c_0 halved
+  auto coeffs = [&](const std::vector<double>& f) {
+    std::vector<double> c(M, 0.0);
+    for (int k = 0; k < M; ++k) {
+      for (int m = 0; m < M; ++m) c[k] += f[m] * std::cos(k * M_PI * (m + 0.5) / M);
+      c[k] *= (k == 0 ? 1.0 : 2.0) / M;
+    }
+    return c;
+  };
+  auto clenshaw = [&](const std::vector<double>& c, double t) {
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = M - 1; k >= 1; --k) {
+      const double b0 = 2.0 * t * b1 - b2 + c[k];
+      b2 = b1;
+      b1 = b0;
+    }
+    return t * b1 - b2 + c[0];
+  };
+  const std::vector<double> cl = coeffs(fl), ct = coeffs(ft), ck = coeffs(fk);
+  std::vector<double> rb(N), re(N), rk(N), rd(N);
+  for (int q = 0; q < N; ++q) {
+    const double t = M > 1 ? (sp[q] - mid) / half : 0.0;
+    const double lam = clenshaw(cl, t), tail = clenshaw(ct, t), kap = clenshaw(ck, t);
+    rb[q] = cds(sp[q]) * std::pow(h, -2.0 * sp[q]);
+    re[q] = -(1.0 + sp[q]);
+    rk[q] = kap;
+    rd[q] = -4.0 * kap - lam - tail;
+  }
+  DevArena& A = H->arena;
+  double *db = nullptr, *de = nullptr, *dk = nullptr, *dd = nullptr;
+  HM_TRY(A.upload(&db, rb));
+  HM_TRY(A.upload(&de, re));
+  HM_TRY(A.upload(&dk, rk));
+  HM_TRY(A.upload(&dd, rd));
+  H->ectx.rowB = db;
+  H->ectx.rowE = de;
+  H->ectx.rowK = dk;
+  H->ectx.rowD = dd;
+  H->ectx.nw = H->nuq.nw;
+  return HM_OK;
+}
+
 static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t st, hm_matrix* H) {
   HM_TRY(check_problem(prob, opts));
   HM_TRY(device_ok());
@@ -229,6 +322,7 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
   H->ectx.coord = H->d_coord;
   H->ectx.tab = H->d_tab;
   H->ectx.gc = H->d_gc;
+  if (prob->s_slope != 0.0) HM_TRY(variable_order_rows(H, st));
 
   // dense leaves and low-rank descriptors (host layout)
   int64_t off = 0, uo = 0, vo = 0;

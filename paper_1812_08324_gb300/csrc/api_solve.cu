@@ -20,6 +20,7 @@ namespace { bool g_batch_graphed = false; }
 struct hm_factors {
   const hm_matrix* H = nullptr;
   double theta = 0.0;
+  double alpha = 1.0;  // factors of alpha I + theta G
   int kf = 0;
   Arena arena;
   std::vector<void*> allocs;
@@ -331,7 +332,7 @@ void factor_plan(FactorJob& J) {
   const hm_matrix* H = J.H;
   hm_factors* F = J.F;
   J.status = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, F->kf, F->theta, H->opts.lu_tol,
-                      F->d_rank, F->arena, J.hb);
+                      F->d_rank, F->arena, J.hb, F->alpha);
   if (J.status != HM_OK) { J.err = J.hb.err; return; }
   F->fact_ops = J.hb.ops;
   F->fact_waves = (int)J.hb.waves.size();
@@ -421,14 +422,36 @@ int batch_one_step(hm_batch* B, cudaStream_t cs) {
 }  // namespace
 }  // namespace hm
 
+namespace hm {
+namespace {
+int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const double* thetas, int count,
+                      void* stream, hm_factors** out);
+}
+}  // namespace hm
+
 extern "C" {
 
 int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out) {
   return hm_factor_batch(&H, &theta, 1, stream, out);
 }
 
+int hm_factor_shifted(const hm_matrix* H, double alpha, double theta, void* stream, hm_factors** out) {
+  if (!std::isfinite(alpha)) { set_error("alpha must be finite"); return HM_ERR_ARG; }
+  return factor_batch_impl(&H, &alpha, &theta, 1, stream, out);
+}
+
 int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count, void* stream,
                     hm_factors** out) {
+  return factor_batch_impl(Hs, nullptr, thetas, count, stream, out);
+}
+
+}  // extern "C"
+
+namespace hm {
+namespace {
+// alphas == nullptr: alpha = 1 for every problem
+int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const double* thetas, int count,
+                      void* stream, hm_factors** out) {
   if (!out || !Hs || !thetas || count < 1) { set_error("bad argument"); return HM_ERR_ARG; }
   for (int i = 0; i < count; ++i) out[i] = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
@@ -452,6 +475,7 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
   for (int i = 0; i < count; ++i) {
     if (!Hs[i]) { set_error("null matrix"); return fail_all(HM_ERR_ARG); }
     if ((s = factor_alloc(jobs[i], Hs[i], thetas[i], st)) != HM_OK) return fail_all(s);
+    jobs[i].F->alpha = alphas ? alphas[i] : 1.0;
   }
   // host planning of every H-LU (independent problems: one host thread each)
   phase("allocate");
@@ -530,6 +554,10 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
   }
   return HM_OK;
 }
+}  // namespace
+}  // namespace hm
+
+extern "C" {
 
 int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, const double* dts, int count,
                     hm_batch** out) {
@@ -540,7 +568,7 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   for (int i = 0; i < count; ++i) {
     if (!Hs[i] || !Fs[i]) { set_error("null entry"); return HM_ERR_ARG; }
     if (Fs[i]->H != Hs[i]) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
-    if (!(dts[i] > 0.0) || std::fabs(Fs[i]->theta + 0.5 * dts[i]) > 1e-12 * std::fabs(0.5 * dts[i])) {
+    if (!(dts[i] > 0.0) || Fs[i]->alpha != 1.0 || std::fabs(Fs[i]->theta + 0.5 * dts[i]) > 1e-12 * std::fabs(0.5 * dts[i])) {
       set_error("factors must come from hm_factor(H, -dt/2)");
       return HM_ERR_ARG;
     }
@@ -723,12 +751,61 @@ int hm_solve(const hm_factors* F, const double* b, double* x, void* stream) {
   return launch_scatter(H->d_perm, N, t, x, st);
 }
 
+int hm_shifted_solve(const hm_matrix* H, const hm_factors* F, const double* b, double* x, double tol, int maxit,
+                     void* stream, int* iters, double* resid) {
+  if (!H || !F || !b || !x || maxit < 0 || !(tol >= 0.0)) { set_error("bad argument"); return HM_ERR_ARG; }
+  if (b == x) { set_error("x must not alias b"); return HM_ERR_ARG; }
+  if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  hm_factors* Fm = const_cast<hm_factors*>(F);
+  const int N = H->plan.N;
+  double* bm = Fm->d_vec + 2 * (size_t)N;  // b, Morton order
+  double* xm = Fm->d_vec + 3 * (size_t)N;  // iterate
+  double* r = Fm->d_vec + 4 * (size_t)N;   // residual, then correction
+  if (H->plan.dim == 2) HM_TRY(launch_gather(H->d_perm, N, b, bm, st));
+  else {
+    count_launches(1);
+    copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, b, bm);
+  }
+  // x_0 = M~^{-1} b, then x_{k+1} = x_k + M~^{-1} (b - M x_k) with M = alpha I + theta G
+  HM_TRY(solve_morton(F, bm, xm, st));
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    HM_TRY(hm_matvec_morton(H, -F->alpha, -F->theta, xm, 0.0, nullptr, nullptr, bm, r, st));
+    count_launches(1);
+    norms_kernel<<<1, 1024, 0, st>>>(N, r, bm, F->d_norm);
+    double nrm[2] = {0.0, 0.0};
+    HM_CK(cudaMemcpyAsync(nrm, F->d_norm, sizeof(nrm), cudaMemcpyDeviceToHost, st));
+    HM_CK(cudaStreamSynchronize(st));
+    rel = nrm[1] > 0.0 ? std::sqrt(nrm[0] / nrm[1]) : std::sqrt(nrm[0]);
+    if (!std::isfinite(rel) || rel <= tol || it >= maxit) break;
+    HM_TRY(solve_morton(F, r, r, st));
+    count_launches(1);
+    axpy_kernel<<<vgrid(N), 256, 0, st>>>(N, 1.0, r, xm);
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (resid) *resid = rel;
+  if (H->plan.dim == 2) HM_TRY(launch_scatter(H->d_perm, N, xm, x, st));
+  else {
+    count_launches(1);
+    copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, xm, x);
+  }
+  HM_CK(cudaGetLastError());
+  if (!(rel <= tol)) {
+    set_error("residual " + std::to_string(rel) + " above tol after " + std::to_string(it) + " iterations");
+    return HM_ERR_NOT_CONVERGED;
+  }
+  return HM_OK;
+}
+
 int cn_step(const hm_matrix* H, const hm_factors* F, double dt, const double* u_n, const double* f_n,
             const double* f_np1, double* u_np1, void* stream) {
   if (!H || !F || !u_n || !u_np1) { set_error("null argument"); return HM_ERR_ARG; }
   if (u_n == u_np1) { set_error("u_np1 must not alias u_n"); return HM_ERR_ARG; }
   if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
-  if (!(dt > 0.0) || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+  if (!(dt > 0.0) || F->alpha != 1.0 || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
     set_error("factors must come from hm_factor(H, -dt/2)");
     return HM_ERR_ARG;
   }
@@ -751,7 +828,7 @@ int cn_solve(const hm_matrix* H, const hm_factors* F, double dt, int steps, int 
              const double* f, void* stream) {
   if (!H || !F || !u || steps < 0 || step0 < 0) { set_error("bad argument"); return HM_ERR_ARG; }
   if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
-  if (!(dt > 0.0) || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
+  if (!(dt > 0.0) || F->alpha != 1.0 || std::fabs(F->theta + 0.5 * dt) > 1e-12 * std::fabs(0.5 * dt)) {
     set_error("factors must come from hm_factor(H, -dt/2)");
     return HM_ERR_ARG;
   }

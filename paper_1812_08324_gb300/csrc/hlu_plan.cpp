@@ -850,7 +850,7 @@ class HLU {
 
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
-             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out) {
+             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha) {
   Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
   HLU H(P, E, kf, lu_tol);
   const int nd = (int)dd.size(), nl = (int)ld.size();
@@ -864,12 +864,12 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     View src = E.wrap(const_cast<double*>(d_dense) + D.off, D.m, D.n, D.ld, 1);
     View dst = E.new_mat(D.m, D.n, false, LU_BASE);
     E.copy(dst, theta, &src, 0.0);
-    if (D.r0 == D.c0) {
+    if (D.r0 == D.c0 && alpha != 0.0) {
       View diag = dst;
       diag.cols = 1;
       diag.rs = dst.rs + 1;
       diag.cs = 0;
-      E.copy(diag, 1.0, nullptr, 1.0);
+      E.copy(diag, alpha, nullptr, 1.0);  // + alpha on the diagonal
     }
     H.dense[d] = dst;
   }

@@ -104,12 +104,12 @@ struct HluBuild {
   std::string err;
 };
 
-// Expand H-LU of M = I + theta G for the block tree of `P`.
+// Expand H-LU of M = alpha I + theta G for the block tree of `P`.
 //  dense_pool/ld: H's dense leaves (DenseDesc order), lr: H's low-rank blocks,
 //  d_rank_f: device array (nlr) that will hold the factor ranks.
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
-             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out);
+             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha = 1.0);
 
 // Expand z = U^{-1} L^{-1} b (forward then backward H-triangular
 // substitution, leaf by leaf over the scaled factors) into phases of row and

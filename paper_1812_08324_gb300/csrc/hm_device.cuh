@@ -60,14 +60,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
 // G between Morton positions p (row) and q (column): the formula of Eq. Aij
 // (sign-flipped) with the singular corrections, evaluated from the offset
 // table w(j) nu(|j| h) and the row-independent constants.
+// Jump entry of a variable-order row p (2D stable kernel): trapezoid weight
+// times c_{2,s_p} / |y|^{2+2 s_p} at y = h j, i.e. B_p (|j|^2)^{E_p} with
+// B_p = c_{2,s_p} h^{-2 s_p}, E_p = -(1 + s_p), halved on each window face.
+__device__ __forceinline__ double var_jump(const EntryCtx& E, int p, int a0, int a1) {
+  double v = E.rowB[p] * pow((double)a0 * a0 + (double)a1 * a1, E.rowE[p]);
+  if (a0 == E.nw) v *= 0.5;
+  if (a1 == E.nw) v *= 0.5;
+  return v;
+}
+
 __device__ __forceinline__ double gen_entry(const EntryCtx& E, const GenConst& g, int p, int q) {
   int2 cp = E.coord[p];
   int2 cq = E.coord[q];
   int d0 = cq.x - cp.x;
   int d1 = cq.y - cp.y;
-  if (d0 == 0 && d1 == 0) return g.diag;
   int a0 = d0 < 0 ? -d0 : d0;
   int a1 = d1 < 0 ? -d1 : d1;
+  if (E.rowB) {  // variable order: per-row constants, stencil kappa_p (a = b = c = 0)
+    if (d0 == 0 && d1 == 0) return E.rowD[p];
+    double v = var_jump(E, p, a0, a1);
+    if (a0 + a1 == 1) v += E.rowK[p];
+    return v;
+  }
+  if (d0 == 0 && d1 == 0) return g.diag;
   double v = E.tab[(size_t)a1 * E.n0 + a0];
   if (a0 + a1 == 1) {
     if (a0 == 1) v = v + (d0 > 0 ? g.stencil_p[0] : g.stencil_m[0]);
@@ -82,6 +98,7 @@ __device__ __forceinline__ double far_entry(const EntryCtx& E, int p, int q) {
   int2 cq = E.coord[q];
   int a0 = abs(cq.x - cp.x);
   int a1 = abs(cq.y - cp.y);
+  if (E.rowB) return var_jump(E, p, a0, a1);
   return E.tab[(size_t)a1 * E.n0 + a0];
 }
 

@@ -74,6 +74,13 @@ struct EntryCtx {
   const int2* coord;      // Morton position -> (i0, i1)
   const double* tab;      // w(j) nu(|j| h) for |j0| < n0, |j1| < n1, index j1 * n0 + j0
   const GenConst* gc;     // device copy
+  // variable order (nullptr otherwise), per Morton row p: jump factor B_p,
+  // exponent E_p, stencil kappa_p, diagonal; nw = window half-width in steps
+  const double* rowB = nullptr;
+  const double* rowE = nullptr;
+  const double* rowK = nullptr;
+  const double* rowD = nullptr;
+  int nw = 0;
 };
 
 struct LRDesc {    // low-rank block U V', U: m x kcap, V: n x kcap, column-major

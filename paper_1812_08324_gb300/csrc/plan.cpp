@@ -7,6 +7,9 @@
 #include <cstdint>
 #include <cstring>
 
+#include <vector_types.h>
+#include <vector_functions.h>
+
 #include "hm_internal.h"
 
 namespace hm {
@@ -151,8 +154,16 @@ int make_plan(const hm_problem& p, const hm_opts& o, Plan& P, std::string& err) 
   P.dim = p.dim;
   P.n[0] = p.n[0];
   P.n[1] = p.dim == 2 ? p.n[1] : 1;
-  int64_t N = (int64_t)P.n[0] * P.n[1];
-  if (N > (1 << 26)) { err = "too many unknowns"; return HM_ERR_ARG; }
+  int64_t full = (int64_t)P.n[0] * P.n[1];
+  if (full > (1 << 26)) { err = "too many unknowns"; return HM_ERR_ARG; }
+  // the L-shaped domain drops the grid points with both coordinates at or
+  // beyond the box centre: x_a = lo_a + (i_a + 1) h >= centre_a iff 2 (i_a + 1) >= n_a + 1
+  const bool lshape = p.domain == HM_DOMAIN_L && p.dim == 2;
+  auto inside = [&](int i0, int i1) { return !(lshape && 2 * (i0 + 1) >= P.n[0] + 1 && 2 * (i1 + 1) >= P.n[1] + 1); };
+  int64_t N = 0;
+  for (int i1 = 0; i1 < P.n[1]; ++i1)
+    for (int i0 = 0; i0 < P.n[0]; ++i0) N += inside(i0, i1);
+  if (N < 1) { err = "the domain holds no grid point"; return HM_ERR_ARG; }
   P.N = (int)N;
   P.leaf = o.leaf;
   P.eta = o.eta;
@@ -169,19 +180,25 @@ int make_plan(const hm_problem& p, const hm_opts& o, Plan& P, std::string& err) 
   if (p.dim == 1) {
     for (int i = 0; i < P.N; ++i) { P.perm[i] = i; P.coord[2 * i] = i; }
   } else {
-    std::vector<std::pair<uint64_t, int>> key(P.N);
+    // natural order: the domain's grid points row by row (axis 0 fastest)
+    std::vector<std::pair<uint64_t, int>> key;
+    std::vector<int2> ij;
+    key.reserve(P.N);
+    ij.reserve(P.N);
     for (int i1 = 0; i1 < P.n[1]; ++i1)
       for (int i0 = 0; i0 < P.n[0]; ++i0) {
-        int nat = i0 + P.n[0] * i1;
-        key[nat] = {spread_bits((uint32_t)i0) | (spread_bits((uint32_t)i1) << 1), nat};
+        if (!inside(i0, i1)) continue;
+        const int nat = (int)key.size();
+        key.push_back({spread_bits((uint32_t)i0) | (spread_bits((uint32_t)i1) << 1), nat});
+        ij.push_back(make_int2(i0, i1));
       }
     std::sort(key.begin(), key.end());
     B.code.resize(P.N);
     for (int q = 0; q < P.N; ++q) {
       P.perm[q] = key[q].second;
       B.code[q] = key[q].first;
-      P.coord[2 * q] = key[q].second % P.n[0];
-      P.coord[2 * q + 1] = key[q].second / P.n[0];
+      P.coord[2 * q] = ij[key[q].second].x;
+      P.coord[2 * q + 1] = ij[key[q].second].y;
     }
   }
   for (int q = 0; q < P.N; ++q) P.iperm[P.perm[q]] = q;

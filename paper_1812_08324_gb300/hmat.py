@@ -15,15 +15,17 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "liblevyhm.so")
 
 HM_OK = 0
+HM_ERR_NOT_CONVERGED = -5
 HM_NU_GAUSS, HM_NU_STABLE = 0, 1
 HM_FP64, HM_MIXED_FP32 = 0, 1
+HM_DOMAIN_BOX, HM_DOMAIN_L = 0, 1
 
 EXPORTED = [
     "hm_error_string", "hm_last_error", "hm_plan_info", "hm_plan_blocks", "hm_build",
     "hm_matvec", "hm_to_dense", "hm_entries", "hm_factor", "hm_solve", "cn_step", "cn_solve",
     "hm_sync", "hm_stats", "hm_free", "hm_factors_free", "hm_plan_factor", "hm_launch_count",
     "hm_matvec_noalloc", "hm_factor_batch", "cn_solve_batch", "hm_batch_graphed",
-    "hm_batch_create", "hm_batch_step", "hm_batch_free",
+    "hm_batch_create", "hm_batch_step", "hm_batch_free", "hm_factor_shifted", "hm_shifted_solve",
 ]
 
 
@@ -31,7 +33,7 @@ class Problem(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 2), ("lo", C.c_double * 2), ("hi", C.c_double * 2),
                 ("a", C.c_double), ("b", C.c_double * 2), ("c", C.c_double), ("kernel", C.c_int),
                 ("s", C.c_double), ("eps", C.c_double), ("lam", C.c_double), ("trunc", C.c_double),
-                ("LW", C.c_double), ("r", C.c_double)]
+                ("LW", C.c_double), ("r", C.c_double), ("domain", C.c_int), ("s_slope", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -109,6 +111,8 @@ def load() -> C.CDLL:
         "hm_batch_create": (i, [C.POINTER(vp), C.POINTER(vp), C.POINTER(d), i, C.POINTER(vp)]),
         "hm_batch_step": (i, [vp, C.POINTER(vp), i, vp]),
         "hm_batch_free": (None, [vp]),
+        "hm_factor_shifted": (i, [vp, d, d, vp, C.POINTER(vp)]),
+        "hm_shifted_solve": (i, [vp, vp, vp, vp, d, i, vp, C.POINTER(i), C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -144,6 +148,9 @@ def make_problem(p: dict) -> Problem:
     s.trunc = float(p.get("trunc", math.inf))
     s.LW = float(p["LW"])
     s.r = float(p.get("r", 0.2))
+    domain = p.get("domain", "box")
+    s.domain = domain if isinstance(domain, int) else {"box": HM_DOMAIN_BOX, "L": HM_DOMAIN_L}[domain]
+    s.s_slope = float(p.get("s_slope", 0.0))
     return s
 
 
@@ -267,6 +274,14 @@ class HMatrix:
     def factor(self, theta: float, stream=None) -> "Factors":
         return Factors(self, theta, stream)
 
+    def factor_shifted(self, alpha: float, theta: float, stream=None) -> "Factors":
+        """H-LU factors of alpha I + theta G (alpha = 0, theta = 1: G itself)."""
+        f = C.c_void_p()
+        _check(load().hm_factor_shifted(self._h, float(alpha), float(theta), _stream(stream), C.byref(f)))
+        F = Factors(self, theta, _handle=f.value)
+        F.alpha = float(alpha)
+        return F
+
     def free(self):
         if self._h:
             load().hm_free(self._h)
@@ -280,11 +295,13 @@ class HMatrix:
 
 
 class Factors:
-    """H-LU factors of I + theta G (owned by the library)."""
+    """H-LU factors of alpha I + theta G (owned by the library); alpha = 1
+    unless made by HMatrix.factor_shifted."""
 
     def __init__(self, H: HMatrix, theta: float, stream=None, _handle=None):
         self.H = H
         self.theta = theta
+        self.alpha = 1.0
         self._f = C.c_void_p()
         if _handle is not None:
             self._f = C.c_void_p(_handle)
@@ -325,6 +342,23 @@ def cn_solve(H: HMatrix, F: Factors, dt: float, steps: int, u, f=None, step0: in
     _check(load().cn_solve(H.handle, F._f, dt, int(steps), int(step0), _ptr(u), _ptr(f),
                            _stream(stream)))
     return u
+
+
+def shifted_solve(H: HMatrix, F: Factors, b, tol: float = 1e-12, maxit: int = 50, out=None, stream=None,
+                  check: bool = True):
+    """x with (alpha I + theta G) x = b by H-LU-preconditioned Richardson
+    iteration; returns (x, iterations, relative residual).  With check=False a
+    missed tolerance is reported only through the residual."""
+    import torch
+    if out is None:
+        out = torch.empty_like(b)
+    it = C.c_int(0)
+    res = C.c_double(0.0)
+    st = load().hm_shifted_solve(H.handle, F._f, _ptr(b), _ptr(out), float(tol), int(maxit), _stream(stream),
+                                 C.byref(it), C.byref(res))
+    if check or st != HM_ERR_NOT_CONVERGED:
+        _check(st)
+    return out, it.value, res.value
 
 
 def factor_batch(Hs, thetas, stream=None):

@@ -105,6 +105,41 @@ def merton_1d(n: int = 1023, eps2: float = 5.0, LW: float = 2.0) -> dict:
                 kernel=GAUSS, s=0.0, eps=math.sqrt(eps2), lam=1.0, trunc=math.inf, LW=LW, r=0.2)
 
 
+# ----------------------------------------------------------------------------
+# Variable-order fractional Poisson problem on the L-shaped domain
+# (Sec. "Application: Variable-Order Fractional Poisson Equation")
+# ----------------------------------------------------------------------------
+
+LSHAPE_SOURCES = ((-0.5, 0.5), (0.5, -0.5), (-0.5, -0.5))
+
+
+def lshape_poisson(n: int = 255, s_center: float = 0.9, s_slope: float = 0.8) -> dict:
+    """G u = f on [-1,1]^2 minus [0,1]^2, u = 0 outside: the n x n interior grid
+    of the square (h = 2/(n+1)) without the points of the closed upper-right
+    quadrant, order s(x) = s_center - s_slope d(x) per row, window L_W = 2."""
+    return dict(dim=2, n=[n, n], lo=[-1.0, -1.0], hi=[1.0, 1.0], a=0.0, b=[0.0, 0.0], c=0.0,
+                kernel=STABLE, s=s_center, eps=0.0, lam=0.0, trunc=math.inf, LW=2.0, r=0.2,
+                domain="L", s_slope=s_slope)
+
+
+def lshape_coords(prob: dict) -> np.ndarray:
+    """Coordinates of the unknowns of the L-shaped domain in natural order
+    (the square's order with the removed points skipped)."""
+    n0, n1 = prob["n"]
+    i1, i0 = np.divmod(np.arange(n0 * n1), n0)
+    keep = ~((2 * (i0 + 1) >= n0 + 1) & (2 * (i1 + 1) >= n1 + 1))
+    return coords(prob)[keep]
+
+
+def lshape_source(prob: dict) -> np.ndarray:
+    """f(x) = sum of three Gaussians exp(-10 |x - x_k|^2) at the unknowns."""
+    X = lshape_coords(prob)
+    f = np.zeros(X.shape[0])
+    for cx, cy in LSHAPE_SOURCES:
+        f += np.exp(-10.0 * ((X[:, 0] - cx) ** 2 + (X[:, 1] - cy) ** 2))
+    return f
+
+
 def default_opts(**kw) -> dict:
     o = dict(leaf=64, eta=1.0, aca_tol=1e-10, max_rank=64, lu_tol=1e-10, lu_max_rank=64,
              precision="fp64", refine_tol=1e-13, refine_max=4)

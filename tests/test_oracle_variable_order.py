@@ -60,7 +60,7 @@ def test_rows_reproduce_the_ball_closed_form_per_order():
     for k, i in enumerate(rows):
         u = np.maximum(0.25 - r2, 0.0) ** s_all[i]
         errs.append(abs(G[k] @ u + LD.k_ds(2, s_all[i])) / LD.k_ds(2, s_all[i]))
-    assert max(errs) < 0.05, errs
+    assert max(errs) < 5e-3, errs   # discretisation error ~1e-3; a wrong order misses by > 50%
 
 
 def test_solution_is_symmetric_under_axis_swap():

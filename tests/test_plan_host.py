@@ -96,6 +96,59 @@ def test_morton_order_2d_is_z_curve():
     assert perm.tolist() == z
 
 
+@pytest.mark.parametrize("n,leaf", [(31, 64), (48, 100), (64, 256)])
+def test_lshape_block_tree(n, leaf):
+    """L-shaped domain: the unknowns are the square's grid points outside the
+    closed upper-right quadrant (n^2 - ceil(n/2)^2 of them), the cluster order
+    is their Z-curve order, and the leaf blocks tile the matrix with every
+    admissible block satisfying the eta condition on the true point boxes."""
+    prob = W.lshape_poisson(n)
+    o = W.default_opts(leaf=leaf)
+    info = hmat.plan_info(prob, o)
+    k = (n + 1) // 2
+    assert info["n"] == n * n - k * k
+    N = info["n"]
+    row0, m, col0, nc, typ, perm = hmat.plan_blocks(prob, o)
+    assert sorted(perm.tolist()) == list(range(N))
+    nat = np.array([i0 + n * i1 for i1 in range(n) for i0 in range(n)
+                    if not (2 * (i0 + 1) >= n + 1 and 2 * (i1 + 1) >= n + 1)])
+    ij = np.stack([nat % n, nat // n], axis=1)[perm]
+
+    def spread(v):
+        out = 0
+        for b in range(16):
+            out |= ((int(v) >> b) & 1) << (2 * b)
+        return out
+    codes = [spread(a) | (spread(b) << 1) for a, b in ij]
+    assert codes == sorted(codes)
+    cover = np.zeros((N, N), dtype=np.int32)
+    for b in range(len(row0)):
+        cover[row0[b]:row0[b] + m[b], col0[b]:col0[b] + nc[b]] += 1
+    assert np.all(cover == 1)
+    for b in range(len(row0)):
+        rt, cs = ij[row0[b]:row0[b] + m[b]], ij[col0[b]:col0[b] + nc[b]]
+        bt = (rt.min(0), rt.max(0) + 1)
+        bs = (cs.min(0), cs.max(0) + 1)
+        if typ[b] == 1:
+            assert _adm(bt, bs, o["eta"]), b
+
+
+def test_variable_order_arguments_are_checked():
+    p = W.lshape_poisson(31)
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, dim=1, n=[31, 1]), W.default_opts())     # L-shape is 2D
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, kernel="gauss", eps=1.0), W.default_opts())
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, c=1.0), W.default_opts())
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, trunc=1.0), W.default_opts())
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(dict(p, domain=7), W.default_opts())
+    # constant order on the L-shape is a valid problem
+    assert hmat.plan_info(dict(p, s_slope=0.0), W.default_opts())["n"] == 31 * 31 - 16 * 16
+
+
 def test_bad_arguments_are_rejected(lib):
     p = W.frac_lap_1d(100)
     p["LW"] = 2.0 + 1e-3   # not a whole number of steps is only checked at build; plan ok
