@@ -15,6 +15,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <queue>
+#include <string>
 
 #include "hlu_plan.h"
 
@@ -101,6 +103,9 @@ struct Acc {
 #ifndef HM_KSLICE
 #define HM_KSLICE 64  // smallest split-K slice (build-time tuning parameter)
 #endif
+#ifndef HM_TMP_LAG
+#define HM_TMP_LAG 512  // waves between the last use of a temporary and its reuse (build-time tuning parameter)
+#endif
 #ifndef HM_GRAM_CHUNK
 #define HM_GRAM_CHUNK 64  // rows per partial Gram product (build-time tuning parameter)
 #endif
@@ -134,14 +139,21 @@ class Emitter {
     return v;
   }
 
-  // Temporaries come from a FIFO pool per size class; a recycled buffer keeps
-  // its dependency tracker, so its next writer waits for its last readers.
+  // Temporaries come from a pool per size class.  A buffer is reused only
+  // once the last op that touched it lies at least tmp_lag waves behind the
+  // deepest wave placed so far: its next writer then waits for ops that are
+  // long finished when the executor reaches it, so reuse adds no false
+  // dependency to the critical path (a plain FIFO reuse chains unrelated
+  // operations of the same size class into one long sequence).
   struct Pooled {
+    int lastw;
     double* p;
     int buf;
+    bool operator>(const Pooled& o) const { return lastw > o.lastw; }
   };
-  std::vector<std::vector<Pooled>> pool = std::vector<std::vector<Pooled>>(64);
-  std::vector<size_t> pool_head = std::vector<size_t>(64, 0);
+  using Heap = std::priority_queue<Pooled, std::vector<Pooled>, std::greater<Pooled>>;
+  std::vector<Heap> pool = std::vector<Heap>(64);
+  int tmp_lag = HM_TMP_LAG;
 
   static int size_class(int64_t n) {
     int c = 0;
@@ -158,11 +170,11 @@ class Emitter {
     if (colmajor) { v.rs = 1; v.cs = rows; } else { v.rs = cols; v.cs = 1; }
     v.br0 = 0;
     v.br1 = 1;
-    auto& fl = pool[c];
-    if (pool_head[c] < fl.size()) {
-      v.p = fl[pool_head[c]].p;
-      v.buf = fl[pool_head[c]].buf;
-      ++pool_head[c];
+    Heap& h = pool[c];
+    if (!h.empty() && h.top().lastw < (int)waves.size() - tmp_lag) {
+      v.p = h.top().p;
+      v.buf = h.top().buf;
+      h.pop();
     } else {
       v.p = A.alloc(int64_t(1) << c);
       if (!v.p) status = HM_ERR_OOM;
@@ -204,7 +216,10 @@ class Emitter {
 
   void release(const View& v) {
     int64_t n = std::max<int64_t>(1, (int64_t)v.rows * v.cols);
-    pool[size_class(n)].push_back({v.p, v.buf});
+    const Tracker::Buf& B = T.bufs[v.buf];
+    int lastw = -1;
+    for (size_t s = 0; s < B.lw.size(); ++s) lastw = std::max(lastw, std::max(B.lw[s], B.lr[s]));
+    pool[size_class(n)].push({lastw, v.p, v.buf});
   }
 
   View wrap(double* p, int rows, int cols, int64_t rs, int64_t cs, int seg = -1) {
@@ -852,6 +867,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha) {
   Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
+  if (const char* lag = std::getenv("HM_TMP_LAG")) E.tmp_lag = std::atoi(lag);
   HLU H(P, E, kf, lu_tol);
   const int nd = (int)dd.size(), nl = (int)ld.size();
   H.dense.resize(nd);
@@ -978,6 +994,68 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   }
   out.ops = E.nops;
   for (int i = 0; i < 3; ++i) out.gemm_fma[i] = E.gemm_fma[i];
+  if (std::getenv("HM_CRIT")) {
+    // planning diagnostic: the longest dependency path of the op graph under
+    // a rough cost model (microseconds: 2 per hand-off, 0.26 k per 32 x 32
+    // GEMM tile, 1.5 m per leaf LU, 0.5 K per truncation) and what it is made of
+    const int nops = (int)out.graph.deps.size();
+    std::vector<int> kind(nops, -1);
+    std::vector<double> cost(nops, 0.0);
+    std::vector<std::string> desc(nops);
+    for (const Wave& W : out.waves) {
+      for (size_t j = 0; j < W.gemm.size(); ++j) {
+        const GemmOp& o = W.gemm[j];
+        kind[W.gemm_id[j]] = 0;
+        cost[W.gemm_id[j]] = 2.0 + 0.26 * o.k * (double)std::min(o.m * o.n, 1024) / 1024.0;
+        desc[W.gemm_id[j]] = "gemm " + std::to_string(o.m) + "x" + std::to_string(o.n) + "x" + std::to_string(o.k);
+      }
+      for (size_t j = 0; j < W.lu.size(); ++j) {
+        kind[W.lu_id[j]] = 1;
+        cost[W.lu_id[j]] = 2.0 + 1.5 * W.lu[j].m;
+        desc[W.lu_id[j]] = "lu " + std::to_string(W.lu[j].m);
+      }
+      for (size_t j = 0; j < W.trunc.size(); ++j) {
+        kind[W.trunc_id[j]] = 2;
+        cost[W.trunc_id[j]] = 2.0 + 0.5 * W.trunc[j].K;
+        desc[W.trunc_id[j]] = "trunc K" + std::to_string(W.trunc[j].K);
+      }
+      for (size_t j = 0; j < W.copy.size(); ++j) {
+        kind[W.copy_id[j]] = 3;
+        cost[W.copy_id[j]] = 2.0;
+        desc[W.copy_id[j]] = "copy " + std::to_string(W.copy[j].m) + "x" + std::to_string(W.copy[j].n);
+      }
+      for (size_t j = 0; j < W.reduce.size(); ++j) {
+        kind[W.reduce_id[j]] = 4;
+        cost[W.reduce_id[j]] = 2.0;
+        desc[W.reduce_id[j]] = "reduce " + std::to_string(W.reduce[j].m) + "x" + std::to_string(W.reduce[j].n) + " p" + std::to_string(W.reduce[j].nparts);
+      }
+    }
+    std::vector<double> fin(nops, 0.0);
+    std::vector<int> from(nops, -1);
+    int last = 0;
+    for (int i = 0; i < nops; ++i) {  // ids are topological (deps < id)
+      double st = 0.0;
+      for (int d : out.graph.deps[i]) if (fin[d] > st) { st = fin[d]; from[i] = d; }
+      fin[i] = st + cost[i];
+      if (fin[i] > fin[last]) last = i;
+    }
+    double kc[5] = {0, 0, 0, 0, 0};
+    int kn[5] = {0, 0, 0, 0, 0};
+    int len = 0;
+    std::map<std::string, std::pair<int, double>> dh;
+    for (int i = last; i >= 0; i = from[i]) {
+      if (kind[i] >= 0) { kc[kind[i]] += cost[i]; kn[kind[i]]++; }
+      auto& e = dh[desc[i]]; e.first++; e.second += cost[i];
+      ++len;
+    }
+    fprintf(stderr, "crit: %d waves, weighted path %.1f ms over %d ops\n", (int)out.waves.size(), fin[last] * 1e-3, len);
+    const char* nm[5] = {"gemm", "lu", "trunc", "copy", "reduce"};
+    for (int k = 0; k < 5; ++k) fprintf(stderr, "crit:   %-6s %7d ops %9.1f ms\n", nm[k], kn[k], kc[k] * 1e-3);
+    std::vector<std::pair<double, std::string>> v;
+    for (auto& kv : dh) v.push_back({kv.second.second, kv.first + " x" + std::to_string(kv.second.first)});
+    std::sort(v.rbegin(), v.rend());
+    for (size_t i = 0; i < v.size() && i < 15; ++i) fprintf(stderr, "crit:     %8.1f ms  %s\n", v[i].first * 1e-3, v[i].second.c_str());
+  }
   FactorLayout& F = out.F;
   F.kf = kf;
   (void)F;

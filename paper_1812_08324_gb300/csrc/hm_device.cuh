@@ -57,19 +57,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
   return ok != 0;
 }
 
-// G between Morton positions p (row) and q (column): the formula of Eq. Aij
-// (sign-flipped) with the singular corrections, evaluated from the offset
-// table w(j) nu(|j| h) and the row-independent constants.
 // Jump entry of a variable-order row p (2D stable kernel): trapezoid weight
 // times c_{2,s_p} / |y|^{2+2 s_p} at y = h j, i.e. B_p (|j|^2)^{E_p} with
 // B_p = c_{2,s_p} h^{-2 s_p}, E_p = -(1 + s_p), halved on each window face.
 __device__ __forceinline__ double var_jump(const EntryCtx& E, int p, int a0, int a1) {
+  if (a0 > E.nw || a1 > E.nw) return 0.0;  // outside the window [-L_W, L_W]^2
   double v = E.rowB[p] * pow((double)a0 * a0 + (double)a1 * a1, E.rowE[p]);
   if (a0 == E.nw) v *= 0.5;
   if (a1 == E.nw) v *= 0.5;
   return v;
 }
 
+// G between Morton positions p (row) and q (column): the formula of Eq. Aij
+// (sign-flipped) with the singular corrections, evaluated from the offset
+// table w(j) nu(|j| h) and the row-independent constants.
 __device__ __forceinline__ double gen_entry(const EntryCtx& E, const GenConst& g, int p, int q) {
   int2 cp = E.coord[p];
   int2 cq = E.coord[q];

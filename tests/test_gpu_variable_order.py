@@ -141,8 +141,8 @@ def test_full_size_sampled_residual():
     exact generator (oracle rows), relative to sum_j |G_ij u_j|."""
     n = 255
     prob = W.lshape_poisson(n)
-    H = hmat.HMatrix(prob, W.default_opts(leaf=128, aca_tol=1e-10, max_rank=48, lu_tol=1e-8,
-                                          lu_max_rank=48))
+    H = hmat.HMatrix(prob, W.default_opts(leaf=256, aca_tol=1e-10, max_rank=48, lu_tol=1e-6,
+                                          lu_max_rank=32))
     F = H.factor_shifted(0.0, 1.0)
     f = W.lshape_source(prob)
     u, iters, res = hmat.shifted_solve(H, F, dev(f), tol=1e-12, maxit=50)
