@@ -125,6 +125,10 @@ typedef struct hm_stats_t {
   int last_refine_iters;      /* refinement sweeps used by the last cn_step */
   double last_refine_resid;   /* ||s|| / ||rhs|| after the last cn_step */
   int64_t device_bytes;       /* device memory held by H (and by F when given) */
+  double factor_fma;          /* FP64 FMAs of the factorisation's GEMM tiles (H-LU, solve-block
+                                 inverses, scaled couplings; F given) */
+  double factor_ms;           /* device time of the factorisation's executor launch (F given;
+                                 shared by all problems of one hm_factor_batch) */
 } hm_stats_t;
 
 /* ---- errors ---- */
@@ -248,10 +252,14 @@ int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out);
 int hm_factor_shifted(const hm_matrix* H, double alpha, double theta, void* stream, hm_factors** out);
 
 /*
- * hm_shifted_solve: x with M x = b, M = alpha I + theta G of F's factors
- * (F from hm_factor or hm_factor_shifted of H), by Richardson iteration
- * preconditioned with the H-LU:  x_0 = (L U)^{-1} b,
- * x_{k+1} = x_k + (L U)^{-1} (b - M x_k), M applied by the H-matvec.  Stops
+ * hm_shifted_solve: x with M x = b, M = alpha I + theta G of F's factors,
+ * by Richardson iteration preconditioned with the H-LU:  x_0 = (L U)^{-1} b,
+ * x_{k+1} = x_k + (L U)^{-1} (b - M x_k), M applied by the H-matvec of H.
+ * F comes from hm_factor / hm_factor_shifted of H or of another H-matrix of
+ * the same problem grid (same unknowns, e.g. compressed at a coarser aca_tol:
+ * the paper preconditions with the H-LU of a 1e-4 compression, Sec.
+ * "Application: Variable-Order Fractional Poisson Equation"); HM_ERR_ARG if
+ * the grids differ.  Stops
  * when |b - M x_k| <= tol |b| (2-norms) or after maxit corrections; *iters
  * gets the corrections taken and *resid the last relative residual (either
  * may be NULL).  Natural-order device vectors of N doubles; x must not alias

@@ -37,6 +37,7 @@ struct hm_factors {
   std::vector<int> h_rank;
   int capped = 0;
   double fact_ms = 0.0;
+  double fact_fma = 0.0;
   hm_batch* batch1 = nullptr;  // cn_solve's persistent one-problem batch (created on first use)
   // host copy of the solve schedule, for merging into batched solves
   std::vector<Wave> sw;
@@ -111,8 +112,8 @@ void trace_schedule(const char* what, const std::vector<Wave>& waves, const OpGr
         const unsigned long long* q = &tr[TRACE_STRIDE * t];
         fprintf(f, "%zu %d %d %d %d %llu %llu %llu %llu %llu %llu %llu :", t, T.id, wave_of[T.id], T.kind, T.nsub, q[3],
                 q[0], q[1], q[2], q[4], q[5], q[6]);
-        if (T.id < (int)graph.deps.size())
-          for (int d : graph.deps[T.id]) fprintf(f, " %d", d);
+        if (T.id < graph.size())
+          for (const int* d = graph.begin(T.id); d != graph.end(T.id); ++d) fprintf(f, " %d", *d);
         fprintf(f, "\n");
       }
       fclose(f);
@@ -489,11 +490,11 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaEventRecord(e0, st);
   DevSchedule fs;
   std::vector<void*> fs_allocs;
   s = upload_schedules(parts, fs, fs_allocs, 0, false);
   phase("upload");
+  cudaEventRecord(e0, st);
   int* d_err = Hs[0]->d_err;  // the batch shares the first matrix's error word
   const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
   if (s == HM_OK && tracing && count == 1) {
@@ -510,7 +511,7 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
   for (void* p : fs_allocs) cudaFree(p);
   for (FactorJob& J : jobs) {
     std::vector<Wave>().swap(J.hb.waves);
-    std::vector<std::vector<int>>().swap(J.hb.graph.deps);
+    J.hb.graph.release();
   }
   phase("run H-LU");
   if (s != HM_OK) {
@@ -527,6 +528,7 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
   }
   for (FactorJob& J : jobs) {
     J.F->fact_ms = ms;
+    J.F->fact_fma = J.hb.gemm_fma[0] + J.hb.gemm_fma[1] + J.hb.gemm_fma[2];
     J.F->capped = (e & DEVERR_RANKCAP) ? 1 : 0;  // in a batch: some problem reached its cap
     const int nlr = (int)J.H->h_ld.size();
     J.F->h_rank.assign(nlr, 0);
@@ -755,7 +757,12 @@ int hm_shifted_solve(const hm_matrix* H, const hm_factors* F, const double* b, d
                      void* stream, int* iters, double* resid) {
   if (!H || !F || !b || !x || maxit < 0 || !(tol >= 0.0)) { set_error("bad argument"); return HM_ERR_ARG; }
   if (b == x) { set_error("x must not alias b"); return HM_ERR_ARG; }
-  if (F->H != H) { set_error("factors belong to another matrix"); return HM_ERR_ARG; }
+  // the preconditioner may be factored from another H-matrix of the same grid
+  // (e.g. a coarser compression): both must share the unknowns' order
+  if (F->H != H && (F->H->plan.N != H->plan.N || F->H->plan.perm != H->plan.perm)) {
+    set_error("factors belong to a matrix of another grid");
+    return HM_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   hm_factors* Fm = const_cast<hm_factors*>(F);
   const int N = H->plan.N;
@@ -956,6 +963,8 @@ int hm_stats(const hm_matrix* H, const hm_factors* F, hm_stats_t* out) {
   if (F) {
     for (auto& r : F->arena.ranges) out->device_bytes += (int64_t)(r.second - r.first);
     out->lu_bytes = F->lu_bytes;
+    out->factor_fma = F->fact_fma;
+    out->factor_ms = F->fact_ms;
     int m2 = 0;
     for (int r : F->h_rank) m2 = std::max(m2, r);
     out->lu_max_rank_seen = m2;

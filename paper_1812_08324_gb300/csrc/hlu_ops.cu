@@ -1128,7 +1128,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   std::vector<int> off(parts.size() + 1, 0), soff(parts.size() + 1, 0);
   size_t nw = 0;
   for (size_t p = 0; p < parts.size(); ++p) {
-    off[p + 1] = off[p] + (int)parts[p].graph->deps.size();
+    off[p + 1] = off[p] + parts[p].graph->size();
     soff[p + 1] = soff[p] + (parts[p].srcs ? (int)parts[p].srcs->size() : 0);
     nw = std::max(nw, parts[p].waves->size());
   }
@@ -1136,15 +1136,14 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   std::vector<OpInfo> info(std::max(nops, 1), OpInfo{0, 0, 0, 0});
   std::vector<int> deps;
   size_t ndeps = 0;
-  for (const SchedPart& P : parts)
-    for (const auto& d : P.graph->deps) ndeps += d.size();
+  for (const SchedPart& P : parts) ndeps += P.graph->flat.size();
   deps.reserve(ndeps);
   for (size_t p = 0; p < parts.size(); ++p) {
-    const auto& gd = parts[p].graph->deps;
-    for (size_t i = 0; i < gd.size(); ++i) {
-      const int id = off[p] + (int)i;
+    const OpGraph& gr = *parts[p].graph;
+    for (int i = 0; i < gr.size(); ++i) {
+      const int id = off[p] + i;
       info[id].dep_begin = (int)deps.size();
-      for (int d : gd[i]) deps.push_back(d + off[p]);
+      for (const int* d = gr.begin(i); d != gr.end(i); ++d) deps.push_back(*d + off[p]);
       info[id].dep_end = (int)deps.size();
     }
   }

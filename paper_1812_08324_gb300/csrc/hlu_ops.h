@@ -150,10 +150,19 @@ struct Wave {
 // Producer ops of every op (by op id): an op may start once all its
 // producers have finished (read-after-write, write-after-read, write-after-write).
 struct OpGraph {
-  std::vector<std::vector<int>> deps;
-  int add_op(std::vector<int> d) {
-    deps.push_back(std::move(d));
-    return (int)deps.size() - 1;
+  std::vector<int> off = std::vector<int>(1, 0);  // producers of op i: flat[off[i] .. off[i+1])
+  std::vector<int> flat;
+  int add_op(const std::vector<int>& d) {
+    flat.insert(flat.end(), d.begin(), d.end());
+    off.push_back((int)flat.size());
+    return (int)off.size() - 2;
+  }
+  int size() const { return (int)off.size() - 1; }
+  const int* begin(int i) const { return flat.data() + off[i]; }
+  const int* end(int i) const { return flat.data() + off[i + 1]; }
+  void release() {
+    std::vector<int>(1, 0).swap(off);
+    std::vector<int>().swap(flat);
   }
 };
 

@@ -68,6 +68,7 @@ struct Tracker {
     std::vector<int> lw, lr;              // waves of the last write / latest read
     std::vector<int> wop;                 // op id of the last write (-1: none)
     std::vector<std::vector<int>> rops;   // op ids of the reads since the last write
+    int maxw = -1;                        // latest wave of any access
   };
   std::vector<Buf> bufs;
   int add_elem(const double* base, int64_t cap) {
@@ -79,7 +80,7 @@ struct Tracker {
     b.lr.assign(64, -1);
     b.wop.assign(64, -1);
     b.rops.resize(64);
-    bufs.push_back(b);
+    bufs.push_back(std::move(b));
     return (int)bufs.size() - 1;
   }
   int add(int rows, int seg) {
@@ -90,7 +91,7 @@ struct Tracker {
     b.lr.assign(ns, -1);
     b.wop.assign(ns, -1);
     b.rops.resize(ns);
-    bufs.push_back(b);
+    bufs.push_back(std::move(b));
     return (int)bufs.size() - 1;
   }
 };
@@ -216,10 +217,7 @@ class Emitter {
 
   void release(const View& v) {
     int64_t n = std::max<int64_t>(1, (int64_t)v.rows * v.cols);
-    const Tracker::Buf& B = T.bufs[v.buf];
-    int lastw = -1;
-    for (size_t s = 0; s < B.lw.size(); ++s) lastw = std::max(lastw, std::max(B.lw[s], B.lr[s]));
-    pool[size_class(n)].push({lastw, v.p, v.buf});
+    pool[size_class(n)].push({T.bufs[v.buf].maxw, v.p, v.buf});
   }
 
   View wrap(double* p, int rows, int cols, int64_t rs, int64_t cs, int seg = -1) {
@@ -250,32 +248,37 @@ class Emitter {
   }
 
   // Wave and producers of a new op from its accesses; records the op.
+  std::vector<int> deps;  // scratch of place()
   int place(std::initializer_list<Acc> acc) {
     int w = -1;
-    std::vector<int> deps;
+    deps.clear();
     for (const Acc& a : acc) {
       const View& v = *a.v;
       Tracker::Buf& B = T.bufs[v.buf];
       int s0, s1;
       seg_range(B, v, s0, s1);
       for (int s = s0; s <= s1; ++s) {
+        // neighbouring segments mostly share their writer and readers: skip repeats
         w = std::max(w, B.lw[s]);
-        if (B.wop[s] >= 0) deps.push_back(B.wop[s]);
+        if (B.wop[s] >= 0 && (deps.empty() || deps.back() != B.wop[s])) deps.push_back(B.wop[s]);
         if (a.write) {
           w = std::max(w, B.lr[s]);
-          deps.insert(deps.end(), B.rops[s].begin(), B.rops[s].end());
+          if (s == s0 || B.rops[s] != B.rops[s - 1]) deps.insert(deps.end(), B.rops[s].begin(), B.rops[s].end());
         }
       }
     }
     ++w;
-    std::sort(deps.begin(), deps.end());
-    deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
-    const int id = graph.add_op(std::move(deps));
+    if (deps.size() > 1) {
+      std::sort(deps.begin(), deps.end());
+      deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+    }
+    const int id = graph.add_op(deps);
     for (const Acc& a : acc) {
       const View& v = *a.v;
       Tracker::Buf& B = T.bufs[v.buf];
       int s0, s1;
       seg_range(B, v, s0, s1);
+      B.maxw = std::max(B.maxw, w);
       for (int s = s0; s <= s1; ++s) {
         if (a.write) {
           B.lw[s] = w;
@@ -998,7 +1001,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     // planning diagnostic: the longest dependency path of the op graph under
     // a rough cost model (microseconds: 2 per hand-off, 0.26 k per 32 x 32
     // GEMM tile, 1.5 m per leaf LU, 0.5 K per truncation) and what it is made of
-    const int nops = (int)out.graph.deps.size();
+    const int nops = out.graph.size();
     std::vector<int> kind(nops, -1);
     std::vector<double> cost(nops, 0.0);
     std::vector<std::string> desc(nops);
@@ -1035,7 +1038,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     int last = 0;
     for (int i = 0; i < nops; ++i) {  // ids are topological (deps < id)
       double st = 0.0;
-      for (int d : out.graph.deps[i]) if (fin[d] > st) { st = fin[d]; from[i] = d; }
+      for (const int* d = out.graph.begin(i); d != out.graph.end(i); ++d)
+        if (fin[*d] > st) { st = fin[*d]; from[i] = *d; }
       fin[i] = st + cost[i];
       if (fin[i] > fin[last]) last = i;
     }
@@ -1101,6 +1105,18 @@ struct Src {
   int row_lo = 0, row_hi = 1 << 30;  // rows (relative to the task rows' start) where M can be nonzero
   int tri = 0;                       // 1: M lower triangular, 2: upper triangular (square, cs == 1)
 };
+
+// Stable sort of sources by the phase they are ready in (through an index
+// permutation: a source carries a vector, so moving them in merges is slow).
+void sort_by_ready(std::vector<Src>& v) {
+  std::vector<int> idx(v.size());
+  for (size_t i = 0; i < v.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return v[a].ready < v[b].ready; });
+  std::vector<Src> out;
+  out.reserve(v.size());
+  for (int i : idx) out.push_back(std::move(v[i]));
+  v.swap(out);
+}
 
 // Producer tracking on named resources (vector segments, partial products).
 struct ResTracker {
@@ -1316,7 +1332,7 @@ class SolvePlanner {
       if ((int)cr.size() > ROWS_MAX_SRC) {
         // the critical task stages a bounded number of sources: the earliest
         // ready of the rest join the non-critical groups
-        std::stable_sort(cr.begin(), cr.end(), [](const Src& x, const Src& y) { return x.ready < y.ready; });
+        sort_by_ready(cr);
         const size_t extra = cr.size() - ROWS_MAX_SRC;
         nc.insert(nc.end(), cr.begin(), cr.begin() + extra);
         cr.erase(cr.begin(), cr.begin() + extra);
@@ -1325,7 +1341,7 @@ class SolvePlanner {
       if (!nc.empty()) {
         // non-critical sources in groups of at most ROWS_MAX_SRC, chained through
         // per-group accumulators (acc_g = acc_{g-1} + group g)
-        std::stable_sort(nc.begin(), nc.end(), [](const Src& x, const Src& y) { return x.ready < y.ready; });
+        sort_by_ready(nc);
         // the first group is the block-inverse product alone when it is ready
         // first, so every block's share of it runs in bulk at the start
         std::vector<std::vector<Src>> groups;

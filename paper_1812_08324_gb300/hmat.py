@@ -49,7 +49,8 @@ class Stats(C.Structure):
                 ("h_bytes", C.c_int64), ("lu_bytes", C.c_int64), ("max_rank_seen", C.c_int),
                 ("rank_capped_blocks", C.c_int), ("lu_max_rank_seen", C.c_int),
                 ("lu_rank_capped", C.c_int), ("last_refine_iters", C.c_int),
-                ("last_refine_resid", C.c_double), ("device_bytes", C.c_int64)]
+                ("last_refine_resid", C.c_double), ("device_bytes", C.c_int64),
+                ("factor_fma", C.c_double), ("factor_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

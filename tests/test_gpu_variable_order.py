@@ -91,6 +91,29 @@ def test_poisson_solve_matches_oracle(n, leaf, dense):
     H.free()
 
 
+@pytest.mark.parametrize("n,leaf", CASES[1:])
+def test_coarse_preconditioner(n, leaf, dense):
+    """The paper's setting: the operator compressed accurately, the
+    preconditioner the H-LU of a 1e-4 compression (eps_1 = 1e-4, eps_2 =
+    1e-10).  Richardson still reaches the dense solution; a preconditioner
+    from another grid is refused."""
+    prob, G, u_ref = dense(n)
+    Hop = hmat.HMatrix(W.lshape_poisson(n), _opts(leaf))
+    Hpre = hmat.HMatrix(W.lshape_poisson(n), W.default_opts(leaf=leaf, aca_tol=1e-4, max_rank=48, lu_tol=1e-10,
+                                                            lu_max_rank=48))
+    assert Hpre.stats()["max_rank_seen"] < Hop.stats()["max_rank_seen"]
+    F = Hpre.factor_shifted(0.0, 1.0)
+    f = W.lshape_source(W.lshape_poisson(n))
+    u, iters, res = hmat.shifted_solve(Hop, F, dev(f), tol=1e-12, maxit=60)
+    assert res <= 1e-12 and 1 <= iters <= 40, (iters, res)
+    assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) < 1e-9
+    other = hmat.HMatrix(W.lshape_poisson(n - 2), _opts(leaf))
+    with pytest.raises(hmat.HMError):
+        hmat.shifted_solve(other, F, dev(np.ones(other.n)))
+    for X in (F, other, Hpre, Hop):
+        X.free()
+
+
 def test_shifted_solve_of_cn_matrix():
     """hm_shifted_solve with hm_factor's factors solves I - dt/2 G (alpha = 1)."""
     n = 31
