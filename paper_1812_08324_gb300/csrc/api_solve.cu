@@ -7,6 +7,9 @@
 #include <cstring>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <thread>
 
 #include "api_common.h"
@@ -450,6 +453,150 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
 
 namespace hm {
 namespace {
+
+#ifndef HM_CHUNK_OPS
+#define HM_CHUNK_OPS 131072  // ops per streamed H-LU slice (build-time tuning parameter)
+#endif
+
+// dst += src with op ids shifted by -base
+void append_rebased(Wave& dst, const Wave& src, int base) {
+  auto cat = [base](auto& d, const auto& s, std::vector<int>& di, const std::vector<int>& si) {
+    d.insert(d.end(), s.begin(), s.end());
+    for (int id : si) di.push_back(id - base);
+  };
+  cat(dst.gemm, src.gemm, dst.gemm_id, src.gemm_id);
+  cat(dst.lu, src.lu, dst.lu_id, src.lu_id);
+  cat(dst.trunc, src.trunc, dst.trunc_id, src.trunc_id);
+  cat(dst.copy, src.copy, dst.copy_id, src.copy_id);
+  cat(dst.reduce, src.reduce, dst.reduce_id, src.reduce_id);
+  cat(dst.rows, src.rows, dst.rows_id, src.rows_id);
+  cat(dst.vpart, src.vpart, dst.vpart_id, src.vpart_id);
+}
+
+// Consecutive slices of one problem as one schedule part: ids relative to the
+// first slice, producers in earlier launches dropped (they have finished: the
+// launches run in stream order), the slices' waves merged in global wave order.
+int merge_chunks(std::vector<HluChunk>& ch, std::vector<Wave>& waves, OpGraph& graph) {
+  const int base = ch.front().first;
+  int expect = base;
+  std::vector<int> wv;
+  for (const HluChunk& c : ch) {
+    if (c.first != expect) return HM_ERR_ARG;
+    expect += c.graph.size();
+    wv.insert(wv.end(), c.wave_idx.begin(), c.wave_idx.end());
+  }
+  std::sort(wv.begin(), wv.end());
+  wv.erase(std::unique(wv.begin(), wv.end()), wv.end());
+  waves.assign(wv.size(), Wave());
+  std::vector<int> d;
+  for (HluChunk& c : ch) {
+    for (size_t k = 0; k < c.wave_idx.size(); ++k) {
+      const size_t lw = std::lower_bound(wv.begin(), wv.end(), c.wave_idx[k]) - wv.begin();
+      append_rebased(waves[lw], c.waves[k], base);
+    }
+    for (int j = 0; j < c.graph.size(); ++j) {
+      d.clear();
+      for (const int* p = c.graph.begin(j); p != c.graph.end(j); ++p)
+        if (*p >= base) d.push_back(*p - base);
+      graph.add_op(d);
+    }
+    std::vector<Wave>().swap(c.waves);
+    c.graph.release();
+  }
+  return HM_OK;
+}
+
+// H-LU planning streamed into execution: the planners (one host thread per
+// problem, up to the core count) hand finished slices of their operation
+// lists over; the main thread uploads whatever slices are ready (copies on a
+// non-blocking stream, so the running launch is not waited for) and launches
+// them as the next executor run on `st`.  Planning of later slices overlaps
+// the execution of earlier ones.  e0/e1 bracket the launches.
+int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, cudaEvent_t e0, cudaEvent_t e1,
+                    std::vector<void*>& allocs, int& launches) {
+  const int count = (int)jobs.size();
+  std::mutex m;
+  std::condition_variable cv;
+  std::vector<std::deque<HluChunk>> ready(count);
+  int finished = 0;
+  const char* co = std::getenv("HM_CHUNK_OPS");  // slice size override (tests)
+  const int64_t chunk = co && std::atoll(co) > 0 ? std::atoll(co) : HM_CHUNK_OPS;
+  for (int i = 0; i < count; ++i) {
+    jobs[i].hb.chunk_ops = chunk;
+    jobs[i].hb.sink = [&, i](HluChunk&& c) {
+      std::lock_guard<std::mutex> g(m);
+      ready[i].push_back(std::move(c));
+      cv.notify_one();
+    };
+  }
+  std::atomic<int> next{0};
+  const int nt = std::max(1, std::min<int>(count, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (int i = next++; i < count; i = next++) {
+        factor_plan(jobs[i]);
+        std::lock_guard<std::mutex> g(m);
+        ++finished;
+        cv.notify_one();
+      }
+    });
+  cudaStream_t cs = nullptr;
+  int s = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+  bool started = false;
+  launches = 0;
+  while (s == HM_OK) {
+    std::vector<std::vector<HluChunk>> got(count);
+    bool any = false, done = false;
+    {
+      std::unique_lock<std::mutex> lk(m);
+      cv.wait(lk, [&] {
+        if (finished == count) return true;
+        for (const auto& q : ready)
+          if (!q.empty()) return true;
+        return false;
+      });
+      for (int i = 0; i < count; ++i)
+        for (; !ready[i].empty(); ready[i].pop_front()) {
+          got[i].push_back(std::move(ready[i].front()));
+          any = true;
+        }
+      done = finished == count;
+    }
+    if (!any) {
+      if (done) break;
+      continue;
+    }
+    std::vector<std::vector<Wave>> pw(count);
+    std::vector<OpGraph> pg(count);
+    std::vector<SchedPart> parts;
+    for (int i = 0; i < count && s == HM_OK; ++i) {
+      if (got[i].empty()) continue;
+      s = merge_chunks(got[i], pw[i], pg[i]);
+      parts.push_back(SchedPart{&pw[i], &pg[i], nullptr});
+    }
+    if (s != HM_OK) break;
+    DevSchedule S;
+    s = upload_schedules(parts, S, allocs, 0, false, cs);
+    if (s != HM_OK) break;
+    if (!started) {
+      cudaEventRecord(e0, st);
+      started = true;
+    }
+    s = run_schedule(S, d_err, st);
+    ++launches;
+  }
+  if (!started) cudaEventRecord(e0, st);
+  cudaEventRecord(e1, st);
+  for (auto& th : pool) th.join();  // after an error the planners still finish
+  for (FactorJob& J : jobs) J.hb.sink = nullptr;
+  if (cs) cudaStreamDestroy(cs);
+  return s;
+}
+
+}  // namespace
+
+namespace {
 // alphas == nullptr: alpha = 1 for every problem
 int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const double* thetas, int count,
                       void* stream, hm_factors** out) {
@@ -478,31 +625,47 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
     if ((s = factor_alloc(jobs[i], Hs[i], thetas[i], st)) != HM_OK) return fail_all(s);
     jobs[i].F->alpha = alphas ? alphas[i] : 1.0;
   }
-  // host planning of every H-LU (independent problems: one host thread each)
   phase("allocate");
-  parallel_for(count, [&](int i) { factor_plan(jobs[i]); });
-  for (FactorJob& J : jobs)
-    if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
-  phase("plan H-LU");
-  // one schedule for all: the problems' operation graphs side by side
-  std::vector<SchedPart> parts;
-  for (FactorJob& J : jobs) parts.push_back(SchedPart{&J.hb.waves, &J.hb.graph, nullptr});
+  int* d_err = Hs[0]->d_err;  // the batch shares the first matrix's error word
+  const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
+  const char* pipe = std::getenv("HM_PIPELINE");
+  const bool streamed = !tracing && !(pipe && pipe[0] == '0');
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  DevSchedule fs;
   std::vector<void*> fs_allocs;
-  s = upload_schedules(parts, fs, fs_allocs, 0, false);
-  phase("upload");
-  cudaEventRecord(e0, st);
-  int* d_err = Hs[0]->d_err;  // the batch shares the first matrix's error word
-  const bool tracing = std::getenv("HM_PHASE_TRACE") != nullptr;
-  if (s == HM_OK && tracing && count == 1) {
-    trace_schedule("factor", jobs[0].hb.waves, jobs[0].hb.graph, fs, d_err, st);  // note: runs the factorisation
-  } else if (s == HM_OK) {
-    s = run_schedule(fs, d_err, st);
+  if (streamed) {
+    // planning streamed into execution (slices of the operation lists)
+    int launches = 0;
+    s = factor_streamed(jobs, st, d_err, e0, e1, fs_allocs, launches);
+    for (FactorJob& J : jobs)
+      if (J.status != HM_OK) {
+        cudaStreamSynchronize(st);
+        for (void* p : fs_allocs) cudaFree(p);
+        set_error(J.err);
+        return fail_all(J.status);
+      }
+    if (timing) fprintf(stderr, "[factor x%d] streamed in %d launches\n", count, launches);
+  } else {
+    // host planning of every H-LU (independent problems: one host thread each)
+    parallel_for(count, [&](int i) { factor_plan(jobs[i]); });
+    for (FactorJob& J : jobs)
+      if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
+    phase("plan H-LU");
+    // one schedule for all: the problems' operation graphs side by side
+    std::vector<SchedPart> parts;
+    for (FactorJob& J : jobs) parts.push_back(SchedPart{&J.hb.waves, &J.hb.graph, nullptr});
+    DevSchedule fs;
+    s = upload_schedules(parts, fs, fs_allocs, 0, false);
+    phase("upload");
+    cudaEventRecord(e0, st);
+    if (s == HM_OK && tracing && count == 1) {
+      trace_schedule("factor", jobs[0].hb.waves, jobs[0].hb.graph, fs, d_err, st);  // note: runs the factorisation
+    } else if (s == HM_OK) {
+      s = run_schedule(fs, d_err, st);
+    }
+    cudaEventRecord(e1, st);
   }
-  cudaEventRecord(e1, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);

@@ -1113,7 +1113,7 @@ int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSch
 }
 
 int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::vector<void*>& allocs, int mode,
-                     bool restage) {
+                     bool restage, cudaStream_t copy_stream) {
   std::vector<RowsOp> ro;
   std::vector<VPartOp> vp;
   std::vector<GemmOp> g;
@@ -1219,8 +1219,12 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return HM_ERR_OOM;
     allocs.push_back(p);
-    if (!vec.empty() && cudaMemcpy(p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice) != cudaSuccess)
-      return HM_ERR_CUDA;
+    if (!vec.empty()) {
+      const size_t n = vec.size() * sizeof(vec[0]);
+      const cudaError_t e = copy_stream ? cudaMemcpyAsync(p, vec.data(), n, cudaMemcpyHostToDevice, copy_stream)
+                                        : cudaMemcpy(p, vec.data(), n, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return HM_ERR_CUDA;
+    }
     *dst = (std::remove_reference_t<decltype(**dst)>*)p;
     return HM_OK;
   };
@@ -1241,6 +1245,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   if ((st = up(deps, &S.deps)) != HM_OK) return st;
   std::vector<int> cnt(nops + 1, 0);
   if ((st = up(cnt, &S.counters)) != HM_OK) return st;
+  if (copy_stream && cudaStreamSynchronize(copy_stream) != cudaSuccess) return HM_ERR_CUDA;
   return HM_OK;
 }
 

@@ -152,8 +152,9 @@ struct Wave {
 struct OpGraph {
   std::vector<int> off = std::vector<int>(1, 0);  // producers of op i: flat[off[i] .. off[i+1])
   std::vector<int> flat;
-  int add_op(const std::vector<int>& d) {
-    flat.insert(flat.end(), d.begin(), d.end());
+  int add_op(const std::vector<int>& d) { return add_op(d.data(), d.data() + d.size()); }
+  int add_op(const int* b, const int* e) {
+    flat.insert(flat.end(), b, e);
     off.push_back((int)flat.size());
     return (int)off.size() - 2;
   }
@@ -210,9 +211,11 @@ struct SchedPart {
 };
 // Uploads the parts as one schedule: op ids shift by the ops of the parts
 // before, wave k of every part joins wave k, row tasks' sources shift
-// likewise; restage: re-plan row-task staging for `mode`.
+// likewise; restage: re-plan row-task staging for `mode`.  copy_stream: copy
+// with cudaMemcpyAsync on that (non-blocking) stream, so that an executor
+// running meanwhile is not waited for; the call returns once the copies are done.
 int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::vector<void*>& allocs, int mode,
-                     bool restage);
+                     bool restage, cudaStream_t copy_stream = nullptr);
 
 // mode: executor mode of a solve schedule (ignored when the schedule holds H-LU operations).
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& g, DevSchedule& S,

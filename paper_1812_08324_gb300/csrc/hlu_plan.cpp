@@ -248,8 +248,35 @@ class Emitter {
   }
 
   // Wave and producers of a new op from its accesses; records the op.
+  // streaming of finished slices (HluBuild::sink)
+  std::function<void(HluChunk&&)>* sink = nullptr;
+  int64_t chunk_ops = 0;
+  int chunk_first = 0;
+  int chunk_wmin = 1 << 30;  // lowest wave holding an op of the open slice
+
+  // Hand the ops placed since the last slice to the sink.  Called only at the
+  // start of place() or after the last op: every op placed so far has been
+  // added to its wave by then.
+  void take_chunk() {
+    const int last = graph.size();
+    if (!sink || last == chunk_first) return;
+    HluChunk c;
+    c.first = chunk_first;
+    for (int w = std::min(chunk_wmin, (int)waves.size()); w < (int)waves.size(); ++w) {
+      if (waves[w].size() == 0) continue;
+      c.wave_idx.push_back(w);
+      c.waves.push_back(std::move(waves[w]));
+      waves[w] = Wave();
+    }
+    for (int i = chunk_first; i < last; ++i) c.graph.add_op(graph.begin(i), graph.end(i));
+    chunk_first = last;
+    chunk_wmin = 1 << 30;
+    (*sink)(std::move(c));
+  }
+
   std::vector<int> deps;  // scratch of place()
   int place(std::initializer_list<Acc> acc) {
+    if (sink && graph.size() - chunk_first >= chunk_ops) take_chunk();
     int w = -1;
     deps.clear();
     for (const Acc& a : acc) {
@@ -291,6 +318,7 @@ class Emitter {
       }
     }
     if ((int)waves.size() <= w) waves.resize(w + 1);
+    chunk_wmin = std::min(chunk_wmin, w);
     ++nops;
     cur_id = id;
     return w;
@@ -871,6 +899,10 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha) {
   Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
   if (const char* lag = std::getenv("HM_TMP_LAG")) E.tmp_lag = std::atoi(lag);
+  if (out.sink && out.chunk_ops > 0) {
+    E.sink = &out.sink;
+    E.chunk_ops = out.chunk_ops;
+  }
   HLU H(P, E, kf, lu_tol);
   const int nd = (int)dd.size(), nl = (int)ld.size();
   H.dense.resize(nd);
@@ -997,7 +1029,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   }
   out.ops = E.nops;
   for (int i = 0; i < 3; ++i) out.gemm_fma[i] = E.gemm_fma[i];
-  if (std::getenv("HM_CRIT")) {
+  E.take_chunk();  // the last slice (streaming only)
+  if (std::getenv("HM_CRIT") && !E.sink) {
     // planning diagnostic: the longest dependency path of the op graph under
     // a rough cost model (microseconds: 2 per hand-off, 0.26 k per 32 x 32
     // GEMM tile, 1.5 m per leaf LU, 0.5 K per truncation) and what it is made of

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,17 @@ struct FactorLayout {
 #endif
 constexpr int SOLVE_BLOCK = HM_SOLVE_BLOCK;
 
+// A slice of the H-LU schedule in emission order: the ops with ids
+// [first, first + graph.size()), grouped by their (global) dependency wave,
+// with their producers (global op ids).  Ops only depend on ops of earlier
+// ids, so slices run one after another in emission order.
+struct HluChunk {
+  int first = 0;
+  std::vector<int> wave_idx;  // global wave of waves[i]
+  std::vector<Wave> waves;    // op ids are global
+  OpGraph graph;              // producers of op first + i, global ids
+};
+
 struct HluBuild {
   std::vector<Wave> waves;
   OpGraph graph;
@@ -102,6 +114,11 @@ struct HluBuild {
   int64_t ops = 0;
   double gemm_fma[3] = {0.0, 0.0, 0.0};  // GEMM FMAs: H-LU, solve-block inverses, scaled couplings
   std::string err;
+  // Streaming: with a sink, every chunk_ops ops emitted are handed to it as a
+  // chunk (called on the planning thread), and the rest when planning ends;
+  // `waves` then ends up empty.
+  std::function<void(HluChunk&&)> sink;
+  int64_t chunk_ops = 0;
 };
 
 // Expand H-LU of M = alpha I + theta G for the block tree of `P`.
