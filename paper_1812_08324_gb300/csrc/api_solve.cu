@@ -685,6 +685,10 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
   cudaMemcpy(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e & DEVERR_ZEROPIVOT) { set_error("zero pivot in a leaf LU"); return fail_all(HM_ERR_DEVICE_ASSERT); }
   if (e & DEVERR_TIMEOUT) { set_error("bounded wait gave up in the H-LU schedule"); return fail_all(HM_ERR_TIMEOUT); }
+  if (e & DEVERR_NONFINITE) {
+    set_error("non-finite value, or an H-LU GEMM operand of magnitude >= 2^128 (beyond double-float range)");
+    return fail_all(HM_ERR_DEVICE_ASSERT);
+  }
   if (e & DEVERR_RANKCAP) {
     int z = e & ~DEVERR_RANKCAP;
     cudaMemcpy(d_err, &z, sizeof(int), cudaMemcpyHostToDevice);

@@ -2,6 +2,7 @@
 // with triangular inverses, low-rank truncation cores, copies and reductions.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "hm_device.cuh"
 #include "hlu_ops.h"
@@ -15,38 +16,121 @@ namespace {
 constexpr int GT = 32;   // GEMM output tile (square shape)
 constexpr int GK = 16;   // GEMM k chunk
 
+// Double-float split of an FP64 operand, integer operations only (no FP64
+// instruction, which this GPU issues at 1/64 of the FP32 rate): a = hi + lo + r
+// with hi the significand truncated to 24 bits, lo the next 29 bits rounded to
+// 24, so |r| <= 2^-47 |a|.  |a| < 2^-126 is flushed to zero and the low part
+// of |a| < 2^-74 is dropped (absolute error below 2^-74, far under the FP64
+// rounding of the O(h^-2s) entries these products combine); |a| >= 2^128, inf
+// and NaN set `bad`.
+__device__ __forceinline__ float2 df_split(double a, bool& bad) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  if (e < -126) return make_float2(0.f, 0.f);
+  if (e > 127) {
+    bad = true;
+    return make_float2(0.f, 0.f);
+  }
+  const unsigned sgn = hw & 0x80000000u;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  float lo = 0.f;
+  if (e >= -74) lo = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __int_as_float((e - 52 + 127) << 23));
+  return make_float2(hi, sgn ? -lo : lo);
+}
+
+// (sh, sl) += a b for double-float a, b: the product's high part exactly
+// (FMA), the cross terms rounded (the lo lo term, below 2^-48, is dropped),
+// the sum by Knuth's two-sum.  __f*_rn keep the compiler from contracting or
+// reordering the error terms.
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
 // One TM x TN output tile of C = beta C + alpha A B (256 threads, 1024
 // outputs, 2 x 2 per thread).  Narrow outputs (n or m <= 16) take the 64 x 16
-// or 16 x 64 shape so that no thread computes padding.
-template <int TM, int TN>
-__device__ void gemm_tile(const GemmOp& op, int local, double* smem) {
+// or 16 x 64 shape so that no thread computes padding.  The next k chunk is
+// loaded into registers while the current one is multiplied.  DF: the
+// products and sums in double-float arithmetic on the FP32 pipes (about 48
+// significant bits; see df_split), otherwise FP64.
+template <int TM, int TN, bool DF>
+__device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
   constexpr int TX = TN / 2;  // threads along n
-  double (*As)[GK + 1] = reinterpret_cast<double (*)[GK + 1]>(smem);
-  double (*Bs)[TN + 1] = reinterpret_cast<double (*)[TN + 1]>(smem + TM * (GK + 1));
+  constexpr int NA = TM * GK / 256, NB = GK * TN / 256;  // chunk elements per thread
+  using T = typename std::conditional<DF, float2, double>::type;
+  static_assert(sizeof(T) == sizeof(double), "same shared-memory layout");
+  T (*As)[GK + 1] = reinterpret_cast<T (*)[GK + 1]>(smem);
+  T (*Bs)[TN + 1] = reinterpret_cast<T (*)[TN + 1]>(smem + TM * (GK + 1));
   const int tn = (op.n + TN - 1) / TN;
   const int i0 = (local / tn) * TM, j0 = (local % tn) * TN;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  double ra[NA], rb[NB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = threadIdx.x + 256 * q, r = e / GK, c = e % GK, gi = i0 + r, gk = k0 + c;
+      ra[q] = (gi < op.m && gk < op.k) ? op.A[gi * op.ars + gk * op.acs] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = threadIdx.x + 256 * q, r = e / TN, c = e % TN, gk = k0 + r, gj = j0 + c;
+      rb[q] = (gk < op.k && gj < op.n) ? op.B[gk * op.brs + gj * op.bcs] : 0.0;
+    }
+  };
+  auto stash = [&]() {
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if constexpr (DF) As[e / GK][e % GK] = df_split(ra[q], bad);
+      else As[e / GK][e % GK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if constexpr (DF) Bs[e / TN][e % TN] = df_split(rb[q], bad);
+      else Bs[e / TN][e % TN] = rb[q];
+    }
+    if (bad) atomicOr(err, DEVERR_NONFINITE);
+  };
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+  load(0);
   for (int k0 = 0; k0 < op.k; k0 += GK) {
-    for (int e = threadIdx.x; e < TM * GK; e += 256) {
-      int r = e / GK, c = e % GK;
-      int gi = i0 + r, gk = k0 + c;
-      As[r][c] = (gi < op.m && gk < op.k) ? op.A[gi * op.ars + gk * op.acs] : 0.0;
-    }
-    for (int e = threadIdx.x; e < GK * TN; e += 256) {
-      int r = e / TN, c = e % TN;
-      int gk = k0 + r, gj = j0 + c;
-      Bs[r][c] = (gk < op.k && gj < op.n) ? op.B[gk * op.brs + gj * op.bcs] : 0.0;
-    }
+    stash();
     __syncthreads();
+    if (k0 + GK < op.k) load(k0 + GK);  // in flight during this chunk's arithmetic
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
-      double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] += a0 * b0;
-      acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0;
-      acc[1][1] += a1 * b1;
+      const T a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
+      const T b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      if constexpr (DF) {
+        df_acc(sh[0], sl[0], a0, b0);
+        df_acc(sh[1], sl[1], a0, b1);
+        df_acc(sh[2], sl[2], a1, b0);
+        df_acc(sh[3], sl[3], a1, b1);
+      } else {
+        acc[0] += a0 * b0;
+        acc[1] += a0 * b1;
+        acc[2] += a1 * b0;
+        acc[3] += a1 * b1;
+      }
+    }
+    if constexpr (DF) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // renormalise: |sl| stays below an ulp of sh
+        const float s = __fadd_rn(sh[q], sl[q]);
+        sl[q] = __fsub_rn(sl[q], __fsub_rn(s, sh[q]));
+        sh[q] = s;
+      }
     }
     __syncthreads();
   }
@@ -57,17 +141,26 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem) {
       int gi = i0 + ty * 2 + a, gj = j0 + tx * 2 + b;
       if (gi < op.m && gj < op.n) {
         double* c = op.C + gi * op.crs + gj * op.ccs;
-        double v = op.alpha * acc[a][b];
+        const double r = DF ? (double)sh[2 * a + b] + (double)sl[2 * a + b] : acc[2 * a + b];
+        double v = op.alpha * r;
         *c = op.beta == 0.0 ? v : op.beta * (*c) + v;
       }
     }
   __syncthreads();
 }
 
-__device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem) {
-  if (op.shape == 1) gemm_tile<64, 16>(op, local, smem);
-  else if (op.shape == 2) gemm_tile<16, 64>(op, local, smem);
-  else gemm_tile<32, 32>(op, local, smem);
+// op.shape: bits 0-1 the tile shape (gemm_shape), bit 2 set = FP64 arithmetic
+__device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
+  const int sh = op.shape & 3;
+  if (op.shape & GEMM_FP64) {
+    if (sh == 1) gemm_tile<64, 16, false>(op, local, smem, err);
+    else if (sh == 2) gemm_tile<16, 64, false>(op, local, smem, err);
+    else gemm_tile<32, 32, false>(op, local, smem, err);
+  } else {
+    if (sh == 1) gemm_tile<64, 16, true>(op, local, smem, err);
+    else if (sh == 2) gemm_tile<16, 64, true>(op, local, smem, err);
+    else gemm_tile<32, 32, true>(op, local, smem, err);
+  }
 }
 
 // Base LU (m <= LU_BASE) in shared memory, then the inverses of L (unit
@@ -1047,7 +1140,7 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
     if (a.trace && threadIdx.x == 0) a.trace[TRACE_STRIDE * (size_t)t + 1] = global_ns();
     if constexpr (!SOLVE) {
       switch (T.kind) {
-        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem); break;
+        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem, a.err); break;
         case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
         case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
         default: break;
@@ -1155,6 +1248,8 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   // copies and reductions are split so that one task does about 2048 FP64
   // operations (a few microseconds on one SM)
   auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
+  const char* g64 = std::getenv("HM_GEMM_FP64");  // FP64 instead of double-float GEMM tiles
+  const bool gemm_fp64 = g64 && g64[0] == '1';
   for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
     for (size_t p = 0; p < parts.size(); ++p) {
@@ -1163,7 +1258,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
       const int o0 = off[p];
       for (size_t k = 0; k < W.gemm.size(); ++k) {
         GemmOp o = W.gemm[k];
-        o.shape = gemm_shape(o.m, o.n);
+        o.shape = gemm_shape(o.m, o.n) | (gemm_fp64 ? GEMM_FP64 : 0);
         int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k] + o0;
         for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
         info[id].ntasks = nt;

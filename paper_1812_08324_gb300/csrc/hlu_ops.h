@@ -14,12 +14,15 @@
 namespace hm {
 
 // C = beta C + alpha A B on strided views: X(i, j) = X[i * rs + j * cs].
+// GemmOp::shape flag: FP64 arithmetic instead of double-float (HM_GEMM_FP64=1)
+constexpr int GEMM_FP64 = 4;
+
 struct GemmOp {
   const double* A;
   const double* B;
   double* C;
   int m, n, k;
-  int shape;         // output tile: 0 = 32 x 32, 1 = 64 x 16, 2 = 16 x 64 (gemm_shape)
+  int shape;         // output tile: 0 = 32 x 32, 1 = 64 x 16, 2 = 16 x 64 (gemm_shape), | GEMM_FP64
   int64_t ars, acs, brs, bcs, crs, ccs;
   double alpha, beta;
 };

@@ -141,3 +141,22 @@ def test_streamed_factor_equals_unstreamed(name, prob, opts, dt, monkeypatch):
     monkeypatch.delenv("HM_CHUNK_OPS")
     H.free()
     assert np.array_equal(x0, x1)
+
+
+@pytest.mark.parametrize("name,prob,opts,dt", CASES, ids=[c[0] for c in CASES])
+def test_double_float_gemm_matches_fp64(name, prob, opts, dt, monkeypatch):
+    """The H-LU's GEMM tiles in double-float arithmetic (operands split into
+    two floats, 2^-47 relative, sums by two-sum) agree with the same tiles in
+    FP64 to far below the compression tolerances."""
+    H = hmat.HMatrix(prob, opts)
+    b = dev(np.random.default_rng(4).standard_normal(H.n))
+    monkeypatch.setenv("HM_GEMM_FP64", "1")
+    F0 = H.factor(-0.5 * dt)
+    x0 = host(F0.solve(b))
+    F0.free()
+    monkeypatch.setenv("HM_GEMM_FP64", "0")
+    F1 = H.factor(-0.5 * dt)
+    x1 = host(F1.solve(b))
+    F1.free()
+    H.free()
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) < 1e-12
