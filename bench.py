@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "levy_batch", "serve", "lshape"])
     ap.add_argument("--lshape-n", type=int, default=255, help="grid side of the L-shaped Poisson workload")
     ap.add_argument("--serve-count", type=int, default=200)
-    ap.add_argument("--serve-sides", default="32,48,64", help="2D grid sides of the served stream")
+    ap.add_argument("--serve-sides", default="64,128", help="2D grid sides of the served stream")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--group-unknowns", type=int, default=1200000)
     return ap.parse_args()

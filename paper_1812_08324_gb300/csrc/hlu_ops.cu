@@ -17,12 +17,12 @@ constexpr int GT = 32;   // GEMM output tile (square shape)
 constexpr int GK = 16;   // GEMM k chunk
 
 // Double-float split of an FP64 operand, integer operations only (no FP64
-// instruction, which this GPU issues at 1/64 of the FP32 rate): a = hi + lo + r
-// with hi the significand truncated to 24 bits, lo the next 29 bits rounded to
-// 24, so |r| <= 2^-47 |a|.  |a| < 2^-126 is flushed to zero and the low part
-// of |a| < 2^-74 is dropped (absolute error below 2^-74, far under the FP64
-// rounding of the O(h^-2s) entries these products combine); |a| >= 2^128, inf
-// and NaN set `bad`.
+// instruction, which this GPU issues at 1/64 of the FP32 rate): hi is the
+// significand rounded to nearest at 24 bits (an integer add on the float's bit
+// pattern carries into the exponent), lo the signed remainder, 29 bits rounded
+// to 24, so a = hi + lo + r with |r| <= 2^-49 |a|.  |a| < 2^-126 is flushed
+// to zero and the low part of |a| < 2^-74 is dropped (absolute error below
+// 2^-74); |a| >= 2^128 (after rounding), inf and NaN set `bad`.
 __device__ __forceinline__ float2 df_split(double a, bool& bad) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(a);
   const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
@@ -33,10 +33,16 @@ __device__ __forceinline__ float2 df_split(double a, bool& bad) {
     return make_float2(0.f, 0.f);
   }
   const unsigned sgn = hw & 0x80000000u;
-  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const unsigned r = lw & 0x1fffffffu;  // the 29 bits below hi's last, in units of 2^(e-52)
+  const unsigned up = r >> 28;          // round half up on the magnitude
+  const unsigned hb = (((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29)) + up;
+  if ((hb >> 23) >= 255u) {
+    bad = true;
+    return make_float2(0.f, 0.f);
+  }
   float lo = 0.f;
-  if (e >= -74) lo = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __int_as_float((e - 52 + 127) << 23));
-  return make_float2(hi, sgn ? -lo : lo);
+  if (e >= -74) lo = __fmul_rn(__int2float_rn((int)r - (int)(up << 29)), __int_as_float((e - 52 + 127) << 23));
+  return make_float2(__uint_as_float(sgn | hb), sgn ? -lo : lo);
 }
 
 // (sh, sl) += a b for double-float a, b: the product's high part exactly
@@ -60,7 +66,8 @@ __device__ __forceinline__ void df_acc(float& sh, float& sl, float2 a, float2 b)
 // or 16 x 64 shape so that no thread computes padding.  The next k chunk is
 // loaded into registers while the current one is multiplied.  DF: the
 // products and sums in double-float arithmetic on the FP32 pipes (about 48
-// significant bits; see df_split), otherwise FP64.
+// significant bits: operands to 2^-49, each product and addition to about
+// 2^-48 of its terms), otherwise FP64.
 template <int TM, int TN, bool DF>
 __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
   constexpr int TX = TN / 2;  // threads along n
@@ -117,19 +124,19 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
         df_acc(sh[1], sl[1], a0, b1);
         df_acc(sh[2], sl[2], a1, b0);
         df_acc(sh[3], sl[3], a1, b1);
+        if ((kk & 3) == 3) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {  // renormalise every 4 terms: sl stays within an ulp of sh
+            const float s = __fadd_rn(sh[q], sl[q]);
+            sl[q] = __fsub_rn(sl[q], __fsub_rn(s, sh[q]));
+            sh[q] = s;
+          }
+        }
       } else {
         acc[0] += a0 * b0;
         acc[1] += a0 * b1;
         acc[2] += a1 * b0;
         acc[3] += a1 * b1;
-      }
-    }
-    if constexpr (DF) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {  // renormalise: |sl| stays below an ulp of sh
-        const float s = __fadd_rn(sh[q], sl[q]);
-        sl[q] = __fsub_rn(sl[q], __fsub_rn(s, sh[q]));
-        sh[q] = s;
       }
     }
     __syncthreads();
