@@ -250,7 +250,8 @@ class Emitter {
   // Wave and producers of a new op from its accesses; records the op.
   // streaming of finished slices (HluBuild::sink)
   std::function<void(HluChunk&&)>* sink = nullptr;
-  int64_t chunk_ops = 0;
+  int64_t chunk_ops = 0;   // slice size; the first slices are smaller (8x, 4x, 2x) so the GPU starts early
+  int64_t chunk_cur = 0;
   int chunk_first = 0;
   int chunk_wmin = 1 << 30;  // lowest wave holding an op of the open slice
 
@@ -271,12 +272,13 @@ class Emitter {
     for (int i = chunk_first; i < last; ++i) c.graph.add_op(graph.begin(i), graph.end(i));
     chunk_first = last;
     chunk_wmin = 1 << 30;
+    chunk_cur = std::min(chunk_ops, 2 * chunk_cur);
     (*sink)(std::move(c));
   }
 
   std::vector<int> deps;  // scratch of place()
   int place(std::initializer_list<Acc> acc) {
-    if (sink && graph.size() - chunk_first >= chunk_ops) take_chunk();
+    if (sink && graph.size() - chunk_first >= chunk_cur) take_chunk();
     int w = -1;
     deps.clear();
     for (const Acc& a : acc) {
@@ -902,6 +904,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   if (out.sink && out.chunk_ops > 0) {
     E.sink = &out.sink;
     E.chunk_ops = out.chunk_ops;
+    E.chunk_cur = std::max<int64_t>(1, out.chunk_ops / 8);
   }
   HLU H(P, E, kf, lu_tol);
   const int nd = (int)dd.size(), nl = (int)ld.size();
@@ -1196,7 +1199,10 @@ struct ResTracker {
 // chunk of rows); a reader of the leaf depends on every chunk.
 int64_t key_y(int sweep, int p, int c = 0) { return (int64_t(1 + sweep) << 40) | (int64_t(p) << 12) | c; }
 int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 44) | (int64_t(p) << 12) | c; }
-constexpr int CR_ROWS = 8, NC_ROWS = 32;
+#ifndef HM_CR_ROWS
+#define HM_CR_ROWS 8  // rows per critical row task (build-time tuning parameter)
+#endif
+constexpr int CR_ROWS = HM_CR_ROWS, NC_ROWS = 32;
 #ifndef HM_NC_LEAD
 #define HM_NC_LEAD 8  // phases by which non-critical row groups precede their block (tuning parameter)
 #endif
