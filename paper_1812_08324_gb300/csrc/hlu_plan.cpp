@@ -954,12 +954,16 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   // Solve blocks and their exact diagonal inverses, then the scaled couplings.
   FactorLayout& FL = out.F;
   {
+    // 1D problems from 32768 unknowns use solve blocks twice as large: half as
+    // many steps on the solve's dependency chain for 36 % more inverse FMAs
+    // (measured at N = 65536: solve 1.57 -> 1.42 ms, factor +0.06 s)
+    const int sb_rows = (P.dim == 1 && P.N >= 32768) ? 2 * SOLVE_BLOCK : SOLVE_BLOCK;
     std::vector<int> stack = {0};
     while (!stack.empty()) {
       int c = stack.back();
       stack.pop_back();
       const Cluster& C = P.cl[c];
-      if (C.end - C.begin <= SOLVE_BLOCK || C.nchild == 0) {
+      if (C.end - C.begin <= sb_rows || C.nchild == 0) {
         FL.sb_cluster.push_back(c);
       } else {
         for (int k = C.nchild - 1; k >= 0; --k) stack.push_back(C.child[k]);

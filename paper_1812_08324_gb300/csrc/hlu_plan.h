@@ -72,7 +72,7 @@ struct FactorLayout {
   int kf = 0;
   int* d_rank = nullptr;                 // per LR block rank (device)
   // Solve blocks: a cut of the cluster tree (clusters of at most
-  // SOLVE_BLOCK rows).  Each keeps the exact inverses of its diagonal factor
+  // SOLVE_BLOCK rows, twice that for 1D problems of >= 32768 unknowns).  Each keeps the exact inverses of its diagonal factor
   // blocks L_BB and U_BB (dense, row-major), and every factor block that
   // couples two solve blocks is stored scaled by the inverse of its row
   // block: P = L_BB^{-1} L_BA (dense blocks, S x n) or L_BB^{-1} U_q (rows of a
