@@ -405,7 +405,8 @@ def run_lshape(args):
     roofline = {"kernel": "exec_kernel<0> (H-LU schedule of the preconditioner)", "bound": "alu",
                 "achieved": gflops, "peak": fp64_peak, "unit": "GFLOP/s",
                 "frac": gflops / fp64_peak if gflops else None, "traffic": None,
-                "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2.07 GHz (nominal unit count and clock)",
+                "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2.07 GHz (nominal unit count and clock); "
+                               "achieved counts FP64-equivalent GEMM FLOPs, the tiles run double-float on the FP32 pipes",
                 "algorithmic_flops": 2.0 * s_pre["factor_fma"], "ms": s_pre["factor_ms"]}
     # accuracy: sampled rows of the exact generator are checked in the tests; here the
     # residual against the accurate operator and the iteration count
