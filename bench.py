@@ -654,12 +654,12 @@ def main():
     sv_ms = s0.elapsed_time(s1) / 10
     sv_gbs = st["lu_bytes"] / (sv_ms * 1e-3) / 1e9
     # DRAM traffic of one solve launch from an ncu capture of the same kernel at
-    # N = 32768 (dram__bytes_read.sum + dram__bytes_write.sum = 516.5 MB against
-    # lu_bytes = 393.6 MB there), scaled to this launch by its factor bytes
-    # (traffic grows in proportion to N in 1D)
+    # N = 32768 (2048-row solve blocks as here; dram__bytes_read.sum +
+    # dram__bytes_write.sum = 786.7 MB against lu_bytes = 393.6 MB there), scaled
+    # to this launch by its factor bytes (traffic grows in proportion to N in 1D)
     roofline = {"kernel": "exec_kernel (H-triangular solve schedule)", "bound": "hbm",
                 "achieved": sv_gbs, "peak": hbm, "unit": "GB/s", "frac": sv_gbs / hbm,
-                "traffic": st["lu_bytes"] * 516.5 / 393.6, "traffic_source": "ncu at N=32768, scaled by lu_bytes",
+                "traffic": st["lu_bytes"] * 786.7 / 393.6, "traffic_source": "ncu at N=32768, scaled by lu_bytes",
                 "peak_source": f"hbm_gbs {peak_src}", "algorithmic_bytes": st["lu_bytes"], "ms": sv_ms}
     mv_roof = {"kernel": "H-matvec (vt_kernel + vt_reduce + rows_kernel)", "bound": "hbm", "achieved": mv_gbs,
                "peak": hbm, "unit": "GB/s", "frac": mv_gbs / hbm, "traffic": None,
