@@ -1206,7 +1206,10 @@ int64_t key_acc(int sweep, int p, int c = 0) { return (int64_t(7 + sweep) << 44)
 #ifndef HM_CR_ROWS
 #define HM_CR_ROWS 8  // rows per critical row task (build-time tuning parameter)
 #endif
-constexpr int CR_ROWS = HM_CR_ROWS, NC_ROWS = 32;
+#ifndef HM_NC_ROWS
+#define HM_NC_ROWS 32  // rows per non-critical row task (build-time tuning parameter)
+#endif
+constexpr int CR_ROWS = HM_CR_ROWS, NC_ROWS = HM_NC_ROWS;
 #ifndef HM_NC_LEAD
 #define HM_NC_LEAD 8  // phases by which non-critical row groups precede their block (tuning parameter)
 #endif
