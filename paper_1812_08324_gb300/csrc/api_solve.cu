@@ -642,6 +642,8 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
       if (J.status != HM_OK) {
         cudaStreamSynchronize(st);
         for (void* p : fs_allocs) cudaFree(p);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
         set_error(J.err);
         return fail_all(J.status);
       }

@@ -261,6 +261,9 @@ class Emitter {
   void take_chunk() {
     const int last = graph.size();
     if (!sink || last == chunk_first) return;
+    // once an allocation has failed, ops may hold null operands: nothing more
+    // is handed out (the slices given earlier precede the failure)
+    if (status != HM_OK || A.status != HM_OK) return;
     HluChunk c;
     c.first = chunk_first;
     for (int w = std::min(chunk_wmin, (int)waves.size()); w < (int)waves.size(); ++w) {
