@@ -74,3 +74,27 @@ def test_solution_is_symmetric_under_axis_swap():
     swap = np.array([key[(round(b, 12), round(a, 12))] for a, b in X])
     np.testing.assert_allclose(u, u[swap], rtol=1e-10, atol=1e-14)
     assert np.all(u < 0)   # G = -(-Delta)^s: positive sources give a negative solution
+
+
+def test_per_order_constants_are_smooth_in_s():
+    """The per-row constants lambda_W(s), T(s), kappa(s) of the variable-order
+    rows are analytic in s over the range the L-shaped problem uses: a
+    24-node Chebyshev interpolant (what the device evaluates per row)
+    reproduces the oracle's direct evaluation to 1e-12 of their scale."""
+    prob = VO.lshape_problem(127)
+    s = VO.order(prob, VO.points(prob))
+    lo, hi = float(s.min()), float(s.max())
+    M = 24
+    t = np.cos(np.pi * (np.arange(M) + 0.5) / M)
+    nodes = 0.5 * (lo + hi) + 0.5 * (hi - lo) * t
+    F = np.array([LD.jump_constants(dict(prob, s=float(x))) for x in nodes])   # M x 3
+    k = np.arange(M)
+    C = (2.0 / M) * np.cos(np.outer(k, np.pi * (np.arange(M) + 0.5) / M)) @ F
+    C[0] *= 0.5
+    probe = np.random.default_rng(1).uniform(lo, hi, 12)
+    for x in probe:
+        tt = (x - 0.5 * (lo + hi)) / (0.5 * (hi - lo))
+        approx = np.polynomial.chebyshev.chebval(tt, C)
+        exact = np.array(LD.jump_constants(dict(prob, s=float(x))))
+        scale = np.abs(F).max(axis=0)
+        assert np.all(np.abs(approx - exact) <= 1e-12 * scale), (x, approx, exact)
