@@ -17,7 +17,7 @@ What it computes (the plain definition the H-matrix method approximates):
   + dt/2 (f^n + f^{n+1})`` (Eq. scheme) with a dense LU with partial pivoting
   (LAPACK through scipy, a library primitive).
 
-Readings of the paper that this file relies on (each also listed in the design doc):
+Readings of the paper that this file relies on:
 
 * G is the generator a d^2 + b d_2x + c + delta_L, i.e. minus the paper's A.
 * Off-diagonal jump entries are w * nu(x_k - x_i) with trapezoid weight w

@@ -19,7 +19,7 @@ Sec. "Singular and/or Slow Decaying Levy Measure"), restricted to the points
 of Omega (u vanishes on the removed quadrant, which the jump sums then skip),
 with the window L_W = 2 covering every pair of points.
 
-Readings (also listed in the design doc):
+Readings:
 * The paper writes -(-Delta)^{s(x)} u = f; with G = -(-Delta)^s that is G u = f.
 * Omega excludes the closed quadrant [0,1]^2: grid points with x >= 0 and
   y >= 0 are not unknowns.
