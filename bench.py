@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--cn-steps", type=int, default=None, help="override the workload's CN steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refine", type=int, default=0, help="refinement sweeps per CN step")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "levy_batch", "serve", "lshape"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "frac_lap_2d_256x256_s0.75",
+                                                             "frac_lap_2d_256x256_s0.3", "levy_batch", "serve",
+                                                             "lshape"])
     ap.add_argument("--lshape-n", type=int, default=255, help="grid side of the L-shaped Poisson workload")
     ap.add_argument("--serve-count", type=int, default=200)
     ap.add_argument("--serve-sides", default="64,128", help="2D grid sides of the served stream")
@@ -133,12 +135,30 @@ def aggregate(ms_local: float, units_local: float, world: int, device: str = "cp
     return ms, world * units_local / (ms * 1e-3)
 
 
-def workload(refine=0):
+def workload(refine=0, name=WORKLOAD):
     from paper_1812_08324_gb300 import workloads as W
-    prob, opts, dt, steps, kind = W.WORKLOADS[WORKLOAD]
-    # the factors' low-rank blocks are capped at rank 16 (ACA ranks here are <= 9)
+    prob, opts, dt, steps, kind = W.WORKLOADS[name]
+    # the factors' low-rank blocks are capped at rank 16 or at the ACA ranks
+    # if larger (1D: ACA ranks <= 9; 2D at ACA 1e-8: <= 25)
     opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=refine)
     return prob, opts, dt, steps, kind
+
+
+def cpu_sample_2d(name, budget_n=64):
+    """The dense oracle on a bounded sample of a 2D workload: the same
+    fractional Laplacian at n = 64 per axis (N = 4096), dense assembly, dense
+    LU and the workload's CN steps; unknown-steps/s over the sample."""
+    from oracle import levy_dense as O
+    from paper_1812_08324_gb300 import workloads as W
+    prob, _, dt, steps, kind = W.WORKLOADS[name]
+    small = dict(prob, n=[budget_n, budget_n])  # the window L_W = 1 is still (n + 1) h
+    t0 = time.perf_counter()
+    G = O.generator_dense(small)
+    O.cn_solve(G, W.initial_data(small, kind), dt, steps)
+    t = time.perf_counter() - t0
+    n = budget_n * budget_n
+    return {"value": n * steps / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"dense oracle on the same 2D problem at {budget_n}x{budget_n}: assembly + LU + {steps} CN steps, {t:.2f} s"}
 
 
 def cpu_sample(steps_override=None, budget_s=20.0):
@@ -546,10 +566,11 @@ def main():
     hmat.load()
     from paper_1812_08324_gb300 import workloads as W
 
-    prob, opts, dt, cn_steps, kind = workload(args.refine)
+    name = args.workload
+    prob, opts, dt, cn_steps, kind = workload(args.refine, name)
     if args.cn_steps:
         cn_steps = args.cn_steps
-    N = prob["n"][0]
+    N = prob["n"][0] * (prob["n"][1] if prob["dim"] == 2 else 1)
     u0_host = torch.tensor(W.initial_data(prob, kind), dtype=torch.float64).pin_memory()
     u0 = u0_host.to("cuda")
     u = torch.empty_like(u0)
@@ -659,7 +680,8 @@ def main():
     # to this launch by its factor bytes (traffic grows in proportion to N in 1D)
     roofline = {"kernel": "exec_kernel (H-triangular solve schedule)", "bound": "hbm",
                 "achieved": sv_gbs, "peak": hbm, "unit": "GB/s", "frac": sv_gbs / hbm,
-                "traffic": st["lu_bytes"] * 786.7 / 393.6, "traffic_source": "ncu at N=32768, scaled by lu_bytes",
+                "traffic": st["lu_bytes"] * 786.7 / 393.6 if prob["dim"] == 1 else None,
+                "traffic_source": "ncu at N=32768, scaled by lu_bytes" if prob["dim"] == 1 else None,
                 "peak_source": f"hbm_gbs {peak_src}", "algorithmic_bytes": st["lu_bytes"], "ms": sv_ms}
     mv_roof = {"kernel": "H-matvec (vt_kernel + vt_reduce + rows_kernel)", "bound": "hbm", "achieved": mv_gbs,
                "peak": hbm, "unit": "GB/s", "frac": mv_gbs / hbm, "traffic": None,
@@ -668,11 +690,12 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "cn_steps": cn_steps, "dt": dt, "leaf": opts["leaf"],
+            "config": {"workload": name, "N": N, "cn_steps": cn_steps, "dt": dt, "leaf": opts["leaf"],
                        "aca_tol": opts["aca_tol"], "max_rank": opts["max_rank"],
                        "lu_max_rank": opts["lu_max_rank"], "refine_sweeps": opts["refine_max"],
                        "parallelism": f"replicas x{world}",
-                       "l2": "working set (H + factors, ~1.4 GB) exceeds L2; no flush needed"},
+                       "l2": f"working set (H + factors, {(st['h_bytes'] + st['lu_bytes']) / 1e9:.1f} GB) "
+                             "exceeds L2; no flush needed"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "matvec_roofline": mv_roof,
             "accuracy": {"rel_l2_vs_converged_fp64_solves": rel_err,
@@ -681,7 +704,7 @@ def main():
             "stats": {k: st[k] for k in ("h_bytes", "lu_bytes", "max_rank_seen", "lu_max_rank_seen",
                                          "dense_blocks", "lowrank_blocks", "last_refine_resid")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_sample()
+        line["cpu_baseline"] = cpu_sample() if prob["dim"] == 1 else cpu_sample_2d(name)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
