@@ -924,7 +924,7 @@ __device__ void dev_rows(const RowsOp& op, double* smem, int pre_cap, unsigned l
       for (int s = 0; s < nsrc; ++s) {
         const RowSrc& S = L.srcs[s];
         if (S.nparts) continue;
-        double a0 = 0.0, a1 = 0.0;  // two chains: FP64 latency, not issue, bounds this loop
+        double a = 0.0;
         const int off = S.pre_off, xo = S.dyn_off;
         for (int c0 = lane; c0 < S.ncols; c0 += 256) {
           double xv[8], mv[8];
@@ -936,24 +936,14 @@ __device__ void dev_rows(const RowsOp& op, double* smem, int pre_cap, unsigned l
             mv[u] = in ? (off >= 0 ? L.pre[off + r * S.ncols + c] : S.M[r * S.rs + c * S.cs]) : 0.0;
           }
 #pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            a0 += mv[u] * xv[u];
-            a1 += mv[u + 1] * xv[u + 1];
-          }
+          for (int u = 0; u < 8; ++u) a += mv[u] * xv[u];
         }
-        acc += S.sign * (a0 + a1);
+        acc += S.sign * a;
       }
     }
     acc = warp_sum(acc);
     if (lane == 0) L.acc_d[r] = acc;
   }
-  // Low-rank sources (x = sum of partial products): warp w takes every 8th
-  // source; its lanes sum the parts into w[l] (lane per column), then lane
-  // (row rr, slice jj) adds M[rr][l] w[l] over the columns l = jj (mod lpr),
-  // with lpr lanes per row (4 for the 8-row critical tasks): a dependent
-  // FP64 chain of ncols / lpr instead of ncols per source.
-  const int lpr = nr <= 8 ? 4 : (nr <= 16 ? 2 : 1);
-  const int rr = lane / lpr, jj = lane % lpr;
   double la = 0.0;
   int k = 0;
   for (int s = 0; s < nsrc; ++s) {
@@ -973,30 +963,29 @@ __device__ void dev_rows(const RowsOp& op, double* smem, int pre_cap, unsigned l
       w[l] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     }
     __syncwarp();
-    if (rr < nr) {
+    if (lane < nr) {
       const int off = S.pre_off;
       double a = 0.0;
       if (off >= 0) {
-        const double* Mr = L.pre + off + rr * (S.ncols + 1);
-        for (int l = jj; l < S.ncols; l += lpr) a += Mr[l] * w[l];
+        const double* Mr = L.pre + off + lane * (S.ncols + 1);
+        for (int l = 0; l < S.ncols; ++l) a += Mr[l] * w[l];
       } else {
-        const double* Mr = S.M + rr * S.rs;
-        for (int l = jj; l < S.ncols; l += lpr) a += Mr[l * S.cs] * w[l];
+        const double* Mr = S.M + lane * S.rs;
+#pragma unroll 8
+        for (int l = 0; l < S.ncols; ++l) a += Mr[l * S.cs] * w[l];
       }
       la += S.sign * a;
     }
     __syncwarp();
   }
-  for (int o = lpr >> 1; o > 0; o >>= 1) la += __shfl_down_sync(0xffffffffu, la, o);  // the row's slices
-  if (jj == 0) L.acc_l[warp * 32 + rr] = la;
+  L.acc_l[warp * 32 + lane] = la;
   __syncthreads();
   if (ts && threadIdx.x == 0) ts[1] = global_ns();
   if (threadIdx.x < nr) {
     const int r = threadIdx.x;
-    const double* al = L.acc_l + r;  // the eight warps' low-rank sums of row r
-    double v = ((al[0] + al[32]) + (al[64] + al[96])) + ((al[128] + al[160]) + (al[192] + al[224]));
+    double v = op.base ? L.dyn[op.dyn_base + r] : 0.0;
     v += L.acc_d[r];
-    if (op.base) v += L.dyn[op.dyn_base + r];
+    for (int w = 0; w < 8; ++w) v += L.acc_l[w * 32 + r];
     op.out[op.r0 + r] = v;
   }
   __syncthreads();
@@ -1032,14 +1021,9 @@ __device__ void dev_vpart(const VPartOp& op, double* smem, int vcap) {
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = warp; l < op.kf; l += 8) {
-    double a0 = 0.0, a1 = 0.0;  // two dependent chains instead of one
-    int r = lane;
-    for (; r + 32 < op.len; r += 64) {
-      a0 += (pre ? smem[l * op.len + r] : op.V[l * op.ldv + r]) * ys[r];
-      a1 += (pre ? smem[l * op.len + r + 32] : op.V[l * op.ldv + r + 32]) * ys[r + 32];
-    }
-    if (r < op.len) a0 += (pre ? smem[l * op.len + r] : op.V[l * op.ldv + r]) * ys[r];
-    const double a = warp_sum(a0 + a1);
+    double a = 0.0;
+    for (int r = lane; r < op.len; r += 32) a += (pre ? smem[l * op.len + r] : op.V[l * op.ldv + r]) * ys[r];
+    a = warp_sum(a);
     if (lane == 0) op.part[l] = a;
   }
 }
