@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <queue>
+#include <unordered_map>
 #include <string>
 
 #include "hlu_plan.h"
@@ -1167,13 +1168,14 @@ struct ResTracker {
     int wop = -1;
     std::vector<int> rops;
   };
-  std::map<int64_t, Res> res;
+  std::unordered_map<int64_t, Res> res;  // looked up by key only (no ordered walk)
   OpGraph& graph;
   std::vector<int> op_wave;
+  std::vector<int> deps;  // scratch
   int bad = 0;
-  explicit ResTracker(OpGraph& g) : graph(g) {}
+  explicit ResTracker(OpGraph& g) : graph(g) { res.reserve(1 << 16); }
   int add(int wave, const std::vector<int64_t>& reads, const std::vector<int64_t>& writes) {
-    std::vector<int> deps;
+    deps.clear();
     for (int64_t r : reads) {
       auto it = res.find(r);
       if (it != res.end() && it->second.wop >= 0) deps.push_back(it->second.wop);
