@@ -13,7 +13,6 @@ namespace hm {
 
 namespace {
 
-constexpr int GT = 32;   // GEMM output tile (square shape)
 constexpr int GK = 16;   // GEMM k chunk
 
 // Double-float split of an FP64 operand, integer operations only (no FP64
@@ -513,7 +512,6 @@ __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K
   }
   // T_B (pivoted rows) = R11_B^{-1} Z, Z[j][c] = R_C[c][posC(j)] for j < rB
   __syncthreads();
-  double* Z = C + 0;  // reuse? C holds R_C and reflectors needed for Z -> build Z in GA
   for (int e = t; e < K * kf; e += blockDim.x) {
     int j = e / kf, c = e % kf;
     double v = 0.0;
@@ -527,7 +525,6 @@ __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K
     }
     GA[e] = v;
   }
-  (void)Z;
   __syncthreads();
   for (int c = t; c < r; c += blockDim.x) {
     for (int i = rB - 1; i >= 0; --i) {
