@@ -70,6 +70,24 @@ struct Tracker {
     std::vector<int> wop;                 // op id of the last write (-1: none)
     std::vector<std::vector<int>> rops;   // op ids of the reads since the last write
     int maxw = -1;                        // latest wave of any access
+    // Segments [u0, u1] share one state (set by a write of exactly that
+    // range and kept while accesses cover exactly that range), held here
+    // instead of in the per-segment arrays: most operations read and write
+    // whole buffers, and this makes their tracking O(1).  A write leaves
+    // ulr = -1: a later op's wave already exceeds the writer's, which
+    // exceeds every earlier read.
+    bool uni = false;
+    int u0 = 0, u1 = -1, ulw = -1, ulr = -1, uwop = -1;
+    std::vector<int> urops;
+    void materialize() {
+      for (int s = u0; s <= u1; ++s) {
+        lw[s] = ulw;
+        lr[s] = ulr;
+        wop[s] = uwop;
+        rops[s] = urops;
+      }
+      uni = false;
+    }
   };
   std::vector<Buf> bufs;
   int add_elem(const double* base, int64_t cap) {
@@ -290,6 +308,16 @@ class Emitter {
       Tracker::Buf& B = T.bufs[v.buf];
       int s0, s1;
       seg_range(B, v, s0, s1);
+      if (B.uni && s0 == B.u0 && s1 == B.u1) {
+        w = std::max(w, B.ulw);
+        if (B.uwop >= 0) deps.push_back(B.uwop);
+        if (a.write) {
+          w = std::max(w, B.ulr);
+          deps.insert(deps.end(), B.urops.begin(), B.urops.end());
+        }
+        continue;
+      }
+      if (B.uni) B.materialize();
       for (int s = s0; s <= s1; ++s) {
         // neighbouring segments mostly share their writer and readers: skip repeats
         w = std::max(w, B.lw[s]);
@@ -312,12 +340,29 @@ class Emitter {
       int s0, s1;
       seg_range(B, v, s0, s1);
       B.maxw = std::max(B.maxw, w);
-      for (int s = s0; s <= s1; ++s) {
+      if (B.uni && s0 == B.u0 && s1 == B.u1) {
         if (a.write) {
-          B.lw[s] = w;
-          B.wop[s] = id;
-          B.rops[s].clear();
+          B.ulw = w;
+          B.uwop = id;
+          B.ulr = -1;
+          B.urops.clear();
         } else {
+          B.ulr = std::max(B.ulr, w);
+          B.urops.push_back(id);
+        }
+        continue;
+      }
+      if (B.uni) B.materialize();
+      if (a.write) {  // the written range becomes one shared state
+        B.uni = true;
+        B.u0 = s0;
+        B.u1 = s1;
+        B.ulw = w;
+        B.uwop = id;
+        B.ulr = -1;
+        B.urops.clear();
+      } else {
+        for (int s = s0; s <= s1; ++s) {
           B.lr[s] = std::max(B.lr[s], w);
           B.rops[s].push_back(id);
         }
