@@ -79,7 +79,16 @@ struct Tracker {
     bool uni = false;
     int u0 = 0, u1 = -1, ulw = -1, ulr = -1, uwop = -1;
     std::vector<int> urops;
+    int nseg = 1;  // segments; the per-segment arrays are allocated on first use
+    void ensure() {
+      if (!lw.empty()) return;
+      lw.assign(nseg, -1);
+      lr.assign(nseg, -1);
+      wop.assign(nseg, -1);
+      rops.resize(nseg);
+    }
     void materialize() {
+      ensure();
       for (int s = u0; s <= u1; ++s) {
         lw[s] = ulw;
         lr[s] = ulr;
@@ -95,21 +104,14 @@ struct Tracker {
     b.elem = true;
     b.base = base;
     b.seg = (int)std::max<int64_t>(1, (cap + 63) / 64);
-    b.lw.assign(64, -1);
-    b.lr.assign(64, -1);
-    b.wop.assign(64, -1);
-    b.rops.resize(64);
+    b.nseg = 64;
     bufs.push_back(std::move(b));
     return (int)bufs.size() - 1;
   }
   int add(int rows, int seg) {
     Buf b;
     b.seg = std::max(1, seg);
-    int ns = std::max(1, (rows + b.seg - 1) / b.seg);
-    b.lw.assign(ns, -1);
-    b.lr.assign(ns, -1);
-    b.wop.assign(ns, -1);
-    b.rops.resize(ns);
+    b.nseg = std::max(1, (rows + b.seg - 1) / b.seg);
     bufs.push_back(std::move(b));
     return (int)bufs.size() - 1;
   }
@@ -253,7 +255,7 @@ class Emitter {
   }
 
   static void seg_range(const Tracker::Buf& B, const View& v, int& s0, int& s1) {
-    const int ns = (int)B.lw.size();
+    const int ns = B.nseg;
     if (B.elem) {
       int64_t off = v.p - B.base;
       int64_t span = (int64_t)(std::max(v.rows, 1) - 1) * (v.rs < 0 ? -v.rs : v.rs) +
@@ -318,6 +320,7 @@ class Emitter {
         continue;
       }
       if (B.uni) B.materialize();
+      B.ensure();
       for (int s = s0; s <= s1; ++s) {
         // neighbouring segments mostly share their writer and readers: skip repeats
         w = std::max(w, B.lw[s]);
@@ -353,7 +356,8 @@ class Emitter {
         continue;
       }
       if (B.uni) B.materialize();
-      if (a.write) {  // the written range becomes one shared state
+      B.ensure();
+      if (a.write && s1 - s0 >= 3) {  // a written range of several segments becomes one shared state
         B.uni = true;
         B.u0 = s0;
         B.u1 = s1;
@@ -363,8 +367,14 @@ class Emitter {
         B.urops.clear();
       } else {
         for (int s = s0; s <= s1; ++s) {
-          B.lr[s] = std::max(B.lr[s], w);
-          B.rops[s].push_back(id);
+          if (a.write) {
+            B.lw[s] = w;
+            B.wop[s] = id;
+            B.rops[s].clear();
+          } else {
+            B.lr[s] = std::max(B.lr[s], w);
+            B.rops[s].push_back(id);
+          }
         }
       }
     }
