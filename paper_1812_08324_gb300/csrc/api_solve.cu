@@ -506,6 +506,83 @@ int merge_chunks(std::vector<HluChunk>& ch, std::vector<Wave>& waves, OpGraph& g
   return HM_OK;
 }
 
+// Plans the H-LU again with a fake arena, handing it out in slices of
+// `chunk` ops, merges consecutive slices in groups of 1, 2, 3, ... and checks
+// each group against the one-piece plan `ref`: the same ops in the same wave
+// order, with exactly the producers of `ref` that lie inside the group.
+bool check_streamed_plan(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld, int kf,
+                         double theta, double lu_tol, int chunk, const HluBuild& ref) {
+  Arena A;
+  A.fake = true;
+  std::vector<HluChunk> chunks;
+  HluBuild hb;
+  hb.chunk_ops = chunk;
+  hb.sink = [&](HluChunk&& c) { chunks.push_back(std::move(c)); };
+  // fake H storage (addresses only) sized from the block layout
+  int64_t dp = 0;
+  for (const DenseDesc& D : dd) dp = std::max<int64_t>(dp, D.off + (int64_t)D.m * D.ld);
+  double* fD = A.alloc(std::max<int64_t>(dp, 1));
+  int64_t uo = 0, vo = 0;
+  for (const LRDesc& L : ld) {
+    uo = std::max<int64_t>(uo, L.uoff + (int64_t)L.m * L.kcap);
+    vo = std::max<int64_t>(vo, L.voff + (int64_t)L.n * L.kcap);
+  }
+  double* fU = A.alloc(std::max<int64_t>(uo, 1));
+  double* fV = A.alloc(std::max<int64_t>(vo, 1));
+  int* frank = (int*)A.alloc((int64_t)ld.size() / 2 + 1);
+  if (plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, lu_tol, frank, A, hb) != HM_OK) {
+    set_error("streamed planning failed");
+    return false;
+  }
+  const int nops = ref.graph.size();
+  // global wave of every op in the one-piece plan
+  std::vector<int> wave_of(nops, -1);
+  for (size_t w = 0; w < ref.waves.size(); ++w) {
+    const Wave& W = ref.waves[w];
+    for (const std::vector<int>* ids : {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id})
+      for (int id : *ids) wave_of[id] = (int)w;
+  }
+  size_t ci = 0;
+  int next = 0, group = 1;
+  std::vector<int> d;
+  while (ci < chunks.size()) {
+    std::vector<HluChunk> grp;
+    for (int g = 0; g < group && ci < chunks.size(); ++g) grp.push_back(std::move(chunks[ci++]));
+    ++group;
+    const int base = grp.front().first;
+    if (base != next) { set_error("streamed slices are not consecutive"); return false; }
+    std::vector<Wave> waves;
+    OpGraph graph;
+    if (merge_chunks(grp, waves, graph) != HM_OK) { set_error("slices failed to merge"); return false; }
+    next = base + graph.size();
+    if (next > nops) { set_error("streamed plan has more ops than the one-piece plan"); return false; }
+    for (int i = 0; i < graph.size(); ++i) {
+      d.clear();
+      for (const int* p = ref.graph.begin(base + i); p != ref.graph.end(base + i); ++p)
+        if (*p >= base) d.push_back(*p - base);
+      if (!std::equal(d.begin(), d.end(), graph.begin(i), graph.end(i)) || (int)d.size() != graph.end(i) - graph.begin(i)) {
+        set_error("producers of op " + std::to_string(base + i) + " differ in the streamed plan");
+        return false;
+      }
+    }
+    int last = -1;
+    for (const Wave& W : waves) {
+      int wmin = 1 << 30, wmax = -1;
+      for (const std::vector<int>* ids : {&W.gemm_id, &W.lu_id, &W.trunc_id, &W.copy_id, &W.reduce_id})
+        for (int id : *ids) {
+          const int gw = wave_of[base + id];
+          wmin = std::min(wmin, gw);
+          wmax = std::max(wmax, gw);
+        }
+      if (wmax < 0) continue;
+      if (wmin != wmax || wmin <= last) { set_error("wave order differs in the streamed plan"); return false; }
+      last = wmin;
+    }
+  }
+  if (next != nops) { set_error("streamed plan misses ops"); return false; }
+  return true;
+}
+
 // H-LU planning streamed into execution: the planners (one host thread per
 // problem, up to the core count) hand finished slices of their operation
 // lists over; the main thread uploads whatever slices are ready (copies on a
@@ -1079,6 +1156,14 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   HluBuild hb;
   int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb);
   if (s != HM_OK) { set_error("planning failed: " + hb.err); return s; }
+  if (const char* cs = std::getenv("HM_CHECK_STREAM")) {
+    // self-check of the streamed planning (slices of HM_CHECK_STREAM ops): the
+    // same planning handed out in slices, merged the way the executor
+    // launches consume them (groups of 1, 2, 3, ... consecutive slices), must
+    // give every op the producers it has in the one-piece plan that lie in its
+    // own group, and the same order of waves
+    if (!check_streamed_plan(P, dd, ld, kf, theta, opts->lu_tol, std::max(1, std::atoi(cs)), hb)) return HM_ERR_ARG;
+  }
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
   OpGraph sg;

@@ -180,3 +180,22 @@ def test_splitmix64_published_outputs_and_batch_stream():
     for p, o in batch[:32]:
         assert 0.25 <= p["s"] <= 0.95 and -1 <= p["b"][0] <= 1 and 0 <= p["a"] <= 0.125
     assert W.levy_batch(4) == W.levy_batch(4)
+
+
+@pytest.mark.parametrize("case", ["levy1d", "frac2d", "lshape"])
+def test_streamed_planning_matches_one_piece(case, monkeypatch):
+    """The H-LU plan handed out in slices (as the factorisation streams it to
+    the executor) and merged in groups of consecutive slices gives every op
+    exactly the producers of the one-piece plan that lie in its group, in the
+    same wave order (host self-check of the dry run; any mismatch is an error)."""
+    if case == "levy1d":
+        prob, opts, dt, steps, kind = W.WORKLOADS["levy_1d_n65536"]
+        opts, theta = dict(opts, lu_max_rank=16, lu_tol=1e-10), -0.5 * dt
+    elif case == "frac2d":
+        prob = W.frac_lap_2d(64)
+        opts, theta = W.default_opts(leaf=64, aca_tol=1e-8, max_rank=25, lu_tol=1e-8, lu_max_rank=25), -1e-3
+    else:
+        prob, opts, theta = W.lshape_poisson(47), W.default_opts(leaf=64, max_rank=32, lu_max_rank=32), 1.0
+    monkeypatch.setenv("HM_CHECK_STREAM", "777")
+    info = hmat.plan_factor(prob, opts, theta)
+    assert info["fact_ops"] > 777 * 8
