@@ -583,6 +583,41 @@ bool check_streamed_plan(const Plan& P, const std::vector<DenseDesc>& dd, const 
   return true;
 }
 
+// Streamed planning that runs out of (fake) memory at `limit` bytes: every op
+// handed out before the failure must have all its operands inside the
+// allocations that succeeded (no op with a missing operand reaches a launch).
+bool check_streamed_failure(const Plan& P, const std::vector<DenseDesc>& dd, const std::vector<LRDesc>& ld,
+                            int kf, double theta, double lu_tol, int chunk, int64_t limit) {
+  Arena A;
+  A.fake = true;
+  A.fake_limit = limit;
+  std::vector<HluChunk> chunks;
+  HluBuild hb;
+  hb.chunk_ops = chunk;
+  hb.sink = [&](HluChunk&& c) { chunks.push_back(std::move(c)); };
+  int64_t dp = 0, uo = 0, vo = 0;
+  for (const DenseDesc& D : dd) dp = std::max<int64_t>(dp, D.off + (int64_t)D.m * D.ld);
+  for (const LRDesc& L : ld) {
+    uo = std::max<int64_t>(uo, L.uoff + (int64_t)L.m * L.kcap);
+    vo = std::max<int64_t>(vo, L.voff + (int64_t)L.n * L.kcap);
+  }
+  double* fD = A.alloc(std::max<int64_t>(dp, 1));
+  double* fU = A.alloc(std::max<int64_t>(uo, 1));
+  double* fV = A.alloc(std::max<int64_t>(vo, 1));
+  int* frank = (int*)A.alloc((int64_t)ld.size() / 2 + 1);
+  if (plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, lu_tol, frank, A, hb) != HM_ERR_OOM) {
+    set_error("streamed planning did not report the injected allocation failure");
+    return false;
+  }
+  std::string first;
+  for (const HluChunk& c : chunks)
+    if (check_spans(c.waves, A.ranges, first) != 0) {
+      set_error("a streamed slice handed out after an allocation failure has an operand outside memory: " + first);
+      return false;
+    }
+  return true;
+}
+
 // H-LU planning streamed into execution: the planners (one host thread per
 // problem, up to the core count) hand finished slices of their operation
 // lists over; the main thread uploads whatever slices are ready (copies on a
@@ -1147,6 +1182,9 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   if (kf > TRUNC_MAXK / 2) { set_error("factor rank cap too large"); return HM_ERR_RANK_CAP; }
   Arena A;
   A.fake = true;
+  // host-side fault injection: HM_ARENA_LIMIT_BYTES makes the planner's
+  // allocations fail past that many bytes, as a full device would
+  if (const char* lim = std::getenv("HM_ARENA_LIMIT_BYTES")) A.fake_limit = std::atoll(lim);
   // fake storage of the H-matrix and of the factor ranks
   double* fD = A.alloc(std::max<int64_t>(dp, 1));
   double* fU = A.alloc(std::max<int64_t>(up, 1));
@@ -1155,7 +1193,14 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   double* fy = A.alloc(5 * (int64_t)P.N);
   HluBuild hb;
   int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb);
-  if (s != HM_OK) { set_error("planning failed: " + hb.err); return s; }
+  if (s != HM_OK) {
+    const char* cs = std::getenv("HM_CHECK_STREAM");
+    if (cs && s == HM_ERR_OOM && A.fake_limit >= 0 &&
+        !check_streamed_failure(P, dd, ld, kf, theta, opts->lu_tol, std::max(1, std::atoi(cs)), A.fake_limit))
+      return HM_ERR_ARG;
+    set_error("planning failed: " + hb.err);
+    return s;
+  }
   if (const char* cs = std::getenv("HM_CHECK_STREAM")) {
     // self-check of the streamed planning (slices of HM_CHECK_STREAM ops): the
     // same planning handed out in slices, merged the way the executor

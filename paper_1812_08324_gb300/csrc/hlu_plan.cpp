@@ -29,6 +29,10 @@ double* Arena::alloc(int64_t n) {
     int64_t chunk = std::max<int64_t>(n, int64_t(1) << 25);
     void* p = nullptr;
     if (fake) {
+      if (fake_limit >= 0 && (int64_t)((fake_next - (uintptr_t(1) << 40)) + chunk * sizeof(double)) > fake_limit) {
+        status = HM_ERR_OOM;  // injected allocation failure (dry runs only)
+        return nullptr;
+      }
       p = (void*)fake_next;
       fake_next += (uintptr_t)(chunk * sizeof(double)) + 4096;
     } else {

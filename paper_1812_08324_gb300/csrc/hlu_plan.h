@@ -53,6 +53,7 @@ struct Arena {
   int status = 0;
   bool fake = false;
   uintptr_t fake_next = uintptr_t(1) << 40;
+  int64_t fake_limit = -1;    // dry runs: bytes after which alloc fails (-1: no limit)
   double* alloc(int64_t n);   // doubles, 32-byte aligned
   void release();
 };

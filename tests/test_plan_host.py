@@ -199,3 +199,23 @@ def test_streamed_planning_matches_one_piece(case, monkeypatch):
     monkeypatch.setenv("HM_CHECK_STREAM", "777")
     info = hmat.plan_factor(prob, opts, theta)
     assert info["fact_ops"] > 777 * 8
+
+
+def test_injected_allocation_failure_is_reported_and_never_streamed(monkeypatch):
+    """Host-side fault injection: the dry run's allocations fail past
+    HM_ARENA_LIMIT_BYTES as a full device would.  Planning reports
+    HM_ERR_OOM, and the streamed planning hands out no slice with an operand
+    outside the allocations that succeeded (checked under HM_CHECK_STREAM;
+    a violation would be reported as HM_ERR_ARG instead)."""
+    prob, opts, dt, steps, kind = W.WORKLOADS["levy_1d_n65536"]
+    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10)
+    monkeypatch.setenv("HM_ARENA_LIMIT_BYTES", str(2 * 10 ** 9))
+    with pytest.raises(hmat.HMError) as e:
+        hmat.plan_factor(prob, opts, -0.5 * dt)
+    assert e.value.status == -2
+    monkeypatch.setenv("HM_CHECK_STREAM", "777")
+    with pytest.raises(hmat.HMError) as e:
+        hmat.plan_factor(prob, opts, -0.5 * dt)
+    assert e.value.status == -2, str(e.value)
+    monkeypatch.setenv("HM_ARENA_LIMIT_BYTES", str(10 ** 12))   # room enough: plans
+    assert hmat.plan_factor(prob, opts, -0.5 * dt)["fact_ops"] > 0
