@@ -30,7 +30,7 @@ from . import hmat
 # Device bytes per unknown assumed at admission (H-matrix + factor arena with
 # its temporaries); replaced by the measured footprint once a request is
 # factored.
-EST_BYTES_PER_UNKNOWN = {1: 120e3, 2: 900e3}
+EST_BYTES_PER_UNKNOWN = {1: 140e3, 2: 900e3}
 
 
 @dataclass
