@@ -316,3 +316,21 @@ def test_cn_literal_matches_identity_form():
     u1 = O.cn_solve(G, u0, 1e-3, 20, forcing=f, literal=True)
     u2 = O.cn_solve(G, u0, 1e-3, 20, forcing=f, literal=False)
     assert np.max(np.abs(u1 - u2)) < 1e-12 * np.max(np.abs(u1))
+
+
+def test_cn_run_inplace_matches_literal_form():
+    """The single-array form used for the largest grids (M formed and factored
+    in place, M^T factored through the Fortran-ordered view) gives the literal
+    Crank-Nicolson iterates: a transposed factor or a wrong solve direction
+    would show up at once, because the drift makes M non-symmetric."""
+    p = prob1d(383, -1.0, 1.0, s=0.75, a=0.02, b=[0.3, 0.0], trunc=2.0, LW=2.0)
+    x = O.grid_points(p)[:, 0]
+    u0 = np.exp(-50 * x * x)
+    G = O.generator_dense(p)
+    assert np.abs(G - G.T).max() > 1.0  # drift: the test would not see a transpose otherwise
+    ref10 = O.cn_solve(G, u0, 1e-3, 10, literal=True)
+    ref25 = O.cn_solve(G, ref10, 1e-3, 15, literal=True)
+    out = O.cn_run_inplace(p, u0, 1e-3, 25, record=[0, 10])
+    assert np.array_equal(out[0], u0)
+    assert np.linalg.norm(out[10] - ref10) <= 1e-12 * np.linalg.norm(ref10)
+    assert np.linalg.norm(out[25] - ref25) <= 1e-12 * np.linalg.norm(ref25)
