@@ -50,7 +50,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cn-steps", type=int, default=None, help="override the workload's CN steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--refine", type=int, default=0, help="refinement sweeps per CN step")
+    ap.add_argument("--refine", type=int, default=None,
+                    help="refinement sweeps per CN step (default: 0 for FP64, 1 for the mixed precisions)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_fp32", "mixed_bf16"],
+                    help="storage of what the triangular solves read (the mixed modes refine in FP64)")
+    ap.add_argument("--solve", default="auto", choices=["auto", "hinv", "subst"],
+                    help="triangular solves: hierarchical inverses (1D default) or substitution")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "frac_lap_2d_256x256_s0.75",
                                                              "frac_lap_2d_256x256_s0.3", "levy_batch", "serve",
                                                              "lshape"])
@@ -135,12 +140,14 @@ def aggregate(ms_local: float, units_local: float, world: int, device: str = "cp
     return ms, world * units_local / (ms * 1e-3)
 
 
-def workload(refine=0, name=WORKLOAD):
+def workload(refine=0, name=WORKLOAD, precision="fp64", solve="auto"):
     from paper_1812_08324_gb300 import workloads as W
     prob, opts, dt, steps, kind = W.WORKLOADS[name]
     # the factors' low-rank blocks are capped at rank 16 or at the ACA ranks
     # if larger (1D: ACA ranks <= 9; 2D at ACA 1e-8: <= 25)
-    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=refine)
+    if refine is None:
+        refine = 0 if precision == "fp64" else 1
+    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=refine, precision=precision, solve=solve)
     return prob, opts, dt, steps, kind
 
 
@@ -227,7 +234,8 @@ def run_batch(args):
     batch = W.levy_batch(args.batch_count)
     dt = W.LEVY_BATCH_DT
     cn_steps = args.cn_steps or W.LEVY_BATCH_STEPS
-    batch = [(p, dict(o, refine_max=args.refine)) for p, o in batch]
+    refine = args.refine if args.refine is not None else (0 if args.precision == "fp64" else 1)
+    batch = [(p, dict(o, refine_max=refine, precision=args.precision, solve=args.solve)) for p, o in batch]
     leafs = autotune.tune_batch(batch, dt, cn_steps, probe_steps=3)
     batch = [(p, dict(o, leaf=l)) for (p, o), l in zip(batch, leafs)]
     ns = [p["n"][0] for p, _ in batch]
@@ -342,7 +350,8 @@ def run_batch(args):
             "config": {"workload": f"levy_batch x{len(batch)} (splitmix64 seed 0)", "sum_N": int(sum(ns)),
                        "cn_steps": cn_steps, "dt": dt, "leafs": {str(l): leafs.count(l) for l in sorted(set(leafs))},
                        "groups": len(groups), "group_unknowns_max": args.group_unknowns,
-                       "refine_sweeps": args.refine, "parallelism": f"replicas x{world}", "cuda_graph": graphed,
+                       "refine_sweeps": refine, "precision": args.precision, "solve": args.solve,
+                       "parallelism": f"replicas x{world}", "cuda_graph": graphed,
                        "l2": "working set (H + factors of all problems) exceeds L2; no flush needed"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "accuracy": {"rel_l2_vs_converged_fp64_solves_sampled": errs,
@@ -567,7 +576,7 @@ def main():
     from paper_1812_08324_gb300 import workloads as W
 
     name = args.workload
-    prob, opts, dt, cn_steps, kind = workload(args.refine, name)
+    prob, opts, dt, cn_steps, kind = workload(args.refine, name, args.precision, args.solve)
     if args.cn_steps:
         cn_steps = args.cn_steps
     N = prob["n"][0] * (prob["n"][1] if prob["dim"] == 2 else 1)

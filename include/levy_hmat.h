@@ -52,9 +52,20 @@ extern "C" {
 #define HM_NU_GAUSS 0   /* nu(y) = lam * exp(-eps^2 |y|^2)   (Merton jumps, Sec. H-matrix construction) */
 #define HM_NU_STABLE 1  /* nu(y) = c_{d,s} / |y|^{d+2s}      (fractional Laplacian, Introduction) */
 
-/* ---- storage precision of the factors (HM_FP64 keeps everything FP64) ---- */
+/* ---- storage precision of what the triangular solves read (HM_FP64 keeps
+ * everything FP64).  The mixed modes store the hierarchical inverses of the
+ * factors in FP32 or BF16 and multiply with FP32 accumulation; the H-matrix
+ * of G, the H-LU factorisation itself (its diagonal-leaf LUs included), the
+ * right-hand side and the refinement residual stay FP64, and the accuracy is
+ * won back by the FP64 refinement sweeps of every CN solve (refine_max). ---- */
 #define HM_FP64 0
 #define HM_MIXED_FP32 1
+#define HM_MIXED_BF16 2
+
+/* ---- how the triangular solves run ---- */
+#define HM_SOLVE_AUTO 0   /* HM_SOLVE_HINV for 1D problems on a box, HM_SOLVE_SUBST otherwise */
+#define HM_SOLVE_SUBST 1  /* block forward/backward substitution over solve blocks (dataflow executor) */
+#define HM_SOLVE_HINV 2   /* products with hierarchical inverses of the factors (1D problems only) */
 
 /*
  * Problem (Sec. "Model Problem"; Sec. "Singular and/or Slow Decaying Levy Measure").
@@ -102,9 +113,14 @@ typedef struct hm_opts {
   int max_rank;      /* rank cap of the ACA blocks */
   double lu_tol;     /* relative truncation tolerance of low-rank sums in H-LU */
   int lu_max_rank;   /* rank cap of the low-rank blocks of the factors */
-  int precision;     /* HM_FP64 (HM_MIXED_FP32 is reserved: hm_build returns HM_ERR_ARG) */
+  int precision;     /* HM_FP64, HM_MIXED_FP32 or HM_MIXED_BF16 (the mixed modes need HM_SOLVE_HINV) */
   double refine_tol; /* stop refinement when ||s||_2 <= refine_tol ||rhs||_2 */
   int refine_max;    /* max refinement sweeps per CN step (0 = plain H-LU solve) */
+  int solve;         /* HM_SOLVE_AUTO, HM_SOLVE_SUBST or HM_SOLVE_HINV */
+  int solve_block;   /* HM_SOLVE_SUBST: rows of the largest solve block (0 = 1024, and 2048 for
+                        1D problems of at least 32768 unknowns) */
+  double hinv_tol;   /* HM_SOLVE_HINV: relative truncation of the inverse blocks (0 = 1e-2 lu_tol
+                        for HM_FP64, 1e-7 for HM_MIXED_FP32, 2e-3 for HM_MIXED_BF16) */
 } hm_opts;
 
 typedef struct hm_matrix hm_matrix;    /* opaque: H-matrix of G on the device */
@@ -117,7 +133,8 @@ typedef struct hm_stats_t {
   int64_t dense_entries;      /* entries stored in dense leaves */
   int64_t lowrank_entries;    /* (m + n) * rank summed over low-rank blocks (actual ranks) */
   int64_t h_bytes;            /* bytes of the H-matrix actually read by one H-matvec */
-  int64_t lu_bytes;           /* bytes of the factors read by one pair of triangular solves */
+  int64_t lu_bytes;           /* bytes read by one pair of triangular solves: the factors
+                                 (HM_SOLVE_SUBST) or their hierarchical inverses (HM_SOLVE_HINV) */
   int max_rank_seen;          /* largest ACA rank */
   int rank_capped_blocks;     /* ACA blocks that stopped at max_rank before aca_tol */
   int lu_max_rank_seen;       /* largest rank in the factors */
@@ -129,6 +146,10 @@ typedef struct hm_stats_t {
                                  inverses, scaled couplings; F given) */
   double factor_ms;           /* device time of the factorisation's executor launch (F given;
                                  shared by all problems of one hm_factor_batch) */
+  int solve_mode;             /* HM_SOLVE_SUBST or HM_SOLVE_HINV (F given) */
+  int hinv_max_rank;          /* largest rank of an inverse block (HM_SOLVE_HINV) */
+  int hinv_capped;            /* inverse blocks that reached the rank cap 40 */
+  double hinv_ms;             /* host wall time of forming the inverses */
 } hm_stats_t;
 
 /* ---- errors ---- */
@@ -207,8 +228,10 @@ int hm_matvec(const hm_matrix* H, double alpha, double beta, const double* x, do
  * H must need at most that much scratch (about N/256 * 3 * depth partials of
  * 128 doubles in 1D); larger problems get HM_ERR_ARG and a message with the
  * size needed.  The first call on a device looks up the array's device address
- * with cudaGetSymbolAddress (that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
+ * with cudaGetSymbolAddress (that device current) and caches it for the life
+ * of the process (threads racing on that first call are safe; the cache
+ * assumes the device is not reset while the library is loaded); make that
+ * first call before any stream capture.  All calls share the array and it keeps the last
  * call's contents; every entry a call reads is written earlier in the same
  * call, so nothing needs clearing.  Calls that overlap on the GPU (other
  * streams, other threads) race on the array: serialise them.  The paper has
@@ -237,6 +260,15 @@ int hm_entries(const hm_matrix* H, int64_t count, const int* rows, const int* co
  * (M = I - dt/2 G of Crank-Nicolson is row diagonally dominant).  Low-rank
  * sums are truncated at opts.lu_tol / lu_max_rank.  Crank-Nicolson uses
  * theta = -dt/2.  *out owns its device memory.
+ * With HM_SOLVE_HINV (opts.solve; the default for 1D problems) it then forms
+ * hierarchical inverses of both factors: for every cluster tau with children
+ * a, b the off-diagonal block -X_b L_ba X_a of L^{-1} (and -Y_a U_ab Y_b of
+ * U^{-1}) is compressed to rank <= 40 at opts.hinv_tol by a randomised
+ * two-sided sketch built from products with the factors and the deeper
+ * levels of the inverse only (seeded, deterministic).  The triangular solves
+ * are then two fully parallel products; the compression error is corrected by
+ * the CN step's FP64 refinement sweeps.  The paper solves by substitution
+ * (App. "LU Decomposition"); the inverses are this library's GPU form of it.
  */
 int hm_factor(const hm_matrix* H, double theta, void* stream, hm_factors** out);
 
@@ -284,8 +316,9 @@ int hm_factor_batch(const hm_matrix* const* H, const double* theta, int count, v
 
 /*
  * hm_solve: x = (L U)^{-1} b by the H-triangular solves of App. "LU
- * Decomposition" (forward then backward substitution over the block tree).
- * Natural-order device vectors; x may alias b.
+ * Decomposition": forward then backward substitution over the block tree
+ * (HM_SOLVE_SUBST), or x = U^{-1} (L^{-1} b) with the hierarchical inverses
+ * (HM_SOLVE_HINV).  Natural-order device vectors; x may alias b.
  */
 int hm_solve(const hm_factors* F, const double* b, double* x, void* stream);
 

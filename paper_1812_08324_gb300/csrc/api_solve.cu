@@ -13,6 +13,7 @@
 #include <thread>
 
 #include "api_common.h"
+#include "hinv.h"
 #include "hlu_plan.h"
 #include "hm_device.cuh"
 
@@ -46,6 +47,8 @@ struct hm_factors {
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
   OpGraph sg;
+  int solve_mode = HM_SOLVE_SUBST;
+  HinvData* hinv = nullptr;    // hierarchical inverses of the factors (HM_SOLVE_HINV)
 };
 
 namespace hm {
@@ -162,6 +165,7 @@ void trace_schedule(const char* what, const std::vector<Wave>& waves, const OpGr
 
 // z = (LU)^{-1} b on Morton-order vectors (b may equal z)
 int solve_morton(const hm_factors* F, const double* b, double* z, cudaStream_t st) {
+  if (F->hinv) return hinv_solve(*F->hinv, b, z, st);
   const int N = F->H->plan.N;
   count_launches(2);
   copy_vec_kernel<<<vgrid(N), 256, 0, st>>>(N, b, F->d_y);
@@ -278,6 +282,21 @@ int upload_mv_batch(const std::vector<MvJob>& h, MvBatch& B, std::vector<void*>&
   return HM_OK;
 }
 
+// Batched hierarchical-inverse products: per job its blocks of the two launches.
+int upload_hinv_batch(const std::vector<HinvJob>& h, HinvBatch& B, std::vector<void*>& allocs) {
+  if (h.empty()) return HM_OK;
+  DevJobs<HinvJob> d0, d1;
+  HM_TRY(upload_jobs(h, [](const HinvJob& J) { return J.A.ntch; }, d0, allocs));
+  HM_TRY(upload_jobs(h, [](const HinvJob& J) { return J.A.nrch; }, d1, allocs));
+  B.jobs = d0.jobs;
+  B.off[0] = d0.off;
+  B.off[1] = d1.off;
+  B.total[0] = d0.total;
+  B.total[1] = d1.total;
+  B.count = (int)h.size();
+  return HM_OK;
+}
+
 // ---- factorisation in phases (shared by hm_factor and hm_factor_batch)
 
 struct FactorJob {
@@ -290,6 +309,10 @@ struct FactorJob {
 
 void factor_discard(FactorJob& J) {
   if (!J.F) return;
+  if (J.F->hinv) {
+    J.F->hinv->release();
+    delete J.F->hinv;
+  }
   for (void* p : J.F->allocs) cudaFree(p);
   J.F->arena.release();
   delete J.F;
@@ -311,6 +334,7 @@ int factor_alloc(FactorJob& J, const hm_matrix* H, double theta, cudaStream_t st
   hm_factors* F = J.F;
   F->H = H;
   F->theta = theta;
+  F->solve_mode = solve_mode(H->prob, H->opts);
   F->kf = std::max(kf, 1);
   const int nlr = (int)H->h_ld.size();
   const int N = H->plan.N;
@@ -336,7 +360,7 @@ void factor_plan(FactorJob& J) {
   const hm_matrix* H = J.H;
   hm_factors* F = J.F;
   J.status = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, F->kf, F->theta, H->opts.lu_tol,
-                      F->d_rank, F->arena, J.hb, F->alpha);
+                      F->d_rank, F->arena, J.hb, F->alpha, H->opts.solve_block, F->solve_mode == HM_SOLVE_SUBST);
   if (J.status != HM_OK) { J.err = J.hb.err; return; }
   F->fact_ops = J.hb.ops;
   F->fact_waves = (int)J.hb.waves.size();
@@ -391,7 +415,8 @@ struct hm_batch {
   std::vector<const hm_factors*> F;
   std::vector<double*> state;
   int refine = 0;
-  DevSchedule sched;
+  DevSchedule sched;           // merged substitution schedule of the HM_SOLVE_SUBST problems
+  hm::HinvBatch hL, hU;        // the HM_SOLVE_HINV problems: L^{-1}, then U^{-1} of every one
   hm::MvBatch A{}, B{};
   hm::DevJobs<hm::VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out;
   std::vector<void*> allocs;
@@ -407,17 +432,24 @@ namespace {
 
 // One CN step of every problem of the batch (stream-ordered launches only,
 // so that it can be recorded as a graph).
+// The solves of every problem: z = (LU)^{-1} y from each factor's input
+// vector y to its output z (the substitution schedule, the inverses' products).
+int batch_solve(hm_batch* B, cudaStream_t cs) {
+  HM_TRY(run_schedule(B->sched, B->H[0]->d_err, cs));
+  HM_TRY(launch_hinv_batch(B->hL, cs));
+  return launch_hinv_batch(B->hU, cs);
+}
+
 int batch_one_step(hm_batch* B, cudaStream_t cs) {
-  int* d_err = B->H[0]->d_err;
   HM_TRY(launch_matvec_batch(B->A, cs));
   HM_TRY(launch_vec_batch(B->rhs_in, cs));
-  HM_TRY(run_schedule(B->sched, d_err, cs));
+  HM_TRY(batch_solve(B, cs));
   if (B->refine == 0) return launch_vec_batch(B->z_out, cs);
   HM_TRY(launch_vec_batch(B->z_u1, cs));
   for (int it = 0; it < B->refine; ++it) {
     HM_TRY(launch_matvec_batch(B->B, cs));
     HM_TRY(launch_vec_batch(B->s_in, cs));
-    HM_TRY(run_schedule(B->sched, d_err, cs));
+    HM_TRY(batch_solve(B, cs));
     HM_TRY(launch_vec_batch(B->u1_add, cs));
   }
   return launch_vec_batch(B->u1_out, cs);
@@ -815,14 +847,31 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
     J.F->h_rank.assign(nlr, 0);
     if (nlr) cudaMemcpy(J.F->h_rank.data(), J.F->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost);
   }
-  // the solve schedules (they read the factor ranks), planned in parallel
+  // the solve schedules (they read the factor ranks), planned in parallel;
+  // or the hierarchical inverses of the factors
   phase("ranks");
-  parallel_for(count, [&](int i) { factor_plan_solve(jobs[i]); });
+  parallel_for(count, [&](int i) {
+    if (jobs[i].F->solve_mode == HM_SOLVE_SUBST) factor_plan_solve(jobs[i]);
+  });
   for (FactorJob& J : jobs)
     if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
   phase("plan solves");
   for (FactorJob& J : jobs) {
     hm_factors* F = J.F;
+    if (F->solve_mode != HM_SOLVE_HINV) continue;
+    F->hinv = new HinvData();
+    const int prec = J.H->opts.precision == HM_MIXED_FP32 ? HINV_F32
+                     : (J.H->opts.precision == HM_MIXED_BF16 ? HINV_BF16 : HINV_F64);
+    std::string herr;
+    s = hinv_build(J.H->plan, J.H->h_dd, F->F, F->d_rank, prec, hinv_tolerance(J.H->opts), J.H->d_err, st,
+                   *F->hinv, herr);
+    if (s != HM_OK) { set_error("hierarchical inverses: " + herr); return fail_all(s); }
+    F->lu_bytes = F->hinv->step_bytes;
+  }
+  if (count > 0) phase("inverses");
+  for (FactorJob& J : jobs) {
+    hm_factors* F = J.F;
+    if (F->solve_mode != HM_SOLVE_SUBST) continue;
     s = upload_schedule(F->sw, F->sg, F->solve, F->allocs, &F->srcs);
     if (s != HM_OK) { set_error("solve schedule upload failed"); return fail_all(s); }
     if (tracing && count == 1) {
@@ -871,13 +920,28 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   // SM, smaller staging; staging changes where operands are read from, not
   // the arithmetic)
   int s = HM_OK;
-  if (count == 1) {
+  int nsub = 0;
+  for (int i = 0; i < count; ++i) nsub += Fs[i]->solve_mode == HM_SOLVE_SUBST ? 1 : 0;
+  if (count == 1 && nsub == 1) {
     B->sched = Fs[0]->solve;  // one problem: its own schedule, latency mode (borrowed, not freed here)
-  } else {
+  } else if (nsub > 0) {
     std::vector<SchedPart> parts;
-    for (int i = 0; i < count; ++i) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
+    for (int i = 0; i < count; ++i)
+      if (Fs[i]->solve_mode == HM_SOLVE_SUBST) parts.push_back(SchedPart{&Fs[i]->sw, &Fs[i]->sg, &Fs[i]->srcs});
     s = upload_schedules(parts, B->sched, B->allocs, SOLVE_MODE_THROUGHPUT, true);
     if (s != HM_OK) { set_error("batched solve schedule upload failed"); return fail(s); }
+  }
+  {
+    std::vector<HinvJob> jl, ju;
+    for (int i = 0; i < count; ++i) {
+      const hm_factors* F = Fs[i];
+      if (F->solve_mode != HM_SOLVE_HINV) continue;
+      const int N = Hs[i]->plan.N;
+      jl.push_back(HinvJob{F->hinv->tri[0].A, F->d_y, F->hinv->d_y});
+      ju.push_back(HinvJob{F->hinv->tri[1].A, F->hinv->d_y, F->d_sv + (size_t)N});
+    }
+    if ((s = upload_hinv_batch(jl, B->hL, B->allocs)) != HM_OK) return fail(s);
+    if ((s = upload_hinv_batch(ju, B->hU, B->allocs)) != HM_OK) return fail(s);
   }
   // per problem: Morton-order state x (owned by the batch), rhs, residual,
   // refined iterate, solve output z
@@ -1017,6 +1081,10 @@ void hm_factors_free(hm_factors* F) {
   if (!F) return;
   if (F->batch1) hm_batch_free(F->batch1);
   cudaDeviceSynchronize();
+  if (F->hinv) {
+    F->hinv->release();
+    delete F->hinv;
+  }
   for (void* p : F->allocs) cudaFree(p);
   F->arena.release();
   delete F;
@@ -1192,7 +1260,7 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
   int* frank = (int*)A.alloc((int64_t)ld.size() / 2 + 1);
   double* fy = A.alloc(5 * (int64_t)P.N);
   HluBuild hb;
-  int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb);
+  int s = plan_hlu(P, dd, fD, ld, fU, fV, kf, theta, opts->lu_tol, frank, A, hb, 1.0, opts->solve_block, true);
   if (s != HM_OK) {
     const char* cs = std::getenv("HM_CHECK_STREAM");
     if (cs && s == HM_ERR_OOM && A.fake_limit >= 0 &&
@@ -1273,6 +1341,13 @@ int hm_stats(const hm_matrix* H, const hm_factors* F, hm_stats_t* out) {
     cudaMemcpy(nrm, F->d_norm, sizeof(nrm), cudaMemcpyDeviceToHost);
     out->last_refine_iters = H->opts.refine_max;
     out->last_refine_resid = nrm[1] > 0 ? std::sqrt(nrm[0] / nrm[1]) : 0.0;
+    out->solve_mode = F->solve_mode;
+    if (F->hinv) {
+      out->device_bytes += F->hinv->bytes;
+      out->hinv_max_rank = F->hinv->max_rank;
+      out->hinv_capped = F->hinv->capped;
+      out->hinv_ms = F->hinv->build_ms;
+    }
   }
   return HM_OK;
 }

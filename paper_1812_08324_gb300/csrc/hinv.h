@@ -1,0 +1,116 @@
+// Hierarchical inverses of the H-LU triangular factors (1D problems).
+//
+// The triangular solves L y = b, U z = y of App. "LU Decomposition" are a
+// chain of dependent leaf steps.  For the binary cluster tree of a 1D grid
+// the inverses of the factors are themselves hierarchical with small ranks:
+// for a cluster tau with children a (first) and b,
+//     L_tau^{-1} = [ X_a  0 ; -X_b L_ba X_a   X_b ],
+//     U_tau^{-1} = [ Y_a  -Y_a U_ab Y_b ;  0   Y_b ],
+// and the off-diagonal blocks W_tau = -X_b L_ba X_a (-Y_a U_ab Y_b) have
+// numerical ranks of a few tens at 1e-12.  They are formed bottom-up, level
+// by level, from products with the factors and the already formed lower
+// levels only (randomised two-sided sketch: Y = W Omega, Z = W^T Psi,
+// W ~ Y (Psi^T Y)^+ Z^T with a column-pivoted QR of the small core as the
+// truncated pseudo-inverse; Nakatsukasa, "Fast and stable randomized low-rank
+// matrix approximation", 2020).  Applying them is then a fully parallel,
+// bandwidth-bound product per factor instead of a substitution chain.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+struct FactorLayout;
+
+constexpr int HINV_S = 48;      // range-sketch columns
+constexpr int HINV_SP = 64;     // co-range-sketch columns
+constexpr int HINV_KCAP = 40;   // rank cap of an inverse block (ranks that reach it are flagged)
+constexpr int HINV_MAXS = 64;   // widest multi-vector of the construction
+constexpr int HINV_RCH = 32;    // rows per row chunk
+constexpr int HINV_TCH = 256;   // rows per chunk of the per-step V'x products
+constexpr int HINV_MCH = 128;   // rows per chunk of the construction's reductions
+
+enum HinvPrec { HINV_F64 = 0, HINV_F32 = 1, HINV_BF16 = 2 };
+
+// ---- per-step application of one triangular inverse (device tables)
+struct HinvLeaf {     // square row-major inverse of a diagonal leaf block
+  int r0, m, ld;
+  int anc_begin, anc_end;   // inverse blocks whose target rows contain the leaf
+  int64_t off;              // into the leaf pool (elements)
+};
+struct HinvNode {     // inverse block P Q^T of an internal cluster
+  int tgt0, tgt_n, src0, src_n;
+  int pld, qld;             // column strides of P and Q (multiples of 8 elements)
+  int tch_begin, tch_end;   // its chunks of the per-step V'x products
+  int64_t poff, qoff;       // col-major P (tgt_n x KCAP), Q (src_n x KCAP) in the pools
+};
+struct HinvApply {
+  int lower;                // 1: L^{-1} (leaf rows read j <= i), 0: U^{-1} (j >= i)
+  int prec;                 // HinvPrec of the pools
+  int nleaf, nnode, ntch, nrch;
+  const HinvLeaf* leaves;
+  const HinvNode* nodes;
+  const int* anc;           // node ids listed per leaf
+  const int2* tch;          // (node, first source row offset) per product chunk
+  const int2* rch;          // (leaf, first row offset) per row chunk
+  const void* leaf_pool;
+  const void* p_pool;
+  const void* q_pool;
+  const int* rank;          // per node
+  double* tpart;            // per product chunk: KCAP partial sums
+  double* tvec;             // per node: KCAP coefficients
+  unsigned* tcount;         // per node: finished chunks (reset by the last one)
+};
+// One triangular inverse applied to a Morton-order vector: y = X b.
+struct HinvJob {
+  HinvApply A;
+  const double* b;
+  double* y;
+};
+
+// Launchers (hinv_apply.cu).  Single: two launches; batch: two launches for all jobs.
+int launch_hinv_apply(const HinvApply& A, const double* b, double* y, cudaStream_t st);
+struct HinvBatch {
+  HinvJob* jobs = nullptr;
+  int* off[2] = {nullptr, nullptr};  // per job its first CTA of the two launches; off[k][count] = total
+  int total[2] = {0, 0};
+  int count = 0;
+};
+int launch_hinv_batch(const HinvBatch& B, cudaStream_t st);
+
+// ---- the inverses of one factorisation
+struct HinvTriangle {
+  HinvApply A{};            // in the chosen storage precision
+  HinvApply A64{};          // FP64 copy (construction; the FP64 solve)
+  std::vector<HinvLeaf> h_leaves;
+  std::vector<HinvNode> h_nodes;
+  std::vector<int> h_rank;
+};
+struct HinvData {
+  int prec = HINV_F64;
+  double tol = 0.0;
+  HinvTriangle tri[2];      // 0: L^{-1}, 1: U^{-1}
+  std::vector<void*> allocs;
+  int64_t bytes = 0;        // device bytes held
+  int64_t step_bytes = 0;   // bytes one application of both inverses reads
+  int max_rank = 0, capped = 0;
+  double build_ms = 0.0;
+  double* d_y = nullptr;    // intermediate vector (N)
+  void release();
+};
+
+// Form the inverses of the factors in F (1D plans only).  Ranks of the factor
+// blocks on the device in d_rank_f.  Synchronises the stream at the end.
+int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
+               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err);
+
+// z = U^{-1} L^{-1} b (Morton order; z may alias b).
+int hinv_solve(const HinvData& D, const double* b, double* z, cudaStream_t st);
+
+}  // namespace hm

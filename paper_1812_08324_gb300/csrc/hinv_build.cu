@@ -1,0 +1,953 @@
+// Construction of the hierarchical inverses of the triangular factors
+// (see hinv.h).  Bottom-up over the levels of the 1D cluster tree; at a
+// level every cluster tau with children (a, b) gets its inverse block
+//     L^{-1}: W = -X_b L_ba X_a   (rows b, columns a)
+//     U^{-1}: W = -Y_a U_ab Y_b   (rows a, columns b)
+// from two sketches made of products only:
+//     range      R3 = X (T_off (X Omega))        = -W Omega     (Omega on the source rows)
+//     co-range   C3 = X^T (T_off^T (X^T Psi))    = -W^T Psi     (Psi on the target rows)
+// where X is the inverse formed so far (the leaves' inverses and the blocks
+// of the deeper levels: block diagonal over the children) and T_off the
+// factor blocks between the children.  With the core G = Psi^T R3 and its
+// column-pivoted QR  G Pi = Q_c R  truncated at the first |R_kk| <= tol |R_00|,
+//     W ~ -(R3 Pi_k R_11^{-1}) (C3 Q_c,k)^T        (generalised Nystrom).
+// All arithmetic is FP64.  Products are "multi-vector" kernels: a reduction
+// T = V^T IN for every low-rank piece (chunks of 128 rows, the last CTA of a
+// piece sums the chunks in order) and a row kernel summing, per 32-row chunk,
+// its dense pieces (optionally one triangle) and its low-rank pieces U T.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "hinv.h"
+#include "hlu_plan.h"
+#include "api_common.h"
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+
+namespace hm {
+
+// ---- multi-vector products (construction only)
+struct MrRed {          // T[slot] (k x S, row-major, stride S) = V^T IN[in0 : in0 + n, :]
+  const double* V;
+  int64_t vrs, vcs;     // V(j, l) = V[j * vrs + l * vcs]
+  int in0, n;
+  const int* rank;      // k = *rank (nullptr: kc)
+  int kc;
+  int c_begin, c_end;   // its reduction chunks
+};
+struct MrItem {         // contribution to the rows of a chunk
+  int kind;             // 0: dense piece, 1: low-rank piece U T[slot]
+  int mask;             // dense square pieces: 1 keeps j <= i, 2 keeps j >= i (local indices)
+  const double* A;      // dense: A(i, j) = A[i rs + j cs]; low rank: U(i, l) = A[i rs + l cs]
+  int64_t rs, cs;
+  int row0;             // output row of local row 0
+  int col0, ncol;       // dense: input rows read
+  const int* rank;      // low rank: k = *rank (nullptr: kc)
+  int kc, slot;
+};
+struct MrChunk { int r0, nr, ib, ie; };
+struct MrPlan {
+  const MrRed* reds;
+  const int2* rch;      // (red item, first row) per reduction chunk
+  int nrch;
+  const MrChunk* chunks;
+  int nchunk;
+  const MrItem* items;
+  double* partial;      // nrch x MAXS^2
+  double* tbuf;         // red items x MAXS^2
+  unsigned* count;      // per red item
+  int S;                // columns of IN and OUT
+};
+
+constexpr int MR_T = HINV_MAXS * HINV_MAXS;
+
+namespace {
+
+__device__ __forceinline__ double urand(unsigned long long key) {
+  // splitmix64 finaliser (Steele, Lea, Flood 2014) -> uniform in (-1, 1)
+  unsigned long long z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// rows [r0, r0 + n) of a row-major block of S columns get seeded uniform values
+struct FillJob { double* buf; int r0, n, S; unsigned long long seed; };
+__global__ void fill_kernel(const FillJob* jobs, int njobs) {
+  const FillJob J = jobs[blockIdx.y];
+  const int64_t total = (int64_t)J.n * J.S;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = J.r0 + e / J.S, c = e % J.S;
+    J.buf[i * J.S + c] = urand(J.seed * 0x100000001B3ull + (unsigned long long)(i * HINV_MAXS + c));
+  }
+}
+
+__global__ void __launch_bounds__(256) mr_red_kernel(MrPlan P, const double* __restrict__ in) {
+  __shared__ int last;
+  const int2 rc = P.rch[blockIdx.x];
+  const MrRed R = P.reds[rc.x];
+  const int k = R.rank ? *R.rank : R.kc;
+  const int S = P.S;
+  const int j0 = rc.y, len = min(HINV_MCH, R.n - j0);
+  const int g = threadIdx.x & 7, lg = threadIdx.x >> 3;  // columns g + 8 q, pieces lg and lg + 32
+  double acc[2][8];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[a][q] = 0.0;
+  const bool l0 = lg < k, l1 = lg + 32 < k;
+  if (l0) {
+    for (int j = 0; j < len; ++j) {
+      const int64_t jj = j0 + j;
+      const double v0 = R.V[jj * R.vrs + (int64_t)lg * R.vcs];
+      const double v1 = l1 ? R.V[jj * R.vrs + (int64_t)(lg + 32) * R.vcs] : 0.0;
+      const double* x = in + (int64_t)(R.in0 + jj) * S;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = g + 8 * q;
+        if (c < S) {
+          const double xv = x[c];
+          acc[0][q] = fma(v0, xv, acc[0][q]);
+          acc[1][q] = fma(v1, xv, acc[1][q]);
+        }
+      }
+    }
+  }
+  double* part = P.partial + (int64_t)blockIdx.x * MR_T;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = g + 8 * q;
+    if (c < S) {
+      if (l0) part[lg * S + c] = acc[0][q];
+      if (l1) part[(lg + 32) * S + c] = acc[1][q];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(P.count + rc.x, 1u) == (unsigned)(R.c_end - R.c_begin - 1) ? 1 : 0;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double* T = P.tbuf + (int64_t)rc.x * MR_T;
+  for (int e = threadIdx.x; e < k * S; e += blockDim.x) {
+    double s = 0.0;
+    for (int cc = R.c_begin; cc < R.c_end; ++cc) s += __ldcg(P.partial + (int64_t)cc * MR_T + e);
+    T[e] = s;
+  }
+  if (threadIdx.x == 0) P.count[rc.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) mr_row_kernel(MrPlan P, const double* __restrict__ in, double* __restrict__ out) {
+  const MrChunk C = P.chunks[blockIdx.x];
+  const int S = P.S;
+  const int g = threadIdx.x & 7, r = threadIdx.x >> 3;
+  const int row = C.r0 + r;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int it = C.ib; it < C.ie; ++it) {
+    const MrItem I = P.items[it];
+    const int i = row - I.row0;  // local row of this thread
+    if (I.kind == 0) {
+      int jlo = 0, jhi = I.ncol;
+      const int ifirst = C.r0 - I.row0, ilast = C.r0 + C.nr - 1 - I.row0;
+      if (I.mask == 1) jhi = min(jhi, ilast + 1);
+      if (I.mask == 2) jlo = max(0, ifirst);
+      const double* arow = I.A + (int64_t)i * I.rs;
+      for (int j = jlo; j < jhi; ++j) {
+        double a = (r < C.nr) ? arow[(int64_t)j * I.cs] : 0.0;
+        if ((I.mask == 1 && j > i) || (I.mask == 2 && j < i)) a = 0.0;
+        const double* x = in + (int64_t)(I.col0 + j) * S;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = g + 8 * q;
+          if (c < S) acc[q] = fma(a, x[c], acc[q]);
+        }
+      }
+    } else {
+      const int k = I.rank ? *I.rank : I.kc;
+      const double* T = P.tbuf + (int64_t)I.slot * MR_T;
+      const double* urow = I.A + (int64_t)i * I.rs;
+      for (int l = 0; l < k; ++l) {
+        const double u = (r < C.nr) ? urow[(int64_t)l * I.cs] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = g + 8 * q;
+          if (c < S) acc[q] = fma(u, T[l * S + c], acc[q]);
+        }
+      }
+    }
+  }
+  if (r < C.nr) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = g + 8 * q;
+      if (c < S) out[(int64_t)row * S + c] = acc[q];
+    }
+  }
+}
+
+// ---- column-pivoted Householder QR of the core G (SP x S, row-major, stride
+// S) of one block, truncated at |R_kk| <= tol |R_00| or the rank cap.  Writes
+// the rank, the pivots, R_11^{-1} (k x k) and the first k columns of Q_c.
+struct Core {
+  int k, capped, pad[2];
+  int piv[HINV_S];
+  double rinv[HINV_KCAP * HINV_KCAP];  // row-major
+  double qc[HINV_SP * HINV_KCAP];      // row-major SP x KCAP
+};
+
+__global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tbuf, Core* cores, int* rank_out,
+                                                   const int* node_of, double tol, int* err) {
+  constexpr int M = HINV_SP, NC = HINV_S;
+  __shared__ double A[M][NC + 1];
+  __shared__ double nrm2[NC];
+  __shared__ double tauv[HINV_KCAP], diagR[HINV_KCAP];
+  __shared__ int piv[NC];
+  __shared__ int s_p, s_stop;
+  __shared__ double s_ref, s_norm;
+  const int b = blockIdx.x;
+  const double* G = tbuf + (int64_t)b * MR_T;  // the core of block b is reduction slot b
+  for (int e = threadIdx.x; e < M * NC; e += blockDim.x) A[e / NC][e % NC] = G[e];
+  if (threadIdx.x < NC) piv[threadIdx.x] = threadIdx.x;
+  __syncthreads();
+  int k = 0;
+  int capped = 0;
+  for (int j = 0; j < NC && j < M; ++j) {
+    if (threadIdx.x < NC && threadIdx.x >= j) {
+      double s = 0.0;
+      for (int i = j; i < M; ++i) s = fma(A[i][threadIdx.x], A[i][threadIdx.x], s);
+      nrm2[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = j;
+      for (int c = j + 1; c < NC; ++c)
+        if (nrm2[c] > nrm2[p]) p = c;
+      const double nm = sqrt(nrm2[p]);
+      if (j == 0) s_ref = nm;
+      int stop = !(nm > tol * s_ref) || nm == 0.0 || !isfinite(nm);
+      if (!stop && j == HINV_KCAP) { stop = 1; capped = 1; }
+      s_stop = stop;
+      s_p = p;
+      s_norm = nm;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != j) {
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double t = A[i][j];
+        A[i][j] = A[i][p];
+        A[i][p] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = piv[j];
+        piv[j] = piv[p];
+        piv[p] = t;
+      }
+    }
+    __syncthreads();
+    // Householder reflector H = I - tau v v^T with v = x - alpha e_1, alpha = -sign(x_0) |x|
+    if (threadIdx.x == 0) {
+      const double x0 = A[j][j];
+      const double alpha = x0 >= 0.0 ? -s_norm : s_norm;
+      const double v0 = x0 - alpha;
+      tauv[j] = -1.0 / (alpha * v0);
+      diagR[j] = alpha;
+      A[j][j] = v0;
+    }
+    __syncthreads();
+    const int c = j + 1 + (int)threadIdx.x;
+    if (c < NC) {
+      double d = 0.0;
+      for (int i = j; i < M; ++i) d = fma(A[i][j], A[i][c], d);
+      d *= tauv[j];
+      for (int i = j; i < M; ++i) A[i][c] = fma(-d, A[i][j], A[i][c]);
+    }
+    __syncthreads();
+    k = j + 1;
+  }
+  Core* out = cores + b;
+  // R_11^{-1}: thread per column, back substitution (R_ii = diagR, R_ic = A[i][c] for i < c)
+  if ((int)threadIdx.x < k) {
+    const int c = threadIdx.x;
+    double x[HINV_KCAP];
+    for (int i = 0; i < HINV_KCAP; ++i) x[i] = 0.0;
+    x[c] = 1.0 / diagR[c];
+    for (int i = c - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int m = i + 1; m <= c; ++m) s = fma(A[i][m], x[m], s);
+      x[i] = -s / diagR[i];
+    }
+    for (int i = 0; i < HINV_KCAP; ++i) out->rinv[i * HINV_KCAP + c] = i <= c ? x[i] : 0.0;
+  }
+  // Q_c columns: e_c through the reflectors in reverse order
+  if ((int)threadIdx.x < k) {
+    const int c = threadIdx.x;
+    double q[M];
+    for (int i = 0; i < M; ++i) q[i] = i == c ? 1.0 : 0.0;
+    for (int h = k - 1; h >= 0; --h) {
+      double d = 0.0;
+      for (int i = h; i < M; ++i) d = fma(A[i][h], q[i], d);
+      d *= tauv[h];
+      for (int i = h; i < M; ++i) q[i] = fma(-d, A[i][h], q[i]);
+    }
+    for (int i = 0; i < M; ++i) out->qc[i * HINV_KCAP + c] = q[i];
+  }
+  if (threadIdx.x < NC) out->piv[threadIdx.x] = piv[threadIdx.x];
+  if (threadIdx.x == 0) {
+    out->k = k;
+    out->capped = capped;
+    rank_out[node_of[b]] = k;
+    if (!isfinite(s_ref)) atomicOr(err, DEVERR_NONFINITE);
+  }
+}
+
+// P = -R3[tgt rows][:, piv_k] R_11^{-1}, Q = C3[src rows] Q_c,k; col-major, zero beyond k
+struct FormJob { int which, core, node_row0, nrow, r_lo; double* dst; int ld; const double* src; int S; };
+__global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Core* cores) {
+  const FormJob J = jobs[blockIdx.x];
+  const Core& K = cores[J.core];
+  const int k = K.k;
+  const int g = threadIdx.x & 7, r = threadIdx.x >> 3;
+  const int i = J.r_lo + r;  // local row of the block
+  if (i >= J.nrow || r >= HINV_RCH) return;
+  const double* x = J.src + (int64_t)(J.node_row0 + i) * J.S;
+  for (int l = g; l < HINV_KCAP; l += 8) {
+    double s = 0.0;
+    if (l < k) {
+      if (J.which == 0) {
+        for (int c = 0; c <= l; ++c) s = fma(x[K.piv[c]], K.rinv[c * HINV_KCAP + l], s);
+        s = -s;
+      } else {
+        for (int c = 0; c < HINV_SP; ++c) s = fma(x[c], K.qc[c * HINV_KCAP + l], s);
+      }
+    }
+    J.dst[(int64_t)l * J.ld + i] = s;
+  }
+}
+
+// leaf inverse -> its triangle in a zero-padded square of row stride ld
+struct LeafCopy { const double* src; int64_t sld; double* dst; int ld, m, lower; };
+__global__ void leaf_copy_kernel(const LeafCopy* jobs) {
+  const LeafCopy J = jobs[blockIdx.y];
+  const int64_t total = (int64_t)J.m * J.ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / J.ld), j = (int)(e % J.ld);
+    const bool keep = j < J.m && (J.lower ? j <= i : j >= i);
+    J.dst[e] = keep ? J.src[(int64_t)i * J.sld + j] : 0.0;
+  }
+}
+
+template <class T>
+__global__ void convert_kernel(const double* src, T* dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) dst[e] = (float)src[e];
+    else dst[e] = __double2bfloat16(src[e]);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+void HinvData::release() {
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+  bytes = 0;
+}
+
+namespace {
+
+int round8(int n) { return (n + 7) & ~7; }
+
+// Host image of one multi-vector product; its arrays live in shared host
+// vectors (one upload for every plan of the construction).
+struct HostMr {
+  int S = 0;
+  int red0 = 0, nred = 0;      // into all reds
+  int rch0 = 0, nrch = 0;      // into all rch
+  int ch0 = 0, nch = 0;        // into all chunks
+  int it0 = 0;                 // into all items
+};
+
+struct Planner {
+  std::vector<MrRed> reds;
+  std::vector<int2> rch;
+  std::vector<MrChunk> chunks;
+  std::vector<MrItem> items;
+  HostMr cur;
+  int max_red = 0, max_rch = 0;
+
+  void begin(int S) {
+    cur = HostMr();
+    cur.S = S;
+    cur.red0 = (int)reds.size();
+    cur.rch0 = (int)rch.size();
+    cur.ch0 = (int)chunks.size();
+    cur.it0 = (int)items.size();
+  }
+  // T slot = returned id (relative to the plan)
+  int red(const double* V, int64_t vrs, int64_t vcs, int in0, int n, const int* rank, int kc) {
+    MrRed R{V, vrs, vcs, in0, n, rank, kc, (int)rch.size() - cur.rch0, 0};
+    const int id = (int)reds.size() - cur.red0;
+    for (int j0 = 0; j0 < n; j0 += HINV_MCH) rch.push_back(make_int2(id, j0));
+    R.c_end = (int)rch.size() - cur.rch0;
+    reds.push_back(R);
+    return id;
+  }
+  void chunk(int r0, int nr) { chunks.push_back(MrChunk{r0, nr, (int)items.size() - cur.it0, 0}); }
+  void item(const MrItem& I) {
+    items.push_back(I);
+    chunks.back().ie = (int)items.size() - cur.it0;
+  }
+  HostMr end() {
+    cur.nred = (int)reds.size() - cur.red0;
+    cur.nrch = (int)rch.size() - cur.rch0;
+    cur.nch = (int)chunks.size() - cur.ch0;
+    max_red = std::max(max_red, cur.nred);
+    max_rch = std::max(max_rch, cur.nrch);
+    return cur;
+  }
+};
+
+MrItem dense_item(const double* A, int64_t rs, int64_t cs, int row0, int col0, int ncol, int mask) {
+  MrItem I{};
+  I.kind = 0;
+  I.mask = mask;
+  I.A = A;
+  I.rs = rs;
+  I.cs = cs;
+  I.row0 = row0;
+  I.col0 = col0;
+  I.ncol = ncol;
+  return I;
+}
+MrItem lr_item(const double* U, int64_t rs, int64_t cs, int row0, const int* rank, int kc, int slot) {
+  MrItem I{};
+  I.kind = 1;
+  I.A = U;
+  I.rs = rs;
+  I.cs = cs;
+  I.row0 = row0;
+  I.rank = rank;
+  I.kc = kc;
+  I.slot = slot;
+  return I;
+}
+
+struct TNode {   // an internal cluster of the 1D tree
+  int cl, level;
+  int a, b;      // children (clusters)
+};
+
+}  // namespace
+
+int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
+               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err) {
+  auto t_start = std::chrono::steady_clock::now();
+  if (P.dim != 1) { err = "hierarchical inverses are built for 1D problems only"; return HM_ERR_ARG; }
+  if (F.kf > HINV_MAXS) { err = "factor rank cap above 64"; return HM_ERR_ARG; }
+  const int N = P.N;
+  out = HinvData();
+  out.prec = prec;
+  out.tol = tol;
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    *p = nullptr;
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+      return HM_ERR_OOM;
+    }
+    out.allocs.push_back(*p);
+    out.bytes += (int64_t)std::max<size_t>(bytes, 16);
+    return HM_OK;
+  };
+  auto upload = [&](auto** dst, const auto& vec) -> int {
+    const size_t n = vec.size() * sizeof(vec[0]);
+    void* p = nullptr;
+    HM_TRY(alloc(&p, n));
+    if (n && cudaMemcpyAsync(p, vec.data(), n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      err = std::string("table upload failed: ") + cudaGetErrorString(cudaGetLastError());
+      return HM_ERR_CUDA;
+    }
+    *dst = (std::remove_reference_t<decltype(**dst)>*)p;
+    return HM_OK;
+  };
+  // ---- tree: leaves (Morton order) with their diagonal dense block, internal nodes
+  const int nl = (int)P.leaves.size();
+  std::vector<int> leaf_of(P.cl.size(), -1), dense_of_leaf(nl, -1);
+  for (int l = 0; l < nl; ++l) leaf_of[P.leaves[l]] = l;
+  for (int d = 0; d < (int)dd.size(); ++d) {
+    if (dd[d].r0 != dd[d].c0) continue;
+    const int t = P.bl[P.dense_block[d]].t;
+    if (leaf_of[t] >= 0) dense_of_leaf[leaf_of[t]] = d;
+  }
+  for (int l = 0; l < nl; ++l) {
+    const int d = dense_of_leaf[l];
+    if (d < 0 || !F.linv[d] || !F.uinv[d]) { err = "a leaf has no inverse of its factors"; return HM_ERR_ARG; }
+    if (P.cl[P.leaves[l]].end - P.cl[P.leaves[l]].begin > 1024) { err = "leaves above 1024 rows"; return HM_ERR_ARG; }
+  }
+  std::vector<TNode> nodes;
+  std::vector<int> node_of(P.cl.size(), -1);
+  int maxlev = -1;
+  for (int c = 0; c < (int)P.cl.size(); ++c) {
+    if (P.cl[c].nchild == 0) continue;
+    if (P.cl[c].nchild != 2) { err = "the 1D cluster tree must be binary"; return HM_ERR_ARG; }
+    node_of[c] = (int)nodes.size();
+    nodes.push_back(TNode{c, P.cl[c].level, P.cl[c].child[0], P.cl[c].child[1]});
+    maxlev = std::max(maxlev, P.cl[c].level);
+  }
+  const int nn = (int)nodes.size();
+  auto range = [&](int c) { return std::make_pair(P.cl[c].begin, P.cl[c].end); };
+  // per triangle: target and source cluster of every node
+  auto tgt = [&](int tri, const TNode& T) { return tri == 0 ? T.b : T.a; };
+  auto src = [&](int tri, const TNode& T) { return tri == 0 ? T.a : T.b; };
+  // per leaf and triangle: nodes whose target (src) range holds the leaf, from the leaf up
+  std::vector<std::vector<int>> anc_t[2], anc_s[2];
+  for (int tri = 0; tri < 2; ++tri) {
+    anc_t[tri].resize(nl);
+    anc_s[tri].resize(nl);
+    for (int l = 0; l < nl; ++l) {
+      int c = P.leaves[l];
+      while (P.cl[c].parent >= 0) {
+        const int par = P.cl[c].parent;
+        const TNode& T = nodes[node_of[par]];
+        if (tgt(tri, T) == c) anc_t[tri][l].push_back(node_of[par]);
+        else anc_s[tri][l].push_back(node_of[par]);
+        c = par;
+      }
+    }
+  }
+  // ---- factor blocks between the children of each node (T_off), by triangle
+  struct OffBlock { bool lowrank; int id; int t, s; };
+  std::vector<std::vector<OffBlock>> toff[2];
+  toff[0].resize(nn);
+  toff[1].resize(nn);
+  auto lca = [&](int t, int s) {
+    int c = t;
+    while (!(P.cl[c].begin <= P.cl[s].begin && P.cl[s].end <= P.cl[c].end)) c = P.cl[c].parent;
+    return c;
+  };
+  for (int d = 0; d < (int)dd.size(); ++d) {
+    const Block& B = P.bl[P.dense_block[d]];
+    if (B.t == B.s) continue;
+    const int A = lca(B.t, B.s);
+    const bool lower = P.cl[B.t].begin >= P.cl[P.cl[A].child[1]].begin;
+    toff[lower ? 0 : 1][node_of[A]].push_back(OffBlock{false, d, B.t, B.s});
+  }
+  for (int q = 0; q < (int)P.lr_block.size(); ++q) {
+    const Block& B = P.bl[P.lr_block[q]];
+    const int A = lca(B.t, B.s);
+    const bool lower = P.cl[B.t].begin >= P.cl[P.cl[A].child[1]].begin;
+    toff[lower ? 0 : 1][node_of[A]].push_back(OffBlock{true, q, B.t, B.s});
+  }
+  // ---- FP64 pools: leaves, P, Q, ranks; per-step tables
+  int* d_rank = nullptr;
+  HM_TRY(alloc((void**)&d_rank, sizeof(int) * 2 * std::max(nn, 1)));
+  if (cudaMemsetAsync(d_rank, 0, sizeof(int) * 2 * std::max(nn, 1), st) != cudaSuccess) {
+    err = std::string("clearing the ranks failed: ") + cudaGetErrorString(cudaGetLastError());
+    return HM_ERR_CUDA;
+  }
+  double* leafpool[2];
+  double* ppool[2];
+  double* qpool[2];
+  int64_t leaf_elems = 0, p_elems[2] = {0, 0}, q_elems[2] = {0, 0};
+  for (int l = 0; l < nl; ++l) {
+    const int m = P.cl[P.leaves[l]].end - P.cl[P.leaves[l]].begin;
+    leaf_elems += (int64_t)m * round8(m);
+  }
+  for (int tri = 0; tri < 2; ++tri) {
+    HinvTriangle& H = out.tri[tri];
+    H.h_leaves.resize(nl);
+    H.h_nodes.resize(nn);
+    int64_t lo = 0, po = 0, qo = 0;
+    for (int l = 0; l < nl; ++l) {
+      const auto r = range(P.leaves[l]);
+      HinvLeaf& L = H.h_leaves[l];
+      L.r0 = r.first;
+      L.m = r.second - r.first;
+      L.ld = round8(L.m);
+      L.off = lo;
+      lo += (int64_t)L.m * L.ld;
+    }
+    for (int v = 0; v < nn; ++v) {
+      HinvNode& Nd = H.h_nodes[v];
+      const auto rt = range(tgt(tri, nodes[v])), rs = range(src(tri, nodes[v]));
+      Nd.tgt0 = rt.first;
+      Nd.tgt_n = rt.second - rt.first;
+      Nd.src0 = rs.first;
+      Nd.src_n = rs.second - rs.first;
+      Nd.pld = round8(Nd.tgt_n);
+      Nd.qld = round8(Nd.src_n);
+      Nd.poff = po;
+      Nd.qoff = qo;
+      po += (int64_t)Nd.pld * HINV_KCAP;
+      qo += (int64_t)Nd.qld * HINV_KCAP;
+    }
+    p_elems[tri] = po;
+    q_elems[tri] = qo;
+    HM_TRY(alloc((void**)&leafpool[tri], sizeof(double) * std::max<int64_t>(leaf_elems, 1)));
+    HM_TRY(alloc((void**)&ppool[tri], sizeof(double) * std::max<int64_t>(po, 1)));
+    HM_TRY(alloc((void**)&qpool[tri], sizeof(double) * std::max<int64_t>(qo, 1)));
+  }
+  // leaf inverses -> triangles
+  {
+    std::vector<LeafCopy> lc;
+    for (int tri = 0; tri < 2; ++tri)
+      for (int l = 0; l < nl; ++l) {
+        const int d = dense_of_leaf[l];
+        const HinvLeaf& L = out.tri[tri].h_leaves[l];
+        lc.push_back(LeafCopy{tri == 0 ? F.linv[d] : F.uinv[d], F.linv_ld[d], leafpool[tri] + L.off, L.ld, L.m,
+                              tri == 0 ? 1 : 0});
+      }
+    LeafCopy* d_lc = nullptr;
+    HM_TRY(upload(&d_lc, lc));
+    count_launches(1);
+    leaf_copy_kernel<<<dim3(16, (unsigned)lc.size()), 256, 0, st>>>(d_lc);
+  }
+  // ---- construction plans, level by level (deepest first), both triangles
+  Planner PL;
+  struct Step {
+    int tri, level;
+    HostMr mr[7];              // XR, TR, XR2, XC, TC, XC2, gram
+    std::vector<FillJob> fill;
+    std::vector<FormJob> form;
+    std::vector<int> core_node;  // rank index per core
+  };
+  std::vector<Step> steps;
+  double* bufA[2];
+  double* bufB[2];
+  double* bufC[2];
+  double* bufD[2];
+  double* bufE[2];
+  std::vector<void*> tmp_allocs;
+  auto tmp_alloc = [&](double** p, int64_t n) -> int {
+    if (cudaMalloc((void**)p, sizeof(double) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      err = "device allocation of construction buffers failed";
+      return HM_ERR_OOM;
+    }
+    tmp_allocs.push_back(*p);
+    return HM_OK;
+  };
+  auto free_tmp = [&]() {
+    for (void* p : tmp_allocs) cudaFree(p);
+    tmp_allocs.clear();
+  };
+  int s = HM_OK;
+  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
+    if ((s = tmp_alloc(&bufA[tri], (int64_t)N * HINV_S)) != HM_OK) break;
+    if ((s = tmp_alloc(&bufB[tri], (int64_t)N * HINV_S)) != HM_OK) break;
+    if ((s = tmp_alloc(&bufC[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
+    if ((s = tmp_alloc(&bufD[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
+    if ((s = tmp_alloc(&bufE[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
+  }
+  if (s != HM_OK) { free_tmp(); return s; }
+  const int kf = F.kf;
+  for (int lev = maxlev; lev >= 0; --lev) {
+    std::vector<int> lv;
+    for (int v = 0; v < nn; ++v)
+      if (nodes[v].level == lev) lv.push_back(v);
+    if (lv.empty()) continue;
+    for (int tri = 0; tri < 2; ++tri) {
+      const HinvTriangle& H = out.tri[tri];
+      const int* rk = d_rank + tri * nn;
+      Step S;
+      S.tri = tri;
+      S.level = lev;
+      // X (transposed or not) on the given part of every node of the level
+      auto x_plan = [&](bool trans, bool on_src, int width) {
+        PL.begin(width);
+        std::vector<int> slot(nn, -1);
+        for (int v : lv) {
+          const int part = on_src ? src(tri, nodes[v]) : tgt(tri, nodes[v]);
+          const auto pr = range(part);
+          for (int l = 0; l < nl; ++l) {
+            const HinvLeaf& L = H.h_leaves[l];
+            if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
+            const std::vector<int>& anc = trans ? anc_s[tri][l] : anc_t[tri][l];
+            for (int q : anc) {
+              if (nodes[q].level <= lev || slot[q] >= 0) continue;
+              const HinvNode& Q = H.h_nodes[q];
+              slot[q] = trans ? PL.red(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, Q.tgt_n, rk + q, HINV_KCAP)
+                              : PL.red(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, Q.src_n, rk + q, HINV_KCAP);
+            }
+            for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
+              PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
+              const double* X = leafpool[tri] + L.off;
+              const int mask = (tri == 0) != trans ? 1 : 2;
+              PL.item(trans ? dense_item(X, 1, L.ld, L.r0, L.r0, L.m, mask)
+                            : dense_item(X, L.ld, 1, L.r0, L.r0, L.m, mask));
+              for (int q : anc) {
+                if (nodes[q].level <= lev) continue;
+                const HinvNode& Q = H.h_nodes[q];
+                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, rk + q, HINV_KCAP, slot[q])
+                              : lr_item(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, rk + q, HINV_KCAP, slot[q]));
+              }
+            }
+          }
+        }
+        return PL.end();
+      };
+      // T_off (transposed or not): output rows = target (source) part
+      auto t_plan = [&](bool trans, int width) {
+        PL.begin(width);
+        for (int v : lv) {
+          const int part = trans ? src(tri, nodes[v]) : tgt(tri, nodes[v]);
+          const auto pr = range(part);
+          const std::vector<OffBlock>& ob = toff[tri][v];
+          std::vector<int> slot(ob.size(), -1);
+          for (size_t k = 0; k < ob.size(); ++k) {
+            if (!ob[k].lowrank) continue;
+            const int q = ob[k].id;
+            const int m = P.cl[ob[k].t].end - P.cl[ob[k].t].begin, n = P.cl[ob[k].s].end - P.cl[ob[k].s].begin;
+            slot[k] = trans ? PL.red(F.lr_u[q], 1, m, P.cl[ob[k].t].begin, m, d_rank_f + q, kf)
+                            : PL.red(F.lr_v[q], 1, n, P.cl[ob[k].s].begin, n, d_rank_f + q, kf);
+          }
+          for (int l = 0; l < nl; ++l) {
+            const HinvLeaf& L = H.h_leaves[l];
+            if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
+            for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
+              PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
+              for (size_t k = 0; k < ob.size(); ++k) {
+                const Cluster& T = P.cl[ob[k].t];
+                const Cluster& Sc = P.cl[ob[k].s];
+                const Cluster& out_cl = trans ? Sc : T;
+                if (L.r0 < out_cl.begin || L.r0 + L.m > out_cl.end) continue;
+                if (!ob[k].lowrank) {
+                  const View& V = F.dense[ob[k].id];
+                  PL.item(trans ? dense_item(V.p, V.cs, V.rs, Sc.begin, T.begin, T.end - T.begin, 0)
+                                : dense_item(V.p, V.rs, V.cs, T.begin, Sc.begin, Sc.end - Sc.begin, 0));
+                } else {
+                  const int q = ob[k].id;
+                  const int m = T.end - T.begin, n = Sc.end - Sc.begin;
+                  PL.item(trans ? lr_item(F.lr_v[q], 1, n, Sc.begin, d_rank_f + q, kf, slot[k])
+                                : lr_item(F.lr_u[q], 1, m, T.begin, d_rank_f + q, kf, slot[k]));
+                }
+              }
+            }
+          }
+        }
+        return PL.end();
+      };
+      S.mr[0] = x_plan(false, true, HINV_S);
+      S.mr[1] = t_plan(false, HINV_S);
+      S.mr[2] = x_plan(false, false, HINV_S);
+      S.mr[3] = x_plan(true, false, HINV_SP);
+      S.mr[4] = t_plan(true, HINV_SP);
+      S.mr[5] = x_plan(true, true, HINV_SP);
+      PL.begin(HINV_S);
+      for (int v : lv) {
+        const HinvNode& Nd = H.h_nodes[v];
+        PL.red(bufC[tri] + (int64_t)Nd.tgt0 * HINV_SP, HINV_SP, 1, Nd.tgt0, Nd.tgt_n, nullptr, HINV_SP);
+      }
+      S.mr[6] = PL.end();
+      const unsigned long long seed = 1000003ull * (unsigned long long)(lev + 1) + 17ull * tri;
+      for (size_t b = 0; b < lv.size(); ++b) {
+        const HinvNode& Nd = H.h_nodes[lv[b]];
+        S.fill.push_back(FillJob{bufA[tri], Nd.src0, Nd.src_n, HINV_S, 2 * seed});
+        S.fill.push_back(FillJob{bufC[tri], Nd.tgt0, Nd.tgt_n, HINV_SP, 2 * seed + 1});
+        S.core_node.push_back(tri * nn + lv[b]);
+        for (int r = 0; r < Nd.tgt_n; r += HINV_RCH)
+          S.form.push_back(FormJob{0, (int)b, Nd.tgt0, Nd.tgt_n, r, ppool[tri] + Nd.poff, Nd.pld, bufB[tri], HINV_S});
+        for (int r = 0; r < Nd.src_n; r += HINV_RCH)
+          S.form.push_back(FormJob{1, (int)b, Nd.src0, Nd.src_n, r, qpool[tri] + Nd.qoff, Nd.qld, bufD[tri], HINV_SP});
+      }
+      steps.push_back(std::move(S));
+    }
+  }
+  // ---- upload every plan at once, then run the levels in order
+  MrRed* d_reds = nullptr;
+  int2* d_rch = nullptr;
+  MrChunk* d_chunks = nullptr;
+  MrItem* d_items = nullptr;
+  double* d_partial = nullptr;
+  double* d_tbuf = nullptr;
+  unsigned* d_count = nullptr;
+  Core* d_cores = nullptr;
+  std::vector<FillJob> all_fill;
+  std::vector<FormJob> all_form;
+  std::vector<int> all_core_node;
+  std::vector<int> fill_off, form_off, core_off;
+  int max_nodes_level = 1;
+  for (const Step& S : steps) {
+    fill_off.push_back((int)all_fill.size());
+    form_off.push_back((int)all_form.size());
+    core_off.push_back((int)all_core_node.size());
+    all_fill.insert(all_fill.end(), S.fill.begin(), S.fill.end());
+    all_form.insert(all_form.end(), S.form.begin(), S.form.end());
+    all_core_node.insert(all_core_node.end(), S.core_node.begin(), S.core_node.end());
+    max_nodes_level = std::max(max_nodes_level, (int)S.core_node.size());
+  }
+  FillJob* d_fill = nullptr;
+  FormJob* d_form = nullptr;
+  int* d_core_node = nullptr;
+  auto tmp_upload = [&](auto** dst, const auto& vec) -> int {
+    const size_t n = std::max<size_t>(vec.size() * sizeof(vec[0]), 16);
+    void* p = nullptr;
+    if (cudaMalloc(&p, n) != cudaSuccess) { cudaGetLastError(); err = "device allocation failed"; return HM_ERR_OOM; }
+    tmp_allocs.push_back(p);
+    if (!vec.empty() && cudaMemcpyAsync(p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return HM_ERR_CUDA;
+    *dst = (std::remove_reference_t<decltype(**dst)>*)p;
+    return HM_OK;
+  };
+  if (s == HM_OK) s = tmp_upload(&d_reds, PL.reds);
+  if (s == HM_OK) s = tmp_upload(&d_rch, PL.rch);
+  if (s == HM_OK) s = tmp_upload(&d_chunks, PL.chunks);
+  if (s == HM_OK) s = tmp_upload(&d_items, PL.items);
+  if (s == HM_OK) s = tmp_upload(&d_fill, all_fill);
+  if (s == HM_OK) s = tmp_upload(&d_form, all_form);
+  if (s == HM_OK) s = tmp_upload(&d_core_node, all_core_node);
+  if (s == HM_OK) s = tmp_alloc(&d_partial, (int64_t)std::max(PL.max_rch, 1) * MR_T);
+  if (s == HM_OK) s = tmp_alloc(&d_tbuf, (int64_t)std::max(PL.max_red, 1) * MR_T);
+  if (s == HM_OK) s = tmp_alloc((double**)&d_count, std::max(PL.max_red, 1));
+  if (s == HM_OK) s = tmp_alloc((double**)&d_cores, ((int64_t)max_nodes_level * sizeof(Core) + 7) / 8);
+  if (s == HM_OK && cudaMemsetAsync(d_count, 0, sizeof(double) * std::max(PL.max_red, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
+  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
+    if (cudaMemsetAsync(ppool[tri], 0, sizeof(double) * std::max<int64_t>(p_elems[tri], 1), st) != cudaSuccess ||
+        cudaMemsetAsync(qpool[tri], 0, sizeof(double) * std::max<int64_t>(q_elems[tri], 1), st) != cudaSuccess) {
+      err = "clearing the inverse pools failed";
+      s = HM_ERR_CUDA;
+    }
+  }
+  if (s != HM_OK) { free_tmp(); return s; }
+  auto run_mr = [&](const HostMr& h, const double* in, double* o) {
+    MrPlan M{d_reds + h.red0, d_rch + h.rch0, h.nrch, d_chunks + h.ch0, h.nch, d_items + h.it0,
+             d_partial, d_tbuf, d_count, h.S};
+    if (h.nrch > 0) {
+      count_launches(1);
+      mr_red_kernel<<<h.nrch, 256, 0, st>>>(M, in);
+    }
+    if (h.nch > 0 && o) {
+      count_launches(1);
+      mr_row_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
+    }
+  };
+  for (size_t k = 0; k < steps.size(); ++k) {
+    const Step& S = steps[k];
+    const int t = S.tri;
+    if (!S.fill.empty()) {
+      count_launches(1);
+      fill_kernel<<<dim3(32, (unsigned)S.fill.size()), 256, 0, st>>>(d_fill + fill_off[k], (int)S.fill.size());
+    }
+    run_mr(S.mr[0], bufA[t], bufB[t]);   // X Omega          (source rows)
+    run_mr(S.mr[1], bufB[t], bufA[t]);   // T_off X Omega    (target rows)
+    run_mr(S.mr[2], bufA[t], bufB[t]);   // R3               (target rows)
+    run_mr(S.mr[3], bufC[t], bufD[t]);   // X^T Psi          (target rows)
+    run_mr(S.mr[4], bufD[t], bufE[t]);   // T_off^T X^T Psi  (source rows)
+    run_mr(S.mr[5], bufE[t], bufD[t]);   // C3               (source rows)
+    run_mr(S.mr[6], bufB[t], nullptr);   // cores Psi^T R3 in slots 0..
+    const int nb = (int)S.core_node.size();
+    count_launches(2);
+    cpqr_kernel<<<nb, 256, 0, st>>>(d_tbuf, d_cores, d_rank, d_core_node + core_off[k], tol, d_err);
+    form_kernel<<<(unsigned)S.form.size(), 256, 0, st>>>(d_form + form_off[k], d_cores);
+  }
+  if (cudaGetLastError() != cudaSuccess) { free_tmp(); err = "construction launch failed"; return HM_ERR_CUDA; }
+  // ---- per-step tables
+  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
+    HinvTriangle& H = out.tri[tri];
+    std::vector<int> anc;
+    std::vector<int2> tch, rch;
+    for (int l = 0; l < nl; ++l) {
+      HinvLeaf& L = H.h_leaves[l];
+      L.anc_begin = (int)anc.size();
+      anc.insert(anc.end(), anc_t[tri][l].begin(), anc_t[tri][l].end());
+      L.anc_end = (int)anc.size();
+      for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) rch.push_back(make_int2(l, i0));
+    }
+    for (int v = 0; v < nn; ++v) {
+      HinvNode& Nd = H.h_nodes[v];
+      Nd.tch_begin = (int)tch.size();
+      for (int j0 = 0; j0 < Nd.src_n; j0 += HINV_TCH) tch.push_back(make_int2(v, j0));
+      Nd.tch_end = (int)tch.size();
+    }
+    HinvApply& A = H.A64;
+    A.lower = tri == 0 ? 1 : 0;
+    A.prec = HINV_F64;
+    A.nleaf = nl;
+    A.nnode = nn;
+    A.ntch = (int)tch.size();
+    A.nrch = (int)rch.size();
+    if (s == HM_OK) s = upload((HinvLeaf**)&A.leaves, H.h_leaves);
+    if (s == HM_OK) s = upload((HinvNode**)&A.nodes, H.h_nodes);
+    if (s == HM_OK) s = upload((int**)&A.anc, anc);
+    if (s == HM_OK) s = upload((int2**)&A.tch, tch);
+    if (s == HM_OK) s = upload((int2**)&A.rch, rch);
+    A.leaf_pool = leafpool[tri];
+    A.p_pool = ppool[tri];
+    A.q_pool = qpool[tri];
+    A.rank = d_rank + tri * nn;
+    if (s == HM_OK) s = alloc((void**)&A.tpart, sizeof(double) * HINV_KCAP * std::max<size_t>(tch.size(), 1));
+    if (s == HM_OK) s = alloc((void**)&A.tvec, sizeof(double) * HINV_KCAP * std::max(nn, 1));
+    if (s == HM_OK) s = alloc((void**)&A.tcount, sizeof(unsigned) * std::max(nn, 1));
+    if (s == HM_OK && cudaMemsetAsync(A.tcount, 0, sizeof(unsigned) * std::max(nn, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
+    H.A = A;
+    if (s == HM_OK && prec != HINV_F64) {
+      const size_t es = prec == HINV_F32 ? 4 : 2;
+      void* pl = nullptr;
+      void* pp = nullptr;
+      void* pq = nullptr;
+      if (s == HM_OK) s = alloc(&pl, es * std::max<int64_t>(leaf_elems, 1));
+      if (s == HM_OK) s = alloc(&pp, es * std::max<int64_t>(p_elems[tri], 1));
+      if (s == HM_OK) s = alloc(&pq, es * std::max<int64_t>(q_elems[tri], 1));
+      if (s == HM_OK) {
+        count_launches(3);
+        if (prec == HINV_F32) {
+          convert_kernel<float><<<1216, 256, 0, st>>>(leafpool[tri], (float*)pl, leaf_elems);
+          convert_kernel<float><<<1216, 256, 0, st>>>(ppool[tri], (float*)pp, p_elems[tri]);
+          convert_kernel<float><<<1216, 256, 0, st>>>(qpool[tri], (float*)pq, q_elems[tri]);
+        } else {
+          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(leafpool[tri], (__nv_bfloat16*)pl, leaf_elems);
+          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(ppool[tri], (__nv_bfloat16*)pp, p_elems[tri]);
+          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(qpool[tri], (__nv_bfloat16*)pq, q_elems[tri]);
+        }
+        H.A.prec = prec;
+        H.A.leaf_pool = pl;
+        H.A.p_pool = pp;
+        H.A.q_pool = pq;
+      }
+    }
+  }
+  if (s == HM_OK) s = alloc((void**)&out.d_y, sizeof(double) * std::max(N, 1));
+  // ranks to the host (synchronises: the construction buffers are then freed)
+  std::vector<int> hr(2 * std::max(nn, 1), 0);
+  if (s == HM_OK && cudaMemcpyAsync(hr.data(), d_rank, sizeof(int) * hr.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    s = HM_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
+  free_tmp();
+  if (s != HM_OK) {
+    if (err.empty()) err = "hierarchical inverse construction failed";
+    return s;
+  }
+  const size_t es = prec == HINV_F64 ? 8 : (prec == HINV_F32 ? 4 : 2);
+  int64_t sb = 0;
+  for (int tri = 0; tri < 2; ++tri) {
+    HinvTriangle& H = out.tri[tri];
+    H.h_rank.assign(hr.begin() + tri * nn, hr.begin() + tri * nn + nn);
+    for (const HinvLeaf& L : H.h_leaves) sb += (int64_t)L.m * (L.m + 1) / 2;
+    for (int v = 0; v < nn; ++v) {
+      const HinvNode& Nd = H.h_nodes[v];
+      sb += (int64_t)(Nd.tgt_n + Nd.src_n) * H.h_rank[v];
+      out.max_rank = std::max(out.max_rank, H.h_rank[v]);
+      out.capped += H.h_rank[v] >= HINV_KCAP ? 1 : 0;
+    }
+  }
+  out.step_bytes = sb * (int64_t)es;
+  out.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return HM_OK;
+}
+
+int hinv_solve(const HinvData& D, const double* b, double* z, cudaStream_t st) {
+  HM_TRY(launch_hinv_apply(D.tri[0].A, b, D.d_y, st));
+  return launch_hinv_apply(D.tri[1].A, D.d_y, z, st);
+}
+
+}  // namespace hm

@@ -1063,6 +1063,7 @@ struct ExecArgs {
   int nops;
   int* err;
   unsigned long long* trace;  // optional, TRACE_STRIDE per task: grabbed, producers-ready, finished (ns), CTA, sub-steps
+  unsigned long long wait_ns; // limit of one dependency wait
 };
 
 // Release add at GPU scope: a CTA-wide barrier followed by one thread's
@@ -1097,7 +1098,7 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
 #if HM_POLL_NS > 0
         __nanosleep(HM_POLL_NS);
 #endif
-        if ((++polls & 255u) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) {
+        if ((++polls & 255u) == 0 && global_ns() - t0 > a.wait_ns) {
           atomicOr(a.err, DEVERR_TIMEOUT);
           good = false;
           break;
@@ -1340,8 +1341,19 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   S.mode = (g.empty() && l.empty() && tr.empty()) ? (mode == SOLVE_MODE_THROUGHPUT ? 2 : 1) : 0;
   if (std::getenv("HM_PHASE_TRACE")) S.host_tasks.swap(tasks);  // kept for tracing only
   if ((st = up(wb, &S.wave_begin)) != HM_OK) return st;
-  if ((st = up(info, &S.ops)) != HM_OK) return st;
   if ((st = up(deps, &S.deps)) != HM_OK) return st;
+  // Test-only fault injection (failure detection of the bounded waits):
+  // HM_TEST_STALL_OP=<op> makes op <op> of this schedule require one task more
+  // than it has, so its consumers' waits can only run out; HM_WAIT_LIMIT_MS
+  // shortens the limit of every dependency wait of the schedule.
+  if (const char* so = std::getenv("HM_TEST_STALL_OP")) {
+    const int id = std::atoi(so);
+    if (id >= 0 && id < nops) info[id].ntasks += 1;
+  }
+  if ((st = up(info, &S.ops)) != HM_OK) return st;
+  S.wait_ns = WAIT_LIMIT_NS;
+  if (const char* wl = std::getenv("HM_WAIT_LIMIT_MS"))
+    if (std::atoll(wl) > 0) S.wait_ns = (unsigned long long)std::atoll(wl) * 1000000ull;
   std::vector<int> cnt(nops + 1, 0);
   if ((st = up(cnt, &S.counters)) != HM_OK) return st;
   if (copy_stream && cudaStreamSynchronize(copy_stream) != cudaSuccess) return HM_ERR_CUDA;
@@ -1382,7 +1394,7 @@ int run_schedule(const DevSchedule& S, int* d_err, cudaStream_t st, unsigned lon
   // counters[nops] is the task dispenser
   if (cudaMemsetAsync(S.counters, 0, sizeof(int) * (S.nops + 1), st) != cudaSuccess) return HM_ERR_CUDA;
   ExecArgs a{S.gemm, S.lu, S.trunc, S.copy, S.reduce, S.rows, S.vpart, S.srcs, S.tasks, S.wave_begin,
-             S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, S.nops, d_err, trace};
+             S.ops, S.deps, S.counters, S.counters + S.nops, (int)S.ntasks, S.nops, d_err, trace, S.wait_ns};
   void* args[] = {&a};
   count_launches(1);
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid[m]), dim3(EXEC_THREADS), args, smem, st);

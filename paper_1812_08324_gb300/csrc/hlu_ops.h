@@ -203,6 +203,7 @@ struct DevSchedule {
   int* counters = nullptr;   // per op: finished tasks
   std::vector<Task> host_tasks;  // the task list in hand-out order (for tracing)
   int mode = 0;                  // executor mode (0: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
+  unsigned long long wait_ns = 4000000000ull;  // limit of one dependency wait (ns; set at upload)
 };
 
 // One schedule among several uploaded side by side (independent problems):

@@ -961,7 +961,8 @@ class HLU {
 
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
-             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha) {
+             double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha,
+             int sb_rows_opt, bool solve_blocks) {
   Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
   if (const char* lag = std::getenv("HM_TMP_LAG")) E.tmp_lag = std::atoi(lag);
   if (out.sink && out.chunk_ops > 0) {
@@ -1013,85 +1014,87 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   }
   H.hlu(0);
   for (int q = 0; q < nl; ++q) H.flush(q);  // recompress what is still pending
-  E.phase = 1;
-  // Solve blocks and their exact diagonal inverses, then the scaled couplings.
-  FactorLayout& FL = out.F;
-  {
-    // 1D problems from 32768 unknowns use solve blocks twice as large: half as
-    // many steps on the solve's dependency chain for 36 % more inverse FMAs
-    // (measured at N = 65536: solve 1.57 -> 1.42 ms, factor +0.06 s)
-    const int sb_rows = (P.dim == 1 && P.N >= 32768) ? 2 * SOLVE_BLOCK : SOLVE_BLOCK;
-    std::vector<int> stack = {0};
-    while (!stack.empty()) {
-      int c = stack.back();
-      stack.pop_back();
-      const Cluster& C = P.cl[c];
-      if (C.end - C.begin <= sb_rows || C.nchild == 0) {
-        FL.sb_cluster.push_back(c);
-      } else {
-        for (int k = C.nchild - 1; k >= 0; --k) stack.push_back(C.child[k]);
+  if (solve_blocks) {
+    E.phase = 1;
+    // Solve blocks and their exact diagonal inverses, then the scaled couplings.
+    FactorLayout& FL = out.F;
+    {
+      // 1D problems from 32768 unknowns use solve blocks twice as large: half as
+      // many steps on the solve's dependency chain for 36 % more inverse FMAs
+      // (measured at N = 65536: solve 1.57 -> 1.42 ms, factor +0.06 s)
+      const int sb_rows = sb_rows_opt > 0 ? sb_rows_opt : ((P.dim == 1 && P.N >= 32768) ? 2 * SOLVE_BLOCK : SOLVE_BLOCK);
+      std::vector<int> stack = {0};
+      while (!stack.empty()) {
+        int c = stack.back();
+        stack.pop_back();
+        const Cluster& C = P.cl[c];
+        if (C.end - C.begin <= sb_rows || C.nchild == 0) {
+          FL.sb_cluster.push_back(c);
+        } else {
+          for (int k = C.nchild - 1; k >= 0; --k) stack.push_back(C.child[k]);
+        }
       }
+      std::sort(FL.sb_cluster.begin(), FL.sb_cluster.end(),
+                [&](int x, int y) { return P.cl[x].begin < P.cl[y].begin; });
     }
-    std::sort(FL.sb_cluster.begin(), FL.sb_cluster.end(),
-              [&](int x, int y) { return P.cl[x].begin < P.cl[y].begin; });
-  }
-  std::vector<int> diag_block(P.cl.size(), -1);
-  for (int bi = 0; bi < (int)P.bl.size(); ++bi)
-    if (P.bl[bi].t == P.bl[bi].s) diag_block[P.bl[bi].t] = bi;
-  const int nsb = (int)FL.sb_cluster.size();
-  std::vector<View> sbL(nsb), sbU(nsb);
-  for (int k = 0; k < nsb; ++k) {
-    const Cluster& C = P.cl[FL.sb_cluster[k]];
-    const int S = C.end - C.begin;
-    const int db = diag_block[FL.sb_cluster[k]];
-    View Li = E.new_mat(S, S, false), UiT = E.new_mat(S, S, false), Ui = E.new_mat(S, S, false);
-    for (View* X : {&Li, &UiT}) E.copy(*X, 0.0, nullptr, 0.0);
-    H.linv_ident(db, Li, 0);    // L_BB^{-1}
-    H.uinvt_ident(db, UiT, 0);  // U_BB^{-T}
-    View UiTt = UiT.T();
-    E.copy(Ui, 1.0, &UiTt, 0.0);
-    sbL[k] = Li;
-    sbU[k] = Ui;
-    FL.sb_linv.push_back(Li.p);
-    FL.sb_uinv.push_back(Ui.p);
-  }
-  std::vector<int> sb_of_row(P.N, 0);
-  for (int k = 0; k < nsb; ++k)
-    for (int r = P.cl[FL.sb_cluster[k]].begin; r < P.cl[FL.sb_cluster[k]].end; ++r) sb_of_row[r] = k;
-  E.phase = 2;
-  auto couple = [&](int tcl, int scl, bool lowrank, int id, bool lower, const View& rowsrc) {
-    // rowsrc: the block's rows (dense m x n, or U m x kf); scale each part in a solve block
-    const Cluster& T = P.cl[tcl];
-    const Cluster& Sc = P.cl[scl];
-    for (int r = T.begin; r < T.end;) {
-      const int k = sb_of_row[r];
+    std::vector<int> diag_block(P.cl.size(), -1);
+    for (int bi = 0; bi < (int)P.bl.size(); ++bi)
+      if (P.bl[bi].t == P.bl[bi].s) diag_block[P.bl[bi].t] = bi;
+    const int nsb = (int)FL.sb_cluster.size();
+    std::vector<View> sbL(nsb), sbU(nsb);
+    for (int k = 0; k < nsb; ++k) {
       const Cluster& C = P.cl[FL.sb_cluster[k]];
-      const int e = std::min(T.end, C.end);
-      const bool internal = Sc.begin >= C.begin && Sc.end <= C.end && T.begin >= C.begin && T.end <= C.end;
-      if (!internal) {
-        const int S = C.end - C.begin, len = e - r;
-        const View& inv = lower ? sbL[k] : sbU[k];
-        View o = E.new_mat(S, rowsrc.cols, false);
-        // a lower (upper) triangular inverse leaves the rows above (below) the
-        // source rows zero: only rows [lo, hi) are products, the rest is zero
-        const int lo = lower ? r - C.begin : 0, hi = lower ? S : e - C.begin;
-        E.gemm(o.sub(lo, 0, hi - lo, rowsrc.cols), 1.0, inv.sub(lo, r - C.begin, hi - lo, len),
-               rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
-        if (lo > 0) E.copy(o.sub(0, 0, lo, rowsrc.cols), 0.0, nullptr, 0.0);
-        if (hi < S) E.copy(o.sub(hi, 0, S - hi, rowsrc.cols), 0.0, nullptr, 0.0);
-        FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols, lo, hi});
-      }
-      r = e;
+      const int S = C.end - C.begin;
+      const int db = diag_block[FL.sb_cluster[k]];
+      View Li = E.new_mat(S, S, false), UiT = E.new_mat(S, S, false), Ui = E.new_mat(S, S, false);
+      for (View* X : {&Li, &UiT}) E.copy(*X, 0.0, nullptr, 0.0);
+      H.linv_ident(db, Li, 0);    // L_BB^{-1}
+      H.uinvt_ident(db, UiT, 0);  // U_BB^{-T}
+      View UiTt = UiT.T();
+      E.copy(Ui, 1.0, &UiTt, 0.0);
+      sbL[k] = Li;
+      sbU[k] = Ui;
+      FL.sb_linv.push_back(Li.p);
+      FL.sb_uinv.push_back(Ui.p);
     }
-  };
-  for (int d = 0; d < nd; ++d) {
-    if (dd[d].r0 == dd[d].c0) continue;
-    const Block& Bk = P.bl[P.dense_block[d]];
-    couple(Bk.t, Bk.s, false, d, dd[d].r0 > dd[d].c0, H.dense[d]);
-  }
-  for (int q = 0; q < nl; ++q) {
-    const Block& Bk = P.bl[P.lr_block[q]];
-    couple(Bk.t, Bk.s, true, q, ld[q].r0 > ld[q].c0, H.lrU(q));
+    std::vector<int> sb_of_row(P.N, 0);
+    for (int k = 0; k < nsb; ++k)
+      for (int r = P.cl[FL.sb_cluster[k]].begin; r < P.cl[FL.sb_cluster[k]].end; ++r) sb_of_row[r] = k;
+    E.phase = 2;
+    auto couple = [&](int tcl, int scl, bool lowrank, int id, bool lower, const View& rowsrc) {
+      // rowsrc: the block's rows (dense m x n, or U m x kf); scale each part in a solve block
+      const Cluster& T = P.cl[tcl];
+      const Cluster& Sc = P.cl[scl];
+      for (int r = T.begin; r < T.end;) {
+        const int k = sb_of_row[r];
+        const Cluster& C = P.cl[FL.sb_cluster[k]];
+        const int e = std::min(T.end, C.end);
+        const bool internal = Sc.begin >= C.begin && Sc.end <= C.end && T.begin >= C.begin && T.end <= C.end;
+        if (!internal) {
+          const int S = C.end - C.begin, len = e - r;
+          const View& inv = lower ? sbL[k] : sbU[k];
+          View o = E.new_mat(S, rowsrc.cols, false);
+          // a lower (upper) triangular inverse leaves the rows above (below) the
+          // source rows zero: only rows [lo, hi) are products, the rest is zero
+          const int lo = lower ? r - C.begin : 0, hi = lower ? S : e - C.begin;
+          E.gemm(o.sub(lo, 0, hi - lo, rowsrc.cols), 1.0, inv.sub(lo, r - C.begin, hi - lo, len),
+                 rowsrc.sub(r - T.begin, 0, len, rowsrc.cols), 0.0);
+          if (lo > 0) E.copy(o.sub(0, 0, lo, rowsrc.cols), 0.0, nullptr, 0.0);
+          if (hi < S) E.copy(o.sub(hi, 0, S - hi, rowsrc.cols), 0.0, nullptr, 0.0);
+          FL.scaled.push_back({lower, lowrank, id, k, o.p, rowsrc.cols, lo, hi});
+        }
+        r = e;
+      }
+    };
+    for (int d = 0; d < nd; ++d) {
+      if (dd[d].r0 == dd[d].c0) continue;
+      const Block& Bk = P.bl[P.dense_block[d]];
+      couple(Bk.t, Bk.s, false, d, dd[d].r0 > dd[d].c0, H.dense[d]);
+    }
+    for (int q = 0; q < nl; ++q) {
+      const Block& Bk = P.bl[P.lr_block[q]];
+      couple(Bk.t, Bk.s, true, q, ld[q].r0 > ld[q].c0, H.lrU(q));
+    }
   }
   if (E.status != HM_OK || arena.status != HM_OK) {
     out.err = "H-LU planning failed (device memory or shape)";

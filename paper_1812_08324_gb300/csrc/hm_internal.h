@@ -54,6 +54,10 @@ struct Plan {
 };
 
 int make_plan(const hm_problem& p, const hm_opts& o, Plan& plan, std::string& err);
+// HM_SOLVE_SUBST or HM_SOLVE_HINV for these options (HM_SOLVE_AUTO resolved).
+int solve_mode(const hm_problem& p, const hm_opts& o);
+// Relative truncation of the hierarchical inverses' blocks.
+double hinv_tolerance(const hm_opts& o);
 
 // ---------------------------------------------------------------- device tables
 

@@ -9,6 +9,8 @@
 //                     every low-rank block covering the rows, then the
 //                     epilogue y = alpha x + beta (H x) + gamma (w1 + w2) + w3.
 // All vectors are in Morton order.  FP64 storage and FP64 accumulation.
+#include <atomic>
+
 #include "hm_device.cuh"
 #include "hm_kernels.h"
 
@@ -78,7 +80,10 @@ __device__ __forceinline__ void rows_body(const MatvecPlan& P, int chunk, double
       for (int r = 0; r < ROWS_PER_WARP; ++r) {
         if (rw0 + r < C.nrow) {
           double2 v = *reinterpret_cast<const double2*>(base + (int64_t)r * D.ld + 2 * p);
-          rsum[r] += v.x * x0 + v.y * x1;
+          // two chained FMAs: one FP64 instruction per matrix entry (the
+          // kernel issues FP64 close to the HBM rate)
+          rsum[r] = fma(v.x, x0, rsum[r]);
+          rsum[r] = fma(v.y, x1, rsum[r]);
         }
       }
     }
@@ -191,17 +196,22 @@ size_t noalloc_capacity() { return NOALLOC_DOUBLES; }
 // Device address of the array for the current device.  In host code the
 // symbol name is only a host-side stand-in, so the address is looked up once
 // per device (with that device current) and cached.
+// The cache slots are atomics: threads that make their first call on a device
+// at the same time each look the address up and store the same value.  The
+// cache assumes the device is not reset while the library is loaded.
 int noalloc_scratch(double** out) {
-  static double* addr[64] = {};
+  static std::atomic<double*> addr[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HM_ERR_CUDA;
-  if (!addr[dev]) {
+  double* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return HM_ERR_CUDA;
-    addr[dev] = static_cast<double*>(p);
+    a = static_cast<double*>(p);
+    addr[dev].store(a, std::memory_order_release);
   }
-  *out = addr[dev];
+  *out = a;
   return HM_OK;
 }
 

@@ -144,12 +144,42 @@ struct Builder {
 
 }  // namespace
 
+int solve_mode(const hm_problem& p, const hm_opts& o) {
+  if (o.solve == HM_SOLVE_SUBST || o.solve == HM_SOLVE_HINV) return o.solve;
+  return (p.dim == 1 && p.domain == HM_DOMAIN_BOX && o.leaf <= 1024) ? HM_SOLVE_HINV : HM_SOLVE_SUBST;
+}
+
+double hinv_tolerance(const hm_opts& o) {
+  if (o.hinv_tol > 0.0) return o.hinv_tol;
+  if (o.precision == HM_MIXED_FP32) return 1e-7;
+  if (o.precision == HM_MIXED_BF16) return 2e-3;
+  return std::min(1e-6, std::max(1e-14, 1e-2 * o.lu_tol));
+}
+
 int make_plan(const hm_problem& p, const hm_opts& o, Plan& P, std::string& err) {
   if (p.dim != 1 && p.dim != 2) { err = "dim must be 1 or 2"; return HM_ERR_ARG; }
   if (p.n[0] < 1 || (p.dim == 2 && p.n[1] < 1)) { err = "n must be positive"; return HM_ERR_ARG; }
   if (o.leaf < 1) { err = "leaf must be >= 1"; return HM_ERR_ARG; }
   if (!(o.eta > 0)) { err = "eta must be > 0"; return HM_ERR_ARG; }
-  if (o.precision != HM_FP64) { err = "only HM_FP64 storage is built"; return HM_ERR_ARG; }
+  if (o.precision != HM_FP64 && o.precision != HM_MIXED_FP32 && o.precision != HM_MIXED_BF16) {
+    err = "precision must be HM_FP64, HM_MIXED_FP32 or HM_MIXED_BF16";
+    return HM_ERR_ARG;
+  }
+  if (o.solve != HM_SOLVE_AUTO && o.solve != HM_SOLVE_SUBST && o.solve != HM_SOLVE_HINV) {
+    err = "unknown solve mode";
+    return HM_ERR_ARG;
+  }
+  if (o.solve_block < 0) { err = "solve_block must be >= 0"; return HM_ERR_ARG; }
+  if (!(o.hinv_tol >= 0.0 && o.hinv_tol < 1.0)) { err = "hinv_tol must lie in [0, 1)"; return HM_ERR_ARG; }
+  const bool hinv_ok = p.dim == 1 && p.domain == HM_DOMAIN_BOX && o.leaf <= 1024;
+  if (o.solve == HM_SOLVE_HINV && !hinv_ok) {
+    err = "HM_SOLVE_HINV needs a 1D problem and leaves of at most 1024 points";
+    return HM_ERR_ARG;
+  }
+  if (o.precision != HM_FP64 && solve_mode(p, o) != HM_SOLVE_HINV) {
+    err = "mixed precision storage is built for the hierarchical-inverse solve (1D problems)";
+    return HM_ERR_ARG;
+  }
   P = Plan();
   P.dim = p.dim;
   P.n[0] = p.n[0];

@@ -17,7 +17,11 @@ LIB_PATH = os.path.join(_PKG, "_build", "liblevyhm.so")
 HM_OK = 0
 HM_ERR_NOT_CONVERGED = -5
 HM_NU_GAUSS, HM_NU_STABLE = 0, 1
-HM_FP64, HM_MIXED_FP32 = 0, 1
+HM_FP64, HM_MIXED_FP32, HM_MIXED_BF16 = 0, 1, 2
+HM_SOLVE_AUTO, HM_SOLVE_SUBST, HM_SOLVE_HINV = 0, 1, 2
+PRECISIONS = {"fp64": HM_FP64, "fp32": HM_MIXED_FP32, "mixed_fp32": HM_MIXED_FP32, "bf16": HM_MIXED_BF16,
+              "mixed_bf16": HM_MIXED_BF16}
+SOLVES = {"auto": HM_SOLVE_AUTO, "subst": HM_SOLVE_SUBST, "hinv": HM_SOLVE_HINV}
 HM_DOMAIN_BOX, HM_DOMAIN_L = 0, 1
 
 EXPORTED = [
@@ -39,7 +43,8 @@ class Problem(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("eta", C.c_double), ("aca_tol", C.c_double),
                 ("max_rank", C.c_int), ("lu_tol", C.c_double), ("lu_max_rank", C.c_int),
-                ("precision", C.c_int), ("refine_tol", C.c_double), ("refine_max", C.c_int)]
+                ("precision", C.c_int), ("refine_tol", C.c_double), ("refine_max", C.c_int),
+                ("solve", C.c_int), ("solve_block", C.c_int), ("hinv_tol", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -50,7 +55,8 @@ class Stats(C.Structure):
                 ("rank_capped_blocks", C.c_int), ("lu_max_rank_seen", C.c_int),
                 ("lu_rank_capped", C.c_int), ("last_refine_iters", C.c_int),
                 ("last_refine_resid", C.c_double), ("device_bytes", C.c_int64),
-                ("factor_fma", C.c_double), ("factor_ms", C.c_double)]
+                ("factor_fma", C.c_double), ("factor_ms", C.c_double), ("solve_mode", C.c_int),
+                ("hinv_max_rank", C.c_int), ("hinv_capped", C.c_int), ("hinv_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,10 +170,13 @@ def make_opts(o: dict) -> Opts:
     s.lu_tol = float(o.get("lu_tol", 1e-10))
     s.lu_max_rank = int(o.get("lu_max_rank", 64))
     prec = o.get("precision", "fp64")
-    s.precision = {"fp64": HM_FP64, "fp32": HM_MIXED_FP32, "mixed_fp32": HM_MIXED_FP32}.get(prec, prec) \
-        if isinstance(prec, str) else int(prec)
+    s.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     s.refine_tol = float(o.get("refine_tol", 1e-13))
     s.refine_max = int(o.get("refine_max", 4))
+    solve = o.get("solve", "auto")
+    s.solve = SOLVES[solve] if isinstance(solve, str) else int(solve)
+    s.solve_block = int(o.get("solve_block", 0))
+    s.hinv_tol = float(o.get("hinv_tol", 0.0))
     return s
 
 

@@ -160,12 +160,44 @@ def test_bad_arguments_are_rejected(lib):
         hmat.plan_info(dict(p, s=1.5), W.default_opts())
 
 
-def test_unbuilt_precision_is_refused():
-    """Only FP64 storage is built: any other precision is an argument error,
-    never a silent FP64 run."""
-    prob = W.frac_lap_1d(255, 0.5)
+def test_precision_and_solve_options_are_checked():
+    """Mixed-precision storage exists for the hierarchical-inverse solve of 1D
+    problems only: elsewhere (2D, or the substitution solve) it is an argument
+    error, never a silent FP64 run; unknown modes and bad tolerances too."""
+    p1 = W.frac_lap_1d(255, 0.5)
+    p2 = W.frac_lap_2d(16, 0.5)
+    for prec in ("mixed_fp32", "mixed_bf16"):
+        hmat.plan_info(p1, W.default_opts(leaf=32, precision=prec))
+        hmat.plan_info(p1, W.default_opts(leaf=32, precision=prec, solve="hinv"))
+        with pytest.raises(hmat.HMError):
+            hmat.plan_info(p1, W.default_opts(leaf=32, precision=prec, solve="subst"))
+        with pytest.raises(hmat.HMError):
+            hmat.plan_info(p2, W.default_opts(leaf=32, precision=prec))
     with pytest.raises(hmat.HMError):
-        hmat.plan_info(prob, W.default_opts(leaf=32, precision="mixed_fp32"))
+        hmat.plan_info(p2, W.default_opts(leaf=32, solve="hinv"))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=2048, solve="hinv"))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=32, precision=7))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=32, solve=9))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=32, hinv_tol=1.5))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=32, solve_block=-1))
+
+
+def test_solve_block_option_changes_the_substitution_plan():
+    """opts.solve_block sets the rows of the substitution solve's blocks: at
+    N = 4095 the default (1024-row blocks) and 2048-row blocks give different
+    schedules, and the larger blocks need fewer dependency waves."""
+    p = W.levy_1d(4095)
+    o = W.default_opts(leaf=128, max_rank=32, lu_max_rank=16, solve="subst")
+    a = hmat.plan_factor(p, o)
+    b = hmat.plan_factor(p, dict(o, solve_block=2048))
+    assert a["bad_spans"] == 0 and b["bad_spans"] == 0
+    assert b["solve_waves"] < a["solve_waves"]
+    assert b["gemm_fma"][1] > a["gemm_fma"][1]  # larger dense inverses of the solve blocks
 
 
 def test_splitmix64_published_outputs_and_batch_stream():
