@@ -36,19 +36,22 @@ constexpr int HINV_RCH = 32;    // rows per row chunk
 constexpr int HINV_TCH = 256;   // rows per chunk of the per-step V'x products
 constexpr int HINV_MCH = 128;   // rows per chunk of the construction's reductions
 
-enum HinvPrec { HINV_F64 = 0, HINV_F32 = 1, HINV_BF16 = 2 };
+// storage of the per-step inverses: FP64; FP32 or BF16 (mixed precision);
+// DF = FP64-accurate pairs of floats (hi + lo) applied in double-float arithmetic
+enum HinvPrec { HINV_F64 = 0, HINV_F32 = 1, HINV_BF16 = 2, HINV_DF = 3 };
+constexpr int HINV_MAX_ANC = 24;  // deepest 1D cluster tree the per-step kernels stage
 
 // ---- per-step application of one triangular inverse (device tables)
-struct HinvLeaf {     // square row-major inverse of a diagonal leaf block
+struct HinvLeaf {     // inverse of a diagonal leaf block: its triangle, column-major, column stride ld
   int r0, m, ld;
   int anc_begin, anc_end;   // inverse blocks whose target rows contain the leaf
   int64_t off;              // into the leaf pool (elements)
 };
 struct HinvNode {     // inverse block P Q^T of an internal cluster
   int tgt0, tgt_n, src0, src_n;
-  int pld, qld;             // column strides of P and Q (multiples of 8 elements)
+  int pld, qld;             // column stride of P (a multiple of 8), row stride of Q (KCAP)
   int tch_begin, tch_end;   // its chunks of the per-step V'x products
-  int64_t poff, qoff;       // col-major P (tgt_n x KCAP), Q (src_n x KCAP) in the pools
+  int64_t poff, qoff;       // column-major P (tgt_n x KCAP), row-major Q (src_n x KCAP) in the pools
 };
 struct HinvApply {
   int lower;                // 1: L^{-1} (leaf rows read j <= i), 0: U^{-1} (j >= i)

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -309,7 +310,8 @@ __global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tb
   }
 }
 
-// P = -R3[tgt rows][:, piv_k] R_11^{-1}, Q = C3[src rows] Q_c,k; col-major, zero beyond k
+// P = -R3[tgt rows][:, piv_k] R_11^{-1} (column-major, column stride ld),
+// Q = C3[src rows] Q_c,k (row-major, row stride ld); zero beyond k
 struct FormJob { int which, core, node_row0, nrow, r_lo; double* dst; int ld; const double* src; int S; };
 __global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Core* cores) {
   const FormJob J = jobs[blockIdx.x];
@@ -329,27 +331,38 @@ __global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Co
         for (int c = 0; c < HINV_SP; ++c) s = fma(x[c], K.qc[c * HINV_KCAP + l], s);
       }
     }
-    J.dst[(int64_t)l * J.ld + i] = s;
+    if (J.which == 0) J.dst[(int64_t)l * J.ld + i] = s;
+    else J.dst[(int64_t)i * J.ld + l] = s;
   }
 }
 
-// leaf inverse -> its triangle in a zero-padded square of row stride ld
+// leaf inverse (row-major, stride sld) -> its triangle, column-major with
+// column stride ld, zeros elsewhere (padding rows included)
 struct LeafCopy { const double* src; int64_t sld; double* dst; int ld, m, lower; };
 __global__ void leaf_copy_kernel(const LeafCopy* jobs) {
   const LeafCopy J = jobs[blockIdx.y];
   const int64_t total = (int64_t)J.m * J.ld;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / J.ld), j = (int)(e % J.ld);
-    const bool keep = j < J.m && (J.lower ? j <= i : j >= i);
+    const int j = (int)(e / J.ld), i = (int)(e % J.ld);
+    const bool keep = i < J.m && (J.lower ? j <= i : j >= i);
     J.dst[e] = keep ? J.src[(int64_t)i * J.sld + j] : 0.0;
   }
 }
 
+// FP64 pools -> the per-step storage: FP32, BF16, or pairs of floats
+// (hi = v rounded to float, lo = the rest rounded to float: 48 bits of v)
 template <class T>
 __global__ void convert_kernel(const double* src, T* dst, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    if constexpr (sizeof(T) == 4) dst[e] = (float)src[e];
-    else dst[e] = __double2bfloat16(src[e]);
+    const double v = src[e];
+    if constexpr (sizeof(T) == 8) {
+      const float hi = __double2float_rn(v);
+      dst[e] = make_float2(hi, __double2float_rn(v - (double)hi));
+    } else if constexpr (sizeof(T) == 4) {
+      dst[e] = (float)v;
+    } else {
+      dst[e] = __double2bfloat16(v);
+    }
   }
 }
 
@@ -455,8 +468,11 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
   if (P.dim != 1) { err = "hierarchical inverses are built for 1D problems only"; return HM_ERR_ARG; }
   if (F.kf > HINV_MAXS) { err = "factor rank cap above 64"; return HM_ERR_ARG; }
   const int N = P.N;
+  // FP64 accuracy: pairs of floats in double-float arithmetic (HM_HINV_FP64=1: FP64 storage and arithmetic)
+  const char* f64 = std::getenv("HM_HINV_FP64");
+  const int aprec = prec == HINV_F64 && !(f64 && f64[0] == '1') ? HINV_DF : prec;
   out = HinvData();
-  out.prec = prec;
+  out.prec = aprec;
   out.tol = tol;
   auto alloc = [&](void** p, size_t bytes) -> int {
     *p = nullptr;
@@ -509,6 +525,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
   // per triangle: target and source cluster of every node
   auto tgt = [&](int tri, const TNode& T) { return tri == 0 ? T.b : T.a; };
   auto src = [&](int tri, const TNode& T) { return tri == 0 ? T.a : T.b; };
+  if (P.depth > HINV_MAX_ANC) { err = "cluster tree deeper than " + std::to_string(HINV_MAX_ANC); return HM_ERR_ARG; }
   // per leaf and triangle: nodes whose target (src) range holds the leaf, from the leaf up
   std::vector<std::vector<int>> anc_t[2], anc_s[2];
   for (int tri = 0; tri < 2; ++tri) {
@@ -585,11 +602,11 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       Nd.src0 = rs.first;
       Nd.src_n = rs.second - rs.first;
       Nd.pld = round8(Nd.tgt_n);
-      Nd.qld = round8(Nd.src_n);
+      Nd.qld = HINV_KCAP;
       Nd.poff = po;
       Nd.qoff = qo;
       po += (int64_t)Nd.pld * HINV_KCAP;
-      qo += (int64_t)Nd.qld * HINV_KCAP;
+      qo += (int64_t)round8(Nd.src_n) * HINV_KCAP;
     }
     p_elems[tri] = po;
     q_elems[tri] = qo;
@@ -677,18 +694,19 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
               if (nodes[q].level <= lev || slot[q] >= 0) continue;
               const HinvNode& Q = H.h_nodes[q];
               slot[q] = trans ? PL.red(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, Q.tgt_n, rk + q, HINV_KCAP)
-                              : PL.red(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, Q.src_n, rk + q, HINV_KCAP);
+                              : PL.red(qpool[tri] + Q.qoff, Q.qld, 1, Q.src0, Q.src_n, rk + q, HINV_KCAP);
             }
             for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
               PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
               const double* X = leafpool[tri] + L.off;
               const int mask = (tri == 0) != trans ? 1 : 2;
-              PL.item(trans ? dense_item(X, 1, L.ld, L.r0, L.r0, L.m, mask)
-                            : dense_item(X, L.ld, 1, L.r0, L.r0, L.m, mask));
+              // the leaf is stored column-major: X(i, j) = X[j ld + i]
+              PL.item(trans ? dense_item(X, L.ld, 1, L.r0, L.r0, L.m, mask)
+                            : dense_item(X, 1, L.ld, L.r0, L.r0, L.m, mask));
               for (int q : anc) {
                 if (nodes[q].level <= lev) continue;
                 const HinvNode& Q = H.h_nodes[q];
-                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, rk + q, HINV_KCAP, slot[q])
+                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, Q.qld, 1, Q.src0, rk + q, HINV_KCAP, slot[q])
                               : lr_item(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, rk + q, HINV_KCAP, slot[q]));
               }
             }
@@ -890,8 +908,8 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     if (s == HM_OK) s = alloc((void**)&A.tcount, sizeof(unsigned) * std::max(nn, 1));
     if (s == HM_OK && cudaMemsetAsync(A.tcount, 0, sizeof(unsigned) * std::max(nn, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
     H.A = A;
-    if (s == HM_OK && prec != HINV_F64) {
-      const size_t es = prec == HINV_F32 ? 4 : 2;
+    if (s == HM_OK && aprec != HINV_F64) {
+      const size_t es = aprec == HINV_DF ? 8 : (aprec == HINV_F32 ? 4 : 2);
       void* pl = nullptr;
       void* pp = nullptr;
       void* pq = nullptr;
@@ -900,7 +918,11 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       if (s == HM_OK) s = alloc(&pq, es * std::max<int64_t>(q_elems[tri], 1));
       if (s == HM_OK) {
         count_launches(3);
-        if (prec == HINV_F32) {
+        if (aprec == HINV_DF) {
+          convert_kernel<float2><<<1216, 256, 0, st>>>(leafpool[tri], (float2*)pl, leaf_elems);
+          convert_kernel<float2><<<1216, 256, 0, st>>>(ppool[tri], (float2*)pp, p_elems[tri]);
+          convert_kernel<float2><<<1216, 256, 0, st>>>(qpool[tri], (float2*)pq, q_elems[tri]);
+        } else if (aprec == HINV_F32) {
           convert_kernel<float><<<1216, 256, 0, st>>>(leafpool[tri], (float*)pl, leaf_elems);
           convert_kernel<float><<<1216, 256, 0, st>>>(ppool[tri], (float*)pp, p_elems[tri]);
           convert_kernel<float><<<1216, 256, 0, st>>>(qpool[tri], (float*)pq, q_elems[tri]);
@@ -909,7 +931,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
           convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(ppool[tri], (__nv_bfloat16*)pp, p_elems[tri]);
           convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(qpool[tri], (__nv_bfloat16*)pq, q_elems[tri]);
         }
-        H.A.prec = prec;
+        H.A.prec = aprec;
         H.A.leaf_pool = pl;
         H.A.p_pool = pp;
         H.A.q_pool = pq;
@@ -927,7 +949,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     if (err.empty()) err = "hierarchical inverse construction failed";
     return s;
   }
-  const size_t es = prec == HINV_F64 ? 8 : (prec == HINV_F32 ? 4 : 2);
+  const size_t es = (aprec == HINV_F64 || aprec == HINV_DF) ? 8 : (aprec == HINV_F32 ? 4 : 2);
   int64_t sb = 0;
   for (int tri = 0; tri < 2; ++tri) {
     HinvTriangle& H = out.tri[tri];
