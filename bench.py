@@ -168,22 +168,35 @@ def cpu_sample_2d(name, budget_n=64):
             "sample": f"dense oracle on the same 2D problem at {budget_n}x{budget_n}: assembly + LU + {steps} CN steps, {t:.2f} s"}
 
 
-def cpu_sample(steps_override=None, budget_s=20.0):
+def cpu_sample(steps_override=None, n=8192, steps=20):
     """The dense oracle, as it stands, on a bounded sample of the workload:
-    the same physics at N = 4095 (h = 2/4096), full dense assembly, dense LU
-    and CN steps; unknown-steps/s over the whole sample."""
-    import numpy as np
+    the same 1D Levy physics at N = 8192 (h = 2/8193): dense assembly, dense
+    LU of I - dt/2 G and `steps` CN steps (identity form, one LU solve per
+    step), each phase timed.  Reports the sample's own unknown-steps/s and,
+    labelled as an extrapolation, the rate at the workload's size (N = 65536,
+    1000 steps) with the phases scaled by their cost laws: assembly N^2, LU
+    N^3, a step N^2 (the oracle itself cannot run there: its host LU stops
+    at 2^32 matrix entries)."""
     from oracle import levy_dense as O
     from paper_1812_08324_gb300 import workloads as W
-    n = 4095
     prob = W.levy_1d(n)
-    _, _, dt, steps, _ = W.WORKLOADS[WORKLOAD]
-    cn = 200 if steps_override is None else min(200, steps_override)
+    _, _, dt, full_steps, _ = W.WORKLOADS[WORKLOAD]
+    cn = steps if steps_override is None else max(1, min(steps, steps_override))
     t0 = time.perf_counter()
     G = O.generator_dense(prob)
+    t1 = time.perf_counter()
     u0 = W.gaussian_u0(prob, 50.0)
-    O.cn_solve(G, u0, dt, cn)
-    t = time.perf_counter() - t0
+    t2 = time.perf_counter()
+    O.cn_solve(G, u0, dt, 0, literal=False)   # assembly of M and its LU
+    t3 = time.perf_counter()
+    O.cn_solve(G, u0, dt, cn, literal=False)  # LU again + cn steps
+    t4 = time.perf_counter()
+    t_asm, t_lu = t1 - t0, t3 - t2
+    t_step = max((t4 - t3) - t_lu, 0.0) / cn
+    sample_s = t_asm + t_lu + cn * t_step
+    sample_rate = n * cn / sample_s
+    big, ratio = 65536, 65536 / n
+    t_big = t_asm * ratio ** 2 + t_lu * ratio ** 3 + full_steps * t_step * ratio ** 2
     cores = os.cpu_count()
     try:
         import threadpoolctl
@@ -191,8 +204,12 @@ def cpu_sample(steps_override=None, budget_s=20.0):
         cores = max((i.get("num_threads", 1) for i in info), default=cores)
     except Exception:
         pass
-    return {"value": n * cn / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"dense oracle on the same 1D Levy workload at N={n} (h=2/{n + 1}): assembly + LU + {cn} CN steps, {t:.2f} s"}
+    return {"value": big * full_steps / t_big, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"dense oracle on the same 1D Levy physics at N={n}: assembly {t_asm:.2f} s, LU {t_lu:.2f} s, "
+                       f"{cn} CN steps at {t_step * 1e3:.1f} ms ({sample_rate:.3g} unknown-steps/s over the sample); "
+                       f"value = extrapolation to N={big}, {full_steps} steps (assembly x{ratio ** 2:.0f}, "
+                       f"LU x{ratio ** 3:.0f}, steps x{ratio ** 2:.0f}): {t_big:.0f} s"),
+            "sample_value": sample_rate, "extrapolated": True}
 
 
 def run_reference(args):
@@ -212,7 +229,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample N=4095)"},
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample N=8192, extrapolated)"},
             "cpu_baseline": dict(last, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -623,11 +640,14 @@ def main():
     H.sync()
     ms, value = aggregate(ms, N * cn_steps, world, "cuda")
 
-    # ---- accuracy of the timed configuration: the same CN run with three FP64
-    # refinement sweeps per step (solves converged to the FP64 H system) as reference
+    # ---- accuracy of the timed configuration: (1) the same CN run with three
+    # FP64 refinement sweeps per step (solves converged to the FP64 H system);
+    # (2) against the dense FP64 oracle: the same physics and options at
+    # N = 32768 (the largest grid whose dense LU the host reaches), u after
+    # 1000 steps stored by tests/golden/make_levy1d_golden.py
     assert torch.isfinite(u).all().item()
     u_ref = torch.empty_like(u0)
-    Href = hmat.HMatrix(prob, dict(opts, refine_max=3))
+    Href = hmat.HMatrix(prob, dict(opts, refine_max=3, precision="fp64"))
     Fref = Href.factor(-0.5 * dt)
     u_ref.copy_(u0)
     hmat.cn_solve(Href, Fref, dt, cn_steps, u_ref)
@@ -635,6 +655,19 @@ def main():
     rel_err = float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref))
     Fref.free()
     Href.free()
+    oracle_err = None
+    gold = os.path.join(ROOT, "tests", "golden", "levy1d_n32768_dt1e-3.npz")
+    if name == WORKLOAD and cn_steps == 1000 and os.path.exists(gold):
+        g = np.load(gold)
+        p32 = W.levy_1d(32768)
+        H32 = hmat.HMatrix(p32, opts)
+        F32 = H32.factor(-0.5 * dt)
+        u32 = torch.tensor(W.gaussian_u0(p32, 50.0), dtype=torch.float64, device="cuda")
+        hmat.cn_solve(H32, F32, dt, 1000, u32)
+        got = u32.cpu().numpy()
+        oracle_err = float(np.linalg.norm(got - g["u1000"]) / np.linalg.norm(g["u1000"]))
+        F32.free()
+        H32.free()
 
     # ---- end to end through the public API from pinned host memory
     out_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -649,7 +682,12 @@ def main():
     e2e = {"value": world * N * cn_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
            "d2h_bytes_per_step": 8 * N}
 
-    # ---- roofline of the dominant kernel and of the H-matvec
+    # ---- rooflines.  Per CN step: the H-matvec (three launches) and the two
+    # triangular solves (hierarchical inverses: four launches; substitution:
+    # one executor launch), timed with CUDA events on the launching stream;
+    # per bench step: the H-LU executor (device time of its launches, CUDA
+    # events inside the library).  The `roofline` object is the kernel with
+    # the largest time per bench step.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -659,59 +697,72 @@ def main():
     peak_src = "of measured" if peaks else "of fallback"
     x = torch.tensor(W.initial_data(prob, kind), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
-    for _ in range(3):
-        H.matvec(x, alpha=1.0, beta=0.5 * dt, out=y)
-    reps = 50
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a0.record(stream)
-    for _ in range(reps):
-        H.matvec(x, alpha=1.0, beta=0.5 * dt, out=y)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    mv_ms = a0.elapsed_time(a1) / reps
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e_a.record(stream)
+        for _ in range(reps):
+            fn()
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        return e_a.elapsed_time(e_b) / reps
+
+    mv_ms = timed(lambda: H.matvec(x, alpha=1.0, beta=0.5 * dt, out=y), 50)
+    sv_ms = timed(lambda: F.solve(x, out=y), 50)
     mv_gbs = st["h_bytes"] / (mv_ms * 1e-3) / 1e9
-    # the triangular-solve schedule dominates a CN step: bytes of the factors per solve
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(2):
-        F.solve(x, out=y)
-    torch.cuda.synchronize()
-    s0.record(stream)
-    for _ in range(10):
-        F.solve(x, out=y)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    sv_ms = s0.elapsed_time(s1) / 10
     sv_gbs = st["lu_bytes"] / (sv_ms * 1e-3) / 1e9
-    # DRAM traffic of one solve launch from an ncu capture of the same kernel at
-    # N = 32768 (2048-row solve blocks as here; dram__bytes_read.sum +
-    # dram__bytes_write.sum = 786.7 MB against lu_bytes = 393.6 MB there), scaled
-    # to this launch by its factor bytes (traffic grows in proportion to N in 1D)
-    roofline = {"kernel": "exec_kernel (H-triangular solve schedule)", "bound": "hbm",
-                "achieved": sv_gbs, "peak": hbm, "unit": "GB/s", "frac": sv_gbs / hbm,
-                "traffic": st["lu_bytes"] * 786.7 / 393.6 if prob["dim"] == 1 else None,
-                "traffic_source": "ncu at N=32768, scaled by lu_bytes" if prob["dim"] == 1 else None,
-                "peak_source": f"hbm_gbs {peak_src}", "algorithmic_bytes": st["lu_bytes"], "ms": sv_ms}
+    hinv = st["solve_mode"] == 2
+    sweeps = opts["refine_max"]
+    n_mv = cn_steps * (1 if sweeps == 0 else sweeps)
+    n_sv = cn_steps * (1 + sweeps)
     mv_roof = {"kernel": "H-matvec (vt_kernel + vt_reduce + rows_kernel)", "bound": "hbm", "achieved": mv_gbs,
                "peak": hbm, "unit": "GB/s", "frac": mv_gbs / hbm, "traffic": None,
-               "algorithmic_bytes": st["h_bytes"], "ms": mv_ms, "peak_source": f"hbm_gbs {peak_src}"}
+               "algorithmic_bytes": st["h_bytes"], "ms": mv_ms, "per_bench_step_ms": n_mv * mv_ms,
+               "peak_source": f"hbm_gbs {peak_src}"}
+    sv_roof = {"kernel": ("hierarchical-inverse products (hinv_t_kernel + hinv_r_kernel, L^-1 then U^-1)" if hinv
+                          else "exec_kernel<1> (H-triangular solve schedule)"),
+               "bound": "hbm", "achieved": sv_gbs, "peak": hbm, "unit": "GB/s", "frac": sv_gbs / hbm,
+               "traffic": None, "algorithmic_bytes": st["lu_bytes"], "ms": sv_ms, "per_bench_step_ms": n_sv * sv_ms,
+               "peak_source": f"hbm_gbs {peak_src}"}
+    # the H-LU's GEMM tiles compute in double-float arithmetic on the FP32 pipes:
+    # 10 FP32 instructions per FP64-equivalent multiply-add, so the ALU peak is
+    # 128 FP32 lanes x SMs x clock / 10 multiply-adds (2 flop each)
+    sm_mhz = (clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    df_peak = 2.0 * 128 * 152 * sm_mhz * 1e6 / 10.0 / 1e12
+    lu_tf = 2.0 * st["factor_fma"] / (st["factor_ms"] * 1e-3) / 1e12 if st["factor_ms"] > 0 else 0.0
+    lu_roof = {"kernel": "exec_kernel<0> (H-LU dataflow executor, double-float GEMM tiles)", "bound": "alu",
+               "achieved": lu_tf, "peak": df_peak, "unit": "TFLOP/s", "frac": lu_tf / df_peak, "traffic": None,
+               "algorithmic_flops": 2.0 * st["factor_fma"], "ms": st["factor_ms"], "per_bench_step_ms": st["factor_ms"],
+               "peak_source": "derived: 128 FP32 lanes x 152 SMs x max SM clock / 10 instructions per double-float FMA",
+               "note": "latency-bound: the planned critical path (chain of diagonal leaf LUs) is about the measured time"}
+    parts = [lu_roof, mv_roof, sv_roof]
+    roofline = max(parts, key=lambda r: r["per_bench_step_ms"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_bf16": "f64+bf16"}[opts["precision"]],
+            "data": "synthetic",
             "config": {"workload": name, "N": N, "cn_steps": cn_steps, "dt": dt, "leaf": opts["leaf"],
                        "aca_tol": opts["aca_tol"], "max_rank": opts["max_rank"],
                        "lu_max_rank": opts["lu_max_rank"], "refine_sweeps": opts["refine_max"],
+                       "precision": opts["precision"], "solve": opts["solve"],
                        "parallelism": f"replicas x{world}",
                        "l2": f"working set (H + factors, {(st['h_bytes'] + st['lu_bytes']) / 1e9:.1f} GB) "
                              "exceeds L2; no flush needed"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "matvec_roofline": mv_roof,
-            "accuracy": {"rel_l2_vs_converged_fp64_solves": rel_err,
-                         "reference": "same H-matrix CN run with 3 FP64 refinement sweeps per step",
-                         "vs_dense_oracle": "tests/test_gpu_hlu.py at N <= 2047 (1e-8)"},
+            "solve_roofline": sv_roof, "matvec_roofline": mv_roof, "factor_roofline": lu_roof,
+            "accuracy": {"rel_l2_vs_dense_fp64_oracle_n32768": oracle_err,
+                         "oracle_reference": "dense FP64 oracle (assembly + dense LU + 1000 CN steps) at N=32768, "
+                                             "same physics, options and steps (tests/golden/levy1d_n32768_dt1e-3.npz)",
+                         "rel_l2_vs_converged_fp64_solves": rel_err,
+                         "reference": "same H-matrix CN run at N=65536 with 3 FP64 refinement sweeps per step"},
             "stats": {k: st[k] for k in ("h_bytes", "lu_bytes", "max_rank_seen", "lu_max_rank_seen",
-                                         "dense_blocks", "lowrank_blocks", "last_refine_resid")}}
+                                         "dense_blocks", "lowrank_blocks", "last_refine_resid", "solve_mode",
+                                         "hinv_max_rank", "hinv_capped", "hinv_ms", "factor_ms", "factor_fma",
+                                         "device_bytes")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample() if prob["dim"] == 1 else cpu_sample_2d(name)
     if rank == 0:

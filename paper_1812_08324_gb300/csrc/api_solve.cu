@@ -174,33 +174,64 @@ int solve_morton(const hm_factors* F, const double* b, double* z, cudaStream_t s
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
+// w = 2 u + theta (f0 + f1)   (f0, f1 may be null)
+__global__ void cn_w_kernel(int N, const double* u, double th, const double* f0, const double* f1, double* w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double v = 2.0 * u[i];
+    if (f0 || f1) v += th * ((f0 ? f0[i] : 0.0) + (f1 ? f1[i] : 0.0));
+    w[i] = v;
+  }
+}
+
+// y = y - x
+__global__ void sub_kernel(int N, const double* x, double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) y[i] = y[i] - x[i];
+}
+
 // One CN step on Morton-order vectors: u1 = CN(u0) with forcing f0, f1 (may be null).
+//  refine_max = 0: rhs = u + theta G u + theta (f^n + f^{n+1}) by the H-matvec,
+//                  u1 = (LU)^{-1} rhs (Eq. scheme as written).
+//  refine_max = R > 0: with w = 2u + theta (f^n + f^{n+1}) the scheme reads
+//                  M v = w for v = u^n + u^{n+1}, M = I - theta G (because
+//                  I + theta G = 2I - M): v = (LU)^{-1} w, then R sweeps
+//                  v += (LU)^{-1} (w - M v) with the FP64 H-matvec residual
+//                  (the H-LU as preconditioner), and u1 = v - u.  One H-matvec
+//                  per sweep: the cheap (e.g. low-precision) solve carries
+//                  the step and the FP64 residual sets its accuracy.
 int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u0,
                    const double* f0, const double* f1, double* u1, cudaStream_t st) {
   const int N = H->plan.N;
   const double th = 0.5 * dt;
   double* rhs = F->d_vec;
   double* s = F->d_vec + (size_t)N;
-  // rhs = u + theta G u + theta (f^n + f^{n+1})
-  HM_TRY(hm_matvec_morton(H, 1.0, th, u0, th, f0, f1, nullptr, rhs, st));
-  HM_TRY(solve_morton(F, rhs, u1, st));
   const int sweeps = H->opts.refine_max;
+  if (sweeps == 0) {
+    HM_TRY(hm_matvec_morton(H, 1.0, th, u0, th, f0, f1, nullptr, rhs, st));
+    return solve_morton(F, rhs, u1, st);
+  }
+  double* w = rhs;
+  count_launches(1);
+  cn_w_kernel<<<vgrid(N), 256, 0, st>>>(N, u0, th, f0, f1, w);
+  HM_TRY(solve_morton(F, w, u1, st));  // v, kept in u1
   for (int it = 0; it < sweeps; ++it) {
-    // s = rhs - (z - theta G z)
-    HM_TRY(hm_matvec_morton(H, -1.0, th, u1, 0.0, nullptr, nullptr, rhs, s, st));
+    // s = w - (v - theta G v)
+    HM_TRY(hm_matvec_morton(H, -1.0, th, u1, 0.0, nullptr, nullptr, w, s, st));
     if (it == sweeps - 1) {
       count_launches(1);
-      norms_kernel<<<1, 1024, 0, st>>>(N, s, rhs, F->d_norm);
+      norms_kernel<<<1, 1024, 0, st>>>(N, s, w, F->d_norm);
     }
     HM_TRY(solve_morton(F, s, s, st));
     count_launches(1);
     axpy_kernel<<<vgrid(N), 256, 0, st>>>(N, 1.0, s, u1);
   }
+  count_launches(1);
+  sub_kernel<<<vgrid(N), 256, 0, st>>>(N, u0, u1);  // u1 = v - u0
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
-// ---- batched vector operations: y = x (mode 0) or y += a x (mode 1) for many
-// vectors in one launch, 2048 elements per CTA
+// ---- batched vector operations: y = x (mode 0), y += a x (mode 1), y = 2 x
+// (mode 2) or y = x - y (mode 3) for many vectors in one launch, 2048 elements
+// per CTA
 
 struct VecJob {
   const double* x;
@@ -227,8 +258,12 @@ __global__ void vec_batch_kernel(const VecJob* jobs, const int* off, int count) 
   const int i0 = (blockIdx.x - off[j]) * VEC_CHUNK, i1 = min(J.n, i0 + VEC_CHUNK);
   if (J.mode == 0) {
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] = J.x[i];
-  } else {
+  } else if (J.mode == 1) {
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] += J.a * J.x[i];
+  } else if (J.mode == 2) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] = 2.0 * J.x[i];
+  } else {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) J.y[i] = J.x[i] - J.y[i];
   }
 }
 
@@ -418,7 +453,7 @@ struct hm_batch {
   DevSchedule sched;           // merged substitution schedule of the HM_SOLVE_SUBST problems
   hm::HinvBatch hL, hU;        // the HM_SOLVE_HINV problems: L^{-1}, then U^{-1} of every one
   hm::MvBatch A{}, B{};
-  hm::DevJobs<hm::VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out;
+  hm::DevJobs<hm::VecJob> rhs_in, w_in, s_in, z_out, z_u1, u1_add, u1_out;
   std::vector<void*> allocs;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev = nullptr;
@@ -441,10 +476,16 @@ int batch_solve(hm_batch* B, cudaStream_t cs) {
 }
 
 int batch_one_step(hm_batch* B, cudaStream_t cs) {
-  HM_TRY(launch_matvec_batch(B->A, cs));
-  HM_TRY(launch_vec_batch(B->rhs_in, cs));
+  if (B->refine == 0) {
+    HM_TRY(launch_matvec_batch(B->A, cs));
+    HM_TRY(launch_vec_batch(B->rhs_in, cs));
+    HM_TRY(batch_solve(B, cs));
+    return launch_vec_batch(B->z_out, cs);
+  }
+  // w = 2 x (kept in rhs and given to the solve), v = (LU)^{-1} w in u1,
+  // sweeps v += (LU)^{-1} (w - M v), x = v - x (as cn_step_morton)
+  HM_TRY(launch_vec_batch(B->w_in, cs));
   HM_TRY(batch_solve(B, cs));
-  if (B->refine == 0) return launch_vec_batch(B->z_out, cs);
   HM_TRY(launch_vec_batch(B->z_u1, cs));
   for (int it = 0; it < B->refine; ++it) {
     HM_TRY(launch_matvec_batch(B->B, cs));
@@ -946,7 +987,7 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   // per problem: Morton-order state x (owned by the batch), rhs, residual,
   // refined iterate, solve output z
   std::vector<MvJob> jA(count), jB(count);
-  std::vector<VecJob> rhs_in, s_in, z_out, z_u1, u1_add, u1_out;
+  std::vector<VecJob> rhs_in, w_in, s_in, z_out, z_u1, u1_add, u1_out;
   for (int i = 0; i < count; ++i) {
     const hm_matrix* H = Hs[i];
     hm_factors* F = const_cast<hm_factors*>(Fs[i]);
@@ -961,16 +1002,19 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
     jA[i] = MvJob{H->mv, 1.0, th, th, x, nullptr, nullptr, nullptr, rhs};   // rhs = x + th G x
     jB[i] = MvJob{H->mv, -1.0, th, 0.0, u1, nullptr, nullptr, rhs, res};    // res = rhs - (u1 - th G u1)
     rhs_in.push_back({rhs, F->d_y, 0.0, N, 0});
+    w_in.push_back({x, rhs, 0.0, N, 2});      // w = 2 x
+    w_in.push_back({x, F->d_y, 0.0, N, 2});   // the solve's input
     s_in.push_back({res, F->d_y, 0.0, N, 0});
     z_out.push_back({z, x, 0.0, N, 0});
     z_u1.push_back({z, u1, 0.0, N, 0});
     u1_add.push_back({z, u1, 1.0, N, 1});
-    u1_out.push_back({u1, x, 0.0, N, 0});
+    u1_out.push_back({u1, x, 0.0, N, 3});     // x = v - x
   }
   auto vblocks = [](const VecJob& J) { return (J.n + VEC_CHUNK - 1) / VEC_CHUNK; };
   if ((s = upload_mv_batch(jA, B->A, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_mv_batch(jB, B->B, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(rhs_in, vblocks, B->rhs_in, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(w_in, vblocks, B->w_in, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(s_in, vblocks, B->s_in, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(z_out, vblocks, B->z_out, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(z_u1, vblocks, B->z_u1, B->allocs)) != HM_OK) return fail(s);

@@ -6,9 +6,10 @@ workload descriptions).  Each output file ``levy1d_n{N}_dt1e-3.npz`` holds
 arrays ``u{k}`` = u at level k in natural grid order.
 
     python tests/golden/make_levy1d_golden.py 32768 20,1000
-    python tests/golden/make_levy1d_golden.py 65536 1000
 
-N = 65536 holds one 34 GB array and runs for about an hour on 8 cores.
+N = 32768 holds one 8.6 GB array and runs for about 20 minutes on 8 cores.
+The workload's own N = 65536 (a 34 GB array) is out of reach: the host
+LAPACK's LU fails on matrices of more than 2^32 entries.
 """
 import os
 import sys
