@@ -11,7 +11,8 @@
 // factor blocks between the children.  With the core G = Psi^T R3 and its
 // column-pivoted QR  G Pi = Q_c R  truncated at the first |R_kk| <= tol |R_00|,
 //     W ~ -(R3 Pi_k R_11^{-1}) (C3 Q_c,k)^T        (generalised Nystrom).
-// All arithmetic is FP64.  Products are "multi-vector" kernels: a reduction
+// FP64 values; the products run in double-float arithmetic (below).
+// Products are "multi-vector" kernels: a reduction
 // T = V^T IN for every low-rank piece (chunks of 128 rows, the last CTA of a
 // piece sums the chunks in order) and a row kernel summing, per 32-row chunk,
 // its dense pieces (optionally one triangle) and its low-rank pieces U T.
@@ -189,6 +190,168 @@ __global__ void __launch_bounds__(256) mr_row_kernel(MrPlan P, const double* __r
     for (int q = 0; q < 8; ++q) {
       const int c = g + 8 * q;
       if (c < S) out[(int64_t)row * S + c] = acc[q];
+    }
+  }
+}
+
+// ---- the same two products in double-float arithmetic on the FP32 pipes
+// (FP64 runs at about two multiply-adds per clock per SM on this GPU): every
+// FP64 operand is split into a float pair with integer operations (df_split),
+// the vectors' rows are split once per CTA into shared memory, products and
+// sums as Dekker / Knuth (about 48 significant bits, far below the sketches'
+// truncation tolerances).  HM_HINV_BUILD_FP64=1 selects the FP64 kernels.
+__device__ __forceinline__ void dd_mac(float2& s, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float t = __fadd_rn(s.x, p);
+  const float bb = __fsub_rn(t, s.x);
+  const float r = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  s.x = t;
+  s.y = __fadd_rn(s.y, __fadd_rn(r, e));
+}
+
+constexpr int DD_JB = 32;  // rows of the input staged per block
+
+__global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* __restrict__ in) {
+  __shared__ float2 xs[DD_JB][HINV_MAXS];
+  __shared__ int last;
+  const int2 rc = P.rch[blockIdx.x];
+  const MrRed R = P.reds[rc.x];
+  const int k = R.rank ? *R.rank : R.kc;
+  const int S = P.S;
+  const int j0 = rc.y, len = min(HINV_MCH, R.n - j0);
+  const int g = threadIdx.x & 7, lg = threadIdx.x >> 3;
+  const float2 z = make_float2(0.f, 0.f);
+  float2 acc[2][8];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[a][q] = z;
+  const bool l0 = lg < k, l1 = lg + 32 < k;
+  bool bad = false;
+  for (int jb = 0; jb < len; jb += DD_JB) {
+    const int nb = min(DD_JB, len - jb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * S; e += blockDim.x) {
+      const int r = e / S, c = e % S;
+      xs[r][c] = df_split(in[(int64_t)(R.in0 + j0 + jb + r) * S + c], bad);
+    }
+    __syncthreads();
+    if (l0) {
+      for (int j = 0; j < nb; ++j) {
+        const int64_t jj = j0 + jb + j;
+        const float2 v0 = df_split(R.V[jj * R.vrs + (int64_t)lg * R.vcs], bad);
+        const float2 v1 = l1 ? df_split(R.V[jj * R.vrs + (int64_t)(lg + 32) * R.vcs], bad) : z;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = g + 8 * q;
+          if (c < S) {
+            dd_mac(acc[0][q], v0, xs[j][c]);
+            if (l1) dd_mac(acc[1][q], v1, xs[j][c]);
+          }
+        }
+      }
+    }
+  }
+  double* part = P.partial + (int64_t)blockIdx.x * MR_T;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = g + 8 * q;
+    if (c < S) {
+      if (l0) part[lg * S + c] = (double)acc[0][q].x + (double)acc[0][q].y;
+      if (l1) part[(lg + 32) * S + c] = (double)acc[1][q].x + (double)acc[1][q].y;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(P.count + rc.x, 1u) == (unsigned)(R.c_end - R.c_begin - 1) ? 1 : 0;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double* T = P.tbuf + (int64_t)rc.x * MR_T;
+  for (int e = threadIdx.x; e < k * S; e += blockDim.x) {
+    double s = 0.0;
+    for (int cc = R.c_begin; cc < R.c_end; ++cc) s += __ldcg(P.partial + (int64_t)cc * MR_T + e);
+    T[e] = s;
+  }
+  if (threadIdx.x == 0) P.count[rc.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* __restrict__ in,
+                                                         double* __restrict__ out) {
+  constexpr int JB = 64;
+  __shared__ float2 xs[JB][HINV_MAXS];
+  const MrChunk C = P.chunks[blockIdx.x];
+  const int S = P.S;
+  const int g = threadIdx.x & 7, r = threadIdx.x >> 3;
+  const int row = C.r0 + r;
+  const bool live = r < C.nr;
+  const float2 z = make_float2(0.f, 0.f);
+  float2 acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = z;
+  bool bad = false;
+  for (int it = C.ib; it < C.ie; ++it) {
+    const MrItem I = P.items[it];
+    const int i = row - I.row0;
+    if (I.kind == 0) {
+      int jlo = 0, jhi = I.ncol;
+      const int ifirst = C.r0 - I.row0, ilast = C.r0 + C.nr - 1 - I.row0;
+      if (I.mask == 1) jhi = min(jhi, ilast + 1);
+      if (I.mask == 2) jlo = max(0, ifirst);
+      const double* arow = I.A + (int64_t)i * I.rs;
+      for (int jb = jlo; jb < jhi; jb += JB) {
+        const int nb = min(JB, jhi - jb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * S; e += blockDim.x) {
+          const int rr = e / S, c = e % S;
+          xs[rr][c] = df_split(in[(int64_t)(I.col0 + jb + rr) * S + c], bad);
+        }
+        __syncthreads();
+        if (live) {
+          for (int j = jb; j < jb + nb; ++j) {
+            const bool keep = !((I.mask == 1 && j > i) || (I.mask == 2 && j < i));
+            const float2 a = keep ? df_split(arow[(int64_t)j * I.cs], bad) : z;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int c = g + 8 * q;
+              if (c < S) dd_mac(acc[q], a, xs[j - jb][c]);
+            }
+          }
+        }
+      }
+    } else {
+      const int k = I.rank ? *I.rank : I.kc;
+      const double* T = P.tbuf + (int64_t)I.slot * MR_T;
+      const double* urow = I.A + (int64_t)i * I.rs;
+      for (int lb = 0; lb < k; lb += JB) {
+        const int nb = min(JB, k - lb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * S; e += blockDim.x) {
+          const int rr = e / S, c = e % S;
+          xs[rr][c] = df_split(T[(lb + rr) * S + c], bad);
+        }
+        __syncthreads();
+        if (live) {
+          for (int l = lb; l < lb + nb; ++l) {
+            const float2 u = df_split(urow[(int64_t)l * I.cs], bad);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int c = g + 8 * q;
+              if (c < S) dd_mac(acc[q], u, xs[l - lb][c]);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = g + 8 * q;
+      if (c < S) out[(int64_t)row * S + c] = (double)acc[q].x + (double)acc[q].y;
     }
   }
 }
@@ -837,16 +1000,20 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     }
   }
   if (s != HM_OK) { free_tmp(); return s; }
+  const char* b64 = std::getenv("HM_HINV_BUILD_FP64");  // FP64 products in the construction (checks)
+  const bool build_fp64 = b64 && b64[0] == '1';
   auto run_mr = [&](const HostMr& h, const double* in, double* o) {
     MrPlan M{d_reds + h.red0, d_rch + h.rch0, h.nrch, d_chunks + h.ch0, h.nch, d_items + h.it0,
              d_partial, d_tbuf, d_count, h.S};
     if (h.nrch > 0) {
       count_launches(1);
-      mr_red_kernel<<<h.nrch, 256, 0, st>>>(M, in);
+      if (build_fp64) mr_red_kernel<<<h.nrch, 256, 0, st>>>(M, in);
+      else mr_red_dd_kernel<<<h.nrch, 256, 0, st>>>(M, in);
     }
     if (h.nch > 0 && o) {
       count_launches(1);
-      mr_row_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
+      if (build_fp64) mr_row_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
+      else mr_row_dd_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
     }
   };
   for (size_t k = 0; k < steps.size(); ++k) {

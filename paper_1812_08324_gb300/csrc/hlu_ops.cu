@@ -15,35 +15,6 @@ namespace {
 
 constexpr int GK = 16;   // GEMM k chunk
 
-// Double-float split of an FP64 operand, integer operations only (no FP64
-// instruction, which this GPU issues at 1/64 of the FP32 rate): hi is the
-// significand rounded to nearest at 24 bits (an integer add on the float's bit
-// pattern carries into the exponent), lo the signed remainder, 29 bits rounded
-// to 24, so a = hi + lo + r with |r| <= 2^-49 |a|.  |a| < 2^-126 is flushed
-// to zero and the low part of |a| < 2^-74 is dropped (absolute error below
-// 2^-74); |a| >= 2^128 (after rounding), inf and NaN set `bad`.
-__device__ __forceinline__ float2 df_split(double a, bool& bad) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
-  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
-  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
-  if (e < -126) return make_float2(0.f, 0.f);
-  if (e > 127) {
-    bad = true;
-    return make_float2(0.f, 0.f);
-  }
-  const unsigned sgn = hw & 0x80000000u;
-  const unsigned r = lw & 0x1fffffffu;  // the 29 bits below hi's last, in units of 2^(e-52)
-  const unsigned up = r >> 28;          // round half up on the magnitude
-  const unsigned hb = (((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29)) + up;
-  if ((hb >> 23) >= 255u) {
-    bad = true;
-    return make_float2(0.f, 0.f);
-  }
-  float lo = 0.f;
-  if (e >= -74) lo = __fmul_rn(__int2float_rn((int)r - (int)(up << 29)), __int_as_float((e - 52 + 127) << 23));
-  return make_float2(__uint_as_float(sgn | hb), sgn ? -lo : lo);
-}
-
 // (sh, sl) += a b for double-float a, b: the product's high part exactly
 // (FMA), the cross terms rounded (the lo lo term, below 2^-48, is dropped),
 // the sum by Knuth's two-sum.  __f*_rn keep the compiler from contracting or
@@ -301,6 +272,142 @@ __device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
     const int i = e / m, j = e % m;
     op.Li[i * op.ldl + j] = S.XL[i][j];
     op.Ui[i * op.ldu + j] = S.XU[i][j];
+  }
+  __syncthreads();
+}
+
+// ---- the same base LU in double-float arithmetic on the FP32 pipes (the
+// helpers in hm_device.cuh).  The diagonal leaf LUs are sequential along the
+// diagonal (each waits for the one before it), and FP64 on this GPU costs 64
+// cycles per dependent instruction and a division hundreds; unevaluated float
+// pairs (about 48 significant bits, as the GEMM tiles) keep a pivot step to a
+// few dozen cycles (1D N = 65536: executor 220.9 -> 216.5 ms; HM_LU_FP64=1
+// selects the FP64 version).
+struct LuSmemDD {
+  float2 (*A)[LB + 1];
+  float2 (*XL)[LB + 1];
+  float2 (*XU)[LB + 1];
+  float2* TL;
+  float2* TU;
+  float2* rd;
+  float2* rp;
+};
+
+__device__ __forceinline__ LuSmemDD lu_smem_dd(double* smem) {
+  float2* f = reinterpret_cast<float2*>(smem);  // the FP64 layout, one float pair per double
+  LuSmemDD S;
+  S.A = reinterpret_cast<float2 (*)[LB + 1]>(f);
+  S.XL = reinterpret_cast<float2 (*)[LB + 1]>(f + LB * (LB + 1));
+  S.XU = reinterpret_cast<float2 (*)[LB + 1]>(f + 2 * LB * (LB + 1));
+  S.TL = f + 3 * LB * (LB + 1);
+  S.TU = S.TL + 512;
+  S.rd = S.TU + 512;
+  S.rp = S.rd + LB;
+  return S;
+}
+
+__device__ void lu_inv_double_dd(const LuSmemDD& S, int s) {
+  const int np = LB / (2 * s), per = np * s * s, t = threadIdx.x;
+  const float2 z = make_float2(0.f, 0.f);
+  for (int e = t; e < 2 * per; e += blockDim.x) {
+    const int f = e / per, r = e % per, pr = r / (s * s), i = (r % (s * s)) / s, j = r % s, b = pr * 2 * s;
+    float2 acc = z;
+    if (f == 0) {
+      for (int k = 0; k < s; ++k) acc = dd_add(acc, dd_mul(S.A[b + s + i][b + k], S.XL[b + k][b + j]));
+      S.TL[r] = acc;
+    } else {
+      for (int k = 0; k < s; ++k) acc = dd_add(acc, dd_mul(S.A[b + i][b + s + k], S.XU[b + s + k][b + s + j]));
+      S.TU[r] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < 2 * per; e += blockDim.x) {
+    const int f = e / per, r = e % per, pr = r / (s * s), i = (r % (s * s)) / s, j = r % s, b = pr * 2 * s;
+    const float2* T = (f == 0 ? S.TL : S.TU) + pr * s * s;
+    float2 acc = z;
+    if (f == 0) {
+      for (int k = 0; k < s; ++k) acc = dd_add(acc, dd_mul(S.XL[b + s + i][b + s + k], T[k * s + j]));
+      S.XL[b + s + i][b + j] = dd_neg(acc);
+    } else {
+      for (int k = 0; k < s; ++k) acc = dd_add(acc, dd_mul(S.XU[b + i][b + k], T[k * s + j]));
+      S.XU[b + i][b + s + j] = dd_neg(acc);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void dev_lu_base_dd(const LuOp& op, int* err, double* smem) {
+  const LuSmemDD S = lu_smem_dd(smem);
+  const int m = op.m, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const float2 z = make_float2(0.f, 0.f);
+  bool bad = false;
+  for (int e = t; e < LB * LB; e += blockDim.x) {
+    const int i = e / LB, j = e % LB;
+    S.A[i][j] = (i < m && j < m) ? df_split(op.A[i * op.lda + j], bad) : make_float2(i == j ? 1.f : 0.f, 0.f);
+    S.XL[i][j] = z;
+    S.XU[i][j] = z;
+  }
+  if (bad) atomicOr(err, DEVERR_NONFINITE);
+  __syncthreads();
+  auto recip = [&](float2 piv) {
+    if (piv.x == 0.f || !isfinite(piv.x)) {
+      atomicOr(err, DEVERR_ZEROPIVOT);
+      piv = make_float2(1e-30f, 0.f);
+    }
+    return dd_recip(piv);
+  };
+  if (t == 0) S.rp[0] = recip(S.A[0][0]);
+  __syncthreads();
+  for (int p = 0; p < m; ++p) {
+    const float2 rp = S.rp[0];
+    for (int i = p + 1 + t; i < m; i += blockDim.x) S.A[i][p] = dd_mul(S.A[i][p], rp);
+    __syncthreads();
+    const int w = m - p - 1;
+    if (warp == 0) {
+      if (lane == 0 && w > 0) {
+        const float2 v = dd_fnms(S.A[p + 1][p + 1], S.A[p + 1][p], S.A[p][p + 1]);
+        S.A[p + 1][p + 1] = v;
+        S.rp[0] = recip(v);
+      }
+    } else {
+      for (int e = t - 32; e < w * w; e += blockDim.x - 32) {
+        if (e == 0) continue;
+        const int i = p + 1 + e / w, j = p + 1 + e % w;
+        S.A[i][j] = dd_fnms(S.A[i][j], S.A[i][p], S.A[p][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 1) {
+    const float2 d = S.A[lane][lane];
+    S.rd[lane] = dd_recip(d.x == 0.f ? make_float2(1e-30f, 0.f) : d);
+  }
+  __syncwarp();
+  if (warp == 0) {
+    const int b = (lane >> 3) * 8, j = lane & 7;
+    S.XL[b + j][b + j] = make_float2(1.f, 0.f);
+    for (int i = j + 1; i < 8; ++i) {
+      float2 v = z;
+      for (int k = j; k < i; ++k) v = dd_fnms(v, S.A[b + i][b + k], S.XL[b + k][b + j]);
+      S.XL[b + i][b + j] = v;
+    }
+  } else if (warp == 1) {
+    const int b = (lane >> 3) * 8, j = lane & 7;
+    S.XU[b + j][b + j] = S.rd[b + j];
+    for (int i = j - 1; i >= 0; --i) {
+      float2 v = z;
+      for (int k = i + 1; k <= j; ++k) v = dd_add(v, dd_mul(S.A[b + i][b + k], S.XU[b + k][b + j]));
+      S.XU[b + i][b + j] = dd_neg(dd_mul(v, S.rd[b + i]));
+    }
+  }
+  __syncthreads();
+  lu_inv_double_dd(S, 8);
+  lu_inv_double_dd(S, 16);
+  for (int e = t; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    const float2 l = S.XL[i][j], u = S.XU[i][j];
+    op.Li[i * op.ldl + j] = (double)l.x + (double)l.y;
+    op.Ui[i * op.ldu + j] = (double)u.x + (double)u.y;
   }
   __syncthreads();
 }
@@ -1146,7 +1253,10 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
     if constexpr (!SOLVE) {
       switch (T.kind) {
         case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem, a.err); break;
-        case TK_LU: dev_lu_base(a.lu[T.op], a.err, smem); break;
+        case TK_LU:
+          if (a.lu[T.op].pad & LU_FP64) dev_lu_base(a.lu[T.op], a.err, smem);
+          else dev_lu_base_dd(a.lu[T.op], a.err, smem);
+          break;
         case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
         default: break;
       }
@@ -1255,6 +1365,8 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
   const char* g64 = std::getenv("HM_GEMM_FP64");  // FP64 instead of double-float GEMM tiles
   const bool gemm_fp64 = g64 && g64[0] == '1';
+  const char* l64 = std::getenv("HM_LU_FP64");  // FP64 instead of double-float base LUs
+  const bool lu_fp64 = l64 && l64[0] == '1';
   for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
     for (size_t p = 0; p < parts.size(); ++p) {
@@ -1272,7 +1384,9 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
       for (size_t k = 0; k < W.lu.size(); ++k) {
         tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k] + o0});
         info[W.lu_id[k] + o0].ntasks = 1;
-        l.push_back(W.lu[k]);
+        LuOp o = W.lu[k];
+        o.pad = lu_fp64 ? LU_FP64 : 0;
+        l.push_back(o);
       }
       for (size_t k = 0; k < W.trunc.size(); ++k) {
         tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k] + o0});

@@ -35,8 +35,10 @@ struct LuOp {
   double* Ui;
   int64_t lda, ldl, ldu;
   int m;
-  int pad;
+  int pad;       // flags: LU_FP64
 };
+// LuOp::pad flag: FP64 base LU instead of double-float (HM_LU_FP64=1)
+constexpr int LU_FP64 = 1;
 
 // Truncation core of a low-rank sum X = A B' (A: m x K, B: n x K) from the
 // Gram matrices GA = A'A, GB = B'B (K x K, row-major): writes TA, TB (K x kf,

@@ -16,6 +16,67 @@ enum : int {
   DEVERR_TIMEOUT = 16,   // a bounded wait in a persistent kernel gave up
 };
 
+// ---- double-float arithmetic (unevaluated pairs of floats, about 48 bits)
+
+// Double-float split of an FP64 operand, integer operations only (no FP64
+// instruction, which this GPU issues at 1/64 of the FP32 rate): hi is the
+// significand rounded to nearest at 24 bits (an integer add on the float's bit
+// pattern carries into the exponent), lo the signed remainder, 29 bits rounded
+// to 24, so a = hi + lo + r with |r| <= 2^-49 |a|.  |a| < 2^-126 is flushed
+// to zero and the low part of |a| < 2^-74 is dropped (absolute error below
+// 2^-74); |a| >= 2^128 (after rounding), inf and NaN set `bad`.
+__device__ __forceinline__ float2 df_split(double a, bool& bad) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  if (e < -126) return make_float2(0.f, 0.f);
+  if (e > 127) {
+    bad = true;
+    return make_float2(0.f, 0.f);
+  }
+  const unsigned sgn = hw & 0x80000000u;
+  const unsigned r = lw & 0x1fffffffu;  // the 29 bits below hi's last, in units of 2^(e-52)
+  const unsigned up = r >> 28;          // round half up on the magnitude
+  const unsigned hb = (((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29)) + up;
+  if ((hb >> 23) >= 255u) {
+    bad = true;
+    return make_float2(0.f, 0.f);
+  }
+  float lo = 0.f;
+  if (e >= -74) lo = __fmul_rn(__int2float_rn((int)r - (int)(up << 29)), __int_as_float((e - 52 + 127) << 23));
+  return make_float2(__uint_as_float(sgn | hb), sgn ? -lo : lo);
+}
+
+// Products by Dekker's method, sums by Knuth's two-sum (Dekker 1971; Knuth,
+// TAOCP 2, sec. 4.2.2), reciprocal by one Newton step from the float
+// reciprocal; __f*_rn keep the compiler from contracting the error terms.
+__device__ __forceinline__ float2 dd_renorm(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+__device__ __forceinline__ float2 dd_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return dd_renorm(p, e);
+}
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return dd_renorm(s, __fadd_rn(t, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 dd_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// c - a b
+__device__ __forceinline__ float2 dd_fnms(float2 c, float2 a, float2 b) { return dd_add(c, dd_neg(dd_mul(a, b))); }
+// 1 / d: r0 = float reciprocal, r = r0 + r0 (1 - d r0) with the residual in double-float
+__device__ __forceinline__ float2 dd_recip(float2 d) {
+  const float r0 = __frcp_rn(d.x);
+  const float2 e = dd_add(make_float2(1.f, 0.f), dd_neg(dd_mul(d, make_float2(r0, 0.f))));
+  return dd_add(make_float2(r0, 0.f), dd_mul(make_float2(r0, 0.f), e));
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

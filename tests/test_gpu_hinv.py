@@ -164,3 +164,29 @@ def test_batch_of_hinv_problems_equals_single():
         hmat.cn_solve(H, F, dt, steps, us)
         assert np.array_equal(host(us), host(u))
     assert [H.stats(F)["solve_mode"] for H, F in zip(Hs, Fs)] == [2, 2, 1]
+
+
+def test_double_float_construction_matches_fp64(monkeypatch):
+    """The inverses' construction products in double-float arithmetic (the
+    default) and in FP64 (HM_HINV_BUILD_FP64=1) give the same solves to far
+    below the inverses' truncation tolerance, with the same ranks; FP64-storage
+    products (HM_HINV_FP64=1) and the float-pair storage agree likewise."""
+    prob, opts, dt = SMALL[1][1], dict(SMALL[1][2], solve="hinv"), SMALL[1][3]
+    H = hmat.HMatrix(prob, opts)
+    b = dev(np.random.default_rng(9).standard_normal(H.n))
+    F0 = H.factor(-0.5 * dt)
+    x0, r0 = host(F0.solve(b)), H.stats(F0)["hinv_max_rank"]
+    F0.free()
+    monkeypatch.setenv("HM_HINV_BUILD_FP64", "1")
+    F1 = H.factor(-0.5 * dt)
+    x1, r1 = host(F1.solve(b)), H.stats(F1)["hinv_max_rank"]
+    F1.free()
+    monkeypatch.delenv("HM_HINV_BUILD_FP64")
+    monkeypatch.setenv("HM_HINV_FP64", "1")
+    F2 = H.factor(-0.5 * dt)
+    x2 = host(F2.solve(b))
+    F2.free()
+    H.free()
+    assert abs(r0 - r1) <= 1
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) < 1e-11
+    assert np.linalg.norm(x2 - x0) / np.linalg.norm(x0) < 1e-12
