@@ -1,5 +1,6 @@
 // C ABI: planning, construction (hm_build), H-matvec and inspection calls.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <atomic>
 #include <cstring>
@@ -409,6 +410,36 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
   M.lr_items = d_li;
   HM_TRY(A.alloc((void**)&M.partial, sizeof(double) * (size_t)std::max(M.nvt, 1) * ACA_MAXK));
   HM_TRY(A.alloc((void**)&M.tvec, sizeof(double) * (size_t)std::max(nlr, 1) * ACA_MAXK));
+  // split form G = S + J for constant-order problems on a box (HM_MATVEC_FP64=1: FP64 products)
+  const char* mv64 = std::getenv("HM_MATVEC_FP64");
+  if (prob->s_slope == 0.0 && prob->domain == HM_DOMAIN_BOX && !(mv64 && mv64[0] == '1')) {
+    float2 *dj = nullptr, *udf = nullptr, *vdf = nullptr;
+    HM_TRY(A.alloc((void**)&dj, sizeof(float2) * (size_t)std::max<int64_t>(off, 1)));
+    HM_TRY(A.alloc((void**)&udf, sizeof(float2) * (size_t)std::max<int64_t>(uo, 1)));
+    HM_TRY(A.alloc((void**)&vdf, sizeof(float2) * (size_t)std::max<int64_t>(vo, 1)));
+    HM_TRY(A.alloc((void**)&M.tdf, sizeof(float2) * (size_t)std::max(nlr, 1) * ACA_MAXK));
+    HM_TRY(launch_near_fill_jump(H->ectx, H->d_dd, (int)H->h_dd.size(), dj, st));
+    HM_TRY(launch_split(H->d_U, udf, uo, st));
+    HM_TRY(launch_split(H->d_V, vdf, vo, st));
+    // axis neighbours of every Morton row: (-axis 0, +axis 0, -axis 1, +axis 1)
+    std::vector<int4> nb(N);
+    for (int q = 0; q < N; ++q) {
+      const int i0 = P.coord[2 * q], i1 = P.coord[2 * q + 1];
+      auto at = [&](int a0, int a1) {
+        if (a0 < 0 || a0 >= P.n[0] || a1 < 0 || a1 >= P.n[1]) return -1;
+        return P.iperm[(size_t)a1 * P.n[0] + a0];
+      };
+      nb[q] = make_int4(at(i0 - 1, i1), at(i0 + 1, i1), P.dim == 2 ? at(i0, i1 - 1) : -1,
+                        P.dim == 2 ? at(i0, i1 + 1) : -1);
+    }
+    int4* d_nb = nullptr;
+    HM_TRY(A.upload(&d_nb, nb));
+    M.Ddf = dj;
+    M.Udf = udf;
+    M.Vdf = vdf;
+    M.nb = d_nb;
+    M.gc = H->d_gc;
+  }
   HM_TRY(A.alloc((void**)&H->d_work, sizeof(double) * (size_t)N * 8));
 
   HM_CK(cudaStreamSynchronize(st));
@@ -482,6 +513,8 @@ int hm_matvec_noalloc(const hm_matrix* H, double alpha, double beta, const doubl
   MatvecPlan Q = H->mv;
   Q.partial = s;
   Q.tvec = s + part;
+  Q.Ddf = nullptr;  // FP64 products: the split form's float-pair coefficients would need more scratch
+  Q.tdf = nullptr;
   if (H->plan.dim == 1) return launch_matvec(Q, alpha, beta, x, gamma, w1, w2, nullptr, y, st);
   double* xm = s + part + tv;
   double* ym = xm + N;

@@ -113,6 +113,28 @@ __global__ void near_fill_kernel(EntryCtx E, const DenseDesc* dd, double* pool) 
   }
 }
 
+// The jump entries of the dense leaves as float pairs (split form of the
+// H-matvec): every entry but the diagonal from the offset table (no stencil:
+// it is applied in FP64 from the constants), zero on the diagonal and in the
+// row padding.  Constant-order problems only.
+__global__ void near_fill_jump_kernel(EntryCtx E, const DenseDesc* dd, float2* pool) {
+  const DenseDesc D = dd[blockIdx.x];
+  float2* out = pool + D.off;
+  const int64_t tot = (int64_t)D.m * D.ld;
+  bool bad = false;
+  for (int64_t t = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.y * blockDim.x) {
+    const int i = (int)(t / D.ld), j = (int)(t % D.ld);
+    const int p = D.r0 + i, q = D.c0 + j;
+    out[(int64_t)i * D.ld + j] = (j < D.n && p != q) ? df_split(far_entry(E, p, q), bad) : make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void split_kernel(const double* src, float2* dst, int64_t n) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = df_split(src[e], bad);
+}
+
 __global__ void entries_kernel(EntryCtx E, const int* iperm, int N, int64_t count, const int* rows,
                                const int* cols, double* out, int* err) {
   const GenConst g = *E.gc;
@@ -166,6 +188,21 @@ int launch_near_fill(const EntryCtx& E, const DenseDesc* d_dd, int ndense, doubl
   dim3 grid(ndense, 8);
   count_launches(1);
   near_fill_kernel<<<grid, 256, 0, st>>>(E, d_dd, pool);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_near_fill_jump(const EntryCtx& E, const DenseDesc* d_dd, int ndense, float2* pool, cudaStream_t st) {
+  if (ndense == 0) return HM_OK;
+  count_launches(1);
+  dim3 grid(ndense, 16);
+  near_fill_jump_kernel<<<grid, 256, 0, st>>>(E, d_dd, pool);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_split(const double* src, float2* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return HM_OK;
+  count_launches(1);
+  split_kernel<<<1216, 256, 0, st>>>(src, dst, n);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

@@ -26,6 +26,10 @@ int launch_finalize_constants(const NuParams& q, double a, const double* b, doub
                               const double* d_scratch, GenConst* d_gc, cudaStream_t st);
 int launch_near_fill(const EntryCtx& E, const DenseDesc* d_dd, int ndense, double* pool,
                      cudaStream_t st);
+// Split form of the H-matvec: jump entries of the dense leaves and a plain
+// FP64 -> float-pair split of an array.
+int launch_near_fill_jump(const EntryCtx& E, const DenseDesc* d_dd, int ndense, float2* pool, cudaStream_t st);
+int launch_split(const double* src, float2* dst, int64_t n, cudaStream_t st);
 int launch_entries(const EntryCtx& E, const int* iperm, int N, int64_t count, const int* rows,
                    const int* cols, double* out, int* err, cudaStream_t st);
 int launch_to_dense(const DenseDesc* d_dd, int ndense, const double* pool, const LRDesc* d_ld,
@@ -52,6 +56,17 @@ struct MatvecPlan {
   double* partial;         // nvt x ACA_MAXK scratch
   double* tvec;            // nlr x ACA_MAXK scratch
   int kmax;                // largest rank cap (<= ACA_MAXK)
+  // Split form (constant-order problems on a box; null otherwise): G = S + J
+  // with S the stencil and the diagonal (applied in FP64 from the constants)
+  // and J the jump entries (dense leaves with the diagonal and the stencil
+  // removed, and the low-rank blocks) stored as float pairs (hi + lo) and
+  // multiplied in double-float arithmetic.
+  const float2* Ddf;       // like D: jump entries, zero on the diagonal
+  const float2* Udf;
+  const float2* Vdf;
+  float2* tdf;             // nlr x ACA_MAXK: tvec as float pairs
+  const int4* nb;          // per Morton row: neighbours (-axis0, +axis0, -axis1, +axis1), -1 if none
+  const GenConst* gc;      // diag and stencil coefficients
 };
 
 // y = alpha x + beta (H x) + gamma (w1 + w2) (+ w3 * 1 if w3 != nullptr)

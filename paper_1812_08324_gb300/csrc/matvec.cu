@@ -8,7 +8,9 @@
 //                     (warp per 4 rows, 16-byte loads) plus U[rows] t_q of
 //                     every low-rank block covering the rows, then the
 //                     epilogue y = alpha x + beta (H x) + gamma (w1 + w2) + w3.
-// All vectors are in Morton order.  FP64 storage and FP64 accumulation.
+// All vectors are in Morton order.  FP64 storage and FP64 accumulation, or the
+// split form (below): the stiff stencil part in FP64, the jump part from
+// float-pair storage in double-float arithmetic.
 #include <atomic>
 
 #include "hm_device.cuh"
@@ -46,6 +48,10 @@ __device__ __forceinline__ void vt_reduce_body(const MatvecPlan& P, int q) {
     double acc = 0.0;
     for (int o = b; o < e; ++o) acc += P.partial[(int64_t)o * ACA_MAXK + l];
     P.tvec[(int64_t)q * ACA_MAXK + l] = acc;
+    if (P.tdf) {
+      bool bad = false;
+      P.tdf[(int64_t)q * ACA_MAXK + l] = df_split(acc, bad);
+    }
   }
 }
 
@@ -129,18 +135,157 @@ __device__ __forceinline__ void rows_body(const MatvecPlan& P, int chunk, double
   }
 }
 
+// ---- split form G = S + J (constant-order problems on a box): the stiff
+// part S -- the diagonal and the axis-neighbour stencil, entries up to
+// 4 a / h^2 -- in FP64 from the constants, the jump part J (every other
+// entry; the diagonal and the stencil removed from the dense leaves) from
+// float-pair storage in double-float arithmetic on the FP32 pipes (FP64 on
+// this GPU issues about two multiply-adds per clock per SM, below the HBM
+// rate of these products).  The double-float rounding is about 2^-47 of
+// sum |J_ij x_j|, which stays far below the FP64 rounding of the stiff part's
+// terms.  Products by Dekker's method, sums by Knuth's two-sum.
+__device__ __forceinline__ void mv_mac(float2& s, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float t = __fadd_rn(s.x, p);
+  const float bb = __fsub_rn(t, s.x);
+  const float r = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  s.x = t;
+  s.y = __fadd_rn(s.y, __fadd_rn(r, e));
+}
+__device__ __forceinline__ float2 mv_wsum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    v = dd_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ void vt_df_body(const MatvecPlan& P, int task, const double* __restrict__ x) {
+  __shared__ float2 xs[VT_CHUNK];
+  const VTask T = P.vt[task];
+  const LRDesc L = P.ld[T.lr];
+  const int k = P.rank[T.lr];
+  const double* xc = x + L.c0 + T.c_lo;
+  bool bad = false;
+  for (int j = threadIdx.x; j < T.len; j += blockDim.x) xs[j] = df_split(xc[j], bad);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const float2* V = P.Vdf + L.voff + T.c_lo;
+  for (int l = warp; l < k; l += nwarp) {
+    const float2* Vl = V + (int64_t)l * L.n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = lane; j < T.len; j += 32) mv_mac(acc, Vl[j], xs[j]);
+    acc = mv_wsum(acc);
+    if (lane == 0) P.partial[(int64_t)T.out * ACA_MAXK + l] = (double)acc.x + (double)acc.y;
+  }
+}
+
+__device__ __forceinline__ void rows_df_body(const MatvecPlan& P, int chunk, double alpha, double beta,
+                                             const double* __restrict__ x, double gamma, const double* w1,
+                                             const double* w2, const double* w3, double* y) {
+  __shared__ float2 acc_d[MV_CHUNK];
+  __shared__ float2 acc_f[8][MV_CHUNK];
+  const RowChunk C = P.chunks[chunk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float2 z = make_float2(0.f, 0.f);
+  bool bad = false;
+  float2 rsum[ROWS_PER_WARP];
+#pragma unroll
+  for (int r = 0; r < ROWS_PER_WARP; ++r) rsum[r] = z;
+  const int rw0 = warp * ROWS_PER_WARP;
+  const int nrw = max(0, min(ROWS_PER_WARP, C.nrow - rw0));
+  // dense leaves: warp has ROWS_PER_WARP rows, lanes over column pairs, two
+  // pairs per lane in flight (16-byte loads of two float pairs; D.ld is a
+  // multiple of 4 and D.off even, the padding holds zeros); x is read and
+  // split in registers (no staging barrier between the blocks)
+  for (int it = C.dense_begin; it < C.dense_end; ++it) {
+    const DenseDesc D = P.dd[P.dense_items[it]];
+    const int i0 = C.r0 - D.r0 + rw0;
+    const float2* base = P.Ddf + D.off + (int64_t)i0 * D.ld;
+    const double* xc = x + D.c0;
+    const int npair = (D.n + 1) >> 1;
+    for (int p0 = lane; p0 < npair; p0 += 64) {
+      const int p1 = p0 + 32;
+      float4 v[2][ROWS_PER_WARP];
+#pragma unroll
+      for (int r = 0; r < ROWS_PER_WARP; ++r) {
+        v[0][r] = r < nrw ? *reinterpret_cast<const float4*>(base + (int64_t)r * D.ld + 2 * p0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[1][r] = (r < nrw && p1 < npair) ? *reinterpret_cast<const float4*>(base + (int64_t)r * D.ld + 2 * p1)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const float2 xa = df_split(__ldg(xc + 2 * p0), bad);
+      const float2 xb = 2 * p0 + 1 < D.n ? df_split(__ldg(xc + 2 * p0 + 1), bad) : z;
+      const float2 xc0 = p1 < npair ? df_split(__ldg(xc + 2 * p1), bad) : z;
+      const float2 xc1 = (p1 < npair && 2 * p1 + 1 < D.n) ? df_split(__ldg(xc + 2 * p1 + 1), bad) : z;
+#pragma unroll
+      for (int r = 0; r < ROWS_PER_WARP; ++r) {
+        mv_mac(rsum[r], make_float2(v[0][r].x, v[0][r].y), xa);
+        mv_mac(rsum[r], make_float2(v[0][r].z, v[0][r].w), xb);
+        mv_mac(rsum[r], make_float2(v[1][r].x, v[1][r].y), xc0);
+        mv_mac(rsum[r], make_float2(v[1][r].z, v[1][r].w), xc1);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS_PER_WARP; ++r) {
+    const float2 sr = mv_wsum(rsum[r]);
+    if (lane == 0) acc_d[rw0 + r] = sr;
+  }
+  // low-rank blocks: warp per block, lane per row
+  float2 facc = z;
+  for (int it = C.lr_begin + warp; it < C.lr_end; it += 8) {
+    const int q = P.lr_items[it];
+    const LRDesc L = P.ld[q];
+    const int k = P.rank[q];
+    const int i = C.r0 - L.r0 + lane;
+    if (lane < C.nrow) {
+      const float2* U = P.Udf + L.uoff + i;
+      const float2* t = P.tdf + (int64_t)q * ACA_MAXK;
+      for (int l = 0; l < k; ++l) mv_mac(facc, U[(int64_t)l * L.m], t[l]);
+    }
+  }
+  acc_f[warp][lane] = facc;
+  __syncthreads();
+  if (threadIdx.x < C.nrow) {
+    const int r = threadIdx.x;
+    float2 jx = acc_d[r];
+    for (int w = 0; w < 8; ++w) jx = dd_add(jx, acc_f[w][r]);
+    const int row = C.r0 + r;
+    // S x in FP64: the diagonal and the axis neighbours
+    const GenConst* g = P.gc;
+    const int4 nb = P.nb[row];
+    double sx = g->diag * x[row];
+    if (nb.x >= 0) sx = fma(g->stencil_m[0], x[nb.x], sx);
+    if (nb.y >= 0) sx = fma(g->stencil_p[0], x[nb.y], sx);
+    if (nb.z >= 0) sx = fma(g->stencil_m[1], x[nb.z], sx);
+    if (nb.w >= 0) sx = fma(g->stencil_p[1], x[nb.w], sx);
+    const double hx = sx + ((double)jx.x + (double)jx.y);
+    double out = alpha * x[row] + beta * hx;
+    if (w1) out += gamma * w1[row];
+    if (w2) out += gamma * w2[row];
+    if (w3) out += w3[row];
+    y[row] = out;
+  }
+}
+
 __global__ void __launch_bounds__(256) vt_kernel(MatvecPlan P, const double* __restrict__ x) {
-  vt_body(P, blockIdx.x, x);
+  if (P.Ddf) vt_df_body(P, blockIdx.x, x);
+  else vt_body(P, blockIdx.x, x);
 }
 
 __global__ void vt_reduce_kernel(MatvecPlan P) {
   if ((int)blockIdx.x < P.nlr) vt_reduce_body(P, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 rows_kernel(MatvecPlan P, double alpha, double beta, const double* __restrict__ x, double gamma, const double* w1,
             const double* w2, const double* w3, double* y) {
-  rows_body(P, blockIdx.x, alpha, beta, x, gamma, w1, w2, w3, y);
+  if (P.Ddf) rows_df_body(P, blockIdx.x, alpha, beta, x, gamma, w1, w2, w3, y);
+  else rows_body(P, blockIdx.x, alpha, beta, x, gamma, w1, w2, w3, y);
 }
 
 // ---- batched: many independent H-matvecs in three launches.  off[j] is the
@@ -157,7 +302,8 @@ __device__ __forceinline__ int batch_job(const int* off, int count, int b) {
 
 __global__ void __launch_bounds__(256) vt_batch_kernel(const MvJob* jobs, const int* off, int count) {
   const int j = batch_job(off, count, blockIdx.x);
-  vt_body(jobs[j].P, blockIdx.x - off[j], jobs[j].x);
+  if (jobs[j].P.Ddf) vt_df_body(jobs[j].P, blockIdx.x - off[j], jobs[j].x);
+  else vt_body(jobs[j].P, blockIdx.x - off[j], jobs[j].x);
 }
 
 __global__ void vt_reduce_batch_kernel(const MvJob* jobs, const int* off, int count) {
@@ -165,10 +311,11 @@ __global__ void vt_reduce_batch_kernel(const MvJob* jobs, const int* off, int co
   vt_reduce_body(jobs[j].P, blockIdx.x - off[j]);
 }
 
-__global__ void __launch_bounds__(256) rows_batch_kernel(const MvJob* jobs, const int* off, int count) {
+__global__ void __launch_bounds__(256, 3) rows_batch_kernel(const MvJob* jobs, const int* off, int count) {
   const int j = batch_job(off, count, blockIdx.x);
   const MvJob& J = jobs[j];
-  rows_body(J.P, blockIdx.x - off[j], J.alpha, J.beta, J.x, J.gamma, J.w1, J.w2, J.w3, J.y);
+  if (J.P.Ddf) rows_df_body(J.P, blockIdx.x - off[j], J.alpha, J.beta, J.x, J.gamma, J.w1, J.w2, J.w3, J.y);
+  else rows_body(J.P, blockIdx.x - off[j], J.alpha, J.beta, J.x, J.gamma, J.w1, J.w2, J.w3, J.y);
 }
 
 __global__ void gather_kernel(const int* perm, int N, const double* src, double* dst) {

@@ -49,7 +49,8 @@ def test_noalloc_matches_matvec_twice(name, prob, opts):
         got = host(y)
         scale = np.max(np.abs(ref)) + 1e-300
         assert np.all(np.isfinite(got)), call
-        # same kernels, same summation order: equal to rounding (the matvec tests use 50 aca_tol)
+        # the same product up to rounding (hm_matvec multiplies the jump part in
+        # double-float arithmetic, 2^-47; the matvec tests allow 50 aca_tol)
         assert np.max(np.abs(got - ref)) <= 1e-13 * scale, call
     H.sync()
 
