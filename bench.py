@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=200)
     ap.add_argument("--serve-sides", default="64,128", help="2D grid sides of the served stream")
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--group-unknowns", type=int, default=1200000)
+    ap.add_argument("--group-unknowns", type=int, default=2400000)
     return ap.parse_args()
 
 

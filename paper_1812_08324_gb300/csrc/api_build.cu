@@ -410,6 +410,66 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
   M.lr_items = d_li;
   HM_TRY(A.alloc((void**)&M.partial, sizeof(double) * (size_t)std::max(M.nvt, 1) * ACA_MAXK));
   HM_TRY(A.alloc((void**)&M.tvec, sizeof(double) * (size_t)std::max(nlr, 1) * ACA_MAXK));
+  HM_TRY(A.alloc((void**)&H->d_work, sizeof(double) * (size_t)N * 8));
+
+  HM_CK(cudaStreamSynchronize(st));
+  H->h_rank.assign(nlr, 0);
+  std::vector<int> capped(nlr, 0);
+  if (nlr) {
+    HM_CK(cudaMemcpy(H->h_rank.data(), H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
+    HM_CK(cudaMemcpy(capped.data(), H->d_capped, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
+  }
+  H->capped_blocks = 0;
+  for (int c : capped) H->capped_blocks += c;
+
+  // low-rank storage compacted to the ranks ACA reached (it was sized for
+  // the cap max_rank): U (m x rank) and V (n x rank), column-major
+  if (nlr) {
+    int64_t uo2 = 0, vo2 = 0;
+    std::vector<LRDesc> ld2 = H->h_ld;
+    std::vector<int64_t> ju, jv;  // (source offset, target offset, count) triples, in doubles
+    for (int q = 0; q < nlr; ++q) {
+      LRDesc& L = ld2[q];
+      const int k = std::max(1, H->h_rank[q]);
+      ju.insert(ju.end(), {H->h_ld[q].uoff, uo2, (int64_t)L.m * k});
+      jv.insert(jv.end(), {H->h_ld[q].voff, vo2, (int64_t)L.n * k});
+      L.uoff = uo2;
+      L.voff = vo2;
+      L.kcap = k;
+      uo2 += ((int64_t)L.m * k + 3) & ~int64_t(3);
+      vo2 += ((int64_t)L.n * k + 3) & ~int64_t(3);
+    }
+    double *U2 = nullptr, *V2 = nullptr;
+    HM_TRY(A.alloc((void**)&U2, sizeof(double) * (size_t)std::max<int64_t>(uo2, 1)));
+    HM_TRY(A.alloc((void**)&V2, sizeof(double) * (size_t)std::max<int64_t>(vo2, 1)));
+    int64_t *d_ju = nullptr, *d_jv = nullptr;
+    HM_TRY(A.upload(&d_ju, ju));
+    HM_TRY(A.upload(&d_jv, jv));
+    HM_TRY(launch_copy_segments(d_ju, nlr, H->d_U, U2, st));
+    HM_TRY(launch_copy_segments(d_jv, nlr, H->d_V, V2, st));
+    LRDesc* d_ld2 = nullptr;
+    HM_TRY(A.upload(&d_ld2, ld2));
+    HM_CK(cudaStreamSynchronize(st));
+    A.free_one(H->d_U);
+    A.free_one(H->d_V);
+    A.free_one(H->d_ld);
+    A.free_one(d_ju);
+    A.free_one(d_jv);
+    H->d_U = U2;
+    H->d_V = V2;
+    H->d_ld = d_ld2;
+    H->h_ld = ld2;
+    H->u_pool = uo2;
+    H->v_pool = vo2;
+    H->kmax = 1;
+    for (const LRDesc& L : ld2) H->kmax = std::max(H->kmax, L.kcap);
+    M.U = U2;
+    M.V = V2;
+    M.ld = d_ld2;
+    M.kmax = H->kmax;
+    uo = uo2;
+    vo = vo2;
+  }
   // split form G = S + J for constant-order problems on a box (HM_MATVEC_FP64=1: FP64 products)
   const char* mv64 = std::getenv("HM_MATVEC_FP64");
   if (prob->s_slope == 0.0 && prob->domain == HM_DOMAIN_BOX && !(mv64 && mv64[0] == '1')) {
@@ -440,17 +500,7 @@ static int build_impl(const hm_problem* prob, const hm_opts* opts, cudaStream_t 
     M.nb = d_nb;
     M.gc = H->d_gc;
   }
-  HM_TRY(A.alloc((void**)&H->d_work, sizeof(double) * (size_t)N * 8));
-
   HM_CK(cudaStreamSynchronize(st));
-  H->h_rank.assign(nlr, 0);
-  std::vector<int> capped(nlr, 0);
-  if (nlr) {
-    HM_CK(cudaMemcpy(H->h_rank.data(), H->d_rank, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
-    HM_CK(cudaMemcpy(capped.data(), H->d_capped, sizeof(int) * nlr, cudaMemcpyDeviceToHost));
-  }
-  H->capped_blocks = 0;
-  for (int c : capped) H->capped_blocks += c;
   return HM_OK;
 }
 

@@ -45,6 +45,7 @@ struct DevArena {
       return HM_ERR_OOM;
     }
     ptrs.push_back(*p);
+    sizes.push_back(bytes);
     bytes_held += (int64_t)bytes;
     return HM_OK;
   }
@@ -54,9 +55,24 @@ struct DevArena {
     if (!h.empty()) HM_CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     return HM_OK;
   }
+  // free one allocation made by this arena (its bytes leave bytes_held)
+  void free_one(void* p, size_t bytes = 0) {
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
+        size_t b = bytes;
+        if (!b) b = sizes.size() > i ? sizes[i] : 0;
+        cudaFree(p);
+        bytes_held -= (int64_t)b;
+        ptrs.erase(ptrs.begin() + i);
+        if (sizes.size() > i) sizes.erase(sizes.begin() + i);
+        return;
+      }
+  }
+  std::vector<size_t> sizes;  // bytes of each allocation (parallel to ptrs)
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+    sizes.clear();
   }
 };
 

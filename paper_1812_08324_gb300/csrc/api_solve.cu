@@ -27,6 +27,7 @@ struct hm_factors {
   double alpha = 1.0;  // factors of alpha I + theta G
   int kf = 0;
   Arena arena;
+  Arena tmp;                   // the H-LU's pooled temporaries, released once it has run
   std::vector<void*> allocs;
   DevSchedule solve;
   FactorLayout F;
@@ -350,6 +351,7 @@ void factor_discard(FactorJob& J) {
   }
   for (void* p : J.F->allocs) cudaFree(p);
   J.F->arena.release();
+  J.F->tmp.release();
   delete J.F;
   J.F = nullptr;
 }
@@ -395,7 +397,8 @@ void factor_plan(FactorJob& J) {
   const hm_matrix* H = J.H;
   hm_factors* F = J.F;
   J.status = plan_hlu(H->plan, H->h_dd, H->d_D, H->h_ld, H->d_U, H->d_V, F->kf, F->theta, H->opts.lu_tol,
-                      F->d_rank, F->arena, J.hb, F->alpha, H->opts.solve_block, F->solve_mode == HM_SOLVE_SUBST);
+                      F->d_rank, F->arena, J.hb, F->alpha, H->opts.solve_block, F->solve_mode == HM_SOLVE_SUBST,
+                      &F->tmp);
   if (J.status != HM_OK) { J.err = J.hb.err; return; }
   F->fact_ops = J.hb.ops;
   F->fact_waves = (int)J.hb.waves.size();
@@ -880,6 +883,7 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
     int z = e & ~DEVERR_RANKCAP;
     cudaMemcpy(d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
   }
+  for (FactorJob& J : jobs) J.F->tmp.release();  // the schedule has run: its temporaries are dead
   for (FactorJob& J : jobs) {
     J.F->fact_ms = ms;
     J.F->fact_fma = J.hb.gemm_fma[0] + J.hb.gemm_fma[1] + J.hb.gemm_fma[2];
@@ -908,6 +912,10 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
                    *F->hinv, herr);
     if (s != HM_OK) { set_error("hierarchical inverses: " + herr); return fail_all(s); }
     F->lu_bytes = F->hinv->step_bytes;
+    // the solves read only the inverses: the factors and the planner's
+    // temporaries are released (the layout's pointers are dropped with them)
+    F->arena.release();
+    F->F = FactorLayout();
   }
   if (count > 0) phase("inverses");
   for (FactorJob& J : jobs) {
@@ -1131,6 +1139,7 @@ void hm_factors_free(hm_factors* F) {
   }
   for (void* p : F->allocs) cudaFree(p);
   F->arena.release();
+  F->tmp.release();
   delete F;
 }
 

@@ -129,6 +129,14 @@ __global__ void near_fill_jump_kernel(EntryCtx E, const DenseDesc* dd, float2* p
   }
 }
 
+// segments (source offset, target offset, count) of src copied into dst, one
+// segment per blockIdx.y
+__global__ void copy_segments_kernel(const int64_t* jobs, const double* src, double* dst) {
+  const int64_t s = jobs[3 * blockIdx.y], d = jobs[3 * blockIdx.y + 1], n = jobs[3 * blockIdx.y + 2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[d + e] = src[s + e];
+}
+
 __global__ void split_kernel(const double* src, float2* dst, int64_t n) {
   bool bad = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -196,6 +204,13 @@ int launch_near_fill_jump(const EntryCtx& E, const DenseDesc* d_dd, int ndense, 
   count_launches(1);
   dim3 grid(ndense, 16);
   near_fill_jump_kernel<<<grid, 256, 0, st>>>(E, d_dd, pool);
+  return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
+}
+
+int launch_copy_segments(const int64_t* d_jobs, int njobs, const double* src, double* dst, cudaStream_t st) {
+  if (njobs <= 0) return HM_OK;
+  count_launches(1);
+  copy_segments_kernel<<<dim3(4, njobs), 256, 0, st>>>(d_jobs, src, dst);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

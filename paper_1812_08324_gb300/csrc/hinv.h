@@ -90,7 +90,7 @@ int launch_hinv_batch(const HinvBatch& B, cudaStream_t st);
 // ---- the inverses of one factorisation
 struct HinvTriangle {
   HinvApply A{};            // in the chosen storage precision
-  HinvApply A64{};          // FP64 copy (construction; the FP64 solve)
+  HinvApply A64{};          // FP64 pools of the construction (released when A converts them)
   std::vector<HinvLeaf> h_leaves;
   std::vector<HinvNode> h_nodes;
   std::vector<int> h_rank;

@@ -1112,6 +1112,24 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     s = HM_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
   free_tmp();
+  // the FP64 pools served the construction; a converted storage replaces them
+  if (s == HM_OK && aprec != HINV_F64) {
+    for (int tri = 0; tri < 2; ++tri) {
+      HinvApply& A64 = out.tri[tri].A64;
+      for (const void* q : {A64.leaf_pool, A64.p_pool, A64.q_pool}) {
+        auto it = std::find(out.allocs.begin(), out.allocs.end(), q);
+        if (it == out.allocs.end()) continue;
+        size_t bytes = 0;
+        if (q == A64.leaf_pool) bytes = sizeof(double) * std::max<int64_t>(leaf_elems, 1);
+        else if (q == A64.p_pool) bytes = sizeof(double) * std::max<int64_t>(p_elems[tri], 1);
+        else bytes = sizeof(double) * std::max<int64_t>(q_elems[tri], 1);
+        cudaFree(*it);
+        out.allocs.erase(it);
+        out.bytes -= (int64_t)bytes;
+      }
+      A64.leaf_pool = A64.p_pool = A64.q_pool = nullptr;
+    }
+  }
   if (s != HM_OK) {
     if (err.empty()) err = "hierarchical inverse construction failed";
     return s;

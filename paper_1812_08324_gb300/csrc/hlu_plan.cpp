@@ -145,6 +145,7 @@ class Emitter {
   OpGraph& graph;
   int cur_id = -1;  // op id assigned by the last place()
   Arena& A;
+  Arena* TA = nullptr;  // pooled temporaries (nullptr: A); no op after the H-LU reads them
   Tracker T;
   int seg_default;
   int64_t nops = 0;
@@ -152,11 +153,11 @@ class Emitter {
   int phase = 0;                        // FMA accounting bucket of the ops emitted now
   double gemm_fma[3] = {0.0, 0.0, 0.0};
 
-  View new_mat(int rows, int cols, bool colmajor, int seg = -1) {
+  View new_mat(int rows, int cols, bool colmajor, int seg = -1, bool scratch = false) {
     View v;
     v.rows = rows;
     v.cols = cols;
-    v.p = A.alloc((int64_t)rows * cols);
+    v.p = (scratch && TA ? *TA : A).alloc((int64_t)rows * cols);
     if (!v.p) status = HM_ERR_OOM;
     if (colmajor) { v.rs = 1; v.cs = rows; } else { v.rs = cols; v.cs = 1; }
     v.buf = T.add(rows, seg < 0 ? seg_default : seg);
@@ -202,7 +203,7 @@ class Emitter {
       v.buf = h.top().buf;
       h.pop();
     } else {
-      v.p = A.alloc(int64_t(1) << c);
+      v.p = (TA ? *TA : A).alloc(int64_t(1) << c);
       if (!v.p) status = HM_ERR_OOM;
       v.buf = T.add_elem(v.p, int64_t(1) << c);
     }
@@ -962,8 +963,9 @@ class HLU {
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha,
-             int sb_rows_opt, bool solve_blocks) {
+             int sb_rows_opt, bool solve_blocks, Arena* tmp_arena) {
   Emitter E(out.waves, out.graph, arena, std::max(1, std::min(P.leaf, 256)));
+  E.TA = tmp_arena;
   if (const char* lag = std::getenv("HM_TMP_LAG")) E.tmp_lag = std::atoi(lag);
   if (out.sink && out.chunk_ops > 0) {
     E.sink = &out.sink;
@@ -998,8 +1000,10 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     S.n = L.n;
     S.rank = d_rank_f + q;
     for (int s = 0; s < 2; ++s) {
-      S.U[s] = E.new_mat(L.m, (1 + H.nacc()) * kf, true);
-      S.V[s] = E.new_mat(L.n, (1 + H.nacc()) * kf, true);
+      // working slots (factor + pending update columns, ping-pong): scratch when
+      // a temporaries arena is given; the final factor is copied out below
+      S.U[s] = E.new_mat(L.m, (1 + H.nacc()) * kf, true, -1, true);
+      S.V[s] = E.new_mat(L.n, (1 + H.nacc()) * kf, true, -1, true);
     }
     S.rankv = E.new_mat(1, 1, false, 1);
     int kc = std::min(L.kcap, kf);
@@ -1014,6 +1018,21 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   }
   H.hlu(0);
   for (int q = 0; q < nl; ++q) H.flush(q);  // recompress what is still pending
+  // the final low-rank factors in tight storage (m x kf, n x kf), copied out of
+  // the working slots (which lie with the temporaries when tmp_arena is given)
+  std::vector<View> fin_u(nl), fin_v(nl);
+  for (int q = 0; q < nl; ++q) {
+    if (tmp_arena) {
+      fin_u[q] = E.new_mat(ld[q].m, kf, true);
+      fin_v[q] = E.new_mat(ld[q].n, kf, true);
+      View su = H.lrU(q), sv = H.lrV(q);
+      E.copy(fin_u[q], 1.0, &su, 0.0);
+      E.copy(fin_v[q], 1.0, &sv, 0.0);
+    } else {
+      fin_u[q] = H.lrU(q);
+      fin_v[q] = H.lrV(q);
+    }
+  }
   if (solve_blocks) {
     E.phase = 1;
     // Solve blocks and their exact diagonal inverses, then the scaled couplings.
@@ -1184,8 +1203,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   F.lr_u.resize(nl);
   F.lr_v.resize(nl);
   for (int q = 0; q < nl; ++q) {
-    F.lr_u[q] = H.lr[q].U[H.lr[q].cur].p;
-    F.lr_v[q] = H.lr[q].V[H.lr[q].cur].p;
+    F.lr_u[q] = fin_u[q].p;
+    F.lr_v[q] = fin_v[q].p;
   }
   return HM_OK;
 }

@@ -128,10 +128,12 @@ struct HluBuild {
 int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_dense,
              const std::vector<LRDesc>& ld, const double* d_U, const double* d_V, int kf,
              double theta, double lu_tol, int* d_rank_f, Arena& arena, HluBuild& out, double alpha = 1.0,
-             int sb_rows_opt = 0, bool solve_blocks = true);
+             int sb_rows_opt = 0, bool solve_blocks = true, Arena* tmp_arena = nullptr);
 // sb_rows_opt: rows of the largest solve block (0: SOLVE_BLOCK, twice that for
 // 1D problems of >= 32768 unknowns); solve_blocks = false skips the solve
-// blocks' inverses and scaled couplings (only the substitution solve reads them).
+// blocks' inverses and scaled couplings (only the substitution solve reads them);
+// tmp_arena (if given) takes the pooled temporaries, which no operation after
+// the schedule reads: the caller may release it once the schedule has run.
 
 // Expand z = U^{-1} L^{-1} b (forward then backward H-triangular
 // substitution, leaf by leaf over the scaled factors) into phases of row and

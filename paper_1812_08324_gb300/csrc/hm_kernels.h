@@ -30,6 +30,8 @@ int launch_near_fill(const EntryCtx& E, const DenseDesc* d_dd, int ndense, doubl
 // FP64 -> float-pair split of an array.
 int launch_near_fill_jump(const EntryCtx& E, const DenseDesc* d_dd, int ndense, float2* pool, cudaStream_t st);
 int launch_split(const double* src, float2* dst, int64_t n, cudaStream_t st);
+// copy segments (source offset, target offset, count: 3 int64 per segment, device) of src to dst
+int launch_copy_segments(const int64_t* d_jobs, int njobs, const double* src, double* dst, cudaStream_t st);
 int launch_entries(const EntryCtx& E, const int* iperm, int N, int64_t count, const int* rows,
                    const int* cols, double* out, int* err, cudaStream_t st);
 int launch_to_dense(const DenseDesc* d_dd, int ndense, const double* pool, const LRDesc* d_ld,

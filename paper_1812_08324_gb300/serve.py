@@ -2,7 +2,7 @@
 
 Requests (problem, options, dt, steps, u0) arrive over time.  The loop admits
 waiting requests in arrival order while their device memory fits the HBM
-budget, builds their H-matrices and factors all newly admitted ones in one
+budget (the estimate per unknown, or the measured footprint once larger), builds their H-matrices and factors all newly admitted ones in one
 batched H-LU launch (hm_factor_batch), and advances every admitted request
 together: each tick runs k CN steps of all active requests through one batch
 (one merged solve launch and one batched H-matvec per step, replayed as a CUDA
@@ -27,10 +27,10 @@ import numpy as np
 
 from . import hmat
 
-# Device bytes per unknown assumed at admission (H-matrix + factor arena with
-# its temporaries); replaced by the measured footprint once a request is
-# factored.
-EST_BYTES_PER_UNKNOWN = {1: 140e3, 2: 900e3}
+# Device bytes per unknown assumed at admission (H-matrix + what the solves
+# read: the factors in 2D, the factors' hierarchical inverses in 1D); a request
+# is charged the larger of this and its measured footprint.
+EST_BYTES_PER_UNKNOWN = {1: 30e3, 2: 450e3}
 
 
 @dataclass
@@ -107,11 +107,13 @@ class Server:
                 Hs = [hmat.HMatrix(r["problem"], r["opts"]) for r in new]
                 Fs = hmat.factor_batch(Hs, [-0.5 * r["dt"] for r in new])
                 for r, H, F in zip(new, Hs, Fs):
-                    measured = float(H.stats(F)["device_bytes"])
-                    self.used += measured - estimate_bytes(r)
+                    # a request holds the larger of its estimate and its measured
+                    # footprint until it finishes
+                    charged = max(float(H.stats(F)["device_bytes"]), estimate_bytes(r))
+                    self.used += charged - estimate_bytes(r)
                     res = Result(r["rid"], H.n, r["steps"], r["arrival"], admitted=t_adm)
                     u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
-                    active.append(_Slot(r, res, H, F, u, r["steps"], measured))
+                    active.append(_Slot(r, res, H, F, u, r["steps"], charged))
                 self.peak_used = max(self.peak_used, self.used)
                 dirty = True
             if not active:
