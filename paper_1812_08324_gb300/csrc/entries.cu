@@ -130,11 +130,10 @@ __global__ void near_fill_jump_kernel(EntryCtx E, const DenseDesc* dd, float2* p
 }
 
 // segments (source offset, target offset, count) of src copied into dst, one
-// segment per blockIdx.y
+// segment per CTA
 __global__ void copy_segments_kernel(const int64_t* jobs, const double* src, double* dst) {
-  const int64_t s = jobs[3 * blockIdx.y], d = jobs[3 * blockIdx.y + 1], n = jobs[3 * blockIdx.y + 2];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[d + e] = src[s + e];
+  const int64_t s = jobs[3 * (int64_t)blockIdx.x], d = jobs[3 * (int64_t)blockIdx.x + 1], n = jobs[3 * (int64_t)blockIdx.x + 2];
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) dst[d + e] = src[s + e];
 }
 
 __global__ void split_kernel(const double* src, float2* dst, int64_t n) {
@@ -210,7 +209,7 @@ int launch_near_fill_jump(const EntryCtx& E, const DenseDesc* d_dd, int ndense, 
 int launch_copy_segments(const int64_t* d_jobs, int njobs, const double* src, double* dst, cudaStream_t st) {
   if (njobs <= 0) return HM_OK;
   count_launches(1);
-  copy_segments_kernel<<<dim3(4, njobs), 256, 0, st>>>(d_jobs, src, dst);
+  copy_segments_kernel<<<njobs, 256, 0, st>>>(d_jobs, src, dst);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

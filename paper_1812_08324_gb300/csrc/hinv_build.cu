@@ -81,9 +81,9 @@ __device__ __forceinline__ double urand(unsigned long long key) {
 // rows [r0, r0 + n) of a row-major block of S columns get seeded uniform values
 struct FillJob { double* buf; int r0, n, S; unsigned long long seed; };
 __global__ void fill_kernel(const FillJob* jobs, int njobs) {
-  const FillJob J = jobs[blockIdx.y];
+  const FillJob J = jobs[blockIdx.x];
   const int64_t total = (int64_t)J.n * J.S;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
     const int64_t i = J.r0 + e / J.S, c = e % J.S;
     J.buf[i * J.S + c] = urand(J.seed * 0x100000001B3ull + (unsigned long long)(i * HINV_MAXS + c));
   }
@@ -503,9 +503,9 @@ __global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Co
 // column stride ld, zeros elsewhere (padding rows included)
 struct LeafCopy { const double* src; int64_t sld; double* dst; int ld, m, lower; };
 __global__ void leaf_copy_kernel(const LeafCopy* jobs) {
-  const LeafCopy J = jobs[blockIdx.y];
+  const LeafCopy J = jobs[blockIdx.x];
   const int64_t total = (int64_t)J.m * J.ld;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
     const int j = (int)(e / J.ld), i = (int)(e % J.ld);
     const bool keep = i < J.m && (J.lower ? j <= i : j >= i);
     J.dst[e] = keep ? J.src[(int64_t)i * J.sld + j] : 0.0;
@@ -790,7 +790,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     LeafCopy* d_lc = nullptr;
     HM_TRY(upload(&d_lc, lc));
     count_launches(1);
-    leaf_copy_kernel<<<dim3(16, (unsigned)lc.size()), 256, 0, st>>>(d_lc);
+    leaf_copy_kernel<<<(unsigned)lc.size(), 256, 0, st>>>(d_lc);
   }
   // ---- construction plans, level by level (deepest first), both triangles
   Planner PL;
@@ -1021,7 +1021,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     const int t = S.tri;
     if (!S.fill.empty()) {
       count_launches(1);
-      fill_kernel<<<dim3(32, (unsigned)S.fill.size()), 256, 0, st>>>(d_fill + fill_off[k], (int)S.fill.size());
+      fill_kernel<<<(unsigned)S.fill.size(), 256, 0, st>>>(d_fill + fill_off[k], (int)S.fill.size());
     }
     run_mr(S.mr[0], bufA[t], bufB[t]);   // X Omega          (source rows)
     run_mr(S.mr[1], bufB[t], bufA[t]);   // T_off X Omega    (target rows)
