@@ -2,7 +2,8 @@
 
 One bench *step* is one pass of the whole hot path over one synthetic input:
 H-matrix assembly (tables, near field, ACA), H-LU of I - dt/2 G, and the full
-CN run (H-matvec right-hand side, H-LU solve, FP64 refinement sweep) of the
+CN run (each step one pair of triangular solves on v = u^n + u^{n+1}, plus
+an H-matvec residual and a solve pair per FP64 refinement sweep) of the
 1D full Levy generator workload (N = 65536, drift 0.3, sigma 0.2, alpha-stable
 alpha = 1.5 truncated to |y| <= 2, leaf 256, ACA rank <= 32, 1000 CN steps,
 dt = 1e-3).  The metric is unknown-steps/s = N * CN steps / time.
@@ -56,6 +57,9 @@ def parse():
                     help="storage of what the triangular solves read (the mixed modes refine in FP64)")
     ap.add_argument("--solve", default="auto", choices=["auto", "hinv", "subst"],
                     help="triangular solves: hierarchical inverses (1D default) or substitution")
+    ap.add_argument("--cn-form", default="identity", choices=["identity", "literal"],
+                    help="CN step as (I - dt/2 G) v = 2u^n, u^{n+1} = v - u^n (no H-matvec), or with the "
+                         "H-matvec right-hand side as the scheme is written")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "frac_lap_2d_256x256_s0.75",
                                                              "frac_lap_2d_256x256_s0.3", "levy_batch", "serve",
                                                              "lshape"])
@@ -140,14 +144,15 @@ def aggregate(ms_local: float, units_local: float, world: int, device: str = "cp
     return ms, world * units_local / (ms * 1e-3)
 
 
-def workload(refine=0, name=WORKLOAD, precision="fp64", solve="auto"):
+def workload(refine=0, name=WORKLOAD, precision="fp64", solve="auto", cn_form="identity"):
     from paper_1812_08324_gb300 import workloads as W
     prob, opts, dt, steps, kind = W.WORKLOADS[name]
     # the factors' low-rank blocks are capped at rank 16 or at the ACA ranks
     # if larger (1D: ACA ranks <= 9; 2D at ACA 1e-8: <= 25)
     if refine is None:
         refine = 0 if precision == "fp64" else 1
-    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=refine, precision=precision, solve=solve)
+    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=refine, precision=precision, solve=solve,
+                cn_form=cn_form)
     return prob, opts, dt, steps, kind
 
 
@@ -252,7 +257,8 @@ def run_batch(args):
     dt = W.LEVY_BATCH_DT
     cn_steps = args.cn_steps or W.LEVY_BATCH_STEPS
     refine = args.refine if args.refine is not None else (0 if args.precision == "fp64" else 1)
-    batch = [(p, dict(o, refine_max=refine, precision=args.precision, solve=args.solve)) for p, o in batch]
+    batch = [(p, dict(o, refine_max=refine, precision=args.precision, solve=args.solve, cn_form=args.cn_form))
+             for p, o in batch]
     leafs = autotune.tune_batch(batch, dt, cn_steps, probe_steps=3)
     batch = [(p, dict(o, leaf=l)) for (p, o), l in zip(batch, leafs)]
     ns = [p["n"][0] for p, _ in batch]
@@ -367,7 +373,7 @@ def run_batch(args):
             "config": {"workload": f"levy_batch x{len(batch)} (splitmix64 seed 0)", "sum_N": int(sum(ns)),
                        "cn_steps": cn_steps, "dt": dt, "leafs": {str(l): leafs.count(l) for l in sorted(set(leafs))},
                        "groups": len(groups), "group_unknowns_max": args.group_unknowns,
-                       "refine_sweeps": refine, "precision": args.precision, "solve": args.solve,
+                       "refine_sweeps": refine, "precision": args.precision, "solve": args.solve, "cn_form": args.cn_form,
                        "parallelism": f"replicas x{world}", "cuda_graph": graphed,
                        "l2": "working set (H + factors of all problems) exceeds L2; no flush needed"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
@@ -593,7 +599,7 @@ def main():
     from paper_1812_08324_gb300 import workloads as W
 
     name = args.workload
-    prob, opts, dt, cn_steps, kind = workload(args.refine, name, args.precision, args.solve)
+    prob, opts, dt, cn_steps, kind = workload(args.refine, name, args.precision, args.solve, args.cn_form)
     if args.cn_steps:
         cn_steps = args.cn_steps
     N = prob["n"][0] * (prob["n"][1] if prob["dim"] == 2 else 1)
@@ -716,7 +722,7 @@ def main():
     sv_gbs = st["lu_bytes"] / (sv_ms * 1e-3) / 1e9
     hinv = st["solve_mode"] == 2
     sweeps = opts["refine_max"]
-    n_mv = cn_steps * (1 if sweeps == 0 else sweeps)
+    n_mv = cn_steps * (sweeps + (1 if opts["cn_form"] == "literal" else 0))
     n_sv = cn_steps * (1 + sweeps)
     mv_roof = {"kernel": "H-matvec (vt_kernel + vt_reduce + rows_kernel)", "bound": "hbm", "achieved": mv_gbs,
                "peak": hbm, "unit": "GB/s", "frac": mv_gbs / hbm, "traffic": None,
@@ -748,7 +754,7 @@ def main():
             "config": {"workload": name, "N": N, "cn_steps": cn_steps, "dt": dt, "leaf": opts["leaf"],
                        "aca_tol": opts["aca_tol"], "max_rank": opts["max_rank"],
                        "lu_max_rank": opts["lu_max_rank"], "refine_sweeps": opts["refine_max"],
-                       "precision": opts["precision"], "solve": opts["solve"],
+                       "precision": opts["precision"], "solve": opts["solve"], "cn_form": opts["cn_form"],
                        "parallelism": f"replicas x{world}",
                        "l2": f"working set (H + factors, {(st['h_bytes'] + st['lu_bytes']) / 1e9:.1f} GB) "
                              "exceeds L2; no flush needed"},

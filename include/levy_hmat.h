@@ -67,6 +67,18 @@ extern "C" {
 #define HM_SOLVE_SUBST 1  /* block forward/backward substitution over solve blocks (dataflow executor) */
 #define HM_SOLVE_HINV 2   /* products with hierarchical inverses of the factors (1D problems only) */
 
+/* hm_opts.cn_form: how a Crank-Nicolson step is arranged (Sec. "Crank Nicolson
+ * Scheme Based on H-matrix", Eq. scheme: (I - theta G) u^{n+1} = (I + theta G) u^n
+ * + theta (f^n + f^{n+1}), theta = dt/2).  Both compute the same scheme.
+ *  HM_CN_IDENTITY: since I + theta G = 2I - (I - theta G), the scheme is
+ *    (I - theta G) v = w with v = u^n + u^{n+1}, w = 2u^n + theta (f^n + f^{n+1});
+ *    v = (LU)^{-1} w, u^{n+1} = v - u^n.  Needs no H-matvec without refinement
+ *    sweeps; each sweep refines v against the FP64 H-matvec residual w - Mv.
+ *  HM_CN_LITERAL: the right-hand side (I + theta G) u^n + theta (f^n + f^{n+1})
+ *    by the H-matvec, u^{n+1} = (LU)^{-1} rhs; sweeps refine u^{n+1}. */
+#define HM_CN_IDENTITY 0
+#define HM_CN_LITERAL 1
+
 /*
  * Problem (Sec. "Model Problem"; Sec. "Singular and/or Slow Decaying Levy Measure").
  * Interior grid: n[d] points per axis strictly inside [lo[d], hi[d]], spacing
@@ -121,6 +133,7 @@ typedef struct hm_opts {
                         1D problems of at least 32768 unknowns) */
   double hinv_tol;   /* HM_SOLVE_HINV: relative truncation of the inverse blocks (0 = 1e-2 lu_tol
                         for HM_FP64, 1e-7 for HM_MIXED_FP32, 2e-3 for HM_MIXED_BF16) */
+  int cn_form;       /* HM_CN_IDENTITY (default) or HM_CN_LITERAL */
 } hm_opts;
 
 typedef struct hm_matrix hm_matrix;    /* opaque: H-matrix of G on the device */

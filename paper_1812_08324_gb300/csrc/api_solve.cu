@@ -189,33 +189,32 @@ __global__ void sub_kernel(int N, const double* x, double* y) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) y[i] = y[i] - x[i];
 }
 
-// One CN step on Morton-order vectors: u1 = CN(u0) with forcing f0, f1 (may be null).
-//  refine_max = 0: rhs = u + theta G u + theta (f^n + f^{n+1}) by the H-matvec,
-//                  u1 = (LU)^{-1} rhs (Eq. scheme as written).
-//  refine_max = R > 0: with w = 2u + theta (f^n + f^{n+1}) the scheme reads
-//                  M v = w for v = u^n + u^{n+1}, M = I - theta G (because
-//                  I + theta G = 2I - M): v = (LU)^{-1} w, then R sweeps
-//                  v += (LU)^{-1} (w - M v) with the FP64 H-matvec residual
-//                  (the H-LU as preconditioner), and u1 = v - u.  One H-matvec
-//                  per sweep: the cheap (e.g. low-precision) solve carries
-//                  the step and the FP64 residual sets its accuracy.
+// One CN step on Morton-order vectors: u1 = CN(u0) with forcing f0, f1 (may be
+// null), M = I - theta G, R = refine_max sweeps (the H-LU as preconditioner,
+// the FP64 H-matvec residual setting the accuracy).
+//  HM_CN_IDENTITY: I + theta G = 2I - M, so the scheme reads M v = w for
+//    v = u^n + u^{n+1}, w = 2u + theta (f^n + f^{n+1}): v = (LU)^{-1} w, R sweeps
+//    v += (LU)^{-1} (w - M v), u1 = v - u.  No H-matvec unless R > 0.
+//  HM_CN_LITERAL: rhs = u + theta G u + theta (f^n + f^{n+1}) by the H-matvec
+//    (Eq. scheme as written), u1 = (LU)^{-1} rhs, R sweeps u1 += (LU)^{-1}
+//    (rhs - M u1).
 int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u0,
                    const double* f0, const double* f1, double* u1, cudaStream_t st) {
   const int N = H->plan.N;
   const double th = 0.5 * dt;
-  double* rhs = F->d_vec;
+  double* w = F->d_vec;  // right-hand side of M x = w: x = v (identity) or u1 (literal)
   double* s = F->d_vec + (size_t)N;
   const int sweeps = H->opts.refine_max;
-  if (sweeps == 0) {
-    HM_TRY(hm_matvec_morton(H, 1.0, th, u0, th, f0, f1, nullptr, rhs, st));
-    return solve_morton(F, rhs, u1, st);
+  const bool literal = H->opts.cn_form == HM_CN_LITERAL;
+  if (literal) {
+    HM_TRY(hm_matvec_morton(H, 1.0, th, u0, th, f0, f1, nullptr, w, st));
+  } else {
+    count_launches(1);
+    cn_w_kernel<<<vgrid(N), 256, 0, st>>>(N, u0, th, f0, f1, w);
   }
-  double* w = rhs;
-  count_launches(1);
-  cn_w_kernel<<<vgrid(N), 256, 0, st>>>(N, u0, th, f0, f1, w);
-  HM_TRY(solve_morton(F, w, u1, st));  // v, kept in u1
+  HM_TRY(solve_morton(F, w, u1, st));  // x, kept in u1
   for (int it = 0; it < sweeps; ++it) {
-    // s = w - (v - theta G v)
+    // s = w - (x - theta G x)
     HM_TRY(hm_matvec_morton(H, -1.0, th, u1, 0.0, nullptr, nullptr, w, s, st));
     if (it == sweeps - 1) {
       count_launches(1);
@@ -225,6 +224,7 @@ int cn_step_morton(const hm_matrix* H, hm_factors* F, double dt, const double* u
     count_launches(1);
     axpy_kernel<<<vgrid(N), 256, 0, st>>>(N, 1.0, s, u1);
   }
+  if (literal) return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
   count_launches(1);
   sub_kernel<<<vgrid(N), 256, 0, st>>>(N, u0, u1);  // u1 = v - u0
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
@@ -453,10 +453,11 @@ struct hm_batch {
   std::vector<const hm_factors*> F;
   std::vector<double*> state;
   int refine = 0;
+  bool literal = false;        // HM_CN_LITERAL (all problems share cn_form)
   DevSchedule sched;           // merged substitution schedule of the HM_SOLVE_SUBST problems
   hm::HinvBatch hL, hU;        // the HM_SOLVE_HINV problems: L^{-1}, then U^{-1} of every one
   hm::MvBatch A{}, B{};
-  hm::DevJobs<hm::VecJob> rhs_in, w_in, s_in, z_out, z_u1, u1_add, u1_out;
+  hm::DevJobs<hm::VecJob> rhs_in, w_in, w_solve, s_in, z_out, z_u1, z_v, u1_add, u1_out, u1_copy;
   std::vector<void*> allocs;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev = nullptr;
@@ -479,24 +480,32 @@ int batch_solve(hm_batch* B, cudaStream_t cs) {
 }
 
 int batch_one_step(hm_batch* B, cudaStream_t cs) {
-  if (B->refine == 0) {
+  if (B->literal) {
+    // rhs = x + th G x, u1 = (LU)^{-1} rhs, sweeps u1 += (LU)^{-1} (rhs - M u1)
     HM_TRY(launch_matvec_batch(B->A, cs));
     HM_TRY(launch_vec_batch(B->rhs_in, cs));
     HM_TRY(batch_solve(B, cs));
-    return launch_vec_batch(B->z_out, cs);
+    if (B->refine == 0) return launch_vec_batch(B->z_out, cs);
+    HM_TRY(launch_vec_batch(B->z_u1, cs));
+  } else if (B->refine == 0) {
+    // the solve's input 2 x, then x = z - x with z = (LU)^{-1} (2 x)
+    HM_TRY(launch_vec_batch(B->w_solve, cs));
+    HM_TRY(batch_solve(B, cs));
+    return launch_vec_batch(B->z_v, cs);
+  } else {
+    // w = 2 x (kept in rhs and given to the solve), v = (LU)^{-1} w in u1
+    HM_TRY(launch_vec_batch(B->w_in, cs));
+    HM_TRY(batch_solve(B, cs));
+    HM_TRY(launch_vec_batch(B->z_u1, cs));
   }
-  // w = 2 x (kept in rhs and given to the solve), v = (LU)^{-1} w in u1,
-  // sweeps v += (LU)^{-1} (w - M v), x = v - x (as cn_step_morton)
-  HM_TRY(launch_vec_batch(B->w_in, cs));
-  HM_TRY(batch_solve(B, cs));
-  HM_TRY(launch_vec_batch(B->z_u1, cs));
   for (int it = 0; it < B->refine; ++it) {
     HM_TRY(launch_matvec_batch(B->B, cs));
     HM_TRY(launch_vec_batch(B->s_in, cs));
     HM_TRY(batch_solve(B, cs));
     HM_TRY(launch_vec_batch(B->u1_add, cs));
   }
-  return launch_vec_batch(B->u1_out, cs);
+  // identity: x = v - x; literal: x = u1
+  return launch_vec_batch(B->literal ? B->u1_copy : B->u1_out, cs);
 }
 
 }  // namespace
@@ -954,6 +963,7 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
       return HM_ERR_ARG;
     }
     if (Hs[i]->opts.refine_max != R) { set_error("all matrices must share refine_max"); return HM_ERR_ARG; }
+    if (Hs[i]->opts.cn_form != Hs[0]->opts.cn_form) { set_error("all matrices must share cn_form"); return HM_ERR_ARG; }
     for (int j = 0; j < i; ++j)
       if (Hs[j] == Hs[i] || Fs[j] == Fs[i]) { set_error("matrices and factors must be distinct"); return HM_ERR_ARG; }
   }
@@ -961,6 +971,7 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   B->H.assign(Hs, Hs + count);
   B->F.assign(Fs, Fs + count);
   B->refine = R;
+  B->literal = Hs[0]->opts.cn_form == HM_CN_LITERAL;
   auto fail = [&](int s) {
     hm_batch_free(B);
     return s;
@@ -995,7 +1006,7 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
   // per problem: Morton-order state x (owned by the batch), rhs, residual,
   // refined iterate, solve output z
   std::vector<MvJob> jA(count), jB(count);
-  std::vector<VecJob> rhs_in, w_in, s_in, z_out, z_u1, u1_add, u1_out;
+  std::vector<VecJob> rhs_in, w_in, w_solve, s_in, z_out, z_u1, z_v, u1_add, u1_out, u1_copy;
   for (int i = 0; i < count; ++i) {
     const hm_matrix* H = Hs[i];
     hm_factors* F = const_cast<hm_factors*>(Fs[i]);
@@ -1012,17 +1023,23 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
     rhs_in.push_back({rhs, F->d_y, 0.0, N, 0});
     w_in.push_back({x, rhs, 0.0, N, 2});      // w = 2 x
     w_in.push_back({x, F->d_y, 0.0, N, 2});   // the solve's input
+    w_solve.push_back({x, F->d_y, 0.0, N, 2});
     s_in.push_back({res, F->d_y, 0.0, N, 0});
     z_out.push_back({z, x, 0.0, N, 0});
     z_u1.push_back({z, u1, 0.0, N, 0});
+    z_v.push_back({z, x, 0.0, N, 3});         // x = v - x, v the solve's output
     u1_add.push_back({z, u1, 1.0, N, 1});
     u1_out.push_back({u1, x, 0.0, N, 3});     // x = v - x
+    u1_copy.push_back({u1, x, 0.0, N, 0});
   }
   auto vblocks = [](const VecJob& J) { return (J.n + VEC_CHUNK - 1) / VEC_CHUNK; };
   if ((s = upload_mv_batch(jA, B->A, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_mv_batch(jB, B->B, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(rhs_in, vblocks, B->rhs_in, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(w_in, vblocks, B->w_in, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(w_solve, vblocks, B->w_solve, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(z_v, vblocks, B->z_v, B->allocs)) != HM_OK) return fail(s);
+  if ((s = upload_jobs(u1_copy, vblocks, B->u1_copy, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(s_in, vblocks, B->s_in, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(z_out, vblocks, B->z_out, B->allocs)) != HM_OK) return fail(s);
   if ((s = upload_jobs(z_u1, vblocks, B->z_u1, B->allocs)) != HM_OK) return fail(s);

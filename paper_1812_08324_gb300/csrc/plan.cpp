@@ -171,6 +171,7 @@ int make_plan(const hm_problem& p, const hm_opts& o, Plan& P, std::string& err) 
   }
   if (o.solve_block < 0) { err = "solve_block must be >= 0"; return HM_ERR_ARG; }
   if (!(o.hinv_tol >= 0.0 && o.hinv_tol < 1.0)) { err = "hinv_tol must lie in [0, 1)"; return HM_ERR_ARG; }
+  if (o.cn_form != HM_CN_IDENTITY && o.cn_form != HM_CN_LITERAL) { err = "unknown cn_form"; return HM_ERR_ARG; }
   const bool hinv_ok = p.dim == 1 && p.domain == HM_DOMAIN_BOX && o.leaf <= 1024;
   if (o.solve == HM_SOLVE_HINV && !hinv_ok) {
     err = "HM_SOLVE_HINV needs a 1D problem and leaves of at most 1024 points";

@@ -22,6 +22,8 @@ HM_SOLVE_AUTO, HM_SOLVE_SUBST, HM_SOLVE_HINV = 0, 1, 2
 PRECISIONS = {"fp64": HM_FP64, "fp32": HM_MIXED_FP32, "mixed_fp32": HM_MIXED_FP32, "bf16": HM_MIXED_BF16,
               "mixed_bf16": HM_MIXED_BF16}
 SOLVES = {"auto": HM_SOLVE_AUTO, "subst": HM_SOLVE_SUBST, "hinv": HM_SOLVE_HINV}
+HM_CN_IDENTITY, HM_CN_LITERAL = 0, 1
+CN_FORMS = {"identity": HM_CN_IDENTITY, "literal": HM_CN_LITERAL}
 HM_DOMAIN_BOX, HM_DOMAIN_L = 0, 1
 
 EXPORTED = [
@@ -44,7 +46,8 @@ class Opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("eta", C.c_double), ("aca_tol", C.c_double),
                 ("max_rank", C.c_int), ("lu_tol", C.c_double), ("lu_max_rank", C.c_int),
                 ("precision", C.c_int), ("refine_tol", C.c_double), ("refine_max", C.c_int),
-                ("solve", C.c_int), ("solve_block", C.c_int), ("hinv_tol", C.c_double)]
+                ("solve", C.c_int), ("solve_block", C.c_int), ("hinv_tol", C.c_double),
+                ("cn_form", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -177,6 +180,8 @@ def make_opts(o: dict) -> Opts:
     s.solve = SOLVES[solve] if isinstance(solve, str) else int(solve)
     s.solve_block = int(o.get("solve_block", 0))
     s.hinv_tol = float(o.get("hinv_tol", 0.0))
+    form = o.get("cn_form", "identity")
+    s.cn_form = CN_FORMS[form] if isinstance(form, str) else int(form)
     return s
 
 

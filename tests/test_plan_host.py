@@ -185,6 +185,10 @@ def test_precision_and_solve_options_are_checked():
         hmat.plan_info(p1, W.default_opts(leaf=32, hinv_tol=1.5))
     with pytest.raises(hmat.HMError):
         hmat.plan_info(p1, W.default_opts(leaf=32, solve_block=-1))
+    for form in ("identity", "literal"):
+        hmat.plan_info(p1, W.default_opts(leaf=32, cn_form=form))
+    with pytest.raises(hmat.HMError):
+        hmat.plan_info(p1, W.default_opts(leaf=32, cn_form=2))
 
 
 def test_solve_block_option_changes_the_substitution_plan():

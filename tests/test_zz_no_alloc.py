@@ -2,9 +2,12 @@
 memory at call time (fixed-budget servers, code where cudaMalloc would
 synchronise the device or is not allowed).  Its scratch is a fixed array
 inside the library; this checks, through the C ABI, that two calls in a row
-give the same result as hm_matvec, and that a problem too large for the
-fixed scratch is refused with a clear error.  Collected last on purpose."""
+give the same result as hm_matvec, that host threads racing on the first
+call (the scratch address is looked up and cached then) all get the right
+product, and that a problem too large for the fixed scratch is refused with a
+clear error.  Collected last on purpose."""
 import ctypes
+import threading
 
 import numpy as np
 import pytest
@@ -33,6 +36,46 @@ def _noalloc(H, x, y, alpha, beta, gamma, w1, w2):
                               ctypes.c_void_p(y.data_ptr()),
                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     hmat._check(s)
+
+
+def test_threads_racing_on_the_first_call():
+    """Eight host threads make the process's first hm_matvec_noalloc calls at
+    the same moment (ctypes releases the GIL, so the address lookup and its
+    cache race for real).  They share one stream, as the header asks of calls
+    that share the scratch, so the products are serialised on the GPU: each
+    must equal hm_matvec's."""
+    name, prob, opts = CASES[0]
+    H = hmat.HMatrix(prob, opts)
+    N = H.n
+    rng = np.random.default_rng(11)
+    xs = [dev(rng.standard_normal(N)) for _ in range(8)]
+    refs = [host(H.matvec(x, alpha=1.0, beta=-1e-3, gamma=0.0, w1=x, w2=x)) for x in xs]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    gate = threading.Barrier(len(xs))
+    errors = []
+
+    def work(i):
+        try:
+            gate.wait()
+            with torch.cuda.stream(stream):
+                _noalloc(H, xs[i], ys[i], 1.0, -1e-3, 0.0, xs[i], xs[i])
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(xs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    assert not errors, errors
+    torch.cuda.synchronize()
+    for i, (y, ref) in enumerate(zip(ys, refs)):
+        got = host(y)
+        assert np.all(np.isfinite(got)), i
+        assert np.max(np.abs(got - ref)) <= 1e-13 * (np.max(np.abs(ref)) + 1e-300), i
+    H.sync()
 
 
 @pytest.mark.parametrize("name,prob,opts", CASES, ids=[c[0] for c in CASES])
