@@ -488,7 +488,8 @@ int batch_one_step(hm_batch* B, cudaStream_t cs) {
     if (B->refine == 0) return launch_vec_batch(B->z_out, cs);
     HM_TRY(launch_vec_batch(B->z_u1, cs));
   } else if (B->refine == 0) {
-    // the solve's input 2 x, then x = z - x with z = (LU)^{-1} (2 x)
+    // the solve's input 2 x, then x = z - x with z = (LU)^{-1} (2 x) (the
+    // hierarchical-inverse members do both inside their products)
     HM_TRY(launch_vec_batch(B->w_solve, cs));
     HM_TRY(batch_solve(B, cs));
     return launch_vec_batch(B->z_v, cs);
@@ -991,14 +992,24 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
     s = upload_schedules(parts, B->sched, B->allocs, SOLVE_MODE_THROUGHPUT, true);
     if (s != HM_OK) { set_error("batched solve schedule upload failed"); return fail(s); }
   }
+  // the unrefined identity form fuses its vector steps into the inverses'
+  // products: v = (LU)^{-1} (2x) = 2 (LU)^{-1} x exactly (a power of two), so
+  // L^{-1} reads the state x and U^{-1} writes x = 2 z - x in place
+  const bool fused = !B->literal && R == 0;
   {
     std::vector<HinvJob> jl, ju;
     for (int i = 0; i < count; ++i) {
       const hm_factors* F = Fs[i];
       if (F->solve_mode != HM_SOLVE_HINV) continue;
       const int N = Hs[i]->plan.N;
-      jl.push_back(HinvJob{F->hinv->tri[0].A, F->d_y, F->hinv->d_y});
-      ju.push_back(HinvJob{F->hinv->tri[1].A, F->hinv->d_y, F->d_sv + (size_t)N});
+      double* x = F->d_vec + 3 * (size_t)N;
+      if (fused) {
+        jl.push_back(HinvJob{F->hinv->tri[0].A, x, F->hinv->d_y, nullptr, 1.0});
+        ju.push_back(HinvJob{F->hinv->tri[1].A, F->hinv->d_y, x, x, 2.0});
+      } else {
+        jl.push_back(HinvJob{F->hinv->tri[0].A, F->d_y, F->hinv->d_y, nullptr, 1.0});
+        ju.push_back(HinvJob{F->hinv->tri[1].A, F->hinv->d_y, F->d_sv + (size_t)N, nullptr, 1.0});
+      }
     }
     if ((s = upload_hinv_batch(jl, B->hL, B->allocs)) != HM_OK) return fail(s);
     if ((s = upload_hinv_batch(ju, B->hU, B->allocs)) != HM_OK) return fail(s);
@@ -1023,11 +1034,12 @@ int hm_batch_create(const hm_matrix* const* Hs, const hm_factors* const* Fs, con
     rhs_in.push_back({rhs, F->d_y, 0.0, N, 0});
     w_in.push_back({x, rhs, 0.0, N, 2});      // w = 2 x
     w_in.push_back({x, F->d_y, 0.0, N, 2});   // the solve's input
-    w_solve.push_back({x, F->d_y, 0.0, N, 2});
+    const bool own = !fused || F->solve_mode != HM_SOLVE_HINV;  // fused: nothing to do here
+    if (own) w_solve.push_back({x, F->d_y, 0.0, N, 2});
     s_in.push_back({res, F->d_y, 0.0, N, 0});
     z_out.push_back({z, x, 0.0, N, 0});
     z_u1.push_back({z, u1, 0.0, N, 0});
-    z_v.push_back({z, x, 0.0, N, 3});         // x = v - x, v the solve's output
+    if (own) z_v.push_back({z, x, 0.0, N, 3});  // x = v - x, v the solve's output
     u1_add.push_back({z, u1, 1.0, N, 1});
     u1_out.push_back({u1, x, 0.0, N, 3});     // x = v - x
     u1_copy.push_back({u1, x, 0.0, N, 0});

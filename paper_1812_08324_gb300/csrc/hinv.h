@@ -32,7 +32,9 @@ constexpr int HINV_S = 48;      // range-sketch columns
 constexpr int HINV_SP = 64;     // co-range-sketch columns
 constexpr int HINV_KCAP = 40;   // rank cap of an inverse block (ranks that reach it are flagged)
 constexpr int HINV_MAXS = 64;   // widest multi-vector of the construction
-constexpr int HINV_RCH = 32;    // rows per row chunk
+constexpr int HINV_RCH = 32;    // rows per row chunk of the construction
+constexpr int HINV_ACH = 64;    // rows per row chunk of the per-step products (two per lane)
+constexpr int HINV_AWARPS = 4;  // warps per row chunk of the per-step products
 constexpr int HINV_TCH = 256;   // rows per chunk of the per-step V'x products
 constexpr int HINV_MCH = 128;   // rows per chunk of the construction's reductions
 
@@ -44,24 +46,37 @@ constexpr int HINV_MAX_ANC = 24;  // deepest 1D cluster tree the per-step kernel
 // ---- per-step application of one triangular inverse (device tables)
 struct HinvLeaf {     // inverse of a diagonal leaf block: its triangle, column-major, column stride ld
   int r0, m, ld;
-  int anc_begin, anc_end;   // inverse blocks whose target rows contain the leaf
   int64_t off;              // into the leaf pool (elements)
 };
 struct HinvNode {     // inverse block P Q^T of an internal cluster
   int tgt0, tgt_n, src0, src_n;
-  int pld, qld;             // column stride of P (a multiple of 8), row stride of Q (KCAP)
+  int pld, qld;             // column strides (multiples of 8) of P (tgt_n x KCAP) and Q (src_n x KCAP)
   int tch_begin, tch_end;   // its chunks of the per-step V'x products
-  int64_t poff, qoff;       // column-major P (tgt_n x KCAP), row-major Q (src_n x KCAP) in the pools
+  int64_t poff, qoff;       // column-major P and Q in the pools
+};
+// A run of columns multiplied into the rows of one row chunk: of a leaf
+// triangle (vector: the input b) or of an inverse block's P (vector: t).
+struct HinvSeg {
+  int64_t off;              // pool element of column 0 at the chunk's first row
+  int64_t voff;             // vector entry of column 0 (into b or into tvec)
+  int ld, n;                // column stride, columns
+  int kind;                 // 0: leaf triangle, 1: P
+  int a_hi;                 // rows [0, 32) of the chunk read columns [0, a_hi)
+  int b_lo;                 // rows [32, 64) read columns [b_lo, n) (the rest is zero)
+  int pad;
+};
+struct HinvRChunk {   // HINV_ACH rows and their segments (host-balanced over the warps)
+  int row0, nr;
+  int seg_begin, seg_end;
 };
 struct HinvApply {
   int lower;                // 1: L^{-1} (leaf rows read j <= i), 0: U^{-1} (j >= i)
   int prec;                 // HinvPrec of the pools
   int nleaf, nnode, ntch, nrch;
-  const HinvLeaf* leaves;
   const HinvNode* nodes;
-  const int* anc;           // node ids listed per leaf
   const int2* tch;          // (node, first source row offset) per product chunk
-  const int2* rch;          // (leaf, first row offset) per row chunk
+  const HinvRChunk* rch;    // row chunks
+  const HinvSeg* segs;      // their segments
   const void* leaf_pool;
   const void* p_pool;
   const void* q_pool;
@@ -70,11 +85,14 @@ struct HinvApply {
   double* tvec;             // per node: KCAP coefficients
   unsigned* tcount;         // per node: finished chunks (reset by the last one)
 };
-// One triangular inverse applied to a Morton-order vector: y = X b.
+// One triangular inverse applied to a Morton-order vector: y = X b, or, with
+// sub given, y = scale (X b) - sub (y may then alias sub, not b).
 struct HinvJob {
   HinvApply A;
   const double* b;
   double* y;
+  const double* sub;
+  double scale;
 };
 
 // Launchers (hinv_apply.cu).  Single: two launches; batch: two launches for all jobs.

@@ -5,11 +5,13 @@
 //                    + sum_{tau: i in tgt(tau)} P_tau[i, :] (Q_tau^T b[src(tau)])
 //
 //   1. hinv_t_kernel  t_tau = Q_tau^T b[src(tau)]: one CTA per 256-row chunk of
-//                     every source range (Q row-major); the last CTA of a
-//                     block sums the chunks' partials in chunk order
-//   2. hinv_r_kernel  one CTA per 32-row chunk of a leaf, lane per row: the
-//                     leaf's triangle (stored column-major) plus P rows times
-//                     t of every block whose target holds the leaf
+//                     every source range (Q column-major, warp per column);
+//                     the last CTA of a block sums the chunks' partials in
+//                     chunk order
+//   2. hinv_r_kernel  one CTA per 64-row chunk of a leaf, lane per two rows:
+//                     the leaf's triangle (stored column-major) plus P rows
+//                     times t of every block whose target holds the rows,
+//                     split evenly over the warps by host-built column runs
 // Every load is a run of consecutive entries and every entry is read once:
 // the step is bandwidth-bound if the arithmetic keeps up.  GB300 issues FP64
 // at about two multiply-adds per clock per SM, below what these products
@@ -22,17 +24,16 @@
 #include <cuda_bf16.h>
 
 #include "hinv.h"
+#include "hm_device.cuh"
 #include "hm_kernels.h"
 
 namespace hm {
 
 namespace {
 
-// ---- double-float arithmetic (no contraction: every step rounds as written)
-__device__ __forceinline__ float2 df_split(double v) {
-  const float hi = __double2float_rn(v);
-  return make_float2(hi, __double2float_rn(v - (double)hi));
-}
+// ---- double-float arithmetic (no contraction: every step rounds as written;
+// FP64 vector entries are split with integer operations, df_split of
+// hm_device.cuh)
 // s += a x   (a, x and s unevaluated pairs; the lo * lo term is dropped)
 __device__ __forceinline__ void df_mac(float2& s, float2 a, float2 x) {
   const float p = __fmul_rn(a.x, x.x);
@@ -68,7 +69,10 @@ template <> struct Tr<HINV_F64> {
 };
 template <> struct Tr<HINV_DF> {
   using S = float2; using X = float2; using A = float2;
-  static __device__ __forceinline__ X cvt(double v) { return df_split(v); }
+  static __device__ __forceinline__ X cvt(double v) {
+    bool bad = false;  // vector entries are finite
+    return df_split(v, bad);
+  }
   static __device__ __forceinline__ S ld(const S* p) { return __ldg(p); }
   static __device__ __forceinline__ S sz() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ void mac(A& s, S a, X x) { df_mac(s, a, x); }
@@ -97,81 +101,70 @@ template <> struct Tr<HINV_BF16> {
   static __device__ __forceinline__ double fin(A a) { return (double)a; }
 };
 
-constexpr int LEAF_SMEM = 1024;  // largest leaf the row kernel stages
-constexpr int ANC_SMEM = HINV_MAX_ANC;  // blocks above a leaf whose coefficients are staged
+// Warp sum by a fixed xor butterfly; lane 0's result is used.
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_x(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_x(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double shfl_i(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float shfl_i(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float2 shfl_i(float2 v, int l) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+}
+template <int P>
+__device__ __forceinline__ typename Tr<P>::A warp_sum(typename Tr<P>::A a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = Tr<P>::add(a, shfl_x(a, o));
+  return a;
+}
 
-// t_tau = Q_tau^T b over one 256-row chunk (Q row-major, stride KCAP).  Lanes
-// take columns (W = 8, 16 or 32 of them, 32 / W rows at a time), warps take
-// 32-row slices, two accumulators per lane.  The warps' partial sums meet in
-// shared memory (fixed order); the last chunk of a block sums the chunks'
+constexpr int T_WARPS = 8;
+
+// t_tau = Q_tau^T b over one 256-row chunk of the source range.  Q is stored
+// column-major, so a warp reads a column of the chunk as 256 consecutive
+// entries: lane takes rows lane + 32u (u < 8) and holds their b values in
+// registers; warps take columns, two at a time (sixteen loads issued before
+// any is used).  Each column's sum is reduced over the warp by a fixed
+// butterfly and written per chunk; the last chunk of a block sums the chunks'
 // partials in chunk order.  Deterministic.
 template <int P>
-constexpr int t_smem() { return (int)(sizeof(typename Tr<P>::X) * HINV_TCH + sizeof(typename Tr<P>::A) * 32 * HINV_KCAP); }
-template <int P>
-constexpr int r_smem() {
-  return (int)(sizeof(typename Tr<P>::X) * (LEAF_SMEM + ANC_SMEM * HINV_KCAP) + sizeof(typename Tr<P>::A) * 8 * HINV_RCH);
-}
-constexpr int T_SMEM_MAX = 12288, R_SMEM_MAX = 17920;  // the largest of the precisions (FP64 and pairs)
-static_assert(t_smem<HINV_F64>() <= T_SMEM_MAX && t_smem<HINV_DF>() <= T_SMEM_MAX, "t smem");
-static_assert(r_smem<HINV_F64>() <= R_SMEM_MAX && r_smem<HINV_DF>() <= R_SMEM_MAX, "r smem");
-
-template <int P>
-__device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* __restrict__ b, char* sm) {
+__device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* __restrict__ b) {
   using T = Tr<P>;
-  typename T::X* xs = reinterpret_cast<typename T::X*>(sm);
-  auto red = reinterpret_cast<typename T::A(*)[HINV_KCAP]>(sm + sizeof(typename T::X) * HINV_TCH);
   __shared__ int last;
   const int2 tc = H.tch[c];
   const HinvNode nd = H.nodes[tc.x];
   const int k = H.rank[tc.x];
   const int j0 = tc.y, len = min(HINV_TCH, nd.src_n - j0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < len; j += blockDim.x) xs[j] = T::cvt(b[nd.src0 + j0 + j]);
-  __syncthreads();
-  const typename T::S* Q = static_cast<const typename T::S*>(H.q_pool) + nd.qoff + (int64_t)j0 * HINV_KCAP;
-  const int rb = warp * 32, re = min(len, rb + 32);
-  const int W = k <= 8 ? 8 : (k <= 16 ? 16 : 32), G = 32 / W;
-  const int col = lane % W, sub = lane / W;
-  typename T::A a0 = T::zero(), a1 = T::zero();
-  if (col < k) {
-    // all of the lane's rows of the slice (32 / G) are loaded before any is used
-    for (int m0 = 0; m0 < 32 / G; m0 += 16) {
-      typename T::S v[16];
+  typename T::X x[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int r = rb + sub + (m0 + u) * G;
-        v[u] = (m0 + u < 32 / G && r < re) ? T::ld(Q + (int64_t)r * HINV_KCAP + col) : T::sz();
-      }
-#pragma unroll
-      for (int u = 0; u < 16; u += 2) {
-        const int r = rb + sub + (m0 + u) * G;
-        if (m0 + u < 32 / G && r < re) T::mac(a0, v[u], xs[r]);
-        if (m0 + u + 1 < 32 / G && r + G < re) T::mac(a1, v[u + 1], xs[r + G]);
-      }
-    }
+  for (int u = 0; u < 8; ++u) {
+    const int r = lane + 32 * u;
+    x[u] = T::cvt(r < len ? b[nd.src0 + j0 + r] : 0.0);
   }
-  typename T::A a2 = T::zero();  // columns [32, KCAP): 8 lanes per row, 4 rows at a time
-  const int col2 = 32 + (lane & 7), sub2 = lane >> 3;
-  if (k > 32 && col2 < k) {
-    typename T::S v[8];
+  const typename T::S* Q = static_cast<const typename T::S*>(H.q_pool) + nd.qoff + j0 + lane;
+  for (int l = warp; l < k; l += 2 * T_WARPS) {  // warp-uniform
+    const int l2 = l + T_WARPS;
+    typename T::S va[8], vb[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int r = rb + sub2 + 4 * u;
-      v[u] = r < re ? T::ld(Q + (int64_t)r * HINV_KCAP + col2) : T::sz();
+      const bool in = lane + 32 * u < len;
+      va[u] = in ? T::ld(Q + (int64_t)l * nd.qld + 32 * u) : T::sz();
+      vb[u] = (in && l2 < k) ? T::ld(Q + (int64_t)l2 * nd.qld + 32 * u) : T::sz();
     }
+    typename T::A sa = T::zero(), sb = T::zero();
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (rb + sub2 + 4 * u < re) T::mac(a2, v[u], xs[rb + sub2 + 4 * u]);
-  }
-  if (col < k) red[warp * G + sub][col] = T::add(a0, a1);
-  if (k > 32 && col2 < k) red[warp * 4 + sub2][col2] = a2;
-  __syncthreads();
-  if ((int)threadIdx.x < k) {
-    const int l = threadIdx.x;
-    const int ns = l < 32 ? 8 * G : 32;
-    typename T::A s = red[0][l];
-    for (int q = 1; q < ns; ++q) s = T::add(s, red[q][l]);
-    H.tpart[(int64_t)c * HINV_KCAP + l] = T::fin(s);
+    for (int u = 0; u < 8; ++u) {
+      T::mac(sa, va[u], x[u]);
+      T::mac(sb, vb[u], x[u]);
+    }
+    sa = warp_sum<P>(sa);
+    sb = warp_sum<P>(sb);
+    if (lane == 0) {
+      H.tpart[(int64_t)c * HINV_KCAP + l] = T::fin(sa);
+      if (l2 < k) H.tpart[(int64_t)c * HINV_KCAP + l2] = T::fin(sb);
+    }
   }
   __threadfence();
   __syncthreads();
@@ -184,7 +177,7 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
     // warp per column, lanes over the chunks (fixed assignment and tree)
     __threadfence();
     const int nch = nd.tch_end - nd.tch_begin;
-    for (int l = warp; l < k; l += 8) {
+    for (int l = warp; l < k; l += T_WARPS) {
       double s = 0.0;
       for (int cc = lane; cc < nch; cc += 32) s += __ldcg(H.tpart + (int64_t)(nd.tch_begin + cc) * HINV_KCAP + l);
 #pragma unroll
@@ -195,90 +188,77 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
   }
 }
 
-// y rows of one 32-row chunk of a leaf: lane = row, warps split the columns.
-// The leaf inverse and P are stored column-major, so every load is 32
-// consecutive rows of one column.  Dense triangle: the columns that can be
-// nonzero for the chunk's rows (lower: [0, i0 + nr), upper: [i0, m); the
-// zeros inside the chunk's diagonal block are stored); low-rank blocks:
-// (block, half of its columns) items over the warps, their coefficients t
-// staged in shared memory.  The warps' sums meet in shared memory.
+// y rows of one 64-row chunk: lane takes rows lane and lane + 32.  The
+// chunk's column runs (its leaf's triangle against b, then P of every block
+// whose target holds the rows, against t) are split into equal column ranges
+// over the warps (the zeros of a triangle outside the rows' own half are
+// skipped, not read).  Every load is 32 consecutive rows of one column,
+// sixteen issued before any is used; the vector entries of eight columns are
+// loaded and converted by eight lanes and broadcast.  The warps' sums meet in
+// shared memory and are added in warp order.  Deterministic.
 template <int P>
-__device__ __forceinline__ void r_body(const HinvApply& H, int c, const double* __restrict__ b,
-                                       double* __restrict__ y, char* sm) {
+__device__ __forceinline__ void r_body(const HinvApply& H, int c, const double* __restrict__ b, double* y,
+                                       const double* sub, double scale) {
   using T = Tr<P>;
-  typename T::X* bs = reinterpret_cast<typename T::X*>(sm);
-  auto ts = reinterpret_cast<typename T::X(*)[HINV_KCAP]>(sm + sizeof(typename T::X) * LEAF_SMEM);
-  auto part = reinterpret_cast<typename T::A(*)[HINV_RCH]>(sm + sizeof(typename T::X) * (LEAF_SMEM + ANC_SMEM * HINV_KCAP));
-  const int2 rc = H.rch[c];
-  const HinvLeaf L = H.leaves[rc.x];
-  const int i0 = rc.y, nr = min(HINV_RCH, L.m - i0);
+  __shared__ typename T::A part[HINV_AWARPS][HINV_ACH];
+  const HinvRChunk ch = H.rch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int na = L.anc_end - L.anc_begin;
-  for (int j = threadIdx.x; j < L.m; j += blockDim.x) bs[j] = T::cvt(b[L.r0 + j]);
-  for (int e = threadIdx.x; e < na * HINV_KCAP; e += blockDim.x) {
-    const int a = e / HINV_KCAP, l = e % HINV_KCAP;
-    const int q = H.anc[L.anc_begin + a];
-    ts[a][l] = T::cvt(l < H.rank[q] ? H.tvec[(int64_t)q * HINV_KCAP + l] : 0.0);
-  }
-  __syncthreads();
-  typename T::A f0 = T::zero(), f1 = T::zero();
-  if (lane < nr) {
-    const int c0 = H.lower ? 0 : i0, c1 = H.lower ? i0 + nr : L.m;
-    const int span = (c1 - c0 + 7) >> 3;
-    const int jb = c0 + warp * span, je = min(c1, jb + span);
-    const typename T::S* X = static_cast<const typename T::S*>(H.leaf_pool) + L.off + i0 + lane;
-    // blocks of 16 columns: the loads are issued before any is used
-    for (int j0 = jb; j0 < je; j0 += 16) {
-      typename T::S v[16];
+  int total = 0;
+  for (int s = ch.seg_begin; s < ch.seg_end; ++s) total += H.segs[s].n;
+  const int w0 = (int)((int64_t)total * warp / HINV_AWARPS);
+  const int w1 = (int)((int64_t)total * (warp + 1) / HINV_AWARPS);
+  const bool ra = lane < ch.nr, rb = lane + 32 < ch.nr;
+  typename T::A fa = T::zero(), fb = T::zero();
+  int base = 0;
+  for (int s = ch.seg_begin; s < ch.seg_end && base < w1; ++s) {
+    const HinvSeg g = H.segs[s];
+    const int lo = max(w0 - base, 0), hi = min(w1 - base, g.n);
+    base += g.n;
+    if (lo >= hi) continue;
+    const typename T::S* M = static_cast<const typename T::S*>(g.kind ? H.p_pool : H.leaf_pool) + g.off + lane;
+    const double* v = (g.kind ? static_cast<const double*>(H.tvec) : b) + g.voff;
+    for (int j0 = lo; j0 < hi; j0 += 8) {
+      typename T::S va[8], vb[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = j0 + u < je ? T::ld(X + (int64_t)(j0 + u) * L.ld) : T::sz();
-#pragma unroll
-      for (int u = 0; u < 16; u += 2) {
-        if (j0 + u < je) T::mac(f0, v[u], bs[j0 + u]);
-        if (j0 + u + 1 < je) T::mac(f1, v[u + 1], bs[j0 + u + 1]);
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        va[u] = (j < hi && ra && j < g.a_hi) ? T::ld(M + (int64_t)j * g.ld) : T::sz();
+        vb[u] = (j < hi && rb && j >= g.b_lo) ? T::ld(M + (int64_t)j * g.ld + 32) : T::sz();
       }
-    }
-    for (int it = warp; it < 2 * na; it += 8) {
-      const int a = it >> 1;
-      const int q = H.anc[L.anc_begin + a];
-      const HinvNode nd = H.nodes[q];
-      const int k = H.rank[q];
-      const int kh = (k + 1) >> 1;
-      const int lb = (it & 1) ? kh : 0, le = (it & 1) ? k : kh;
-      const typename T::S* Pp = static_cast<const typename T::S*>(H.p_pool) + nd.poff + (L.r0 + i0 + lane - nd.tgt0);
-      for (int l0 = lb; l0 < le; l0 += 16) {
-        typename T::S v[16];
+      const typename T::X xl = T::cvt(lane < 8 && j0 + lane < hi ? __ldg(v + j0 + lane) : 0.0);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = l0 + u < le ? T::ld(Pp + (int64_t)(l0 + u) * nd.pld) : T::sz();
-#pragma unroll
-        for (int u = 0; u < 16; u += 2) {
-          if (l0 + u < le) T::mac(f0, v[u], ts[a][l0 + u]);
-          if (l0 + u + 1 < le) T::mac(f1, v[u + 1], ts[a][l0 + u + 1]);
-        }
+      for (int u = 0; u < 8; ++u) {
+        const typename T::X x = shfl_i(xl, u);
+        T::mac(fa, va[u], x);
+        T::mac(fb, vb[u], x);
       }
     }
   }
-  part[warp][lane] = T::add(f0, f1);
+  part[warp][lane] = fa;
+  part[warp][lane + 32] = fb;
   __syncthreads();
-  if ((int)threadIdx.x < nr) {
+  if ((int)threadIdx.x < ch.nr) {
     const int r = threadIdx.x;
     typename T::A s = part[0][r];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) s = T::add(s, part[w][r]);
-    y[L.r0 + i0 + r] = T::fin(s);
+    for (int w = 1; w < HINV_AWARPS; ++w) s = T::add(s, part[w][r]);
+    double o = T::fin(s);
+    if (sub) o = scale * o - sub[ch.row0 + r];
+    y[ch.row0 + r] = o;
   }
 }
 
+constexpr int R_THREADS = 32 * HINV_AWARPS;
+
 template <int P>
-__global__ void __launch_bounds__(256) hinv_t_kernel(HinvApply H, const double* __restrict__ b) {
-  extern __shared__ __align__(16) char smem_t[];
-  t_body<P>(H, blockIdx.x, b, smem_t);
+__global__ void __launch_bounds__(32 * T_WARPS, 4) hinv_t_kernel(HinvApply H, const double* __restrict__ b) {
+  t_body<P>(H, blockIdx.x, b);
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) hinv_r_kernel(HinvApply H, const double* __restrict__ b, double* y) {
-  extern __shared__ __align__(16) char smem_r[];
-  r_body<P>(H, blockIdx.x, b, y, smem_r);
+__global__ void __launch_bounds__(R_THREADS, 7) hinv_r_kernel(HinvApply H, const double* __restrict__ b, double* y,
+                                                              const double* sub, double scale) {
+  r_body<P>(H, blockIdx.x, b, y, sub, scale);
 }
 
 __device__ __forceinline__ int job_of(const int* off, int count, int blk) {
@@ -290,37 +270,35 @@ __device__ __forceinline__ int job_of(const int* off, int count, int blk) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256) hinv_t_batch_kernel(const HinvJob* jobs, const int* off, int count) {
+__global__ void __launch_bounds__(32 * T_WARPS, 4) hinv_t_batch_kernel(const HinvJob* jobs, const int* off, int count) {
   const int j = job_of(off, count, blockIdx.x);
   const HinvJob& J = jobs[j];
   const int c = blockIdx.x - off[j];
-  extern __shared__ __align__(16) char smem_tb[];
   switch (J.A.prec) {
-    case HINV_F64: t_body<HINV_F64>(J.A, c, J.b, smem_tb); break;
-    case HINV_DF: t_body<HINV_DF>(J.A, c, J.b, smem_tb); break;
-    case HINV_F32: t_body<HINV_F32>(J.A, c, J.b, smem_tb); break;
-    default: t_body<HINV_BF16>(J.A, c, J.b, smem_tb); break;
+    case HINV_F64: t_body<HINV_F64>(J.A, c, J.b); break;
+    case HINV_DF: t_body<HINV_DF>(J.A, c, J.b); break;
+    case HINV_F32: t_body<HINV_F32>(J.A, c, J.b); break;
+    default: t_body<HINV_BF16>(J.A, c, J.b); break;
   }
 }
 
-__global__ void __launch_bounds__(256) hinv_r_batch_kernel(const HinvJob* jobs, const int* off, int count) {
+__global__ void __launch_bounds__(R_THREADS, 7) hinv_r_batch_kernel(const HinvJob* jobs, const int* off, int count) {
   const int j = job_of(off, count, blockIdx.x);
   const HinvJob& J = jobs[j];
   const int c = blockIdx.x - off[j];
-  extern __shared__ __align__(16) char smem_rb[];
   switch (J.A.prec) {
-    case HINV_F64: r_body<HINV_F64>(J.A, c, J.b, J.y, smem_rb); break;
-    case HINV_DF: r_body<HINV_DF>(J.A, c, J.b, J.y, smem_rb); break;
-    case HINV_F32: r_body<HINV_F32>(J.A, c, J.b, J.y, smem_rb); break;
-    default: r_body<HINV_BF16>(J.A, c, J.b, J.y, smem_rb); break;
+    case HINV_F64: r_body<HINV_F64>(J.A, c, J.b, J.y, J.sub, J.scale); break;
+    case HINV_DF: r_body<HINV_DF>(J.A, c, J.b, J.y, J.sub, J.scale); break;
+    case HINV_F32: r_body<HINV_F32>(J.A, c, J.b, J.y, J.sub, J.scale); break;
+    default: r_body<HINV_BF16>(J.A, c, J.b, J.y, J.sub, J.scale); break;
   }
 }
 
 template <int P>
 int launch_typed(const HinvApply& H, const double* b, double* y, cudaStream_t st) {
   count_launches(H.ntch > 0 ? 2 : 1);
-  if (H.ntch > 0) hinv_t_kernel<P><<<H.ntch, 256, t_smem<P>(), st>>>(H, b);
-  hinv_r_kernel<P><<<H.nrch, 256, r_smem<P>(), st>>>(H, b, y);
+  if (H.ntch > 0) hinv_t_kernel<P><<<H.ntch, 32 * T_WARPS, 0, st>>>(H, b);
+  hinv_r_kernel<P><<<H.nrch, R_THREADS, 0, st>>>(H, b, y, nullptr, 1.0);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 
@@ -339,8 +317,8 @@ int launch_hinv_apply(const HinvApply& H, const double* b, double* y, cudaStream
 int launch_hinv_batch(const HinvBatch& B, cudaStream_t st) {
   if (B.count == 0) return HM_OK;
   count_launches(B.total[0] > 0 ? 2 : 1);
-  if (B.total[0] > 0) hinv_t_batch_kernel<<<B.total[0], 256, T_SMEM_MAX, st>>>(B.jobs, B.off[0], B.count);
-  hinv_r_batch_kernel<<<B.total[1], 256, R_SMEM_MAX, st>>>(B.jobs, B.off[1], B.count);
+  if (B.total[0] > 0) hinv_t_batch_kernel<<<B.total[0], 32 * T_WARPS, 0, st>>>(B.jobs, B.off[0], B.count);
+  hinv_r_batch_kernel<<<B.total[1], R_THREADS, 0, st>>>(B.jobs, B.off[1], B.count);
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

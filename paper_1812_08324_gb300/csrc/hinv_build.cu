@@ -473,8 +473,8 @@ __global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tb
   }
 }
 
-// P = -R3[tgt rows][:, piv_k] R_11^{-1} (column-major, column stride ld),
-// Q = C3[src rows] Q_c,k (row-major, row stride ld); zero beyond k
+// P = -R3[tgt rows][:, piv_k] R_11^{-1}, Q = C3[src rows] Q_c,k (both
+// column-major, column stride ld); zero beyond k
 struct FormJob { int which, core, node_row0, nrow, r_lo; double* dst; int ld; const double* src; int S; };
 __global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Core* cores) {
   const FormJob J = jobs[blockIdx.x];
@@ -494,8 +494,7 @@ __global__ void __launch_bounds__(256) form_kernel(const FormJob* jobs, const Co
         for (int c = 0; c < HINV_SP; ++c) s = fma(x[c], K.qc[c * HINV_KCAP + l], s);
       }
     }
-    if (J.which == 0) J.dst[(int64_t)l * J.ld + i] = s;
-    else J.dst[(int64_t)i * J.ld + l] = s;
+    J.dst[(int64_t)l * J.ld + i] = s;
   }
 }
 
@@ -765,11 +764,11 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       Nd.src0 = rs.first;
       Nd.src_n = rs.second - rs.first;
       Nd.pld = round8(Nd.tgt_n);
-      Nd.qld = HINV_KCAP;
+      Nd.qld = round8(Nd.src_n);
       Nd.poff = po;
       Nd.qoff = qo;
       po += (int64_t)Nd.pld * HINV_KCAP;
-      qo += (int64_t)round8(Nd.src_n) * HINV_KCAP;
+      qo += (int64_t)Nd.qld * HINV_KCAP;
     }
     p_elems[tri] = po;
     q_elems[tri] = qo;
@@ -857,7 +856,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
               if (nodes[q].level <= lev || slot[q] >= 0) continue;
               const HinvNode& Q = H.h_nodes[q];
               slot[q] = trans ? PL.red(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, Q.tgt_n, rk + q, HINV_KCAP)
-                              : PL.red(qpool[tri] + Q.qoff, Q.qld, 1, Q.src0, Q.src_n, rk + q, HINV_KCAP);
+                              : PL.red(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, Q.src_n, rk + q, HINV_KCAP);
             }
             for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
               PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
@@ -869,7 +868,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
               for (int q : anc) {
                 if (nodes[q].level <= lev) continue;
                 const HinvNode& Q = H.h_nodes[q];
-                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, Q.qld, 1, Q.src0, rk + q, HINV_KCAP, slot[q])
+                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, rk + q, HINV_KCAP, slot[q])
                               : lr_item(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, rk + q, HINV_KCAP, slot[q]));
               }
             }
@@ -1039,15 +1038,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
   // ---- per-step tables
   for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
     HinvTriangle& H = out.tri[tri];
-    std::vector<int> anc;
-    std::vector<int2> tch, rch;
-    for (int l = 0; l < nl; ++l) {
-      HinvLeaf& L = H.h_leaves[l];
-      L.anc_begin = (int)anc.size();
-      anc.insert(anc.end(), anc_t[tri][l].begin(), anc_t[tri][l].end());
-      L.anc_end = (int)anc.size();
-      for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) rch.push_back(make_int2(l, i0));
-    }
+    std::vector<int2> tch;
     for (int v = 0; v < nn; ++v) {
       HinvNode& Nd = H.h_nodes[v];
       Nd.tch_begin = (int)tch.size();
@@ -1060,12 +1051,9 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     A.nleaf = nl;
     A.nnode = nn;
     A.ntch = (int)tch.size();
-    A.nrch = (int)rch.size();
-    if (s == HM_OK) s = upload((HinvLeaf**)&A.leaves, H.h_leaves);
+    A.nrch = 0;  // the row chunks follow once the ranks are on the host
     if (s == HM_OK) s = upload((HinvNode**)&A.nodes, H.h_nodes);
-    if (s == HM_OK) s = upload((int**)&A.anc, anc);
     if (s == HM_OK) s = upload((int2**)&A.tch, tch);
-    if (s == HM_OK) s = upload((int2**)&A.rch, rch);
     A.leaf_pool = leafpool[tri];
     A.p_pool = ppool[tri];
     A.q_pool = qpool[tri];
@@ -1139,6 +1127,61 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
   for (int tri = 0; tri < 2; ++tri) {
     HinvTriangle& H = out.tri[tri];
     H.h_rank.assign(hr.begin() + tri * nn, hr.begin() + tri * nn + nn);
+    // row chunks of the per-step products and their column runs: the leaf's
+    // triangle (lower: columns [0, i0 + nr), upper: [i0, m)), then P of every
+    // block above the leaf whose target holds it, at its rank
+    std::vector<HinvRChunk> rch;
+    std::vector<HinvSeg> segs;
+    for (int l = 0; l < nl; ++l) {
+      const HinvLeaf& L = H.h_leaves[l];
+      for (int i0 = 0; i0 < L.m; i0 += HINV_ACH) {
+        const int nr = std::min(HINV_ACH, L.m - i0);
+        HinvRChunk C{L.r0 + i0, nr, (int)segs.size(), 0};
+        HinvSeg t{};
+        t.kind = 0;
+        t.ld = L.ld;
+        if (tri == 0) {
+          t.off = L.off + i0;
+          t.voff = L.r0;
+          t.n = i0 + nr;
+          t.a_hi = std::min(t.n, i0 + 32);
+          t.b_lo = 0;
+        } else {
+          t.off = L.off + (int64_t)i0 * L.ld + i0;
+          t.voff = L.r0 + i0;
+          t.n = L.m - i0;
+          t.a_hi = t.n;
+          t.b_lo = 32;
+        }
+        segs.push_back(t);
+        for (int q : anc_t[tri][l]) {
+          const HinvNode& Nd = H.h_nodes[q];
+          const int k = H.h_rank[q];
+          if (k <= 0) continue;
+          HinvSeg g{};
+          g.kind = 1;
+          g.off = Nd.poff + (L.r0 + i0 - Nd.tgt0);
+          g.voff = (int64_t)q * HINV_KCAP;
+          g.ld = Nd.pld;
+          g.n = k;
+          g.a_hi = k;
+          g.b_lo = 0;
+          segs.push_back(g);
+        }
+        C.seg_end = (int)segs.size();
+        rch.push_back(C);
+      }
+    }
+    HinvRChunk* d_rch = nullptr;
+    HinvSeg* d_segs = nullptr;
+    if (s == HM_OK) s = upload(&d_rch, rch);
+    if (s == HM_OK) s = upload(&d_segs, segs);
+    if (s != HM_OK) break;
+    for (HinvApply* A : {&H.A, &H.A64}) {
+      A->nrch = (int)rch.size();
+      A->rch = d_rch;
+      A->segs = d_segs;
+    }
     for (const HinvLeaf& L : H.h_leaves) sb += (int64_t)L.m * (L.m + 1) / 2;
     for (int v = 0; v < nn; ++v) {
       const HinvNode& Nd = H.h_nodes[v];
@@ -1146,6 +1189,10 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       out.max_rank = std::max(out.max_rank, H.h_rank[v]);
       out.capped += H.h_rank[v] >= HINV_KCAP ? 1 : 0;
     }
+  }
+  if (s != HM_OK) {
+    if (err.empty()) err = "row-chunk table upload failed";
+    return s;
   }
   out.step_bytes = sb * (int64_t)es;
   out.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
