@@ -584,7 +584,7 @@ int merge_chunks(std::vector<HluChunk>& ch, std::vector<Wave>& waves, OpGraph& g
       d.clear();
       for (const int* p = c.graph.begin(j); p != c.graph.end(j); ++p)
         if (*p >= base) d.push_back(*p - base);
-      graph.add_op(d);
+      graph.add_op(d, c.graph.prio_of(j));
     }
     std::vector<Wave>().swap(c.waves);
     c.graph.release();

@@ -74,8 +74,9 @@ struct HinvApply {
   int prec;                 // HinvPrec of the pools
   int nleaf, nnode, ntch, nrch;
   const HinvNode* nodes;
-  const int2* tch;          // (node, first source row offset) per product chunk
-  const HinvRChunk* rch;    // row chunks
+  const int4* tch;          // (node, first source row offset, partial slot, -) per product chunk,
+                            // heaviest first; slots run in chunk order per node
+  const HinvRChunk* rch;    // row chunks, heaviest first
   const HinvSeg* segs;      // their segments
   const void* leaf_pool;
   const void* p_pool;

@@ -132,7 +132,7 @@ template <int P>
 __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* __restrict__ b) {
   using T = Tr<P>;
   __shared__ int last;
-  const int2 tc = H.tch[c];
+  const int4 tc = H.tch[c];
   const HinvNode nd = H.nodes[tc.x];
   const int k = H.rank[tc.x];
   const int j0 = tc.y, len = min(HINV_TCH, nd.src_n - j0);
@@ -162,20 +162,23 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
     sa = warp_sum<P>(sa);
     sb = warp_sum<P>(sb);
     if (lane == 0) {
-      H.tpart[(int64_t)c * HINV_KCAP + l] = T::fin(sa);
-      if (l2 < k) H.tpart[(int64_t)c * HINV_KCAP + l2] = T::fin(sb);
+      H.tpart[(int64_t)tc.z * HINV_KCAP + l] = T::fin(sa);
+      if (l2 < k) H.tpart[(int64_t)tc.z * HINV_KCAP + l2] = T::fin(sb);
     }
   }
-  __threadfence();
+  // the CTA's partials are published by one acquire-release count after the
+  // barrier (release is cumulative over what the barrier ordered); the last
+  // chunk's CTA acquires everyone's and sums them
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned n = (unsigned)(nd.tch_end - nd.tch_begin);
-    last = atomicAdd(H.tcount + tc.x, 1u) == n - 1 ? 1 : 0;
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(H.tcount + tc.x) : "memory");
+    last = prev == n - 1 ? 1 : 0;
   }
   __syncthreads();
   if (last) {
     // warp per column, lanes over the chunks (fixed assignment and tree)
-    __threadfence();
     const int nch = nd.tch_end - nd.tch_begin;
     for (int l = warp; l < k; l += T_WARPS) {
       double s = 0.0;

@@ -1038,27 +1038,26 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
   // ---- per-step tables
   for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
     HinvTriangle& H = out.tri[tri];
-    std::vector<int2> tch;
+    int ntch = 0;
     for (int v = 0; v < nn; ++v) {
       HinvNode& Nd = H.h_nodes[v];
-      Nd.tch_begin = (int)tch.size();
-      for (int j0 = 0; j0 < Nd.src_n; j0 += HINV_TCH) tch.push_back(make_int2(v, j0));
-      Nd.tch_end = (int)tch.size();
+      Nd.tch_begin = ntch;
+      ntch += (Nd.src_n + HINV_TCH - 1) / HINV_TCH;
+      Nd.tch_end = ntch;
     }
     HinvApply& A = H.A64;
     A.lower = tri == 0 ? 1 : 0;
     A.prec = HINV_F64;
     A.nleaf = nl;
     A.nnode = nn;
-    A.ntch = (int)tch.size();
-    A.nrch = 0;  // the row chunks follow once the ranks are on the host
+    A.ntch = ntch;
+    A.nrch = 0;  // the chunk tables follow once the ranks are on the host
     if (s == HM_OK) s = upload((HinvNode**)&A.nodes, H.h_nodes);
-    if (s == HM_OK) s = upload((int2**)&A.tch, tch);
     A.leaf_pool = leafpool[tri];
     A.p_pool = ppool[tri];
     A.q_pool = qpool[tri];
     A.rank = d_rank + tri * nn;
-    if (s == HM_OK) s = alloc((void**)&A.tpart, sizeof(double) * HINV_KCAP * std::max<size_t>(tch.size(), 1));
+    if (s == HM_OK) s = alloc((void**)&A.tpart, sizeof(double) * HINV_KCAP * std::max(ntch, 1));
     if (s == HM_OK) s = alloc((void**)&A.tvec, sizeof(double) * HINV_KCAP * std::max(nn, 1));
     if (s == HM_OK) s = alloc((void**)&A.tcount, sizeof(unsigned) * std::max(nn, 1));
     if (s == HM_OK && cudaMemsetAsync(A.tcount, 0, sizeof(unsigned) * std::max(nn, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
@@ -1172,15 +1171,37 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
         rch.push_back(C);
       }
     }
+    // the chunks of one launch are all resident at once; heaviest first, so
+    // that the CTAs handed to each SM mix heavy and light chunks
+    auto rcost = [&](const HinvRChunk& C) {
+      int64_t c = 0;
+      for (int k = C.seg_begin; k < C.seg_end; ++k) c += segs[k].n;
+      return c * (C.nr > 32 ? 2 : 1);
+    };
+    std::stable_sort(rch.begin(), rch.end(),
+                     [&](const HinvRChunk& a, const HinvRChunk& b) { return rcost(a) > rcost(b); });
+    std::vector<int4> tch;
+    for (int v = 0; v < nn; ++v) {
+      const HinvNode& Nd = H.h_nodes[v];
+      for (int j0 = 0, q = Nd.tch_begin; j0 < Nd.src_n; j0 += HINV_TCH, ++q) tch.push_back(make_int4(v, j0, q, 0));
+    }
+    auto tcost = [&](const int4& c) {
+      const HinvNode& Nd = H.h_nodes[c.x];
+      return (int64_t)H.h_rank[c.x] * std::min(HINV_TCH, Nd.src_n - c.y);
+    };
+    std::stable_sort(tch.begin(), tch.end(), [&](const int4& a, const int4& b) { return tcost(a) > tcost(b); });
     HinvRChunk* d_rch = nullptr;
     HinvSeg* d_segs = nullptr;
+    int4* d_tch = nullptr;
     if (s == HM_OK) s = upload(&d_rch, rch);
     if (s == HM_OK) s = upload(&d_segs, segs);
+    if (s == HM_OK) s = upload(&d_tch, tch);
     if (s != HM_OK) break;
     for (HinvApply* A : {&H.A, &H.A64}) {
       A->nrch = (int)rch.size();
       A->rch = d_rch;
       A->segs = d_segs;
+      A->tch = d_tch;
     }
     for (const HinvLeaf& L : H.h_leaves) sb += (int64_t)L.m * (L.m + 1) / 2;
     for (int v = 0; v < nn; ++v) {

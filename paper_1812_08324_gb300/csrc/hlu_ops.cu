@@ -277,12 +277,13 @@ __device__ void dev_lu_base(const LuOp& op, int* err, double* smem) {
 }
 
 // ---- the same base LU in double-float arithmetic on the FP32 pipes (the
-// helpers in hm_device.cuh).  The diagonal leaf LUs are sequential along the
-// diagonal (each waits for the one before it), and FP64 on this GPU costs 64
-// cycles per dependent instruction and a division hundreds; unevaluated float
-// pairs (about 48 significant bits, as the GEMM tiles) keep a pivot step to a
-// few dozen cycles (1D N = 65536: executor 220.9 -> 216.5 ms; HM_LU_FP64=1
-// selects the FP64 version).
+// helpers in hm_device.cuh; HM_LU_DF=1).  Unevaluated float pairs (about 48
+// significant bits, as the GEMM tiles) shorten the pivot steps (1D N = 65536:
+// executor 220.9 -> 216.5 ms) but are not the default: the pivots carry the
+// cancellation between the identity and the stiff part of I - dt/2 G, and
+// their rounding reaches the Crank-Nicolson solution (1D Levy workload at
+// N = 32768, 1000 steps against the dense FP64 oracle: 1.5e-8 with a
+// double-float 64 x 64 base, 7e-9 with FP64, the compression's own error).
 struct LuSmemDD {
   float2 (*A)[LB + 1];
   float2 (*XL)[LB + 1];
@@ -1254,8 +1255,8 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
       switch (T.kind) {
         case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem, a.err); break;
         case TK_LU:
-          if (a.lu[T.op].pad & LU_FP64) dev_lu_base(a.lu[T.op], a.err, smem);
-          else dev_lu_base_dd(a.lu[T.op], a.err, smem);
+          if (a.lu[T.op].pad & LU_DF) dev_lu_base_dd(a.lu[T.op], a.err, smem);
+          else dev_lu_base(a.lu[T.op], a.err, smem);
           break;
         case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
         default: break;
@@ -1342,6 +1343,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   }
   const int nops = off.back();
   std::vector<OpInfo> info(std::max(nops, 1), OpInfo{0, 0, 0, 0});
+  std::vector<int> prio(std::max(nops, 1), 0);
   std::vector<int> deps;
   size_t ndeps = 0;
   for (const SchedPart& P : parts) ndeps += P.graph->flat.size();
@@ -1350,6 +1352,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
     const OpGraph& gr = *parts[p].graph;
     for (int i = 0; i < gr.size(); ++i) {
       const int id = off[p] + i;
+      prio[id] = gr.prio_of(i);
       info[id].dep_begin = (int)deps.size();
       for (const int* d = gr.begin(i); d != gr.end(i); ++d) deps.push_back(*d + off[p]);
       info[id].dep_end = (int)deps.size();
@@ -1365,15 +1368,15 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
   const char* g64 = std::getenv("HM_GEMM_FP64");  // FP64 instead of double-float GEMM tiles
   const bool gemm_fp64 = g64 && g64[0] == '1';
-  const char* l64 = std::getenv("HM_LU_FP64");  // FP64 instead of double-float base LUs
-  const bool lu_fp64 = l64 && l64[0] == '1';
-  // Within a wave the tasks of one kind follow each other, every problem's in
-  // turn.  Tasks are handed out in this order, so the few ops that lie on the
-  // factorisation's dependency chain (the base LUs, truncations, split-K
-  // reductions and copies along the diagonal) come before the wave's many
-  // GEMM tiles: they start as soon as their producers finish instead of
-  // waiting until every tile of the wave has been taken.  Ops of one wave do
-  // not depend on each other, so any order within a wave is a valid one.
+  const char* ldf = std::getenv("HM_LU_DF");  // double-float instead of FP64 base LUs
+  const bool lu_df = ldf && ldf[0] == '1';
+  // Tasks are handed out in this order.  Within a wave they are sorted by the
+  // ops' urgency (OpGraph::prio: for the H-LU the diagonal position at which
+  // the result is first needed), ties by kind (base LUs, truncations, split-K
+  // reductions and copies before GEMM tiles), so that the ops on the
+  // factorisation's dependency chain start as soon as their producers finish
+  // instead of waiting until the wave's far-field work has been taken.  Ops
+  // of one wave do not depend on each other: any order within a wave is valid.
   for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
     for (int kind : {TK_LU, TK_TRUNC, TK_REDUCE, TK_COPY, TK_GEMM, TK_ROWS, TK_VPART}) {
@@ -1395,7 +1398,7 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
             tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k] + o0});
             info[W.lu_id[k] + o0].ntasks = 1;
             LuOp o = W.lu[k];
-            o.pad = lu_fp64 ? LU_FP64 : 0;
+            o.pad = lu_df ? LU_DF : 0;
             l.push_back(o);
           }
         } else if (kind == TK_TRUNC) {
@@ -1440,6 +1443,8 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
         }
       }
     }
+    std::stable_sort(tasks.begin() + wb.back(), tasks.end(),
+                     [&](const Task& x, const Task& y) { return prio[x.id] < prio[y.id]; });
   }
   wb.push_back((int)tasks.size());
   S.nwaves = (int)nw;

@@ -35,10 +35,10 @@ struct LuOp {
   double* Ui;
   int64_t lda, ldl, ldu;
   int m;
-  int pad;       // flags: LU_FP64
+  int pad;       // flags: LU_DF
 };
-// LuOp::pad flag: FP64 base LU instead of double-float (HM_LU_FP64=1)
-constexpr int LU_FP64 = 1;
+// LuOp::pad flag: double-float base LU instead of FP64 (HM_LU_DF=1)
+constexpr int LU_DF = 1;
 
 // Truncation core of a low-rank sum X = A B' (A: m x K, B: n x K) from the
 // Gram matrices GA = A'A, GB = B'B (K x K, row-major): writes TA, TB (K x kf,
@@ -128,6 +128,7 @@ struct VPartOp {
 };
 
 constexpr int LU_BASE = 32;    // leaf LU base-case size (one CTA)
+constexpr int LU_SEG = 32;     // rows per dependency-tracking segment of the factor blocks
 constexpr int TRUNC_MAXK = 96;   // 3 K x K FP64 matrices fit in 227 KB of shared memory
 
 // Operations of one wave (a topological level), with their global op ids.
@@ -157,18 +158,22 @@ struct Wave {
 struct OpGraph {
   std::vector<int> off = std::vector<int>(1, 0);  // producers of op i: flat[off[i] .. off[i+1])
   std::vector<int> flat;
-  int add_op(const std::vector<int>& d) { return add_op(d.data(), d.data() + d.size()); }
-  int add_op(const int* b, const int* e) {
+  std::vector<int> prio;  // per op: urgency, lower first among the tasks of a wave
+  int add_op(const std::vector<int>& d, int p = 0) { return add_op(d.data(), d.data() + d.size(), p); }
+  int add_op(const int* b, const int* e, int p = 0) {
     flat.insert(flat.end(), b, e);
     off.push_back((int)flat.size());
+    prio.push_back(p);
     return (int)off.size() - 2;
   }
   int size() const { return (int)off.size() - 1; }
   const int* begin(int i) const { return flat.data() + off[i]; }
   const int* end(int i) const { return flat.data() + off[i + 1]; }
+  int prio_of(int i) const { return i < (int)prio.size() ? prio[i] : 0; }
   void release() {
     std::vector<int>(1, 0).swap(off);
     std::vector<int>().swap(flat);
+    std::vector<int>().swap(prio);
   }
 };
 

@@ -151,6 +151,7 @@ class Emitter {
   int64_t nops = 0;
   int status = HM_OK;
   int phase = 0;                        // FMA accounting bucket of the ops emitted now
+  int prio = 0;                         // urgency recorded with the ops emitted now (OpGraph::prio)
   double gemm_fma[3] = {0.0, 0.0, 0.0};
 
   View new_mat(int rows, int cols, bool colmajor, int seg = -1, bool scratch = false) {
@@ -298,7 +299,7 @@ class Emitter {
       c.waves.push_back(std::move(waves[w]));
       waves[w] = Wave();
     }
-    for (int i = chunk_first; i < last; ++i) c.graph.add_op(graph.begin(i), graph.end(i));
+    for (int i = chunk_first; i < last; ++i) c.graph.add_op(graph.begin(i), graph.end(i), graph.prio_of(i));
     chunk_first = last;
     chunk_wmin = 1 << 30;
     chunk_cur = std::min(chunk_ops, 2 * chunk_cur);
@@ -341,7 +342,7 @@ class Emitter {
       std::sort(deps.begin(), deps.end());
       deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
     }
-    const int id = graph.add_op(deps);
+    const int id = graph.add_op(deps, prio);
     for (const Acc& a : acc) {
       const View& v = *a.v;
       Tracker::Buf& B = T.bufs[v.buf];
@@ -560,6 +561,7 @@ struct LRState {
   int cur = 0;
   int pend = 0;      // pending columns after the first kf of the current slot
   int m = 0, n = 0;
+  int urg = 0;       // urgency of its recompressions: max(row, column) of the block
   int* rank = nullptr;
 };
 
@@ -577,6 +579,7 @@ class HLU {
   Emitter& E;
   int kf;
   double tol;
+  int lu_base = LU_BASE;          // base-case size of the dense leaf LUs (HM_LU_BASE, <= LU_BASE)
   std::vector<View> dense;        // per dense id: current storage
   std::vector<View> linv, uinv;   // per dense id (diagonal leaves only)
   std::vector<LRState> lr;
@@ -588,6 +591,21 @@ class HLU {
   int nrc(int b) const { return B(b).type == BT_H ? B(b).nrc : 1; }
   int ncc(int b) const { return B(b).type == BT_H ? B(b).ncc : 1; }
   int sub(int b, int i, int j) const { return B(b).type == BT_H ? child(b, i, j) : b; }
+
+  // Urgency of the ops that write (rows ro.., columns co.. of) block b: the
+  // elimination along the diagonal first needs the result when it reaches
+  // the block's later corner, max(row, column).  Among the ops of one wave
+  // the executor hands out the lower values first, so the ops on the
+  // diagonal's dependency chain go ahead of the far-field updates.
+  int urgency(int b, int ro = 0, int co = 0) const {
+    return std::max(P.cl[B(b).t].begin + ro, P.cl[B(b).s].begin + co);
+  }
+  struct Prio {  // sets the emitter's urgency for a scope
+    Emitter& E;
+    int old;
+    Prio(Emitter& e, int p) : E(e), old(e.prio) { E.prio = p; }
+    ~Prio() { E.prio = old; }
+  };
   // offset of child row cluster inside the parent row cluster
   int roff(int parent, int ch) const { return P.cl[B(ch).t].begin - P.cl[B(parent).t].begin; }
   int coff(int parent, int ch) const { return P.cl[B(ch).s].begin - P.cl[B(parent).s].begin; }
@@ -602,6 +620,7 @@ class HLU {
   View lrV(int q) { flush(q); return lr[q].V[lr[q].cur].sub(0, 0, lr[q].n, kf); }
   void flush(int q) {
     if (lr[q].pend > 0) {
+      Prio g(E, lr[q].urg);
       const int K = kf + lr[q].pend;
       lr[q].pend = 0;
       truncate(q, K);
@@ -611,7 +630,7 @@ class HLU {
   // ---- leaf LU with inverses of both factors
   void luinv(const View& Am, const View& Li, const View& Ui) {
     const int m = Am.rows;
-    if (m <= LU_BASE) { E.lu(Am, Li, Ui); return; }
+    if (m <= lu_base) { E.lu(Am, Li, Ui); return; }
     const int h = m / 2, r = m - h;
     View A11 = Am.sub(0, 0, h, h), A12 = Am.sub(0, h, h, r), A21 = Am.sub(h, 0, r, h), A22 = Am.sub(h, h, r, r);
     View Li11 = Li.sub(0, 0, h, h), Li21 = Li.sub(h, 0, r, h), Li12 = Li.sub(0, h, h, r), Li22 = Li.sub(h, h, r, r);
@@ -621,12 +640,14 @@ class HLU {
     E.gemm(T12, 1.0, Li11, A12, 0.0);   // U12 = L11^{-1} A12
     E.gemm(T21, 1.0, A21, Ui11, 0.0);   // L21 = A21 U11^{-1}
     E.gemm(A22, -1.0, T21, T12, 1.0);   // Schur complement
-    luinv(A22, Li22, Ui22);
+    // the halves of the off-diagonal inverse blocks that need no factor of
+    // A22, formed while A22 is factored: one product after its LU, not two
     View X = E.tmp(r, h, false), Y = E.tmp(h, r, false);
-    E.gemm(X, 1.0, T21, Li11, 0.0);
+    E.gemm(X, 1.0, T21, Li11, 0.0);     // L21 L11^{-1}
+    E.gemm(Y, 1.0, Ui11, T12, 0.0);     // U11^{-1} U12
+    luinv(A22, Li22, Ui22);
     E.gemm(Li21, -1.0, Li22, X, 0.0);   // (L^{-1})_21 = -L22^{-1} L21 L11^{-1}
-    E.gemm(Y, 1.0, T12, Ui22, 0.0);
-    E.gemm(Ui12, -1.0, Ui11, Y, 0.0);   // (U^{-1})_12 = -U11^{-1} U12 U22^{-1}
+    E.gemm(Ui12, -1.0, Y, Ui22, 0.0);   // (U^{-1})_12 = -U11^{-1} U12 U22^{-1}
     E.copy(Li12, 0.0, nullptr, 0.0);
     E.copy(Ui21, 0.0, nullptr, 0.0);
     E.release(T12);
@@ -655,6 +676,7 @@ class HLU {
   // ---- tgt += alpha Up Vp'
   void add_lr(const Target& tg, const View& Up, const View& Vp, double alpha) {
     const Block& C = B(tg.b);
+    Prio g(E, urgency(tg.b, tg.ro, tg.co));
     const int w = Up.cols;
     if (w == 0 || tg.nr == 0 || tg.nc == 0) return;
     if (C.type == BT_DENSE) {
@@ -830,6 +852,7 @@ class HLU {
   // ---- X <- L_ll^{-1} X  (X block with the row cluster of l)
   void trsm_l(int l, int x) {
     const Block& X = B(x);
+    Prio g(E, urgency(x));
     if (X.type == BT_DENSE) {
       const Block& L = B(l);
       View Tm = E.new_mat(rows(x), cols(x), false);
@@ -856,6 +879,7 @@ class HLU {
   // ---- X <- X U_uu^{-1}  (X block with the column cluster of u)
   void trsm_u(int u, int x) {
     const Block& X = B(x);
+    Prio g(E, urgency(x));
     if (X.type == BT_DENSE) {
       const Block& U = B(u);
       View Tm = E.new_mat(rows(x), cols(x), false);
@@ -883,6 +907,7 @@ class HLU {
   void mulsub(const Target& tg, int a, int b) {
     const Block& A = B(a);
     const Block& Bb = B(b);
+    Prio g(E, urgency(tg.b, tg.ro, tg.co));
     if (A.type == BT_LR) {
       View W = E.tmp(cols(b), kf, true);
       E.copy(W, 0.0, nullptr, 0.0);
@@ -936,9 +961,10 @@ class HLU {
   void hlu(int b) {
     const Block& X = B(b);
     if (X.type == BT_DENSE) {
+      Prio g(E, urgency(b));
       int m = rows(b);
-      linv[X.id] = E.new_mat(m, m, false, LU_BASE);
-      uinv[X.id] = E.new_mat(m, m, false, LU_BASE);
+      linv[X.id] = E.new_mat(m, m, false, LU_SEG);
+      uinv[X.id] = E.new_mat(m, m, false, LU_SEG);
       luinv(dense[X.id], linv[X.id], uinv[X.id]);
       return;
     }
@@ -973,6 +999,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     E.chunk_cur = std::max<int64_t>(1, out.chunk_ops / 8);
   }
   HLU H(P, E, kf, lu_tol);
+  if (const char* lb = std::getenv("HM_LU_BASE")) H.lu_base = std::max(8, std::min(LU_BASE, std::atoi(lb)));
   const int nd = (int)dd.size(), nl = (int)ld.size();
   H.dense.resize(nd);
   H.linv.resize(nd);
@@ -982,7 +1009,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   for (int d = 0; d < nd; ++d) {
     const DenseDesc& D = dd[d];
     View src = E.wrap(const_cast<double*>(d_dense) + D.off, D.m, D.n, D.ld, 1);
-    View dst = E.new_mat(D.m, D.n, false, LU_BASE);
+    View dst = E.new_mat(D.m, D.n, false, LU_SEG);
     E.copy(dst, theta, &src, 0.0);
     if (D.r0 == D.c0 && alpha != 0.0) {
       View diag = dst;
@@ -998,6 +1025,7 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
     LRState& S = H.lr[q];
     S.m = L.m;
     S.n = L.n;
+    S.urg = std::max(L.r0, L.c0);
     S.rank = d_rank_f + q;
     for (int s = 0; s < 2; ++s) {
       // working slots (factor + pending update columns, ping-pong): scratch when
@@ -1124,8 +1152,8 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
   E.take_chunk();  // the last slice (streaming only)
   if (std::getenv("HM_CRIT") && !E.sink) {
     // planning diagnostic: the longest dependency path of the op graph under
-    // a rough cost model (microseconds: 2 per hand-off, 0.26 k per 32 x 32
-    // GEMM tile, 1.5 m per leaf LU, 0.5 K per truncation) and what it is made of
+    // a rough cost model (microseconds: 2 per hand-off, 0.16 k per 32 x 32
+    // GEMM tile, 0.3 m per base LU, 0.5 K per truncation) and what it is made of
     const int nops = out.graph.size();
     std::vector<int> kind(nops, -1);
     std::vector<double> cost(nops, 0.0);
@@ -1134,12 +1162,12 @@ int plan_hlu(const Plan& P, const std::vector<DenseDesc>& dd, const double* d_de
       for (size_t j = 0; j < W.gemm.size(); ++j) {
         const GemmOp& o = W.gemm[j];
         kind[W.gemm_id[j]] = 0;
-        cost[W.gemm_id[j]] = 2.0 + 0.26 * o.k * (double)std::min(o.m * o.n, 1024) / 1024.0;
+        cost[W.gemm_id[j]] = 2.0 + 0.16 * o.k * (double)std::min(o.m * o.n, 1024) / 1024.0;
         desc[W.gemm_id[j]] = "gemm " + std::to_string(o.m) + "x" + std::to_string(o.n) + "x" + std::to_string(o.k);
       }
       for (size_t j = 0; j < W.lu.size(); ++j) {
         kind[W.lu_id[j]] = 1;
-        cost[W.lu_id[j]] = 2.0 + 1.5 * W.lu[j].m;
+        cost[W.lu_id[j]] = 2.0 + 0.3 * W.lu[j].m;
         desc[W.lu_id[j]] = "lu " + std::to_string(W.lu[j].m);
       }
       for (size_t j = 0; j < W.trunc.size(); ++j) {

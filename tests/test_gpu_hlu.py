@@ -145,20 +145,20 @@ def test_streamed_factor_equals_unstreamed(name, prob, opts, dt, monkeypatch):
 
 @pytest.mark.parametrize("name,prob,opts,dt", CASES, ids=[c[0] for c in CASES])
 def test_double_float_gemm_matches_fp64(name, prob, opts, dt, monkeypatch):
-    """The H-LU's GEMM tiles and leaf LUs in double-float arithmetic (operands
-    split into two floats, 2^-47 relative, sums by two-sum, reciprocals by a
-    Newton step) agree with the same operations in FP64 to far below the
-    compression tolerances (substitution solves: the inverses' own truncation
-    would blur the comparison)."""
+    """The H-LU's GEMM tiles in double-float arithmetic (operands split into
+    two floats, 2^-47 relative, sums by two-sum; the default) and the leaf
+    LUs in double-float (HM_LU_DF=1; FP64 is the default) agree with the same
+    operations in FP64 to far below the compression tolerances (substitution
+    solves: the inverses' own truncation would blur the comparison)."""
     H = hmat.HMatrix(prob, dict(opts, solve="subst"))
     b = dev(np.random.default_rng(4).standard_normal(H.n))
     monkeypatch.setenv("HM_GEMM_FP64", "1")
-    monkeypatch.setenv("HM_LU_FP64", "1")
+    monkeypatch.setenv("HM_LU_DF", "0")
     F0 = H.factor(-0.5 * dt)
     x0 = host(F0.solve(b))
     F0.free()
     monkeypatch.setenv("HM_GEMM_FP64", "0")
-    monkeypatch.setenv("HM_LU_FP64", "0")
+    monkeypatch.setenv("HM_LU_DF", "1")
     F1 = H.factor(-0.5 * dt)
     x1 = host(F1.solve(b))
     F1.free()
