@@ -1370,79 +1370,82 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   const bool gemm_fp64 = g64 && g64[0] == '1';
   const char* ldf = std::getenv("HM_LU_DF");  // double-float instead of FP64 base LUs
   const bool lu_df = ldf && ldf[0] == '1';
-  // Tasks are handed out in this order.  Within a wave they are sorted by the
-  // ops' urgency (OpGraph::prio: for the H-LU the diagonal position at which
-  // the result is first needed), ties by kind (base LUs, truncations, split-K
-  // reductions and copies before GEMM tiles), so that the ops on the
-  // factorisation's dependency chain start as soon as their producers finish
-  // instead of waiting until the wave's far-field work has been taken.  Ops
-  // of one wave do not depend on each other: any order within a wave is valid.
+  // the tasks of one op (kind, index k in its wave's list of that kind)
+  auto emit = [&](size_t p, const Wave& W, int kind, size_t k) {
+    const int o0 = off[p];
+    if (kind == TK_GEMM) {
+      GemmOp o = W.gemm[k];
+      o.shape = gemm_shape(o.m, o.n) | (gemm_fp64 ? GEMM_FP64 : 0);
+      int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k] + o0;
+      for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
+      info[id].ntasks = nt;
+      g.push_back(o);
+    } else if (kind == TK_LU) {
+      tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k] + o0});
+      info[W.lu_id[k] + o0].ntasks = 1;
+      LuOp o = W.lu[k];
+      o.pad = lu_df ? LU_DF : 0;
+      l.push_back(o);
+    } else if (kind == TK_TRUNC) {
+      tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k] + o0});
+      info[W.trunc_id[k] + o0].ntasks = 1;
+      tr.push_back(W.trunc[k]);
+    } else if (kind == TK_COPY) {
+      const CopyOp& o = W.copy[k];
+      int nc = chunks((int64_t)o.m * o.n), id = W.copy_id[k] + o0;
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc, id});
+      info[id].ntasks = nc;
+      c.push_back(o);
+    } else if (kind == TK_REDUCE) {
+      const ReduceOp& o = W.reduce[k];
+      int nc = chunks((int64_t)o.m * o.n * std::max(o.nparts, 1)), id = W.reduce_id[k] + o0;
+      for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
+      info[id].ntasks = nc;
+      r.push_back(o);
+    } else if (kind == TK_ROWS) {
+      RowsOp o = W.rows[k];
+      o.src_begin += soff[p];
+      o.src_end += soff[p];
+      if (restage) plan_rows_staging(o, msrc.data() + o.src_begin, mode);
+      const int id = W.rows_id[k] + o0;
+      tasks.push_back({TK_ROWS, (int)ro.size(), 0, o.nr, id});  // nsub: rows of the chunk
+      info[id].ntasks += 1;  // the chunks of one row op share its id
+      ro.push_back(o);
+    } else {
+      tasks.push_back({TK_VPART, (int)vp.size(), 0, 1, W.vpart_id[k] + o0});
+      info[W.vpart_id[k] + o0].ntasks = 1;
+      vp.push_back(W.vpart[k]);
+    }
+  };
+  auto count_of = [](const Wave& W, int kind) -> size_t {
+    switch (kind) {
+      case TK_GEMM: return W.gemm.size();
+      case TK_LU: return W.lu.size();
+      case TK_TRUNC: return W.trunc.size();
+      case TK_COPY: return W.copy.size();
+      case TK_REDUCE: return W.reduce.size();
+      case TK_ROWS: return W.rows.size();
+      default: return W.vpart.size();
+    }
+  };
+  // Tasks are handed out in this order: wave by wave (an op's producers lie
+  // in earlier waves, so a CTA only ever waits for tasks handed out before its
+  // own).  Within a wave by the ops' urgency (OpGraph::prio: for the H-LU the
+  // diagonal position at which the result is first needed), ties by kind
+  // (base LUs, truncations, split-K reductions and copies before GEMM tiles),
+  // so that the ops on the factorisation's dependency chain start as soon as
+  // their producers finish instead of after the wave's far-field work.  (A
+  // topological order by urgency alone, across waves, defers the far field
+  // until the chain waits for it: 2x slower at 1D N = 65536.)
+  static const int kinds[] = {TK_LU, TK_TRUNC, TK_REDUCE, TK_COPY, TK_GEMM, TK_ROWS, TK_VPART};
   for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
-    for (int kind : {TK_LU, TK_TRUNC, TK_REDUCE, TK_COPY, TK_GEMM, TK_ROWS, TK_VPART}) {
+    for (int kind : kinds)
       for (size_t p = 0; p < parts.size(); ++p) {
         if (w >= parts[p].waves->size()) continue;
         const Wave& W = (*parts[p].waves)[w];
-        const int o0 = off[p];
-        if (kind == TK_GEMM) {
-          for (size_t k = 0; k < W.gemm.size(); ++k) {
-            GemmOp o = W.gemm[k];
-            o.shape = gemm_shape(o.m, o.n) | (gemm_fp64 ? GEMM_FP64 : 0);
-            int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k] + o0;
-            for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
-            info[id].ntasks = nt;
-            g.push_back(o);
-          }
-        } else if (kind == TK_LU) {
-          for (size_t k = 0; k < W.lu.size(); ++k) {
-            tasks.push_back({TK_LU, (int)l.size(), 0, 1, W.lu_id[k] + o0});
-            info[W.lu_id[k] + o0].ntasks = 1;
-            LuOp o = W.lu[k];
-            o.pad = lu_df ? LU_DF : 0;
-            l.push_back(o);
-          }
-        } else if (kind == TK_TRUNC) {
-          for (size_t k = 0; k < W.trunc.size(); ++k) {
-            tasks.push_back({TK_TRUNC, (int)tr.size(), 0, 1, W.trunc_id[k] + o0});
-            info[W.trunc_id[k] + o0].ntasks = 1;
-            tr.push_back(W.trunc[k]);
-          }
-        } else if (kind == TK_COPY) {
-          for (size_t k = 0; k < W.copy.size(); ++k) {
-            const CopyOp& o = W.copy[k];
-            int nc = chunks((int64_t)o.m * o.n), id = W.copy_id[k] + o0;
-            for (int t = 0; t < nc; ++t) tasks.push_back({TK_COPY, (int)c.size(), t, nc, id});
-            info[id].ntasks = nc;
-            c.push_back(o);
-          }
-        } else if (kind == TK_REDUCE) {
-          for (size_t k = 0; k < W.reduce.size(); ++k) {
-            const ReduceOp& o = W.reduce[k];
-            int nc = chunks((int64_t)o.m * o.n * std::max(o.nparts, 1)), id = W.reduce_id[k] + o0;
-            for (int t = 0; t < nc; ++t) tasks.push_back({TK_REDUCE, (int)r.size(), t, nc, id});
-            info[id].ntasks = nc;
-            r.push_back(o);
-          }
-        } else if (kind == TK_ROWS) {
-          for (size_t k = 0; k < W.rows.size(); ++k) {
-            RowsOp o = W.rows[k];
-            o.src_begin += soff[p];
-            o.src_end += soff[p];
-            if (restage) plan_rows_staging(o, msrc.data() + o.src_begin, mode);
-            const int id = W.rows_id[k] + o0;
-            tasks.push_back({TK_ROWS, (int)ro.size(), 0, o.nr, id});  // nsub: rows of the chunk
-            info[id].ntasks += 1;  // the chunks of one row op share its id
-            ro.push_back(o);
-          }
-        } else {
-          for (size_t k = 0; k < W.vpart.size(); ++k) {
-            tasks.push_back({TK_VPART, (int)vp.size(), 0, 1, W.vpart_id[k] + o0});
-            info[W.vpart_id[k] + o0].ntasks = 1;
-            vp.push_back(W.vpart[k]);
-          }
-        }
+        for (size_t k = 0; k < count_of(W, kind); ++k) emit(p, W, kind, k);
       }
-    }
     std::stable_sort(tasks.begin() + wb.back(), tasks.end(),
                      [&](const Task& x, const Task& y) { return prio[x.id] < prio[y.id]; });
   }
