@@ -330,6 +330,9 @@ int upload_hinv_batch(const std::vector<HinvJob>& h, HinvBatch& B, std::vector<v
   B.total[0] = d0.total;
   B.total[1] = d1.total;
   B.count = (int)h.size();
+  B.prec = h[0].A.prec;
+  for (const HinvJob& J : h)
+    if (J.A.prec != B.prec) B.prec = -1;
   return HM_OK;
 }
 

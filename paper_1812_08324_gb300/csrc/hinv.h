@@ -82,8 +82,8 @@ struct HinvApply {
   const void* p_pool;
   const void* q_pool;
   const int* rank;          // per node
-  double* tpart;            // per product chunk: KCAP partial sums
-  double* tvec;             // per node: KCAP coefficients
+  void* tpart;              // per product chunk: KCAP partial sums   (in the accumulator type of prec:
+  void* tvec;               // per node: KCAP coefficients             FP64 double, pairs float2, else float)
   unsigned* tcount;         // per node: finished chunks (reset by the last one)
 };
 // One triangular inverse applied to a Morton-order vector: y = X b, or, with
@@ -103,6 +103,7 @@ struct HinvBatch {
   int* off[2] = {nullptr, nullptr};  // per job its first CTA of the two launches; off[k][count] = total
   int total[2] = {0, 0};
   int count = 0;
+  int prec = -1;  // the jobs' common HinvPrec, -1 if they differ
 };
 int launch_hinv_batch(const HinvBatch& B, cudaStream_t st);
 

@@ -112,6 +112,9 @@ __device__ __forceinline__ float shfl_i(float v, int l) { return __shfl_sync(0xf
 __device__ __forceinline__ float2 shfl_i(float2 v, int l) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
 }
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
 template <int P>
 __device__ __forceinline__ typename Tr<P>::A warp_sum(typename Tr<P>::A a) {
 #pragma unroll
@@ -119,7 +122,7 @@ __device__ __forceinline__ typename Tr<P>::A warp_sum(typename Tr<P>::A a) {
   return a;
 }
 
-constexpr int T_WARPS = 8;
+constexpr int T_WARPS = 4;
 
 // t_tau = Q_tau^T b over one 256-row chunk of the source range.  Q is stored
 // column-major, so a warp reads a column of the chunk as 256 consecutive
@@ -161,9 +164,10 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
     }
     sa = warp_sum<P>(sa);
     sb = warp_sum<P>(sb);
-    if (lane == 0) {
-      H.tpart[(int64_t)tc.z * HINV_KCAP + l] = T::fin(sa);
-      if (l2 < k) H.tpart[(int64_t)tc.z * HINV_KCAP + l2] = T::fin(sb);
+    if (lane == 0) {  // kept in the accumulator type: no FP64 instruction
+      typename T::A* tp = static_cast<typename T::A*>(H.tpart) + (int64_t)tc.z * HINV_KCAP;
+      tp[l] = sa;
+      if (l2 < k) tp[l2] = sb;
     }
   }
   // the CTA's partials are published by one acquire-release count after the
@@ -180,12 +184,12 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
   if (last) {
     // warp per column, lanes over the chunks (fixed assignment and tree)
     const int nch = nd.tch_end - nd.tch_begin;
+    const typename T::A* tp = static_cast<const typename T::A*>(H.tpart);
     for (int l = warp; l < k; l += T_WARPS) {
-      double s = 0.0;
-      for (int cc = lane; cc < nch; cc += 32) s += __ldcg(H.tpart + (int64_t)(nd.tch_begin + cc) * HINV_KCAP + l);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) H.tvec[(int64_t)tc.x * HINV_KCAP + l] = s;
+      typename T::A s = T::zero();
+      for (int cc = lane; cc < nch; cc += 32) s = T::add(s, ld_cg(tp + (int64_t)(nd.tch_begin + cc) * HINV_KCAP + l));
+      s = warp_sum<P>(s);
+      if (lane == 0) static_cast<typename T::A*>(H.tvec)[(int64_t)tc.x * HINV_KCAP + l] = s;
     }
     if (threadIdx.x == 0) H.tcount[tc.x] = 0u;
   }
@@ -219,7 +223,8 @@ __device__ __forceinline__ void r_body(const HinvApply& H, int c, const double* 
     base += g.n;
     if (lo >= hi) continue;
     const typename T::S* M = static_cast<const typename T::S*>(g.kind ? H.p_pool : H.leaf_pool) + g.off + lane;
-    const double* v = (g.kind ? static_cast<const double*>(H.tvec) : b) + g.voff;
+    const typename T::A* tv = static_cast<const typename T::A*>(H.tvec) + g.voff;  // t: already converted
+    const double* v = b + g.voff;
     for (int j0 = lo; j0 < hi; j0 += 8) {
       typename T::S va[8], vb[8];
 #pragma unroll
@@ -228,7 +233,8 @@ __device__ __forceinline__ void r_body(const HinvApply& H, int c, const double* 
         va[u] = (j < hi && ra && j < g.a_hi) ? T::ld(M + (int64_t)j * g.ld) : T::sz();
         vb[u] = (j < hi && rb && j >= g.b_lo) ? T::ld(M + (int64_t)j * g.ld + 32) : T::sz();
       }
-      const typename T::X xl = T::cvt(lane < 8 && j0 + lane < hi ? __ldg(v + j0 + lane) : 0.0);
+      typename T::X xl = T::cvt(0.0);
+      if (lane < 8 && j0 + lane < hi) xl = g.kind ? tv[j0 + lane] : T::cvt(__ldg(v + j0 + lane));
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const typename T::X x = shfl_i(xl, u);
@@ -254,7 +260,7 @@ __device__ __forceinline__ void r_body(const HinvApply& H, int c, const double* 
 constexpr int R_THREADS = 32 * HINV_AWARPS;
 
 template <int P>
-__global__ void __launch_bounds__(32 * T_WARPS, 4) hinv_t_kernel(HinvApply H, const double* __restrict__ b) {
+__global__ void __launch_bounds__(32 * T_WARPS, 8) hinv_t_kernel(HinvApply H, const double* __restrict__ b) {
   t_body<P>(H, blockIdx.x, b);
 }
 
@@ -273,7 +279,20 @@ __device__ __forceinline__ int job_of(const int* off, int count, int blk) {
   return lo;
 }
 
-__global__ void __launch_bounds__(32 * T_WARPS, 4) hinv_t_batch_kernel(const HinvJob* jobs, const int* off, int count) {
+// one precision for every job (the common case: no switch, no spills)
+template <int P>
+__global__ void __launch_bounds__(32 * T_WARPS, 8) hinv_t_batch1_kernel(const HinvJob* jobs, const int* off, int count) {
+  const int j = job_of(off, count, blockIdx.x);
+  t_body<P>(jobs[j].A, blockIdx.x - off[j], jobs[j].b);
+}
+template <int P>
+__global__ void __launch_bounds__(R_THREADS, 7) hinv_r_batch1_kernel(const HinvJob* jobs, const int* off, int count) {
+  const int j = job_of(off, count, blockIdx.x);
+  const HinvJob& J = jobs[j];
+  r_body<P>(J.A, blockIdx.x - off[j], J.b, J.y, J.sub, J.scale);
+}
+
+__global__ void __launch_bounds__(32 * T_WARPS, 8) hinv_t_batch_kernel(const HinvJob* jobs, const int* off, int count) {
   const int j = job_of(off, count, blockIdx.x);
   const HinvJob& J = jobs[j];
   const int c = blockIdx.x - off[j];
@@ -317,11 +336,24 @@ int launch_hinv_apply(const HinvApply& H, const double* b, double* y, cudaStream
   }
 }
 
+template <int P>
+void launch_batch1(const HinvBatch& B, cudaStream_t st) {
+  if (B.total[0] > 0) hinv_t_batch1_kernel<P><<<B.total[0], 32 * T_WARPS, 0, st>>>(B.jobs, B.off[0], B.count);
+  hinv_r_batch1_kernel<P><<<B.total[1], R_THREADS, 0, st>>>(B.jobs, B.off[1], B.count);
+}
+
 int launch_hinv_batch(const HinvBatch& B, cudaStream_t st) {
   if (B.count == 0) return HM_OK;
   count_launches(B.total[0] > 0 ? 2 : 1);
-  if (B.total[0] > 0) hinv_t_batch_kernel<<<B.total[0], 32 * T_WARPS, 0, st>>>(B.jobs, B.off[0], B.count);
-  hinv_r_batch_kernel<<<B.total[1], R_THREADS, 0, st>>>(B.jobs, B.off[1], B.count);
+  switch (B.prec) {
+    case HINV_F64: launch_batch1<HINV_F64>(B, st); break;
+    case HINV_DF: launch_batch1<HINV_DF>(B, st); break;
+    case HINV_F32: launch_batch1<HINV_F32>(B, st); break;
+    case HINV_BF16: launch_batch1<HINV_BF16>(B, st); break;
+    default:
+      if (B.total[0] > 0) hinv_t_batch_kernel<<<B.total[0], 32 * T_WARPS, 0, st>>>(B.jobs, B.off[0], B.count);
+      hinv_r_batch_kernel<<<B.total[1], R_THREADS, 0, st>>>(B.jobs, B.off[1], B.count);
+  }
   return cudaGetLastError() == cudaSuccess ? HM_OK : HM_ERR_CUDA;
 }
 

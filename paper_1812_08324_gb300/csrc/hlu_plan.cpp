@@ -635,6 +635,10 @@ class HLU {
     View A11 = Am.sub(0, 0, h, h), A12 = Am.sub(0, h, h, r), A21 = Am.sub(h, 0, r, h), A22 = Am.sub(h, h, r, r);
     View Li11 = Li.sub(0, 0, h, h), Li21 = Li.sub(h, 0, r, h), Li12 = Li.sub(0, h, h, r), Li22 = Li.sub(h, h, r, r);
     View Ui11 = Ui.sub(0, 0, h, h), Ui12 = Ui.sub(0, h, h, r), Ui21 = Ui.sub(h, 0, r, h), Ui22 = Ui.sub(h, h, r, r);
+    // the zero blocks of the triangular inverses first: they depend on nothing,
+    // so the products that read a whole inverse do not wait for them at the end
+    E.copy(Li12, 0.0, nullptr, 0.0);
+    E.copy(Ui21, 0.0, nullptr, 0.0);
     luinv(A11, Li11, Ui11);
     View T12 = E.tmp(h, r, false), T21 = E.tmp(r, h, false);
     E.gemm(T12, 1.0, Li11, A12, 0.0);   // U12 = L11^{-1} A12
@@ -648,8 +652,6 @@ class HLU {
     luinv(A22, Li22, Ui22);
     E.gemm(Li21, -1.0, Li22, X, 0.0);   // (L^{-1})_21 = -L22^{-1} L21 L11^{-1}
     E.gemm(Ui12, -1.0, Y, Ui22, 0.0);   // (U^{-1})_12 = -U11^{-1} U12 U22^{-1}
-    E.copy(Li12, 0.0, nullptr, 0.0);
-    E.copy(Ui21, 0.0, nullptr, 0.0);
     E.release(T12);
     E.release(T21);
     E.release(X);

@@ -6,16 +6,25 @@ Builds the H-matrix of the 1D Levy generator workload (drift 0.3, sigma 0.2,
 alpha-stable alpha = 1.5 truncated to |y| <= 2, leaf 256, ACA rank <= 32,
 factor rank <= 16, dt = 1e-3) at N unknowns, factors I - dt/2 G, then runs
 one warm-up and `reps` timed repetitions of the chosen operation:
-  matvec   y = x + dt/2 G x (H-matvec)
-  solve    z = (LU)^{-1} b (the persistent solve schedule; the factorisation
-           is the first launch of the same executor kernel)
-  cn_step  one Crank-Nicolson step (right-hand side H-matvec + solve)
-and prints the mean time per repetition (CUDA events).
+  matvec   y = x + dt/2 G x (H-matvec: vt_kernel, vt_reduce_kernel, rows_kernel)
+  solve    z = (LU)^{-1} b (1D: the hierarchical inverses' products, hinv_t_kernel
+           and hinv_r_kernel per factor)
+  cn_step  one Crank-Nicolson step (identity form: one pair of solves)
+  factor   the H-LU of I - dt/2 G again (the executor's exec_kernel<0>
+           launches; HM_PIPELINE=0 makes it one launch) and the hierarchical
+           inverses' construction
+and prints the mean time per repetition (CUDA events).  With --trace PREFIX
+the timed repetitions run with the executor's per-task trace (HM_PHASE_TRACE,
+HM_TRACE_FILE=PREFIX; read by ``python -m paper_1812_08324_gb300.trace_chain``)
+and the trace files are gzip-compressed afterwards.
 """
 from __future__ import annotations
 
 import argparse
+import gzip
 import json
+import os
+import shutil
 
 from . import build, hmat, workloads as W
 
@@ -23,8 +32,9 @@ from . import build, hmat, workloads as W
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=32768)
-    ap.add_argument("--what", choices=["matvec", "solve", "cn_step"], default="solve")
+    ap.add_argument("--what", choices=["matvec", "solve", "cn_step", "factor"], default="solve")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--trace", default=None, help="file prefix of the per-task trace of the timed repetitions")
     args = ap.parse_args()
     import torch
 
@@ -43,17 +53,31 @@ def main() -> int:
             H.matvec(x, alpha=1.0, beta=0.5 * dt, out=y)
         elif args.what == "solve":
             F.solve(x, out=y)
+        elif args.what == "factor":
+            H.factor(-0.5 * dt).free()
         else:
             hmat.cn_step(H, F, dt, x, out=y)
 
     op()
     torch.cuda.synchronize()
+    if args.trace:
+        os.environ["HM_PHASE_TRACE"] = "1"
+        os.environ["HM_TRACE_FILE"] = args.trace
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.reps):
         op()
     e1.record()
     torch.cuda.synchronize()
+    if args.trace:
+        del os.environ["HM_PHASE_TRACE"], os.environ["HM_TRACE_FILE"]
+        folder, stem = os.path.split(os.path.abspath(args.trace))
+        for name in os.listdir(folder):
+            if name.startswith(stem + ".") and name.endswith(".txt"):
+                path = os.path.join(folder, name)
+                with open(path, "rb") as a, gzip.open(path + ".gz", "wb") as b:
+                    shutil.copyfileobj(a, b)
+                os.remove(path)
     st = H.stats(F)
     print(json.dumps({"n": args.n, "what": args.what, "reps": args.reps,
                       "ms": e0.elapsed_time(e1) / max(args.reps, 1),
