@@ -82,8 +82,8 @@ __device__ __forceinline__ double urand(unsigned long long key) {
 struct FillJob { double* buf; int r0, n, S; unsigned long long seed; };
 __global__ void fill_kernel(const FillJob* jobs, int njobs) {
   const FillJob J = jobs[blockIdx.x];
-  const int64_t total = (int64_t)J.n * J.S;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+  const int total = J.n * J.S;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int64_t i = J.r0 + e / J.S, c = e % J.S;
     J.buf[i * J.S + c] = urand(J.seed * 0x100000001B3ull + (unsigned long long)(i * HINV_MAXS + c));
   }
@@ -240,16 +240,27 @@ __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* 
     }
     __syncthreads();
     if (l0) {
-      for (int j = 0; j < nb; ++j) {
-        const int64_t jj = j0 + jb + j;
-        const float2 v0 = df_split(R.V[jj * R.vrs + (int64_t)lg * R.vcs], bad);
-        const float2 v1 = l1 ? df_split(R.V[jj * R.vrs + (int64_t)(lg + 32) * R.vcs], bad) : z;
+      for (int jq = 0; jq < nb; jq += 4) {  // four rows of V loaded before any is used
+        double w0[4], w1[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = g + 8 * q;
-          if (c < S) {
-            dd_mac(acc[0][q], v0, xs[j][c]);
-            if (l1) dd_mac(acc[1][q], v1, xs[j][c]);
+        for (int u = 0; u < 4; ++u) {
+          const int64_t jj = j0 + jb + jq + u;
+          const bool in = jq + u < nb;
+          w0[u] = in ? R.V[jj * R.vrs + (int64_t)lg * R.vcs] : 0.0;
+          w1[u] = in && l1 ? R.V[jj * R.vrs + (int64_t)(lg + 32) * R.vcs] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (jq + u >= nb) break;
+          const float2 v0 = df_split(w0[u], bad);
+          const float2 v1 = l1 ? df_split(w1[u], bad) : z;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int c = g + 8 * q;
+            if (c < S) {
+              dd_mac(acc[0][q], v0, xs[jq + u][c]);
+              if (l1) dd_mac(acc[1][q], v1, xs[jq + u][c]);
+            }
           }
         }
       }
@@ -311,13 +322,24 @@ __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* 
         }
         __syncthreads();
         if (live) {
-          for (int j = jb; j < jb + nb; ++j) {
-            const bool keep = !((I.mask == 1 && j > i) || (I.mask == 2 && j < i));
-            const float2 a = keep ? df_split(arow[(int64_t)j * I.cs], bad) : z;
+          // eight matrix entries loaded before any is used
+          for (int j0 = jb; j0 < jb + nb; j0 += 8) {
+            double av[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int c = g + 8 * q;
-              if (c < S) dd_mac(acc[q], a, xs[j - jb][c]);
+            for (int u = 0; u < 8; ++u) {
+              const int j = j0 + u;
+              const bool keep = j < jb + nb && !((I.mask == 1 && j > i) || (I.mask == 2 && j < i));
+              av[u] = keep ? arow[(int64_t)j * I.cs] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (j0 + u >= jb + nb) break;
+              const float2 a = df_split(av[u], bad);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int c = g + 8 * q;
+                if (c < S) dd_mac(acc[q], a, xs[j0 + u - jb][c]);
+              }
             }
           }
         }
@@ -335,12 +357,19 @@ __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* 
         }
         __syncthreads();
         if (live) {
-          for (int l = lb; l < lb + nb; ++l) {
-            const float2 u = df_split(urow[(int64_t)l * I.cs], bad);
+          for (int l0 = lb; l0 < lb + nb; l0 += 8) {
+            double uv[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int c = g + 8 * q;
-              if (c < S) dd_mac(acc[q], u, xs[l - lb][c]);
+            for (int w = 0; w < 8; ++w) uv[w] = l0 + w < lb + nb ? urow[(int64_t)(l0 + w) * I.cs] : 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              if (l0 + w >= lb + nb) break;
+              const float2 u = df_split(uv[w], bad);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int c = g + 8 * q;
+                if (c < S) dd_mac(acc[q], u, xs[l0 + w - lb][c]);
+              }
             }
           }
         }
@@ -932,8 +961,11 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       const unsigned long long seed = 1000003ull * (unsigned long long)(lev + 1) + 17ull * tri;
       for (size_t b = 0; b < lv.size(); ++b) {
         const HinvNode& Nd = H.h_nodes[lv[b]];
-        S.fill.push_back(FillJob{bufA[tri], Nd.src0, Nd.src_n, HINV_S, 2 * seed});
-        S.fill.push_back(FillJob{bufC[tri], Nd.tgt0, Nd.tgt_n, HINV_SP, 2 * seed + 1});
+        // 128-row pieces (one CTA each; the values depend on the absolute row only)
+        for (int r = 0; r < Nd.src_n; r += HINV_MCH)
+          S.fill.push_back(FillJob{bufA[tri], Nd.src0 + r, std::min(HINV_MCH, Nd.src_n - r), HINV_S, 2 * seed});
+        for (int r = 0; r < Nd.tgt_n; r += HINV_MCH)
+          S.fill.push_back(FillJob{bufC[tri], Nd.tgt0 + r, std::min(HINV_MCH, Nd.tgt_n - r), HINV_SP, 2 * seed + 1});
         S.core_node.push_back(tri * nn + lv[b]);
         for (int r = 0; r < Nd.tgt_n; r += HINV_RCH)
           S.form.push_back(FormJob{0, (int)b, Nd.tgt0, Nd.tgt_n, r, ppool[tri] + Nd.poff, Nd.pld, bufB[tri], HINV_S});

@@ -34,6 +34,8 @@ def main() -> int:
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--what", choices=["matvec", "solve", "cn_step", "factor"], default="solve")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--solve", choices=["auto", "hinv", "subst"], default="auto",
+                    help="triangular solves: hierarchical inverses (1D default) or substitution")
     ap.add_argument("--trace", default=None, help="file prefix of the per-task trace of the timed repetitions")
     args = ap.parse_args()
     import torch
@@ -42,7 +44,7 @@ def main() -> int:
     hmat.load()
     prob = W.levy_1d(args.n)
     _, opts, dt, _, kind = W.WORKLOADS["levy_1d_n65536"]
-    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=0)
+    opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=0, solve=args.solve)
     H = hmat.HMatrix(prob, opts)
     F = H.factor(-0.5 * dt)
     x = torch.tensor(W.initial_data(prob, kind), dtype=torch.float64, device="cuda")
