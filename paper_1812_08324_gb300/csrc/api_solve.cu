@@ -746,6 +746,12 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
   int s = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess ? HM_OK : HM_ERR_CUDA;
   bool started = false;
   launches = 0;
+  // HM_TIME_PHASES: per slice, when it was handed to the device (host clock)
+  // and when its launch ended (device clock), both from the first launch
+  const bool timing = std::getenv("HM_TIME_PHASES") != nullptr;
+  struct SliceTime { int64_t tasks; double host_ms; cudaEvent_t end; };
+  std::vector<SliceTime> slices;
+  const auto t_host0 = std::chrono::steady_clock::now();
   while (s == HM_OK) {
     std::vector<std::vector<HluChunk>> got(count);
     bool any = false, done = false;
@@ -768,6 +774,7 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
       if (done) break;
       continue;
     }
+    const auto t_m0 = std::chrono::steady_clock::now();
     std::vector<std::vector<Wave>> pw(count);
     std::vector<OpGraph> pg(count);
     std::vector<SchedPart> parts;
@@ -777,18 +784,41 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
       parts.push_back(SchedPart{&pw[i], &pg[i], nullptr});
     }
     if (s != HM_OK) break;
+    const auto t_m1 = std::chrono::steady_clock::now();
     DevSchedule S;
     s = upload_schedules(parts, S, allocs, 0, false, cs);
     if (s != HM_OK) break;
+    const auto t_m2 = std::chrono::steady_clock::now();
+    if (timing)
+      fprintf(stderr, "[factor slices] merged in %.1f ms, uploaded in %.1f ms\n",
+              std::chrono::duration<double, std::milli>(t_m1 - t_m0).count(),
+              std::chrono::duration<double, std::milli>(t_m2 - t_m1).count());
     if (!started) {
       cudaEventRecord(e0, st);
       started = true;
     }
     s = run_schedule(S, d_err, st);
     ++launches;
+    if (timing) {
+      SliceTime T{S.ntasks, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count(),
+                  nullptr};
+      cudaEventCreate(&T.end);
+      cudaEventRecord(T.end, st);
+      slices.push_back(T);
+    }
   }
   if (!started) cudaEventRecord(e0, st);
   cudaEventRecord(e1, st);
+  if (timing) {
+    cudaEventSynchronize(e1);
+    for (size_t k = 0; k < slices.size(); ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, slices[k].end);
+      fprintf(stderr, "[factor slices] %zu: %lld tasks, handed out at %.1f ms, done at %.1f ms\n", k,
+              (long long)slices[k].tasks, slices[k].host_ms, ms);
+      cudaEventDestroy(slices[k].end);
+    }
+  }
   for (auto& th : pool) th.join();  // after an error the planners still finish
   for (FactorJob& J : jobs) J.hb.sink = nullptr;
   if (cs) cudaStreamDestroy(cs);
