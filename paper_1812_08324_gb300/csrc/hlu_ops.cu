@@ -1164,7 +1164,7 @@ struct ExecArgs {
   const Task* tasks;
   const int* wave_begin;
   const OpInfo* ops;
-  const int* deps;
+  const int2* deps;  // per dependency edge: (producer op, tasks it has)
   int* counters;
   int* grab;        // next task to hand out
   int ntasks;
@@ -1198,9 +1198,9 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
     bool good = true;
     const unsigned long long t0 = global_ns();
     for (int k = op.dep_begin + (int)threadIdx.x; k < op.dep_end && good; k += 32) {
-      const int d = a.deps[k];
-      const int need = a.ops[d].ntasks;
-      const int* c = a.counters + d;
+      const int2 dn = a.deps[k];  // the producer's task count travels with the edge
+      const int need = dn.y;
+      const int* c = a.counters + dn.x;
       unsigned polls = 0;
       while (ld_relaxed(c) < need) {
 #if HM_POLL_NS > 0
@@ -1228,6 +1228,15 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
   constexpr bool SOLVE = MODE != 0;
   extern __shared__ double smem[];
   __shared__ int next;
+  // descriptor of the current op (factorisation), copied before the wait
+  __shared__ union OpDesc {
+    int w[1];
+    GemmOp gemm;
+    LuOp lu;
+    TruncOp trunc;
+    CopyOp copy;
+    ReduceOp reduce;
+  } opdesc;
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(a.grab, 1);
     __syncthreads();
@@ -1245,6 +1254,21 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
     if constexpr (SOLVE) {
       if (T.kind == TK_ROWS) dev_rows_prefetch(a.rows[T.op], a.srcs, smem, mode_prefetch(MODE));
       if (T.kind == TK_VPART) dev_vpart_prefetch(a.vpart[T.op], smem, mode_vpart(MODE));
+    } else {
+      // the op's descriptor to shared memory while warp 0 waits for its producers
+      if (threadIdx.x >= 32) {
+        const int* src = nullptr;
+        int words = 0;
+        switch (T.kind) {
+          case TK_GEMM: src = reinterpret_cast<const int*>(a.gemm + T.op); words = sizeof(GemmOp) / 4; break;
+          case TK_LU: src = reinterpret_cast<const int*>(a.lu + T.op); words = sizeof(LuOp) / 4; break;
+          case TK_TRUNC: src = reinterpret_cast<const int*>(a.trunc + T.op); words = sizeof(TruncOp) / 4; break;
+          case TK_COPY: src = reinterpret_cast<const int*>(a.copy + T.op); words = sizeof(CopyOp) / 4; break;
+          case TK_REDUCE: src = reinterpret_cast<const int*>(a.reduce + T.op); words = sizeof(ReduceOp) / 4; break;
+          default: break;
+        }
+        for (int w = threadIdx.x - 32; w < words; w += blockDim.x - 32) opdesc.w[w] = src[w];
+      }
     }
     if (!wait_deps(a, T.id)) {
       cp_async_wait_all();  // no copy may outlive the CTA
@@ -1253,18 +1277,24 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
     if (a.trace && threadIdx.x == 0) a.trace[TRACE_STRIDE * (size_t)t + 1] = global_ns();
     if constexpr (!SOLVE) {
       switch (T.kind) {
-        case TK_GEMM: dev_gemm_tile(a.gemm[T.op], T.sub, smem, a.err); break;
+        case TK_GEMM: dev_gemm_tile(opdesc.gemm, T.sub, smem, a.err); break;
         case TK_LU:
-          if (a.lu[T.op].pad & LU_DF) dev_lu_base_dd(a.lu[T.op], a.err, smem);
-          else dev_lu_base(a.lu[T.op], a.err, smem);
+          if (opdesc.lu.pad & LU_DF) dev_lu_base_dd(opdesc.lu, a.err, smem);
+          else dev_lu_base(opdesc.lu, a.err, smem);
           break;
-        case TK_TRUNC: dev_trunc(a.trunc[T.op], a.err, smem); break;
+        case TK_TRUNC: dev_trunc(opdesc.trunc, a.err, smem); break;
+        case TK_COPY: dev_copy(opdesc.copy, T.sub, T.nsub); break;
+        case TK_REDUCE: dev_reduce(opdesc.reduce, T.sub, T.nsub); break;
         default: break;
       }
     }
     switch (T.kind) {
-      case TK_COPY: dev_copy(a.copy[T.op], T.sub, T.nsub); break;
-      case TK_REDUCE: dev_reduce(a.reduce[T.op], T.sub, T.nsub); break;
+      case TK_COPY:
+        if constexpr (SOLVE) dev_copy(a.copy[T.op], T.sub, T.nsub);
+        break;
+      case TK_REDUCE:
+        if constexpr (SOLVE) dev_reduce(a.reduce[T.op], T.sub, T.nsub);
+        break;
       case TK_ROWS:
         if constexpr (SOLVE)
           dev_rows(a.rows[T.op], smem, mode_prefetch(MODE), a.trace ? a.trace + TRACE_STRIDE * (size_t)t + 4 : nullptr);
@@ -1480,7 +1510,6 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   S.mode = (g.empty() && l.empty() && tr.empty()) ? (mode == SOLVE_MODE_THROUGHPUT ? 2 : 1) : 0;
   if (std::getenv("HM_PHASE_TRACE")) S.host_tasks.swap(tasks);  // kept for tracing only
   if ((st = up(wb, &S.wave_begin)) != HM_OK) return st;
-  if ((st = up(deps, &S.deps)) != HM_OK) return st;
   // Test-only fault injection (failure detection of the bounded waits):
   // HM_TEST_STALL_OP=<op> makes op <op> of this schedule require one task more
   // than it has, so its consumers' waits can only run out; HM_WAIT_LIMIT_MS
@@ -1490,6 +1519,11 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
     if (id >= 0 && id < nops) info[id].ntasks += 1;
   }
   if ((st = up(info, &S.ops)) != HM_OK) return st;
+  {  // dependency edges with the producer's task count (one load fewer per wait)
+    std::vector<int2> deps2(deps.size());
+    for (size_t e = 0; e < deps.size(); ++e) deps2[e] = make_int2(deps[e], info[deps[e]].ntasks);
+    if ((st = up(deps2, &S.deps)) != HM_OK) return st;
+  }
   S.wait_ns = WAIT_LIMIT_NS;
   if (const char* wl = std::getenv("HM_WAIT_LIMIT_MS"))
     if (std::atoll(wl) > 0) S.wait_ns = (unsigned long long)std::atoll(wl) * 1000000ull;

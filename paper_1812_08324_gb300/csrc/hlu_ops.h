@@ -206,7 +206,7 @@ struct DevSchedule {
   Task* tasks = nullptr;
   int* wave_begin = nullptr;
   OpInfo* ops = nullptr;
-  int* deps = nullptr;
+  int2* deps = nullptr;      // dependency edges: (producer op, its task count)
   int* counters = nullptr;   // per op: finished tasks
   std::vector<Task> host_tasks;  // the task list in hand-out order (for tracing)
   int mode = 0;                  // executor mode (0: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
