@@ -259,8 +259,9 @@ def run_batch(args):
     refine = args.refine if args.refine is not None else (0 if args.precision == "fp64" else 1)
     batch = [(p, dict(o, refine_max=refine, precision=args.precision, solve=args.solve, cn_form=args.cn_form))
              for p, o in batch]
-    leafs = autotune.tune_batch(batch, dt, cn_steps, probe_steps=3)
-    batch = [(p, dict(o, leaf=l)) for (p, o), l in zip(batch, leafs)]
+    cfgs = autotune.tune_batch_configs(batch, dt, cn_steps, probe_steps=3)
+    batch = [(p, dict(o, **c)) for (p, o), c in zip(batch, cfgs)]
+    leafs = [c["leaf"] for c in cfgs]
     ns = [p["n"][0] for p, _ in batch]
     units = float(sum(ns)) * cn_steps
     u0_host = [torch.tensor(W.gaussian_u0(p, 50.0), dtype=torch.float64).pin_memory() for p, _ in batch]
@@ -376,6 +377,8 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"levy_batch x{len(batch)} (splitmix64 seed 0)", "sum_N": int(sum(ns)),
                        "cn_steps": cn_steps, "dt": dt, "leafs": {str(l): leafs.count(l) for l in sorted(set(leafs))},
+                       "tuned": {f"leaf {c['leaf']}, {c['solve']}" + (f" blocks {c['solve_block']}" if c.get("solve_block") else ""):
+                                 sum(1 for d in cfgs if d == c) for c in [dict(t) for t in sorted({tuple(sorted(d.items())) for d in cfgs})]},
                        "groups": len(groups), "group_unknowns_max": args.group_unknowns,
                        "refine_sweeps": refine, "precision": args.precision, "solve": args.solve, "cn_form": args.cn_form,
                        "parallelism": f"replicas x{world}", "cuda_graph": graphed,

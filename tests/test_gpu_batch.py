@@ -89,6 +89,30 @@ def test_cn_solve_batch_rejects_bad_input():
         hmat.cn_solve_batch([Hs[0], Hs[0]], [Fs[0], Fs[0]], dt, 3, us)
 
 
+def test_autotune_configs_cover_leaf_solve_and_block():
+    """The autotuner's search space for a 1D problem holds the inverses and the
+    substitution solve with each block size below N, and its choice is one of
+    them; the batch with the chosen options matches the oracle."""
+    from paper_1812_08324_gb300 import autotune
+    batch = _small_batch(2)
+    dt = W.LEVY_BATCH_DT
+    p0, o0 = batch[0]
+    cands = autotune.configurations(p0, o0, leafs=(32, 64), solve_blocks=(256, 512))
+    kinds = {(c["solve"], c.get("solve_block", 0)) for c in cands}
+    assert ("hinv", 0) in kinds and ("subst", 256) in kinds
+    cfgs = autotune.tune_batch_configs(batch, dt, 50, leafs=(32, 64), solve_blocks=(256, 512), probe_steps=2)
+    tuned = [(p, dict(o, **c)) for (p, o), c in zip(batch, cfgs)]
+    for c, (p, o) in zip(cfgs, batch):
+        assert c in autotune.configurations(p, o, leafs=(32, 64), solve_blocks=(256, 512))
+    Hs = [hmat.HMatrix(p, o) for p, o in tuned]
+    Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+    us = [dev(W.gaussian_u0(p, 50.0)) for p, _ in tuned]
+    hmat.cn_solve_batch(Hs, Fs, dt, 10, us)
+    for (p, o), u in zip(tuned, us):
+        ref = O.cn_solve(O.generator_dense(p), W.gaussian_u0(p, 50.0), dt, 10)
+        assert np.linalg.norm(host(u) - ref) / np.linalg.norm(ref) < 1e-8
+
+
 def test_autotune_picks_a_candidate_and_batch_stays_exact():
     from paper_1812_08324_gb300 import autotune
     batch = _small_batch(3)
