@@ -42,6 +42,41 @@ WORKLOAD = "levy_1d_n65536"
 METRIC = "CN unknown-steps/s at <=1e-6 rel err vs FP64 (H-matrix build + H-LU + CN run)"
 UNIT = "unknown-steps/s"
 
+# stored dense-oracle solutions for the accuracy figure of a workload: the
+# same physics, options, dt and step count on a smaller grid (written by the
+# scripts beside them, which call only the oracle)
+ORACLE_GOLDEN = {
+    "levy_1d_n65536": {
+        "file": "tests/golden/levy1d_n32768_dt1e-3.npz", "steps": 1000,
+        "prob": ("levy_1d", (32768,)),
+        "what": "dense FP64 oracle (assembly + dense LU + 1000 CN steps) at N=32768, same physics, options "
+                "and steps (tests/golden/levy1d_n32768_dt1e-3.npz)"},
+    "frac_lap_2d_256x256_s0.75": {
+        "file": "tests/golden/frac2d_n128_s0.75_dt5e-3.npz", "steps": 200,
+        "prob": ("frac_lap_2d", (128, 0.75)),
+        "what": "dense FP64 oracle (assembly + dense LU + 200 CN steps) at side 128 (N=16384), same order, "
+                "options and steps (tests/golden/frac2d_n128_s0.75_dt5e-3.npz)"},
+}
+
+def load_peaks() -> dict:
+    """The measured peaks (HBM copy GB/s, cuBLAS bf16 TFLOP/s, clocks), or {}."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+DF_PEAK_SOURCE = "derived: 128 FP32 lanes x 152 SMs x max SM clock / 10 instructions per double-float FMA"
+
+
+def df_alu_peak(clocks) -> float:
+    """TFLOP/s (FP64-equivalent) of double-float FMAs on the FP32 pipes: 128
+    FP32 lanes per SM x 152 SMs x the maximum SM clock, 10 FP32 instructions
+    per double-float FMA, 2 flop per FMA."""
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or load_peaks().get("sm_max_mhz") or 2070.0
+    return 2.0 * 128 * 152 * sm_mhz * 1e6 / 10.0 / 1e12
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -345,11 +380,7 @@ def run_batch(args):
     c1.record(stream)
     torch.cuda.synchronize()
     cn_ms = c0.elapsed_time(c1) / 20
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     gbs = byts / (cn_ms * 1e-3) / 1e9
     roofline = {"kernel": "batched CN step (inverse products of the 1D members, merged substitution schedule, "
@@ -458,14 +489,12 @@ def run_lshape(args):
     N = Hop.n
     ms, value = aggregate(ms, float(N), world, "cuda")
     s_op, s_pre = Hop.stats(), Hpre.stats(F)
-    # roofline of the dominant kernel: the H-LU executor (FP64 GEMM tiles on the CUDA cores)
-    fp64_peak = 2.0 * 152 * 2.0 * 2.07  # GFLOP/s nominal: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-    gflops = 2.0 * s_pre["factor_fma"] / (s_pre["factor_ms"] * 1e-3) / 1e9 if s_pre["factor_ms"] > 0 else None
-    roofline = {"kernel": "exec_kernel<0> (H-LU schedule of the preconditioner)", "bound": "alu",
-                "achieved": gflops, "peak": fp64_peak, "unit": "GFLOP/s",
-                "frac": gflops / fp64_peak if gflops else None, "traffic": None,
-                "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA/clk x 2.07 GHz (nominal unit count and clock); "
-                               "achieved counts FP64-equivalent GEMM FLOPs, the tiles run double-float on the FP32 pipes",
+    # roofline of the dominant kernel: the H-LU executor (double-float GEMM tiles on the FP32 pipes)
+    peak = df_alu_peak(clocks)
+    tflops = 2.0 * s_pre["factor_fma"] / (s_pre["factor_ms"] * 1e-3) / 1e12 if s_pre["factor_ms"] > 0 else None
+    roofline = {"kernel": "exec_kernel<0> (H-LU schedule of the preconditioner, double-float GEMM tiles)",
+                "bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": tflops / peak if tflops else None, "traffic": None, "peak_source": DF_PEAK_SOURCE,
                 "algorithmic_flops": 2.0 * s_pre["factor_fma"], "ms": s_pre["factor_ms"]}
     # accuracy: sampled rows of the exact generator are checked in the tests; here the
     # residual against the accurate operator and the iteration count
@@ -655,9 +684,9 @@ def main():
 
     # ---- accuracy of the timed configuration: (1) the same CN run with three
     # FP64 refinement sweeps per step (solves converged to the FP64 H system);
-    # (2) against the dense FP64 oracle: the same physics and options at
-    # N = 32768 (the largest grid whose dense LU the host reaches), u after
-    # 1000 steps stored by tests/golden/make_levy1d_golden.py
+    # (2) against the dense FP64 oracle: the same physics, options and steps
+    # on the largest grid whose dense LU the host reaches, u stored by the
+    # scripts under tests/golden (ORACLE_GOLDEN)
     assert torch.isfinite(u).all().item()
     u_ref = torch.empty_like(u0)
     Href = hmat.HMatrix(prob, dict(opts, refine_max=3, precision="fp64"))
@@ -668,19 +697,21 @@ def main():
     rel_err = float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref))
     Fref.free()
     Href.free()
-    oracle_err = None
-    gold = os.path.join(ROOT, "tests", "golden", "levy1d_n32768_dt1e-3.npz")
-    if name == WORKLOAD and cn_steps == 1000 and os.path.exists(gold):
-        g = np.load(gold)
-        p32 = W.levy_1d(32768)
-        H32 = hmat.HMatrix(p32, opts)
-        F32 = H32.factor(-0.5 * dt)
-        u32 = torch.tensor(W.gaussian_u0(p32, 50.0), dtype=torch.float64, device="cuda")
-        hmat.cn_solve(H32, F32, dt, 1000, u32)
-        got = u32.cpu().numpy()
-        oracle_err = float(np.linalg.norm(got - g["u1000"]) / np.linalg.norm(g["u1000"]))
-        F32.free()
-        H32.free()
+    oracle_err, oracle_ref = None, None
+    gold = ORACLE_GOLDEN.get(name)
+    if gold is not None and cn_steps == gold["steps"] and os.path.exists(os.path.join(ROOT, gold["file"])):
+        g = np.load(os.path.join(ROOT, gold["file"]))
+        p_s = getattr(W, gold["prob"][0])(*gold["prob"][1])
+        H_s = hmat.HMatrix(p_s, opts)
+        F_s = H_s.factor(-0.5 * dt)
+        u_s = torch.tensor(W.initial_data(p_s, kind), dtype=torch.float64, device="cuda")
+        hmat.cn_solve(H_s, F_s, dt, cn_steps, u_s)
+        got = u_s.cpu().numpy()
+        want = g[f"u{cn_steps}"]
+        oracle_err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        oracle_ref = gold["what"]
+        F_s.free()
+        H_s.free()
 
     # ---- end to end through the public API from pinned host memory
     out_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -701,11 +732,7 @@ def main():
     # per bench step: the H-LU executor (device time of its launches, CUDA
     # events inside the library).  The `roofline` object is the kernel with
     # the largest time per bench step.
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "of measured" if peaks else "of fallback"
     x = torch.tensor(W.initial_data(prob, kind), dtype=torch.float64, device="cuda")
@@ -743,13 +770,12 @@ def main():
     # the H-LU's GEMM tiles compute in double-float arithmetic on the FP32 pipes:
     # 10 FP32 instructions per FP64-equivalent multiply-add, so the ALU peak is
     # 128 FP32 lanes x SMs x clock / 10 multiply-adds (2 flop each)
-    sm_mhz = (clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
-    df_peak = 2.0 * 128 * 152 * sm_mhz * 1e6 / 10.0 / 1e12
+    df_peak = df_alu_peak(clocks)
     lu_tf = 2.0 * st["factor_fma"] / (st["factor_ms"] * 1e-3) / 1e12 if st["factor_ms"] > 0 else 0.0
     lu_roof = {"kernel": "exec_kernel<0> (H-LU dataflow executor, double-float GEMM tiles)", "bound": "alu",
                "achieved": lu_tf, "peak": df_peak, "unit": "TFLOP/s", "frac": lu_tf / df_peak, "traffic": None,
                "algorithmic_flops": 2.0 * st["factor_fma"], "ms": st["factor_ms"], "per_bench_step_ms": st["factor_ms"],
-               "peak_source": "derived: 128 FP32 lanes x 152 SMs x max SM clock / 10 instructions per double-float FMA",
+               "peak_source": DF_PEAK_SOURCE,
                "note": "latency-bound: the planned critical path (chain of diagonal leaf LUs) is about the measured time"}
     parts = [lu_roof, mv_roof, sv_roof]
     roofline = max(parts, key=lambda r: r["per_bench_step_ms"])
@@ -767,11 +793,9 @@ def main():
                              "exceeds L2; no flush needed"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "solve_roofline": sv_roof, "matvec_roofline": mv_roof, "factor_roofline": lu_roof,
-            "accuracy": {"rel_l2_vs_dense_fp64_oracle_n32768": oracle_err,
-                         "oracle_reference": "dense FP64 oracle (assembly + dense LU + 1000 CN steps) at N=32768, "
-                                             "same physics, options and steps (tests/golden/levy1d_n32768_dt1e-3.npz)",
+            "accuracy": {"rel_l2_vs_dense_fp64_oracle": oracle_err, "oracle_reference": oracle_ref,
                          "rel_l2_vs_converged_fp64_solves": rel_err,
-                         "reference": "same H-matrix CN run at N=65536 with 3 FP64 refinement sweeps per step"},
+                         "reference": f"same H-matrix CN run at N={N} with 3 FP64 refinement sweeps per step"},
             "stats": {k: st[k] for k in ("h_bytes", "lu_bytes", "max_rank_seen", "lu_max_rank_seen",
                                          "dense_blocks", "lowrank_blocks", "last_refine_resid", "solve_mode",
                                          "hinv_max_rank", "hinv_capped", "hinv_ms", "factor_ms", "factor_fma",

@@ -65,7 +65,7 @@ def configurations(prob: dict, opts: dict, leafs=(64, 128, 256), solve_blocks=(1
     A `solve` other than "auto" in opts fixes the solve mode."""
     n = _n(prob)
     fixed = opts.get("solve", "auto")
-    hinv_ok = prob["dim"] == 1 and prob.get("domain", 0) == 0 and opts.get("precision", "fp64") == "fp64"
+    hinv_ok = prob["dim"] == 1 and prob.get("domain", 0) == 0
     out = []
     for leaf in leafs:
         if leaf > max(n, 1):
@@ -78,6 +78,9 @@ def configurations(prob: dict, opts: dict, leafs=(64, 128, 256), solve_blocks=(1
                 out.append({"leaf": int(leaf), "solve": "subst", "solve_block": int(b)})
     if opts.get("precision", "fp64") != "fp64":  # the mixed precisions need the inverses
         out = [c for c in out if c["solve"] == "hinv"]
+    if not out:
+        raise ValueError("no solve configuration fits this problem with these options "
+                         f"(dim {prob['dim']}, precision {opts.get('precision', 'fp64')}, solve {fixed})")
     return out
 
 

@@ -962,21 +962,32 @@ int factor_batch_impl(const hm_matrix* const* Hs, const double* alphas, const do
   for (FactorJob& J : jobs)
     if (J.status != HM_OK) { set_error(J.err); return fail_all(J.status); }
   phase("plan solves");
-  for (FactorJob& J : jobs) {
-    hm_factors* F = J.F;
-    if (F->solve_mode != HM_SOLVE_HINV) continue;
-    F->hinv = new HinvData();
-    const int prec = J.H->opts.precision == HM_MIXED_FP32 ? HINV_F32
-                     : (J.H->opts.precision == HM_MIXED_BF16 ? HINV_BF16 : HINV_F64);
-    std::string herr;
-    s = hinv_build(J.H->plan, J.H->h_dd, F->F, F->d_rank, prec, hinv_tolerance(J.H->opts), J.H->d_err, st,
-                   *F->hinv, herr);
-    if (s != HM_OK) { set_error("hierarchical inverses: " + herr); return fail_all(s); }
-    F->lu_bytes = F->hinv->step_bytes;
-    // the solves read only the inverses: the factors and the planner's
-    // temporaries are released (the layout's pointers are dropped with them)
-    F->arena.release();
-    F->F = FactorLayout();
+  {
+    // the inverses of every problem that solves with them, built together
+    std::vector<HinvBuildJob> hjobs;
+    for (FactorJob& J : jobs) {
+      hm_factors* F = J.F;
+      if (F->solve_mode != HM_SOLVE_HINV) continue;
+      F->hinv = new HinvData();
+      const int prec = J.H->opts.precision == HM_MIXED_FP32 ? HINV_F32
+                       : (J.H->opts.precision == HM_MIXED_BF16 ? HINV_BF16 : HINV_F64);
+      hjobs.push_back(HinvBuildJob{&J.H->plan, &J.H->h_dd, &F->F, F->d_rank, prec, hinv_tolerance(J.H->opts),
+                                   F->hinv});
+    }
+    if (!hjobs.empty()) {
+      std::string herr;
+      s = hinv_build_batch(hjobs, d_err, st, herr);
+      if (s != HM_OK) { set_error("hierarchical inverses: " + herr); return fail_all(s); }
+    }
+    for (FactorJob& J : jobs) {
+      hm_factors* F = J.F;
+      if (F->solve_mode != HM_SOLVE_HINV) continue;
+      F->lu_bytes = F->hinv->step_bytes;
+      // the solves read only the inverses: the factors and the planner's
+      // temporaries are released (the layout's pointers are dropped with them)
+      F->arena.release();
+      F->F = FactorLayout();
+    }
   }
   if (count > 0) phase("inverses");
   for (FactorJob& J : jobs) {

@@ -133,6 +133,21 @@ struct HinvData {
 int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
                int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err);
 
+// The same for several factorisations at once: the construction steps of all
+// of them (in groups of at most 2^19 stacked rows) run in one launch per
+// kernel and step.  Each out receives what hinv_build would give it, bit for
+// bit; build_ms is the time of the whole call.  d_err collects device errors.
+struct HinvBuildJob {
+  const Plan* P;
+  const std::vector<DenseDesc>* dd;
+  const FactorLayout* F;
+  const int* d_rank_f;
+  int prec;
+  double tol;
+  HinvData* out;
+};
+int hinv_build_batch(const std::vector<HinvBuildJob>& jobs, int* d_err, cudaStream_t st, std::string& err);
+
 // z = U^{-1} L^{-1} b (Morton order; z may alias b).
 int hinv_solve(const HinvData& D, const double* b, double* z, cudaStream_t st);
 

@@ -395,8 +395,12 @@ struct Core {
   double qc[HINV_SP * HINV_KCAP];      // row-major SP x KCAP
 };
 
-__global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tbuf, Core* cores, int* rank_out,
-                                                   const int* node_of, double tol, int* err) {
+struct CoreOut {   // where the rank of core b goes, and its truncation tolerance
+  int* rank;
+  double tol;
+};
+__global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tbuf, Core* cores,
+                                                   const CoreOut* core_out, int* err) {
   constexpr int M = HINV_SP, NC = HINV_S;
   __shared__ double A[M][NC + 1];
   __shared__ double nrm2[NC];
@@ -405,6 +409,7 @@ __global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tb
   __shared__ int s_p, s_stop;
   __shared__ double s_ref, s_norm;
   const int b = blockIdx.x;
+  const double tol = core_out[b].tol;
   const double* G = tbuf + (int64_t)b * MR_T;  // the core of block b is reduction slot b
   for (int e = threadIdx.x; e < M * NC; e += blockDim.x) A[e / NC][e % NC] = G[e];
   if (threadIdx.x < NC) piv[threadIdx.x] = threadIdx.x;
@@ -497,7 +502,7 @@ __global__ void __launch_bounds__(256) cpqr_kernel(const double* __restrict__ tb
   if (threadIdx.x == 0) {
     out->k = k;
     out->capped = capped;
-    rank_out[node_of[b]] = k;
+    *core_out[b].rank = k;
     if (!isfinite(s_ref)) atomicOr(err, DEVERR_NONFINITE);
   }
 }
@@ -588,6 +593,7 @@ struct Planner {
   std::vector<MrItem> items;
   HostMr cur;
   int max_red = 0, max_rch = 0;
+  int base = 0;  // row offset of the current problem in the shared buffers (added to every row below)
 
   void begin(int S) {
     cur = HostMr();
@@ -599,15 +605,17 @@ struct Planner {
   }
   // T slot = returned id (relative to the plan)
   int red(const double* V, int64_t vrs, int64_t vcs, int in0, int n, const int* rank, int kc) {
-    MrRed R{V, vrs, vcs, in0, n, rank, kc, (int)rch.size() - cur.rch0, 0};
+    MrRed R{V, vrs, vcs, in0 + base, n, rank, kc, (int)rch.size() - cur.rch0, 0};
     const int id = (int)reds.size() - cur.red0;
     for (int j0 = 0; j0 < n; j0 += HINV_MCH) rch.push_back(make_int2(id, j0));
     R.c_end = (int)rch.size() - cur.rch0;
     reds.push_back(R);
     return id;
   }
-  void chunk(int r0, int nr) { chunks.push_back(MrChunk{r0, nr, (int)items.size() - cur.it0, 0}); }
-  void item(const MrItem& I) {
+  void chunk(int r0, int nr) { chunks.push_back(MrChunk{r0 + base, nr, (int)items.size() - cur.it0, 0}); }
+  void item(MrItem I) {
+    I.row0 += base;
+    if (I.kind == 0) I.col0 += base;
     items.push_back(I);
     chunks.back().ie = (int)items.size() - cur.it0;
   }
@@ -651,93 +659,117 @@ struct TNode {   // an internal cluster of the 1D tree
   int a, b;      // children (clusters)
 };
 
-}  // namespace
+struct OffBlock { bool lowrank; int id; int t, s; };
 
-int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
-               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err) {
-  auto t_start = std::chrono::steady_clock::now();
+// One problem of a construction: its tree, the factor blocks between
+// children, its pools and its first row in the shared construction buffers.
+struct Ctx {
+  const Plan* P = nullptr;
+  const std::vector<DenseDesc>* dd = nullptr;
+  const FactorLayout* F = nullptr;
+  const int* d_rank_f = nullptr;
+  HinvData* out = nullptr;
+  double tol = 0.0;
+  int N = 0, nl = 0, nn = 0, maxlev = -1;
+  int base = 0;
+  std::vector<int> dense_of_leaf, node_of;
+  std::vector<TNode> nodes;
+  std::vector<std::vector<int>> anc_t[2], anc_s[2];  // per leaf: nodes whose target (source) holds it, upwards
+  std::vector<std::vector<int>> level_nodes;
+  std::vector<std::vector<OffBlock>> toff[2];        // per node: factor blocks between its children
+  int* d_rank = nullptr;                             // 2 x nn inverse-block ranks
+  double* leafpool[2] = {nullptr, nullptr};
+  double* ppool[2] = {nullptr, nullptr};
+  double* qpool[2] = {nullptr, nullptr};
+  int64_t leaf_elems = 0, p_elems[2] = {0, 0}, q_elems[2] = {0, 0};
+  std::vector<int> h_rank;
+
+  std::pair<int, int> range(int c) const { return std::make_pair(P->cl[c].begin, P->cl[c].end); }
+  // per triangle: target and source cluster of a node
+  static int tgt(int tri, const TNode& T) { return tri == 0 ? T.b : T.a; }
+  static int src(int tri, const TNode& T) { return tri == 0 ? T.a : T.b; }
+};
+
+int out_alloc(HinvData& out, void** p, size_t bytes, std::string& err) {
+  *p = nullptr;
+  if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+    return HM_ERR_OOM;
+  }
+  out.allocs.push_back(*p);
+  out.bytes += (int64_t)std::max<size_t>(bytes, 16);
+  return HM_OK;
+}
+
+template <class T>
+int out_upload(HinvData& out, T** dst, const std::vector<T>& vec, cudaStream_t st, std::string& err) {
+  const size_t n = vec.size() * sizeof(T);
+  void* p = nullptr;
+  HM_TRY(out_alloc(out, &p, n, err));
+  if (n && cudaMemcpyAsync(p, vec.data(), n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    err = std::string("table upload failed: ") + cudaGetErrorString(cudaGetLastError());
+    return HM_ERR_CUDA;
+  }
+  *dst = (T*)p;
+  return HM_OK;
+}
+
+// The tree, the ancestors of every leaf and the blocks between children, and
+// the layout of the per-step pools (host only).
+int ctx_prepare(Ctx& C, std::string& err) {
+  const Plan& P = *C.P;
+  const FactorLayout& F = *C.F;
+  const std::vector<DenseDesc>& dd = *C.dd;
   if (P.dim != 1) { err = "hierarchical inverses are built for 1D problems only"; return HM_ERR_ARG; }
   if (F.kf > HINV_MAXS) { err = "factor rank cap above 64"; return HM_ERR_ARG; }
-  const int N = P.N;
-  // FP64 accuracy: pairs of floats in double-float arithmetic (HM_HINV_FP64=1: FP64 storage and arithmetic)
-  const char* f64 = std::getenv("HM_HINV_FP64");
-  const int aprec = prec == HINV_F64 && !(f64 && f64[0] == '1') ? HINV_DF : prec;
-  out = HinvData();
-  out.prec = aprec;
-  out.tol = tol;
-  auto alloc = [&](void** p, size_t bytes) -> int {
-    *p = nullptr;
-    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-      cudaGetLastError();
-      err = "device allocation of " + std::to_string(bytes) + " bytes failed";
-      return HM_ERR_OOM;
-    }
-    out.allocs.push_back(*p);
-    out.bytes += (int64_t)std::max<size_t>(bytes, 16);
-    return HM_OK;
-  };
-  auto upload = [&](auto** dst, const auto& vec) -> int {
-    const size_t n = vec.size() * sizeof(vec[0]);
-    void* p = nullptr;
-    HM_TRY(alloc(&p, n));
-    if (n && cudaMemcpyAsync(p, vec.data(), n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      err = std::string("table upload failed: ") + cudaGetErrorString(cudaGetLastError());
-      return HM_ERR_CUDA;
-    }
-    *dst = (std::remove_reference_t<decltype(**dst)>*)p;
-    return HM_OK;
-  };
+  if (P.depth > HINV_MAX_ANC) { err = "cluster tree deeper than " + std::to_string(HINV_MAX_ANC); return HM_ERR_ARG; }
+  C.N = P.N;
   // ---- tree: leaves (Morton order) with their diagonal dense block, internal nodes
-  const int nl = (int)P.leaves.size();
-  std::vector<int> leaf_of(P.cl.size(), -1), dense_of_leaf(nl, -1);
+  C.nl = (int)P.leaves.size();
+  const int nl = C.nl;
+  std::vector<int> leaf_of(P.cl.size(), -1);
+  C.dense_of_leaf.assign(nl, -1);
   for (int l = 0; l < nl; ++l) leaf_of[P.leaves[l]] = l;
   for (int d = 0; d < (int)dd.size(); ++d) {
     if (dd[d].r0 != dd[d].c0) continue;
     const int t = P.bl[P.dense_block[d]].t;
-    if (leaf_of[t] >= 0) dense_of_leaf[leaf_of[t]] = d;
+    if (leaf_of[t] >= 0) C.dense_of_leaf[leaf_of[t]] = d;
   }
   for (int l = 0; l < nl; ++l) {
-    const int d = dense_of_leaf[l];
+    const int d = C.dense_of_leaf[l];
     if (d < 0 || !F.linv[d] || !F.uinv[d]) { err = "a leaf has no inverse of its factors"; return HM_ERR_ARG; }
     if (P.cl[P.leaves[l]].end - P.cl[P.leaves[l]].begin > 1024) { err = "leaves above 1024 rows"; return HM_ERR_ARG; }
   }
-  std::vector<TNode> nodes;
-  std::vector<int> node_of(P.cl.size(), -1);
-  int maxlev = -1;
+  C.node_of.assign(P.cl.size(), -1);
   for (int c = 0; c < (int)P.cl.size(); ++c) {
     if (P.cl[c].nchild == 0) continue;
     if (P.cl[c].nchild != 2) { err = "the 1D cluster tree must be binary"; return HM_ERR_ARG; }
-    node_of[c] = (int)nodes.size();
-    nodes.push_back(TNode{c, P.cl[c].level, P.cl[c].child[0], P.cl[c].child[1]});
-    maxlev = std::max(maxlev, P.cl[c].level);
+    C.node_of[c] = (int)C.nodes.size();
+    C.nodes.push_back(TNode{c, P.cl[c].level, P.cl[c].child[0], P.cl[c].child[1]});
+    C.maxlev = std::max(C.maxlev, P.cl[c].level);
   }
-  const int nn = (int)nodes.size();
-  auto range = [&](int c) { return std::make_pair(P.cl[c].begin, P.cl[c].end); };
-  // per triangle: target and source cluster of every node
-  auto tgt = [&](int tri, const TNode& T) { return tri == 0 ? T.b : T.a; };
-  auto src = [&](int tri, const TNode& T) { return tri == 0 ? T.a : T.b; };
-  if (P.depth > HINV_MAX_ANC) { err = "cluster tree deeper than " + std::to_string(HINV_MAX_ANC); return HM_ERR_ARG; }
-  // per leaf and triangle: nodes whose target (src) range holds the leaf, from the leaf up
-  std::vector<std::vector<int>> anc_t[2], anc_s[2];
+  C.nn = (int)C.nodes.size();
+  const int nn = C.nn;
+  C.level_nodes.assign(std::max(C.maxlev + 1, 0), {});
+  for (int v = 0; v < nn; ++v) C.level_nodes[C.nodes[v].level].push_back(v);
   for (int tri = 0; tri < 2; ++tri) {
-    anc_t[tri].resize(nl);
-    anc_s[tri].resize(nl);
+    C.anc_t[tri].resize(nl);
+    C.anc_s[tri].resize(nl);
     for (int l = 0; l < nl; ++l) {
       int c = P.leaves[l];
       while (P.cl[c].parent >= 0) {
         const int par = P.cl[c].parent;
-        const TNode& T = nodes[node_of[par]];
-        if (tgt(tri, T) == c) anc_t[tri][l].push_back(node_of[par]);
-        else anc_s[tri][l].push_back(node_of[par]);
+        const TNode& T = C.nodes[C.node_of[par]];
+        if (Ctx::tgt(tri, T) == c) C.anc_t[tri][l].push_back(C.node_of[par]);
+        else C.anc_s[tri][l].push_back(C.node_of[par]);
         c = par;
       }
     }
   }
   // ---- factor blocks between the children of each node (T_off), by triangle
-  struct OffBlock { bool lowrank; int id; int t, s; };
-  std::vector<std::vector<OffBlock>> toff[2];
-  toff[0].resize(nn);
-  toff[1].resize(nn);
+  C.toff[0].assign(nn, {});
+  C.toff[1].assign(nn, {});
   auto lca = [&](int t, int s) {
     int c = t;
     while (!(P.cl[c].begin <= P.cl[s].begin && P.cl[s].end <= P.cl[c].end)) c = P.cl[c].parent;
@@ -748,36 +780,27 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     if (B.t == B.s) continue;
     const int A = lca(B.t, B.s);
     const bool lower = P.cl[B.t].begin >= P.cl[P.cl[A].child[1]].begin;
-    toff[lower ? 0 : 1][node_of[A]].push_back(OffBlock{false, d, B.t, B.s});
+    C.toff[lower ? 0 : 1][C.node_of[A]].push_back(OffBlock{false, d, B.t, B.s});
   }
   for (int q = 0; q < (int)P.lr_block.size(); ++q) {
     const Block& B = P.bl[P.lr_block[q]];
     const int A = lca(B.t, B.s);
     const bool lower = P.cl[B.t].begin >= P.cl[P.cl[A].child[1]].begin;
-    toff[lower ? 0 : 1][node_of[A]].push_back(OffBlock{true, q, B.t, B.s});
+    C.toff[lower ? 0 : 1][C.node_of[A]].push_back(OffBlock{true, q, B.t, B.s});
   }
-  // ---- FP64 pools: leaves, P, Q, ranks; per-step tables
-  int* d_rank = nullptr;
-  HM_TRY(alloc((void**)&d_rank, sizeof(int) * 2 * std::max(nn, 1)));
-  if (cudaMemsetAsync(d_rank, 0, sizeof(int) * 2 * std::max(nn, 1), st) != cudaSuccess) {
-    err = std::string("clearing the ranks failed: ") + cudaGetErrorString(cudaGetLastError());
-    return HM_ERR_CUDA;
-  }
-  double* leafpool[2];
-  double* ppool[2];
-  double* qpool[2];
-  int64_t leaf_elems = 0, p_elems[2] = {0, 0}, q_elems[2] = {0, 0};
+  // ---- layout of the pools: leaves, P, Q
+  C.leaf_elems = 0;
   for (int l = 0; l < nl; ++l) {
     const int m = P.cl[P.leaves[l]].end - P.cl[P.leaves[l]].begin;
-    leaf_elems += (int64_t)m * round8(m);
+    C.leaf_elems += (int64_t)m * round8(m);
   }
   for (int tri = 0; tri < 2; ++tri) {
-    HinvTriangle& H = out.tri[tri];
+    HinvTriangle& H = C.out->tri[tri];
     H.h_leaves.resize(nl);
     H.h_nodes.resize(nn);
     int64_t lo = 0, po = 0, qo = 0;
     for (int l = 0; l < nl; ++l) {
-      const auto r = range(P.leaves[l]);
+      const auto r = C.range(P.leaves[l]);
       HinvLeaf& L = H.h_leaves[l];
       L.r0 = r.first;
       L.m = r.second - r.first;
@@ -787,7 +810,7 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     }
     for (int v = 0; v < nn; ++v) {
       HinvNode& Nd = H.h_nodes[v];
-      const auto rt = range(tgt(tri, nodes[v])), rs = range(src(tri, nodes[v]));
+      const auto rt = C.range(Ctx::tgt(tri, C.nodes[v])), rs = C.range(Ctx::src(tri, C.nodes[v]));
       Nd.tgt0 = rt.first;
       Nd.tgt_n = rt.second - rt.first;
       Nd.src0 = rs.first;
@@ -799,26 +822,223 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
       po += (int64_t)Nd.pld * HINV_KCAP;
       qo += (int64_t)Nd.qld * HINV_KCAP;
     }
-    p_elems[tri] = po;
-    q_elems[tri] = qo;
-    HM_TRY(alloc((void**)&leafpool[tri], sizeof(double) * std::max<int64_t>(leaf_elems, 1)));
-    HM_TRY(alloc((void**)&ppool[tri], sizeof(double) * std::max<int64_t>(po, 1)));
-    HM_TRY(alloc((void**)&qpool[tri], sizeof(double) * std::max<int64_t>(qo, 1)));
+    C.p_elems[tri] = po;
+    C.q_elems[tri] = qo;
   }
-  // leaf inverses -> triangles
+  return HM_OK;
+}
+
+// X (transposed or not) on the source (target) part of every node of the
+// level: the leaf inverses and the inverse blocks of the deeper levels
+void plan_x(Planner& PL, const Ctx& C, int tri, int lev, bool trans, bool on_src) {
+  const HinvTriangle& H = C.out->tri[tri];
+  const int* rk = C.d_rank + tri * C.nn;
+  std::vector<int> slot(C.nn, -1);
+  for (int v : C.level_nodes[lev]) {
+    const int part = on_src ? Ctx::src(tri, C.nodes[v]) : Ctx::tgt(tri, C.nodes[v]);
+    const auto pr = C.range(part);
+    for (int l = 0; l < C.nl; ++l) {
+      const HinvLeaf& L = H.h_leaves[l];
+      if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
+      const std::vector<int>& anc = trans ? C.anc_s[tri][l] : C.anc_t[tri][l];
+      for (int q : anc) {
+        if (C.nodes[q].level <= lev || slot[q] >= 0) continue;
+        const HinvNode& Q = H.h_nodes[q];
+        slot[q] = trans ? PL.red(C.ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, Q.tgt_n, rk + q, HINV_KCAP)
+                        : PL.red(C.qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, Q.src_n, rk + q, HINV_KCAP);
+      }
+      for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
+        PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
+        const double* X = C.leafpool[tri] + L.off;
+        const int mask = (tri == 0) != trans ? 1 : 2;
+        // the leaf is stored column-major: X(i, j) = X[j ld + i]
+        PL.item(trans ? dense_item(X, L.ld, 1, L.r0, L.r0, L.m, mask)
+                      : dense_item(X, 1, L.ld, L.r0, L.r0, L.m, mask));
+        for (int q : anc) {
+          if (C.nodes[q].level <= lev) continue;
+          const HinvNode& Q = H.h_nodes[q];
+          PL.item(trans ? lr_item(C.qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, rk + q, HINV_KCAP, slot[q])
+                        : lr_item(C.ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, rk + q, HINV_KCAP, slot[q]));
+        }
+      }
+    }
+  }
+}
+
+// T_off (transposed or not) of every node of the level: output rows = its
+// target (source) part
+void plan_t(Planner& PL, const Ctx& C, int tri, int lev, bool trans) {
+  const Plan& P = *C.P;
+  const FactorLayout& F = *C.F;
+  const HinvTriangle& H = C.out->tri[tri];
+  const int kf = F.kf;
+  for (int v : C.level_nodes[lev]) {
+    const int part = trans ? Ctx::src(tri, C.nodes[v]) : Ctx::tgt(tri, C.nodes[v]);
+    const auto pr = C.range(part);
+    const std::vector<OffBlock>& ob = C.toff[tri][v];
+    std::vector<int> slot(ob.size(), -1);
+    for (size_t k = 0; k < ob.size(); ++k) {
+      if (!ob[k].lowrank) continue;
+      const int q = ob[k].id;
+      const int m = P.cl[ob[k].t].end - P.cl[ob[k].t].begin, n = P.cl[ob[k].s].end - P.cl[ob[k].s].begin;
+      slot[k] = trans ? PL.red(F.lr_u[q], 1, m, P.cl[ob[k].t].begin, m, C.d_rank_f + q, kf)
+                      : PL.red(F.lr_v[q], 1, n, P.cl[ob[k].s].begin, n, C.d_rank_f + q, kf);
+    }
+    for (int l = 0; l < C.nl; ++l) {
+      const HinvLeaf& L = H.h_leaves[l];
+      if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
+      for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
+        PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
+        for (size_t k = 0; k < ob.size(); ++k) {
+          const Cluster& T = P.cl[ob[k].t];
+          const Cluster& Sc = P.cl[ob[k].s];
+          const Cluster& out_cl = trans ? Sc : T;
+          if (L.r0 < out_cl.begin || L.r0 + L.m > out_cl.end) continue;
+          if (!ob[k].lowrank) {
+            const View& V = F.dense[ob[k].id];
+            PL.item(trans ? dense_item(V.p, V.cs, V.rs, Sc.begin, T.begin, T.end - T.begin, 0)
+                          : dense_item(V.p, V.rs, V.cs, T.begin, Sc.begin, Sc.end - Sc.begin, 0));
+          } else {
+            const int q = ob[k].id;
+            const int m = T.end - T.begin, n = Sc.end - Sc.begin;
+            PL.item(trans ? lr_item(F.lr_v[q], 1, n, Sc.begin, C.d_rank_f + q, kf, slot[k])
+                          : lr_item(F.lr_u[q], 1, m, T.begin, C.d_rank_f + q, kf, slot[k]));
+          }
+        }
+      }
+    }
+  }
+}
+
+// The inverses of a group of problems.  The problems' rows are stacked in the
+// shared construction buffers; every construction step (level, triangle)
+// runs for all problems with nodes on that level in one launch per kernel.
+// The values do not depend on the grouping: every reduction sums its chunks
+// in a fixed order, the sketches are seeded by level, triangle and the
+// problem's own row.  Synchronises the stream.
+int build_group(std::vector<Ctx>& G, int* d_err, cudaStream_t st, std::string& err) {
+  const auto t_start = std::chrono::steady_clock::now();
+  std::vector<void*> tmp;
+  auto free_tmp = [&]() {
+    for (void* p : tmp) cudaFree(p);
+    tmp.clear();
+  };
+  auto tmp_alloc = [&](void** p, size_t bytes) -> int {
+    *p = nullptr;
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      err = "device allocation of construction buffers failed";
+      return HM_ERR_OOM;
+    }
+    tmp.push_back(*p);
+    return HM_OK;
+  };
+  auto tmp_upload = [&](auto** dst, const auto& vec) -> int {
+    const size_t n = vec.size() * sizeof(vec[0]);
+    void* p = nullptr;
+    HM_TRY(tmp_alloc(&p, n));
+    if (n && cudaMemcpyAsync(p, vec.data(), n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      err = std::string("construction table upload failed: ") + cudaGetErrorString(cudaGetLastError());
+      return HM_ERR_CUDA;
+    }
+    *dst = (std::remove_reference_t<decltype(**dst)>*)p;
+    return HM_OK;
+  };
+  auto fail = [&](int s) {
+    free_tmp();
+    if (err.empty()) err = "hierarchical inverse construction failed";
+    return s;
+  };
+  // ---- rows in the shared buffers; pools (FP64: the construction's; they
+  // are the per-step storage only in FP64, otherwise one shared temporary)
+  int64_t rows = 0, tmp_pool = 0;
+  auto pad32 = [](int64_t n) { return (n + 31) & ~int64_t(31); };
+  int gmax = -1;
+  for (Ctx& C : G) {
+    if (rows + C.N > INT32_MAX) return fail(HM_ERR_ARG);
+    C.base = (int)rows;
+    rows += C.N;
+    gmax = std::max(gmax, C.maxlev);
+    if (C.out->prec != HINV_F64)
+      for (int tri = 0; tri < 2; ++tri) tmp_pool += pad32(C.p_elems[tri]) + pad32(C.q_elems[tri]) + pad32(C.leaf_elems);
+  }
+  int s = HM_OK;
+  double* pool64 = nullptr;
+  if ((s = tmp_alloc((void**)&pool64, sizeof(double) * std::max<int64_t>(tmp_pool, 1))) != HM_OK) return fail(s);
+  // P and Q pools first (one clear for all), then the leaves
+  int64_t at = 0;
+  for (Ctx& C : G)
+    if (C.out->prec != HINV_F64)
+      for (int tri = 0; tri < 2; ++tri) {
+        C.ppool[tri] = pool64 + at;
+        at += pad32(C.p_elems[tri]);
+        C.qpool[tri] = pool64 + at;
+        at += pad32(C.q_elems[tri]);
+      }
+  const int64_t pq_elems = at;
+  for (Ctx& C : G)
+    if (C.out->prec != HINV_F64)
+      for (int tri = 0; tri < 2; ++tri) {
+        C.leafpool[tri] = pool64 + at;
+        at += pad32(C.leaf_elems);
+      }
+  if (pq_elems && cudaMemsetAsync(pool64, 0, sizeof(double) * pq_elems, st) != cudaSuccess) {
+    err = "clearing the inverse pools failed";
+    return fail(HM_ERR_CUDA);
+  }
+  for (Ctx& C : G) {
+    HinvData& out = *C.out;
+    if ((s = out_alloc(out, (void**)&C.d_rank, sizeof(int) * 2 * std::max(C.nn, 1), err)) != HM_OK) return fail(s);
+    if (cudaMemsetAsync(C.d_rank, 0, sizeof(int) * 2 * std::max(C.nn, 1), st) != cudaSuccess) {
+      err = std::string("clearing the ranks failed: ") + cudaGetErrorString(cudaGetLastError());
+      return fail(HM_ERR_CUDA);
+    }
+    if (out.prec != HINV_F64) continue;
+    for (int tri = 0; tri < 2; ++tri) {
+      if ((s = out_alloc(out, (void**)&C.leafpool[tri], sizeof(double) * std::max<int64_t>(C.leaf_elems, 1), err)) != HM_OK ||
+          (s = out_alloc(out, (void**)&C.ppool[tri], sizeof(double) * std::max<int64_t>(C.p_elems[tri], 1), err)) != HM_OK ||
+          (s = out_alloc(out, (void**)&C.qpool[tri], sizeof(double) * std::max<int64_t>(C.q_elems[tri], 1), err)) != HM_OK)
+        return fail(s);
+      if (cudaMemsetAsync(C.ppool[tri], 0, sizeof(double) * std::max<int64_t>(C.p_elems[tri], 1), st) != cudaSuccess ||
+          cudaMemsetAsync(C.qpool[tri], 0, sizeof(double) * std::max<int64_t>(C.q_elems[tri], 1), st) != cudaSuccess) {
+        err = "clearing the inverse pools failed";
+        return fail(HM_ERR_CUDA);
+      }
+    }
+  }
+  // ---- leaf inverses -> triangles (one launch)
   {
     std::vector<LeafCopy> lc;
-    for (int tri = 0; tri < 2; ++tri)
-      for (int l = 0; l < nl; ++l) {
-        const int d = dense_of_leaf[l];
-        const HinvLeaf& L = out.tri[tri].h_leaves[l];
-        lc.push_back(LeafCopy{tri == 0 ? F.linv[d] : F.uinv[d], F.linv_ld[d], leafpool[tri] + L.off, L.ld, L.m,
-                              tri == 0 ? 1 : 0});
-      }
+    for (Ctx& C : G)
+      for (int tri = 0; tri < 2; ++tri)
+        for (int l = 0; l < C.nl; ++l) {
+          const int d = C.dense_of_leaf[l];
+          const HinvLeaf& L = C.out->tri[tri].h_leaves[l];
+          lc.push_back(LeafCopy{tri == 0 ? C.F->linv[d] : C.F->uinv[d], C.F->linv_ld[d], C.leafpool[tri] + L.off, L.ld,
+                                L.m, tri == 0 ? 1 : 0});
+        }
     LeafCopy* d_lc = nullptr;
-    HM_TRY(upload(&d_lc, lc));
-    count_launches(1);
-    leaf_copy_kernel<<<(unsigned)lc.size(), 256, 0, st>>>(d_lc);
+    if ((s = tmp_upload(&d_lc, lc)) != HM_OK) return fail(s);
+    if (!lc.empty()) {
+      count_launches(1);
+      leaf_copy_kernel<<<(unsigned)lc.size(), 256, 0, st>>>(d_lc);
+    }
+  }
+  // ---- shared construction buffers (rows x width, row-major), per triangle
+  double* bufA[2];
+  double* bufB[2];
+  double* bufC[2];
+  double* bufD[2];
+  double* bufE[2];
+  for (int tri = 0; tri < 2; ++tri) {
+    double* blk = nullptr;
+    if ((s = tmp_alloc((void**)&blk, sizeof(double) * std::max<int64_t>(rows, 1) * (2 * HINV_S + 3 * HINV_SP))) != HM_OK)
+      return fail(s);
+    bufA[tri] = blk;
+    bufB[tri] = bufA[tri] + rows * HINV_S;
+    bufC[tri] = bufB[tri] + rows * HINV_S;
+    bufD[tri] = bufC[tri] + rows * HINV_SP;
+    bufE[tri] = bufD[tri] + rows * HINV_SP;
   }
   // ---- construction plans, level by level (deepest first), both triangles
   Planner PL;
@@ -827,210 +1047,104 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     HostMr mr[7];              // XR, TR, XR2, XC, TC, XC2, gram
     std::vector<FillJob> fill;
     std::vector<FormJob> form;
-    std::vector<int> core_node;  // rank index per core
+    std::vector<CoreOut> core_out;  // per core (reduction slot of the gram plan)
   };
   std::vector<Step> steps;
-  double* bufA[2];
-  double* bufB[2];
-  double* bufC[2];
-  double* bufD[2];
-  double* bufE[2];
-  std::vector<void*> tmp_allocs;
-  auto tmp_alloc = [&](double** p, int64_t n) -> int {
-    if (cudaMalloc((void**)p, sizeof(double) * std::max<int64_t>(n, 1)) != cudaSuccess) {
-      cudaGetLastError();
-      err = "device allocation of construction buffers failed";
-      return HM_ERR_OOM;
-    }
-    tmp_allocs.push_back(*p);
-    return HM_OK;
-  };
-  auto free_tmp = [&]() {
-    for (void* p : tmp_allocs) cudaFree(p);
-    tmp_allocs.clear();
-  };
-  int s = HM_OK;
-  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
-    if ((s = tmp_alloc(&bufA[tri], (int64_t)N * HINV_S)) != HM_OK) break;
-    if ((s = tmp_alloc(&bufB[tri], (int64_t)N * HINV_S)) != HM_OK) break;
-    if ((s = tmp_alloc(&bufC[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
-    if ((s = tmp_alloc(&bufD[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
-    if ((s = tmp_alloc(&bufE[tri], (int64_t)N * HINV_SP)) != HM_OK) break;
-  }
-  if (s != HM_OK) { free_tmp(); return s; }
-  const int kf = F.kf;
-  for (int lev = maxlev; lev >= 0; --lev) {
-    std::vector<int> lv;
-    for (int v = 0; v < nn; ++v)
-      if (nodes[v].level == lev) lv.push_back(v);
-    if (lv.empty()) continue;
+  for (int lev = gmax; lev >= 0; --lev) {
+    std::vector<Ctx*> on;  // problems with nodes on this level
+    for (Ctx& C : G)
+      if (lev <= C.maxlev && !C.level_nodes[lev].empty()) on.push_back(&C);
+    if (on.empty()) continue;
     for (int tri = 0; tri < 2; ++tri) {
-      const HinvTriangle& H = out.tri[tri];
-      const int* rk = d_rank + tri * nn;
       Step S;
       S.tri = tri;
       S.level = lev;
-      // X (transposed or not) on the given part of every node of the level
-      auto x_plan = [&](bool trans, bool on_src, int width) {
+      auto plan_all = [&](int width, auto&& body) {
         PL.begin(width);
-        std::vector<int> slot(nn, -1);
-        for (int v : lv) {
-          const int part = on_src ? src(tri, nodes[v]) : tgt(tri, nodes[v]);
-          const auto pr = range(part);
-          for (int l = 0; l < nl; ++l) {
-            const HinvLeaf& L = H.h_leaves[l];
-            if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
-            const std::vector<int>& anc = trans ? anc_s[tri][l] : anc_t[tri][l];
-            for (int q : anc) {
-              if (nodes[q].level <= lev || slot[q] >= 0) continue;
-              const HinvNode& Q = H.h_nodes[q];
-              slot[q] = trans ? PL.red(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, Q.tgt_n, rk + q, HINV_KCAP)
-                              : PL.red(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, Q.src_n, rk + q, HINV_KCAP);
-            }
-            for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
-              PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
-              const double* X = leafpool[tri] + L.off;
-              const int mask = (tri == 0) != trans ? 1 : 2;
-              // the leaf is stored column-major: X(i, j) = X[j ld + i]
-              PL.item(trans ? dense_item(X, L.ld, 1, L.r0, L.r0, L.m, mask)
-                            : dense_item(X, 1, L.ld, L.r0, L.r0, L.m, mask));
-              for (int q : anc) {
-                if (nodes[q].level <= lev) continue;
-                const HinvNode& Q = H.h_nodes[q];
-                PL.item(trans ? lr_item(qpool[tri] + Q.qoff, 1, Q.qld, Q.src0, rk + q, HINV_KCAP, slot[q])
-                              : lr_item(ppool[tri] + Q.poff, 1, Q.pld, Q.tgt0, rk + q, HINV_KCAP, slot[q]));
-              }
-            }
-          }
+        for (Ctx* C : on) {
+          PL.base = C->base;
+          body(*C);
         }
+        PL.base = 0;
         return PL.end();
       };
-      // T_off (transposed or not): output rows = target (source) part
-      auto t_plan = [&](bool trans, int width) {
-        PL.begin(width);
-        for (int v : lv) {
-          const int part = trans ? src(tri, nodes[v]) : tgt(tri, nodes[v]);
-          const auto pr = range(part);
-          const std::vector<OffBlock>& ob = toff[tri][v];
-          std::vector<int> slot(ob.size(), -1);
-          for (size_t k = 0; k < ob.size(); ++k) {
-            if (!ob[k].lowrank) continue;
-            const int q = ob[k].id;
-            const int m = P.cl[ob[k].t].end - P.cl[ob[k].t].begin, n = P.cl[ob[k].s].end - P.cl[ob[k].s].begin;
-            slot[k] = trans ? PL.red(F.lr_u[q], 1, m, P.cl[ob[k].t].begin, m, d_rank_f + q, kf)
-                            : PL.red(F.lr_v[q], 1, n, P.cl[ob[k].s].begin, n, d_rank_f + q, kf);
-          }
-          for (int l = 0; l < nl; ++l) {
-            const HinvLeaf& L = H.h_leaves[l];
-            if (L.r0 < pr.first || L.r0 + L.m > pr.second) continue;
-            for (int i0 = 0; i0 < L.m; i0 += HINV_RCH) {
-              PL.chunk(L.r0 + i0, std::min(HINV_RCH, L.m - i0));
-              for (size_t k = 0; k < ob.size(); ++k) {
-                const Cluster& T = P.cl[ob[k].t];
-                const Cluster& Sc = P.cl[ob[k].s];
-                const Cluster& out_cl = trans ? Sc : T;
-                if (L.r0 < out_cl.begin || L.r0 + L.m > out_cl.end) continue;
-                if (!ob[k].lowrank) {
-                  const View& V = F.dense[ob[k].id];
-                  PL.item(trans ? dense_item(V.p, V.cs, V.rs, Sc.begin, T.begin, T.end - T.begin, 0)
-                                : dense_item(V.p, V.rs, V.cs, T.begin, Sc.begin, Sc.end - Sc.begin, 0));
-                } else {
-                  const int q = ob[k].id;
-                  const int m = T.end - T.begin, n = Sc.end - Sc.begin;
-                  PL.item(trans ? lr_item(F.lr_v[q], 1, n, Sc.begin, d_rank_f + q, kf, slot[k])
-                                : lr_item(F.lr_u[q], 1, m, T.begin, d_rank_f + q, kf, slot[k]));
-                }
-              }
-            }
-          }
+      S.mr[0] = plan_all(HINV_S, [&](const Ctx& C) { plan_x(PL, C, tri, lev, false, true); });
+      S.mr[1] = plan_all(HINV_S, [&](const Ctx& C) { plan_t(PL, C, tri, lev, false); });
+      S.mr[2] = plan_all(HINV_S, [&](const Ctx& C) { plan_x(PL, C, tri, lev, false, false); });
+      S.mr[3] = plan_all(HINV_SP, [&](const Ctx& C) { plan_x(PL, C, tri, lev, true, false); });
+      S.mr[4] = plan_all(HINV_SP, [&](const Ctx& C) { plan_t(PL, C, tri, lev, true); });
+      S.mr[5] = plan_all(HINV_SP, [&](const Ctx& C) { plan_x(PL, C, tri, lev, true, true); });
+      S.mr[6] = plan_all(HINV_S, [&](const Ctx& C) {
+        for (int v : C.level_nodes[lev]) {
+          const HinvNode& Nd = C.out->tri[tri].h_nodes[v];
+          PL.red(bufC[tri] + ((int64_t)C.base + Nd.tgt0) * HINV_SP, HINV_SP, 1, Nd.tgt0, Nd.tgt_n, nullptr, HINV_SP);
         }
-        return PL.end();
-      };
-      S.mr[0] = x_plan(false, true, HINV_S);
-      S.mr[1] = t_plan(false, HINV_S);
-      S.mr[2] = x_plan(false, false, HINV_S);
-      S.mr[3] = x_plan(true, false, HINV_SP);
-      S.mr[4] = t_plan(true, HINV_SP);
-      S.mr[5] = x_plan(true, true, HINV_SP);
-      PL.begin(HINV_S);
-      for (int v : lv) {
-        const HinvNode& Nd = H.h_nodes[v];
-        PL.red(bufC[tri] + (int64_t)Nd.tgt0 * HINV_SP, HINV_SP, 1, Nd.tgt0, Nd.tgt_n, nullptr, HINV_SP);
-      }
-      S.mr[6] = PL.end();
+      });
       const unsigned long long seed = 1000003ull * (unsigned long long)(lev + 1) + 17ull * tri;
-      for (size_t b = 0; b < lv.size(); ++b) {
-        const HinvNode& Nd = H.h_nodes[lv[b]];
-        // 128-row pieces (one CTA each; the values depend on the absolute row only)
-        for (int r = 0; r < Nd.src_n; r += HINV_MCH)
-          S.fill.push_back(FillJob{bufA[tri], Nd.src0 + r, std::min(HINV_MCH, Nd.src_n - r), HINV_S, 2 * seed});
-        for (int r = 0; r < Nd.tgt_n; r += HINV_MCH)
-          S.fill.push_back(FillJob{bufC[tri], Nd.tgt0 + r, std::min(HINV_MCH, Nd.tgt_n - r), HINV_SP, 2 * seed + 1});
-        S.core_node.push_back(tri * nn + lv[b]);
-        for (int r = 0; r < Nd.tgt_n; r += HINV_RCH)
-          S.form.push_back(FormJob{0, (int)b, Nd.tgt0, Nd.tgt_n, r, ppool[tri] + Nd.poff, Nd.pld, bufB[tri], HINV_S});
-        for (int r = 0; r < Nd.src_n; r += HINV_RCH)
-          S.form.push_back(FormJob{1, (int)b, Nd.src0, Nd.src_n, r, qpool[tri] + Nd.qoff, Nd.qld, bufD[tri], HINV_SP});
+      int b = 0;
+      for (Ctx* C : on) {
+        double* A0 = bufA[tri] + (int64_t)C->base * HINV_S;
+        double* B0 = bufB[tri] + (int64_t)C->base * HINV_S;
+        double* C0 = bufC[tri] + (int64_t)C->base * HINV_SP;
+        double* D0 = bufD[tri] + (int64_t)C->base * HINV_SP;
+        for (int v : C->level_nodes[lev]) {
+          const HinvNode& Nd = C->out->tri[tri].h_nodes[v];
+          // 128-row pieces (one CTA each; the values depend on the problem's own row only)
+          for (int r = 0; r < Nd.src_n; r += HINV_MCH)
+            S.fill.push_back(FillJob{A0, Nd.src0 + r, std::min(HINV_MCH, Nd.src_n - r), HINV_S, 2 * seed});
+          for (int r = 0; r < Nd.tgt_n; r += HINV_MCH)
+            S.fill.push_back(FillJob{C0, Nd.tgt0 + r, std::min(HINV_MCH, Nd.tgt_n - r), HINV_SP, 2 * seed + 1});
+          S.core_out.push_back(CoreOut{C->d_rank + tri * C->nn + v, C->tol});
+          for (int r = 0; r < Nd.tgt_n; r += HINV_RCH)
+            S.form.push_back(FormJob{0, b, Nd.tgt0, Nd.tgt_n, r, C->ppool[tri] + Nd.poff, Nd.pld, B0, HINV_S});
+          for (int r = 0; r < Nd.src_n; r += HINV_RCH)
+            S.form.push_back(FormJob{1, b, Nd.src0, Nd.src_n, r, C->qpool[tri] + Nd.qoff, Nd.qld, D0, HINV_SP});
+          ++b;
+        }
       }
       steps.push_back(std::move(S));
     }
   }
-  // ---- upload every plan at once, then run the levels in order
+  // ---- upload every plan at once, then run the steps in order
+  std::vector<FillJob> all_fill;
+  std::vector<FormJob> all_form;
+  std::vector<CoreOut> all_core;
+  std::vector<int> fill_off, form_off, core_off;
+  int max_cores = 1;
+  for (const Step& S : steps) {
+    fill_off.push_back((int)all_fill.size());
+    form_off.push_back((int)all_form.size());
+    core_off.push_back((int)all_core.size());
+    all_fill.insert(all_fill.end(), S.fill.begin(), S.fill.end());
+    all_form.insert(all_form.end(), S.form.begin(), S.form.end());
+    all_core.insert(all_core.end(), S.core_out.begin(), S.core_out.end());
+    max_cores = std::max(max_cores, (int)S.core_out.size());
+  }
   MrRed* d_reds = nullptr;
   int2* d_rch = nullptr;
   MrChunk* d_chunks = nullptr;
   MrItem* d_items = nullptr;
+  FillJob* d_fill = nullptr;
+  FormJob* d_form = nullptr;
+  CoreOut* d_core = nullptr;
   double* d_partial = nullptr;
   double* d_tbuf = nullptr;
   unsigned* d_count = nullptr;
   Core* d_cores = nullptr;
-  std::vector<FillJob> all_fill;
-  std::vector<FormJob> all_form;
-  std::vector<int> all_core_node;
-  std::vector<int> fill_off, form_off, core_off;
-  int max_nodes_level = 1;
-  for (const Step& S : steps) {
-    fill_off.push_back((int)all_fill.size());
-    form_off.push_back((int)all_form.size());
-    core_off.push_back((int)all_core_node.size());
-    all_fill.insert(all_fill.end(), S.fill.begin(), S.fill.end());
-    all_form.insert(all_form.end(), S.form.begin(), S.form.end());
-    all_core_node.insert(all_core_node.end(), S.core_node.begin(), S.core_node.end());
-    max_nodes_level = std::max(max_nodes_level, (int)S.core_node.size());
-  }
-  FillJob* d_fill = nullptr;
-  FormJob* d_form = nullptr;
-  int* d_core_node = nullptr;
-  auto tmp_upload = [&](auto** dst, const auto& vec) -> int {
-    const size_t n = std::max<size_t>(vec.size() * sizeof(vec[0]), 16);
-    void* p = nullptr;
-    if (cudaMalloc(&p, n) != cudaSuccess) { cudaGetLastError(); err = "device allocation failed"; return HM_ERR_OOM; }
-    tmp_allocs.push_back(p);
-    if (!vec.empty() && cudaMemcpyAsync(p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return HM_ERR_CUDA;
-    *dst = (std::remove_reference_t<decltype(**dst)>*)p;
-    return HM_OK;
-  };
   if (s == HM_OK) s = tmp_upload(&d_reds, PL.reds);
   if (s == HM_OK) s = tmp_upload(&d_rch, PL.rch);
   if (s == HM_OK) s = tmp_upload(&d_chunks, PL.chunks);
   if (s == HM_OK) s = tmp_upload(&d_items, PL.items);
   if (s == HM_OK) s = tmp_upload(&d_fill, all_fill);
   if (s == HM_OK) s = tmp_upload(&d_form, all_form);
-  if (s == HM_OK) s = tmp_upload(&d_core_node, all_core_node);
-  if (s == HM_OK) s = tmp_alloc(&d_partial, (int64_t)std::max(PL.max_rch, 1) * MR_T);
-  if (s == HM_OK) s = tmp_alloc(&d_tbuf, (int64_t)std::max(PL.max_red, 1) * MR_T);
-  if (s == HM_OK) s = tmp_alloc((double**)&d_count, std::max(PL.max_red, 1));
-  if (s == HM_OK) s = tmp_alloc((double**)&d_cores, ((int64_t)max_nodes_level * sizeof(Core) + 7) / 8);
-  if (s == HM_OK && cudaMemsetAsync(d_count, 0, sizeof(double) * std::max(PL.max_red, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
-  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
-    if (cudaMemsetAsync(ppool[tri], 0, sizeof(double) * std::max<int64_t>(p_elems[tri], 1), st) != cudaSuccess ||
-        cudaMemsetAsync(qpool[tri], 0, sizeof(double) * std::max<int64_t>(q_elems[tri], 1), st) != cudaSuccess) {
-      err = "clearing the inverse pools failed";
-      s = HM_ERR_CUDA;
-    }
-  }
-  if (s != HM_OK) { free_tmp(); return s; }
+  if (s == HM_OK) s = tmp_upload(&d_core, all_core);
+  if (s == HM_OK) s = tmp_alloc((void**)&d_partial, sizeof(double) * std::max(PL.max_rch, 1) * MR_T);
+  if (s == HM_OK) s = tmp_alloc((void**)&d_tbuf, sizeof(double) * std::max(PL.max_red, 1) * MR_T);
+  if (s == HM_OK) s = tmp_alloc((void**)&d_count, sizeof(unsigned) * std::max(PL.max_red, 1));
+  if (s == HM_OK) s = tmp_alloc((void**)&d_cores, sizeof(Core) * max_cores);
+  if (s == HM_OK && cudaMemsetAsync(d_count, 0, sizeof(unsigned) * std::max(PL.max_red, 1), st) != cudaSuccess)
+    s = HM_ERR_CUDA;
+  if (s != HM_OK) return fail(s);
   const char* b64 = std::getenv("HM_HINV_BUILD_FP64");  // FP64 products in the construction (checks)
   const bool build_fp64 = b64 && b64[0] == '1';
   auto run_mr = [&](const HostMr& h, const double* in, double* o) {
@@ -1061,195 +1175,233 @@ int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayo
     run_mr(S.mr[4], bufD[t], bufE[t]);   // T_off^T X^T Psi  (source rows)
     run_mr(S.mr[5], bufE[t], bufD[t]);   // C3               (source rows)
     run_mr(S.mr[6], bufB[t], nullptr);   // cores Psi^T R3 in slots 0..
-    const int nb = (int)S.core_node.size();
+    const int nb = (int)S.core_out.size();
     count_launches(2);
-    cpqr_kernel<<<nb, 256, 0, st>>>(d_tbuf, d_cores, d_rank, d_core_node + core_off[k], tol, d_err);
+    cpqr_kernel<<<nb, 256, 0, st>>>(d_tbuf, d_cores, d_core + core_off[k], d_err);
     form_kernel<<<(unsigned)S.form.size(), 256, 0, st>>>(d_form + form_off[k], d_cores);
   }
-  if (cudaGetLastError() != cudaSuccess) { free_tmp(); err = "construction launch failed"; return HM_ERR_CUDA; }
-  // ---- per-step tables
-  for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
-    HinvTriangle& H = out.tri[tri];
-    int ntch = 0;
-    for (int v = 0; v < nn; ++v) {
-      HinvNode& Nd = H.h_nodes[v];
-      Nd.tch_begin = ntch;
-      ntch += (Nd.src_n + HINV_TCH - 1) / HINV_TCH;
-      Nd.tch_end = ntch;
-    }
-    HinvApply& A = H.A64;
-    A.lower = tri == 0 ? 1 : 0;
-    A.prec = HINV_F64;
-    A.nleaf = nl;
-    A.nnode = nn;
-    A.ntch = ntch;
-    A.nrch = 0;  // the chunk tables follow once the ranks are on the host
-    if (s == HM_OK) s = upload((HinvNode**)&A.nodes, H.h_nodes);
-    A.leaf_pool = leafpool[tri];
-    A.p_pool = ppool[tri];
-    A.q_pool = qpool[tri];
-    A.rank = d_rank + tri * nn;
-    if (s == HM_OK) s = alloc((void**)&A.tpart, sizeof(double) * HINV_KCAP * std::max(ntch, 1));
-    if (s == HM_OK) s = alloc((void**)&A.tvec, sizeof(double) * HINV_KCAP * std::max(nn, 1));
-    if (s == HM_OK) s = alloc((void**)&A.tcount, sizeof(unsigned) * std::max(nn, 1));
-    if (s == HM_OK && cudaMemsetAsync(A.tcount, 0, sizeof(unsigned) * std::max(nn, 1), st) != cudaSuccess) s = HM_ERR_CUDA;
-    H.A = A;
-    if (s == HM_OK && aprec != HINV_F64) {
-      const size_t es = aprec == HINV_DF ? 8 : (aprec == HINV_F32 ? 4 : 2);
-      void* pl = nullptr;
-      void* pp = nullptr;
-      void* pq = nullptr;
-      if (s == HM_OK) s = alloc(&pl, es * std::max<int64_t>(leaf_elems, 1));
-      if (s == HM_OK) s = alloc(&pp, es * std::max<int64_t>(p_elems[tri], 1));
-      if (s == HM_OK) s = alloc(&pq, es * std::max<int64_t>(q_elems[tri], 1));
-      if (s == HM_OK) {
-        count_launches(3);
-        if (aprec == HINV_DF) {
-          convert_kernel<float2><<<1216, 256, 0, st>>>(leafpool[tri], (float2*)pl, leaf_elems);
-          convert_kernel<float2><<<1216, 256, 0, st>>>(ppool[tri], (float2*)pp, p_elems[tri]);
-          convert_kernel<float2><<<1216, 256, 0, st>>>(qpool[tri], (float2*)pq, q_elems[tri]);
-        } else if (aprec == HINV_F32) {
-          convert_kernel<float><<<1216, 256, 0, st>>>(leafpool[tri], (float*)pl, leaf_elems);
-          convert_kernel<float><<<1216, 256, 0, st>>>(ppool[tri], (float*)pp, p_elems[tri]);
-          convert_kernel<float><<<1216, 256, 0, st>>>(qpool[tri], (float*)pq, q_elems[tri]);
-        } else {
-          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(leafpool[tri], (__nv_bfloat16*)pl, leaf_elems);
-          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(ppool[tri], (__nv_bfloat16*)pp, p_elems[tri]);
-          convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(qpool[tri], (__nv_bfloat16*)pq, q_elems[tri]);
+  if (cudaGetLastError() != cudaSuccess) {
+    err = "construction launch failed";
+    return fail(HM_ERR_CUDA);
+  }
+  // ---- per-step tables and storage of every problem
+  for (Ctx& C : G) {
+    HinvData& out = *C.out;
+    const int aprec = out.prec;
+    for (int tri = 0; tri < 2 && s == HM_OK; ++tri) {
+      HinvTriangle& H = out.tri[tri];
+      int ntch = 0;
+      for (int v = 0; v < C.nn; ++v) {
+        HinvNode& Nd = H.h_nodes[v];
+        Nd.tch_begin = ntch;
+        ntch += (Nd.src_n + HINV_TCH - 1) / HINV_TCH;
+        Nd.tch_end = ntch;
+      }
+      HinvApply& A = H.A64;
+      A.lower = tri == 0 ? 1 : 0;
+      A.prec = HINV_F64;
+      A.nleaf = C.nl;
+      A.nnode = C.nn;
+      A.ntch = ntch;
+      A.nrch = 0;  // the chunk tables follow once the ranks are on the host
+      if (s == HM_OK) s = out_upload(out, (HinvNode**)&A.nodes, H.h_nodes, st, err);
+      A.leaf_pool = C.leafpool[tri];
+      A.p_pool = C.ppool[tri];
+      A.q_pool = C.qpool[tri];
+      A.rank = C.d_rank + tri * C.nn;
+      if (s == HM_OK) s = out_alloc(out, (void**)&A.tpart, sizeof(double) * HINV_KCAP * std::max(ntch, 1), err);
+      if (s == HM_OK) s = out_alloc(out, (void**)&A.tvec, sizeof(double) * HINV_KCAP * std::max(C.nn, 1), err);
+      if (s == HM_OK) s = out_alloc(out, (void**)&A.tcount, sizeof(unsigned) * std::max(C.nn, 1), err);
+      if (s == HM_OK && cudaMemsetAsync(A.tcount, 0, sizeof(unsigned) * std::max(C.nn, 1), st) != cudaSuccess)
+        s = HM_ERR_CUDA;
+      H.A = A;
+      if (s == HM_OK && aprec != HINV_F64) {
+        const size_t es = aprec == HINV_DF ? 8 : (aprec == HINV_F32 ? 4 : 2);
+        void* pl = nullptr;
+        void* pp = nullptr;
+        void* pq = nullptr;
+        if (s == HM_OK) s = out_alloc(out, &pl, es * std::max<int64_t>(C.leaf_elems, 1), err);
+        if (s == HM_OK) s = out_alloc(out, &pp, es * std::max<int64_t>(C.p_elems[tri], 1), err);
+        if (s == HM_OK) s = out_alloc(out, &pq, es * std::max<int64_t>(C.q_elems[tri], 1), err);
+        if (s == HM_OK) {
+          count_launches(3);
+          if (aprec == HINV_DF) {
+            convert_kernel<float2><<<1216, 256, 0, st>>>(C.leafpool[tri], (float2*)pl, C.leaf_elems);
+            convert_kernel<float2><<<1216, 256, 0, st>>>(C.ppool[tri], (float2*)pp, C.p_elems[tri]);
+            convert_kernel<float2><<<1216, 256, 0, st>>>(C.qpool[tri], (float2*)pq, C.q_elems[tri]);
+          } else if (aprec == HINV_F32) {
+            convert_kernel<float><<<1216, 256, 0, st>>>(C.leafpool[tri], (float*)pl, C.leaf_elems);
+            convert_kernel<float><<<1216, 256, 0, st>>>(C.ppool[tri], (float*)pp, C.p_elems[tri]);
+            convert_kernel<float><<<1216, 256, 0, st>>>(C.qpool[tri], (float*)pq, C.q_elems[tri]);
+          } else {
+            convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(C.leafpool[tri], (__nv_bfloat16*)pl, C.leaf_elems);
+            convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(C.ppool[tri], (__nv_bfloat16*)pp, C.p_elems[tri]);
+            convert_kernel<__nv_bfloat16><<<1216, 256, 0, st>>>(C.qpool[tri], (__nv_bfloat16*)pq, C.q_elems[tri]);
+          }
+          H.A.prec = aprec;
+          H.A.leaf_pool = pl;
+          H.A.p_pool = pp;
+          H.A.q_pool = pq;
+          // the FP64 pools of the construction are temporaries: gone after this group
+          H.A64.leaf_pool = H.A64.p_pool = H.A64.q_pool = nullptr;
         }
-        H.A.prec = aprec;
-        H.A.leaf_pool = pl;
-        H.A.p_pool = pp;
-        H.A.q_pool = pq;
       }
     }
-  }
-  if (s == HM_OK) s = alloc((void**)&out.d_y, sizeof(double) * std::max(N, 1));
-  // ranks to the host (synchronises: the construction buffers are then freed)
-  std::vector<int> hr(2 * std::max(nn, 1), 0);
-  if (s == HM_OK && cudaMemcpyAsync(hr.data(), d_rank, sizeof(int) * hr.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    s = HM_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) s = HM_ERR_CUDA;
-  free_tmp();
-  // the FP64 pools served the construction; a converted storage replaces them
-  if (s == HM_OK && aprec != HINV_F64) {
-    for (int tri = 0; tri < 2; ++tri) {
-      HinvApply& A64 = out.tri[tri].A64;
-      for (const void* q : {A64.leaf_pool, A64.p_pool, A64.q_pool}) {
-        auto it = std::find(out.allocs.begin(), out.allocs.end(), q);
-        if (it == out.allocs.end()) continue;
-        size_t bytes = 0;
-        if (q == A64.leaf_pool) bytes = sizeof(double) * std::max<int64_t>(leaf_elems, 1);
-        else if (q == A64.p_pool) bytes = sizeof(double) * std::max<int64_t>(p_elems[tri], 1);
-        else bytes = sizeof(double) * std::max<int64_t>(q_elems[tri], 1);
-        cudaFree(*it);
-        out.allocs.erase(it);
-        out.bytes -= (int64_t)bytes;
-      }
-      A64.leaf_pool = A64.p_pool = A64.q_pool = nullptr;
-    }
-  }
-  if (s != HM_OK) {
-    if (err.empty()) err = "hierarchical inverse construction failed";
-    return s;
-  }
-  const size_t es = (aprec == HINV_F64 || aprec == HINV_DF) ? 8 : (aprec == HINV_F32 ? 4 : 2);
-  int64_t sb = 0;
-  for (int tri = 0; tri < 2; ++tri) {
-    HinvTriangle& H = out.tri[tri];
-    H.h_rank.assign(hr.begin() + tri * nn, hr.begin() + tri * nn + nn);
-    // row chunks of the per-step products and their column runs: the leaf's
-    // triangle (lower: columns [0, i0 + nr), upper: [i0, m)), then P of every
-    // block above the leaf whose target holds it, at its rank
-    std::vector<HinvRChunk> rch;
-    std::vector<HinvSeg> segs;
-    for (int l = 0; l < nl; ++l) {
-      const HinvLeaf& L = H.h_leaves[l];
-      for (int i0 = 0; i0 < L.m; i0 += HINV_ACH) {
-        const int nr = std::min(HINV_ACH, L.m - i0);
-        HinvRChunk C{L.r0 + i0, nr, (int)segs.size(), 0};
-        HinvSeg t{};
-        t.kind = 0;
-        t.ld = L.ld;
-        if (tri == 0) {
-          t.off = L.off + i0;
-          t.voff = L.r0;
-          t.n = i0 + nr;
-          t.a_hi = std::min(t.n, i0 + 32);
-          t.b_lo = 0;
-        } else {
-          t.off = L.off + (int64_t)i0 * L.ld + i0;
-          t.voff = L.r0 + i0;
-          t.n = L.m - i0;
-          t.a_hi = t.n;
-          t.b_lo = 32;
-        }
-        segs.push_back(t);
-        for (int q : anc_t[tri][l]) {
-          const HinvNode& Nd = H.h_nodes[q];
-          const int k = H.h_rank[q];
-          if (k <= 0) continue;
-          HinvSeg g{};
-          g.kind = 1;
-          g.off = Nd.poff + (L.r0 + i0 - Nd.tgt0);
-          g.voff = (int64_t)q * HINV_KCAP;
-          g.ld = Nd.pld;
-          g.n = k;
-          g.a_hi = k;
-          g.b_lo = 0;
-          segs.push_back(g);
-        }
-        C.seg_end = (int)segs.size();
-        rch.push_back(C);
-      }
-    }
-    // the chunks of one launch are all resident at once; heaviest first, so
-    // that the CTAs handed to each SM mix heavy and light chunks
-    auto rcost = [&](const HinvRChunk& C) {
-      int64_t c = 0;
-      for (int k = C.seg_begin; k < C.seg_end; ++k) c += segs[k].n;
-      return c * (C.nr > 32 ? 2 : 1);
-    };
-    std::stable_sort(rch.begin(), rch.end(),
-                     [&](const HinvRChunk& a, const HinvRChunk& b) { return rcost(a) > rcost(b); });
-    std::vector<int4> tch;
-    for (int v = 0; v < nn; ++v) {
-      const HinvNode& Nd = H.h_nodes[v];
-      for (int j0 = 0, q = Nd.tch_begin; j0 < Nd.src_n; j0 += HINV_TCH, ++q) tch.push_back(make_int4(v, j0, q, 0));
-    }
-    auto tcost = [&](const int4& c) {
-      const HinvNode& Nd = H.h_nodes[c.x];
-      return (int64_t)H.h_rank[c.x] * std::min(HINV_TCH, Nd.src_n - c.y);
-    };
-    std::stable_sort(tch.begin(), tch.end(), [&](const int4& a, const int4& b) { return tcost(a) > tcost(b); });
-    HinvRChunk* d_rch = nullptr;
-    HinvSeg* d_segs = nullptr;
-    int4* d_tch = nullptr;
-    if (s == HM_OK) s = upload(&d_rch, rch);
-    if (s == HM_OK) s = upload(&d_segs, segs);
-    if (s == HM_OK) s = upload(&d_tch, tch);
+    if (s == HM_OK) s = out_alloc(out, (void**)&out.d_y, sizeof(double) * std::max(C.N, 1), err);
+    // ranks to the host (the group synchronises once below)
+    C.h_rank.assign(2 * std::max(C.nn, 1), 0);
+    if (s == HM_OK && cudaMemcpyAsync(C.h_rank.data(), C.d_rank, sizeof(int) * C.h_rank.size(),
+                                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      s = HM_ERR_CUDA;
     if (s != HM_OK) break;
-    for (HinvApply* A : {&H.A, &H.A64}) {
-      A->nrch = (int)rch.size();
-      A->rch = d_rch;
-      A->segs = d_segs;
-      A->tch = d_tch;
-    }
-    for (const HinvLeaf& L : H.h_leaves) sb += (int64_t)L.m * (L.m + 1) / 2;
-    for (int v = 0; v < nn; ++v) {
-      const HinvNode& Nd = H.h_nodes[v];
-      sb += (int64_t)(Nd.tgt_n + Nd.src_n) * H.h_rank[v];
-      out.max_rank = std::max(out.max_rank, H.h_rank[v]);
-      out.capped += H.h_rank[v] >= HINV_KCAP ? 1 : 0;
-    }
   }
-  if (s != HM_OK) {
-    if (err.empty()) err = "row-chunk table upload failed";
-    return s;
+  if (cudaStreamSynchronize(st) != cudaSuccess && s == HM_OK) s = HM_ERR_CUDA;
+  free_tmp();
+  if (s != HM_OK) return fail(s);
+  // ---- per problem: row chunks of the per-step products and their column runs
+  for (Ctx& C : G) {
+    HinvData& out = *C.out;
+    const int aprec = out.prec;
+    const size_t es = (aprec == HINV_F64 || aprec == HINV_DF) ? 8 : (aprec == HINV_F32 ? 4 : 2);
+    int64_t sb = 0;
+    for (int tri = 0; tri < 2; ++tri) {
+      HinvTriangle& H = out.tri[tri];
+      H.h_rank.assign(C.h_rank.begin() + tri * C.nn, C.h_rank.begin() + tri * C.nn + C.nn);
+      // the leaf's triangle (lower: columns [0, i0 + nr), upper: [i0, m)),
+      // then P of every block above the leaf whose target holds it, at its rank
+      std::vector<HinvRChunk> rch;
+      std::vector<HinvSeg> segs;
+      for (int l = 0; l < C.nl; ++l) {
+        const HinvLeaf& L = H.h_leaves[l];
+        for (int i0 = 0; i0 < L.m; i0 += HINV_ACH) {
+          const int nr = std::min(HINV_ACH, L.m - i0);
+          HinvRChunk R{L.r0 + i0, nr, (int)segs.size(), 0};
+          HinvSeg t{};
+          t.kind = 0;
+          t.ld = L.ld;
+          if (tri == 0) {
+            t.off = L.off + i0;
+            t.voff = L.r0;
+            t.n = i0 + nr;
+            t.a_hi = std::min(t.n, i0 + 32);
+            t.b_lo = 0;
+          } else {
+            t.off = L.off + (int64_t)i0 * L.ld + i0;
+            t.voff = L.r0 + i0;
+            t.n = L.m - i0;
+            t.a_hi = t.n;
+            t.b_lo = 32;
+          }
+          segs.push_back(t);
+          for (int q : C.anc_t[tri][l]) {
+            const HinvNode& Nd = H.h_nodes[q];
+            const int k = H.h_rank[q];
+            if (k <= 0) continue;
+            HinvSeg g{};
+            g.kind = 1;
+            g.off = Nd.poff + (L.r0 + i0 - Nd.tgt0);
+            g.voff = (int64_t)q * HINV_KCAP;
+            g.ld = Nd.pld;
+            g.n = k;
+            g.a_hi = k;
+            g.b_lo = 0;
+            segs.push_back(g);
+          }
+          R.seg_end = (int)segs.size();
+          rch.push_back(R);
+        }
+      }
+      // the chunks of one launch are all resident at once; heaviest first, so
+      // that the CTAs handed to each SM mix heavy and light chunks
+      auto rcost = [&](const HinvRChunk& R) {
+        int64_t c = 0;
+        for (int k = R.seg_begin; k < R.seg_end; ++k) c += segs[k].n;
+        return c * (R.nr > 32 ? 2 : 1);
+      };
+      std::stable_sort(rch.begin(), rch.end(),
+                       [&](const HinvRChunk& a, const HinvRChunk& b) { return rcost(a) > rcost(b); });
+      std::vector<int4> tch;
+      for (int v = 0; v < C.nn; ++v) {
+        const HinvNode& Nd = H.h_nodes[v];
+        for (int j0 = 0, q = Nd.tch_begin; j0 < Nd.src_n; j0 += HINV_TCH, ++q) tch.push_back(make_int4(v, j0, q, 0));
+      }
+      auto tcost = [&](const int4& c) {
+        const HinvNode& Nd = H.h_nodes[c.x];
+        return (int64_t)H.h_rank[c.x] * std::min(HINV_TCH, Nd.src_n - c.y);
+      };
+      std::stable_sort(tch.begin(), tch.end(), [&](const int4& a, const int4& b) { return tcost(a) > tcost(b); });
+      HinvRChunk* d_rch_t = nullptr;
+      HinvSeg* d_segs = nullptr;
+      int4* d_tch = nullptr;
+      if (s == HM_OK) s = out_upload(out, &d_rch_t, rch, st, err);
+      if (s == HM_OK) s = out_upload(out, &d_segs, segs, st, err);
+      if (s == HM_OK) s = out_upload(out, &d_tch, tch, st, err);
+      if (s != HM_OK) return fail(s);
+      for (HinvApply* A : {&H.A, &H.A64}) {
+        A->nrch = (int)rch.size();
+        A->rch = d_rch_t;
+        A->segs = d_segs;
+        A->tch = d_tch;
+      }
+      for (const HinvLeaf& L : H.h_leaves) sb += (int64_t)L.m * (L.m + 1) / 2;
+      for (int v = 0; v < C.nn; ++v) {
+        const HinvNode& Nd = H.h_nodes[v];
+        sb += (int64_t)(Nd.tgt_n + Nd.src_n) * H.h_rank[v];
+        out.max_rank = std::max(out.max_rank, H.h_rank[v]);
+        out.capped += H.h_rank[v] >= HINV_KCAP ? 1 : 0;
+      }
+    }
+    out.step_bytes = sb * (int64_t)es;
   }
-  out.step_bytes = sb * (int64_t)es;
-  out.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  for (Ctx& C : G) C.out->build_ms = ms;
   return HM_OK;
+}
+
+}  // namespace
+
+int hinv_build_batch(const std::vector<HinvBuildJob>& jobs, int* d_err, cudaStream_t st, std::string& err) {
+  // groups of at most HM_HINV_GROUP_ROWS stacked rows (default 2^19): the
+  // construction's temporaries grow with the rows of a group (about 10 KB per row)
+  int64_t limit = int64_t(1) << 19;
+  if (const char* g = std::getenv("HM_HINV_GROUP_ROWS")) limit = std::max<int64_t>(1, std::atoll(g));
+  const auto t0 = std::chrono::steady_clock::now();
+  size_t i = 0;
+  while (i < jobs.size()) {
+    std::vector<Ctx> G;
+    int64_t rows = 0;
+    while (i < jobs.size() && (G.empty() || rows + jobs[i].P->N <= limit)) {
+      const HinvBuildJob& J = jobs[i++];
+      G.emplace_back();
+      Ctx& C = G.back();
+      C.P = J.P;
+      C.dd = J.dd;
+      C.F = J.F;
+      C.d_rank_f = J.d_rank_f;
+      C.out = J.out;
+      C.tol = J.tol;
+      *C.out = HinvData();
+      // FP64 accuracy: pairs of floats in double-float arithmetic (HM_HINV_FP64=1: FP64 storage and arithmetic)
+      const char* f64 = std::getenv("HM_HINV_FP64");
+      C.out->prec = J.prec == HINV_F64 && !(f64 && f64[0] == '1') ? HINV_DF : J.prec;
+      C.out->tol = J.tol;
+      HM_TRY(ctx_prepare(C, err));
+      rows += C.N;
+    }
+    HM_TRY(build_group(G, d_err, st, err));
+  }
+  if (jobs.size() > 1) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (const HinvBuildJob& J : jobs) J.out->build_ms = ms;
+  }
+  return HM_OK;
+}
+
+int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
+               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err) {
+  std::vector<HinvBuildJob> jobs(1);
+  jobs[0] = HinvBuildJob{&P, &dd, &F, d_rank_f, prec, tol, &out};
+  return hinv_build_batch(jobs, d_err, st, err);
 }
 
 int hinv_solve(const HinvData& D, const double* b, double* z, cudaStream_t st) {

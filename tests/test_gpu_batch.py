@@ -36,6 +36,32 @@ def test_factor_batch_equals_single():
         assert H.stats(Fi)["lu_max_rank_seen"] == H.stats(F1)["lu_max_rank_seen"]
 
 
+def test_inverses_do_not_depend_on_the_construction_grouping(monkeypatch):
+    """A batch's hierarchical inverses are built with the construction steps
+    of several problems merged into shared launches (groups of stacked rows);
+    the solves they give are the same bit for bit whether every problem is
+    alone in its group, a few share one, or all share one."""
+    batch = _small_batch(8)
+    dt = W.LEVY_BATCH_DT
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    rng = np.random.default_rng(5)
+    bs = [dev(rng.standard_normal(H.n)) for H in Hs]
+    sols = []
+    for rows in (None, "1", "2500"):
+        if rows is None:
+            monkeypatch.delenv("HM_HINV_GROUP_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("HM_HINV_GROUP_ROWS", rows)
+        Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+        assert all(H.stats(F)["solve_mode"] == hmat.HM_SOLVE_HINV for H, F in zip(Hs, Fs))
+        sols.append([host(F.solve(b)) for F, b in zip(Fs, bs)])
+        for F in Fs:
+            F.free()
+    for other in sols[1:]:
+        for x0, x1 in zip(sols[0], other):
+            assert np.array_equal(x0, x1)
+
+
 def test_cn_solve_batch_equals_single_and_oracle():
     batch = _small_batch()
     dt, steps = W.LEVY_BATCH_DT, 20

@@ -255,3 +255,25 @@ def test_injected_allocation_failure_is_reported_and_never_streamed(monkeypatch)
     assert e.value.status == -2, str(e.value)
     monkeypatch.setenv("HM_ARENA_LIMIT_BYTES", str(10 ** 12))   # room enough: plans
     assert hmat.plan_factor(prob, opts, -0.5 * dt)["fact_ops"] > 0
+
+
+def test_autotune_search_space_per_precision_and_dimension():
+    """The autotuner's candidates (no GPU): a 1D box problem gets the inverses
+    and the substitution solve at every block below N; a mixed precision keeps
+    only the inverses (its refinement needs them); a 2D problem gets only the
+    substitution solve, and a 2D problem in a mixed precision has no candidate
+    at all, which is an error rather than an empty choice."""
+    from paper_1812_08324_gb300 import autotune
+    p1, o1 = W.levy_batch(1)[0]
+    n1 = p1["n"][0]
+    c64 = autotune.configurations(p1, o1, leafs=(64,), solve_blocks=(256, 1 << 30))
+    assert {(c["solve"], c.get("solve_block", 0)) for c in c64} == {("hinv", 0), ("subst", 256)}
+    mixed = autotune.configurations(p1, dict(o1, precision="mixed_fp32"), leafs=(32, 64))
+    assert mixed and all(c["solve"] == "hinv" for c in mixed)
+    assert {c["leaf"] for c in mixed} == {32, 64}
+    assert all(c["leaf"] <= n1 for c in autotune.configurations(p1, o1, leafs=(64, 1 << 20)))
+    p2 = W.frac_lap_2d(64, 0.5)
+    c2 = autotune.configurations(p2, W.default_opts(leaf=64), leafs=(64,), solve_blocks=(1024,))
+    assert c2 == [{"leaf": 64, "solve": "subst", "solve_block": 1024}]
+    with pytest.raises(ValueError):
+        autotune.configurations(p2, W.default_opts(leaf=64, precision="mixed_fp32"), leafs=(64,))
