@@ -543,6 +543,9 @@ int hm_factor_batch(const hm_matrix* const* Hs, const double* thetas, int count,
 namespace hm {
 namespace {
 
+#ifndef HM_SLICE_OPS
+#define HM_SLICE_OPS (1 << 20)  // at most this many ops (whole planner chunks, at least one) per executor launch
+#endif
 #ifndef HM_CHUNK_OPS
 #define HM_CHUNK_OPS 49152  // ops per planner chunk (build-time tuning parameter; 1D N = 65536: 131072 -> 49152 gave 231 -> 213 ms, the device waits less for each slice's merge and upload)
 #endif
@@ -722,6 +725,8 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
   int finished = 0;
   const char* co = std::getenv("HM_CHUNK_OPS");  // slice size override (tests)
   const int64_t chunk = co && std::atoll(co) > 0 ? std::atoll(co) : HM_CHUNK_OPS;
+  const char* so = std::getenv("HM_SLICE_OPS");
+  const int64_t slice_cap = so && std::atoll(so) > 0 ? std::atoll(so) : HM_SLICE_OPS;
   for (int i = 0; i < count; ++i) {
     jobs[i].hb.chunk_ops = chunk;
     jobs[i].hb.sink = [&, i](HluChunk&& c) {
@@ -773,12 +778,23 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
           if (!q.empty()) return true;
         return false;
       });
-      for (int i = 0; i < count; ++i)
-        for (; !ready[i].empty(); ready[i].pop_front()) {
+      // a prefix of every problem's queue, round robin over the problems,
+      // up to slice_cap ops: a backlog goes out as several launches, so the
+      // device starts on its first part while the host merges the next
+      int64_t taken = 0;
+      for (bool more = true; more && taken < slice_cap;) {
+        more = false;
+        for (int i = 0; i < count && taken < slice_cap; ++i) {
+          if (ready[i].empty()) continue;
+          taken += ready[i].front().graph.size();
           got[i].push_back(std::move(ready[i].front()));
-          any = true;
+          ready[i].pop_front();
+          any = more = true;
         }
-      done = finished == count;
+      }
+      bool left = false;
+      for (const auto& q : ready) left = left || !q.empty();
+      done = finished == count && !left;
     }
     if (!any) {
       if (done) break;
@@ -788,10 +804,14 @@ int factor_streamed(std::vector<FactorJob>& jobs, cudaStream_t st, int* d_err, c
     std::vector<std::vector<Wave>> pw(count);
     std::vector<OpGraph> pg(count);
     std::vector<SchedPart> parts;
-    for (int i = 0; i < count && s == HM_OK; ++i) {
-      if (got[i].empty()) continue;
-      s = merge_chunks(got[i], pw[i], pg[i]);
-      parts.push_back(SchedPart{&pw[i], &pg[i], nullptr});
+    std::vector<int> idx;  // the problems in this slice, merged in parallel
+    for (int i = 0; i < count; ++i)
+      if (!got[i].empty()) idx.push_back(i);
+    std::vector<int> ms(idx.size(), HM_OK);
+    parallel_for((int)idx.size(), [&](int k) { ms[k] = merge_chunks(got[idx[k]], pw[idx[k]], pg[idx[k]]); });
+    for (size_t k = 0; k < idx.size(); ++k) {
+      if (ms[k] != HM_OK) s = ms[k];
+      parts.push_back(SchedPart{&pw[idx[k]], &pg[idx[k]], nullptr});
     }
     if (s != HM_OK) break;
     const auto t_m1 = std::chrono::steady_clock::now();

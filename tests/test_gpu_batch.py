@@ -62,6 +62,31 @@ def test_inverses_do_not_depend_on_the_construction_grouping(monkeypatch):
             assert np.array_equal(x0, x1)
 
 
+def test_factor_batch_in_many_small_launches_is_identical(monkeypatch):
+    """The streamed H-LU with small planner chunks and a small cap on the ops
+    of one launch (each problem's chunks spread over many launches, taken
+    round robin over the problems) gives the same solves bit for bit as the
+    default slicing."""
+    batch = _small_batch(6)
+    dt = W.LEVY_BATCH_DT
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    rng = np.random.default_rng(9)
+    bs = [dev(rng.standard_normal(H.n)) for H in Hs]
+    sols = []
+    for chunk, cap in ((None, None), ("700", "2000")):
+        for k, v in (("HM_CHUNK_OPS", chunk), ("HM_SLICE_OPS", cap)):
+            if v is None:
+                monkeypatch.delenv(k, raising=False)
+            else:
+                monkeypatch.setenv(k, v)
+        Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+        sols.append([host(F.solve(b)) for F, b in zip(Fs, bs)])
+        for F in Fs:
+            F.free()
+    for x0, x1 in zip(*sols):
+        assert np.array_equal(x0, x1)
+
+
 def test_cn_solve_batch_equals_single_and_oracle():
     batch = _small_batch()
     dt, steps = W.LEVY_BATCH_DT, 20
