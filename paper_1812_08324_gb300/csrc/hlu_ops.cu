@@ -560,17 +560,18 @@ __device__ int pivoted_cholesky(double* G, int K, int* perm, double rel_thresh, 
 
 // Tail of the truncation when Q and Z do not fit beside the K x K matrices:
 // Q is formed in the output TA (global memory), then staged through GA.
+template <int KM>
 __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K, int kf, int rA, int rB, int r,
                                   bool capped) {
-  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
-  double* tau = cn + TRUNC_MAXK;
-  double* red_v = tau + TRUNC_MAXK;
+  double* cn = sm + 3 * KM * KM;
+  double* tau = cn + KM;
+  double* red_v = tau + KM;
   int* permA = reinterpret_cast<int*>(red_v + 32);
-  int* permB = permA + TRUNC_MAXK;
-  int* permC = permB + TRUNC_MAXK;
-  int* posA = permC + TRUNC_MAXK;
-  int* posB = posA + TRUNC_MAXK;
-  int* red_i = posB + TRUNC_MAXK;
+  int* permB = permA + KM;
+  int* permC = permB + KM;
+  int* posA = permC + KM;
+  int* posB = posA + KM;
+  int* red_i = posB + KM;
   int* kexp = red_i + 8;
   const int t = threadIdx.x;
   double* GA = sm;
@@ -597,13 +598,19 @@ __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K
     }
     __syncthreads();
   }
+  // reciprocal diagonals of R_A and R_B (cn and tau are free now): the same
+  // arithmetic as the shared-memory tail, so the factors do not depend on
+  // which tail (which executor mode) ran
+  for (int i = t; i < rA; i += blockDim.x) cn[i] = 1.0 / GA[i * K + i];
+  for (int i = t; i < rB; i += blockDim.x) tau[i] = 1.0 / GB[i * K + i];
+  __syncthreads();
   // T_A (pivoted rows) = R11_A^{-1} Q; R11_A is the leading rA x rA block of GA (upper)
   // solve in place column by column (back substitution), then scatter rows by permA.
   for (int c = t; c < r; c += blockDim.x) {
     for (int i = rA - 1; i >= 0; --i) {
       double v = Q[i * kf + c];
       for (int k = i + 1; k < rA; ++k) v -= GA[i * K + k] * Q[k * kf + c];
-      Q[i * kf + c] = v / GA[i * K + i];
+      Q[i * kf + c] = v * cn[i];
     }
   }
   __syncthreads();
@@ -638,7 +645,7 @@ __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K
     for (int i = rB - 1; i >= 0; --i) {
       double v = GA[i * kf + c];
       for (int k = i + 1; k < rB; ++k) v -= GB[i * K + k] * GA[k * kf + c];
-      GA[i * kf + c] = v / GB[i * K + i];
+      GA[i * kf + c] = v * tau[i];
     }
   }
   __syncthreads();
@@ -656,17 +663,18 @@ __device__ void trunc_tail_global(const TruncOp& op, int* err, double* sm, int K
 // Tail of the truncation with Q and Z in shared memory: Q = the first r
 // columns of C's orthogonal factor, TA = R_A^{-1} Q (half 0) and Z = R_C P_C',
 // TB = R_B^{-1} Z (half 1) side by side; reciprocal diagonals precomputed.
+template <int KM>
 __device__ void trunc_tail_smem(const TruncOp& op, int* err, double* sm, int K, int kf, int rA, int rB, int r,
                                 bool capped) {
-  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
-  double* tau = cn + TRUNC_MAXK;
-  double* red_v = tau + TRUNC_MAXK;
+  double* cn = sm + 3 * KM * KM;
+  double* tau = cn + KM;
+  double* red_v = tau + KM;
   int* permA = reinterpret_cast<int*>(red_v + 32);
-  int* permB = permA + TRUNC_MAXK;
-  int* permC = permB + TRUNC_MAXK;
-  int* posA = permC + TRUNC_MAXK;
-  int* posB = posA + TRUNC_MAXK;
-  int* red_i = posB + TRUNC_MAXK;
+  int* permB = permA + KM;
+  int* permC = permB + KM;
+  int* posA = permC + KM;
+  int* posB = posA + KM;
+  int* red_i = posB + KM;
   int* kexp = red_i + 8;
   const int t = threadIdx.x;
   double* GA = sm;
@@ -731,22 +739,23 @@ __device__ void trunc_tail_smem(const TruncOp& op, int* err, double* sm, int K, 
   __syncthreads();
 }
 
+template <int KM>
 __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
   // scratch after the three K x K matrices
-  double* cn = sm + 3 * TRUNC_MAXK * TRUNC_MAXK;
-  double* tau = cn + TRUNC_MAXK;
-  double* red_v = tau + TRUNC_MAXK;
+  double* cn = sm + 3 * KM * KM;
+  double* tau = cn + KM;
+  double* red_v = tau + KM;
   int* permA = reinterpret_cast<int*>(red_v + 32);
-  int* permB = permA + TRUNC_MAXK;
-  int* permC = permB + TRUNC_MAXK;
-  int* posA = permC + TRUNC_MAXK;
-  int* posB = posA + TRUNC_MAXK;
-  int* red_i = posB + TRUNC_MAXK;
+  int* permB = permA + KM;
+  int* permC = permB + KM;
+  int* posA = permC + KM;
+  int* posB = posA + KM;
+  int* red_i = posB + KM;
   const int K = op.K, kf = op.kf, t = threadIdx.x;
   double* GA = sm;
   double* GB = sm + K * K;
   double* C = sm + 2 * K * K;
-  int* kexp = red_i + 8;  // K ints (the int scratch holds 7 x TRUNC_MAXK)
+  int* kexp = red_i + 8;  // K ints (the int scratch holds 7 x KM)
   for (int e = t; e < K * K; e += blockDim.x) {
     GA[e] = op.GA[e];
     GB[e] = op.GB[e];
@@ -822,7 +831,7 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
     if (p == rmax) { capped = true; break; }
     const int q = red_i[0];
     // swap columns p and q; the thread that owns row p in the swap (thread p,
-    // rA <= TRUNC_MAXK < blockDim.x) first forms the reflector of column q:
+    // rA <= KM < blockDim.x) first forms the reflector of column q:
     // s = sum_{i >= p} C[i][q]^2 is its trailing norm, the maximum red_v[0]
     if (t == p) {
       const double sq = red_v[0];
@@ -875,11 +884,11 @@ __device__ void dev_trunc(const TruncOp& op, int* err, double* sm) {
     __syncthreads();
   }
   __syncthreads();
-  if (3 * K * K + 2 * K * kf <= 3 * TRUNC_MAXK * TRUNC_MAXK) {
-    trunc_tail_smem(op, err, sm, K, kf, rA, rB, r, capped);
+  if (3 * K * K + 2 * K * kf <= 3 * KM * KM) {
+    trunc_tail_smem<KM>(op, err, sm, K, kf, rA, rB, r, capped);
     return;
   }
-  trunc_tail_global(op, err, sm, K, kf, rA, rB, r, capped);
+  trunc_tail_global<KM>(op, err, sm, K, kf, rA, rB, r, capped);
 }
 
 __device__ void dev_copy(const CopyOp& op, int chunk, int nchunks) {
@@ -1135,16 +1144,21 @@ __device__ void dev_vpart(const VPartOp& op, double* smem, int vcap) {
 
 constexpr int EXEC_THREADS = 256;
 static_assert(TRUNC_MAXK < EXEC_THREADS, "the truncation core maps rows of C to threads");
-constexpr size_t EXEC_SMEM = sizeof(double) * (3 * TRUNC_MAXK * TRUNC_MAXK + 2 * TRUNC_MAXK + 32) +
-                             sizeof(int) * 7 * TRUNC_MAXK;
+static_assert(TRUNC_MAXK_2CTA <= TRUNC_MAXK, "the two-CTA mode takes a subset of the schedules");
+// shared memory of an H-LU mode: the truncation core's three K x K matrices and scratch
+constexpr size_t factor_smem(int km) { return sizeof(double) * (3 * km * km + 2 * km + 32) + sizeof(int) * 7 * km; }
+__host__ __device__ constexpr int mode_trunc_maxk(int m) { return m == FACTOR_MODE_2CTA ? TRUNC_MAXK_2CTA : TRUNC_MAXK; }
 // shared memory of a solve mode: the larger of a row task's and a partial-product task's needs
 constexpr size_t rows_smem_bytes(int m) {
   return sizeof(double) * (32 + 256 + 512 + mode_prefetch(m) + mode_dyn(m)) + sizeof(RowSrc) * ROWS_MAX_SRC;
 }
 constexpr size_t vpart_smem_bytes(int m) { return sizeof(double) * (mode_vpart(m) + 256); }
 constexpr size_t mode_smem(int m) {
-  return m == 0 ? EXEC_SMEM : (rows_smem_bytes(m) > vpart_smem_bytes(m) ? rows_smem_bytes(m) : vpart_smem_bytes(m));
+  return mode_factor(m) ? factor_smem(mode_trunc_maxk(m))
+                        : (rows_smem_bytes(m) > vpart_smem_bytes(m) ? rows_smem_bytes(m) : vpart_smem_bytes(m));
 }
+static_assert(mode_ctas(FACTOR_MODE_2CTA) * (mode_smem(FACTOR_MODE_2CTA) + 1024) <= 228 * 1024,
+              "two-CTA H-LU mode shared memory");
 static_assert(mode_ctas(1) * (mode_smem(1) + 1024) <= 228 * 1024, "latency solve mode shared memory");
 static_assert(mode_ctas(2) * (mode_smem(2) + 1024) <= 228 * 1024, "throughput solve mode shared memory");
 constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;  // 4 s for one dependency wait
@@ -1225,7 +1239,7 @@ __device__ __forceinline__ bool wait_deps(const ExecArgs& a, int id) {
 // waiting on a producer never holds up a task that is ready elsewhere.
 template <int MODE>
 __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(ExecArgs a) {
-  constexpr bool SOLVE = MODE != 0;
+  constexpr bool SOLVE = !mode_factor(MODE);
   extern __shared__ double smem[];
   __shared__ int next;
   // descriptor of the current op (factorisation), copied before the wait
@@ -1282,7 +1296,7 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
           if (opdesc.lu.pad & LU_DF) dev_lu_base_dd(opdesc.lu, a.err, smem);
           else dev_lu_base(opdesc.lu, a.err, smem);
           break;
-        case TK_TRUNC: dev_trunc(opdesc.trunc, a.err, smem); break;
+        case TK_TRUNC: dev_trunc<mode_trunc_maxk(MODE)>(opdesc.trunc, a.err, smem); break;
         case TK_COPY: dev_copy(opdesc.copy, T.sub, T.nsub); break;
         case TK_REDUCE: dev_reduce(opdesc.reduce, T.sub, T.nsub); break;
         default: break;
@@ -1507,7 +1521,16 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   if ((st = up(vp, &S.vpart)) != HM_OK) return st;
   if ((st = up(msrc, &S.srcs)) != HM_OK) return st;
   if ((st = up(tasks, &S.tasks)) != HM_OK) return st;
-  S.mode = (g.empty() && l.empty() && tr.empty()) ? (mode == SOLVE_MODE_THROUGHPUT ? 2 : 1) : 0;
+  if (g.empty() && l.empty() && tr.empty()) {
+    S.mode = mode == SOLVE_MODE_THROUGHPUT ? 2 : 1;
+  } else {
+    // H-LU: two CTAs per SM when every truncation core fits the smaller
+    // shared-memory layout (HM_EXEC_2CTA=0: always one)
+    int kmax = 0;
+    for (const TruncOp& o : tr) kmax = std::max(kmax, o.K);
+    const char* two = std::getenv("HM_EXEC_2CTA");
+    S.mode = kmax <= TRUNC_MAXK_2CTA && !(two && two[0] == '0') ? FACTOR_MODE_2CTA : 0;
+  }
   if (std::getenv("HM_PHASE_TRACE")) S.host_tasks.swap(tasks);  // kept for tracing only
   if ((st = up(wb, &S.wave_begin)) != HM_OK) return st;
   // Test-only fault injection (failure detection of the bounded waits):
@@ -1534,9 +1557,14 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
 }
 
 namespace {
-int g_exec_grid[EXEC_MODES] = {0, 0, 0};
+int g_exec_grid[EXEC_MODES] = {0, 0, 0, 0};
 void* exec_fn(int m) {
-  return m == 0 ? (void*)exec_kernel<0> : (m == 1 ? (void*)exec_kernel<1> : (void*)exec_kernel<2>);
+  switch (m) {
+    case 0: return (void*)exec_kernel<0>;
+    case 1: return (void*)exec_kernel<1>;
+    case 2: return (void*)exec_kernel<2>;
+    default: return (void*)exec_kernel<FACTOR_MODE_2CTA>;
+  }
 }
 }
 

@@ -101,13 +101,18 @@ struct RowsOp {
 };
 
 // Executor modes: 0 runs H-LU schedules (one CTA per SM, 225 KB shared
-// memory); the solve modes trade shared-memory staging for CTAs per SM:
-// mode 1 (latency: one solve) two CTAs per SM, mode 2 (throughput: batched
-// solves) four.  Staging of a row task (doubles): copied matrix rows, gathered
-// inputs; and the copied V rows of a partial-product task.
-constexpr int EXEC_MODES = 3;
-constexpr int SOLVE_MODE_LATENCY = 1, SOLVE_MODE_THROUGHPUT = 2;
-__host__ __device__ constexpr int mode_ctas(int m) { return m == 0 ? 1 : (m == 1 ? 2 : 4); }
+// memory, truncation cores up to TRUNC_MAXK); 3 runs H-LU schedules whose
+// truncation cores stay within TRUNC_MAXK_2CTA with two CTAs per SM (101 KB
+// each: twice the warps to hide the latency of the small tasks); the solve
+// modes trade shared-memory staging for CTAs per SM: mode 1 (latency: one
+// solve) two CTAs per SM, mode 2 (throughput: batched solves) four.  Staging
+// of a row task (doubles): copied matrix rows, gathered inputs; and the
+// copied V rows of a partial-product task.
+constexpr int EXEC_MODES = 4;
+constexpr int SOLVE_MODE_LATENCY = 1, SOLVE_MODE_THROUGHPUT = 2, FACTOR_MODE_2CTA = 3;
+constexpr int TRUNC_MAXK_2CTA = 64;
+__host__ __device__ constexpr int mode_ctas(int m) { return m == 0 ? 1 : (m == 2 ? 4 : 2); }
+__host__ __device__ constexpr bool mode_factor(int m) { return m == 0 || m == FACTOR_MODE_2CTA; }
 __host__ __device__ constexpr int mode_prefetch(int m) { return m == 1 ? 6144 : 3072; }
 __host__ __device__ constexpr int mode_dyn(int m) { return m == 1 ? 5120 : 2560; }
 __host__ __device__ constexpr int mode_vpart(int m) { return m == 1 ? 8192 : 4096; }
@@ -209,7 +214,7 @@ struct DevSchedule {
   int2* deps = nullptr;      // dependency edges: (producer op, its task count)
   int* counters = nullptr;   // per op: finished tasks
   std::vector<Task> host_tasks;  // the task list in hand-out order (for tracing)
-  int mode = 0;                  // executor mode (0: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
+  int mode = 0;                  // executor mode (0 / FACTOR_MODE_2CTA: H-LU; SOLVE_MODE_LATENCY / _THROUGHPUT)
   unsigned long long wait_ns = 4000000000ull;  // limit of one dependency wait (ns; set at upload)
 };
 
