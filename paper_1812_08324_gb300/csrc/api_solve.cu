@@ -9,6 +9,8 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 
@@ -708,6 +710,52 @@ bool check_streamed_failure(const Plan& P, const std::vector<DenseDesc>& dd, con
       return false;
     }
   return true;
+}
+
+// HM_PLAN_HIST (hm_plan_factor): the executor's tasks of an H-LU schedule by
+// op kind (32 x 32 GEMM tiles), and the GEMMs by output and inner size
+// rounded up to powers of two, on stderr
+void plan_histogram(const std::vector<Wave>& waves) {
+  auto p2 = [](int v) { int b = 1; while (b < v) b <<= 1; return b; };
+  std::map<std::tuple<int, int, int>, std::pair<int64_t, int64_t>> gem;  // (m, n, k) -> ops, tasks
+  int64_t ops[5] = {0, 0, 0, 0, 0}, tasks[5] = {0, 0, 0, 0, 0};
+  double fma = 0.0;
+  for (const Wave& W : waves) {
+    for (const GemmOp& o : W.gemm) {
+      const int t = gemm_tiles(o.m, o.n);
+      auto& e = gem[std::make_tuple(p2(o.m), p2(o.n), p2(o.k))];
+      e.first += 1;
+      e.second += t;
+      ops[0] += 1;
+      tasks[0] += t;
+      fma += (double)o.m * o.n * o.k;
+    }
+    ops[1] += (int64_t)W.lu.size();
+    tasks[1] += (int64_t)W.lu.size();
+    ops[2] += (int64_t)W.trunc.size();
+    tasks[2] += (int64_t)W.trunc.size();
+    for (const CopyOp& o : W.copy) {
+      ops[3] += 1;
+      tasks[3] += std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)o.m * o.n / 2048));
+    }
+    for (const ReduceOp& o : W.reduce) {
+      ops[4] += 1;
+      tasks[4] += std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)o.m * o.n * std::max(o.nparts, 1) / 2048));
+    }
+  }
+  const char* names[5] = {"gemm", "lu", "trunc", "copy", "reduce"};
+  for (int k = 0; k < 5; ++k)
+    fprintf(stderr, "[plan] %-6s %10lld ops %11lld tasks\n", names[k], (long long)ops[k], (long long)tasks[k]);
+  fprintf(stderr, "[plan] gemm FMAs %.3e (%.0f per task)\n", fma, fma / std::max<int64_t>(tasks[0], 1));
+  std::vector<std::pair<int64_t, std::tuple<int, int, int>>> by;
+  for (auto& kv : gem) by.push_back({kv.second.second, kv.first});
+  std::sort(by.rbegin(), by.rend());
+  for (size_t i = 0; i < by.size() && i < 24; ++i) {
+    const auto& k = by[i].second;
+    const auto& e = gem[k];
+    fprintf(stderr, "[plan] gemm m<=%-5d n<=%-5d k<=%-5d %9lld ops %10lld tasks\n", std::get<0>(k), std::get<1>(k),
+            std::get<2>(k), (long long)e.first, (long long)e.second);
+  }
 }
 
 // H-LU planning streamed into execution: the planners (one host thread per
@@ -1441,6 +1489,7 @@ int hm_plan_factor(const hm_problem* prob, const hm_opts* opts, double theta, hm
     // own group, and the same order of waves
     if (!check_streamed_plan(P, dd, ld, kf, theta, opts->lu_tol, std::max(1, std::atoi(cs)), hb)) return HM_ERR_ARG;
   }
+  if (std::getenv("HM_PLAN_HIST")) plan_histogram(hb.waves);
   std::vector<Wave> sw;
   std::vector<RowSrc> srcs;
   OpGraph sg;

@@ -14,6 +14,12 @@ namespace hm {
 namespace {
 
 constexpr int GK = 16;   // GEMM k chunk
+#ifndef HM_GEMM_BIG_TILES
+#define HM_GEMM_BIG_TILES 16  // 32 x 32 tiles from which a GEMM may take 64 x 64 tiles (0: never; build-time tuning parameter)
+#endif
+#ifndef HM_GEMM_BIG_WAVE
+#define HM_GEMM_BIG_WAVE 4096  // ... when its wave has at least this many 32 x 32 GEMM tiles (build-time tuning parameter)
+#endif
 
 // (sh, sl) += a b for double-float a, b: the product's high part exactly
 // (FMA), the cross terms rounded (the lo lo term, below 2^-48, is dropped),
@@ -31,17 +37,23 @@ __device__ __forceinline__ void df_acc(float& sh, float& sl, float2 a, float2 b)
   sl = __fadd_rn(sl, __fadd_rn(t, e));
 }
 
-// One TM x TN output tile of C = beta C + alpha A B (256 threads, 1024
-// outputs, 2 x 2 per thread).  Narrow outputs (n or m <= 16) take the 64 x 16
-// or 16 x 64 shape so that no thread computes padding.  The next k chunk is
-// loaded into registers while the current one is multiplied.  DF: the
-// products and sums in double-float arithmetic on the FP32 pipes (about 48
-// significant bits: operands to 2^-49, each product and addition to about
-// 2^-48 of its terms), otherwise FP64.
+// One TM x TN output tile of C = beta C + alpha A B (256 threads; 32 x 32,
+// 64 x 16 and 16 x 64 tiles give each thread 2 x 2 outputs, 64 x 64 tiles
+// 4 x 4).  Thread (tx, ty) owns rows ty + TY a and columns tx + TX b, so the
+// shared-memory reads of a warp are broadcasts (A) and consecutive words (B).
+// Narrow outputs (n or m <= 16) take the 64 x 16 or 16 x 64 shape so that no
+// thread computes padding; large ones may take 64 x 64 (fewer, longer tasks).
+// The next k chunk is loaded into registers while the current one is
+// multiplied.  DF: the products and sums in double-float arithmetic on the
+// FP32 pipes (about 48 significant bits: operands to 2^-49, each product and
+// addition to about 2^-48 of its terms), otherwise FP64.  Every output sums
+// its k terms in the same order whatever the tile shape.
 template <int TM, int TN, bool DF>
 __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
-  constexpr int TX = TN / 2;  // threads along n
-  constexpr int NA = TM * GK / 256, NB = GK * TN / 256;  // chunk elements per thread
+  constexpr int RN = TM * TN / 256 == 16 ? 4 : 2;        // outputs per thread along n
+  constexpr int TX = TN / RN, TY = 256 / TX, RM = TM / TY;  // threads along n, m; outputs along m
+  static_assert(RM * RN * 256 == TM * TN, "tile shape");
+  constexpr int NA = TM * GK / 256, NB = GK * TN / 256;     // chunk elements per thread
   using T = typename std::conditional<DF, float2, double>::type;
   static_assert(sizeof(T) == sizeof(double), "same shared-memory layout");
   T (*As)[GK + 1] = reinterpret_cast<T (*)[GK + 1]>(smem);
@@ -78,8 +90,15 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
     }
     if (bad) atomicOr(err, DEVERR_NONFINITE);
   };
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+  constexpr int RO = RM * RN;
+  double acc[RO];
+  float sh[RO], sl[RO];
+#pragma unroll
+  for (int q = 0; q < RO; ++q) {
+    acc[q] = 0.0;
+    sh[q] = 0.f;
+    sl[q] = 0.f;
+  }
   load(0);
   for (int k0 = 0; k0 < op.k; k0 += GK) {
     stash();
@@ -87,38 +106,41 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
     if (k0 + GK < op.k) load(k0 + GK);  // in flight during this chunk's arithmetic
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      const T a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
-      const T b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      T a[RM], b[RN];
+#pragma unroll
+      for (int x = 0; x < RM; ++x) a[x] = As[ty + TY * x][kk];
+#pragma unroll
+      for (int y = 0; y < RN; ++y) b[y] = Bs[kk][tx + TX * y];
       if constexpr (DF) {
-        df_acc(sh[0], sl[0], a0, b0);
-        df_acc(sh[1], sl[1], a0, b1);
-        df_acc(sh[2], sl[2], a1, b0);
-        df_acc(sh[3], sl[3], a1, b1);
+#pragma unroll
+        for (int x = 0; x < RM; ++x)
+#pragma unroll
+          for (int y = 0; y < RN; ++y) df_acc(sh[x * RN + y], sl[x * RN + y], a[x], b[y]);
         if ((kk & 3) == 3) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {  // renormalise every 4 terms: sl stays within an ulp of sh
+          for (int q = 0; q < RO; ++q) {  // renormalise every 4 terms: sl stays within an ulp of sh
             const float s = __fadd_rn(sh[q], sl[q]);
             sl[q] = __fsub_rn(sl[q], __fsub_rn(s, sh[q]));
             sh[q] = s;
           }
         }
       } else {
-        acc[0] += a0 * b0;
-        acc[1] += a0 * b1;
-        acc[2] += a1 * b0;
-        acc[3] += a1 * b1;
+#pragma unroll
+        for (int x = 0; x < RM; ++x)
+#pragma unroll
+          for (int y = 0; y < RN; ++y) acc[x * RN + y] += a[x] * b[y];
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int x = 0; x < RM; ++x)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int gi = i0 + ty * 2 + a, gj = j0 + tx * 2 + b;
+    for (int y = 0; y < RN; ++y) {
+      const int gi = i0 + ty + TY * x, gj = j0 + tx + TX * y;
       if (gi < op.m && gj < op.n) {
         double* c = op.C + gi * op.crs + gj * op.ccs;
-        const double r = DF ? (double)sh[2 * a + b] + (double)sl[2 * a + b] : acc[2 * a + b];
+        const double r = DF ? (double)sh[x * RN + y] + (double)sl[x * RN + y] : acc[x * RN + y];
         double v = op.alpha * r;
         *c = op.beta == 0.0 ? v : op.beta * (*c) + v;
       }
@@ -126,16 +148,18 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
   __syncthreads();
 }
 
-// op.shape: bits 0-1 the tile shape (gemm_shape), bit 2 set = FP64 arithmetic
+// op.shape: bits 0-1 the tile shape (gemm_shape; 3 = 64 x 64), bit 2 set = FP64 arithmetic
 __device__ void dev_gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
   const int sh = op.shape & 3;
   if (op.shape & GEMM_FP64) {
     if (sh == 1) gemm_tile<64, 16, false>(op, local, smem, err);
     else if (sh == 2) gemm_tile<16, 64, false>(op, local, smem, err);
+    else if (sh == 3) gemm_tile<64, 64, false>(op, local, smem, err);
     else gemm_tile<32, 32, false>(op, local, smem, err);
   } else {
     if (sh == 1) gemm_tile<64, 16, true>(op, local, smem, err);
     else if (sh == 2) gemm_tile<16, 64, true>(op, local, smem, err);
+    else if (sh == 3) gemm_tile<64, 64, true>(op, local, smem, err);
     else gemm_tile<32, 32, true>(op, local, smem, err);
   }
 }
@@ -1354,11 +1378,11 @@ void plan_rows_staging(RowsOp& op, RowSrc* src, int mode) {
 }
 
 int gemm_shape(int m, int n) { return n <= 16 && m > 16 ? 1 : (m <= 16 && n > 16 ? 2 : 0); }
-int gemm_tiles(int m, int n) {
-  const int sh = gemm_shape(m, n);
-  const int tm = sh == 1 ? 64 : sh == 2 ? 16 : 32, tn = sh == 1 ? 16 : sh == 2 ? 64 : 32;
+int shape_tiles(int sh, int m, int n) {
+  const int tm = sh == 1 || sh == 3 ? 64 : sh == 2 ? 16 : 32, tn = sh == 2 || sh == 3 ? 64 : sh == 1 ? 16 : 32;
   return ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
 }
+int gemm_tiles(int m, int n) { return shape_tiles(gemm_shape(m, n), m, n); }
 
 int upload_schedule(const std::vector<Wave>& waves, const OpGraph& graph, DevSchedule& S,
                     std::vector<void*>& allocs, const std::vector<RowSrc>* srcs, int mode) {
@@ -1412,15 +1436,24 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   auto chunks = [](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, work / 2048)); };
   const char* g64 = std::getenv("HM_GEMM_FP64");  // FP64 instead of double-float GEMM tiles
   const bool gemm_fp64 = g64 && g64[0] == '1';
+  // GEMMs of at least big_tiles 32 x 32 tiles, in waves of at least big_wave
+  // such tiles, run as 64 x 64 tiles (a quarter of the tasks; the same
+  // arithmetic per output)
+  int big_tiles = HM_GEMM_BIG_TILES;
+  if (const char* gb = std::getenv("HM_GEMM_BIG_TILES")) big_tiles = std::atoi(gb);
+  int64_t big_wave = HM_GEMM_BIG_WAVE;
+  if (const char* gw = std::getenv("HM_GEMM_BIG_WAVE")) big_wave = std::atoll(gw);
   const char* ldf = std::getenv("HM_LU_DF");  // double-float instead of FP64 base LUs
   const bool lu_df = ldf && ldf[0] == '1';
   // the tasks of one op (kind, index k in its wave's list of that kind)
-  auto emit = [&](size_t p, const Wave& W, int kind, size_t k) {
+  auto emit = [&](size_t p, const Wave& W, int kind, size_t k, bool wide) {
     const int o0 = off[p];
     if (kind == TK_GEMM) {
       GemmOp o = W.gemm[k];
-      o.shape = gemm_shape(o.m, o.n) | (gemm_fp64 ? GEMM_FP64 : 0);
-      int nt = gemm_tiles(o.m, o.n), id = W.gemm_id[k] + o0;
+      int sh = gemm_shape(o.m, o.n);
+      if (sh == 0 && wide && big_tiles > 0 && shape_tiles(0, o.m, o.n) >= big_tiles) sh = 3;
+      o.shape = sh | (gemm_fp64 ? GEMM_FP64 : 0);
+      int nt = shape_tiles(sh, o.m, o.n), id = W.gemm_id[k] + o0;
       for (int t = 0; t < nt; ++t) tasks.push_back({TK_GEMM, (int)g.size(), t, nt, id});
       info[id].ntasks = nt;
       g.push_back(o);
@@ -1484,11 +1517,19 @@ int upload_schedules(const std::vector<SchedPart>& parts, DevSchedule& S, std::v
   static const int kinds[] = {TK_LU, TK_TRUNC, TK_REDUCE, TK_COPY, TK_GEMM, TK_ROWS, TK_VPART};
   for (size_t w = 0; w < nw; ++w) {
     wb.push_back((int)tasks.size());
+    // a wave of many GEMM tiles keeps every SM busy whatever the tile size:
+    // its large GEMMs take 64 x 64 tiles (a wave of few tiles keeps 32 x 32
+    // ones, which finish sooner on the dependency chain)
+    int64_t wt = 0;
+    for (size_t p = 0; p < parts.size(); ++p)
+      if (w < parts[p].waves->size())
+        for (const GemmOp& o : (*parts[p].waves)[w].gemm) wt += gemm_tiles(o.m, o.n);
+    const bool wide = wt >= big_wave;
     for (int kind : kinds)
       for (size_t p = 0; p < parts.size(); ++p) {
         if (w >= parts[p].waves->size()) continue;
         const Wave& W = (*parts[p].waves)[w];
-        for (size_t k = 0; k < count_of(W, kind); ++k) emit(p, W, kind, k);
+        for (size_t k = 0; k < count_of(W, kind); ++k) emit(p, W, kind, k, wide);
       }
     std::stable_sort(tasks.begin() + wb.back(), tasks.end(),
                      [&](const Task& x, const Task& y) { return prio[x.id] < prio[y.id]; });

@@ -22,7 +22,7 @@ struct GemmOp {
   const double* B;
   double* C;
   int m, n, k;
-  int shape;         // output tile: 0 = 32 x 32, 1 = 64 x 16, 2 = 16 x 64 (gemm_shape), | GEMM_FP64
+  int shape;         // output tile: 0 = 32 x 32, 1 = 64 x 16, 2 = 16 x 64 (gemm_shape), 3 = 64 x 64, | GEMM_FP64
   int64_t ars, acs, brs, bcs, crs, ccs;
   double alpha, beta;
 };

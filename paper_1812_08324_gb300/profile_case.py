@@ -4,7 +4,9 @@
 
 Builds the H-matrix of the 1D Levy generator workload (drift 0.3, sigma 0.2,
 alpha-stable alpha = 1.5 truncated to |y| <= 2, leaf 256, ACA rank <= 32,
-factor rank <= 16, dt = 1e-3) at N unknowns, factors I - dt/2 G, then runs
+factor rank <= 16, dt = 1e-3) at N unknowns (or, with --workload, of another
+named workload: a 2D fractional Laplacian on a grid of side sqrt(N)), factors
+I - dt/2 G, then runs
 one warm-up and `reps` timed repetitions of the chosen operation:
   matvec   y = x + dt/2 G x (H-matvec: vt_kernel, vt_reduce_kernel, rows_kernel)
   solve    z = (LU)^{-1} b (1D: the hierarchical inverses' products, hinv_t_kernel
@@ -32,6 +34,9 @@ from . import build, hmat, workloads as W
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--workload", default="levy_1d_n65536",
+                    help="named workload whose physics and options are used (1D Levy: N = --n; the 2D "
+                         "fractional Laplacian workloads: grid side sqrt(--n))")
     ap.add_argument("--what", choices=["matvec", "solve", "cn_step", "factor"], default="solve")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--solve", choices=["auto", "hinv", "subst"], default="auto",
@@ -42,8 +47,11 @@ def main() -> int:
 
     build.build()
     hmat.load()
-    prob = W.levy_1d(args.n)
-    _, opts, dt, _, kind = W.WORKLOADS["levy_1d_n65536"]
+    prob, opts, dt, _, kind = W.WORKLOADS[args.workload]
+    if prob["dim"] == 1:
+        prob = W.levy_1d(args.n) if args.workload.startswith("levy_1d") else dict(prob)
+    else:
+        prob = W.frac_lap_2d(int(round(args.n ** 0.5)), prob["s"])
     opts = dict(opts, lu_max_rank=16, lu_tol=1e-10, refine_max=0, solve=args.solve)
     H = hmat.HMatrix(prob, opts)
     F = H.factor(-0.5 * dt)

@@ -87,6 +87,29 @@ def test_factor_batch_in_many_small_launches_is_identical(monkeypatch):
         assert np.array_equal(x0, x1)
 
 
+def test_factor_with_64x64_gemm_tiles_is_identical(monkeypatch):
+    """GEMMs run as 64 x 64 output tiles (HM_GEMM_BIG_TILES=1 and
+    HM_GEMM_BIG_WAVE=0: every GEMM that is not narrow, in every wave) give the
+    same factors bit for bit as 32 x 32 tiles: every output sums its k terms
+    in the same order whatever the tile; 1D members and a 2D problem."""
+    batch = _small_batch(4) + [(W.frac_lap_2d(40, 0.6), W.default_opts(leaf=64, aca_tol=1e-8, max_rank=32,
+                                                                         lu_max_rank=16, refine_max=0))]
+    dt = W.LEVY_BATCH_DT
+    Hs = [hmat.HMatrix(p, o) for p, o in batch]
+    rng = np.random.default_rng(11)
+    bs = [dev(rng.standard_normal(H.n)) for H in Hs]
+    sols = []
+    for big in ("0", "1"):
+        monkeypatch.setenv("HM_GEMM_BIG_TILES", big)
+        monkeypatch.setenv("HM_GEMM_BIG_WAVE", "0")
+        Fs = hmat.factor_batch(Hs, [-0.5 * dt] * len(Hs))
+        sols.append([host(F.solve(b)) for F, b in zip(Fs, bs)])
+        for F in Fs:
+            F.free()
+    for x0, x1 in zip(*sols):
+        assert np.array_equal(x0, x1)
+
+
 def test_cn_solve_batch_equals_single_and_oracle():
     batch = _small_batch()
     dt, steps = W.LEVY_BATCH_DT, 20
