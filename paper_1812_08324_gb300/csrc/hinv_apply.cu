@@ -182,14 +182,29 @@ __device__ __forceinline__ void t_body(const HinvApply& H, int c, const double* 
   }
   __syncthreads();
   if (last) {
-    // warp per column, lanes over the chunks (fixed assignment and tree)
+    // warp per column, lanes over the chunks (fixed assignment and tree);
+    // four columns of a warp at a time, so that their partials' loads are in
+    // flight together (each column's sum keeps its order)
     const int nch = nd.tch_end - nd.tch_begin;
     const typename T::A* tp = static_cast<const typename T::A*>(H.tpart);
-    for (int l = warp; l < k; l += T_WARPS) {
-      typename T::A s = T::zero();
-      for (int cc = lane; cc < nch; cc += 32) s = T::add(s, ld_cg(tp + (int64_t)(nd.tch_begin + cc) * HINV_KCAP + l));
-      s = warp_sum<P>(s);
-      if (lane == 0) static_cast<typename T::A*>(H.tvec)[(int64_t)tc.x * HINV_KCAP + l] = s;
+    for (int l0 = warp; l0 < k; l0 += 4 * T_WARPS) {
+      typename T::A s[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] = T::zero();
+      for (int cc = lane; cc < nch; cc += 32) {
+        const typename T::A* row = tp + (int64_t)(nd.tch_begin + cc) * HINV_KCAP;
+        typename T::A v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = l0 + q * T_WARPS < k ? ld_cg(row + l0 + q * T_WARPS) : T::zero();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = T::add(s[q], v[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = l0 + q * T_WARPS;
+        const typename T::A r = warp_sum<P>(s[q]);
+        if (lane == 0 && l < k) static_cast<typename T::A*>(H.tvec)[(int64_t)tc.x * HINV_KCAP + l] = r;
+      }
     }
     if (threadIdx.x == 0) H.tcount[tc.x] = 0u;
   }
