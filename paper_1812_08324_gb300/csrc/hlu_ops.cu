@@ -131,7 +131,7 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
           for (int y = 0; y < RN; ++y) acc[x * RN + y] += a[x] * b[y];
       }
     }
-    __syncthreads();
+    if (k0 + GK < op.k) __syncthreads();  // the next chunk overwrites As, Bs
   }
 #pragma unroll
   for (int x = 0; x < RM; ++x)
@@ -145,7 +145,8 @@ __device__ void gemm_tile(const GemmOp& op, int local, double* smem, int* err) {
         *c = op.beta == 0.0 ? v : op.beta * (*c) + v;
       }
     }
-  __syncthreads();
+  // no barrier here: the executor's completion barrier follows every task
+  // before shared memory is written again
 }
 
 // op.shape: bits 0-1 the tile shape (gemm_shape; 3 = 64 x 64), bit 2 set = FP64 arithmetic
@@ -1265,7 +1266,11 @@ template <int MODE>
 __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(ExecArgs a) {
   constexpr bool SOLVE = !mode_factor(MODE);
   extern __shared__ double smem[];
-  __shared__ int next;
+  // the task index, in two slots used alternately: thread 0 writes the other
+  // slot next time, after barriers that every thread passes only once it has
+  // read this one, so no barrier is needed between the read and the next write
+  __shared__ int next[2];
+  int slot = 0;
   // descriptor of the current op (factorisation), copied before the wait
   __shared__ union OpDesc {
     int w[1];
@@ -1276,10 +1281,10 @@ __global__ void __launch_bounds__(EXEC_THREADS, mode_ctas(MODE)) exec_kernel(Exe
     ReduceOp reduce;
   } opdesc;
   for (;;) {
-    if (threadIdx.x == 0) next = atomicAdd(a.grab, 1);
+    if (threadIdx.x == 0) next[slot] = atomicAdd(a.grab, 1);
     __syncthreads();
-    const int t = next;
-    __syncthreads();
+    const int t = next[slot];
+    slot ^= 1;
     if (t >= a.ntasks) return;
     const Task T = a.tasks[t];
     if (a.trace && threadIdx.x == 0) {
