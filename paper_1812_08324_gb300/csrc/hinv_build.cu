@@ -214,13 +214,14 @@ __device__ __forceinline__ void dd_mac(float2& s, float2 a, float2 b) {
 
 constexpr int DD_JB = 32;  // rows of the input staged per block
 
+template <int SC>
 __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* __restrict__ in) {
   __shared__ float2 xs[DD_JB][HINV_MAXS];
   __shared__ int last;
   const int2 rc = P.rch[blockIdx.x];
   const MrRed R = P.reds[rc.x];
   const int k = R.rank ? *R.rank : R.kc;
-  const int S = P.S;
+  constexpr int S = SC, NQ = SC / 8;  // columns per thread: NQ, all live
   const int j0 = rc.y, len = min(HINV_MCH, R.n - j0);
   const int g = threadIdx.x & 7, lg = threadIdx.x >> 3;
   const float2 z = make_float2(0.f, 0.f);
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* 
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[a][q] = z;
+    for (int q = 0; q < NQ; ++q) acc[a][q] = z;
   const bool l0 = lg < k, l1 = lg + 32 < k;
   bool bad = false;
   for (int jb = 0; jb < len; jb += DD_JB) {
@@ -255,9 +256,9 @@ __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* 
           const float2 v0 = df_split(w0[u], bad);
           const float2 v1 = l1 ? df_split(w1[u], bad) : z;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < NQ; ++q) {
             const int c = g + 8 * q;
-            if (c < S) {
+            {
               dd_mac(acc[0][q], v0, xs[jq + u][c]);
               if (l1) dd_mac(acc[1][q], v1, xs[jq + u][c]);
             }
@@ -268,9 +269,9 @@ __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* 
   }
   double* part = P.partial + (int64_t)blockIdx.x * MR_T;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     const int c = g + 8 * q;
-    if (c < S) {
+    {
       if (l0) part[lg * S + c] = (double)acc[0][q].x + (double)acc[0][q].y;
       if (l1) part[(lg + 32) * S + c] = (double)acc[1][q].x + (double)acc[1][q].y;
     }
@@ -290,19 +291,20 @@ __global__ void __launch_bounds__(256) mr_red_dd_kernel(MrPlan P, const double* 
   if (threadIdx.x == 0) P.count[rc.x] = 0u;
 }
 
+template <int SC>
 __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* __restrict__ in,
                                                          double* __restrict__ out) {
   constexpr int JB = 64;
   __shared__ float2 xs[JB][HINV_MAXS];
   const MrChunk C = P.chunks[blockIdx.x];
-  const int S = P.S;
+  constexpr int S = SC, NQ = SC / 8;  // columns per thread: NQ, all live
   const int g = threadIdx.x & 7, r = threadIdx.x >> 3;
   const int row = C.r0 + r;
   const bool live = r < C.nr;
   const float2 z = make_float2(0.f, 0.f);
   float2 acc[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = z;
+  for (int q = 0; q < NQ; ++q) acc[q] = z;
   bool bad = false;
   for (int it = C.ib; it < C.ie; ++it) {
     const MrItem I = P.items[it];
@@ -336,9 +338,9 @@ __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* 
               if (j0 + u >= jb + nb) break;
               const float2 a = df_split(av[u], bad);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
+              for (int q = 0; q < NQ; ++q) {
                 const int c = g + 8 * q;
-                if (c < S) dd_mac(acc[q], a, xs[j0 + u - jb][c]);
+                dd_mac(acc[q], a, xs[j0 + u - jb][c]);
               }
             }
           }
@@ -366,9 +368,9 @@ __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* 
               if (l0 + w >= lb + nb) break;
               const float2 u = df_split(uv[w], bad);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
+              for (int q = 0; q < NQ; ++q) {
                 const int c = g + 8 * q;
-                if (c < S) dd_mac(acc[q], u, xs[l0 + w - lb][c]);
+                dd_mac(acc[q], u, xs[l0 + w - lb][c]);
               }
             }
           }
@@ -378,9 +380,9 @@ __global__ void __launch_bounds__(256) mr_row_dd_kernel(MrPlan P, const double* 
   }
   if (live) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       const int c = g + 8 * q;
-      if (c < S) out[(int64_t)row * S + c] = (double)acc[q].x + (double)acc[q].y;
+      out[(int64_t)row * S + c] = (double)acc[q].x + (double)acc[q].y;
     }
   }
 }
@@ -585,6 +587,8 @@ struct HostMr {
   int ch0 = 0, nch = 0;        // into all chunks
   int it0 = 0;                 // into all items
 };
+
+static_assert(HINV_S % 8 == 0 && HINV_SP % 8 == 0 && HINV_SP <= HINV_MAXS, "multi-vector widths: whole groups of 8");
 
 struct Planner {
   std::vector<MrRed> reds;
@@ -1153,12 +1157,14 @@ int build_group(std::vector<Ctx>& G, int* d_err, cudaStream_t st, std::string& e
     if (h.nrch > 0) {
       count_launches(1);
       if (build_fp64) mr_red_kernel<<<h.nrch, 256, 0, st>>>(M, in);
-      else mr_red_dd_kernel<<<h.nrch, 256, 0, st>>>(M, in);
+      else if (h.S == HINV_S) mr_red_dd_kernel<HINV_S><<<h.nrch, 256, 0, st>>>(M, in);
+      else mr_red_dd_kernel<HINV_SP><<<h.nrch, 256, 0, st>>>(M, in);
     }
     if (h.nch > 0 && o) {
       count_launches(1);
       if (build_fp64) mr_row_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
-      else mr_row_dd_kernel<<<h.nch, 256, 0, st>>>(M, in, o);
+      else if (h.S == HINV_S) mr_row_dd_kernel<HINV_S><<<h.nch, 256, 0, st>>>(M, in, o);
+      else mr_row_dd_kernel<HINV_SP><<<h.nch, 256, 0, st>>>(M, in, o);
     }
   };
   for (size_t k = 0; k < steps.size(); ++k) {
