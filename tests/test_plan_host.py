@@ -277,3 +277,21 @@ def test_autotune_search_space_per_precision_and_dimension():
     assert c2 == [{"leaf": 64, "solve": "subst", "solve_block": 1024}]
     with pytest.raises(ValueError):
         autotune.configurations(p2, W.default_opts(leaf=64, precision="mixed_fp32"), leafs=(64,))
+
+
+def test_plan_histogram_counts_every_op(monkeypatch, capfd):
+    """HM_PLAN_HIST=1 prints the planned H-LU's tasks by op kind; the op
+    counts it reports add up to the dry run's fact_ops, and the GEMM task
+    count is at least the GEMM op count (one or more 32 x 32 tiles each)."""
+    prob, opts, dt, steps, kind = W.WORKLOADS["frac_lap_1d_n1023"]
+    monkeypatch.setenv("HM_PLAN_HIST", "1")
+    info = hmat.plan_factor(prob, dict(opts, lu_max_rank=16, max_rank=16), -0.5 * dt)
+    err = capfd.readouterr().err
+    rows = {}
+    for line in err.splitlines():
+        m = re.match(r"\[plan\] (\w+)\s+(\d+) ops\s+(\d+) tasks", line)
+        if m:
+            rows[m.group(1)] = (int(m.group(2)), int(m.group(3)))
+    assert set(rows) == {"gemm", "lu", "trunc", "copy", "reduce"}
+    assert sum(o for o, _ in rows.values()) == info["fact_ops"]
+    assert rows["gemm"][1] >= rows["gemm"][0] > 0 and rows["lu"][0] > 0
