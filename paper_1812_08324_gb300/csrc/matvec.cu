@@ -281,7 +281,7 @@ __global__ void vt_reduce_kernel(MatvecPlan P) {
   if ((int)blockIdx.x < P.nlr) vt_reduce_body(P, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 rows_kernel(MatvecPlan P, double alpha, double beta, const double* __restrict__ x, double gamma, const double* w1,
             const double* w2, const double* w3, double* y) {
   if (P.Ddf) rows_df_body(P, blockIdx.x, alpha, beta, x, gamma, w1, w2, w3, y);
@@ -311,7 +311,7 @@ __global__ void vt_reduce_batch_kernel(const MvJob* jobs, const int* off, int co
   vt_reduce_body(jobs[j].P, blockIdx.x - off[j]);
 }
 
-__global__ void __launch_bounds__(256, 3) rows_batch_kernel(const MvJob* jobs, const int* off, int count) {
+__global__ void __launch_bounds__(256, 4) rows_batch_kernel(const MvJob* jobs, const int* off, int count) {
   const int j = batch_job(off, count, blockIdx.x);
   const MvJob& J = jobs[j];
   if (J.P.Ddf) rows_df_body(J.P, blockIdx.x - off[j], J.alpha, J.beta, J.x, J.gamma, J.w1, J.w2, J.w3, J.y);
