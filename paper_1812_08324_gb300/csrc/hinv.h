@@ -128,15 +128,12 @@ struct HinvData {
   void release();
 };
 
-// Form the inverses of the factors in F (1D plans only).  Ranks of the factor
-// blocks on the device in d_rank_f.  Synchronises the stream at the end.
-int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
-               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err);
-
-// The same for several factorisations at once: the construction steps of all
-// of them (in groups of at most 2^19 stacked rows) run in one launch per
-// kernel and step.  Each out receives what hinv_build would give it, bit for
-// bit; build_ms is the time of the whole call.  d_err collects device errors.
+// Form the inverses of the factors of one or more factorisations (1D plans
+// only; the ranks of each factor's blocks on the device in d_rank_f).  The
+// construction steps of all of them (in groups of at most 2^19 stacked rows)
+// run in one launch per kernel and step; each out receives the same inverses,
+// bit for bit, as when built alone.  build_ms is the time of the whole call;
+// d_err collects device errors.  Synchronises the stream.
 struct HinvBuildJob {
   const Plan* P;
   const std::vector<DenseDesc>* dd;

@@ -1403,13 +1403,6 @@ int hinv_build_batch(const std::vector<HinvBuildJob>& jobs, int* d_err, cudaStre
   return HM_OK;
 }
 
-int hinv_build(const Plan& P, const std::vector<DenseDesc>& dd, const FactorLayout& F, const int* d_rank_f,
-               int prec, double tol, int* d_err, cudaStream_t st, HinvData& out, std::string& err) {
-  std::vector<HinvBuildJob> jobs(1);
-  jobs[0] = HinvBuildJob{&P, &dd, &F, d_rank_f, prec, tol, &out};
-  return hinv_build_batch(jobs, d_err, st, err);
-}
-
 int hinv_solve(const HinvData& D, const double* b, double* z, cudaStream_t st) {
   HM_TRY(launch_hinv_apply(D.tri[0].A, b, D.d_y, st));
   return launch_hinv_apply(D.tri[1].A, D.d_y, z, st);
